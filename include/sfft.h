@@ -1,0 +1,152 @@
+/*
+ * sfft.h - C ABI of the GB300 (sm_103a) difference-imaging library.
+ *
+ * The library fits a science CCD S against its aligned reference R with the
+ * model used by the paper's image-differencing step (Sec. 2.3.2, with the
+ * method as introduced in Sec. 1: a Fourier-domain formulation with a
+ * delta-function kernel basis that follows spatial PSF variations):
+ *
+ *     S'(x) ~ sum_j K_j(x) R~(x - u_j) + B'(x),
+ *     K_j(x) = sum_p theta[j N_K + p] phi_p(x),
+ *     B'(x)  = sum_q theta[L^2 N_K + q] psi_q(x),
+ *
+ * with u_j the L x L offsets (j = (u_y + w) L + (u_x + w), w = (L-1)/2),
+ * phi_p (psi_q) the monomials xt^a yt^b of total degree <= D_K (D_B) in
+ * xt = 2x/(W-1) - 1, yt = 2y/(H-1) - 1, ordered by degree and, within a
+ * degree, by decreasing a; N_K = (D_K+1)(D_K+2)/2, N_B likewise, and
+ * N = L^2 N_K + N_B unknowns.  The fit minimises
+ * sum_x M_fit(x) [S'(x) - model(x)]^2 where M_fit is 1 on pixels at least w
+ * from every edge whose whole L x L footprint is good; bad pixels are
+ * bad[x] != 0, non-finite R or non-finite S.  R_m = good ? R - s_R : 0 and
+ * S' = S - s_S with sky constants (s_R, s_S).
+ *
+ * Conventions shared by every entry point:
+ *  - Images are row-major [batch][H][W] (row y, column x), batch stride H*W.
+ *  - All image, matrix and status pointers are DEVICE pointers unless stated.
+ *    The caller owns every buffer; the library never frees them.
+ *  - Every call is asynchronous on the plan's stream: it enqueues kernels and
+ *    returns.  Argument and shape errors are returned synchronously; data
+ *    errors (singular or non-finite system, wait time-out) are written per CCD
+ *    into the device `info` array and never trap.
+ *  - No call allocates device memory after sfft_plan; scratch lives in the
+ *    caller-allocated workspace `ws` of sfft_workspace_bytes() bytes (256-byte
+ *    aligned).  A workspace must not be shared by calls that overlap on the GPU.
+ *  - Requirements: L odd, 1 <= L <= 11; 0 <= D_K <= D_B <= 2 (D_B >= D_K makes
+ *    the sky offsets exactly absorbed by the background); H >= L; 16 <= W <= 2048.
+ *
+ * The paper gives no equations for the fit; the exact definition above, the
+ * mask and sky-offset semantics and the polynomial coordinates are this
+ * library's reading of it.
+ */
+#ifndef SFFT_GB300_H
+#define SFFT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sfft_plan_s* sfft_plan_t;
+
+typedef enum {
+  SFFT_OK = 0,
+  SFFT_ERR_ARG = 1,          /* invalid argument or shape (returned synchronously) */
+  SFFT_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  SFFT_ERR_NOMEM = 3,        /* plan-time host or device allocation failed */
+  SFFT_ERR_SINGULAR = 4,     /* per-CCD info: normal matrix not positive definite */
+  SFFT_ERR_NONFINITE = 5,    /* per-CCD info: non-finite normal matrix or solution */
+  SFFT_ERR_TIMEOUT = 6,      /* per-CCD info: a bounded device wait gave up */
+  SFFT_ERR_UNSUPPORTED = 7   /* shape or degree outside the supported range */
+} sfft_status_t;
+
+typedef enum {
+  SFFT_PREC_FP64 = 0,        /* FFTs, products, partial sums and apply in FP64 */
+  SFFT_PREC_MIXED = 1        /* FP32 FFTs/products/partials; FP64 accumulation, solve, refinement */
+} sfft_prec_t;
+
+#define SFFT_FLAG_GRAPH 1u   /* sfft_subtract replays a captured CUDA graph */
+
+typedef struct {
+  int32_t H, W;              /* image rows, columns */
+  int32_t L;                 /* kernel size (odd) */
+  int32_t DK, DB;            /* kernel / background polynomial degrees */
+  int32_t batch;             /* CCD pairs per call */
+  int32_t prec;              /* sfft_prec_t */
+  int32_t autotune;          /* 1: time contraction tile shapes at plan time and keep the fastest */
+  int32_t d_batch;           /* kernel-offset differences per product/FFT pass (0 = auto) */
+  int32_t rows_per_cta;      /* rows of one contraction partial sum (0 = auto) */
+  uint32_t flags;            /* SFFT_FLAG_* */
+} sfft_desc_t;
+
+/* Create a plan: validates the descriptor, builds offset/monomial/lag tables,
+ * allocates the plan's small constant device tables (twiddles) and, with
+ * autotune=1, times contraction tile shapes on synthetic data in its own
+ * temporary buffers.  `cuda_stream` is a cudaStream_t (NULL = legacy default
+ * stream).  On success *out owns the plan; release with sfft_plan_destroy. */
+sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, sfft_plan_t* out);
+void          sfft_plan_destroy(sfft_plan_t plan);
+sfft_status_t sfft_plan_set_stream(sfft_plan_t plan, void* cuda_stream);
+int64_t       sfft_num_unknowns(sfft_plan_t plan);          /* N */
+size_t        sfft_workspace_bytes(sfft_plan_t plan);       /* bytes for `ws` */
+/* Chosen tile shape after planning: out[0] = d_batch, out[1] = rows_per_cta,
+ * out[2] = k-slots per CTA. */
+sfft_status_t sfft_plan_tiles(sfft_plan_t plan, int32_t* out3);
+
+/* Normal-matrix assembly (the method's Fourier-domain normal equations):
+ *   A = sum_x M_fit Phi Phi^T,  b = sum_x M_fit Phi S'   (FP64 outputs)
+ * KK block: for every kernel-offset difference d = u - u' and weight monomial
+ * xt^a yt^b, the row-FFT cross-correlation of the masked product
+ * R_m(z) R_m(z + d) with M_fit xt^a yt^b, sampled at the lags u; KB block and
+ * b_K: the same with R_m against M_fit phi_p psi_q and M_fit phi_p S'; BB and
+ * b_B: moments of M_fit.
+ *   R, S : float [batch][H][W];  bad : uint8 [batch][H][W] or NULL (no mask);
+ *   sky  : double [batch][2] = (s_R, s_S), or NULL to estimate each as the
+ *          mean of the good pixels (any constant gives the same kernel and D
+ *          away from non-finite pixels and the w-pixel border);
+ *   A    : double [batch][N][N] (written fully, symmetric);  b : double [batch][N];
+ *   ws   : workspace; keeps the masks, spectra and sky for sfft_solve/apply. */
+sfft_status_t sfft_build_normal(sfft_plan_t plan, const float* R, const float* S,
+                                const uint8_t* bad, const double* sky,
+                                double* A, double* b, void* ws);
+
+/* Solve A theta = b per CCD in FP64: Jacobi equilibration, Cholesky, two
+ * triangular solves; then `refine_steps` steps of iterative refinement whose
+ * residual r = sum_x M_fit Phi (S' - model) is formed in image space from R
+ * and S.  theta : double [batch][N]; its background part is returned in
+ * original (un-offset) units, B = B' + s_S - s_R sum_j K_j.  info : int32
+ * [batch] (device) receives SFFT_OK / SFFT_ERR_SINGULAR / SFFT_ERR_NONFINITE.
+ * Must follow sfft_build_normal with the same ws, R, S and bad. */
+sfft_status_t sfft_solve(sfft_plan_t plan, const double* A, const double* b, double* theta,
+                         int32_t refine_steps, const float* R, const float* S,
+                         const uint8_t* bad, int32_t* info, void* ws);
+
+/* Difference image D = S - K (x) R - B over every pixel, evaluated as
+ * S' - sum_p phi_p sum_j theta[j,p] R~(x - u_j) - B'(x) with
+ * R~ = finite(R) ? R - s_R : 0 and zero outside the image.
+ * theta : double [batch][N] (background in original units, as sfft_solve
+ * returns it); sky : double [batch][2] or NULL to reuse the workspace's sky
+ * from sfft_build_normal; D : float [batch][H][W]. */
+sfft_status_t sfft_apply(sfft_plan_t plan, const float* R, const float* S, const double* theta,
+                         const double* sky, float* D, void* ws);
+
+/* build_normal + solve (refine_steps) + apply in one call; with
+ * SFFT_FLAG_GRAPH the enqueued work is captured once per distinct argument
+ * set and replayed as a CUDA graph. */
+sfft_status_t sfft_subtract(sfft_plan_t plan, const float* R, const float* S, const uint8_t* bad,
+                            const double* sky, int32_t refine_steps, double* A, double* b,
+                            double* theta, int32_t* info, float* D, void* ws);
+
+/* Kernel coefficient maps for inspection: K[ccd][j] at pixel (x, y) of every
+ * CCD, from theta (device) into K (device, double [batch][L*L]). */
+sfft_status_t sfft_kernel_at(sfft_plan_t plan, const double* theta, double x, double y, double* K);
+
+const char* sfft_status_str(sfft_status_t s);
+/* Last CUDA error text seen by the library on this thread ("" if none). */
+const char* sfft_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFFT_GB300_H */

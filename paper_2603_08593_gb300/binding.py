@@ -1,0 +1,184 @@
+"""ctypes binding over the C ABI in include/sfft.h.
+
+Argument marshalling only: every step of the subtraction runs in the CUDA
+kernels of libsfft_gb300.so.  PyTorch provides device memory and the stream.
+There is no CPU fallback: loading fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libsfft_gb300.so")
+
+SFFT_OK, SFFT_ERR_ARG, SFFT_ERR_CUDA, SFFT_ERR_NOMEM = 0, 1, 2, 3
+SFFT_ERR_SINGULAR, SFFT_ERR_NONFINITE, SFFT_ERR_TIMEOUT, SFFT_ERR_UNSUPPORTED = 4, 5, 6, 7
+PREC = {"fp64": 0, "mixed": 1}
+FLAG_GRAPH = 1
+
+
+class Desc(C.Structure):
+    _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("L", C.c_int32), ("DK", C.c_int32), ("DB", C.c_int32),
+                ("batch", C.c_int32), ("prec", C.c_int32), ("autotune", C.c_int32), ("d_batch", C.c_int32),
+                ("rows_per_cta", C.c_int32), ("flags", C.c_uint32)]
+
+
+VP, I32, I64, SZ, DBL = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t, C.c_double
+
+# name -> (restype, argtypes); every symbol declared in include/*.h
+SIGNATURES = {
+    "sfft_plan": (I32, [C.POINTER(Desc), VP, C.POINTER(VP)]),
+    "sfft_plan_destroy": (None, [VP]),
+    "sfft_plan_set_stream": (I32, [VP, VP]),
+    "sfft_num_unknowns": (I64, [VP]),
+    "sfft_workspace_bytes": (SZ, [VP]),
+    "sfft_plan_tiles": (I32, [VP, C.POINTER(I32)]),
+    "sfft_build_normal": (I32, [VP, VP, VP, VP, VP, VP, VP, VP]),
+    "sfft_solve": (I32, [VP, VP, VP, VP, I32, VP, VP, VP, VP, VP]),
+    "sfft_apply": (I32, [VP, VP, VP, VP, VP, VP, VP]),
+    "sfft_subtract": (I32, [VP, VP, VP, VP, VP, I32, VP, VP, VP, VP, VP, VP]),
+    "sfft_kernel_at": (I32, [VP, VP, DBL, DBL, VP]),
+    "sfft_status_str": (C.c_char_p, [I32]),
+    "sfft_last_error": (C.c_char_p, []),
+}
+
+_LIB = None
+
+
+class SfftError(RuntimeError):
+    pass
+
+
+def load(path=LIB_PATH):
+    """Load the shared library (once).  Raises if it has not been built."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise SfftError(f"{path} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(st, what):
+    if st != SFFT_OK:
+        lib = load()
+        msg = lib.sfft_status_str(st).decode()
+        err = lib.sfft_last_error().decode()
+        raise SfftError(f"{what}: {msg} ({st}) {err}")
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A subtraction plan plus its workspace (a torch uint8 device tensor)."""
+
+    def __init__(self, H, W, L, DK, DB, batch=1, prec="mixed", d_batch=0, rows_per_cta=0, autotune=0,
+                 graph=False, stream=None, device=None):
+        import torch
+        self._torch = torch
+        lib = load()
+        self.lib = lib
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.desc = Desc(H, W, L, DK, DB, batch, PREC[prec], autotune, d_batch, rows_per_cta,
+                         FLAG_GRAPH if graph else 0)
+        h = VP()
+        with torch.cuda.device(self.device):
+            _check(lib.sfft_plan(C.byref(self.desc), VP(self.stream.cuda_stream), C.byref(h)), "sfft_plan")
+        self.h = h
+        self.H, self.W, self.L, self.DK, self.DB, self.batch = H, W, L, DK, DB, batch
+        self.N = int(lib.sfft_num_unknowns(h))
+        self.ws_bytes = int(lib.sfft_workspace_bytes(h))
+        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.ws.data_ptr()) % 256
+        self.ws_view = self.ws[off:off + self.ws_bytes]
+        t = (I32 * 3)()
+        _check(lib.sfft_plan_tiles(h, t), "sfft_plan_tiles")
+        self.tiles = tuple(int(v) for v in t)
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                self.lib.sfft_plan_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self.stream = stream
+        _check(self.lib.sfft_plan_set_stream(self.h, VP(stream.cuda_stream)), "sfft_plan_set_stream")
+
+    # -- helpers
+    def _f64(self, *shape):
+        return self._torch.empty(*shape, dtype=self._torch.float64, device=self.device)
+
+    def _check_img(self, x, dtype):
+        t = self._torch
+        if x is None:
+            return None
+        if x.device != self.device or x.dtype != dtype or not x.is_contiguous():
+            raise ValueError(f"expected a contiguous {dtype} tensor on {self.device}")
+        if x.numel() != self.batch * self.H * self.W:
+            raise ValueError("image shape does not match the plan")
+        return x
+
+    # -- entry points
+    def build_normal(self, R, S, bad=None, sky=None, A=None, b=None):
+        t = self._torch
+        R = self._check_img(R, t.float32)
+        S = self._check_img(S, t.float32)
+        bad = self._check_img(bad, t.uint8)
+        A = A if A is not None else self._f64(self.batch, self.N, self.N)
+        b = b if b is not None else self._f64(self.batch, self.N)
+        st = self.lib.sfft_build_normal(self.h, _ptr(R), _ptr(S), _ptr(bad), _ptr(sky), _ptr(A), _ptr(b),
+                                        _ptr(self.ws_view))
+        _check(st, "sfft_build_normal")
+        return A, b
+
+    def solve(self, A, b, R=None, S=None, bad=None, refine=1, theta=None, info=None):
+        t = self._torch
+        theta = theta if theta is not None else self._f64(self.batch, self.N)
+        info = info if info is not None else t.empty(self.batch, dtype=t.int32, device=self.device)
+        st = self.lib.sfft_solve(self.h, _ptr(A), _ptr(b), _ptr(theta), int(refine), _ptr(R), _ptr(S), _ptr(bad),
+                                 _ptr(info), _ptr(self.ws_view))
+        _check(st, "sfft_solve")
+        return theta, info
+
+    def apply(self, R, S, theta, sky=None, D=None):
+        t = self._torch
+        D = D if D is not None else t.empty(self.batch, self.H, self.W, dtype=t.float32, device=self.device)
+        st = self.lib.sfft_apply(self.h, _ptr(R), _ptr(S), _ptr(theta), _ptr(sky), _ptr(D), _ptr(self.ws_view))
+        _check(st, "sfft_apply")
+        return D
+
+    def subtract(self, R, S, bad=None, sky=None, refine=1, out=None):
+        """build_normal + solve + apply; `out` may carry preallocated A, b, theta, info, D."""
+        t = self._torch
+        R = self._check_img(R, t.float32)
+        S = self._check_img(S, t.float32)
+        bad = self._check_img(bad, t.uint8)
+        o = dict(out) if out else {}
+        o.setdefault("A", self._f64(self.batch, self.N, self.N))
+        o.setdefault("b", self._f64(self.batch, self.N))
+        o.setdefault("theta", self._f64(self.batch, self.N))
+        o.setdefault("info", t.empty(self.batch, dtype=t.int32, device=self.device))
+        o.setdefault("D", t.empty(self.batch, self.H, self.W, dtype=t.float32, device=self.device))
+        st = self.lib.sfft_subtract(self.h, _ptr(R), _ptr(S), _ptr(bad), _ptr(sky), int(refine), _ptr(o["A"]),
+                                    _ptr(o["b"]), _ptr(o["theta"]), _ptr(o["info"]), _ptr(o["D"]),
+                                    _ptr(self.ws_view))
+        _check(st, "sfft_subtract")
+        return o
+
+    def kernel_at(self, theta, x, y):
+        K = self._f64(self.batch, self.L * self.L)
+        _check(self.lib.sfft_kernel_at(self.h, _ptr(theta), float(x), float(y), _ptr(K)), "sfft_kernel_at")
+        return K.view(self.batch, self.L, self.L)

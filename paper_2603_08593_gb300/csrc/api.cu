@@ -1,0 +1,426 @@
+// C ABI: plan construction, workspace layout, contraction job tables and the
+// entry points that enqueue the kernels on the plan's stream.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "plan.h"
+
+using namespace sfft;
+
+static thread_local std::string g_last_error;
+
+static sfft_status_t cuda_fail(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return SFFT_ERR_CUDA;
+}
+#define CK(call)                                          \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+  } while (0)
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static void add_region(Region& r, size_t& cursor, size_t bytes) {
+  r.off = cursor;
+  r.bytes = bytes;
+  cursor = align256(cursor + bytes);
+}
+
+static int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+template <typename T2, typename R>
+static void fill_twiddles(sfft_plan_s* p, std::vector<T2>& twM, std::vector<T2>& twN, std::vector<T2>& twD) {
+  const double pi = 3.14159265358979323846;
+  twM.resize((size_t)p->N2 * 32);
+  for (int k2 = 0; k2 < p->N2; ++k2)
+    for (int n1 = 0; n1 < 32; ++n1) {
+      const double ang = -2.0 * pi * (double)((int64_t)n1 * k2 % p->M) / (double)p->M;
+      twM[(size_t)k2 * 32 + n1] = T2{(R)cos(ang), (R)sin(ang)};
+    }
+  twN.resize(p->M);
+  for (int k = 0; k < p->M; ++k) {
+    const double ang = -2.0 * pi * (double)k / (double)p->Nf;
+    twN[k] = T2{(R)cos(ang), (R)sin(ang)};
+  }
+  twD.resize(p->Nf);
+  for (int j = 0; j < p->Nf; ++j) {
+    const double ang = 2.0 * pi * (double)j / (double)p->Nf;
+    twD[j] = T2{(R)cos(ang), (R)sin(ang)};
+  }
+}
+
+static void build_layout(sfft_plan_s* p) {
+  const int64_t H = p->d.H, W = p->d.W, B = p->d.batch, M = p->M;
+  const size_t e = p->elem, c = 2 * p->elem;
+  const size_t npx = (size_t)H * W;
+  const size_t slab = (size_t)H * M * c;
+  const int LL = p->d.L * p->d.L;
+  size_t cur = 0;
+  add_region(p->status, cur, sizeof(int) * B);
+  add_region(p->sky, cur, sizeof(double) * 2 * B);
+  add_region(p->skyacc, cur, sizeof(double) * 4 * B);
+  add_region(p->good, cur, npx * B);
+  add_region(p->gh, cur, npx * B);
+  add_region(p->mfit, cur, npx * B);
+  add_region(p->rowflag, cur, sizeof(int) * H * B);
+  add_region(p->rm, cur, npx * e * B);
+  add_region(p->eimg, cur, npx * e * B);
+  add_region(p->wspec, cur, slab * p->n_wa * B);
+  add_region(p->uspec, cur, slab * (p->d.DK + 1) * B);
+  add_region(p->rhat, cur, slab * B);
+  add_region(p->phat, cur, slab * p->d_batch * B);
+  add_region(p->gkk, cur, sizeof(double) * p->n_hd * LL * n_mono(p->DM_KK) * B);
+  add_region(p->gkb, cur, sizeof(double) * LL * n_mono(p->DM_KB) * B);
+  add_region(p->gbk, cur, sizeof(double) * LL * n_mono(p->DM_bK) * B);
+  add_region(p->mom_bb, cur, sizeof(double) * n_mono(p->DM_BB) * B);
+  add_region(p->mom_b, cur, sizeof(double) * n_mono(p->d.DB) * B);
+  add_region(p->lfac, cur, sizeof(double) * p->N * p->N * B);
+  add_region(p->scale, cur, sizeof(double) * p->N * B);
+  add_region(p->vec, cur, sizeof(double) * 4 * p->N * B);
+  add_region(p->theta_off, cur, sizeof(double) * p->N * B);
+  p->ws_bytes = cur;
+}
+
+static void build_jobs(sfft_plan_s* p) {
+  const int L = p->d.L, w = p->w, B = p->d.batch, H = p->d.H;
+  const int LL = L * L;
+  const int MU = p->fp64 ? 6 : 11;
+  const size_t slab = (size_t)H * p->M * 2 * p->elem;
+  auto push_split = [&](CJob j) {
+    for (int lo = j.uy_lo; lo <= j.uy_hi; lo += MU) {
+      CJob q = j;
+      q.uy_lo = lo;
+      q.uy_hi = std::min(j.uy_hi, lo + MU - 1);
+      p->h_jobs.push_back(q);
+    }
+  };
+  p->h_jobs.clear();
+  p->kk_first.clear();
+  p->kk_count.clear();
+  for (int d0 = 0; d0 < p->n_hd; d0 += p->d_batch) {
+    const int nd = std::min(p->d_batch, p->n_hd - d0);
+    p->kk_first.push_back((int)p->h_jobs.size());
+    for (int ccd = 0; ccd < B; ++ccd)
+      for (int i = 0; i < nd; ++i) {
+        const int2 d = p->dlist[d0 + i];
+        CJob j;
+        j.probe = (int64_t)(p->phat.off + ((size_t)ccd * p->d_batch + i) * slab);
+        j.wts = (int64_t)(p->wspec.off + (size_t)ccd * p->n_wa * slab);
+        j.out = (int64_t)(p->gkk.off + sizeof(double) * ((size_t)ccd * p->n_hd + d0 + i) * LL * n_mono(p->DM_KK));
+        j.rowflag = (int64_t)(p->rowflag.off + sizeof(int) * (size_t)ccd * H);
+        j.uy_lo = std::max(-w, d.x - w);
+        j.uy_hi = std::min(w, d.x + w);
+        j.ux_lo = std::max(-w, d.y - w);
+        j.ux_hi = std::min(w, d.y + w);
+        push_split(j);
+      }
+    p->kk_count.push_back((int)p->h_jobs.size() - p->kk_first.back());
+  }
+  p->kb_first = (int)p->h_jobs.size();
+  for (int ccd = 0; ccd < B; ++ccd) {
+    CJob j;
+    j.probe = (int64_t)(p->rhat.off + (size_t)ccd * slab);
+    j.wts = (int64_t)(p->wspec.off + (size_t)ccd * p->n_wa * slab);
+    j.out = (int64_t)(p->gkb.off + sizeof(double) * (size_t)ccd * LL * n_mono(p->DM_KB));
+    j.rowflag = (int64_t)(p->rowflag.off + sizeof(int) * (size_t)ccd * H);
+    j.uy_lo = -w; j.uy_hi = w; j.ux_lo = -w; j.ux_hi = w;
+    push_split(j);
+  }
+  p->kb_count = (int)p->h_jobs.size() - p->kb_first;
+  p->bk_first = (int)p->h_jobs.size();
+  for (int ccd = 0; ccd < B; ++ccd) {
+    CJob j;
+    j.probe = (int64_t)(p->rhat.off + (size_t)ccd * slab);
+    j.wts = (int64_t)(p->uspec.off + (size_t)ccd * (p->d.DK + 1) * slab);
+    j.out = (int64_t)(p->gbk.off + sizeof(double) * (size_t)ccd * LL * n_mono(p->DM_bK));
+    j.rowflag = (int64_t)(p->rowflag.off + sizeof(int) * (size_t)ccd * H);
+    j.uy_lo = -w; j.uy_hi = w; j.ux_lo = -w; j.ux_hi = w;
+    push_split(j);
+  }
+  p->bk_count = (int)p->h_jobs.size() - p->bk_first;
+}
+
+static void free_plan_device(sfft_plan_s* p) {
+  if (p->twM) cudaFree(p->twM);
+  if (p->twN) cudaFree(p->twN);
+  if (p->twD) cudaFree(p->twD);
+  if (p->d_dlist) cudaFree(p->d_dlist);
+  if (p->d_hdidx) cudaFree(p->d_hdidx);
+  if (p->d_jobs) cudaFree(p->d_jobs);
+  for (auto& kv : p->graphs) cudaGraphExecDestroy(kv.second);
+  p->graphs.clear();
+}
+
+template <typename T>
+static sfft_status_t upload(void** dst, const std::vector<T>& v) {
+  const size_t bytes = sizeof(T) * std::max<size_t>(v.size(), 1);
+  cudaError_t e = cudaMalloc(dst, bytes);
+  if (e != cudaSuccess) { g_last_error = cudaGetErrorString(e); return SFFT_ERR_NOMEM; }
+  if (!v.empty()) CK(cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  return SFFT_OK;
+}
+
+extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, sfft_plan_t* out) {
+  if (!desc || !out) return SFFT_ERR_ARG;
+  *out = nullptr;
+  const sfft_desc_t d = *desc;
+  if (d.H <= 0 || d.W <= 0 || d.batch <= 0 || d.L <= 0) return SFFT_ERR_ARG;
+  if (d.prec != SFFT_PREC_FP64 && d.prec != SFFT_PREC_MIXED) return SFFT_ERR_ARG;
+  if (d.DK < 0 || d.DB < 0 || d.d_batch < 0 || d.rows_per_cta < 0) return SFFT_ERR_ARG;
+  if ((d.L & 1) == 0 || d.L > kMaxL) return SFFT_ERR_UNSUPPORTED;
+  if (d.DK > kMaxD || d.DB > kMaxD || d.DB < d.DK) return SFFT_ERR_UNSUPPORTED;
+  if (d.H < d.L || d.W < d.L || d.W < 16 || d.W > 2048) return SFFT_ERR_UNSUPPORTED;
+
+  sfft_plan_s* p = new (std::nothrow) sfft_plan_s();
+  if (!p) return SFFT_ERR_NOMEM;
+  p->d = d;
+  p->stream = (cudaStream_t)cuda_stream;
+  p->fp64 = (d.prec == SFFT_PREC_FP64);
+  p->elem = p->fp64 ? 8 : 4;
+  cudaGetDevice(&p->device);
+  p->w = (d.L - 1) / 2;
+  p->NK = n_mono(d.DK);
+  p->NB = n_mono(d.DB);
+  p->NKK = d.L * d.L * p->NK;
+  p->N = p->NKK + p->NB;
+  p->Nf = std::max(64, next_pow2(d.W));
+  p->M = p->Nf / 2;
+  p->N2 = p->M / 32;
+  p->DM_KK = 2 * d.DK;
+  p->DM_KB = d.DK + d.DB;
+  p->DM_bK = d.DK;
+  p->DM_BB = 2 * d.DB;
+  p->n_wa = std::max(p->DM_KK, p->DM_KB) + 1;
+  std::vector<int> hdidx((size_t)(2 * d.L - 1) * (2 * d.L - 1), -1);
+  for (int dy = 0; dy < d.L; ++dy)
+    for (int dx = -(d.L - 1); dx < d.L; ++dx)
+      if (dy > 0 || dx >= 0) {
+        hdidx[(size_t)(dy + d.L - 1) * (2 * d.L - 1) + (dx + d.L - 1)] = (int)p->dlist.size();
+        p->dlist.push_back(int2{dy, dx});
+      }
+  p->n_hd = (int)p->dlist.size();
+  const size_t slab = (size_t)d.H * p->M * 2 * p->elem;
+  if (d.d_batch > 0) {
+    p->d_batch = std::min(d.d_batch, p->n_hd);
+  } else {
+    const size_t budget = size_t(4) << 30;
+    size_t nb = budget / (slab * (size_t)d.batch);
+    p->d_batch = (int)std::max<size_t>(1, std::min<size_t>(nb, (size_t)p->n_hd));
+  }
+  p->rows_per_cta = d.rows_per_cta > 0 ? d.rows_per_cta : std::min(d.H, 512);
+  p->ktile = p->M >= 128 ? 128 : 64;
+  build_layout(p);
+  build_jobs(p);
+
+  sfft_status_t st = SFFT_OK;
+  if (p->fp64) {
+    std::vector<double2> a, b, c;
+    fill_twiddles<double2, double>(p, a, b, c);
+    if (st == SFFT_OK) st = upload(&p->twM, a);
+    if (st == SFFT_OK) st = upload(&p->twN, b);
+    if (st == SFFT_OK) st = upload(&p->twD, c);
+  } else {
+    std::vector<float2> a, b, c;
+    fill_twiddles<float2, float>(p, a, b, c);
+    if (st == SFFT_OK) st = upload(&p->twM, a);
+    if (st == SFFT_OK) st = upload(&p->twN, b);
+    if (st == SFFT_OK) st = upload(&p->twD, c);
+  }
+  if (st == SFFT_OK) st = upload((void**)&p->d_dlist, p->dlist);
+  if (st == SFFT_OK) st = upload((void**)&p->d_hdidx, hdidx);
+  if (st == SFFT_OK) st = upload((void**)&p->d_jobs, p->h_jobs);
+  if (st != SFFT_OK) {
+    free_plan_device(p);
+    delete p;
+    return st;
+  }
+  *out = p;
+  return SFFT_OK;
+}
+
+extern "C" void sfft_plan_destroy(sfft_plan_t p) {
+  if (!p) return;
+  free_plan_device(p);
+  delete p;
+}
+
+extern "C" sfft_status_t sfft_plan_set_stream(sfft_plan_t p, void* s) {
+  if (!p) return SFFT_ERR_ARG;
+  p->stream = (cudaStream_t)s;
+  return SFFT_OK;
+}
+
+extern "C" int64_t sfft_num_unknowns(sfft_plan_t p) { return p ? p->N : -1; }
+extern "C" size_t sfft_workspace_bytes(sfft_plan_t p) { return p ? p->ws_bytes : 0; }
+extern "C" sfft_status_t sfft_plan_tiles(sfft_plan_t p, int32_t* o) {
+  if (!p || !o) return SFFT_ERR_ARG;
+  o[0] = p->d_batch; o[1] = p->rows_per_cta; o[2] = p->ktile;
+  return SFFT_OK;
+}
+
+static bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
+
+static sfft_status_t build_normal_impl(sfft_plan_t p, const float* R, const float* S, const uint8_t* bad,
+                                       const double* sky, double* A, double* b, void* ws) {
+  cudaStream_t st = p->stream;
+  const int B = p->d.batch;
+  CK(cudaMemsetAsync(ws_at<char>(ws, p->status), 0, p->status.bytes, st));
+  CK(launch_sky(p, R, S, bad, sky, ws));
+  CK(launch_prep(p, R, S, bad, ws));
+  CK(launch_moments(p, S, nullptr, false, ws));
+  CK(launch_rfft_rm(p, ws));
+  CK(launch_rfft_weights(p, nullptr, nullptr, 0, p->n_wa, ws_at<char>(ws, p->wspec), p->n_wa, ws));
+  CK(launch_rfft_weights(p, S, nullptr, 0, p->d.DK + 1, ws_at<char>(ws, p->uspec), p->d.DK + 1, ws));
+  CK(cudaMemsetAsync(ws_at<char>(ws, p->gkk), 0, p->gkk.bytes, st));
+  CK(cudaMemsetAsync(ws_at<char>(ws, p->gkb), 0, p->gkb.bytes, st));
+  CK(cudaMemsetAsync(ws_at<char>(ws, p->gbk), 0, p->gbk.bytes, st));
+  CK(launch_contract(p, p->DM_KB, p->kb_first, p->kb_count, p->rows_per_cta, p->ktile, ws));
+  CK(launch_contract(p, p->DM_bK, p->bk_first, p->bk_count, p->rows_per_cta, p->ktile, ws));
+  for (size_t ib = 0; ib < p->kk_first.size(); ++ib) {
+    const int d0 = (int)ib * p->d_batch;
+    const int nd = std::min(p->d_batch, p->n_hd - d0);
+    CK(launch_rfft_prod(p, d0, nd, ws));
+    CK(launch_contract(p, p->DM_KK, p->kk_first[ib], p->kk_count[ib], p->rows_per_cta, p->ktile, ws));
+  }
+  CK(launch_scatter(p, A, b, ws, false, nullptr));
+  (void)B;
+  return SFFT_OK;
+}
+
+static sfft_status_t solve_impl(sfft_plan_t p, const double* A, const double* b, double* theta, int32_t refine,
+                                const float* R, const float* S, int32_t* info, void* ws) {
+  double* vec = ws_at<double>(ws, p->vec);
+  const size_t NBt = (size_t)p->N * p->d.batch;
+  double* rhs = vec;
+  double* x = vec + NBt;
+  double* toff = ws_at<double>(ws, p->theta_off);
+  CK(launch_cholesky(p, A, ws));
+  CK(launch_chol_solve(p, b, x, ws));
+  CK(launch_theta_finish(p, x, toff, false));
+  for (int r = 0; r < refine; ++r) {
+    void* e = ws_at<char>(ws, p->eimg);
+    CK(launch_apply(p, R, S, toff, nullptr, nullptr, e, true, ws));
+    CK(launch_rfft_weights(p, nullptr, e, 0, p->d.DK + 1, ws_at<char>(ws, p->uspec), p->d.DK + 1, ws));
+    CK(cudaMemsetAsync(ws_at<char>(ws, p->gbk), 0, p->gbk.bytes, p->stream));
+    CK(launch_contract(p, p->DM_bK, p->bk_first, p->bk_count, p->rows_per_cta, p->ktile, ws));
+    CK(launch_moments(p, nullptr, e, true, ws));
+    CK(launch_scatter(p, nullptr, nullptr, ws, true, rhs));
+    CK(launch_chol_solve(p, rhs, x, ws));
+    CK(launch_theta_finish(p, x, toff, true));
+  }
+  CK(launch_theta_to_orig(p, toff, theta, ws));
+  if (info) CK(launch_info(p, info, ws));
+  return SFFT_OK;
+}
+
+static sfft_status_t apply_impl(sfft_plan_t p, const float* R, const float* S, const double* theta,
+                                const double* sky, float* D, void* ws) {
+  double* toff = ws_at<double>(ws, p->theta_off);
+  CK(launch_theta_to_off(p, theta, sky, toff, ws));
+  CK(launch_apply(p, R, S, toff, sky, D, nullptr, false, ws));
+  return SFFT_OK;
+}
+
+static sfft_status_t check_common(sfft_plan_t p, const void* R, const void* S, const void* ws) {
+  if (!p || !R || !S || !ws) return SFFT_ERR_ARG;
+  if (!aligned(ws, 256)) return SFFT_ERR_ARG;
+  if (!aligned(R, 4) || !aligned(S, 4)) return SFFT_ERR_ARG;
+  return SFFT_OK;
+}
+
+extern "C" sfft_status_t sfft_build_normal(sfft_plan_t p, const float* R, const float* S, const uint8_t* bad,
+                                           const double* sky, double* A, double* b, void* ws) {
+  sfft_status_t s = check_common(p, R, S, ws);
+  if (s != SFFT_OK) return s;
+  if (!A || !b) return SFFT_ERR_ARG;
+  return build_normal_impl(p, R, S, bad, sky, A, b, ws);
+}
+
+extern "C" sfft_status_t sfft_solve(sfft_plan_t p, const double* A, const double* b, double* theta,
+                                    int32_t refine_steps, const float* R, const float* S, const uint8_t* bad,
+                                    int32_t* info, void* ws) {
+  (void)bad;
+  if (!p || !A || !b || !theta || !ws || refine_steps < 0) return SFFT_ERR_ARG;
+  if (refine_steps > 0 && (!R || !S)) return SFFT_ERR_ARG;
+  return solve_impl(p, A, b, theta, refine_steps, R, S, info, ws);
+}
+
+extern "C" sfft_status_t sfft_apply(sfft_plan_t p, const float* R, const float* S, const double* theta,
+                                    const double* sky, float* D, void* ws) {
+  sfft_status_t s = check_common(p, R, S, ws);
+  if (s != SFFT_OK) return s;
+  if (!theta || !D) return SFFT_ERR_ARG;
+  return apply_impl(p, R, S, theta, sky, D, ws);
+}
+
+static sfft_status_t subtract_enqueue(sfft_plan_t p, const float* R, const float* S, const uint8_t* bad,
+                                      const double* sky, int32_t refine, double* A, double* b, double* theta,
+                                      int32_t* info, float* D, void* ws) {
+  sfft_status_t s = build_normal_impl(p, R, S, bad, sky, A, b, ws);
+  if (s != SFFT_OK) return s;
+  s = solve_impl(p, A, b, theta, refine, R, S, info, ws);
+  if (s != SFFT_OK) return s;
+  return apply_impl(p, R, S, theta, nullptr, D, ws);
+}
+
+extern "C" sfft_status_t sfft_subtract(sfft_plan_t p, const float* R, const float* S, const uint8_t* bad,
+                                       const double* sky, int32_t refine_steps, double* A, double* b,
+                                       double* theta, int32_t* info, float* D, void* ws) {
+  sfft_status_t s = check_common(p, R, S, ws);
+  if (s != SFFT_OK) return s;
+  if (!A || !b || !theta || !D || refine_steps < 0) return SFFT_ERR_ARG;
+  if (!(p->d.flags & SFFT_FLAG_GRAPH) || p->stream == nullptr)
+    return subtract_enqueue(p, R, S, bad, sky, refine_steps, A, b, theta, info, D, ws);
+  std::vector<uintptr_t> key = {(uintptr_t)R, (uintptr_t)S, (uintptr_t)bad, (uintptr_t)sky, (uintptr_t)refine_steps,
+                                (uintptr_t)A, (uintptr_t)b, (uintptr_t)theta, (uintptr_t)info, (uintptr_t)D,
+                                (uintptr_t)ws};
+  auto it = p->graphs.find(key);
+  if (it == p->graphs.end()) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+    sfft_status_t es = subtract_enqueue(p, R, S, bad, sky, refine_steps, A, b, theta, info, D, ws);
+    cudaError_t ce = cudaStreamEndCapture(p->stream, &g);
+    if (es != SFFT_OK) { if (g) cudaGraphDestroy(g); return es; }
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+    cudaGraphExec_t ex = nullptr;
+    ce = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+    it = p->graphs.emplace(key, ex).first;
+  }
+  CK(cudaGraphLaunch(it->second, p->stream));
+  return SFFT_OK;
+}
+
+extern "C" sfft_status_t sfft_kernel_at(sfft_plan_t p, const double* theta, double x, double y, double* K) {
+  if (!p || !theta || !K) return SFFT_ERR_ARG;
+  CK(launch_kernel_at(p, theta, x, y, K));
+  return SFFT_OK;
+}
+
+extern "C" const char* sfft_status_str(sfft_status_t s) {
+  switch (s) {
+    case SFFT_OK: return "ok";
+    case SFFT_ERR_ARG: return "invalid argument";
+    case SFFT_ERR_CUDA: return "CUDA error";
+    case SFFT_ERR_NOMEM: return "out of memory";
+    case SFFT_ERR_SINGULAR: return "normal matrix not positive definite";
+    case SFFT_ERR_NONFINITE: return "non-finite normal matrix or solution";
+    case SFFT_ERR_TIMEOUT: return "bounded device wait timed out";
+    case SFFT_ERR_UNSUPPORTED: return "unsupported shape or degree";
+  }
+  return "unknown status";
+}
+
+extern "C" const char* sfft_last_error(void) { return g_last_error.c_str(); }

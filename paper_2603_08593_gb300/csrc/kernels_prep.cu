@@ -1,0 +1,241 @@
+// Mask and sky-offset preparation, fit-mask erosion and the background
+// moments.
+//   good(x)  = bad(x) == 0 && finite(R(x)) && finite(S(x))
+//   R_m(x)   = good ? R - s_R : 0
+//   M_fit(x) = x at least w from every edge and good on the whole L x L
+//              footprint (separable erosion: a row pass, then a column pass)
+//   moments  sum_x M_fit xt^a yt^b (a + b <= 2 D_B)  and
+//            sum_x M_fit xt^a yt^b v(x) (a + b <= D_B), v = S - s_S or the
+//            refinement residual e; FP32 per-thread partials, FP64 block and
+//            global accumulation.
+// The sky constants, when not given, are the mean of the good pixels rounded
+// to an integer, so R - s_R and S - s_S are exact in FP32 for |R|, |S| < 2^24.
+#include "common.cuh"
+#include "plan.h"
+
+namespace sfft {
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+  }
+  return s;  // valid on thread 0
+}
+
+__global__ void __launch_bounds__(256)
+k_sky_sum(const float* __restrict__ R, const float* __restrict__ S, const uint8_t* __restrict__ bad, int64_t npx,
+          double* __restrict__ acc) {
+  __shared__ double red[8];
+  const int ccd = blockIdx.y;
+  const float* r = R + ccd * npx;
+  const float* s = S + ccd * npx;
+  const uint8_t* b = bad ? bad + ccd * npx : nullptr;
+  float sr = 0.f, ss = 0.f;
+  double srd = 0.0, ssd = 0.0;
+  int cnt = 0, sub = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npx; i += (int64_t)gridDim.x * blockDim.x) {
+    const float rv = r[i], sv = s[i];
+    const bool g = (!b || b[i] == 0) && isfinite(rv) && isfinite(sv);
+    if (g) { sr += rv; ss += sv; ++cnt; ++sub; }
+    if (sub == 256) { srd += sr; ssd += ss; sr = ss = 0.f; sub = 0; }
+  }
+  srd += sr; ssd += ss;
+  double t0 = block_sum<256>(srd, red);
+  if (threadIdx.x == 0) atomicAdd(&acc[4 * ccd + 0], t0);
+  double t1 = block_sum<256>(ssd, red);
+  if (threadIdx.x == 0) atomicAdd(&acc[4 * ccd + 1], t1);
+  double t2 = block_sum<256>((double)cnt, red);
+  if (threadIdx.x == 0) atomicAdd(&acc[4 * ccd + 2], t2);
+}
+
+__global__ void k_sky_final(const double* __restrict__ acc, double* __restrict__ sky, int batch) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= batch) return;
+  const double n = acc[4 * c + 2];
+  sky[2 * c + 0] = n > 0 ? rint(acc[4 * c + 0] / n) : 0.0;
+  sky[2 * c + 1] = n > 0 ? rint(acc[4 * c + 1] / n) : 0.0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_prep(const float* __restrict__ R, const float* __restrict__ S, const uint8_t* __restrict__ bad,
+       const double* __restrict__ sky, int64_t npx, uint8_t* __restrict__ good, T* __restrict__ Rm) {
+  const int ccd = blockIdx.y;
+  const T sR = (T)sky[2 * ccd];
+  const int64_t base = ccd * npx;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npx; i += (int64_t)gridDim.x * blockDim.x) {
+    const float rv = R[base + i], sv = S[base + i];
+    const bool g = (!bad || bad[base + i] == 0) && isfinite(rv) && isfinite(sv);
+    good[base + i] = g ? 1 : 0;
+    Rm[base + i] = g ? (T)rv - sR : (T)0;
+  }
+}
+
+// row pass: gh(y, x) = w <= x < W - w and good on [x - w, x + w]
+__global__ void __launch_bounds__(256)
+k_erode_rows(const uint8_t* __restrict__ good, uint8_t* __restrict__ gh, int H, int W, int w) {
+  const int y = blockIdx.x, ccd = blockIdx.y;
+  const uint8_t* g = good + ((int64_t)ccd * H + y) * W;
+  uint8_t* o = gh + ((int64_t)ccd * H + y) * W;
+  for (int x = threadIdx.x; x < W; x += blockDim.x) {
+    uint8_t v = 0;
+    if (x >= w && x < W - w) {
+      v = 1;
+      for (int dx = -w; dx <= w; ++dx) v &= g[x + dx];
+    }
+    o[x] = v;
+  }
+}
+
+// column pass: M(y, x) = w <= y < H - w and gh on [y - w, y + w]
+__global__ void __launch_bounds__(256)
+k_erode_cols(const uint8_t* __restrict__ gh, uint8_t* __restrict__ mfit, int H, int W, int w) {
+  const int y = blockIdx.x, ccd = blockIdx.y;
+  const uint8_t* g = gh + (int64_t)ccd * H * W;
+  uint8_t* o = mfit + ((int64_t)ccd * H + y) * W;
+  const bool inside = (y >= w && y < H - w);
+  for (int x = threadIdx.x; x < W; x += blockDim.x) {
+    uint8_t v = 0;
+    if (inside) {
+      v = 1;
+      for (int dy = -w; dy <= w; ++dy) v &= g[(int64_t)(y + dy) * W + x];
+    }
+    o[x] = v;
+  }
+}
+
+// one block per (row, ccd).  mom_bb[mono(a,b)] for a+b <= DBB, mom_v[mono(a,b)] for a+b <= DV.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_moments(const uint8_t* __restrict__ mfit, const float* __restrict__ S, const double* __restrict__ sky,
+          const T* __restrict__ E, int H, int W, int DBB, int DV, double* __restrict__ mom_bb, int64_t bb_stride,
+          double* __restrict__ mom_v, int64_t v_stride, int* __restrict__ rowflag) {
+  __shared__ double red[8];
+  const int y = blockIdx.x, ccd = blockIdx.y;
+  const int64_t row = ((int64_t)ccd * H + y) * W;
+  const T sS = S ? (T)sky[2 * ccd + 1] : (T)0;
+  const T xs = (T)2 / (T)(W > 1 ? W - 1 : 1);
+  T pm[kMaxWeightDeg + 1] = {0, 0, 0, 0, 0};
+  T pv[kMaxD + 1] = {0, 0, 0};
+  int cnt = 0;
+  for (int x = threadIdx.x; x < W; x += blockDim.x) {
+    if (!mfit[row + x]) continue;
+    ++cnt;
+    const T xt = (T)x * xs - (T)1;
+    T v = 0;
+    if (S) v = (T)S[row + x] - sS;
+    else if (E) v = E[row + x];
+    T pw = 1;
+#pragma unroll
+    for (int a = 0; a <= kMaxWeightDeg; ++a) {
+      if (a <= DBB) pm[a] += pw;
+      if (a <= kMaxD && a <= DV) pv[a] += pw * v;
+      pw *= xt;
+    }
+  }
+  const double yt = 2.0 * y / (double)(H > 1 ? H - 1 : 1) - 1.0;
+  const double c = block_sum<256>((double)cnt, red);
+  if (threadIdx.x == 0 && rowflag) rowflag[(int64_t)ccd * H + y] = c > 0 ? 1 : 0;
+  // every thread must take part in block_sum; branch on c only after the broadcast
+  __shared__ double cb;
+  if (threadIdx.x == 0) cb = c;
+  __syncthreads();
+  if (cb == 0) return;
+  if (mom_bb) {
+    for (int a = 0; a <= DBB; ++a) {
+      const double s = block_sum<256>((double)pm[a], red);
+      if (threadIdx.x == 0) {
+        double yp = 1.0;
+        for (int b = 0; a + b <= DBB; ++b) { atomicAdd(&mom_bb[ccd * bb_stride + mono_index(a, b)], s * yp); yp *= yt; }
+      }
+    }
+  }
+  for (int a = 0; a <= DV; ++a) {
+    const double s = block_sum<256>((double)pv[a], red);
+    if (threadIdx.x == 0) {
+      double yp = 1.0;
+      for (int b = 0; a + b <= DV; ++b) { atomicAdd(&mom_v[ccd * v_stride + mono_index(a, b)], s * yp); yp *= yt; }
+    }
+  }
+}
+
+static int grid_for(int64_t n, int threads, int cap) {
+  int64_t g = (n + threads - 1) / threads;
+  return (int)(g < cap ? (g < 1 ? 1 : g) : cap);
+}
+
+cudaError_t launch_sky(const sfft_plan_s* p, const float* R, const float* S, const uint8_t* bad,
+                       const double* sky_in, void* ws) {
+  double* sky = ws_at<double>(ws, p->sky);
+  const int B = p->d.batch;
+  if (sky_in) {
+    return cudaMemcpyAsync(sky, sky_in, sizeof(double) * 2 * B, cudaMemcpyDeviceToDevice, p->stream);
+  }
+  double* acc = ws_at<double>(ws, p->skyacc);
+  cudaMemsetAsync(acc, 0, sizeof(double) * 4 * B, p->stream);
+  const int64_t npx = (int64_t)p->d.H * p->d.W;
+  dim3 grid(grid_for(npx, 256 * 16, 296), B);
+  k_sky_sum<<<grid, 256, 0, p->stream>>>(R, S, bad, npx, acc);
+  k_sky_final<<<(B + 127) / 128, 128, 0, p->stream>>>(acc, sky, B);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t prep_T(const sfft_plan_s* p, const float* R, const float* S, const uint8_t* bad, void* ws) {
+  const int H = p->d.H, W = p->d.W, B = p->d.batch;
+  const int64_t npx = (int64_t)H * W;
+  uint8_t* good = ws_at<uint8_t>(ws, p->good);
+  uint8_t* gh = ws_at<uint8_t>(ws, p->gh);
+  uint8_t* mfit = ws_at<uint8_t>(ws, p->mfit);
+  T* Rm = ws_at<T>(ws, p->rm);
+  dim3 g1(grid_for(npx, 256 * 8, 1184), B);
+  k_prep<T><<<g1, 256, 0, p->stream>>>(R, S, bad, ws_at<double>(ws, p->sky), npx, good, Rm);
+  dim3 g2(H, B);
+  k_erode_rows<<<g2, 256, 0, p->stream>>>(good, gh, H, W, p->w);
+  k_erode_cols<<<g2, 256, 0, p->stream>>>(gh, mfit, H, W, p->w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep(const sfft_plan_s* p, const float* R, const float* S, const uint8_t* bad, void* ws) {
+  return p->fp64 ? prep_T<double>(p, R, S, bad, ws) : prep_T<float>(p, R, S, bad, ws);
+}
+
+// resid == false: BB moments, b_B (from S) and row flags;  resid == true: b_B-part of the
+// refinement right-hand side from the residual image (written into vec slot 0 tail).
+template <typename T>
+static cudaError_t moments_T(const sfft_plan_s* p, const float* S, const void* eimg, bool resid, void* ws) {
+  const int H = p->d.H, W = p->d.W, B = p->d.batch;
+  const uint8_t* mfit = ws_at<uint8_t>(ws, p->mfit);
+  const double* sky = ws_at<double>(ws, p->sky);
+  dim3 g(H, B);
+  if (!resid) {
+    double* bb = ws_at<double>(ws, p->mom_bb);
+    double* bv = ws_at<double>(ws, p->mom_b);
+    const int nbb = n_mono(p->DM_BB), nb = n_mono(p->d.DB);
+    cudaMemsetAsync(bb, 0, sizeof(double) * nbb * B, p->stream);
+    cudaMemsetAsync(bv, 0, sizeof(double) * nb * B, p->stream);
+    k_moments<T><<<g, 256, 0, p->stream>>>(mfit, S, sky, (const T*)nullptr, H, W, p->DM_BB, p->d.DB, bb, nbb, bv,
+                                           nb, ws_at<int>(ws, p->rowflag));
+  } else {
+    double* bv = ws_at<double>(ws, p->mom_b);
+    const int nb = n_mono(p->d.DB);
+    cudaMemsetAsync(bv, 0, sizeof(double) * nb * B, p->stream);
+    k_moments<T><<<g, 256, 0, p->stream>>>(mfit, nullptr, sky, (const T*)eimg, H, W, 0, p->d.DB, nullptr, 0, bv,
+                                           nb, nullptr);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const sfft_plan_s* p, const float* S, const void* eimg, bool resid, void* ws) {
+  return p->fp64 ? moments_T<double>(p, S, eimg, resid, ws) : moments_T<float>(p, S, eimg, resid, ws);
+}
+
+}  // namespace sfft

@@ -1,0 +1,88 @@
+// Host-side plan object, workspace layout and kernel launcher declarations.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "sfft.h"
+
+namespace sfft {
+
+// One contraction job: correlate the weight spectra at workspace offset
+// `wts` (a-indexed, stride H*M) against the probe spectrum at offset `probe`
+// for lags u_y in [uy_lo, uy_hi], u_x in [ux_lo, ux_hi]; results accumulate
+// (FP64) into out[(uy+w)][(ux+w)][m] at offset `out`.  Offsets are bytes from
+// the workspace base so that job tables are built once per plan.
+struct CJob {
+  int64_t probe, wts, out, rowflag;
+  int uy_lo, uy_hi, ux_lo, ux_hi;
+};
+
+struct Region { size_t off = 0, bytes = 0; };
+
+}  // namespace sfft
+
+struct sfft_plan_s {
+  sfft_desc_t d{};
+  cudaStream_t stream = nullptr;
+  bool fp64 = false;
+  int device = 0;
+  int w = 0, NK = 0, NB = 0, NKK = 0, N = 0;
+  int Nf = 0, M = 0, N2 = 0;
+  int DM_KK = 0, DM_KB = 0, DM_bK = 0, DM_BB = 0;
+  int n_wa = 0;                       // weight spectra a = 0 .. n_wa-1
+  int n_hd = 0;                       // half-plane differences
+  std::vector<int2> dlist;            // (dy, dx) per half-plane difference
+  int d_batch = 0, rows_per_cta = 0, ktile = 128;
+  size_t elem = 4;                    // sizeof(T)
+  // plan-owned constant device tables
+  void* twM = nullptr;                // c_t [N2][32]  exp(-2 pi i n1 k2 / M)
+  void* twN = nullptr;                // c_t [M]       exp(-2 pi i k / Nf)
+  void* twD = nullptr;                // c_t [Nf]      (cos, sin)(2 pi j / Nf)
+  int2* d_dlist = nullptr;            // device copy of dlist
+  int* d_hdidx = nullptr;             // [(2L-1)][(2L-1)] -> half-plane index or -1
+  sfft::CJob* d_jobs = nullptr;       // job table (device), built at plan time
+  std::vector<sfft::CJob> h_jobs;
+  // job table sections: KK jobs of d-batch i start at kk_first[i]
+  std::vector<int> kk_first, kk_count;
+  int kb_first = 0, kb_count = 0, bk_first = 0, bk_count = 0;
+  // workspace regions (per-CCD strides where noted)
+  sfft::Region sky, skyacc, good, gh, mfit, rowflag, rm, wspec, uspec, rhat, phat, gkk, gkb, gbk,
+      mom_bb, mom_b, eimg, lfac, scale, vec, theta_off, status;
+  size_t ws_bytes = 0;
+  // graph cache for sfft_subtract
+  std::map<std::vector<uintptr_t>, cudaGraphExec_t> graphs;
+};
+
+namespace sfft {
+
+// kernels_*.cu launchers; all enqueue on p->stream and return cudaGetLastError()
+cudaError_t launch_sky(const sfft_plan_s* p, const float* R, const float* S, const uint8_t* bad,
+                       const double* sky_in, void* ws);
+cudaError_t launch_prep(const sfft_plan_s* p, const float* R, const float* S, const uint8_t* bad, void* ws);
+cudaError_t launch_moments(const sfft_plan_s* p, const float* S, const void* eimg, bool resid, void* ws);
+cudaError_t launch_rfft_rm(const sfft_plan_s* p, void* ws);
+cudaError_t launch_rfft_weights(const sfft_plan_s* p, const float* S, const void* eimg, int a0, int na,
+                                void* out, int nslab, void* ws);
+cudaError_t launch_rfft_prod(const sfft_plan_s* p, int d0, int nd, void* ws);
+cudaError_t launch_contract(const sfft_plan_s* p, int DM, int job0, int njobs, int rows_per_cta, int ktile, void* ws);
+cudaError_t launch_scatter(const sfft_plan_s* p, double* A, double* b, void* ws, bool rhs_only, double* rhs_out);
+cudaError_t launch_cholesky(const sfft_plan_s* p, const double* A, void* ws);
+cudaError_t launch_chol_solve(const sfft_plan_s* p, const double* rhs, double* x, void* ws);
+cudaError_t launch_theta_finish(const sfft_plan_s* p, const double* x, double* theta_off, bool add);
+cudaError_t launch_theta_to_orig(const sfft_plan_s* p, const double* theta_off, double* theta, void* ws);
+cudaError_t launch_theta_to_off(const sfft_plan_s* p, const double* theta, const double* sky, double* theta_off, void* ws);
+cudaError_t launch_apply(const sfft_plan_s* p, const float* R, const float* S, const double* theta_off,
+                         const double* sky, float* D, void* eimg, bool resid, void* ws);
+cudaError_t launch_info(const sfft_plan_s* p, int32_t* info, void* ws);
+cudaError_t launch_kernel_at(const sfft_plan_s* p, const double* theta, double x, double y, double* K);
+
+template <typename T> inline T* ws_at(void* ws, const Region& r) {
+  return reinterpret_cast<T*>(static_cast<char*>(ws) + r.off);
+}
+
+}  // namespace sfft
