@@ -1,0 +1,315 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the difference-imaging path on synthetic
+DECam-shaped CCD pairs (2048 x 4096, L = 11, D_K = D_B = 2).
+
+One step = one full subtraction of one CCD pair per GPU: masks and sky
+offsets, Fourier-domain normal-matrix assembly, FP64 Cholesky solve, one
+image-space refinement step and the convolve-and-subtract.  Prints one JSON
+line (rank 0).  `--impl reference` times the FP64 CPU oracle instead, on a
+bounded strip of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+_CORES = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, str(_CORES))
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SFFT CCD-pairs/sec (2k×4k, L=11, D_K=2), mixed vs FP64 at stated error; HBM %"
+UNIT = "CCD-pairs/s"
+H, W, L, DK, DB = 4096, 2048, 11, 2, 2
+REFINE = 1
+L2_FLUSH_BYTES = 256 << 20
+WORKLOAD = ("one DECam CCD pair per GPU per step: 2048x4096 FP32, 20k stars, PSF FWHM 1.0-1.4 (R) / "
+            "1.5-2.1 (S) px across the chip, saturation mask with 3 px dilation, two bad columns, "
+            "50 transients; L=11, D_K=D_B=2, mixed precision, 1 refinement step")
+PHASES = ("prep", "fft_weights", "fft_prod", "contract_kk", "contract_rk", "scatter", "solve", "apply")
+
+
+def half_plane_lag_rows(L):
+    """sum over half-plane kernel-offset differences d of (L - |d_y|): the number
+    of (d, u_y) pairs the product-spectrum contraction evaluates."""
+    return sum((L - dy) * (L if dy == 0 else 2 * L - 1) for dy in range(L))
+
+
+def kk_flops_per_ccd(H, W, L, DK):
+    """Algorithmic FP32 work of the KK contraction for one CCD: for every (d, u_y)
+    pair, interior row y and packed spectrum slot k, (2 D_K + 1) complex products
+    conj(V_a) P (6 flop each) and n_mono(2 D_K) complex accumulations scaled by
+    yt^b (4 flop each, FMA = 2 flop)."""
+    M = max(64, 1 << (W - 1).bit_length()) // 2
+    DM = 2 * DK
+    per = (DM + 1) * 6 + (DM + 1) * (DM + 2) // 2 * 4
+    return half_plane_lag_rows(L) * (H - (L - 1)) * M * per
+
+
+def fp32_alu_peak_tflops(clock_mhz):
+    """152 SMs x 128 FP32 lanes x 2 flop per FMA x SM clock."""
+    return 152 * 128 * 2 * clock_mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0])); mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+def oracle_strip_seconds(d, rows):
+    """Time the FP64 oracle (definition form, solve, apply) on the first `rows`
+    rows of the pair; returns (seconds, strip fraction)."""
+    from oracle import sfft_oracle as O
+    R = d["R"][:rows]; S = d["S"][:rows]; bad = d["bad"][:rows]
+    t0 = time.perf_counter()
+    out = O.fit(R, S, bad, L, DK, DB)
+    dt = time.perf_counter() - t0
+    assert out["status"] == O.STATUS_OK
+    return dt, rows / float(H)
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    from synth import config_pair
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    d = config_pair("c2")
+    rows = args.ref_rows
+    for _ in range(args.warmup):
+        oracle_strip_seconds(d, rows)
+    times = []
+    for _ in range(args.steps):
+        dt, frac = oracle_strip_seconds(d, rows)
+        times.append(dt / frac)
+    sec_per_ccd = float(np.mean(times))
+    v = 1.0 / sec_per_ccd
+    sample = (f"FP64 NumPy/SciPy oracle (definition-form normal equations, Cholesky, FP64 apply) on the first "
+              f"{rows} of 4096 rows of the CCD pair, scaled by 4096/{rows} to CCD-pairs/s")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_per_ccd * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "H": H, "W": W, "L": L, "DK": DK, "DB": DB},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": _CORES, "kind": "oracle", "sample": sample,
+                             "cpu": cpu_model()},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+    from paper_2603_08593_gb300 import Plan
+    from synth import config_pair, make_pair
+    from synth.decam import SAT_CLIP_ADU
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    if rank == 0:
+        d = config_pair("c2")
+    else:   # replicas: an independent CCD pair with the same recipe per rank
+        d = make_pair(4096, 2048, seed=2 + 1000 * rank, n_src=20000, fwhm_R=(1.0, 1.4), fwhm_S=(1.5, 2.1),
+                      shift=(0.1, 0.0), n_transients=50, snr=(5.0, 50.0), clip=SAT_CLIP_ADU,
+                      mask_saturated=True, bad_columns=(700, 1500))
+
+    cpu_base = None
+    if rank == 0 and not args.no_cpu_baseline:
+        dt, frac = oracle_strip_seconds(d, args.cpu_rows)
+        cpu_base = {"value": frac / dt, "unit": UNIT, "cores": _CORES, "kind": "oracle",
+                    "sample": (f"FP64 NumPy/SciPy oracle (definition-form normal equations, Cholesky, FP64 apply) "
+                               f"on the first {args.cpu_rows} of 4096 rows, {dt:.1f} s, scaled to CCD-pairs/s"),
+                    "cpu": cpu_model()}
+
+    stream = torch.cuda.Stream(device=dev)
+    R = torch.from_numpy(d["R"]).to(dev)[None].contiguous()
+    S = torch.from_numpy(d["S"]).to(dev)[None].contiguous()
+    bad = torch.from_numpy(d["bad"]).to(dev)[None].contiguous()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(stream):
+        plan = Plan(H, W, L, DK, DB, batch=1, prec="mixed", stream=stream, device=dev)
+        out = plan.subtract(R, S, bad, None, refine=REFINE)
+        for _ in range(max(args.warmup - 1, 0)):
+            plan.subtract(R, S, bad, None, refine=REFINE, out=out)
+        stream.synchronize()
+        info = int(out["info"][0])
+        plan.profile(True)
+        plan.profile_read(reset=True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        with ClockSampler(local) as clk:
+            t0 = time.perf_counter()
+            for i in range(args.steps):
+                flush.fill_(i & 0xff)                        # evict L2 between timed steps
+                evs[i][0].record(stream)
+                plan.subtract(R, S, bad, None, refine=REFINE, out=out)
+                evs[i][1].record(stream)
+            stream.synchronize()
+            wall = time.perf_counter() - t0
+        prof = plan.profile_read(reset=True)
+        plan.profile(False)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    dev_s = sum(step_ms) / 1e3
+    if dist is not None:
+        t = torch.tensor([dev_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_s = float(t.item())
+    value = world * args.steps / dev_s
+
+    # end to end through the public API: pinned host inputs in, difference image and theta out
+    e2e = None
+    if not args.no_e2e:
+        hR = torch.from_numpy(d["R"]).pin_memory(); hS = torch.from_numpy(d["S"]).pin_memory()
+        hb = torch.from_numpy(d["bad"]).pin_memory()
+        hD = torch.empty((H, W), dtype=torch.float32).pin_memory()
+        hth = torch.empty((plan.N,), dtype=torch.float64).pin_memory()
+        hinfo = torch.empty((1,), dtype=torch.int32).pin_memory()
+        with torch.cuda.stream(stream):
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for it in range(args.steps + 1):
+                if it == 1:
+                    ev0.record(stream)
+                R[0].copy_(hR, non_blocking=True); S[0].copy_(hS, non_blocking=True); bad[0].copy_(hb, non_blocking=True)
+                plan.subtract(R, S, bad, None, refine=REFINE, out=out)
+                hD.copy_(out["D"][0], non_blocking=True); hth.copy_(out["theta"][0], non_blocking=True)
+                hinfo.copy_(out["info"], non_blocking=True)
+            ev1.record(stream)
+            stream.synchronize()
+        e_s = ev0.elapsed_time(ev1) / 1e3
+        if dist is not None:
+            t = torch.tensor([e_s], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_s = float(t.item())
+        e2e = {"value": world * args.steps / e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(hR.numel() * 4 + hS.numel() * 4 + hb.numel()),
+               "d2h_bytes_per_step": int(hD.numel() * 4 + hth.numel() * 8 + 4)}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    launches = sum(n for _, n in prof.values())
+    kk_ms, kk_n = prof["contract_kk"]
+    roof = None
+    clocks = clk.summary()
+    if kk_n:
+        per_launch_flop = kk_flops_per_ccd(H, W, L, DK) / (kk_n / args.steps)
+        avg_ms = kk_ms / kk_n
+        achieved = per_launch_flop / (avg_ms * 1e-3) / 1e12
+        clock = 2070.0
+        peak = fp32_alu_peak_tflops(clock)
+        roof = {"bound": "alu", "kernel": "k_contract (product-spectrum lag contraction)", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": args.traffic,
+                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz max SM clock (derived, not measured)",
+                "avg_launch_ms": avg_ms, "launches_per_step": kk_n / args.steps}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "H": H, "W": W, "L": L, "DK": DK, "DB": DB, "prec": "mixed",
+                       "refine": REFINE, "ccd_pairs_per_gpu_per_step": 1, "parallelism": f"replicas x{world}",
+                       "l2": "256 MB buffer written between timed steps (L2 flushed)"},
+            "roofline": roof, "cpu_baseline": cpu_base, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks, "status": info, "wall_s": wall,
+            "phases_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=512, help="rows of the CCD the CPU oracle baseline runs on")
+    ap.add_argument("--ref-rows", type=int, default=256, help="rows per reference-arm step")
+    ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per contraction launch, if known")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -142,6 +142,27 @@ sfft_status_t sfft_subtract(sfft_plan_t plan, const float* R, const float* S, co
  * CCD, from theta (device) into K (device, double [batch][L*L]). */
 sfft_status_t sfft_kernel_at(sfft_plan_t plan, const double* theta, double x, double y, double* K);
 
+/* Per-phase device timing (not part of the method; instrumentation for
+ * roofline reports).  When enabled, every later call records CUDA events on
+ * the plan's stream around each phase; sfft_profile_read synchronizes the
+ * stream, then returns accumulated milliseconds and kernel-launch counts per
+ * phase (arrays of SFFT_PROF_N) and optionally resets them.  Phases are not
+ * timed while the stream is being captured into a graph.  Launch counts are
+ * kept whether or not timing is enabled. */
+enum {
+  SFFT_PROF_PREP = 0,        /* sky, masks, erosion, moments */
+  SFFT_PROF_FFT_WEIGHTS = 1, /* row FFTs of weight maps, R_m and residual maps */
+  SFFT_PROF_FFT_PROD = 2,    /* row FFTs of the products R_m(z) R_m(z + d) */
+  SFFT_PROF_CONTRACT_KK = 3, /* lag contraction of the product spectra (KK block) */
+  SFFT_PROF_CONTRACT_RK = 4, /* lag contraction against R_m spectra (KB, b_K, refinement) */
+  SFFT_PROF_SCATTER = 5,     /* assembly of A and b from the accumulators */
+  SFFT_PROF_SOLVE = 6,       /* Cholesky and triangular solves */
+  SFFT_PROF_APPLY = 7,       /* convolve-and-subtract and refinement residual */
+  SFFT_PROF_N = 8
+};
+sfft_status_t sfft_profile_enable(sfft_plan_t plan, int32_t enable);
+sfft_status_t sfft_profile_read(sfft_plan_t plan, double* ms, int64_t* launches, int32_t reset);
+
 const char* sfft_status_str(sfft_status_t s);
 /* Last CUDA error text seen by the library on this thread ("" if none). */
 const char* sfft_last_error(void);

@@ -39,6 +39,8 @@ SIGNATURES = {
     "sfft_apply": (I32, [VP, VP, VP, VP, VP, VP, VP]),
     "sfft_subtract": (I32, [VP, VP, VP, VP, VP, I32, VP, VP, VP, VP, VP, VP]),
     "sfft_kernel_at": (I32, [VP, VP, DBL, DBL, VP]),
+    "sfft_profile_enable": (I32, [VP, I32]),
+    "sfft_profile_read": (I32, [VP, C.POINTER(C.c_double), C.POINTER(I64), I32]),
     "sfft_status_str": (C.c_char_p, [I32]),
     "sfft_last_error": (C.c_char_p, []),
 }
@@ -177,6 +179,18 @@ class Plan:
                                     _ptr(self.ws_view))
         _check(st, "sfft_subtract")
         return o
+
+    PROF_PHASES = ("prep", "fft_weights", "fft_prod", "contract_kk", "contract_rk", "scatter", "solve", "apply")
+
+    def profile(self, enable=True):
+        _check(self.lib.sfft_profile_enable(self.h, 1 if enable else 0), "sfft_profile_enable")
+
+    def profile_read(self, reset=True):
+        """{phase: (milliseconds, kernel launches)} accumulated since the last reset."""
+        ms = (C.c_double * len(self.PROF_PHASES))()
+        n = (I64 * len(self.PROF_PHASES))()
+        _check(self.lib.sfft_profile_read(self.h, ms, n, 1 if reset else 0), "sfft_profile_read")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.PROF_PHASES)}
 
     def kernel_at(self, theta, x, y):
         K = self._f64(self.batch, self.L * self.L)

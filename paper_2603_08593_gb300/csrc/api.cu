@@ -27,6 +27,50 @@ static sfft_status_t cuda_fail(cudaError_t e, const char* where) {
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// ------------------------------------------------------------------ instrumentation
+static bool stream_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
+  return st != cudaStreamCaptureStatusNone;
+}
+
+static cudaEvent_t pool_event(sfft_plan_s* p) {
+  if (!p->evpool.empty()) {
+    cudaEvent_t e = p->evpool.back();
+    p->evpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Counts the kernels a phase enqueues and, when profiling, brackets it with events.
+struct Phase {
+  sfft_plan_s* p;
+  int cls;
+  int64_t n0;
+  cudaEvent_t a = nullptr;
+  Phase(sfft_plan_s* pp, int c) : p(pp), cls(c), n0(pp->nlaunch) {
+    if (p->prof && !stream_capturing(p->stream)) {
+      a = pool_event(p);
+      if (a) cudaEventRecord(a, p->stream);
+    }
+  }
+  ~Phase() {
+    p->prof_launch[cls] += p->nlaunch - n0;
+    if (a) {
+      cudaEvent_t b = pool_event(p);
+      if (b) {
+        cudaEventRecord(b, p->stream);
+        p->pending.push_back({cls, a, b});
+      } else {
+        p->evpool.push_back(a);
+      }
+    }
+  }
+};
+
 static void add_region(Region& r, size_t& cursor, size_t bytes) {
   r.off = cursor;
   r.bytes = bytes;
@@ -160,6 +204,10 @@ static void free_plan_device(sfft_plan_s* p) {
   if (p->d_jobs) cudaFree(p->d_jobs);
   for (auto& kv : p->graphs) cudaGraphExecDestroy(kv.second);
   p->graphs.clear();
+  for (auto& e : p->pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+  p->pending.clear();
+  for (auto e : p->evpool) cudaEventDestroy(e);
+  p->evpool.clear();
 }
 
 template <typename T>
@@ -274,27 +322,43 @@ static bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 
 static sfft_status_t build_normal_impl(sfft_plan_t p, const float* R, const float* S, const uint8_t* bad,
                                        const double* sky, double* A, double* b, void* ws) {
   cudaStream_t st = p->stream;
-  const int B = p->d.batch;
-  CK(cudaMemsetAsync(ws_at<char>(ws, p->status), 0, p->status.bytes, st));
-  CK(launch_sky(p, R, S, bad, sky, ws));
-  CK(launch_prep(p, R, S, bad, ws));
-  CK(launch_moments(p, S, nullptr, false, ws));
-  CK(launch_rfft_rm(p, ws));
-  CK(launch_rfft_weights(p, nullptr, nullptr, 0, p->n_wa, ws_at<char>(ws, p->wspec), p->n_wa, ws));
-  CK(launch_rfft_weights(p, S, nullptr, 0, p->d.DK + 1, ws_at<char>(ws, p->uspec), p->d.DK + 1, ws));
-  CK(cudaMemsetAsync(ws_at<char>(ws, p->gkk), 0, p->gkk.bytes, st));
-  CK(cudaMemsetAsync(ws_at<char>(ws, p->gkb), 0, p->gkb.bytes, st));
-  CK(cudaMemsetAsync(ws_at<char>(ws, p->gbk), 0, p->gbk.bytes, st));
-  CK(launch_contract(p, p->DM_KB, p->kb_first, p->kb_count, p->rows_per_cta, p->ktile, ws));
-  CK(launch_contract(p, p->DM_bK, p->bk_first, p->bk_count, p->rows_per_cta, p->ktile, ws));
+  {
+    Phase ph(p, SFFT_PROF_PREP);
+    CK(cudaMemsetAsync(ws_at<char>(ws, p->status), 0, p->status.bytes, st));
+    CK(launch_sky(p, R, S, bad, sky, ws));
+    CK(launch_prep(p, R, S, bad, ws));
+    CK(launch_moments(p, S, nullptr, false, ws));
+  }
+  {
+    Phase ph(p, SFFT_PROF_FFT_WEIGHTS);
+    CK(launch_rfft_rm(p, ws));
+    CK(launch_rfft_weights(p, nullptr, nullptr, 0, p->n_wa, ws_at<char>(ws, p->wspec), p->n_wa, ws));
+    CK(launch_rfft_weights(p, S, nullptr, 0, p->d.DK + 1, ws_at<char>(ws, p->uspec), p->d.DK + 1, ws));
+  }
+  {
+    Phase ph(p, SFFT_PROF_CONTRACT_RK);
+    CK(cudaMemsetAsync(ws_at<char>(ws, p->gkk), 0, p->gkk.bytes, st));
+    CK(cudaMemsetAsync(ws_at<char>(ws, p->gkb), 0, p->gkb.bytes, st));
+    CK(cudaMemsetAsync(ws_at<char>(ws, p->gbk), 0, p->gbk.bytes, st));
+    CK(launch_contract(p, p->DM_KB, p->kb_first, p->kb_count, p->rows_per_cta, p->ktile, ws));
+    CK(launch_contract(p, p->DM_bK, p->bk_first, p->bk_count, p->rows_per_cta, p->ktile, ws));
+  }
   for (size_t ib = 0; ib < p->kk_first.size(); ++ib) {
     const int d0 = (int)ib * p->d_batch;
     const int nd = std::min(p->d_batch, p->n_hd - d0);
-    CK(launch_rfft_prod(p, d0, nd, ws));
-    CK(launch_contract(p, p->DM_KK, p->kk_first[ib], p->kk_count[ib], p->rows_per_cta, p->ktile, ws));
+    {
+      Phase ph(p, SFFT_PROF_FFT_PROD);
+      CK(launch_rfft_prod(p, d0, nd, ws));
+    }
+    {
+      Phase ph(p, SFFT_PROF_CONTRACT_KK);
+      CK(launch_contract(p, p->DM_KK, p->kk_first[ib], p->kk_count[ib], p->rows_per_cta, p->ktile, ws));
+    }
   }
-  CK(launch_scatter(p, A, b, ws, false, nullptr));
-  (void)B;
+  {
+    Phase ph(p, SFFT_PROF_SCATTER);
+    CK(launch_scatter(p, A, b, ws, false, nullptr));
+  }
   return SFFT_OK;
 }
 
@@ -305,28 +369,53 @@ static sfft_status_t solve_impl(sfft_plan_t p, const double* A, const double* b,
   double* rhs = vec;
   double* x = vec + NBt;
   double* toff = ws_at<double>(ws, p->theta_off);
-  CK(launch_cholesky(p, A, ws));
-  CK(launch_chol_solve(p, b, x, ws));
-  CK(launch_theta_finish(p, x, toff, false));
+  {
+    Phase ph(p, SFFT_PROF_SOLVE);
+    CK(launch_cholesky(p, A, ws));
+    CK(launch_chol_solve(p, b, x, ws));
+    CK(launch_theta_finish(p, x, toff, false));
+  }
   for (int r = 0; r < refine; ++r) {
     void* e = ws_at<char>(ws, p->eimg);
-    CK(launch_apply(p, R, S, toff, nullptr, nullptr, e, true, ws));
-    CK(launch_rfft_weights(p, nullptr, e, 0, p->d.DK + 1, ws_at<char>(ws, p->uspec), p->d.DK + 1, ws));
-    CK(cudaMemsetAsync(ws_at<char>(ws, p->gbk), 0, p->gbk.bytes, p->stream));
-    CK(launch_contract(p, p->DM_bK, p->bk_first, p->bk_count, p->rows_per_cta, p->ktile, ws));
-    CK(launch_moments(p, nullptr, e, true, ws));
-    CK(launch_scatter(p, nullptr, nullptr, ws, true, rhs));
-    CK(launch_chol_solve(p, rhs, x, ws));
-    CK(launch_theta_finish(p, x, toff, true));
+    {
+      Phase ph(p, SFFT_PROF_APPLY);
+      CK(launch_apply(p, R, S, toff, nullptr, nullptr, e, true, ws));
+    }
+    {
+      Phase ph(p, SFFT_PROF_FFT_WEIGHTS);
+      CK(launch_rfft_weights(p, nullptr, e, 0, p->d.DK + 1, ws_at<char>(ws, p->uspec), p->d.DK + 1, ws));
+    }
+    {
+      Phase ph(p, SFFT_PROF_CONTRACT_RK);
+      CK(cudaMemsetAsync(ws_at<char>(ws, p->gbk), 0, p->gbk.bytes, p->stream));
+      CK(launch_contract(p, p->DM_bK, p->bk_first, p->bk_count, p->rows_per_cta, p->ktile, ws));
+    }
+    {
+      Phase ph(p, SFFT_PROF_PREP);
+      CK(launch_moments(p, nullptr, e, true, ws));
+    }
+    {
+      Phase ph(p, SFFT_PROF_SCATTER);
+      CK(launch_scatter(p, nullptr, nullptr, ws, true, rhs));
+    }
+    {
+      Phase ph(p, SFFT_PROF_SOLVE);
+      CK(launch_chol_solve(p, rhs, x, ws));
+      CK(launch_theta_finish(p, x, toff, true));
+    }
   }
-  CK(launch_theta_to_orig(p, toff, theta, ws));
-  if (info) CK(launch_info(p, info, ws));
+  {
+    Phase ph(p, SFFT_PROF_SOLVE);
+    CK(launch_theta_to_orig(p, toff, theta, ws));
+    if (info) CK(launch_info(p, info, ws));
+  }
   return SFFT_OK;
 }
 
 static sfft_status_t apply_impl(sfft_plan_t p, const float* R, const float* S, const double* theta,
                                 const double* sky, float* D, void* ws) {
   double* toff = ws_at<double>(ws, p->theta_off);
+  Phase ph(p, SFFT_PROF_APPLY);
   CK(launch_theta_to_off(p, theta, sky, toff, ws));
   CK(launch_apply(p, R, S, toff, sky, D, nullptr, false, ws));
   return SFFT_OK;
@@ -406,6 +495,32 @@ extern "C" sfft_status_t sfft_subtract(sfft_plan_t p, const float* R, const floa
 extern "C" sfft_status_t sfft_kernel_at(sfft_plan_t p, const double* theta, double x, double y, double* K) {
   if (!p || !theta || !K) return SFFT_ERR_ARG;
   CK(launch_kernel_at(p, theta, x, y, K));
+  return SFFT_OK;
+}
+
+extern "C" sfft_status_t sfft_profile_enable(sfft_plan_t p, int32_t enable) {
+  if (!p) return SFFT_ERR_ARG;
+  p->prof = enable != 0;
+  return SFFT_OK;
+}
+
+extern "C" sfft_status_t sfft_profile_read(sfft_plan_t p, double* ms, int64_t* launches, int32_t reset) {
+  if (!p) return SFFT_ERR_ARG;
+  if (!p->pending.empty()) {
+    CK(cudaStreamSynchronize(p->stream));
+    for (auto& e : p->pending) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, e.a, e.b) == cudaSuccess) p->prof_ms[e.cls] += t;
+      p->evpool.push_back(e.a);
+      p->evpool.push_back(e.b);
+    }
+    p->pending.clear();
+  }
+  for (int i = 0; i < SFFT_PROF_N; ++i) {
+    if (ms) ms[i] = p->prof_ms[i];
+    if (launches) launches[i] = p->prof_launch[i];
+    if (reset) { p->prof_ms[i] = 0.0; p->prof_launch[i] = 0; }
+  }
   return SFFT_OK;
 }
 

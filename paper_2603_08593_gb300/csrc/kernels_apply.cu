@@ -108,6 +108,7 @@ static cudaError_t run_apply(const sfft_plan_s* p, const float* R, const float* 
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid((p->d.W + AP_TX - 1) / AP_TX, (p->d.H + AP_TY - 1) / AP_TY, p->d.batch);
   kern<<<grid, AP_THREADS, smem, p->stream>>>(R, S, theta_off, sky, mfit, D, E, p->d.H, p->d.W, L, p->d.DB);
+  p->nlaunch += 1;
   return cudaGetLastError();
 }
 

@@ -181,6 +181,7 @@ static cudaError_t contract_T(const sfft_plan_s* p, int job0, int njobs, int row
     k_contract<T, DM, KT><<<grid, KT * n_groups<DM>(), smem, p->stream>>>(p->d_jobs + job0, (char*)ws, H, p->M, p->Nf, L, rows_per_cta,
                                                                           (const c_t<T>*)p->twD);
   }
+  p->nlaunch += 1;
   return cudaGetLastError();
 }
 

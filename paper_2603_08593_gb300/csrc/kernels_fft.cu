@@ -165,6 +165,7 @@ static cudaError_t run_prod(const sfft_plan_s* p, const T* Rm, int d0, int nd, i
   dim3 grid(gx, self ? 1 : nd, p->d.batch);
   kern<<<grid, 32 * warps, smem, p->stream>>>(Rm, H, p->d.W, p->d_dlist, d0, self, out, slab_stride, ccd_stride,
                                               (const c_t<T>*)p->twM, (const c_t<T>*)p->twN);
+  p->nlaunch += 1;
   return cudaGetLastError();
 }
 
@@ -179,6 +180,7 @@ static cudaError_t run_weight(const sfft_plan_s* p, const uint8_t* Mfit, const f
   dim3 grid((H + warps - 1) / warps, na, p->d.batch);
   kern<<<grid, 32 * warps, smem, p->stream>>>(Mfit, S, sky, E, H, p->d.W, a0, out, slab_stride, ccd_stride,
                                               (const c_t<T>*)p->twM, (const c_t<T>*)p->twN);
+  p->nlaunch += 1;
   return cudaGetLastError();
 }
 

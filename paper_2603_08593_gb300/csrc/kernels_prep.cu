@@ -185,6 +185,7 @@ cudaError_t launch_sky(const sfft_plan_s* p, const float* R, const float* S, con
   dim3 grid(grid_for(npx, 256 * 16, 296), B);
   k_sky_sum<<<grid, 256, 0, p->stream>>>(R, S, bad, npx, acc);
   k_sky_final<<<(B + 127) / 128, 128, 0, p->stream>>>(acc, sky, B);
+  p->nlaunch += 2;
   return cudaGetLastError();
 }
 
@@ -201,6 +202,7 @@ static cudaError_t prep_T(const sfft_plan_s* p, const float* R, const float* S, 
   dim3 g2(H, B);
   k_erode_rows<<<g2, 256, 0, p->stream>>>(good, gh, H, W, p->w);
   k_erode_cols<<<g2, 256, 0, p->stream>>>(gh, mfit, H, W, p->w);
+  p->nlaunch += 3;
   return cudaGetLastError();
 }
 
@@ -231,6 +233,7 @@ static cudaError_t moments_T(const sfft_plan_s* p, const float* S, const void* e
     k_moments<T><<<g, 256, 0, p->stream>>>(mfit, nullptr, sky, (const T*)eimg, H, W, 0, p->d.DB, nullptr, 0, bv,
                                            nb, nullptr);
   }
+  p->nlaunch += 1;
   return cudaGetLastError();
 }
 

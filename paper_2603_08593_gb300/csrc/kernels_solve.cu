@@ -343,6 +343,7 @@ cudaError_t launch_scatter(const sfft_plan_s* p, double* A, double* b, void* ws,
                                          ws_at<double>(ws, p->gbk), ws_at<double>(ws, p->mom_bb),
                                          ws_at<double>(ws, p->mom_b), p->d_hdidx, A, rhs_only ? rhs_out : b,
                                          rhs_only ? 1 : 0);
+  p->nlaunch += 1;
   return cudaGetLastError();
 }
 
@@ -353,14 +354,17 @@ cudaError_t launch_cholesky(const sfft_plan_s* p, const double* A, void* ws) {
   int* status = ws_at<int>(ws, p->status);
   dim3 gi(64, B);
   k_chol_init<<<gi, 256, 0, p->stream>>>(A, Lf, scale, status, N);
+  p->nlaunch += 1;
   for (int kb = 0; kb < N; kb += NBK) {
     k_chol_diag<<<B, NBK * NBK / 4, 0, p->stream>>>(Lf, status, N, kb);
+    p->nlaunch += 1;
     const int nb = N - kb < NBK ? N - kb : NBK;
     const int rem = N - kb - nb;
     if (rem > 0) {
       const int T = (rem + NBK - 1) / NBK;
       k_chol_panel<<<dim3(T, B), NBK, 0, p->stream>>>(Lf, N, kb);
       k_chol_update<<<dim3(T * (T + 1) / 2, B), 256, 0, p->stream>>>(Lf, N, kb);
+      p->nlaunch += 2;
     }
   }
   return cudaGetLastError();
@@ -372,17 +376,20 @@ cudaError_t launch_chol_solve(const sfft_plan_s* p, const double* rhs, double* x
   cudaFuncSetAttribute(k_chol_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_chol_solve<<<p->d.batch, 1024, smem, p->stream>>>(ws_at<double>(ws, p->lfac), ws_at<double>(ws, p->scale), rhs,
                                                       x, N, ws_at<int>(ws, p->status));
+  p->nlaunch += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_theta_finish(const sfft_plan_s* p, const double* x, double* theta_off, bool add) {
   const int64_t n = (int64_t)p->N * p->d.batch;
   k_theta_finish<<<(int)((n + 255) / 256), 256, 0, p->stream>>>(x, theta_off, p->N, p->d.batch, add ? 1 : 0);
+  p->nlaunch += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_theta_to_orig(const sfft_plan_s* p, const double* theta_off, double* theta, void* ws) {
   k_theta_units<<<p->d.batch, 128, 0, p->stream>>>(theta_off, theta, ws_at<double>(ws, p->sky), p->d.L, p->NK, p->NB, 1);
+  p->nlaunch += 1;
   return cudaGetLastError();
 }
 
@@ -390,11 +397,13 @@ cudaError_t launch_theta_to_off(const sfft_plan_s* p, const double* theta, const
                                 void* ws) {
   k_theta_units<<<p->d.batch, 128, 0, p->stream>>>(theta, theta_off, sky ? sky : ws_at<double>(ws, p->sky), p->d.L,
                                                    p->NK, p->NB, 0);
+  p->nlaunch += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_info(const sfft_plan_s* p, int32_t* info, void* ws) {
   k_info<<<(p->d.batch + 127) / 128, 128, 0, p->stream>>>(ws_at<int>(ws, p->status), info, p->d.batch);
+  p->nlaunch += 1;
   return cudaGetLastError();
 }
 
@@ -402,6 +411,7 @@ cudaError_t launch_kernel_at(const sfft_plan_s* p, const double* theta, double x
   const double xt = 2.0 * x / (double)(p->d.W > 1 ? p->d.W - 1 : 1) - 1.0;
   const double yt = 2.0 * y / (double)(p->d.H > 1 ? p->d.H - 1 : 1) - 1.0;
   k_kernel_at<<<p->d.batch, 128, 0, p->stream>>>(theta, K, p->d.L, p->d.DK, p->NK, p->NB, xt, yt);
+  p->nlaunch += 1;
   return cudaGetLastError();
 }
 

@@ -56,6 +56,14 @@ struct sfft_plan_s {
   size_t ws_bytes = 0;
   // graph cache for sfft_subtract
   std::map<std::vector<uintptr_t>, cudaGraphExec_t> graphs;
+  // instrumentation: kernel launches (incremented by the launchers) and per-phase event timing
+  mutable int64_t nlaunch = 0;
+  bool prof = false;
+  struct PendingEv { int cls; cudaEvent_t a, b; };
+  std::vector<PendingEv> pending;
+  std::vector<cudaEvent_t> evpool;
+  double prof_ms[SFFT_PROF_N] = {};
+  int64_t prof_launch[SFFT_PROF_N] = {};
 };
 
 namespace sfft {
