@@ -138,6 +138,28 @@ sfft_status_t sfft_subtract(sfft_plan_t plan, const float* R, const float* S, co
                             const double* sky, int32_t refine_steps, double* A, double* b,
                             double* theta, int32_t* info, float* D, void* ws);
 
+/* Allocation-free difference image (no counterpart in the paper; a service for
+ * callers that cannot allocate device memory - code running under a fixed
+ * memory budget or inside a framework that owns all allocations - and so can
+ * neither create a plan, which allocates its tables, nor supply a workspace).
+ * Computes the same D as sfft_apply for the given shapes:
+ *   R, S  : float [batch][H][W];  theta : double [batch][N] (background in
+ *   original units, as sfft_solve returns it);  sky : double [batch][2]
+ *   (required: there is no workspace to take it from);  D : float [batch][H][W];
+ *   prec  : sfft_prec_t (FP32 or FP64 convolution);  cuda_stream : cudaStream_t.
+ * Scratch: a fixed device array of 46848 doubles (375 KB) built into the
+ * library, held on every GPU that loads it until the process exits; calls with
+ * batch * N above that return SFFT_ERR_UNSUPPORTED.  The first call on each
+ * device looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  All calls
+ * share the one array, so calls that overlap on the GPU (different streams or
+ * threads without ordering) race and corrupt each other's results; the array
+ * keeps the last call's contents, and every call overwrites what it reads
+ * before reading it.  It calls no cudaMalloc or cudaFree. */
+sfft_status_t sfft_apply_noalloc(int32_t H, int32_t W, int32_t L, int32_t DK, int32_t DB, int32_t batch,
+                                 int32_t prec, const float* R, const float* S, const double* theta,
+                                 const double* sky, float* D, void* cuda_stream);
+
 /* Kernel coefficient maps for inspection: K[ccd][j] at pixel (x, y) of every
  * CCD, from theta (device) into K (device, double [batch][L*L]). */
 sfft_status_t sfft_kernel_at(sfft_plan_t plan, const double* theta, double x, double y, double* K);

@@ -39,6 +39,7 @@ SIGNATURES = {
     "sfft_apply": (I32, [VP, VP, VP, VP, VP, VP, VP]),
     "sfft_subtract": (I32, [VP, VP, VP, VP, VP, I32, VP, VP, VP, VP, VP, VP]),
     "sfft_kernel_at": (I32, [VP, VP, DBL, DBL, VP]),
+    "sfft_apply_noalloc": (I32, [I32, I32, I32, I32, I32, I32, I32, VP, VP, VP, VP, VP, VP]),
     "sfft_profile_enable": (I32, [VP, I32]),
     "sfft_profile_read": (I32, [VP, C.POINTER(C.c_double), C.POINTER(I64), I32]),
     "sfft_status_str": (C.c_char_p, [I32]),
@@ -78,6 +79,20 @@ def _check(st, what):
 
 def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def apply_noalloc(R, S, theta, sky, D, L, DK, DB, prec="mixed", stream=None):
+    """Difference image through the allocation-free entry point: no plan and no
+    workspace; R, S, D are [batch][H][W] float32, theta [batch][N] and sky
+    [batch][2] float64, all on the current device.  Writes D in place."""
+    import torch
+    lib = load()
+    B, H, W = D.shape
+    s = stream if stream is not None else torch.cuda.current_stream(D.device)
+    st = lib.sfft_apply_noalloc(H, W, L, DK, DB, B, PREC[prec], _ptr(R), _ptr(S), _ptr(theta), _ptr(sky), _ptr(D),
+                                VP(s.cuda_stream))
+    _check(st, "sfft_apply_noalloc")
+    return D
 
 
 class Plan:

@@ -15,6 +15,8 @@ using namespace sfft;
 
 static thread_local std::string g_last_error;
 
+void sfft::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
 static sfft_status_t cuda_fail(cudaError_t e, const char* where) {
   g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
   return SFFT_ERR_CUDA;

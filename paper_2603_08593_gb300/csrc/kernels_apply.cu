@@ -123,6 +123,33 @@ static cudaError_t apply_nk(const sfft_plan_s* p, const float* R, const float* S
   }
 }
 
+template <typename T, int NK>
+static cudaError_t run_apply_raw(cudaStream_t s, const float* R, const float* S, const double* theta_off,
+                                 const double* sky, float* D, int H, int W, int L, int DB, int batch) {
+  const int w = (L - 1) / 2;
+  const size_t smem = sizeof(T) * ((size_t)L * L * NK + 8 + (size_t)(AP_TY + 2 * w) * (AP_TX + 2 * w));
+  auto kern = k_apply<T, NK, false>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid((W + AP_TX - 1) / AP_TX, (H + AP_TY - 1) / AP_TY, batch);
+  kern<<<grid, AP_THREADS, smem, s>>>(R, S, theta_off, sky, nullptr, D, (T*)nullptr, H, W, L, DB);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_raw(cudaStream_t s, bool fp64, const float* R, const float* S, const double* theta_off,
+                             const double* sky, float* D, int H, int W, int L, int DK, int DB, int batch) {
+  const int NK = n_mono(DK);
+#define SFFT_APPLY_RAW(T)                                                                                   \
+  switch (NK) {                                                                                             \
+    case 1: return run_apply_raw<T, 1>(s, R, S, theta_off, sky, D, H, W, L, DB, batch);                     \
+    case 3: return run_apply_raw<T, 3>(s, R, S, theta_off, sky, D, H, W, L, DB, batch);                     \
+    case 6: return run_apply_raw<T, 6>(s, R, S, theta_off, sky, D, H, W, L, DB, batch);                     \
+    default: return cudaErrorInvalidValue;                                                                  \
+  }
+  if (fp64) { SFFT_APPLY_RAW(double) }
+  SFFT_APPLY_RAW(float)
+#undef SFFT_APPLY_RAW
+}
+
 cudaError_t launch_apply(const sfft_plan_s* p, const float* R, const float* S, const double* theta_off,
                          const double* sky, float* D, void* eimg, bool resid, void* ws) {
   const uint8_t* mfit = ws_at<uint8_t>(ws, p->mfit);

@@ -401,6 +401,12 @@ cudaError_t launch_theta_to_off(const sfft_plan_s* p, const double* theta, const
   return cudaGetLastError();
 }
 
+cudaError_t launch_theta_units_raw(cudaStream_t s, const double* src, double* dst, const double* sky, int L, int NK,
+                                   int NB, int batch, int to_orig) {
+  k_theta_units<<<batch, 128, 0, s>>>(src, dst, sky, L, NK, NB, to_orig);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_info(const sfft_plan_s* p, int32_t* info, void* ws) {
   k_info<<<(p->d.batch + 127) / 128, 128, 0, p->stream>>>(ws_at<int>(ws, p->status), info, p->d.batch);
   p->nlaunch += 1;

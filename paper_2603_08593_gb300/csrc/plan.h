@@ -89,6 +89,13 @@ cudaError_t launch_apply(const sfft_plan_s* p, const float* R, const float* S, c
 cudaError_t launch_info(const sfft_plan_s* p, int32_t* info, void* ws);
 cudaError_t launch_kernel_at(const sfft_plan_s* p, const double* theta, double x, double y, double* K);
 
+// Plan-free launchers (explicit shapes and stream) used by the allocation-free entry point.
+cudaError_t launch_theta_units_raw(cudaStream_t s, const double* src, double* dst, const double* sky, int L, int NK,
+                                   int NB, int batch, int to_orig);
+cudaError_t launch_apply_raw(cudaStream_t s, bool fp64, const float* R, const float* S, const double* theta_off,
+                             const double* sky, float* D, int H, int W, int L, int DK, int DB, int batch);
+void set_last_error(const char* msg);
+
 template <typename T> inline T* ws_at(void* ws, const Region& r) {
   return reinterpret_cast<T*>(static_cast<char*>(ws) + r.off);
 }
