@@ -88,12 +88,11 @@ static int next_pow2(int v) {
 template <typename T2, typename R>
 static void fill_twiddles(sfft_plan_s* p, std::vector<T2>& twM, std::vector<T2>& twN, std::vector<T2>& twD) {
   const double pi = 3.14159265358979323846;
-  twM.resize((size_t)p->N2 * 32);
-  for (int k2 = 0; k2 < p->N2; ++k2)
-    for (int n1 = 0; n1 < 32; ++n1) {
-      const double ang = -2.0 * pi * (double)((int64_t)n1 * k2 % p->M) / (double)p->M;
-      twM[(size_t)k2 * 32 + n1] = T2{(R)cos(ang), (R)sin(ang)};
-    }
+  twM.resize((size_t)p->M);
+  for (int j = 0; j < p->M; ++j) {
+    const double ang = -2.0 * pi * (double)j / (double)p->M;
+    twM[j] = T2{(R)cos(ang), (R)sin(ang)};
+  }
   twN.resize(p->M);
   for (int k = 0; k < p->M; ++k) {
     const double ang = -2.0 * pi * (double)k / (double)p->Nf;

@@ -40,7 +40,7 @@ struct sfft_plan_s {
   int d_batch = 0, rows_per_cta = 0, ktile = 128;
   size_t elem = 4;                    // sizeof(T)
   // plan-owned constant device tables
-  void* twM = nullptr;                // c_t [N2][32]  exp(-2 pi i n1 k2 / M)
+  void* twM = nullptr;                // c_t [M]       exp(-2 pi i j / M)
   void* twN = nullptr;                // c_t [M]       exp(-2 pi i k / Nf)
   void* twD = nullptr;                // c_t [Nf]      (cos, sin)(2 pi j / Nf)
   int2* d_dlist = nullptr;            // device copy of dlist
