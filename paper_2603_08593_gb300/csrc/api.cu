@@ -267,7 +267,7 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
     size_t nb = budget / (slab * (size_t)d.batch);
     p->d_batch = (int)std::max<size_t>(1, std::min<size_t>(nb, (size_t)p->n_hd));
   }
-  p->rows_per_cta = d.rows_per_cta > 0 ? d.rows_per_cta : std::min(d.H, 512);
+  p->rows_per_cta = d.rows_per_cta > 0 ? d.rows_per_cta : std::min(d.H, 1024);
   p->ktile = p->M >= 128 ? 128 : 64;
   build_layout(p);
   build_jobs(p);

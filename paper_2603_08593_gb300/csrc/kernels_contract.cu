@@ -9,16 +9,20 @@
 //   C_{a,b}(u_y, k) = sum_y yt^b conj(V^_a(y, k)) P^(y - u_y, k)      (y sum, FP32)
 //   g_{a,b}(u_y, u_x) = (1/Nf) sum_k h_k Re[C e^{-2 pi i k u_x / Nf}]  (lag DFT)
 // with h_0 = h_{Nf/2} = 1, else 2.  The y sum runs over one band of rows per
-// CTA with the whole (u_y, monomial) accumulator set of one k-slot held in
-// registers; each band ends with the lag DFT over the CTA's k-slots, a warp
-// shuffle reduction, a shared-memory reduction over warps and an FP64 global
-// atomic add.  Threads own one k-slot and one group of monomials: a group is
-// one or two exponents a with all their b (at most five monomials), so one
-// complex product conj(V^_a) P^ feeds up to five FMA pairs.
+// CTA with the accumulators in registers; each band ends with the lag DFT
+// over the CTA's k-slots, a warp shuffle reduction, a shared-memory reduction
+// over warps and an FP64 global atomic add.
 //
-// Slot 0 packs the real bins k = 0 and Nf/2 as (re, im); its thread forms the
-// two real products instead of a complex product by using per-thread
-// coefficients (c1, c2, c3, c4): X = (c1 Pr + c2 Pi, c3 Pi + c4 Pr).
+// Thread layout: one k-slot x one monomial group x one half of the lags.  A
+// monomial group is one or two exponents a with all their b (at most five
+// monomials), so one complex product conj(V^_a) P^ feeds up to five FMA
+// pairs; splitting the lags over two threads halves the accumulators per
+// thread (at most 6 lags x 5 monomials) so that two or three CTAs fit on an SM.
+//
+// Slot 0 packs the real bins k = 0 and Nf/2 as (re, im).  The main kernel
+// treats it as an ordinary complex slot and drops it at the flush; the small
+// kernel k_contract_slot0 adds the two real-bin terms exactly, which keeps the
+// hot loop free of per-slot special cases.
 #include "common.cuh"
 #include "plan.h"
 
@@ -43,14 +47,21 @@ template <> struct GroupCfg<0, 0> { static constexpr int ALO = 0, NLO = 1, AHI =
 
 template <int DM> constexpr int n_groups() { return DM >= 3 ? 3 : (DM == 2 ? 2 : 1); }
 template <typename T> constexpr int max_uy() { return sizeof(T) == 4 ? 11 : 6; }
+constexpr int kHalves = 2;                         // threads sharing the lags of one (k, group)
+template <typename T> constexpr int max_half() { return (max_uy<T>() + 1) / 2; }
+// k-slots per CTA and CTAs per SM the register budget is sized for: the
+// five-monomial groups (DM >= 3) use 32-slot tiles at three CTAs per SM
+// (576 threads, <= 113 registers each); FP64 accumulators take one CTA per SM.
+template <typename T, int DM> constexpr int kt_for() { return DM >= 3 ? 32 : 64; }
+template <typename T, int DM> constexpr int minb_for() { return sizeof(T) == 8 ? 1 : (DM >= 3 ? 3 : 2); }
 
 // ---------------------------------------------------------------- shared-memory pipeline
-// A CTA walks its band of weight rows y in chunks of CH rows.  For each chunk
-// it stages, with cp.async (16-byte copies, double buffered), the probe rows
-// z = y - u_y for every lag of the chunk (CH + nuy - 1 rows) and the weight
-// rows of every exponent a <= DM, restricted to the CTA's KT k-slots.  The
-// arithmetic then reads shared memory only.
-constexpr int kChunk = 8;
+// A CTA walks its band of weight rows y in chunks of kChunk rows.  For each
+// chunk it stages, with cp.async (16-byte copies, double buffered), the probe
+// rows z = y - u_y for every lag of the chunk (kChunk + nuy - 1 rows) and the
+// weight rows of every exponent a <= DM, restricted to the CTA's k-slots.
+// The arithmetic then reads shared memory only.
+constexpr int kChunk = 16;
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -64,6 +75,7 @@ template <typename T, int DM, int KT, int MU>
 struct Stage {
   c_t<T> P[kChunk + MU - 1][KT];
   c_t<T> V[DM + 1][kChunk][KT];
+  T ypw[kChunk][8];   // yt^b of the chunk's rows, b = 0..4
 };
 
 // issue the copies of chunk [yc, ye) into stage `st`
@@ -71,67 +83,68 @@ template <typename T, int DM, int KT, int MU>
 __device__ __forceinline__ void stage_chunk(Stage<T, DM, KT, MU>& st, const c_t<T>* __restrict__ P,
                                             const c_t<T>* __restrict__ V, int64_t HM, int M, int k0, int yc, int ye,
                                             int uy_lo, int uy_hi) {
-  constexpr int PER_ROW = KT * (int)sizeof(c_t<T>) / 16;   // 16-byte pieces per row segment
+  constexpr int PER_ROW = KT * (int)sizeof(c_t<T>) / 16;   // 16-byte pieces per row segment (power of 2)
+  constexpr int SLOTS = 16 / (int)sizeof(c_t<T>);           // k-slots per piece
   const int np = (ye - yc) + (uy_hi - uy_lo);             // probe rows z = yc - uy_hi ... ye - 1 - uy_lo
   const int nv = (ye - yc);
-  const int total = (np + (DM + 1) * nv) * PER_ROW;
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+  const bool full = k0 + KT <= M;                           // false only for rows narrower than a tile
+  const c_t<T>* psrc = P + (int64_t)(yc - uy_hi) * M + k0;
+  for (int t = threadIdx.x; t < np * PER_ROW; t += blockDim.x) {
     const int row = t / PER_ROW, piece = t % PER_ROW;
-    if (k0 + piece * 16 / (int)sizeof(c_t<T>) >= M) continue;   // k-tile wider than the row (tiny W)
-    const c_t<T>* src;
-    char* dst;
-    if (row < np) {
-      const int z = yc - uy_hi + row;
-      src = P + (int64_t)z * M + k0;
-      dst = reinterpret_cast<char*>(&st.P[row][0]);
-    } else {
-      const int r2 = row - np, a = r2 / nv, yy = r2 % nv;
-      src = V + a * HM + (int64_t)(yc + yy) * M + k0;
-      dst = reinterpret_cast<char*>(&st.V[a][yy][0]);
-    }
-    cp_async16(dst + piece * 16, reinterpret_cast<const char*>(src) + piece * 16);
+    if (!full && k0 + piece * SLOTS >= M) continue;
+    cp_async16(&st.P[row][piece * SLOTS], psrc + (int64_t)row * M + piece * SLOTS);
+  }
+  const c_t<T>* vsrc = V + (int64_t)yc * M + k0;
+  for (int t = threadIdx.x; t < (DM + 1) * kChunk * PER_ROW; t += blockDim.x) {
+    const int piece = t % PER_ROW, rr = t / PER_ROW;
+    const int a = rr / kChunk, yy = rr % kChunk;
+    if (yy >= nv || (!full && k0 + piece * SLOTS >= M)) continue;
+    cp_async16(&st.V[a][yy][piece * SLOTS], vsrc + a * HM + (int64_t)yy * M + piece * SLOTS);
+  }
+  // powers of yt for the chunk's rows (plain stores; read after the next barrier)
+  if (threadIdx.x < nv) {
+    const T ysc = (T)2 / (T)(HM / M > 1 ? HM / M - 1 : 1);
+    const T yt = (T)(yc + (int)threadIdx.x) * ysc - (T)1;
+    T p = 1;
+#pragma unroll
+    for (int b = 0; b < 5; ++b) { st.ypw[threadIdx.x][b] = p; p *= yt; }
   }
 }
 
-// accumulate the rows [yc, ye) of one staged chunk for monomial group G.
-// NUY is the number of lags of the job (compile time, so that the lag loop is
-// one straight-line block the scheduler can interleave); NUY = 0 means a
-// run-time count `nuy` (used by the FP64 path).
-template <typename T, int DM, int KT, int MU, int G, int NUY>
-__device__ __forceinline__ void group_chunk(c_t<T> (&acc)[MU][5], const Stage<T, DM, KT, MU>& st, int kk,
-                                            bool slot0, int yc, int ye, int nuy_rt, const int* __restrict__ rowflag,
-                                            T ysc) {
+// Accumulate the rows [yc, ye) of one staged chunk for monomial group G and
+// lags iu = lag0 .. lag0 + nlag - 1 (accumulator index iu - lag0).  NLAG > 0
+// fixes the lag count at compile time (one straight-line lag block the
+// scheduler can interleave); NLAG = 0 uses the run-time count (FP64 path).
+// Every slot is treated as a complex bin here, slot 0 included; slot 0 (the
+// packed real bins k = 0 and Nf/2) is dropped at the flush and summed exactly
+// by k_contract_slot0.
+template <typename T, int DM, int KT, int MU, int MH, int G, int NLAG>
+__device__ __forceinline__ void group_chunk(c_t<T> (&acc)[MH][5], const Stage<T, DM, KT, MU>& st, int kk,
+                                            int nrow, int nuy, int lag0, int nlag_rt) {
   using T2 = c_t<T>;
   using C = GroupCfg<DM, G>;
-  const int nuy = NUY > 0 ? NUY : nuy_rt;
-  for (int y = yc; y < ye; ++y) {
-    if (!rowflag[y]) continue;
-    const int r = y - yc;
+  const int nlag = NLAG > 0 ? NLAG : nlag_rt;
+  for (int r = 0; r < nrow; ++r) {
     const T2 vl = st.V[C::ALO][r][kk];
-    const T l1 = vl.x, l2 = slot0 ? (T)0 : vl.y, l3 = slot0 ? vl.y : vl.x, l4 = slot0 ? (T)0 : -vl.y;
-    T h1 = 0, h2 = 0, h3 = 0, h4 = 0;
-    if constexpr (C::NHI > 0) {
-      const T2 vh = st.V[C::AHI][r][kk];
-      h1 = vh.x; h2 = slot0 ? (T)0 : vh.y; h3 = slot0 ? vh.y : vh.x; h4 = slot0 ? (T)0 : -vh.y;
-    }
-    const T yt = (T)y * ysc - (T)1;
+    T2 vh;
+    if constexpr (C::NHI > 0) vh = st.V[C::AHI][r][kk];
     T yp[5];
-    yp[0] = 1;
 #pragma unroll
-    for (int b = 1; b < 5; ++b) yp[b] = yp[b - 1] * yt;
-    // probe row for lag index iu: z = y - uy_lo - iu  ->  staged row r + (nuy - 1) - iu
-    const T2* prow = &st.P[r + nuy - 1][kk];
+    for (int b = 0; b < 5; ++b) yp[b] = st.ypw[r][b];
+    // probe row for lag iu: z = y - uy_lo - iu  ->  staged row r + (nuy - 1) - iu
+    const T2* prow = &st.P[r + nuy - 1 - lag0][kk];
 #pragma unroll
-    for (int iu = 0; iu < (NUY > 0 ? NUY : MU); ++iu) {
-      if (NUY > 0 || iu < nuy) {
-        const T2 pv = prow[-iu * KT];
-        const T xr = l1 * pv.x + l2 * pv.y, xi = l3 * pv.y + l4 * pv.x;
+    for (int i = 0; i < (NLAG > 0 ? NLAG : MH); ++i) {
+      if (NLAG > 0 || i < nlag) {
+        const T2 pv = prow[-i * KT];
+        // conj(V) P
+        const T xr = vl.x * pv.x + vl.y * pv.y, xi = vl.x * pv.y - vl.y * pv.x;
 #pragma unroll
-        for (int s = 0; s < C::NLO; ++s) { acc[iu][s].x += yp[s] * xr; acc[iu][s].y += yp[s] * xi; }
+        for (int s = 0; s < C::NLO; ++s) { acc[i][s].x += yp[s] * xr; acc[i][s].y += yp[s] * xi; }
         if constexpr (C::NHI > 0) {
-          const T hr = h1 * pv.x + h2 * pv.y, hi = h3 * pv.y + h4 * pv.x;
+          const T hr = vh.x * pv.x + vh.y * pv.y, hi = vh.x * pv.y - vh.y * pv.x;
 #pragma unroll
-          for (int s = 0; s < C::NHI; ++s) { acc[iu][C::NLO + s].x += yp[s] * hr; acc[iu][C::NLO + s].y += yp[s] * hi; }
+          for (int s = 0; s < C::NHI; ++s) { acc[i][C::NLO + s].x += yp[s] * hr; acc[i][C::NLO + s].y += yp[s] * hi; }
         }
       }
     }
@@ -139,21 +152,20 @@ __device__ __forceinline__ void group_chunk(c_t<T> (&acc)[MU][5], const Stage<T,
 }
 
 // lag DFT over this thread's k, warp reduction over 32 k-slots, shared accumulation
-template <typename T, int DM, int MU, int G>
-__device__ __forceinline__ void group_flush(const c_t<T> (&acc)[MU][5], const CJob& job, int k, int Nf, int L,
-                                            T* red, const c_t<T>* __restrict__ twD) {
+template <typename T, int DM, int MH, int G>
+__device__ __forceinline__ void group_flush(const c_t<T> (&acc)[MH][5], const CJob& job, int k, int Nf, int L,
+                                            int lag0, int nlag, T* red, const c_t<T>* __restrict__ twD) {
   using T2 = c_t<T>;
   using C = GroupCfg<DM, G>;
   constexpr int NS = C::NLO + C::NHI;
   constexpr int NMONO = n_mono(DM);
   const int lane = threadIdx.x & 31;
-  const int nuy = job.uy_hi - job.uy_lo + 1;
   const int w = (L - 1) / 2;
   const bool slot0 = (k == 0);
   for (int ux = job.ux_lo; ux <= job.ux_hi; ++ux) {
     T tre, tim;
     if (slot0) {
-      tre = 1; tim = (ux & 1) ? (T)-1 : (T)1;
+      tre = 0; tim = 0;   // packed real bins: summed by k_contract_slot0
     } else {
       int idx = (int)(((int64_t)k * ux) % Nf);
       if (idx < 0) idx += Nf;
@@ -161,12 +173,12 @@ __device__ __forceinline__ void group_flush(const c_t<T> (&acc)[MU][5], const CJ
       tre = 2 * cs.x; tim = 2 * cs.y;
     }
 #pragma unroll
-    for (int iu = 0; iu < MU; ++iu) {
-      if (iu < nuy) {
-        const int ridx = ((job.uy_lo + iu + w) * L + (ux + w)) * NMONO;
+    for (int i = 0; i < MH; ++i) {
+      if (i < nlag) {
+        const int ridx = ((job.uy_lo + lag0 + i + w) * L + (ux + w)) * NMONO;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-          T v = acc[iu][s].x * tre + acc[iu][s].y * tim;
+          T v = acc[i][s].x * tre + acc[i][s].y * tim;
           v = warp_sum(v);
           if (lane == 0) {
             const int m = s < C::NLO ? mono_index(C::ALO, s) : mono_index(C::AHI, s - C::NLO);
@@ -178,13 +190,33 @@ __device__ __forceinline__ void group_flush(const c_t<T> (&acc)[MU][5], const CJ
   }
 }
 
+template <typename T, int DM, int KT, int MU, int MH, int G>
+__device__ __forceinline__ void chunk_dispatch(c_t<T> (&acc)[MH][5], const Stage<T, DM, KT, MU>& st, int kk,
+                                               int nrow, int nuy, int half) {
+  const int lag0 = half == 0 ? 0 : (nuy + 1) / 2;
+  const int nlag = half == 0 ? (nuy + 1) / 2 : nuy / 2;
+  if constexpr (sizeof(T) == 4) {
+    switch (nlag) {
+#define SFFT_NLAG_CASE(NV) \
+  case NV: group_chunk<T, DM, KT, MU, MH, G, NV>(acc, st, kk, nrow, nuy, lag0, nlag); break;
+      SFFT_NLAG_CASE(1) SFFT_NLAG_CASE(2) SFFT_NLAG_CASE(3) SFFT_NLAG_CASE(4) SFFT_NLAG_CASE(5) SFFT_NLAG_CASE(6)
+#undef SFFT_NLAG_CASE
+      default: break;
+    }
+  } else {
+    if (nlag > 0) group_chunk<T, DM, KT, MU, MH, G, 0>(acc, st, kk, nrow, nuy, lag0, nlag);
+  }
+}
+
 template <typename T, int DM, int KT>
-__global__ void __launch_bounds__(KT * n_groups<DM>(), 1)
+__global__ void __launch_bounds__(KT * n_groups<DM>() * kHalves, minb_for<T, DM>())
 k_contract(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, int M, int Nf, int L, int rows_per_cta,
            const c_t<T>* __restrict__ twD) {
   using T2 = c_t<T>;
   constexpr int MU = max_uy<T>();
+  constexpr int MH = max_half<T>();
   constexpr int NMONO = n_mono(DM);
+  constexpr int NG = n_groups<DM>();
   using St = Stage<T, DM, KT, MU>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   St* stages = reinterpret_cast<St*>(smem_raw);
@@ -194,7 +226,8 @@ k_contract(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, int M, i
   for (int i = threadIdx.x; i < nred; i += blockDim.x) red[i] = (T)0;
 
   const int w = (L - 1) / 2;
-  const int g = threadIdx.x / KT, kk = threadIdx.x % KT;
+  const int kk = threadIdx.x % KT, gh = threadIdx.x / KT;     // gh = group * kHalves + half (warp-uniform)
+  const int g = gh / kHalves, half = gh % kHalves;
   const int k0 = blockIdx.x * KT, k = k0 + kk;
   int y0 = blockIdx.y * rows_per_cta, y1 = y0 + rows_per_cta;
   if (y0 < w) y0 = w;
@@ -204,12 +237,10 @@ k_contract(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, int M, i
   const T2* V = reinterpret_cast<const T2*>(ws + job.wts);
   const int* rowflag = reinterpret_cast<const int*>(ws + job.rowflag);
   const int nuy = job.uy_hi - job.uy_lo + 1;
-  const T ysc = (T)2 / (T)(H > 1 ? H - 1 : 1);
-  const bool slot0 = (k == 0);
 
-  T2 acc[MU][5];
+  T2 acc[MH][5];
 #pragma unroll
-  for (int i = 0; i < MU; ++i)
+  for (int i = 0; i < MH; ++i)
 #pragma unroll
     for (int s = 0; s < 5; ++s) { acc[i][s].x = 0; acc[i][s].y = 0; }
 
@@ -229,37 +260,24 @@ k_contract(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, int M, i
     } else {
       cp_async_wait<0>();
     }
-    __syncthreads();
-    const St& st = stages[c & 1];
-    if constexpr (sizeof(T) == 4) {
-      switch (nuy) {
-#define SFFT_NUY_CASE(NV)                                                                                      \
-  case NV:                                                                                                     \
-    if (g == 0) group_chunk<T, DM, KT, MU, 0, NV>(acc, st, kk, slot0, yc, ye, nuy, rowflag, ysc);              \
-    if constexpr (n_groups<DM>() > 1) {                                                                        \
-      if (g == 1) group_chunk<T, DM, KT, MU, 1, NV>(acc, st, kk, slot0, yc, ye, nuy, rowflag, ysc);            \
-    }                                                                                                          \
-    if constexpr (n_groups<DM>() > 2) {                                                                        \
-      if (g == 2) group_chunk<T, DM, KT, MU, 2, NV>(acc, st, kk, slot0, yc, ye, nuy, rowflag, ysc);            \
-    }                                                                                                          \
-    break;
-        SFFT_NUY_CASE(1) SFFT_NUY_CASE(2) SFFT_NUY_CASE(3) SFFT_NUY_CASE(4) SFFT_NUY_CASE(5) SFFT_NUY_CASE(6)
-        SFFT_NUY_CASE(7) SFFT_NUY_CASE(8) SFFT_NUY_CASE(9) SFFT_NUY_CASE(10) SFFT_NUY_CASE(11)
-#undef SFFT_NUY_CASE
-        default: break;
-      }
-    } else {
-      if (g == 0) group_chunk<T, DM, KT, MU, 0, 0>(acc, st, kk, slot0, yc, ye, nuy, rowflag, ysc);
-      if constexpr (n_groups<DM>() > 1) { if (g == 1) group_chunk<T, DM, KT, MU, 1, 0>(acc, st, kk, slot0, yc, ye, nuy, rowflag, ysc); }
-      if constexpr (n_groups<DM>() > 2) { if (g == 2) group_chunk<T, DM, KT, MU, 2, 0>(acc, st, kk, slot0, yc, ye, nuy, rowflag, ysc); }
+    // rows without fit pixels have all-zero weight spectra; skip chunks made only of such rows
+    const int any = __syncthreads_or(threadIdx.x < (unsigned)(ye - yc) ? rowflag[yc + threadIdx.x] : 0);
+    if (any) {
+      const St& st = stages[c & 1];
+      const int nrow = ye - yc;
+      if (g == 0) chunk_dispatch<T, DM, KT, MU, MH, 0>(acc, st, kk, nrow, nuy, half);
+      if constexpr (NG > 1) { if (g == 1) chunk_dispatch<T, DM, KT, MU, MH, 1>(acc, st, kk, nrow, nuy, half); }
+      if constexpr (NG > 2) { if (g == 2) chunk_dispatch<T, DM, KT, MU, MH, 2>(acc, st, kk, nrow, nuy, half); }
     }
     __syncthreads();
   }
   // k-slots past the row (whole warps, since M and KT are multiples of 32) hold junk
   if (k < M) {
-    if (g == 0) group_flush<T, DM, MU, 0>(acc, job, k, Nf, L, red, twD);
-    if constexpr (n_groups<DM>() > 1) { if (g == 1) group_flush<T, DM, MU, 1>(acc, job, k, Nf, L, red, twD); }
-    if constexpr (n_groups<DM>() > 2) { if (g == 2) group_flush<T, DM, MU, 2>(acc, job, k, Nf, L, red, twD); }
+    const int lag0 = half == 0 ? 0 : (nuy + 1) / 2;
+    const int nlag = half == 0 ? (nuy + 1) / 2 : nuy / 2;
+    if (g == 0) group_flush<T, DM, MH, 0>(acc, job, k, Nf, L, lag0, nlag, red, twD);
+    if constexpr (NG > 1) { if (g == 1) group_flush<T, DM, MH, 1>(acc, job, k, Nf, L, lag0, nlag, red, twD); }
+    if constexpr (NG > 2) { if (g == 2) group_flush<T, DM, MH, 2>(acc, job, k, Nf, L, lag0, nlag, red, twD); }
   }
   __syncthreads();
   const double inv = 1.0 / (double)Nf;
@@ -274,8 +292,72 @@ k_contract(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, int M, i
   }
 }
 
-template <typename T, int DM, int KT>
-static cudaError_t contract_launch(const sfft_plan_s* p, int job0, int njobs, int rows_per_cta, void* ws) {
+// The two real bins packed in slot 0 (k = 0 and k = Nf/2, each with h = 1):
+//   g_{a,b}(u) += (1/Nf) sum_y yt^b [V_a(y,0) P(y-u_y,0) + (-1)^{u_x} V_a(y,Nf/2) P(y-u_y,Nf/2)]
+// One CTA per (job, lag u_y); FP32 per-thread partial sums over rows, FP64 block sums.
+template <typename T, int DM>
+__global__ void __launch_bounds__(256)
+k_contract_slot0(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, int M, int Nf, int L) {
+  using T2 = c_t<T>;
+  constexpr int NMONO = n_mono(DM);
+  __shared__ double red[8][2 * NMONO];
+  const CJob job = jobs[blockIdx.x];
+  const int iu = blockIdx.y;
+  const int nuy = job.uy_hi - job.uy_lo + 1;
+  if (iu >= nuy) return;
+  const int uy = job.uy_lo + iu;
+  const int w = (L - 1) / 2;
+  const int64_t HM = (int64_t)H * M;
+  const T2* P = reinterpret_cast<const T2*>(ws + job.probe);
+  const T2* V = reinterpret_cast<const T2*>(ws + job.wts);
+  const int* rowflag = reinterpret_cast<const int*>(ws + job.rowflag);
+  const T ysc = (T)2 / (T)(H > 1 ? H - 1 : 1);
+  T dc[NMONO], nq[NMONO];
+#pragma unroll
+  for (int m = 0; m < NMONO; ++m) { dc[m] = 0; nq[m] = 0; }
+  for (int y = w + (int)threadIdx.x; y < H - w; y += blockDim.x) {
+    if (!rowflag[y]) continue;
+    const T2 p = P[(int64_t)(y - uy) * M];
+    const T yt = (T)y * ysc - (T)1;
+#pragma unroll
+    for (int a = 0; a <= DM; ++a) {
+      const T2 v = V[a * HM + (int64_t)y * M];
+      const T d0 = v.x * p.x, n0 = v.y * p.y;
+      T yp = 1;
+#pragma unroll
+      for (int b = 0; a + b <= DM; ++b) {
+        dc[mono_index(a, b)] += yp * d0;
+        nq[mono_index(a, b)] += yp * n0;
+        yp *= yt;
+      }
+    }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int m = 0; m < NMONO; ++m) {
+    const double s0 = warp_sum((double)dc[m]), s1 = warp_sum((double)nq[m]);
+    if (lane == 0) { red[warp][m] = s0; red[warp][NMONO + m] = s1; }
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * NMONO) {
+    double s = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i][threadIdx.x];
+    red[0][threadIdx.x] = s;   // each entry is read and rewritten by the same thread
+  }
+  __syncthreads();
+  const double inv = 1.0 / (double)Nf;
+  const int nux = job.ux_hi - job.ux_lo + 1;
+  for (int i = threadIdx.x; i < nux * NMONO; i += blockDim.x) {
+    const int m = i % NMONO, ux = job.ux_lo + i / NMONO;
+    const double v = red[0][m] + ((ux & 1) ? -red[0][NMONO + m] : red[0][NMONO + m]);
+    double* out = reinterpret_cast<double*>(ws + job.out);
+    atomicAdd(out + ((uy + w) * L + (ux + w)) * NMONO + m, v * inv);
+  }
+}
+
+template <typename T, int DM>
+static cudaError_t contract_T(const sfft_plan_s* p, int job0, int njobs, int rows_per_cta, void* ws) {
+  constexpr int KT = kt_for<T, DM>();
   const int H = p->d.H, L = p->d.L;
   constexpr int MU = max_uy<T>();
   const size_t smem = 2 * sizeof(Stage<T, DM, KT, MU>) + sizeof(T) * L * L * n_mono(DM);
@@ -283,37 +365,32 @@ static cudaError_t contract_launch(const sfft_plan_s* p, int job0, int njobs, in
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int nb = (H + rows_per_cta - 1) / rows_per_cta;
   dim3 grid((p->M + KT - 1) / KT, nb, njobs);
-  kern<<<grid, KT * n_groups<DM>(), smem, p->stream>>>(p->d_jobs + job0, (char*)ws, H, p->M, p->Nf, L, rows_per_cta,
-                                                       (const c_t<T>*)p->twD);
-  p->nlaunch += 1;
+  kern<<<grid, KT * n_groups<DM>() * kHalves, smem, p->stream>>>(p->d_jobs + job0, (char*)ws, H, p->M, p->Nf, L,
+                                                                 rows_per_cta, (const c_t<T>*)p->twD);
+  k_contract_slot0<T, DM><<<dim3(njobs, max_uy<T>()), 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, H, p->M,
+                                                                          p->Nf, L);
+  p->nlaunch += 2;
   return cudaGetLastError();
 }
 
-template <typename T, int DM>
-static cudaError_t contract_T(const sfft_plan_s* p, int job0, int njobs, int rows_per_cta, int ktile, void* ws) {
-  // shared memory per stage grows with KT; FP64 stages hold twice the bytes, so FP64 uses KT = 64
-  if (sizeof(T) == 8 || ktile == 64) return contract_launch<T, DM, 64>(p, job0, njobs, rows_per_cta, ws);
-  return contract_launch<T, DM, 128>(p, job0, njobs, rows_per_cta, ws);
-}
-
 template <typename T>
-static cudaError_t contract_dm(const sfft_plan_s* p, int DM, int job0, int njobs, int rows_per_cta, int ktile,
-                               void* ws) {
+static cudaError_t contract_dm(const sfft_plan_s* p, int DM, int job0, int njobs, int rows_per_cta, void* ws) {
   switch (DM) {
-    case 0: return contract_T<T, 0>(p, job0, njobs, rows_per_cta, ktile, ws);
-    case 1: return contract_T<T, 1>(p, job0, njobs, rows_per_cta, ktile, ws);
-    case 2: return contract_T<T, 2>(p, job0, njobs, rows_per_cta, ktile, ws);
-    case 3: return contract_T<T, 3>(p, job0, njobs, rows_per_cta, ktile, ws);
-    case 4: return contract_T<T, 4>(p, job0, njobs, rows_per_cta, ktile, ws);
+    case 0: return contract_T<T, 0>(p, job0, njobs, rows_per_cta, ws);
+    case 1: return contract_T<T, 1>(p, job0, njobs, rows_per_cta, ws);
+    case 2: return contract_T<T, 2>(p, job0, njobs, rows_per_cta, ws);
+    case 3: return contract_T<T, 3>(p, job0, njobs, rows_per_cta, ws);
+    case 4: return contract_T<T, 4>(p, job0, njobs, rows_per_cta, ws);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_contract(const sfft_plan_s* p, int DM, int job0, int njobs, int rows_per_cta, int ktile,
                             void* ws) {
+  (void)ktile;
   if (njobs <= 0) return cudaSuccess;
-  return p->fp64 ? contract_dm<double>(p, DM, job0, njobs, rows_per_cta, ktile, ws)
-                 : contract_dm<float>(p, DM, job0, njobs, rows_per_cta, ktile, ws);
+  return p->fp64 ? contract_dm<double>(p, DM, job0, njobs, rows_per_cta, ws)
+                 : contract_dm<float>(p, DM, job0, njobs, rows_per_cta, ws);
 }
 
 }  // namespace sfft
