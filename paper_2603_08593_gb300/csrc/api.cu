@@ -118,7 +118,7 @@ static void build_layout(sfft_plan_s* p) {
   add_region(p->good, cur, npx * B);
   add_region(p->gh, cur, npx * B);
   add_region(p->mfit, cur, npx * B);
-  add_region(p->rowflag, cur, sizeof(int) * H * B);
+  add_region(p->rowflag, cur, sizeof(int) * (size_t)p->rf_stride * B);
   add_region(p->rm, cur, npx * e * B);
   add_region(p->eimg, cur, npx * e * B);
   add_region(p->wspec, cur, slab * p->n_wa * B);
@@ -163,7 +163,8 @@ static void build_jobs(sfft_plan_s* p) {
         j.probe = (int64_t)(p->phat.off + ((size_t)ccd * p->d_batch + i) * slab);
         j.wts = (int64_t)(p->wspec.off + (size_t)ccd * p->n_wa * slab);
         j.out = (int64_t)(p->gkk.off + sizeof(double) * ((size_t)ccd * p->n_hd + d0 + i) * LL * n_mono(p->DM_KK));
-        j.rowflag = (int64_t)(p->rowflag.off + sizeof(int) * (size_t)ccd * H);
+        j.rowflag = (int64_t)(p->rowflag.off + sizeof(int) * (size_t)ccd * p->rf_stride);
+        j.status = (int64_t)(p->status.off + sizeof(int) * (size_t)ccd);
         j.uy_lo = std::max(-w, d.x - w);
         j.uy_hi = std::min(w, d.x + w);
         j.ux_lo = std::max(-w, d.y - w);
@@ -178,7 +179,8 @@ static void build_jobs(sfft_plan_s* p) {
     j.probe = (int64_t)(p->rhat.off + (size_t)ccd * slab);
     j.wts = (int64_t)(p->wspec.off + (size_t)ccd * p->n_wa * slab);
     j.out = (int64_t)(p->gkb.off + sizeof(double) * (size_t)ccd * LL * n_mono(p->DM_KB));
-    j.rowflag = (int64_t)(p->rowflag.off + sizeof(int) * (size_t)ccd * H);
+    j.rowflag = (int64_t)(p->rowflag.off + sizeof(int) * (size_t)ccd * p->rf_stride);
+    j.status = (int64_t)(p->status.off + sizeof(int) * (size_t)ccd);
     j.uy_lo = -w; j.uy_hi = w; j.ux_lo = -w; j.ux_hi = w;
     push_split(j);
   }
@@ -189,7 +191,8 @@ static void build_jobs(sfft_plan_s* p) {
     j.probe = (int64_t)(p->rhat.off + (size_t)ccd * slab);
     j.wts = (int64_t)(p->uspec.off + (size_t)ccd * (p->d.DK + 1) * slab);
     j.out = (int64_t)(p->gbk.off + sizeof(double) * (size_t)ccd * LL * n_mono(p->DM_bK));
-    j.rowflag = (int64_t)(p->rowflag.off + sizeof(int) * (size_t)ccd * H);
+    j.rowflag = (int64_t)(p->rowflag.off + sizeof(int) * (size_t)ccd * p->rf_stride);
+    j.status = (int64_t)(p->status.off + sizeof(int) * (size_t)ccd);
     j.uy_lo = -w; j.uy_hi = w; j.ux_lo = -w; j.ux_hi = w;
     push_split(j);
   }
@@ -200,6 +203,7 @@ static void free_plan_device(sfft_plan_s* p) {
   if (p->twM) cudaFree(p->twM);
   if (p->twN) cudaFree(p->twN);
   if (p->twD) cudaFree(p->twD);
+  if (p->ytab) cudaFree(p->ytab);
   if (p->d_dlist) cudaFree(p->d_dlist);
   if (p->d_hdidx) cudaFree(p->d_hdidx);
   if (p->d_jobs) cudaFree(p->d_jobs);
@@ -269,8 +273,18 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
   }
   p->rows_per_cta = d.rows_per_cta > 0 ? d.rows_per_cta : std::min(d.H, 1024);
   p->ktile = p->M >= 128 ? 128 : 64;
+  // row flags are bulk-copied in 16-byte aligned runs of up to 20 ints past a chunk start
+  p->rf_stride = ((d.H + 32) + 63) / 64 * 64;
   build_layout(p);
   build_jobs(p);
+
+  // yt(y)^b for b = 0..4 per row, FP64 on the host, stored in the path's precision
+  std::vector<double> ypow((size_t)d.H * 8, 0.0);
+  for (int y = 0; y < d.H; ++y) {
+    const double yt = 2.0 * y / (double)(d.H > 1 ? d.H - 1 : 1) - 1.0;
+    double pw = 1.0;
+    for (int b = 0; b < 5; ++b) { ypow[(size_t)y * 8 + b] = pw; pw *= yt; }
+  }
 
   sfft_status_t st = SFFT_OK;
   if (p->fp64) {
@@ -279,12 +293,15 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
     if (st == SFFT_OK) st = upload(&p->twM, a);
     if (st == SFFT_OK) st = upload(&p->twN, b);
     if (st == SFFT_OK) st = upload(&p->twD, c);
+    if (st == SFFT_OK) st = upload(&p->ytab, ypow);
   } else {
     std::vector<float2> a, b, c;
     fill_twiddles<float2, float>(p, a, b, c);
     if (st == SFFT_OK) st = upload(&p->twM, a);
     if (st == SFFT_OK) st = upload(&p->twN, b);
     if (st == SFFT_OK) st = upload(&p->twD, c);
+    std::vector<float> ypf(ypow.begin(), ypow.end());
+    if (st == SFFT_OK) st = upload(&p->ytab, ypf);
   }
   if (st == SFFT_OK) st = upload((void**)&p->d_dlist, p->dlist);
   if (st == SFFT_OK) st = upload((void**)&p->d_hdidx, hdidx);

@@ -49,65 +49,91 @@ template <int DM> constexpr int n_groups() { return DM >= 3 ? 3 : (DM == 2 ? 2 :
 template <typename T> constexpr int max_uy() { return sizeof(T) == 4 ? 11 : 6; }
 constexpr int kHalves = 2;                         // threads sharing the lags of one (k, group)
 template <typename T> constexpr int max_half() { return (max_uy<T>() + 1) / 2; }
-// k-slots per CTA and CTAs per SM the register budget is sized for: the
-// five-monomial groups (DM >= 3) use 32-slot tiles at three CTAs per SM
-// (576 threads, <= 113 registers each); FP64 accumulators take one CTA per SM.
+// k-slots per CTA: the five-monomial groups (DM >= 3) use 32-slot tiles so
+// that three CTAs fit on an SM; FP64 accumulators take one CTA per SM.
 template <typename T, int DM> constexpr int kt_for() { return DM >= 3 ? 32 : 64; }
-template <typename T, int DM> constexpr int minb_for() { return sizeof(T) == 8 ? 1 : (DM >= 3 ? 3 : 2); }
+// register cap per thread: three CTAs of 192 threads (DM >= 3) or two of 256 fit in 64K registers
+template <typename T, int DM> constexpr int maxreg_for() { return sizeof(T) == 8 ? 255 : (DM >= 3 ? 96 : 112); }
 
 // ---------------------------------------------------------------- shared-memory pipeline
 // A CTA walks its band of weight rows y in chunks of kChunk rows.  For each
-// chunk it stages, with cp.async (16-byte copies, double buffered), the probe
-// rows z = y - u_y for every lag of the chunk (kChunk + nuy - 1 rows) and the
-// weight rows of every exponent a <= DM, restricted to the CTA's k-slots.
-// The arithmetic then reads shared memory only.
+// chunk it stages, with bulk (TMA-engine) copies into two alternating stages,
+// the probe rows z = y - u_y for every lag of the chunk (kChunk + nuy - 1
+// rows), the weight rows of every exponent a <= DM (restricted to the CTA's
+// k-slots), the powers of yt and the row flags.  The chunk after next is in
+// flight while a chunk is being consumed; the arithmetic reads shared memory only.
 constexpr int kChunk = 16;
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+// Bulk (TMA-engine) row copies tracked by an mbarrier transaction count.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* m, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* m, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* m) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(m))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* m, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(m)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: every try_wait suspends for at most a hardware-defined
+// interval, so the loop gives up after a bounded time instead of hanging.
+constexpr int kMaxSpin = 1 << 22;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, unsigned parity) {
+  for (int it = 0; it < kMaxSpin; ++it)
+    if (mbar_try_wait(m, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* m) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(m)) : "memory");
+}
 
 template <typename T, int DM, int KT, int MU>
 struct Stage {
   c_t<T> P[kChunk + MU - 1][KT];
   c_t<T> V[DM + 1][kChunk][KT];
-  T ypw[kChunk][8];   // yt^b of the chunk's rows, b = 0..4
+  T ypw[kChunk][8];        // yt^b of the chunk's rows, b = 0..4 (from the plan's power table)
+  int rf[kChunk + 4];      // row flags from the 16-byte aligned row at or below the chunk start
 };
 
-// issue the copies of chunk [yc, ye) into stage `st`
+// Issue the bulk copies of chunk [yc, ye) into stage `st`: one per probe /
+// weight row segment of KT slots, one for the powers of yt and one for the row
+// flags, each from its own thread, counted on `full`.  Thread 0 registers the
+// expected bytes with its arrival; the phase completes once every byte landed.
 template <typename T, int DM, int KT, int MU>
-__device__ __forceinline__ void stage_chunk(Stage<T, DM, KT, MU>& st, const c_t<T>* __restrict__ P,
-                                            const c_t<T>* __restrict__ V, int64_t HM, int M, int k0, int yc, int ye,
-                                            int uy_lo, int uy_hi) {
-  constexpr int PER_ROW = KT * (int)sizeof(c_t<T>) / 16;   // 16-byte pieces per row segment (power of 2)
-  constexpr int SLOTS = 16 / (int)sizeof(c_t<T>);           // k-slots per piece
+__device__ __forceinline__ void produce_chunk(Stage<T, DM, KT, MU>& st, uint64_t* full, const c_t<T>* __restrict__ P,
+                                              const c_t<T>* __restrict__ V, const T* __restrict__ ytab,
+                                              const int* __restrict__ rowflag, int64_t HM, int M, int k0, int yc,
+                                              int ye, int uy_lo, int uy_hi) {
   const int np = (ye - yc) + (uy_hi - uy_lo);             // probe rows z = yc - uy_hi ... ye - 1 - uy_lo
   const int nv = (ye - yc);
-  const bool full = k0 + KT <= M;                           // false only for rows narrower than a tile
-  const c_t<T>* psrc = P + (int64_t)(yc - uy_hi) * M + k0;
-  for (int t = threadIdx.x; t < np * PER_ROW; t += blockDim.x) {
-    const int row = t / PER_ROW, piece = t % PER_ROW;
-    if (!full && k0 + piece * SLOTS >= M) continue;
-    cp_async16(&st.P[row][piece * SLOTS], psrc + (int64_t)row * M + piece * SLOTS);
-  }
-  const c_t<T>* vsrc = V + (int64_t)yc * M + k0;
-  for (int t = threadIdx.x; t < (DM + 1) * kChunk * PER_ROW; t += blockDim.x) {
-    const int piece = t % PER_ROW, rr = t / PER_ROW;
-    const int a = rr / kChunk, yy = rr % kChunk;
-    if (yy >= nv || (!full && k0 + piece * SLOTS >= M)) continue;
-    cp_async16(&st.V[a][yy][piece * SLOTS], vsrc + a * HM + (int64_t)yy * M + piece * SLOTS);
-  }
-  // powers of yt for the chunk's rows (plain stores; read after the next barrier)
-  if (threadIdx.x < nv) {
-    const T ysc = (T)2 / (T)(HM / M > 1 ? HM / M - 1 : 1);
-    const T yt = (T)(yc + (int)threadIdx.x) * ysc - (T)1;
-    T p = 1;
-#pragma unroll
-    for (int b = 0; b < 5; ++b) { st.ypw[threadIdx.x][b] = p; p *= yt; }
+  const int slots = min(KT, M - k0);                       // a tile wider than a tiny row copies less
+  const unsigned seg = (unsigned)(slots * sizeof(c_t<T>)); // multiple of 256 bytes
+  const unsigned ybytes = (unsigned)(nv * 8 * sizeof(T));
+  const unsigned fbytes = (unsigned)((kChunk + 4) * sizeof(int));
+  const int ncopy = np + (DM + 1) * nv;
+  const int t = threadIdx.x;
+  if (t == 0) mbar_arrive_expect_tx(full, seg * (unsigned)ncopy + ybytes + fbytes);
+  if (t < np) {
+    bulk_copy_g2s(&st.P[t][0], P + (int64_t)(yc - uy_hi + t) * M + k0, seg, full);
+  } else if (t < ncopy) {
+    const int r2 = t - np, a = r2 / nv, yy = r2 - a * nv;
+    bulk_copy_g2s(&st.V[a][yy][0], V + a * HM + (int64_t)(yc + yy) * M + k0, seg, full);
+  } else if (t == ncopy) {
+    bulk_copy_g2s(&st.ypw[0][0], ytab + (int64_t)yc * 8, ybytes, full);
+  } else if (t == ncopy + 1) {
+    bulk_copy_g2s(&st.rf[0], rowflag + (yc & ~3), fbytes, full);
   }
 }
 
@@ -120,11 +146,12 @@ __device__ __forceinline__ void stage_chunk(Stage<T, DM, KT, MU>& st, const c_t<
 // by k_contract_slot0.
 template <typename T, int DM, int KT, int MU, int MH, int G, int NLAG>
 __device__ __forceinline__ void group_chunk(c_t<T> (&acc)[MH][5], const Stage<T, DM, KT, MU>& st, int kk,
-                                            int nrow, int nuy, int lag0, int nlag_rt) {
+                                            int nrow, int nuy, int lag0, int nlag_rt, const int* rf) {
   using T2 = c_t<T>;
   using C = GroupCfg<DM, G>;
   const int nlag = NLAG > 0 ? NLAG : nlag_rt;
   for (int r = 0; r < nrow; ++r) {
+    if (!rf[r]) continue;   // no fit pixel on this row: its weight spectra are zero
     const T2 vl = st.V[C::ALO][r][kk];
     T2 vh;
     if constexpr (C::NHI > 0) vh = st.V[C::AHI][r][kk];
@@ -146,6 +173,72 @@ __device__ __forceinline__ void group_chunk(c_t<T> (&acc)[MH][5], const Stage<T,
 #pragma unroll
           for (int s = 0; s < C::NHI; ++s) { acc[i][C::NLO + s].x += yp[s] * hr; acc[i][C::NLO + s].y += yp[s] * hi; }
         }
+      }
+    }
+  }
+}
+
+// FP32 hot loop with explicit 32-bit shared-memory addresses: three row
+// pointers advance by a constant per row and every load uses a compile-time
+// immediate offset, so address arithmetic costs a few integer adds per row.
+template <int OFF>
+__device__ __forceinline__ float2 lds2(unsigned addr) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2+%3];" : "=f"(v.x), "=f"(v.y) : "r"(addr), "n"(OFF));
+  return v;
+}
+__device__ __forceinline__ float4 lds4(unsigned addr) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ float lds1(unsigned addr) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1+16];" : "=f"(v) : "r"(addr));
+  return v;
+}
+
+template <int NLAG, int KT, int I>
+__device__ __forceinline__ float2 lag_load(unsigned p_lo) {
+  // lag i lives (NLAG - 1 - i) staged rows above the lowest row of this thread's lags
+  return lds2<(NLAG - 1 - I) * KT * 8>(p_lo);
+}
+
+template <int DM, int KT, int MU, int MH, int G, int NLAG>
+__device__ __forceinline__ void group_chunk_f32(c_t<float> (&acc)[MH][5], const Stage<float, DM, KT, MU>& st, int kk,
+                                                int nrow, int nuy, int lag0, const int* rf) {
+  using C = GroupCfg<DM, G>;
+  unsigned vlo = (unsigned)__cvta_generic_to_shared(&st.V[C::ALO][0][kk]);
+  unsigned vhi = (unsigned)__cvta_generic_to_shared(&st.V[C::NHI > 0 ? C::AHI : C::ALO][0][kk]);
+  unsigned ypa = (unsigned)__cvta_generic_to_shared(&st.ypw[0][0]);
+  // staged row of lag lag0 + NLAG - 1 for r = 0
+  unsigned plo = (unsigned)__cvta_generic_to_shared(&st.P[nuy - 1 - lag0 - (NLAG - 1)][kk]);
+  for (int r = 0; r < nrow; ++r, vlo += KT * 8, vhi += KT * 8, ypa += 8 * 4, plo += KT * 8) {
+    if (!rf[r]) continue;   // no fit pixel on this row: its weight spectra are zero
+    const float2 vl = lds2<0>(vlo);
+    float2 vh = vl;
+    if constexpr (C::NHI > 0) vh = lds2<0>(vhi);
+    const float4 y4 = lds4(ypa);
+    const float yp[5] = {y4.x, y4.y, y4.z, y4.w, lds1(ypa)};
+    float2 pv[NLAG];
+#pragma unroll
+    for (int i = 0; i < NLAG; ++i) {
+      if (i == 0) pv[i] = lag_load<NLAG, KT, 0>(plo);
+      if constexpr (NLAG > 1) { if (i == 1) pv[i] = lag_load<NLAG, KT, (NLAG > 1 ? 1 : 0)>(plo); }
+      if constexpr (NLAG > 2) { if (i == 2) pv[i] = lag_load<NLAG, KT, (NLAG > 2 ? 2 : 0)>(plo); }
+      if constexpr (NLAG > 3) { if (i == 3) pv[i] = lag_load<NLAG, KT, (NLAG > 3 ? 3 : 0)>(plo); }
+      if constexpr (NLAG > 4) { if (i == 4) pv[i] = lag_load<NLAG, KT, (NLAG > 4 ? 4 : 0)>(plo); }
+      if constexpr (NLAG > 5) { if (i == 5) pv[i] = lag_load<NLAG, KT, (NLAG > 5 ? 5 : 0)>(plo); }
+    }
+#pragma unroll
+    for (int i = 0; i < NLAG; ++i) {
+      const float xr = vl.x * pv[i].x + vl.y * pv[i].y, xi = vl.x * pv[i].y - vl.y * pv[i].x;
+#pragma unroll
+      for (int s = 0; s < C::NLO; ++s) { acc[i][s].x += yp[s] * xr; acc[i][s].y += yp[s] * xi; }
+      if constexpr (C::NHI > 0) {
+        const float hr = vh.x * pv[i].x + vh.y * pv[i].y, hi = vh.x * pv[i].y - vh.y * pv[i].x;
+#pragma unroll
+        for (int s = 0; s < C::NHI; ++s) { acc[i][C::NLO + s].x += yp[s] * hr; acc[i][C::NLO + s].y += yp[s] * hi; }
       }
     }
   }
@@ -192,26 +285,28 @@ __device__ __forceinline__ void group_flush(const c_t<T> (&acc)[MH][5], const CJ
 
 template <typename T, int DM, int KT, int MU, int MH, int G>
 __device__ __forceinline__ void chunk_dispatch(c_t<T> (&acc)[MH][5], const Stage<T, DM, KT, MU>& st, int kk,
-                                               int nrow, int nuy, int half) {
+                                               int nrow, int nuy, int half, const int* rf) {
   const int lag0 = half == 0 ? 0 : (nuy + 1) / 2;
   const int nlag = half == 0 ? (nuy + 1) / 2 : nuy / 2;
   if constexpr (sizeof(T) == 4) {
     switch (nlag) {
 #define SFFT_NLAG_CASE(NV) \
-  case NV: group_chunk<T, DM, KT, MU, MH, G, NV>(acc, st, kk, nrow, nuy, lag0, nlag); break;
+  case NV: group_chunk_f32<DM, KT, MU, MH, G, NV>(acc, st, kk, nrow, nuy, lag0, rf); break;
       SFFT_NLAG_CASE(1) SFFT_NLAG_CASE(2) SFFT_NLAG_CASE(3) SFFT_NLAG_CASE(4) SFFT_NLAG_CASE(5) SFFT_NLAG_CASE(6)
 #undef SFFT_NLAG_CASE
       default: break;
     }
   } else {
-    if (nlag > 0) group_chunk<T, DM, KT, MU, MH, G, 0>(acc, st, kk, nrow, nuy, lag0, nlag);
+    if (nlag > 0) group_chunk<T, DM, KT, MU, MH, G, 0>(acc, st, kk, nrow, nuy, lag0, nlag, rf);
   }
 }
 
+template <typename T, int DM, int KT> constexpr int cta_threads() { return KT * n_groups<DM>() * kHalves; }
+
 template <typename T, int DM, int KT>
-__global__ void __launch_bounds__(KT * n_groups<DM>() * kHalves, minb_for<T, DM>())
+__global__ void __launch_bounds__(cta_threads<T, DM, KT>()) __maxnreg__((maxreg_for<T, DM>()))
 k_contract(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, int M, int Nf, int L, int rows_per_cta,
-           const c_t<T>* __restrict__ twD) {
+           const c_t<T>* __restrict__ twD, const T* __restrict__ ytab) {
   using T2 = c_t<T>;
   constexpr int MU = max_uy<T>();
   constexpr int MH = max_half<T>();
@@ -220,10 +315,17 @@ k_contract(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, int M, i
   using St = Stage<T, DM, KT, MU>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   St* stages = reinterpret_cast<St*>(smem_raw);
-  T* red = reinterpret_cast<T*>(smem_raw + 2 * sizeof(St));   // [L][L][n_mono(DM)]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + 2 * sizeof(St));    // [2]
+  T* red = reinterpret_cast<T*>(smem_raw + 2 * sizeof(St) + 32);              // [L][L][n_mono(DM)]
   const CJob job = jobs[blockIdx.z];
   const int nred = L * L * NMONO;
   for (int i = threadIdx.x; i < nred; i += blockDim.x) red[i] = (T)0;
+  if (threadIdx.x == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
 
   const int w = (L - 1) / 2;
   const int kk = threadIdx.x % KT, gh = threadIdx.x / KT;     // gh = group * kHalves + half (warp-uniform)
@@ -245,30 +347,30 @@ k_contract(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, int M, i
     for (int s = 0; s < 5; ++s) { acc[i][s].x = 0; acc[i][s].y = 0; }
 
   const int nchunk = y1 > y0 ? (y1 - y0 + kChunk - 1) / kChunk : 0;
-  if (nchunk > 0) {
-    stage_chunk<T, DM, KT, MU>(stages[0], P, V, HM, M, k0, y0, min(y0 + kChunk, y1), job.uy_lo, job.uy_hi);
-    cp_async_commit();
-  }
+  if (nchunk > 0)
+    produce_chunk<T, DM, KT, MU>(stages[0], &full[0], P, V, ytab, rowflag, HM, M, k0, y0, min(y0 + kChunk, y1),
+                                 job.uy_lo, job.uy_hi);
   for (int c = 0; c < nchunk; ++c) {
     const int yc = y0 + c * kChunk, ye = min(yc + kChunk, y1);
-    if (c + 1 < nchunk) {
+    if (c + 1 < nchunk) {   // stage (c+1)&1 was released by the barrier that closed chunk c - 1
       const int yn = yc + kChunk;
-      stage_chunk<T, DM, KT, MU>(stages[(c + 1) & 1], P, V, HM, M, k0, yn, min(yn + kChunk, y1), job.uy_lo,
-                                 job.uy_hi);
-      cp_async_commit();
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
+      produce_chunk<T, DM, KT, MU>(stages[(c + 1) & 1], &full[(c + 1) & 1], P, V, ytab, rowflag, HM, M, k0, yn,
+                                   min(yn + kChunk, y1), job.uy_lo, job.uy_hi);
     }
-    // rows without fit pixels have all-zero weight spectra; skip chunks made only of such rows
-    const int any = __syncthreads_or(threadIdx.x < (unsigned)(ye - yc) ? rowflag[yc + threadIdx.x] : 0);
-    if (any) {
-      const St& st = stages[c & 1];
-      const int nrow = ye - yc;
-      if (g == 0) chunk_dispatch<T, DM, KT, MU, MH, 0>(acc, st, kk, nrow, nuy, half);
-      if constexpr (NG > 1) { if (g == 1) chunk_dispatch<T, DM, KT, MU, MH, 1>(acc, st, kk, nrow, nuy, half); }
-      if constexpr (NG > 2) { if (g == 2) chunk_dispatch<T, DM, KT, MU, MH, 2>(acc, st, kk, nrow, nuy, half); }
+    // stage c & 1 serves chunks c, c + 2, ...: its (c >> 1)-th phase completes chunk c
+    const bool landed = mbar_wait_bounded(&full[c & 1], (unsigned)((c >> 1) & 1));
+    if (!__syncthreads_and(landed)) {
+      // copies never completed: flag the CCD, give the in-flight copies a bounded
+      // chance to drain, and leave without touching the accumulators
+      if (threadIdx.x == 0) atomicOr(reinterpret_cast<int*>(ws + job.status), 4);
+      if (c + 1 < nchunk) mbar_wait_bounded(&full[(c + 1) & 1], (unsigned)(((c + 1) >> 1) & 1));
+      return;
     }
+    const St& st = stages[c & 1];
+    const int* rf = st.rf + (yc & 3);
+    if (g == 0) chunk_dispatch<T, DM, KT, MU, MH, 0>(acc, st, kk, ye - yc, nuy, half, rf);
+    if constexpr (NG > 1) { if (g == 1) chunk_dispatch<T, DM, KT, MU, MH, 1>(acc, st, kk, ye - yc, nuy, half, rf); }
+    if constexpr (NG > 2) { if (g == 2) chunk_dispatch<T, DM, KT, MU, MH, 2>(acc, st, kk, ye - yc, nuy, half, rf); }
     __syncthreads();
   }
   // k-slots past the row (whole warps, since M and KT are multiples of 32) hold junk
@@ -360,13 +462,14 @@ static cudaError_t contract_T(const sfft_plan_s* p, int job0, int njobs, int row
   constexpr int KT = kt_for<T, DM>();
   const int H = p->d.H, L = p->d.L;
   constexpr int MU = max_uy<T>();
-  const size_t smem = 2 * sizeof(Stage<T, DM, KT, MU>) + sizeof(T) * L * L * n_mono(DM);
+  const size_t smem = 2 * sizeof(Stage<T, DM, KT, MU>) + 32 + sizeof(T) * L * L * n_mono(DM);
   auto kern = k_contract<T, DM, KT>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int nb = (H + rows_per_cta - 1) / rows_per_cta;
   dim3 grid((p->M + KT - 1) / KT, nb, njobs);
-  kern<<<grid, KT * n_groups<DM>() * kHalves, smem, p->stream>>>(p->d_jobs + job0, (char*)ws, H, p->M, p->Nf, L,
-                                                                 rows_per_cta, (const c_t<T>*)p->twD);
+  kern<<<grid, cta_threads<T, DM, KT>(), smem, p->stream>>>(p->d_jobs + job0, (char*)ws, H, p->M, p->Nf,
+                                                                      L, rows_per_cta, (const c_t<T>*)p->twD,
+                                                                      (const T*)p->ytab);
   k_contract_slot0<T, DM><<<dim3(njobs, max_uy<T>()), 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, H, p->M,
                                                                           p->Nf, L);
   p->nlaunch += 2;

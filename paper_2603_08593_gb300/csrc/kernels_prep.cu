@@ -117,7 +117,7 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 k_moments(const uint8_t* __restrict__ mfit, const float* __restrict__ S, const double* __restrict__ sky,
           const T* __restrict__ E, int H, int W, int DBB, int DV, double* __restrict__ mom_bb, int64_t bb_stride,
-          double* __restrict__ mom_v, int64_t v_stride, int* __restrict__ rowflag) {
+          double* __restrict__ mom_v, int64_t v_stride, int* __restrict__ rowflag, int rf_stride) {
   __shared__ double red[8];
   const int y = blockIdx.x, ccd = blockIdx.y;
   const int64_t row = ((int64_t)ccd * H + y) * W;
@@ -143,7 +143,7 @@ k_moments(const uint8_t* __restrict__ mfit, const float* __restrict__ S, const d
   }
   const double yt = 2.0 * y / (double)(H > 1 ? H - 1 : 1) - 1.0;
   const double c = block_sum<256>((double)cnt, red);
-  if (threadIdx.x == 0 && rowflag) rowflag[(int64_t)ccd * H + y] = c > 0 ? 1 : 0;
+  if (threadIdx.x == 0 && rowflag) rowflag[(int64_t)ccd * rf_stride + y] = c > 0 ? 1 : 0;
   // every thread must take part in block_sum; branch on c only after the broadcast
   __shared__ double cb;
   if (threadIdx.x == 0) cb = c;
@@ -225,13 +225,13 @@ static cudaError_t moments_T(const sfft_plan_s* p, const float* S, const void* e
     cudaMemsetAsync(bb, 0, sizeof(double) * nbb * B, p->stream);
     cudaMemsetAsync(bv, 0, sizeof(double) * nb * B, p->stream);
     k_moments<T><<<g, 256, 0, p->stream>>>(mfit, S, sky, (const T*)nullptr, H, W, p->DM_BB, p->d.DB, bb, nbb, bv,
-                                           nb, ws_at<int>(ws, p->rowflag));
+                                           nb, ws_at<int>(ws, p->rowflag), p->rf_stride);
   } else {
     double* bv = ws_at<double>(ws, p->mom_b);
     const int nb = n_mono(p->d.DB);
     cudaMemsetAsync(bv, 0, sizeof(double) * nb * B, p->stream);
     k_moments<T><<<g, 256, 0, p->stream>>>(mfit, nullptr, sky, (const T*)eimg, H, W, 0, p->d.DB, nullptr, 0, bv,
-                                           nb, nullptr);
+                                           nb, nullptr, 0);
   }
   p->nlaunch += 1;
   return cudaGetLastError();

@@ -18,7 +18,7 @@ namespace sfft {
 // (FP64) into out[(uy+w)][(ux+w)][m] at offset `out`.  Offsets are bytes from
 // the workspace base so that job tables are built once per plan.
 struct CJob {
-  int64_t probe, wts, out, rowflag;
+  int64_t probe, wts, out, rowflag, status;
   int uy_lo, uy_hi, ux_lo, ux_hi;
 };
 
@@ -43,6 +43,8 @@ struct sfft_plan_s {
   void* twM = nullptr;                // c_t [M]       exp(-2 pi i j / M)
   void* twN = nullptr;                // c_t [M]       exp(-2 pi i k / Nf)
   void* twD = nullptr;                // c_t [Nf]      (cos, sin)(2 pi j / Nf)
+  void* ytab = nullptr;               // T [H][8]      yt(y)^b, b = 0..4 (zero padded)
+  int rf_stride = 0;                  // ints per CCD in the row-flag array (padded, multiple of 64)
   int2* d_dlist = nullptr;            // device copy of dlist
   int* d_hdidx = nullptr;             // [(2L-1)][(2L-1)] -> half-plane index or -1
   sfft::CJob* d_jobs = nullptr;       // job table (device), built at plan time
