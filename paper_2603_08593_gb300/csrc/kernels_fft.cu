@@ -30,24 +30,20 @@ struct RowFFT {
   using T2 = c_t<T>;
   static constexpr int TPR = M / 16;              // threads per row
   static constexpr int RPB = kFftThreads / TPR;   // rows per CTA
-  static constexpr int SROW = fft_pad(M) + 1;     // padded floats per row plane
-  static constexpr size_t smem_bytes() { return sizeof(T) * 2 * (size_t)SROW * RPB; }
+  static constexpr int SROW = fft_pad(M) + 1;     // padded complex elements per row
+  static constexpr size_t smem_bytes() { return sizeof(T2) * (size_t)SROW * RPB; }
 
   // One Stockham pass of radix R with span NS over shared memory (in place:
   // every thread loads its inputs, the CTA synchronizes, then stores).
   template <int R, int NS>
-  __device__ static void pass(T* re, T* im, int t, const T2* __restrict__ tw) {
+  __device__ static void pass(T2* buf, int t, const T2* __restrict__ tw) {
     constexpr int Q = 16 / R;
     T2 v[Q][R];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const int j = t + TPR * q;
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int i = fft_pad(j + r * (M / R));
-        v[q][r].x = re[i];
-        v[q][r].y = im[i];
-      }
+      for (int r = 0; r < R; ++r) v[q][r] = buf[fft_pad(j + r * (M / R))];
     }
     __syncthreads();
 #pragma unroll
@@ -61,51 +57,43 @@ struct RowFFT {
       fft_reg<R>(v[q]);
       const int base = (j / NS) * NS * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int i = fft_pad(base + r * NS);
-        re[i] = v[q][r].x;
-        im[i] = v[q][r].y;
-      }
+      for (int r = 0; r < R; ++r) buf[fft_pad(base + r * NS)] = v[q][r];
     }
     __syncthreads();
   }
 
   template <int NS>
-  __device__ static void passes(T* re, T* im, int t, const T2* tw) {
+  __device__ static void passes(T2* buf, int t, const T2* tw) {
     if constexpr (NS < M) {
       constexpr int R = (M / NS) >= 16 ? 16 : (M / NS);
-      pass<R, NS>(re, im, t, tw);
-      passes<NS * R>(re, im, t, tw);
+      pass<R, NS>(buf, t, tw);
+      passes<NS * R>(buf, t, tw);
     }
   }
 
   // v[r] = z[t + TPR r] (the first pass's inputs, radix 16, span 1) -> spectrum row `out`
-  __device__ static void run(T2 (&v)[16], T* re, T* im, int t, bool valid, const T2* __restrict__ twM,
+  __device__ static void run(T2 (&v)[16], T2* buf, int t, bool valid, const T2* __restrict__ twM,
                              const T2* __restrict__ twN, T2* __restrict__ out) {
     // first pass straight from registers
     fft_reg<16>(v);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      const int i = fft_pad(t * 16 + r);
-      re[i] = v[r].x;
-      im[i] = v[r].y;
-    }
+    for (int r = 0; r < 16; ++r) buf[fft_pad(t * 16 + r)] = v[r];
     __syncthreads();
-    passes<16>(re, im, t, twM);
+    passes<16>(buf, t, twM);
     // real-input split: X[k] = E + (-i) exp(-2 pi i k / Nf) O
     if (valid) {
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const int k = t + TPR * q;
         const int km = (M - k) & (M - 1);
-        const T zr = re[fft_pad(k)], zi = im[fft_pad(k)], mr = re[fft_pad(km)], mi = im[fft_pad(km)];
+        const T2 zk = buf[fft_pad(k)], zm = buf[fft_pad(km)];
         T2 X;
         if (k == 0) {
-          X.x = zr + zi;
-          X.y = zr - zi;
+          X.x = zk.x + zk.y;
+          X.y = zk.x - zk.y;
         } else {
-          const T er = (T)0.5 * (zr + mr), ei = (T)0.5 * (zi - mi);
-          const T orr = (T)0.5 * (zr - mr), oi = (T)0.5 * (zi + mi);
+          const T er = (T)0.5 * (zk.x + zm.x), ei = (T)0.5 * (zk.y - zm.y);
+          const T orr = (T)0.5 * (zk.x - zm.x), oi = (T)0.5 * (zk.y + zm.y);
           const T2 wk = twN[k];
           const T wr = wk.x * orr - wk.y * oi, wi = wk.x * oi + wk.y * orr;
           X.x = er + wi;
@@ -127,8 +115,7 @@ k_rfft_prod(const T* __restrict__ Rm, int H, int W, const int2* __restrict__ dl,
   using F = RowFFT<T, M>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int rloc = threadIdx.x / F::TPR, t = threadIdx.x % F::TPR;
-  T* re = reinterpret_cast<T*>(smem_raw) + (size_t)rloc * 2 * F::SROW;
-  T* im = re + F::SROW;
+  c_t<T>* buf = reinterpret_cast<c_t<T>*>(smem_raw) + (size_t)rloc * F::SROW;
   const int jd = blockIdx.y, ccd = blockIdx.z;
   int dy = 0, dx = 0;
   if (!self) { const int2 dd = dl[d0 + jd]; dy = dd.x; dx = dd.y; }
@@ -154,7 +141,58 @@ k_rfft_prod(const T* __restrict__ Rm, int H, int W, const int2* __restrict__ dl,
       v[r].x = v0;
       v[r].y = v1;
     }
-    F::run(v, re, im, t, valid, twM, twN, obase + (int64_t)(valid ? y : 0) * M);
+    F::run(v, buf, t, valid, twM, twN, obase + (int64_t)(valid ? y : 0) * M);
+  }
+}
+
+// Products for one image row y and one kernel-offset row difference d_y: the
+// CTA stages R_m(y, .) and R_m(y + d_y, .) in shared memory (zero padded by
+// 16 on each side for the d_x shift), then forms RPB products at a time -- one
+// per d_x of this d_y in the batch -- and transforms them side by side.
+// grid = (H, number of d_y values met by the batch [d0, d0 + nd), batch).
+template <typename T, int M>
+__global__ void __launch_bounds__(kFftThreads)
+k_rfft_prod_dy(const T* __restrict__ Rm, int H, int W, int L, int d0, int nd, c_t<T>* __restrict__ out,
+               int64_t slab_stride, int64_t ccd_stride_out, const c_t<T>* __restrict__ twM,
+               const c_t<T>* __restrict__ twN) {
+  using F = RowFFT<T, M>;
+  constexpr int NF = 2 * M, PADX = 16;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  c_t<T>* bufs = reinterpret_cast<c_t<T>*>(smem_raw);
+  T* r1 = reinterpret_cast<T*>(smem_raw + F::smem_bytes());   // [NF]
+  T* r2 = r1 + NF;                                              // [NF + 2 PADX]
+  const int rloc = threadIdx.x / F::TPR, t = threadIdx.x % F::TPR;
+  c_t<T>* buf = bufs + (size_t)rloc * F::SROW;
+  const int y = blockIdx.x, ccd = blockIdx.z;
+  // half-plane order: d_y = 0 holds d_x = 0..L-1, each d_y > 0 holds d_x = -(L-1)..L-1
+  auto first_of = [L](int dy) { return dy == 0 ? 0 : L + (2 * L - 1) * (dy - 1); };
+  auto dy_of = [L](int id) { return id < L ? 0 : 1 + (id - L) / (2 * L - 1); };
+  const int dy = dy_of(d0) + blockIdx.y;
+  const int lo = max(d0, first_of(dy)), hi = min(d0 + nd, first_of(dy) + (dy == 0 ? L : 2 * L - 1));
+  if (lo >= hi) return;   // uniform over the CTA
+  const T* img = Rm + (int64_t)ccd * H * W;
+  const bool ok2 = y + dy < H;
+  for (int x = threadIdx.x; x < NF; x += blockDim.x) r1[x] = x < W ? img[(int64_t)y * W + x] : (T)0;
+  for (int x = threadIdx.x; x < NF + 2 * PADX; x += blockDim.x) {
+    const int gx = x - PADX;
+    r2[x] = (ok2 && gx >= 0 && gx < W) ? img[(int64_t)(y + dy) * W + gx] : (T)0;
+  }
+  __syncthreads();
+  const int dx0 = dy == 0 ? 0 : -(L - 1);
+  c_t<T>* obase = out + (int64_t)ccd * ccd_stride_out + (int64_t)y * M;
+  for (int id0 = lo; id0 < hi; id0 += F::RPB) {
+    const int id = id0 + rloc;
+    const bool valid = id < hi;
+    const int dx = dx0 + (id - first_of(dy));
+    c_t<T> v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int x0 = 2 * (t + F::TPR * r);
+      // products vanish where R_m(y + d_y, x + d_x) falls outside the image (r2 is zero there)
+      v[r].x = valid ? r1[x0] * r2[x0 + dx + PADX] : (T)0;
+      v[r].y = valid ? r1[x0 + 1] * r2[x0 + 1 + dx + PADX] : (T)0;
+    }
+    F::run(v, buf, t, valid, twM, twN, obase + (int64_t)(valid ? id - d0 : 0) * slab_stride);
   }
 }
 
@@ -167,8 +205,7 @@ k_rfft_weight(const uint8_t* __restrict__ Mfit, const float* __restrict__ S, con
   using F = RowFFT<T, M>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int rloc = threadIdx.x / F::TPR, t = threadIdx.x % F::TPR;
-  T* re = reinterpret_cast<T*>(smem_raw) + (size_t)rloc * 2 * F::SROW;
-  T* im = re + F::SROW;
+  c_t<T>* buf = reinterpret_cast<c_t<T>*>(smem_raw) + (size_t)rloc * F::SROW;
   const int a = a0 + blockIdx.y, ccd = blockIdx.z;
   const int64_t img_off = (int64_t)ccd * H * W;
   const T sS = S ? (T)sky[2 * ccd + 1] : (T)0;
@@ -199,7 +236,7 @@ k_rfft_weight(const uint8_t* __restrict__ Mfit, const float* __restrict__ S, con
       v[r].x = vv[0];
       v[r].y = vv[1];
     }
-    F::run(v, re, im, t, valid, twM, twN, obase + (int64_t)(valid ? y : 0) * M);
+    F::run(v, buf, t, valid, twM, twN, obase + (int64_t)(valid ? y : 0) * M);
   }
 }
 
@@ -242,12 +279,29 @@ static cudaError_t run_weight(const sfft_plan_s* p, const uint8_t* Mfit, const f
     default: return cudaErrorInvalidValue;           \
   }
 
+template <typename T, int M>
+static cudaError_t run_prod_dy(const sfft_plan_s* p, const T* Rm, int d0, int nd, c_t<T>* out, int64_t slab_stride,
+                               int64_t ccd_stride) {
+  using F = RowFFT<T, M>;
+  const size_t smem = F::smem_bytes() + sizeof(T) * (size_t)(2 * (2 * M) + 32);
+  auto kern = k_rfft_prod_dy<T, M>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int L = p->d.L;
+  auto dy_of = [L](int id) { return id < L ? 0 : 1 + (id - L) / (2 * L - 1); };
+  const int ndy = dy_of(d0 + nd - 1) - dy_of(d0) + 1;
+  dim3 grid(p->d.H, ndy, p->d.batch);
+  kern<<<grid, kFftThreads, smem, p->stream>>>(Rm, p->d.H, p->d.W, L, d0, nd, out, slab_stride, ccd_stride,
+                                               (const c_t<T>*)p->twM, (const c_t<T>*)p->twN);
+  p->nlaunch += 1;
+  return cudaGetLastError();
+}
+
 template <typename T>
 static cudaError_t prod_T(const sfft_plan_s* p, int d0, int nd, void* ws) {
   const int64_t HM = (int64_t)p->d.H * p->M;
   const T* Rm = ws_at<T>(ws, p->rm);
   c_t<T>* out = ws_at<c_t<T>>(ws, p->phat);
-  SFFT_DISPATCH_M(p->M, (run_prod<T, M>(p, Rm, d0, nd, 0, out, HM, HM * p->d_batch)))
+  SFFT_DISPATCH_M(p->M, (run_prod_dy<T, M>(p, Rm, d0, nd, out, HM, HM * p->d_batch)))
 }
 
 template <typename T>

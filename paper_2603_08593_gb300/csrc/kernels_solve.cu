@@ -6,8 +6,9 @@
 // M_fit psi_q psi_q', b_(j,p) = g^{bK}_p(u_j), b_q = moment of M_fit psi_q S'.
 //
 // Solve: Jacobi equilibration D_s = diag(A)^-1/2, right-looking blocked
-// Cholesky (32 x 32 blocks: diagonal factor, panel triangular solve, trailing
-// update) of D_s A D_s, forward and backward substitution, theta = D_s y.
+// Cholesky (32 x 32 blocks: one launch factors the diagonal block and solves
+// the panel below it, one launch applies the trailing update) of D_s A D_s,
+// blocked forward and backward substitution, theta = D_s y.
 // Per-CCD status flags (never a trap): 1 = not positive definite, 2 = non-finite.
 #include "common.cuh"
 #include "plan.h"
@@ -117,53 +118,41 @@ k_chol_init(const double* __restrict__ A, double* __restrict__ Lf, double* __res
   }
 }
 
-// factor the diagonal block [kb, kb+nb) in shared memory
-__global__ void __launch_bounds__(NBK * NBK / 4)
-k_chol_diag(double* __restrict__ Lf, int* __restrict__ status, int N, int kb) {
+// Factor the diagonal block [kb, kb+nb) in shared memory (one warp, lane i
+// owns row i) and solve this CTA's 32 panel rows r >= kb + nb against it:
+// X = A_rk L_kk^-T.  Every panel CTA factors the small block itself, so one
+// launch per block column does both; CTA 0 writes the factor back and reports
+// a non-positive or non-finite pivot.  blockDim = 32.
+__global__ void __launch_bounds__(NBK)
+k_chol_panel(double* __restrict__ Lf, int* __restrict__ status, int N, int kb) {
   __shared__ double blk[NBK][NBK + 1];
-  const int ccd = blockIdx.x;
+  const int ccd = blockIdx.y, lane = threadIdx.x;
   double* l = Lf + (int64_t)ccd * N * N;
   const int nb = min(NBK, N - kb);
-  for (int t = threadIdx.x; t < NBK * NBK; t += blockDim.x) {
-    const int i = t / NBK, j = t % NBK;
-    blk[i][j] = (i < nb && j <= i) ? l[(int64_t)(kb + i) * N + kb + j] : 0.0;
-  }
-  __syncthreads();
+  for (int i = 0; i < NBK; ++i) blk[i][lane] = (i < nb && lane <= i) ? l[(int64_t)(kb + i) * N + kb + lane] : 0.0;
+  __syncwarp();
+  bool bad = false, nonfinite = false;
   for (int c = 0; c < nb; ++c) {
-    if (threadIdx.x == 0) {
+    if (lane == c) {
       double d = blk[c][c];
-      if (!(d > 0.0) || !isfinite(d)) { atomicOr(&status[ccd], isfinite(d) ? 1 : 2); d = 1.0; }
+      if (!(d > 0.0) || !isfinite(d)) { bad = true; nonfinite = !isfinite(d); d = 1.0; }
       blk[c][c] = sqrt(d);
     }
-    __syncthreads();
-    const double inv = 1.0 / blk[c][c];
-    for (int i = c + 1 + threadIdx.x; i < nb; i += blockDim.x) blk[i][c] *= inv;
-    __syncthreads();
-    for (int t = threadIdx.x; t < NBK * NBK; t += blockDim.x) {
-      const int i = t / NBK, j = t % NBK;
-      if (i > c && j > c && j <= i && i < nb) blk[i][j] -= blk[i][c] * blk[j][c];
+    __syncwarp();
+    if (lane > c && lane < nb) blk[lane][c] /= blk[c][c];
+    __syncwarp();
+    if (lane > c && lane < nb) {
+      const double lic = blk[lane][c];
+      for (int j = c + 1; j <= lane; ++j) blk[lane][j] -= lic * blk[j][c];
     }
-    __syncthreads();
+    __syncwarp();
   }
-  for (int t = threadIdx.x; t < NBK * NBK; t += blockDim.x) {
-    const int i = t / NBK, j = t % NBK;
-    if (i < nb && j <= i) l[(int64_t)(kb + i) * N + kb + j] = blk[i][j];
+  if (blockIdx.x == 0) {
+    if (bad) atomicOr(&status[ccd], nonfinite ? 2 : 1);
+    for (int i = 0; i < nb; ++i)
+      if (lane <= i) l[(int64_t)(kb + i) * N + kb + lane] = blk[i][lane];
   }
-}
-
-// panel: rows r >= kb + nb, columns [kb, kb+nb): X = A_rk L_kk^-T (row-wise forward substitution)
-__global__ void __launch_bounds__(NBK)
-k_chol_panel(double* __restrict__ Lf, int N, int kb) {
-  __shared__ double lkk[NBK][NBK + 1];
-  const int ccd = blockIdx.y;
-  double* l = Lf + (int64_t)ccd * N * N;
-  const int nb = min(NBK, N - kb);
-  for (int t = threadIdx.x; t < NBK * NBK; t += blockDim.x) {
-    const int i = t / NBK, j = t % NBK;
-    lkk[i][j] = (i < nb && j <= i) ? l[(int64_t)(kb + i) * N + kb + j] : 0.0;
-  }
-  __syncthreads();
-  const int r = kb + nb + blockIdx.x * NBK + threadIdx.x;
+  const int r = kb + nb + blockIdx.x * NBK + lane;
   if (r >= N) return;
   double x[NBK];
   double* row = l + (int64_t)r * N + kb;
@@ -174,8 +163,8 @@ k_chol_panel(double* __restrict__ Lf, int N, int kb) {
     if (c < nb) {
       double v = x[c];
 #pragma unroll
-      for (int t = 0; t < c; ++t) v -= x[t] * lkk[c][t];
-      x[c] = v / lkk[c][c];
+      for (int t = 0; t < c; ++t) v -= x[t] * blk[c][t];
+      x[c] = v / blk[c][c];
     }
   }
 #pragma unroll
@@ -212,49 +201,63 @@ k_chol_update(double* __restrict__ Lf, int N, int kb) {
   }
 }
 
-// x = D_s (L L^T)^-1 D_s rhs, one CTA per CCD; x may alias nothing in ws except `tmp`
+// x = D_s (L L^T)^-1 D_s rhs, one CTA per CCD.  Blocked substitution: each
+// 32 x 32 diagonal block is solved by one warp from shared memory (lane i owns
+// unknown i, one shuffle per column), the coupling to the remaining unknowns
+// is applied by all threads, one unknown per thread.
 __global__ void __launch_bounds__(1024)
 k_chol_solve(const double* __restrict__ Lf, const double* __restrict__ scale, const double* __restrict__ rhs,
              double* __restrict__ x, int N, int* __restrict__ status) {
   extern __shared__ double sh[];   // y[N]
+  __shared__ double ld[32][33];
   const int ccd = blockIdx.x;
   const double* l = Lf + (int64_t)ccd * N * N;
   const double* s = scale + (int64_t)ccd * N;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < N; i += blockDim.x) sh[i] = rhs[(int64_t)ccd * N + i] * s[i];
-  __syncthreads();
+  const int nblk = (N + 31) / 32;
   // forward: L y = r
-  for (int jb = 0; jb < N; jb += 32) {
-    const int nb = min(32, N - jb);
-    if (warp == 0) {
-      for (int c = 0; c < nb; ++c) {
-        double v = 0.0;
-        if (lane < c) v = l[(int64_t)(jb + c) * N + jb + lane] * sh[jb + lane];
-        v = warp_sum(v);
-        if (lane == 0) sh[jb + c] = (sh[jb + c] - v) / l[(int64_t)(jb + c) * N + jb + c];
-        __syncwarp();
-      }
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int jb = bi * 32, nb = min(32, N - jb);
+    for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+      const int i = t >> 5, j = t & 31;
+      ld[i][j] = (i < nb && j <= i) ? l[(int64_t)(jb + i) * N + jb + j] : 0.0;
     }
     __syncthreads();
-    for (int i = jb + nb + warp; i < N; i += nw) {
-      double v = lane < nb ? l[(int64_t)i * N + jb + lane] * sh[jb + lane] : 0.0;
-      v = warp_sum(v);
-      if (lane == 0) sh[i] -= v;
+    if (warp == 0) {
+      double y = lane < nb ? sh[jb + lane] : 0.0;
+      for (int c = 0; c < nb; ++c) {
+        if (lane == c) y /= ld[c][c];
+        const double yc = __shfl_sync(0xffffffffu, y, c);
+        if (lane > c) y -= ld[lane][c] * yc;
+      }
+      if (lane < nb) sh[jb + lane] = y;
+    }
+    __syncthreads();
+    for (int i = jb + nb + threadIdx.x; i < N; i += blockDim.x) {
+      const double* row = l + (int64_t)i * N + jb;
+      double v = 0.0;
+      for (int c = 0; c < nb; ++c) v += row[c] * sh[jb + c];
+      sh[i] -= v;
     }
     __syncthreads();
   }
   // backward: L^T z = y
-  const int nblk = (N + 31) / 32;
   for (int bi = nblk - 1; bi >= 0; --bi) {
     const int jb = bi * 32, nb = min(32, N - jb);
+    for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+      const int i = t >> 5, j = t & 31;
+      ld[i][j] = (i < nb && j <= i) ? l[(int64_t)(jb + i) * N + jb + j] : 0.0;
+    }
+    __syncthreads();
     if (warp == 0) {
+      double z = lane < nb ? sh[jb + lane] : 0.0;
       for (int c = nb - 1; c >= 0; --c) {
-        double v = 0.0;
-        if (lane > c && lane < nb) v = l[(int64_t)(jb + lane) * N + jb + c] * sh[jb + lane];
-        v = warp_sum(v);
-        if (lane == 0) sh[jb + c] = (sh[jb + c] - v) / l[(int64_t)(jb + c) * N + jb + c];
-        __syncwarp();
+        if (lane == c) z /= ld[c][c];
+        const double zc = __shfl_sync(0xffffffffu, z, c);
+        if (lane < c) z -= ld[c][lane] * zc;
       }
+      if (lane < nb) sh[jb + lane] = z;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < jb; i += blockDim.x) {
@@ -356,15 +359,14 @@ cudaError_t launch_cholesky(const sfft_plan_s* p, const double* A, void* ws) {
   k_chol_init<<<gi, 256, 0, p->stream>>>(A, Lf, scale, status, N);
   p->nlaunch += 1;
   for (int kb = 0; kb < N; kb += NBK) {
-    k_chol_diag<<<B, NBK * NBK / 4, 0, p->stream>>>(Lf, status, N, kb);
-    p->nlaunch += 1;
     const int nb = N - kb < NBK ? N - kb : NBK;
     const int rem = N - kb - nb;
+    const int T = (rem + NBK - 1) / NBK;
+    k_chol_panel<<<dim3(T > 0 ? T : 1, B), NBK, 0, p->stream>>>(Lf, status, N, kb);
+    p->nlaunch += 1;
     if (rem > 0) {
-      const int T = (rem + NBK - 1) / NBK;
-      k_chol_panel<<<dim3(T, B), NBK, 0, p->stream>>>(Lf, N, kb);
       k_chol_update<<<dim3(T * (T + 1) / 2, B), 256, 0, p->stream>>>(Lf, N, kb);
-      p->nlaunch += 2;
+      p->nlaunch += 1;
     }
   }
   return cudaGetLastError();
