@@ -1,0 +1,229 @@
+"""FP64 CPU oracle for the stamp real-bogus classifier.
+
+TEST INFRASTRUCTURE ONLY: used by the tests, the smoke check and the
+benchmark's CPU-baseline leg; the product path never imports it.
+
+The paper (Sec. 2.3.4) scores each detection on the difference image with a
+CNN that takes a three-channel stamp (science, template, difference) centred
+on the candidate and returns a score in [0, 1]; it gives no layer sizes for
+the small network built here, which follows the project's stated design:
+
+  normalise   per channel c: (x - median_c) / (1.4826 MAD_c), clipped to +-64
+              (MAD_c <= 0 -> scale 1)
+  conv1       3 -> 32, 3 x 3, zero 'same' padding, + bias, ReLU, max-pool 2 (31 -> 15)
+  conv2       32 -> 64, same, ReLU, pool (15 -> 7)
+  conv3       64 -> 64, same, ReLU, pool (7 -> 3)
+  fc1         576 -> 128 (flatten order channel, row, column), ReLU
+  fc2         128 -> 1 logit z, score = sigmoid(z)
+  loss        binary cross-entropy on the logit, mean over the batch
+  optimiser   Adam (beta1 0.9, beta2 0.999, eps 1e-8) on FP32-style master weights
+
+Max-pool is 2 x 2 with stride 2 over the top-left even part (floor); its
+gradient goes to the first maximum in the order (0,0), (0,1), (1,0), (1,1).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+STAMP = 31
+SHAPES = {
+    "w1": (32, 3, 3, 3), "b1": (32,),
+    "w2": (64, 32, 3, 3), "b2": (64,),
+    "w3": (64, 64, 3, 3), "b3": (64,),
+    "w4": (128, 576), "b4": (128,),
+    "w5": (1, 128), "b5": (1,),
+}
+ORDER = ["w1", "b1", "w2", "b2", "w3", "b3", "w4", "b4", "w5", "b5"]
+
+
+def n_params():
+    return int(sum(np.prod(SHAPES[k]) for k in ORDER))
+
+
+def unflatten(vec):
+    out, o = {}, 0
+    for k in ORDER:
+        n = int(np.prod(SHAPES[k]))
+        out[k] = np.asarray(vec[o:o + n], dtype=np.float64).reshape(SHAPES[k])
+        o += n
+    return out
+
+
+def flatten(params):
+    return np.concatenate([np.asarray(params[k], dtype=np.float64).ravel() for k in ORDER])
+
+
+def init_params(seed):
+    """Uniform He-style initialisation, U(-sqrt(6/fan_in), sqrt(6/fan_in)), zero biases."""
+    rng = np.random.default_rng(seed)
+    p = {}
+    for k in ORDER:
+        shp = SHAPES[k]
+        if k.startswith("b"):
+            p[k] = np.zeros(shp)
+        else:
+            fan_in = int(np.prod(shp[1:]))
+            lim = np.sqrt(6.0 / fan_in)
+            p[k] = rng.uniform(-lim, lim, shp)
+    return p
+
+
+def normalise(stamps):
+    """Per-stamp, per-channel robust standardisation, clipped to +-64."""
+    x = np.asarray(stamps, dtype=np.float64)
+    n = x.shape[0]
+    flat = x.reshape(n, 3, -1)
+    med = np.median(flat, axis=2, keepdims=True)
+    mad = np.median(np.abs(flat - med), axis=2, keepdims=True)
+    scale = 1.4826 * mad
+    scale = np.where(scale > 0, scale, 1.0)
+    return np.clip((flat - med) / scale, -64.0, 64.0).reshape(x.shape)
+
+
+def conv_same(x, w, b):
+    """x [n][cin][h][w], w [cout][cin][3][3]: y = b + sum w * x(i + ky - 1, j + kx - 1), zero outside."""
+    n, cin, h, wd = x.shape
+    xp = np.zeros((n, cin, h + 2, wd + 2))
+    xp[:, :, 1:-1, 1:-1] = x
+    y = np.zeros((n, w.shape[0], h, wd)) + b[None, :, None, None]
+    for ky in range(3):
+        for kx in range(3):
+            patch = xp[:, :, ky:ky + h, kx:kx + wd]
+            y += np.einsum("ncij,oc->noij", patch, w[:, :, ky, kx])
+    return y
+
+
+def conv_same_backward(x, w, dy):
+    """Gradients of conv_same with respect to x, w and b."""
+    n, cin, h, wd = x.shape
+    xp = np.zeros((n, cin, h + 2, wd + 2))
+    xp[:, :, 1:-1, 1:-1] = x
+    dw = np.zeros_like(w)
+    dxp = np.zeros_like(xp)
+    for ky in range(3):
+        for kx in range(3):
+            patch = xp[:, :, ky:ky + h, kx:kx + wd]
+            dw[:, :, ky, kx] = np.einsum("noij,ncij->oc", dy, patch)
+            dxp[:, :, ky:ky + h, kx:kx + wd] += np.einsum("noij,oc->ncij", dy, w[:, :, ky, kx])
+    db = dy.sum(axis=(0, 2, 3))
+    return dxp[:, :, 1:-1, 1:-1], dw, db
+
+
+def maxpool2(x):
+    n, c, h, wd = x.shape
+    ho, wo = h // 2, wd // 2
+    v = x[:, :, :2 * ho, :2 * wo].reshape(n, c, ho, 2, wo, 2).transpose(0, 1, 2, 4, 3, 5).reshape(n, c, ho, wo, 4)
+    idx = np.argmax(v, axis=-1)   # first maximum in (0,0), (0,1), (1,0), (1,1)
+    return np.take_along_axis(v, idx[..., None], axis=-1)[..., 0], idx
+
+
+def maxpool2_backward(dy, idx, shape):
+    n, c, h, wd = shape
+    ho, wo = dy.shape[2], dy.shape[3]
+    dv = np.zeros((n, c, ho, wo, 4))
+    np.put_along_axis(dv, idx[..., None], dy[..., None], axis=-1)
+    dx = np.zeros(shape)
+    dx[:, :, :2 * ho, :2 * wo] = dv.reshape(n, c, ho, wo, 2, 2).transpose(0, 1, 2, 4, 3, 5).reshape(n, c, 2 * ho, 2 * wo)
+    return dx
+
+
+def forward(params, xn, keep=False):
+    """Logits for normalised stamps xn [n][3][31][31]."""
+    cache = {}
+    a = xn
+    for li, (wk, bk) in enumerate([("w1", "b1"), ("w2", "b2"), ("w3", "b3")]):
+        z = conv_same(a, params[wk], params[bk])
+        r = np.maximum(z, 0.0)
+        p, idx = maxpool2(r)
+        cache[li] = (a, z, idx, r.shape)
+        a = p
+    flat = a.reshape(a.shape[0], -1)
+    z4 = flat @ params["w4"].T + params["b4"]
+    h4 = np.maximum(z4, 0.0)
+    z5 = h4 @ params["w5"].T + params["b5"]
+    logit = z5[:, 0]
+    if keep:
+        cache["flat"], cache["z4"], cache["h4"], cache["pool_shape"] = flat, z4, h4, a.shape
+        return logit, cache
+    return logit
+
+
+def bce_loss(logit, target):
+    t = np.asarray(target, dtype=np.float64)
+    return float(np.mean(np.maximum(logit, 0) - logit * t + np.log1p(np.exp(-np.abs(logit)))))
+
+
+def sigmoid(z):
+    return 0.5 * (1.0 + np.tanh(0.5 * z))
+
+
+def loss_and_grads(params, xn, target):
+    logit, c = forward(params, xn, keep=True)
+    n = logit.shape[0]
+    loss = bce_loss(logit, target)
+    dz5 = ((sigmoid(logit) - np.asarray(target, dtype=np.float64)) / n)[:, None]
+    g = {}
+    g["w5"] = dz5.T @ c["h4"]
+    g["b5"] = dz5.sum(axis=0)
+    dh4 = dz5 @ params["w5"]
+    dz4 = dh4 * (c["z4"] > 0)
+    g["w4"] = dz4.T @ c["flat"]
+    g["b4"] = dz4.sum(axis=0)
+    da = (dz4 @ params["w4"]).reshape(c["pool_shape"])
+    for li, (wk, bk) in reversed(list(enumerate([("w1", "b1"), ("w2", "b2"), ("w3", "b3")]))):
+        a_in, z, idx, rshape = c[li]
+        dr = maxpool2_backward(da, idx, rshape)
+        dz = dr * (z > 0)
+        dx, dw, db = conv_same_backward(a_in, params[wk], dz)
+        g[wk], g[bk] = dw, db
+        da = dx
+    return loss, g
+
+
+def score(params, stamps):
+    return sigmoid(forward(params, normalise(stamps)))
+
+
+class Adam:
+    def __init__(self, params, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        self.lr, self.b1, self.b2, self.eps = lr, b1, b2, eps
+        self.m = {k: np.zeros_like(v) for k, v in params.items()}
+        self.v = {k: np.zeros_like(v) for k, v in params.items()}
+        self.t = 0
+
+    def step(self, params, grads):
+        self.t += 1
+        for k in params:
+            self.m[k] = self.b1 * self.m[k] + (1 - self.b1) * grads[k]
+            self.v[k] = self.b2 * self.v[k] + (1 - self.b2) * grads[k] ** 2
+            mh = self.m[k] / (1 - self.b1 ** self.t)
+            vh = self.v[k] / (1 - self.b2 ** self.t)
+            params[k] = params[k] - self.lr * mh / (np.sqrt(vh) + self.eps)
+        return params
+
+
+# ---------------------------------------------------------------- fallback cuts
+def shape_cuts(dstamp, snr, fwhm_psf, snr_min=5.0):
+    """Plain SNR and shape cuts on a difference-image stamp (31 x 31, candidate
+    at the centre): SNR >= snr_min; second-moment FWHM within [0.5, 2.0] of the
+    PSF FWHM; negative-flux fraction of the central 7 x 7 below 0.3; axis ratio
+    below 2.5.  Moments use the positive pixels of the central 9 x 9."""
+    c = STAMP // 2
+    box = np.asarray(dstamp, dtype=np.float64)[c - 4:c + 5, c - 4:c + 5]
+    pos = np.maximum(box, 0.0)
+    tot = pos.sum()
+    if snr < snr_min or tot <= 0:
+        return False
+    yy, xx = np.mgrid[-4:5, -4:5]
+    mx, my = (pos * xx).sum() / tot, (pos * yy).sum() / tot
+    sxx = (pos * (xx - mx) ** 2).sum() / tot
+    syy = (pos * (yy - my) ** 2).sum() / tot
+    sxy = (pos * (xx - mx) * (yy - my)).sum() / tot
+    tr, det = sxx + syy, sxx * syy - sxy ** 2
+    disc = np.sqrt(max(tr * tr / 4 - det, 0.0))
+    l1, l2 = tr / 2 + disc, max(tr / 2 - disc, 1e-12)
+    fwhm = 2.3548200450309493 * np.sqrt(max(0.5 * (l1 + l2), 0.0))
+    inner = np.asarray(dstamp, dtype=np.float64)[c - 3:c + 4, c - 3:c + 4]
+    neg_frac = np.abs(np.minimum(inner, 0)).sum() / max(np.abs(inner).sum(), 1e-12)
+    ratio = np.sqrt(l1 / l2)
+    return (0.5 * fwhm_psf <= fwhm <= 2.0 * fwhm_psf) and neg_frac < 0.3 and ratio < 2.5

@@ -1,0 +1,128 @@
+"""Pins of the FP64 classifier oracle: library correlation, delta filters,
+hand-computed pooling, central finite differences, the closed-form first
+Adam step, the naive BCE formula and the shape cuts on constructed stamps."""
+import math
+
+import numpy as np
+import pytest
+from scipy import signal
+
+from oracle import cnn_oracle as C
+
+RNG = np.random.default_rng(2024)
+
+
+def test_param_count():
+    assert C.n_params() == 896 + 18496 + 36928 + 73856 + 129
+
+
+def test_conv_matches_library_correlation():
+    x = RNG.normal(size=(2, 3, 9, 11))
+    w = RNG.normal(size=(4, 3, 3, 3))
+    b = RNG.normal(size=4)
+    y = C.conv_same(x, w, b)
+    for n in range(2):
+        for o in range(4):
+            ref = b[o] + sum(signal.correlate2d(x[n, c], w[o, c], mode="same", boundary="fill") for c in range(3))
+            assert np.allclose(y[n, o], ref, atol=1e-12)
+
+
+def test_delta_filter_is_identity():
+    x = RNG.normal(size=(1, 3, 7, 7))
+    w = np.zeros((3, 3, 3, 3))
+    for c in range(3):
+        w[c, c, 1, 1] = 1.0
+    assert np.array_equal(C.conv_same(x, w, np.zeros(3)), x)
+
+
+def test_maxpool_hand_computed_and_floor():
+    x = np.array([[1, 5, 2, 0, 9], [3, 4, 8, 8, 9], [7, 0, 1, 1, 9], [6, 6, 2, 3, 9], [9, 9, 9, 9, 9]], float)
+    p, idx = C.maxpool2(x[None, None])
+    assert np.array_equal(p[0, 0], [[5, 8], [7, 3]])
+    assert np.array_equal(idx[0, 0], [[1, 2], [0, 3]])   # first maximum on the tie (8, 8)
+    d = C.maxpool2_backward(np.ones((1, 1, 2, 2)), idx, (1, 1, 5, 5))
+    assert d.sum() == 4 and d[0, 0, 0, 1] == 1 and d[0, 0, 1, 2] == 1 and d[0, 0, 1, 3] == 0
+
+
+def test_normalise_median_mad():
+    s = np.zeros((1, 3, 31, 31))
+    s[0, 0] = np.arange(961).reshape(31, 31)        # median 480; |x - 480| = 0, 1, 1, 2, 2, ... -> MAD 240
+    s[0, 1] = 7.0                                   # MAD 0 -> scale 1
+    s[0, 2] = RNG.normal(0, 1e4, (31, 31))
+    xn = C.normalise(s)
+    assert abs(xn[0, 0, 0, 0] - (0 - 480) / (1.4826 * 240.0)) < 1e-12
+    assert np.all(xn[0, 1] == 0.0)
+    assert np.abs(xn).max() <= 64.0
+
+
+def test_bce_matches_naive_formula():
+    z = np.array([-3.0, -0.5, 0.0, 0.7, 4.0])
+    t = np.array([0, 1, 1, 0, 1.0])
+    s = 1 / (1 + np.exp(-z))
+    naive = np.mean(-(t * np.log(s) + (1 - t) * np.log(1 - s)))
+    assert abs(C.bce_loss(z, t) - naive) < 1e-14
+
+
+def test_gradients_match_central_differences():
+    p = C.init_params(7)
+    for k in p:
+        if k.startswith("b"):
+            p[k] = RNG.normal(0, 0.05, p[k].shape)
+    x = C.normalise(RNG.normal(1000, 30, (3, 3, 31, 31)))
+    t = np.array([1.0, 0.0, 1.0])
+    loss, g = C.loss_and_grads(p, x, t)
+    h = 1e-6
+    rng = np.random.default_rng(8)
+    for k in C.ORDER:
+        for _ in range(6):
+            idx = tuple(rng.integers(0, s) for s in p[k].shape)
+            old = p[k][idx]
+            p[k][idx] = old + h
+            lp = C.bce_loss(C.forward(p, x), t)
+            p[k][idx] = old - h
+            lm = C.bce_loss(C.forward(p, x), t)
+            p[k][idx] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - g[k][idx]) <= 1e-6 * max(abs(fd), 1e-3) + 1e-9, (k, idx, fd, g[k][idx])
+
+
+def test_first_adam_step_closed_form():
+    p = {"w": np.array([1.0, -2.0, 0.5])}
+    g = {"w": np.array([0.3, -4.0, 1e-3])}
+    opt = C.Adam(p, lr=0.01)
+    p2 = opt.step({"w": p["w"].copy()}, g)
+    # first step: m_hat = g, v_hat = g^2  ->  theta - lr g / (|g| + eps)
+    assert np.allclose(p2["w"], p["w"] - 0.01 * g["w"] / (np.abs(g["w"]) + 1e-8), rtol=0, atol=1e-15)
+
+
+def _gauss_stamp(fwhm, amp=500.0, cx=15.0, cy=15.0):
+    s = fwhm / 2.3548200450309493
+    yy, xx = np.mgrid[0:31, 0:31]
+    return amp * np.exp(-((xx - cx) ** 2 + (yy - cy) ** 2) / (2 * s * s))
+
+
+def test_shape_cuts_on_constructed_stamps():
+    assert C.shape_cuts(_gauss_stamp(2.0), snr=10.0, fwhm_psf=2.0)
+    assert not C.shape_cuts(_gauss_stamp(2.0), snr=4.0, fwhm_psf=2.0)           # below SNR
+    dip = _gauss_stamp(2.0, cx=14.4) - _gauss_stamp(2.0, cx=15.6)
+    assert not C.shape_cuts(dip, snr=10.0, fwhm_psf=2.0)                        # dipole residual
+    hot = np.zeros((31, 31)); hot[15, 15] = 1e4
+    assert not C.shape_cuts(hot, snr=50.0, fwhm_psf=2.0)                        # cosmic-ray point
+    col = np.zeros((31, 31)); col[:, 15] = 800.0
+    assert not C.shape_cuts(col, snr=20.0, fwhm_psf=2.0)                        # column segment
+
+
+def test_training_reduces_loss_on_separable_toy():
+    rng = np.random.default_rng(3)
+    p = C.init_params(3)
+    n = 16
+    st = rng.normal(1000, 30, (n, 3, 31, 31))
+    t = (np.arange(n) % 2).astype(float)
+    st[t == 1, 2] += _gauss_stamp(2.0, amp=400.0)
+    xn = C.normalise(st)
+    opt = C.Adam(p, lr=2e-3)
+    l0 = C.loss_and_grads(p, xn, t)[0]
+    for _ in range(15):
+        _, g = C.loss_and_grads(p, xn, t)
+        p = opt.step(p, g)
+    assert C.loss_and_grads(p, xn, t)[0] < 0.5 * l0
