@@ -126,6 +126,7 @@ k_chol_init(const double* __restrict__ A, double* __restrict__ Lf, double* __res
 __global__ void __launch_bounds__(NBK)
 k_chol_panel(double* __restrict__ Lf, int* __restrict__ status, int N, int kb) {
   __shared__ double blk[NBK][NBK + 1];
+  __shared__ double rdiag[NBK];   // 1 / L_cc
   const int ccd = blockIdx.y, lane = threadIdx.x;
   double* l = Lf + (int64_t)ccd * N * N;
   const int nb = min(NBK, N - kb);
@@ -136,10 +137,12 @@ k_chol_panel(double* __restrict__ Lf, int* __restrict__ status, int N, int kb) {
     if (lane == c) {
       double d = blk[c][c];
       if (!(d > 0.0) || !isfinite(d)) { bad = true; nonfinite = !isfinite(d); d = 1.0; }
-      blk[c][c] = sqrt(d);
+      const double s = sqrt(d);
+      blk[c][c] = s;
+      rdiag[c] = 1.0 / s;
     }
     __syncwarp();
-    if (lane > c && lane < nb) blk[lane][c] /= blk[c][c];
+    if (lane > c && lane < nb) blk[lane][c] *= rdiag[c];
     __syncwarp();
     if (lane > c && lane < nb) {
       const double lic = blk[lane][c];
@@ -161,10 +164,18 @@ k_chol_panel(double* __restrict__ Lf, int* __restrict__ status, int N, int kb) {
 #pragma unroll
   for (int c = 0; c < NBK; ++c) {
     if (c < nb) {
-      double v = x[c];
+      // four independent partial sums keep the FP64 dependency chains short
+      double v0 = x[c], v1 = 0.0, v2 = 0.0, v3 = 0.0;
 #pragma unroll
-      for (int t = 0; t < c; ++t) v -= x[t] * blk[c][t];
-      x[c] = v / blk[c][c];
+      for (int t = 0; t + 3 < c; t += 4) {
+        v0 -= x[t] * blk[c][t];
+        v1 -= x[t + 1] * blk[c][t + 1];
+        v2 -= x[t + 2] * blk[c][t + 2];
+        v3 -= x[t + 3] * blk[c][t + 3];
+      }
+#pragma unroll
+      for (int t = c & ~3; t < c; ++t) v0 -= x[t] * blk[c][t];
+      x[c] = ((v0 + v1) + (v2 + v3)) * rdiag[c];
     }
   }
 #pragma unroll
@@ -226,8 +237,9 @@ k_chol_solve(const double* __restrict__ Lf, const double* __restrict__ scale, co
     __syncthreads();
     if (warp == 0) {
       double y = lane < nb ? sh[jb + lane] : 0.0;
+      const double rd = lane < nb ? 1.0 / ld[lane][lane] : 0.0;
       for (int c = 0; c < nb; ++c) {
-        if (lane == c) y /= ld[c][c];
+        if (lane == c) y *= rd;
         const double yc = __shfl_sync(0xffffffffu, y, c);
         if (lane > c) y -= ld[lane][c] * yc;
       }
@@ -236,9 +248,16 @@ k_chol_solve(const double* __restrict__ Lf, const double* __restrict__ scale, co
     __syncthreads();
     for (int i = jb + nb + threadIdx.x; i < N; i += blockDim.x) {
       const double* row = l + (int64_t)i * N + jb;
-      double v = 0.0;
-      for (int c = 0; c < nb; ++c) v += row[c] * sh[jb + c];
-      sh[i] -= v;
+      double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+      int c = 0;
+      for (; c + 3 < nb; c += 4) {
+        v0 += row[c] * sh[jb + c];
+        v1 += row[c + 1] * sh[jb + c + 1];
+        v2 += row[c + 2] * sh[jb + c + 2];
+        v3 += row[c + 3] * sh[jb + c + 3];
+      }
+      for (; c < nb; ++c) v0 += row[c] * sh[jb + c];
+      sh[i] -= (v0 + v1) + (v2 + v3);
     }
     __syncthreads();
   }
@@ -252,8 +271,9 @@ k_chol_solve(const double* __restrict__ Lf, const double* __restrict__ scale, co
     __syncthreads();
     if (warp == 0) {
       double z = lane < nb ? sh[jb + lane] : 0.0;
+      const double rd = lane < nb ? 1.0 / ld[lane][lane] : 0.0;
       for (int c = nb - 1; c >= 0; --c) {
-        if (lane == c) z /= ld[c][c];
+        if (lane == c) z *= rd;
         const double zc = __shfl_sync(0xffffffffu, z, c);
         if (lane < c) z -= ld[c][lane] * zc;
       }
@@ -261,9 +281,16 @@ k_chol_solve(const double* __restrict__ Lf, const double* __restrict__ scale, co
     }
     __syncthreads();
     for (int i = threadIdx.x; i < jb; i += blockDim.x) {
-      double v = 0.0;
-      for (int c = 0; c < nb; ++c) v += l[(int64_t)(jb + c) * N + i] * sh[jb + c];
-      sh[i] -= v;
+      double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+      int c = 0;
+      for (; c + 3 < nb; c += 4) {
+        v0 += l[(int64_t)(jb + c) * N + i] * sh[jb + c];
+        v1 += l[(int64_t)(jb + c + 1) * N + i] * sh[jb + c + 1];
+        v2 += l[(int64_t)(jb + c + 2) * N + i] * sh[jb + c + 2];
+        v3 += l[(int64_t)(jb + c + 3) * N + i] * sh[jb + c + 3];
+      }
+      for (; c < nb; ++c) v0 += l[(int64_t)(jb + c) * N + i] * sh[jb + c];
+      sh[i] -= (v0 + v1) + (v2 + v3);
     }
     __syncthreads();
   }
