@@ -1,0 +1,101 @@
+/*
+ * rb.h - C ABI of the stamp real-bogus classifier and the candidate detector.
+ *
+ * The paper (Sec. 2.3.3-2.3.5) detects sources on the difference image,
+ * cuts a three-channel stamp (science, template, difference) around each one
+ * and scores it with a CNN in [0, 1]; alerts pass a score threshold (0.3 hot,
+ * 0.6 cold).  Its network is not specified beyond that; this library's network
+ * is: per-channel robust normalisation (median, 1.4826 MAD, clip +-64), three
+ * 3 x 3 'same' convolutions (3 -> 32 -> 64 -> 64) each followed by ReLU and a
+ * 2 x 2 max-pool (31 -> 15 -> 7 -> 3), a 576 -> 128 ReLU layer and a 128 -> 1
+ * logit; score = sigmoid(logit).  Training minimises binary cross-entropy with
+ * Adam (beta1 0.9, beta2 0.999, eps 1e-8) on FP32 master weights; forward and
+ * backward matrix products run on BF16 tensor-core MMA with FP32 accumulation.
+ *
+ * Stamps are float [n][3][31][31] in raw ADU (channel 0 science, 1 template,
+ * 2 difference), centred on the candidate pixel.  All data pointers are
+ * DEVICE pointers unless named host_*; calls are asynchronous on `stream`
+ * except where stated.  Statuses are the sfft_status_t codes of sfft.h.
+ */
+#ifndef RB_GB300_H
+#define RB_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "sfft.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RB_STAMP 31
+#define RB_NPARAM 130305   /* w1 b1 w2 b2 w3 b3 w4 b4 w5 b5 */
+
+typedef struct rb_model_s* rb_model_t;
+
+/* desc[0] = max stamps per internal batch (>= 1), desc[1] = initialisation
+ * seed (uniform He-style weights, zero biases).  Allocates the weights, Adam
+ * state and activation scratch for desc[0] stamps on the current device. */
+sfft_status_t rb_create(const int32_t* desc, rb_model_t* out);
+sfft_status_t rb_destroy(rb_model_t m);
+
+/* Weights as RB_NPARAM floats in the order w1 [32][3][3][3], b1 [32],
+ * w2 [64][32][3][3], b2, w3 [64][64][3][3], b3, w4 [128][576] (input index
+ * channel * 9 + row * 3 + column), b4, w5 [1][128], b5 [1].  Host buffers;
+ * synchronous.  bytes must be RB_NPARAM * 4. */
+sfft_status_t rb_set_weights(rb_model_t m, const void* host_buf, size_t bytes);
+sfft_status_t rb_get_weights(rb_model_t m, void* host_buf, size_t bytes);
+/* Gradients of the last rb_backward / rb_train_step, same layout (synchronous). */
+sfft_status_t rb_get_grads(rb_model_t m, void* host_buf, size_t bytes);
+/* Full training state for checkpoint/resume: weights, Adam first and second
+ * moments (3 * RB_NPARAM floats, same layout) and the step count. */
+sfft_status_t rb_get_state(rb_model_t m, void* host_buf, size_t bytes, int64_t* step);
+sfft_status_t rb_set_state(rb_model_t m, const void* host_buf, size_t bytes, int64_t step);
+
+/* Logits and scores of n stamps (any n; processed in internal batches). */
+sfft_status_t rb_logits(rb_model_t m, const float* stamps, int64_t n, float* logit, void* stream);
+sfft_status_t rb_score(rb_model_t m, const float* stamps, int64_t n, float* score, void* stream);
+
+/* Mean BCE loss (written to loss_dev, float) and parameter gradients of one
+ * batch of n <= max stamps with labels (float 0/1); no parameter update. */
+sfft_status_t rb_backward(rb_model_t m, const float* stamps, const float* labels, int64_t n, float* loss_dev,
+                          void* stream);
+/* rb_backward followed by one Adam step with learning rate lr. */
+sfft_status_t rb_train_step(rb_model_t m, const float* stamps, const float* labels, int64_t n, float lr,
+                            float* loss_dev, void* stream);
+
+/* Candidate detection on difference images (Sec. 2.3.3's detection step,
+ * here a matched filter): SNR(x) = sum_u G(u) D^(x - u) / (sigma_D ||G||_2)
+ * with D^ = D at good finite pixels and 0 elsewhere (and outside the image),
+ * G(u) = g(u_x) g(u_y), g(t) = exp(-t^2 / (2 psf_sigma^2)) on |t| <= r =
+ * ceil(3 psf_sigma), 0 < psf_sigma <= 5; sigma_D the RMS of D about its mean
+ * over the good finite pixels at least 15 px from every edge after three
+ * 3-sigma clipping passes (|D - mean| <= 3 RMS of the previous pass), divided
+ * by sqrt(0.97334), the share of a Gaussian's variance inside +-3 sigma.
+ * Candidates are pixels at least 15 px from every edge, not bad, with
+ * SNR >= thresh and SNR >= every SNR in their 5 x 5 neighbourhood.  Per CCD,
+ * up to max_cand candidates are written in row-major order: xy int32
+ * [batch][max_cand][2] (x, y), snr float [batch][max_cand], count int32
+ * [batch] (the number found, which may exceed max_cand), and stamps float
+ * [batch][max_cand][3][31][31] (S, R, D; non-finite values written as 0).
+ * Entries past the count are left untouched.  D, S, R float [batch][H][W]
+ * with H, W >= 31; bad uint8 or NULL.  The filter runs in FP32 and the clipped
+ * statistics in FP64.  ws: device scratch of
+ * rb_detect_workspace_bytes(H, W, batch, max_cand), 256-byte aligned. */
+size_t rb_detect_workspace_bytes(int32_t H, int32_t W, int32_t batch, int32_t max_cand);
+sfft_status_t rb_detect(int32_t H, int32_t W, int32_t batch, const float* D, const float* S, const float* R,
+                        const uint8_t* bad, float psf_sigma, float thresh, int32_t max_cand, int32_t* xy,
+                        float* snr, int32_t* count, float* stamps, void* ws, void* stream);
+
+/* Plain SNR/shape cuts on difference stamps (the classifier's fallback):
+ * pass[i] = 1 iff snr[i] >= snr_min, the second-moment FWHM of the positive
+ * central 9 x 9 lies in [0.5, 2.0] psf_fwhm, the negative-flux fraction of the
+ * central 7 x 7 is below 0.3 and the axis ratio is below 2.5. */
+sfft_status_t rb_shape_cuts(const float* stamps, const float* snr, int64_t n, float psf_fwhm, float snr_min,
+                            int32_t* pass, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RB_GB300_H */

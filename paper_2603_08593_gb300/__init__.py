@@ -1,8 +1,10 @@
 """GB300 (sm_103a) difference imaging: delta-basis, spatially varying kernel
-fit by Fourier-domain normal equations, FP64 solve, convolve-and-subtract.
+fit by Fourier-domain normal equations, FP64 solve, convolve-and-subtract;
+matched-filter candidate detection and a BF16 tensor-core stamp classifier.
 
 The compute path is the CUDA library libsfft_gb300.so (C ABI in
-include/sfft.h); `binding` marshals arguments to it through ctypes.
+include/sfft.h and include/rb.h); `binding` marshals arguments to it through
+ctypes.
 """
 from . import binding  # noqa: F401
-from .binding import Plan, SfftError, load  # noqa: F401
+from .binding import Detector, Plan, RBModel, SfftError, load, shape_cuts  # noqa: F401

@@ -1,4 +1,4 @@
-"""ctypes binding over the C ABI in include/sfft.h.
+"""ctypes binding over the C ABI in include/sfft.h and include/rb.h.
 
 Argument marshalling only: every step of the subtraction runs in the CUDA
 kernels of libsfft_gb300.so.  PyTorch provides device memory and the stream.
@@ -44,7 +44,25 @@ SIGNATURES = {
     "sfft_profile_read": (I32, [VP, C.POINTER(C.c_double), C.POINTER(I64), I32]),
     "sfft_status_str": (C.c_char_p, [I32]),
     "sfft_last_error": (C.c_char_p, []),
+    # classifier and detector (include/rb.h)
+    "rb_create": (I32, [VP, C.POINTER(VP)]),
+    "rb_destroy": (I32, [VP]),
+    "rb_set_weights": (I32, [VP, VP, SZ]),
+    "rb_get_weights": (I32, [VP, VP, SZ]),
+    "rb_get_grads": (I32, [VP, VP, SZ]),
+    "rb_get_state": (I32, [VP, VP, SZ, C.POINTER(I64)]),
+    "rb_set_state": (I32, [VP, VP, SZ, I64]),
+    "rb_logits": (I32, [VP, VP, I64, VP, VP]),
+    "rb_score": (I32, [VP, VP, I64, VP, VP]),
+    "rb_backward": (I32, [VP, VP, VP, I64, VP, VP]),
+    "rb_train_step": (I32, [VP, VP, VP, I64, C.c_float, VP, VP]),
+    "rb_detect_workspace_bytes": (SZ, [I32, I32, I32, I32]),
+    "rb_detect": (I32, [I32, I32, I32, VP, VP, VP, VP, C.c_float, C.c_float, I32, VP, VP, VP, VP, VP, VP]),
+    "rb_shape_cuts": (I32, [VP, VP, I64, C.c_float, C.c_float, VP, VP]),
 }
+
+RB_STAMP = 31
+RB_NPARAM = 130305
 
 _LIB = None
 
@@ -211,3 +229,149 @@ class Plan:
         K = self._f64(self.batch, self.L * self.L)
         _check(self.lib.sfft_kernel_at(self.h, _ptr(theta), float(x), float(y), _ptr(K)), "sfft_kernel_at")
         return K.view(self.batch, self.L, self.L)
+
+
+def _stream(t, stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream(t.device)
+    return VP(s.cuda_stream)
+
+
+def _need(t, dtype, what):
+    if t.dtype != dtype or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{what}: expected a contiguous {dtype} CUDA tensor")
+    return t
+
+
+class RBModel:
+    """The stamp classifier: FP32 master weights and Adam state on the device,
+    BF16 tensor-core forward/backward.  Weight vectors use the layout of
+    include/rb.h (w1 b1 ... w5 b5, RB_NPARAM floats)."""
+
+    def __init__(self, max_batch=1024, seed=0):
+        import numpy as np
+        self._np = np
+        self.lib = load()
+        desc = (I32 * 2)(int(max_batch), int(seed))
+        h = VP()
+        _check(self.lib.rb_create(desc, C.byref(h)), "rb_create")
+        self.h = h
+        self.max_batch = int(max_batch)
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                self.lib.rb_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    def _vec(self, fn, n=RB_NPARAM):
+        out = self._np.empty(n, dtype=self._np.float32)
+        _check(fn(self.h, out.ctypes.data_as(VP), out.nbytes), fn.__name__)
+        return out
+
+    def set_weights(self, w):
+        w = self._np.ascontiguousarray(w, dtype=self._np.float32)
+        if w.size != RB_NPARAM:
+            raise ValueError(f"expected {RB_NPARAM} weights")
+        _check(self.lib.rb_set_weights(self.h, w.ctypes.data_as(VP), w.nbytes), "rb_set_weights")
+
+    def get_weights(self):
+        return self._vec(self.lib.rb_get_weights)
+
+    def get_grads(self):
+        return self._vec(self.lib.rb_get_grads)
+
+    def get_state(self):
+        """(weights, adam_m, adam_v) as one array of 3 * RB_NPARAM floats, and the step count."""
+        out = self._np.empty(3 * RB_NPARAM, dtype=self._np.float32)
+        step = I64()
+        _check(self.lib.rb_get_state(self.h, out.ctypes.data_as(VP), out.nbytes, C.byref(step)), "rb_get_state")
+        return out, int(step.value)
+
+    def set_state(self, state, step):
+        s = self._np.ascontiguousarray(state, dtype=self._np.float32)
+        _check(self.lib.rb_set_state(self.h, s.ctypes.data_as(VP), s.nbytes, int(step)), "rb_set_state")
+
+    def logits(self, stamps, out=None, stream=None):
+        import torch
+        _need(stamps, torch.float32, "stamps")
+        n = stamps.shape[0]
+        out = out if out is not None else torch.empty(n, dtype=torch.float32, device=stamps.device)
+        _check(self.lib.rb_logits(self.h, _ptr(stamps), n, _ptr(out), _stream(stamps, stream)), "rb_logits")
+        return out
+
+    def score(self, stamps, out=None, stream=None):
+        import torch
+        _need(stamps, torch.float32, "stamps")
+        n = stamps.shape[0]
+        out = out if out is not None else torch.empty(n, dtype=torch.float32, device=stamps.device)
+        _check(self.lib.rb_score(self.h, _ptr(stamps), n, _ptr(out), _stream(stamps, stream)), "rb_score")
+        return out
+
+    def backward(self, stamps, labels, loss=None, stream=None):
+        import torch
+        _need(stamps, torch.float32, "stamps")
+        _need(labels, torch.float32, "labels")
+        loss = loss if loss is not None else torch.empty(1, dtype=torch.float32, device=stamps.device)
+        _check(self.lib.rb_backward(self.h, _ptr(stamps), _ptr(labels), stamps.shape[0], _ptr(loss),
+                                    _stream(stamps, stream)), "rb_backward")
+        return loss
+
+    def train_step(self, stamps, labels, lr, loss=None, stream=None):
+        import torch
+        _need(stamps, torch.float32, "stamps")
+        _need(labels, torch.float32, "labels")
+        loss = loss if loss is not None else torch.empty(1, dtype=torch.float32, device=stamps.device)
+        _check(self.lib.rb_train_step(self.h, _ptr(stamps), _ptr(labels), stamps.shape[0], float(lr), _ptr(loss),
+                                      _stream(stamps, stream)), "rb_train_step")
+        return loss
+
+
+class Detector:
+    """Matched-filter candidate detection with a reusable workspace.  After a
+    call, `snr_map` views the [batch][H][W] SNR image left in the workspace."""
+
+    def __init__(self, H, W, batch=1, max_cand=4096, device=None):
+        import torch
+        self.lib = load()
+        self.H, self.W, self.batch, self.max_cand = H, W, batch, max_cand
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        nb = int(self.lib.rb_detect_workspace_bytes(H, W, batch, max_cand))
+        if nb == 0:
+            raise SfftError("rb_detect_workspace_bytes: invalid sizes")
+        self.ws = torch.empty(nb + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.ws.data_ptr()) % 256
+        self.ws_view = self.ws[off:off + nb]
+        self.xy = torch.empty(batch, max_cand, 2, dtype=torch.int32, device=self.device)
+        self.snr = torch.empty(batch, max_cand, dtype=torch.float32, device=self.device)
+        self.count = torch.empty(batch, dtype=torch.int32, device=self.device)
+        self.stamps = torch.empty(batch, max_cand, 3, RB_STAMP, RB_STAMP, dtype=torch.float32, device=self.device)
+        self.snr_map = self.ws_view[:batch * H * W * 4].view(torch.float32).view(batch, H, W)
+
+    def __call__(self, D, S, R, bad=None, psf_sigma=1.0, thresh=5.0, stream=None):
+        import torch
+        for t, name in ((D, "D"), (S, "S"), (R, "R")):
+            _need(t, torch.float32, name)
+            if t.numel() != self.batch * self.H * self.W:
+                raise ValueError(f"{name}: shape does not match the detector")
+        if bad is not None:
+            _need(bad, torch.uint8, "bad")
+        st = self.lib.rb_detect(self.H, self.W, self.batch, _ptr(D), _ptr(S), _ptr(R), _ptr(bad), float(psf_sigma),
+                                float(thresh), self.max_cand, _ptr(self.xy), _ptr(self.snr), _ptr(self.count),
+                                _ptr(self.stamps), _ptr(self.ws_view), _stream(D, stream))
+        _check(st, "rb_detect")
+        return self.xy, self.snr, self.count, self.stamps
+
+
+def shape_cuts(stamps, snr, psf_fwhm, snr_min=5.0, out=None, stream=None):
+    """Plain SNR/shape cuts on [n][3][31][31] stamps: int32 pass flags."""
+    import torch
+    _need(stamps, torch.float32, "stamps")
+    _need(snr, torch.float32, "snr")
+    n = stamps.shape[0]
+    out = out if out is not None else torch.empty(n, dtype=torch.int32, device=stamps.device)
+    _check(load().rb_shape_cuts(_ptr(stamps), _ptr(snr), n, float(psf_fwhm), float(snr_min), _ptr(out),
+                                _stream(stamps, stream)), "rb_shape_cuts")
+    return out

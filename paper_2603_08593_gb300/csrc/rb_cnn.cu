@@ -1,0 +1,684 @@
+// Stamp real-bogus classifier: BF16 tensor-core training and inference.
+//
+// Activations are NHWC.  Every convolution is an explicit im2col followed by
+// one GEMM C[M][N] = A[M][K] B[K][N] (+ bias) on mma.sync m16n8k16 BF16 with
+// FP32 accumulation; the backward pass reuses the same GEMM with transposed
+// operands (weight gradients: cols^T dZ; input gradients: dZ W^T then a
+// gather col2im).  Master weights, gradients and Adam moments are FP32 and
+// stored in GEMM layout: conv weights as [(ky*3 + kx)*cin + ci][cout] (conv1
+// padded from K = 27 to 32 with zero rows), the 576 -> 128 layer as
+// [(i*3 + j)*64 + c][128]; rb_set/get_weights convert from/to the
+// [cout][cin][ky][kx] and channel-major flatten order of the C ABI.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "plan.h"
+#include "rb.h"
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+constexpr int S31 = 31, PIX1 = 961, PIX2 = 225, PIX3 = 49, PIX4 = 9;
+constexpr int C1 = 32, C2 = 64, C3 = 64, F4 = 128;
+constexpr int K1 = 32, K2 = 9 * C1, K3 = 9 * C2, K4 = PIX4 * C3;   // GEMM K (conv1 padded)
+
+// master parameter offsets (GEMM layout, floats)
+constexpr int OW1 = 0, OB1 = OW1 + K1 * C1, OW2 = OB1 + C1, OB2 = OW2 + K2 * C2, OW3 = OB2 + C2,
+              OB3 = OW3 + K3 * C3, OW4 = OB3 + C3, OB4 = OW4 + K4 * F4, OW5 = OB4 + F4, OB5 = OW5 + F4,
+              NMASTER = OB5 + 1;
+
+// ---------------------------------------------------------------- GEMM
+// C[M][N] (FP32, row-major, ldc) = op(A)[M][K] op(B)[K][N] (+ bias[N]).
+// op(A)(m, k) = transA ? A[k * lda + m] : A[m * lda + k]; same for B.
+constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__global__ void __launch_bounds__(128)
+k_gemm_bf16(int M, int N, int K, const bf16* __restrict__ A, int lda, int transA, const bf16* __restrict__ B,
+            int ldb, int transB, float* __restrict__ C, int ldc, const float* __restrict__ bias) {
+  __shared__ __align__(16) bf16 As[GBM][GBK + GPAD];
+  __shared__ __align__(16) bf16 Bs[GBN][GBK + GPAD];   // [n][k]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int wm = warp >> 1, wn = warp & 1;
+  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+  const bf16 zero = __float2bfloat16(0.f);
+  for (int k0 = 0; k0 < K; k0 += GBK) {
+    for (int e = tid; e < GBM * GBK; e += 128) {
+      int mm, kk;
+      if (transA) { kk = e / GBM; mm = e % GBM; } else { mm = e / GBK; kk = e % GBK; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      bf16 v = zero;
+      if (gm < M && gk < K) v = transA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk];
+      As[mm][kk] = v;
+    }
+    for (int e = tid; e < GBN * GBK; e += 128) {
+      int nn, kk;
+      if (transB) { nn = e / GBK; kk = e % GBK; } else { kk = e / GBN; nn = e % GBN; }
+      const int gn = n0 + nn, gk = k0 + kk;
+      bf16 v = zero;
+      if (gn < N && gk < K) v = transB ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn];
+      Bs[nn][kk] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GBK; kk += 16) {
+      uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm * 32 + i * 16;
+        af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r + g][kk + 2 * t]);
+        af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + g + 8][kk + 2 * t]);
+        af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r + g][kk + 8 + 2 * t]);
+        af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + g + 8][kk + 8 + 2 * t]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = wn * 32 + j * 8;
+        bfr[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[c + g][kk + 2 * t]);
+        bfr[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[c + g][kk + 8 + 2 * t]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = m0 + wm * 32 + i * 16 + g, c = n0 + wn * 32 + j * 8 + 2 * t;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int rr = r + (q >= 2 ? 8 : 0), cc = c + (q & 1);
+        if (rr < M && cc < N) C[(int64_t)rr * ldc + cc] = acc[i][j][q] + (bias ? bias[cc] : 0.f);
+      }
+    }
+}
+
+cudaError_t gemm(cudaStream_t s, int M, int N, int K, const bf16* A, int lda, int transA, const bf16* B, int ldb,
+                 int transB, float* C, int ldc, const float* bias) {
+  dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
+  k_gemm_bf16<<<grid, 128, 0, s>>>(M, N, K, A, lda, transA, B, ldb, transB, C, ldc, bias);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- elementwise kernels
+// per stamp: normalise the three channels (median, 1.4826 MAD, clip) -> NHWC bf16 [31][31][3]
+__device__ void bitonic_sort_1024(float* v) {
+  for (int k = 2; k <= 1024; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool up = (i & k) == 0;
+          const float a = v[i], b = v[l];
+          if ((a > b) == up) { v[i] = b; v[l] = a; }
+        }
+      }
+      __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_normalise(const float* __restrict__ stamps, bf16* __restrict__ xn) {
+  __shared__ float raw[PIX1], v[1024];
+  __shared__ float med_s, scale_s;
+  const int n = blockIdx.x;
+  for (int ch = 0; ch < 3; ++ch) {
+    const float* src = stamps + ((int64_t)n * 3 + ch) * PIX1;
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
+      const float x = i < PIX1 ? src[i] : INFINITY;
+      if (i < PIX1) raw[i] = x;
+      v[i] = x;
+    }
+    __syncthreads();
+    bitonic_sort_1024(v);
+    if (threadIdx.x == 0) med_s = v[480];
+    __syncthreads();
+    const float med = med_s;
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) v[i] = i < PIX1 ? fabsf(raw[i] - med) : INFINITY;
+    __syncthreads();
+    bitonic_sort_1024(v);
+    if (threadIdx.x == 0) {
+      const float sc = 1.4826f * v[480];
+      scale_s = sc > 0.f ? sc : 1.f;
+    }
+    __syncthreads();
+    const float inv = 1.f / scale_s;
+    for (int i = threadIdx.x; i < PIX1; i += blockDim.x) {
+      float x = (raw[i] - med) * inv;
+      x = fminf(fmaxf(x, -64.f), 64.f);
+      xn[((int64_t)n * PIX1 + i) * 3 + ch] = __float2bfloat16(x);
+    }
+    __syncthreads();
+  }
+}
+
+// im2col for a 3 x 3 'same' convolution: NHWC x [n][h][w][c] -> cols [n*h*w][kp], k = (ky*3 + kx)*c + ci
+__global__ void k_im2col(const bf16* __restrict__ x, int n, int h, int w, int c, int kp, bf16* __restrict__ cols) {
+  const int64_t total = (int64_t)n * h * w * kp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e % kp);
+    const int64_t row = e / kp;
+    bf16 v = __float2bfloat16(0.f);
+    if (k < 9 * c) {
+      const int tap = k / c, ci = k % c, ky = tap / 3, kx = tap % 3;
+      const int xx = (int)(row % w), yy = (int)((row / w) % h), nn = (int)(row / ((int64_t)w * h));
+      const int sy = yy + ky - 1, sx = xx + kx - 1;
+      if (sy >= 0 && sy < h && sx >= 0 && sx < w) v = x[(((int64_t)nn * h + sy) * w + sx) * c + ci];
+    }
+    cols[e] = v;
+  }
+}
+
+// gather col2im: dx[n][y][x][ci] = sum_taps dcols[(n, y-ky+1, x-kx+1)][(ky*3+kx)*c + ci]
+__global__ void k_col2im(const float* __restrict__ dcols, int n, int h, int w, int c, int kp, float* __restrict__ dx) {
+  const int64_t total = (int64_t)n * h * w * c;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int ci = (int)(e % c);
+    const int64_t pix = e / c;
+    const int xx = (int)(pix % w), yy = (int)((pix / w) % h), nn = (int)(pix / ((int64_t)w * h));
+    float s = 0.f;
+    for (int ky = 0; ky < 3; ++ky)
+      for (int kx = 0; kx < 3; ++kx) {
+        const int oy = yy - ky + 1, ox = xx - kx + 1;
+        if (oy >= 0 && oy < h && ox >= 0 && ox < w)
+          s += dcols[(((int64_t)nn * h + oy) * w + ox) * kp + (ky * 3 + kx) * c + ci];
+      }
+    dx[e] = s;
+  }
+}
+
+// ReLU + 2 x 2 max-pool (floor): z [n][h][w][c] -> a (bf16) [n][h/2][w/2][c], idx (first max in (0,0),(0,1),(1,0),(1,1))
+__global__ void k_relu_pool(const float* __restrict__ z, int n, int h, int w, int c, bf16* __restrict__ a,
+                            uint8_t* __restrict__ idx) {
+  const int ho = h / 2, wo = w / 2;
+  const int64_t total = (int64_t)n * ho * wo * c;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int ci = (int)(e % c);
+    const int64_t p = e / c;
+    const int xo = (int)(p % wo), yo = (int)((p / wo) % ho), nn = (int)(p / ((int64_t)wo * ho));
+    float best = -INFINITY;
+    int bi = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int yy = 2 * yo + (q >> 1), xx = 2 * xo + (q & 1);
+      const float v = fmaxf(z[(((int64_t)nn * h + yy) * w + xx) * c + ci], 0.f);
+      if (v > best) { best = v; bi = q; }
+    }
+    a[e] = __float2bfloat16(best);
+    if (idx) idx[e] = (uint8_t)bi;
+  }
+}
+
+// pool + ReLU backward: dz[n][h][w][c] = (position == argmax) * da * (z > 0); bf16 output
+__global__ void k_pool_relu_back(const float* __restrict__ da, const uint8_t* __restrict__ idx,
+                                 const float* __restrict__ z, int n, int h, int w, int c, bf16* __restrict__ dz) {
+  const int ho = h / 2, wo = w / 2;
+  const int64_t total = (int64_t)n * h * w * c;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int ci = (int)(e % c);
+    const int64_t p = e / c;
+    const int xx = (int)(p % w), yy = (int)((p / w) % h), nn = (int)(p / ((int64_t)w * h));
+    float v = 0.f;
+    const int yo = yy / 2, xo = xx / 2;
+    if (yo < ho && xo < wo && z[e] > 0.f) {
+      const int64_t pe = (((int64_t)nn * ho + yo) * wo + xo) * c + ci;
+      if (idx[pe] == (uint8_t)(((yy & 1) << 1) | (xx & 1))) v = da[pe];
+    }
+    dz[e] = __float2bfloat16(v);
+  }
+}
+
+// dense layer: z5 = relu(z4) . w5 + b5 (FP32, one warp per sample)
+__global__ void k_fc2(const float* __restrict__ z4, const float* __restrict__ w5, const float* __restrict__ b5,
+                      int n, float* __restrict__ logit) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  float s = 0.f;
+  for (int i = lane; i < F4; i += 32) s += fmaxf(z4[(int64_t)warp * F4 + i], 0.f) * w5[i];
+  s = sfft::warp_sum(s);
+  if (lane == 0) logit[warp] = s + b5[0];
+}
+
+__global__ void k_sigmoid(const float* __restrict__ z, int64_t n, float* __restrict__ s) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    s[e] = 1.f / (1.f + expf(-z[e]));
+}
+
+// BCE head: loss (mean), dz5 = (sigmoid - t) / n; then dW5, db5, dz4 = dz5 w5 (z4 > 0) (bf16)
+__global__ void k_bce_head(const float* __restrict__ logit, const float* __restrict__ target, int n,
+                           const float* __restrict__ z4, const float* __restrict__ w5, float* __restrict__ dz5,
+                           bf16* __restrict__ dz4, float* __restrict__ loss_dev) {
+  __shared__ float red[32];
+  float l = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float z = logit[i], t = target[i];
+    l += fmaxf(z, 0.f) - z * t + log1pf(expf(-fabsf(z)));
+    dz5[i] = (1.f / (1.f + expf(-z)) - t) / (float)n;
+  }
+  l = sfft::warp_sum(l);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+    s = sfft::warp_sum(s);
+    if (threadIdx.x == 0 && loss_dev) *loss_dev = s / (float)n;
+  }
+  __syncthreads();
+  for (int64_t e = threadIdx.x; e < (int64_t)n * F4; e += blockDim.x) {
+    const int i = (int)(e / F4), j = (int)(e % F4);
+    dz4[e] = __float2bfloat16(z4[e] > 0.f ? dz5[i] * w5[j] : 0.f);
+  }
+}
+
+// dw5[j] = sum_i dz5[i] relu(z4[i][j]); db5 = sum dz5
+__global__ void k_fc2_grad(const float* __restrict__ dz5, const float* __restrict__ z4, int n, float* __restrict__ dw5,
+                           float* __restrict__ db5) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < F4) {
+    float s = 0.f;
+    for (int i = 0; i < n; ++i) s += dz5[i] * fmaxf(z4[(int64_t)i * F4 + j], 0.f);
+    dw5[j] = s;
+  }
+  if (j == 0) {
+    float s = 0.f;
+    for (int i = 0; i < n; ++i) s += dz5[i];
+    db5[0] = s;
+  }
+}
+
+// column sums of a bf16 matrix [rows][cols] into FP32 (bias gradients)
+__global__ void k_colsum(const bf16* __restrict__ x, int64_t rows, int cols, float* __restrict__ out) {
+  const int c = blockIdx.x;
+  float s = 0.f;
+  for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) s += __bfloat162float(x[r * cols + c]);
+  s = sfft::warp_sum(s);
+  __shared__ float red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+    t = sfft::warp_sum(t);
+    if (threadIdx.x == 0) out[c] = t;
+  }
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, int64_t n, float lr, float c1, float c2) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const float ge = g[e];
+    const float me = 0.9f * m[e] + 0.1f * ge;
+    const float ve = 0.999f * v[e] + 0.001f * ge * ge;
+    m[e] = me;
+    v[e] = ve;
+    p[e] -= lr * (me / c1) / (sqrtf(ve / c2) + 1e-8f);
+  }
+}
+
+__global__ void k_to_bf16(const float* __restrict__ x, int64_t n, bf16* __restrict__ y) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = __float2bfloat16(x[e]);
+}
+
+int grid1(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  return (int)(g > 4096 ? 4096 : (g < 1 ? 1 : g));
+}
+
+// ---------------------------------------------------------------- layout conversion (host)
+// C-ABI order (oracle layout) <-> GEMM-layout master vector
+void abi_to_master(const float* a, std::vector<float>& m) {
+  m.assign(NMASTER, 0.f);
+  const float* w1 = a;                      // [32][3][3][3]
+  const float* b1 = w1 + 32 * 27;
+  const float* w2 = b1 + 32;                // [64][32][3][3]
+  const float* b2 = w2 + 64 * 288;
+  const float* w3 = b2 + 64;                // [64][64][3][3]
+  const float* b3 = w3 + 64 * 576;
+  const float* w4 = b3 + 64;                // [128][576] (c*9 + i*3 + j)
+  const float* b4 = w4 + 128 * 576;
+  const float* w5 = b4 + 128;
+  const float* b5 = w5 + 128;
+  auto conv = [&](const float* w, int cin, int cout, int off) {
+    for (int o = 0; o < cout; ++o)
+      for (int ci = 0; ci < cin; ++ci)
+        for (int ky = 0; ky < 3; ++ky)
+          for (int kx = 0; kx < 3; ++kx)
+            m[off + ((ky * 3 + kx) * cin + ci) * cout + o] = w[((o * cin + ci) * 3 + ky) * 3 + kx];
+  };
+  conv(w1, 3, C1, OW1);
+  conv(w2, C1, C2, OW2);
+  conv(w3, C2, C3, OW3);
+  for (int i = 0; i < C1; ++i) m[OB1 + i] = b1[i];
+  for (int i = 0; i < C2; ++i) m[OB2 + i] = b2[i];
+  for (int i = 0; i < C3; ++i) m[OB3 + i] = b3[i];
+  for (int o = 0; o < F4; ++o)
+    for (int c = 0; c < C3; ++c)
+      for (int p = 0; p < PIX4; ++p) m[OW4 + (p * C3 + c) * F4 + o] = w4[o * K4 + c * PIX4 + p];
+  for (int i = 0; i < F4; ++i) m[OB4 + i] = b4[i];
+  for (int i = 0; i < F4; ++i) m[OW5 + i] = w5[i];
+  m[OB5] = b5[0];
+}
+
+void master_to_abi(const float* m, float* a) {
+  float* w1 = a;
+  float* b1 = w1 + 32 * 27;
+  float* w2 = b1 + 32;
+  float* b2 = w2 + 64 * 288;
+  float* w3 = b2 + 64;
+  float* b3 = w3 + 64 * 576;
+  float* w4 = b3 + 64;
+  float* b4 = w4 + 128 * 576;
+  float* w5 = b4 + 128;
+  float* b5 = w5 + 128;
+  auto conv = [&](float* w, int cin, int cout, int off) {
+    for (int o = 0; o < cout; ++o)
+      for (int ci = 0; ci < cin; ++ci)
+        for (int ky = 0; ky < 3; ++ky)
+          for (int kx = 0; kx < 3; ++kx)
+            w[((o * cin + ci) * 3 + ky) * 3 + kx] = m[off + ((ky * 3 + kx) * cin + ci) * cout + o];
+  };
+  conv(w1, 3, C1, OW1);
+  conv(w2, C1, C2, OW2);
+  conv(w3, C2, C3, OW3);
+  for (int i = 0; i < C1; ++i) b1[i] = m[OB1 + i];
+  for (int i = 0; i < C2; ++i) b2[i] = m[OB2 + i];
+  for (int i = 0; i < C3; ++i) b3[i] = m[OB3 + i];
+  for (int o = 0; o < F4; ++o)
+    for (int c = 0; c < C3; ++c)
+      for (int p = 0; p < PIX4; ++p) w4[o * K4 + c * PIX4 + p] = m[OW4 + (p * C3 + c) * F4 + o];
+  for (int i = 0; i < F4; ++i) b4[i] = m[OB4 + i];
+  for (int i = 0; i < F4; ++i) w5[i] = m[OW5 + i];
+  b5[0] = m[OB5];
+}
+
+// splitmix64 -> uniform in [0, 1)
+double hash_uniform(uint64_t seed, uint64_t i) {
+  uint64_t z = seed * 0x9E3779B97F4A7C15ull + i + 0x632BE59BD9B4E019ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+}  // namespace
+
+struct rb_model_s {
+  int max_batch = 0;
+  int64_t step = 0;
+  float *params = nullptr, *grads = nullptr, *adam_m = nullptr, *adam_v = nullptr;
+  bf16* wbf = nullptr;                         // bf16 copy of the master vector
+  // activations / scratch for max_batch stamps
+  bf16 *xn = nullptr, *cols = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *dzb = nullptr, *dz4 = nullptr;
+  float *z1 = nullptr, *z2 = nullptr, *z3 = nullptr, *z4 = nullptr, *logit = nullptr, *dz5 = nullptr,
+        *dcols = nullptr, *da = nullptr;
+  uint8_t *i1 = nullptr, *i2 = nullptr, *i3 = nullptr;
+  size_t cols_elems = 0;
+};
+
+namespace {
+
+void free_model(rb_model_s* m) {
+  void* ptrs[] = {m->params, m->grads, m->adam_m, m->adam_v, m->wbf, m->xn,  m->cols, m->a1,   m->a2,
+                  m->a3,     m->dzb,    m->dz4,    m->z1,  m->z2,  m->z3,   m->z4,   m->logit,
+                  m->dz5,    m->dcols, m->da,     m->i1,     m->i2,  m->i3};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+template <typename T>
+bool alloc(T** p, size_t n) {
+  return cudaMalloc((void**)p, sizeof(T) * (n > 0 ? n : 1)) == cudaSuccess;
+}
+
+// forward for n <= max_batch normalised stamps in m->xn; logits to m->logit
+cudaError_t forward(rb_model_s* m, int n, cudaStream_t s, bool keep_idx) {
+  const bf16* W = m->wbf;
+  const float* P = m->params;
+  cudaError_t e;
+  // conv1
+  k_im2col<<<grid1((int64_t)n * PIX1 * K1), 256, 0, s>>>(m->xn, n, S31, S31, 3, K1, m->cols);
+  if ((e = gemm(s, n * PIX1, C1, K1, m->cols, K1, 0, W + OW1, C1, 0, m->z1, C1, P + OB1))) return e;
+  k_relu_pool<<<grid1((int64_t)n * PIX2 * C1), 256, 0, s>>>(m->z1, n, S31, S31, C1, m->a1, keep_idx ? m->i1 : nullptr);
+  // conv2
+  k_im2col<<<grid1((int64_t)n * PIX2 * K2), 256, 0, s>>>(m->a1, n, 15, 15, C1, K2, m->cols);
+  if ((e = gemm(s, n * PIX2, C2, K2, m->cols, K2, 0, W + OW2, C2, 0, m->z2, C2, P + OB2))) return e;
+  k_relu_pool<<<grid1((int64_t)n * PIX3 * C2), 256, 0, s>>>(m->z2, n, 15, 15, C2, m->a2, keep_idx ? m->i2 : nullptr);
+  // conv3
+  k_im2col<<<grid1((int64_t)n * PIX3 * K3), 256, 0, s>>>(m->a2, n, 7, 7, C2, K3, m->cols);
+  if ((e = gemm(s, n * PIX3, C3, K3, m->cols, K3, 0, W + OW3, C3, 0, m->z3, C3, P + OB3))) return e;
+  k_relu_pool<<<grid1((int64_t)n * PIX4 * C3), 256, 0, s>>>(m->z3, n, 7, 7, C3, m->a3, keep_idx ? m->i3 : nullptr);
+  // fc1 (NHWC flatten of a3 matches the W4 rows) and fc2
+  if ((e = gemm(s, n, F4, K4, m->a3, K4, 0, W + OW4, F4, 0, m->z4, F4, P + OB4))) return e;
+  k_fc2<<<(n * 32 + 255) / 256, 256, 0, s>>>(m->z4, P + OW5, P + OB5, n, m->logit);
+  return cudaGetLastError();
+}
+
+cudaError_t backward(rb_model_s* m, int n, const float* labels, float* loss_dev, cudaStream_t s) {
+  const bf16* W = m->wbf;
+  float* G = m->grads;
+  cudaError_t e;
+  cudaMemsetAsync(G, 0, sizeof(float) * NMASTER, s);
+  k_bce_head<<<1, 1024, 0, s>>>(m->logit, labels, n, m->z4, m->params + OW5, m->dz5, m->dz4, loss_dev);
+  k_fc2_grad<<<1, F4, 0, s>>>(m->dz5, m->z4, n, G + OW5, G + OB5);
+  // fc1: dW4 = a3^T dz4, db4 = colsum(dz4), da3 = dz4 W4^T
+  if ((e = gemm(s, K4, F4, n, m->a3, K4, 1, m->dz4, F4, 0, G + OW4, F4, nullptr))) return e;
+  k_colsum<<<F4, 256, 0, s>>>(m->dz4, n, F4, G + OB4);
+  if ((e = gemm(s, n, K4, F4, m->dz4, F4, 0, W + OW4, F4, 1, m->da, K4, nullptr))) return e;
+  // conv3
+  k_pool_relu_back<<<grid1((int64_t)n * PIX3 * C3), 256, 0, s>>>(m->da, m->i3, m->z3, n, 7, 7, C3, m->dzb);
+  k_im2col<<<grid1((int64_t)n * PIX3 * K3), 256, 0, s>>>(m->a2, n, 7, 7, C2, K3, m->cols);
+  if ((e = gemm(s, K3, C3, n * PIX3, m->cols, K3, 1, m->dzb, C3, 0, G + OW3, C3, nullptr))) return e;
+  k_colsum<<<C3, 256, 0, s>>>(m->dzb, (int64_t)n * PIX3, C3, G + OB3);
+  if ((e = gemm(s, n * PIX3, K3, C3, m->dzb, C3, 0, W + OW3, C3, 1, m->dcols, K3, nullptr))) return e;
+  k_col2im<<<grid1((int64_t)n * PIX3 * C2), 256, 0, s>>>(m->dcols, n, 7, 7, C2, K3, m->da);
+  // conv2
+  k_pool_relu_back<<<grid1((int64_t)n * PIX2 * C2), 256, 0, s>>>(m->da, m->i2, m->z2, n, 15, 15, C2, m->dzb);
+  k_im2col<<<grid1((int64_t)n * PIX2 * K2), 256, 0, s>>>(m->a1, n, 15, 15, C1, K2, m->cols);
+  if ((e = gemm(s, K2, C2, n * PIX2, m->cols, K2, 1, m->dzb, C2, 0, G + OW2, C2, nullptr))) return e;
+  k_colsum<<<C2, 256, 0, s>>>(m->dzb, (int64_t)n * PIX2, C2, G + OB2);
+  if ((e = gemm(s, n * PIX2, K2, C2, m->dzb, C2, 0, W + OW2, C2, 1, m->dcols, K2, nullptr))) return e;
+  k_col2im<<<grid1((int64_t)n * PIX2 * C1), 256, 0, s>>>(m->dcols, n, 15, 15, C1, K2, m->da);
+  // conv1 (no input gradient)
+  k_pool_relu_back<<<grid1((int64_t)n * PIX1 * C1), 256, 0, s>>>(m->da, m->i1, m->z1, n, S31, S31, C1, m->dzb);
+  k_im2col<<<grid1((int64_t)n * PIX1 * K1), 256, 0, s>>>(m->xn, n, S31, S31, 3, K1, m->cols);
+  if ((e = gemm(s, K1, C1, n * PIX1, m->cols, K1, 1, m->dzb, C1, 0, G + OW1, C1, nullptr))) return e;
+  k_colsum<<<C1, 256, 0, s>>>(m->dzb, (int64_t)n * PIX1, C1, G + OB1);
+  return cudaGetLastError();
+}
+
+void refresh_bf16(rb_model_s* m, cudaStream_t s) { k_to_bf16<<<grid1(NMASTER), 256, 0, s>>>(m->params, NMASTER, m->wbf); }
+
+sfft_status_t fail(cudaError_t e, const char* where) {
+  sfft::set_last_error((std::string(where) + ": " + cudaGetErrorString(e)).c_str());
+  return SFFT_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" sfft_status_t rb_create(const int32_t* desc, rb_model_t* out) {
+  if (!desc || !out || desc[0] < 1) return SFFT_ERR_ARG;
+  *out = nullptr;
+  rb_model_s* m = new (std::nothrow) rb_model_s();
+  if (!m) return SFFT_ERR_NOMEM;
+  const int B = desc[0];
+  m->max_batch = B;
+  const size_t cols = std::max<size_t>({(size_t)B * PIX1 * K1, (size_t)B * PIX2 * K2, (size_t)B * PIX3 * K3});
+  m->cols_elems = cols;
+  bool ok = alloc(&m->params, NMASTER) && alloc(&m->grads, NMASTER) && alloc(&m->adam_m, NMASTER) &&
+            alloc(&m->adam_v, NMASTER) && alloc(&m->wbf, NMASTER) && alloc(&m->xn, (size_t)B * PIX1 * 3) &&
+            alloc(&m->cols, cols) && alloc(&m->a1, (size_t)B * PIX2 * C1) && alloc(&m->a2, (size_t)B * PIX3 * C2) &&
+            alloc(&m->a3, (size_t)B * PIX4 * C3) &&
+            alloc(&m->dzb, (size_t)B * PIX1 * C1) && alloc(&m->dz4, (size_t)B * F4) &&
+            alloc(&m->z1, (size_t)B * PIX1 * C1) && alloc(&m->z2, (size_t)B * PIX2 * C2) &&
+            alloc(&m->z3, (size_t)B * PIX3 * C3) && alloc(&m->z4, (size_t)B * F4) && alloc(&m->logit, (size_t)B) &&
+            alloc(&m->dz5, (size_t)B) && alloc(&m->dcols, cols) && alloc(&m->da, (size_t)B * PIX2 * C1 + B * K4) &&
+            alloc(&m->i1, (size_t)B * PIX2 * C1) && alloc(&m->i2, (size_t)B * PIX3 * C2) &&
+            alloc(&m->i3, (size_t)B * PIX4 * C3);
+  if (!ok) {
+    free_model(m);
+    delete m;
+    return SFFT_ERR_NOMEM;
+  }
+  // uniform He-style initialisation in the C-ABI layout, zero biases
+  std::vector<float> abi(RB_NPARAM, 0.f);
+  const int wsz[5] = {32 * 27, 64 * 288, 64 * 576, 128 * 576, 128};
+  const int bsz[5] = {32, 64, 64, 128, 1};
+  const int fan[5] = {27, 288, 576, 576, 128};
+  size_t o = 0;
+  for (int l = 0; l < 5; ++l) {
+    const double lim = sqrt(6.0 / fan[l]);
+    for (int i = 0; i < wsz[l]; ++i) abi[o + i] = (float)((2.0 * hash_uniform((uint64_t)desc[1], o + i) - 1.0) * lim);
+    o += wsz[l] + bsz[l];
+  }
+  std::vector<float> master;
+  abi_to_master(abi.data(), master);
+  cudaError_t e = cudaMemcpy(m->params, master.data(), sizeof(float) * NMASTER, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(m->adam_m, 0, sizeof(float) * NMASTER);
+  if (e == cudaSuccess) e = cudaMemset(m->adam_v, 0, sizeof(float) * NMASTER);
+  if (e == cudaSuccess) e = cudaMemset(m->grads, 0, sizeof(float) * NMASTER);
+  if (e == cudaSuccess) {
+    refresh_bf16(m, nullptr);
+    e = cudaDeviceSynchronize();
+  }
+  if (e != cudaSuccess) {
+    free_model(m);
+    delete m;
+    return fail(e, "rb_create");
+  }
+  *out = m;
+  return SFFT_OK;
+}
+
+extern "C" sfft_status_t rb_destroy(rb_model_t m) {
+  if (!m) return SFFT_ERR_ARG;
+  free_model(m);
+  delete m;
+  return SFFT_OK;
+}
+
+extern "C" sfft_status_t rb_set_weights(rb_model_t m, const void* host_buf, size_t bytes) {
+  if (!m || !host_buf || bytes != sizeof(float) * RB_NPARAM) return SFFT_ERR_ARG;
+  std::vector<float> master;
+  abi_to_master(static_cast<const float*>(host_buf), master);
+  cudaError_t e = cudaMemcpy(m->params, master.data(), sizeof(float) * NMASTER, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(e, "rb_set_weights");
+  refresh_bf16(m, nullptr);
+  e = cudaDeviceSynchronize();
+  return e == cudaSuccess ? SFFT_OK : fail(e, "rb_set_weights");
+}
+
+static sfft_status_t get_vec(const float* dev, void* host_buf, size_t bytes, const char* where) {
+  if (!dev || !host_buf || bytes != sizeof(float) * RB_NPARAM) return SFFT_ERR_ARG;
+  std::vector<float> master(NMASTER);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(master.data(), dev, sizeof(float) * NMASTER, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(e, where);
+  master_to_abi(master.data(), static_cast<float*>(host_buf));
+  return SFFT_OK;
+}
+
+extern "C" sfft_status_t rb_get_weights(rb_model_t m, void* host_buf, size_t bytes) {
+  return m ? get_vec(m->params, host_buf, bytes, "rb_get_weights") : SFFT_ERR_ARG;
+}
+extern "C" sfft_status_t rb_get_grads(rb_model_t m, void* host_buf, size_t bytes) {
+  return m ? get_vec(m->grads, host_buf, bytes, "rb_get_grads") : SFFT_ERR_ARG;
+}
+
+extern "C" sfft_status_t rb_get_state(rb_model_t m, void* host_buf, size_t bytes, int64_t* step) {
+  if (!m || !host_buf || bytes != 3 * sizeof(float) * RB_NPARAM) return SFFT_ERR_ARG;
+  float* h = static_cast<float*>(host_buf);
+  sfft_status_t st = get_vec(m->params, h, sizeof(float) * RB_NPARAM, "rb_get_state");
+  if (st == SFFT_OK) st = get_vec(m->adam_m, h + RB_NPARAM, sizeof(float) * RB_NPARAM, "rb_get_state");
+  if (st == SFFT_OK) st = get_vec(m->adam_v, h + 2 * RB_NPARAM, sizeof(float) * RB_NPARAM, "rb_get_state");
+  if (st == SFFT_OK && step) *step = m->step;
+  return st;
+}
+
+extern "C" sfft_status_t rb_set_state(rb_model_t m, const void* host_buf, size_t bytes, int64_t step) {
+  if (!m || !host_buf || bytes != 3 * sizeof(float) * RB_NPARAM || step < 0) return SFFT_ERR_ARG;
+  const float* h = static_cast<const float*>(host_buf);
+  float* dst[3] = {m->params, m->adam_m, m->adam_v};
+  for (int i = 0; i < 3; ++i) {
+    std::vector<float> master;
+    abi_to_master(h + (size_t)i * RB_NPARAM, master);
+    cudaError_t e = cudaMemcpy(dst[i], master.data(), sizeof(float) * NMASTER, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(e, "rb_set_state");
+  }
+  m->step = step;
+  refresh_bf16(m, nullptr);
+  cudaError_t e = cudaDeviceSynchronize();
+  return e == cudaSuccess ? SFFT_OK : fail(e, "rb_set_state");
+}
+
+extern "C" sfft_status_t rb_logits(rb_model_t m, const float* stamps, int64_t n, float* logit, void* stream) {
+  if (!m || (n > 0 && (!stamps || !logit)) || n < 0) return SFFT_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int64_t i0 = 0; i0 < n; i0 += m->max_batch) {
+    const int nb = (int)std::min<int64_t>(m->max_batch, n - i0);
+    k_normalise<<<nb, 256, 0, s>>>(stamps + i0 * 3 * PIX1, m->xn);
+    cudaError_t e = forward(m, nb, s, false);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(logit + i0, m->logit, sizeof(float) * nb, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return fail(e, "rb_logits");
+  }
+  return SFFT_OK;
+}
+
+extern "C" sfft_status_t rb_score(rb_model_t m, const float* stamps, int64_t n, float* score, void* stream) {
+  sfft_status_t st = rb_logits(m, stamps, n, score, stream);
+  if (st != SFFT_OK || n == 0) return st;
+  k_sigmoid<<<grid1(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(score, n, score);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SFFT_OK : fail(e, "rb_score");
+}
+
+extern "C" sfft_status_t rb_backward(rb_model_t m, const float* stamps, const float* labels, int64_t n,
+                                     float* loss_dev, void* stream) {
+  if (!m || !stamps || !labels || n < 1 || n > m->max_batch) return SFFT_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int nb = (int)n;
+  k_normalise<<<nb, 256, 0, s>>>(stamps, m->xn);
+  cudaError_t e = forward(m, nb, s, true);
+  if (e == cudaSuccess) e = backward(m, nb, labels, loss_dev, s);
+  return e == cudaSuccess ? SFFT_OK : fail(e, "rb_backward");
+}
+
+extern "C" sfft_status_t rb_train_step(rb_model_t m, const float* stamps, const float* labels, int64_t n, float lr,
+                                       float* loss_dev, void* stream) {
+  sfft_status_t st = rb_backward(m, stamps, labels, n, loss_dev, stream);
+  if (st != SFFT_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  m->step += 1;
+  const float c1 = (float)(1.0 - pow(0.9, (double)m->step)), c2 = (float)(1.0 - pow(0.999, (double)m->step));
+  k_adam<<<grid1(NMASTER), 256, 0, s>>>(m->params, m->grads, m->adam_m, m->adam_v, NMASTER, lr, c1, c2);
+  refresh_bf16(m, s);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SFFT_OK : fail(e, "rb_train_step");
+}

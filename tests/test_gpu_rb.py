@@ -1,0 +1,252 @@
+"""GPU parity of the stamp classifier, the detector and the shape cuts
+(through the C ABI) against the FP64 oracles.
+
+Tolerances.  The classifier rounds its normalised inputs, weights and every
+hidden activation to BF16 (relative rounding error <= 2^-9) and accumulates in
+FP32.  Five rounded layers give an expected relative error of a few 1e-3 in
+the logits; the bar is 2e-2 of the logits' RMS.  Gradients add one more
+rounding of each back-propagated signal and sign flips of ReLU/max-pool
+decisions taken on slightly different values, so they are compared per tensor
+by cosine similarity (>= 0.99) and relative L2 error (<= 0.1).  The detector
+filters in FP32 (31 taps per pass, two passes): its SNR map agrees with the
+FP64 map to 1e-5 of max |SNR| + 1e-5; candidate decisions may differ only where
+the oracle's margin (to the threshold or to a neighbour) is below 1e-3.  The
+shape cuts run in FP64 on both sides and must agree exactly.
+"""
+import numpy as np
+import pytest
+
+from oracle import cnn_oracle as C
+from oracle import detect_oracle as DO
+from synth.stamps import make_stamps
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+def _dev(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV).to(dtype)
+
+
+def _params(seed, bias_sd=0.05):
+    p = C.init_params(seed)
+    rng = np.random.default_rng(seed + 1)
+    for k in C.ORDER:
+        if k.startswith("b"):
+            p[k] = rng.normal(0, bias_sd, p[k].shape)
+    return p
+
+
+def _model(params, max_batch):
+    from paper_2603_08593_gb300 import RBModel
+    m = RBModel(max_batch=max_batch, seed=0)
+    m.set_weights(C.flatten(params).astype(np.float32))
+    return m
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def test_weights_roundtrip_exact():
+    from paper_2603_08593_gb300 import RBModel
+    m = RBModel(max_batch=4, seed=3)
+    w = np.random.default_rng(0).normal(0, 1, C.n_params()).astype(np.float32)
+    m.set_weights(w)
+    assert np.array_equal(m.get_weights(), w)
+    # the initialiser follows the uniform He ranges with zero biases
+    m2 = RBModel(max_batch=4, seed=11)
+    p = C.unflatten(m2.get_weights())
+    for k in C.ORDER:
+        if k.startswith("b"):
+            assert np.all(p[k] == 0)
+        else:
+            lim = np.sqrt(6.0 / np.prod(C.SHAPES[k][1:]))
+            assert np.abs(p[k]).max() <= lim and np.abs(p[k]).max() > 0.9 * lim
+
+
+@pytest.mark.parametrize("n,max_batch", [(1, 8), (37, 16), (300, 128)])
+def test_logits_and_scores_match_oracle(n, max_batch):
+    d = make_stamps(n, seed=100 + n)
+    p = _params(5)
+    m = _model(p, max_batch)
+    st = _dev(d["stamps"])
+    z = m.logits(st).cpu().numpy().astype(np.float64)
+    s = m.score(st).cpu().numpy().astype(np.float64)
+    zo = C.forward(p, C.normalise(d["stamps"].astype(np.float64)))
+    rms = max(np.sqrt(np.mean(zo ** 2)), 1e-3)
+    assert np.max(np.abs(z - zo)) <= 2e-2 * rms + 1e-4, (np.max(np.abs(z - zo)), rms)
+    assert np.allclose(s, 1 / (1 + np.exp(-z)), rtol=0, atol=2e-6)
+
+
+def test_normalisation_edge_cases():
+    # constant channels (MAD 0 -> scale 1), huge outliers (clip at +-64) and a
+    # channel of a few distinct values all go through the same path as the oracle
+    rng = np.random.default_rng(9)
+    st = rng.normal(1000, 30, (4, 3, 31, 31)).astype(np.float32)
+    st[0, 0] = 500.0
+    st[1, 2, 15, 15] = 1e7
+    st[2, 1] = rng.integers(0, 3, (31, 31)).astype(np.float32)
+    st[3] *= 0
+    p = _params(2)
+    m = _model(p, 4)
+    z = m.logits(_dev(st)).cpu().numpy().astype(np.float64)
+    zo = C.forward(p, C.normalise(st.astype(np.float64)))
+    assert np.max(np.abs(z - zo)) <= 2e-2 * np.sqrt(np.mean(zo ** 2)) + 1e-4
+
+
+def test_gradients_match_oracle():
+    d = make_stamps(48, seed=7)
+    p = _params(13)
+    m = _model(p, 64)
+    loss = m.backward(_dev(d["stamps"]), _dev(d["labels"]))
+    g = C.unflatten(m.get_grads())
+    lo, go = C.loss_and_grads(p, C.normalise(d["stamps"].astype(np.float64)), d["labels"].astype(np.float64))
+    assert abs(float(loss.item()) - lo) <= 2e-2 * abs(lo)
+    for k in C.ORDER:
+        a, b = g[k].ravel().astype(np.float64), go[k].ravel()
+        cos = float(a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30))
+        assert cos >= 0.99 and _rel(a, b) <= 0.1, (k, cos, _rel(a, b))
+
+
+def test_adam_step_and_checkpoint_resume():
+    d = make_stamps(32, seed=21)
+    p = _params(4)
+    st, lab = _dev(d["stamps"]), _dev(d["labels"])
+    m = _model(p, 32)
+    m.train_step(st, lab, lr=1e-3)
+    g = m.get_grads().astype(np.float64)
+    w1 = m.get_weights().astype(np.float64)
+    # first Adam step: theta - lr g / (|g| + eps) with the model's own gradient
+    w0 = C.flatten(p).astype(np.float32).astype(np.float64)
+    exp = w0 - 1e-3 * g / (np.abs(g) + 1e-8)
+    assert np.allclose(w1, exp, rtol=0, atol=2e-6)
+    state, step = m.get_state()
+    assert step == 1 and state.size == 3 * C.n_params()
+    # resume on a fresh model: the next step is identical
+    m.train_step(st, lab, lr=1e-3)
+    w2 = m.get_weights()
+    m2 = _model(p, 32)
+    m2.set_state(state, step)
+    m2.train_step(st, lab, lr=1e-3)
+    assert np.array_equal(m2.get_weights(), w2)
+
+
+def test_training_reduces_loss():
+    d = make_stamps(256, seed=31)
+    from paper_2603_08593_gb300 import RBModel
+    m = RBModel(max_batch=256, seed=1)
+    st, lab = _dev(d["stamps"]), _dev(d["labels"])
+    l0 = float(m.backward(st, lab).item())
+    for _ in range(60):
+        m.train_step(st, lab, lr=2e-3)
+    l1 = float(m.backward(st, lab).item())
+    assert l1 < 0.5 * l0, (l0, l1)
+
+
+# ---------------------------------------------------------------- detection
+def _det_image(H, W, seed, n_blobs=12, sigma=1.4):
+    rng = np.random.default_rng(seed)
+    D = rng.normal(0, 30.0, (H, W))
+    yy, xx = np.mgrid[0:H, 0:W]
+    for _ in range(n_blobs):
+        y, x = rng.uniform(0, H), rng.uniform(0, W)
+        D += rng.uniform(100, 3000) * np.exp(-((yy - y) ** 2 + (xx - x) ** 2) / (2 * sigma * sigma))
+    bad = (rng.random((H, W)) < 0.01).astype(np.uint8)
+    bad[:, W // 3] = 1
+    D[rng.random((H, W)) < 0.001] = np.nan
+    S = rng.normal(1000, 30, (H, W))
+    R = rng.normal(1000, 30, (H, W))
+    return D.astype(np.float32), S.astype(np.float32), R.astype(np.float32), bad
+
+
+def _margins(snr, y, x, thresh):
+    v = snr[y, x]
+    nb = snr[y - 2:y + 3, x - 2:x + 3].copy()
+    nb[2, 2] = -np.inf
+    return min(abs(v - thresh), abs(v - np.nanmax(nb)))
+
+
+@pytest.mark.parametrize("H,W,batch,use_bad", [(64, 80, 1, True), (157, 203, 2, True), (300, 129, 3, False)])
+def test_detect_matches_oracle(H, W, batch, use_bad):
+    from paper_2603_08593_gb300 import Detector
+    imgs = [_det_image(H, W, 40 + b) for b in range(batch)]
+    D = np.stack([i[0] for i in imgs]); S = np.stack([i[1] for i in imgs]); R = np.stack([i[2] for i in imgs])
+    bad = np.stack([i[3] for i in imgs])
+    det = Detector(H, W, batch=batch, max_cand=64)
+    xy, snr, count, stamps = det(_dev(D), _dev(S), _dev(R), _dev(bad, torch.uint8) if use_bad else None,
+                                 psf_sigma=1.4, thresh=5.0)
+    torch.cuda.synchronize()
+    smap = det.snr_map.cpu().numpy()
+    xy, snr, count, stamps = xy.cpu().numpy(), snr.cpu().numpy(), count.cpu().numpy(), stamps.cpu().numpy()
+    for b in range(batch):
+        o = DO.detect(D[b], S[b], R[b], bad[b] if use_bad else None, 1.4, 5.0, max_cand=64)
+        ref = o["snr_map"]
+        assert np.max(np.abs(smap[b] - ref)) <= 1e-5 * np.max(np.abs(ref)) + 1e-5
+        got = set(map(tuple, xy[b, :min(count[b], 64)][:, ::-1].tolist()))
+        exp = set(zip(o["y"].tolist(), o["x"].tolist()))
+        for (y, x) in got ^ exp:
+            assert _margins(ref, y, x, 5.0) < 1e-3, (y, x)
+        if got == exp:
+            assert count[b] == o["count"]
+            n = min(count[b], 64)
+            order = [tuple(v) for v in xy[b, :n][:, ::-1].tolist()]
+            assert order == sorted(order)
+            assert np.array_equal(stamps[b, :n], o["stamps"].astype(np.float32))
+            assert np.array_equal(snr[b, :n], smap[b][xy[b, :n, 1], xy[b, :n, 0]])
+
+
+def test_detect_truncation_and_empty():
+    from paper_2603_08593_gb300 import Detector
+    D, S, R, bad = _det_image(120, 150, 3, n_blobs=30)
+    det = Detector(120, 150, batch=1, max_cand=3)
+    xy, snr, count, _ = det(_dev(D[None]), _dev(S[None]), _dev(R[None]), _dev(bad[None], torch.uint8), 1.4, 5.0)
+    o = DO.detect(D, S, R, bad, 1.4, 5.0)
+    assert int(count[0]) == o["count"] > 3
+    assert [tuple(v) for v in xy[0].cpu().numpy()[:, ::-1].tolist()] == list(zip(o["y"][:3], o["x"][:3]))
+    _, _, count, _ = det(_dev(D[None]), _dev(S[None]), _dev(R[None]), None, 1.4, 1e30)
+    assert int(count[0]) == 0
+
+
+def test_detect_full_ccd_sampled():
+    """A 4096 x 2048 CCD: clipped sigma from the oracle on the whole image, the
+    SNR map checked at sampled windows computed by the oracle on crops."""
+    from paper_2603_08593_gb300 import Detector
+    H, W = 4096, 2048
+    rng = np.random.default_rng(5)
+    D = rng.normal(0, 45.0, (H, W)).astype(np.float32)
+    bad = np.zeros((H, W), np.uint8)
+    bad[:, 700] = 1
+    bad[:, 1500] = 1
+    det = Detector(H, W, 1, max_cand=4096)
+    Dd = _dev(D[None])
+    xy, snr, count, _ = det(Dd, Dd, Dd, _dev(bad[None], torch.uint8), psf_sigma=0.8, thresh=4.0)
+    torch.cuda.synchronize()
+    smap = det.snr_map[0].cpu().numpy()
+    mu, sd = DO.clipped_sigma(D, bad)
+    r = 3
+    for _ in range(12):
+        y0, x0 = int(rng.integers(40, H - 80)), int(rng.integers(40, W - 80))
+        crop = D[y0 - r:y0 + 40 + r, x0 - r:x0 + 40 + r]
+        cbad = bad[y0 - r:y0 + 40 + r, x0 - r:x0 + 40 + r]
+        ref = DO.matched_snr(crop, cbad, 0.8, sd)[r:-r, r:-r]
+        assert np.max(np.abs(smap[y0:y0 + 40, x0:x0 + 40] - ref)) <= 1e-4
+    # white noise: the SNR map is unit variance; the count is that of the map's own local maxima
+    assert abs(np.std(smap[100:-100, 100:-100]) - 1.0) < 0.01
+    n_exp = len(DO.candidates(smap.astype(np.float64), bad, 4.0)[0])
+    assert int(count[0]) == n_exp
+
+
+def test_shape_cuts_match_oracle():
+    from paper_2603_08593_gb300 import shape_cuts
+    d = make_stamps(400, seed=17)
+    rng = np.random.default_rng(2)
+    snr = rng.uniform(2, 60, 400).astype(np.float32)
+    st = d["stamps"].copy()
+    st[:5, 2] = 0.0                          # no positive flux
+    out = shape_cuts(_dev(st), _dev(snr), psf_fwhm=1.8, snr_min=5.0).cpu().numpy()
+    exp = np.array([C.shape_cuts(st[i, 2], float(snr[i]), 1.8, 5.0) for i in range(400)], np.int32)
+    assert np.array_equal(out, exp)
+    assert 0 < exp.sum() < 400
