@@ -34,7 +34,8 @@ extern "C" {
 
 typedef struct rb_model_s* rb_model_t;
 
-/* desc[0] = max stamps per internal batch (>= 1), desc[1] = initialisation
+/* desc[0] = max stamps per internal batch (1 .. 4096, else
+ * SFFT_ERR_UNSUPPORTED), desc[1] = initialisation
  * seed (uniform He-style weights, zero biases).  Allocates the weights, Adam
  * state and activation scratch for desc[0] stamps on the current device. */
 sfft_status_t rb_create(const int32_t* desc, rb_model_t* out);

@@ -526,6 +526,7 @@ sfft_status_t fail(cudaError_t e, const char* where) {
 extern "C" sfft_status_t rb_create(const int32_t* desc, rb_model_t* out) {
   if (!desc || !out || desc[0] < 1) return SFFT_ERR_ARG;
   *out = nullptr;
+  if (desc[0] > 4096) return SFFT_ERR_UNSUPPORTED;   // GEMM grid rows: 961 * batch / 64 <= 65535
   rb_model_s* m = new (std::nothrow) rb_model_s();
   if (!m) return SFFT_ERR_NOMEM;
   const int B = desc[0];

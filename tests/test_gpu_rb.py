@@ -3,8 +3,14 @@
 
 Tolerances.  The classifier rounds its normalised inputs, weights and every
 hidden activation to BF16 (relative rounding error <= 2^-9) and accumulates in
-FP32.  Five rounded layers give an expected relative error of a few 1e-3 in
-the logits; the bar is 2e-2 of the logits' RMS.  Gradients add one more
+FP32.  Against the FP64 oracle that gives, on these inputs, a relative L2
+error of 2e-3 to 7e-3 in the logits with single logits off by up to ~4 % of
+the logits' RMS (an FP64 model of the same roundings reproduces these errors);
+the bars are 1.5e-2 (L2) and 6e-2 of the RMS (max).  The same oracle layers
+with the kernel's roundings applied (inputs, weights and pooled activations
+rounded to BF16) must agree with the GPU to 5e-3 of the RMS (the GPU
+normalises in FP32, so a few inputs round to the neighbouring BF16 value),
+which separates layout or indexing mistakes from rounding.  Gradients add one more
 rounding of each back-propagated signal and sign flips of ReLU/max-pool
 decisions taken on slightly different values, so they are compared per tensor
 by cosine similarity (>= 0.99) and relative L2 error (<= 0.1).  The detector
@@ -50,6 +56,33 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
+def _bf16(x):
+    """Round to the nearest BF16 (ties to even), as the kernels store operands."""
+    a = np.ascontiguousarray(x, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _forward_bf16(p, xn):
+    """Oracle layers with the kernels' BF16 roundings applied."""
+    a = _bf16(xn)
+    for wk, bk in [("w1", "b1"), ("w2", "b2"), ("w3", "b3")]:
+        a = _bf16(C.maxpool2(np.maximum(C.conv_same(a, _bf16(p[wk]), p[bk]), 0.0))[0])
+    h4 = np.maximum(a.reshape(a.shape[0], -1) @ _bf16(p["w4"]).T + p["b4"], 0.0)
+    return (h4 @ p["w5"].T + p["b5"])[:, 0]
+
+
+def _check_logits(z, p, stamps):
+    xn = C.normalise(stamps.astype(np.float64))
+    zo = C.forward(p, xn)
+    rms = max(np.sqrt(np.mean(zo ** 2)), 1e-3)
+    assert _rel(z, zo) <= 1.5e-2, _rel(z, zo)
+    assert np.max(np.abs(z - zo)) <= 6e-2 * rms + 1e-4, (np.max(np.abs(z - zo)), rms)
+    zb = _forward_bf16(p, xn)
+    assert np.max(np.abs(z - zb)) <= 5e-3 * rms + 1e-4, (np.max(np.abs(z - zb)), rms)
+
+
 def test_weights_roundtrip_exact():
     from paper_2603_08593_gb300 import RBModel
     m = RBModel(max_batch=4, seed=3)
@@ -75,9 +108,7 @@ def test_logits_and_scores_match_oracle(n, max_batch):
     st = _dev(d["stamps"])
     z = m.logits(st).cpu().numpy().astype(np.float64)
     s = m.score(st).cpu().numpy().astype(np.float64)
-    zo = C.forward(p, C.normalise(d["stamps"].astype(np.float64)))
-    rms = max(np.sqrt(np.mean(zo ** 2)), 1e-3)
-    assert np.max(np.abs(z - zo)) <= 2e-2 * rms + 1e-4, (np.max(np.abs(z - zo)), rms)
+    _check_logits(z, p, d["stamps"])
     assert np.allclose(s, 1 / (1 + np.exp(-z)), rtol=0, atol=2e-6)
 
 
@@ -93,8 +124,7 @@ def test_normalisation_edge_cases():
     p = _params(2)
     m = _model(p, 4)
     z = m.logits(_dev(st)).cpu().numpy().astype(np.float64)
-    zo = C.forward(p, C.normalise(st.astype(np.float64)))
-    assert np.max(np.abs(z - zo)) <= 2e-2 * np.sqrt(np.mean(zo ** 2)) + 1e-4
+    _check_logits(z, p, st)
 
 
 def test_gradients_match_oracle():
