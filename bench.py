@@ -35,6 +35,11 @@ L2_FLUSH_BYTES = 256 << 20
 WORKLOAD = ("one DECam CCD pair per GPU per step: 2048x4096 FP32, 20k stars, PSF FWHM 1.0-1.4 (R) / "
             "1.5-2.1 (S) px across the chip, saturation mask with 3 px dilation, two bad columns, "
             "50 transients; L=11, D_K=D_B=2, mixed precision, 1 refinement step")
+# DRAM bytes (read + write) of one full-size KK contraction launch, scaled from an
+# ncu capture of the same kernel on a 512-row strip (profiles/k_contract_*.md);
+# reported only while the kernel source is the one that was measured.
+KK_TRAFFIC_BYTES = 4.41e9 + 0.09e9
+KK_TRAFFIC_SOURCE_SHA256_16 = "f16859dc5ad5cc81"
 PHASES = ("prep", "fft_weights", "fft_prod", "contract_kk", "contract_rk", "scatter", "solve", "apply")
 
 
@@ -53,6 +58,16 @@ def kk_flops_per_ccd(H, W, L, DK):
     DM = 2 * DK
     per = (DM + 1) * 6 + (DM + 1) * (DM + 2) // 2 * 4
     return half_plane_lag_rows(L) * (H - (L - 1)) * M * per
+
+
+def kk_traffic_bytes():
+    import hashlib
+    path = os.path.join(ROOT, "paper_2603_08593_gb300", "csrc", "kernels_contract.cu")
+    try:
+        h = hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return KK_TRAFFIC_BYTES if h == KK_TRAFFIC_SOURCE_SHA256_16 else None
 
 
 def fp32_alu_peak_tflops(clock_mhz):
@@ -164,102 +179,164 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+def _c4_pair(index):
+    from synth import config_pair
+    d = config_pair("c4", index)
+    return {k: d[k] for k in ("R", "S", "bad", "transients", "masked_fraction")}
+
+
+def load_pairs(args, rank):
+    """The step's CCD pairs: the C2/C3 pair (or a shorter strip of the same
+    recipe for profiling captures), or `batch` CCDs of one C4 exposure.
+    Replica ranks draw independent pairs from the same recipe."""
+    from synth import config_pair, make_pair
+    from synth.decam import SAT_CLIP_ADU
+    if args.batch > 1:
+        import multiprocessing as mp
+        idx = [60 * rank + i for i in range(args.batch)]
+        with mp.get_context("spawn").Pool(max(1, min(16, _CORES))) as pool:
+            return pool.map(_c4_pair, idx)
+    if rank == 0 and args.rows == H:
+        return [config_pair("c2")]
+    return [make_pair(args.rows, W, seed=2 + 1000 * rank, n_src=max(1, 20000 * args.rows // H),
+                      fwhm_R=(1.0, 1.4), fwhm_S=(1.5, 2.1), shift=(0.1, 0.0), n_transients=50,
+                      snr=(5.0, 50.0), clip=SAT_CLIP_ADU, mask_saturated=True, bad_columns=(700, 1500))]
+
+
+def _subtract_steps(plan, R, S, bad, out, n, stream, flush=None, events=None):
+    for i in range(n):
+        if flush is not None:
+            flush.fill_(i & 0xff)                           # evict L2 between timed steps
+        if events is not None:
+            events[i][0].record(stream)
+        plan.subtract(R, S, bad, None, refine=REFINE, out=out)
+        if events is not None:
+            events[i][1].record(stream)
+
+
+def _max_over_ranks(dist, dev, x):
+    import torch
+    if dist is None:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_gpu(args):
     import torch
     from paper_2603_08593_gb300 import Plan
-    from synth import config_pair, make_pair
-    from synth.decam import SAT_CLIP_ADU
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    pairs = load_pairs(args, rank)                          # before the first CUDA call (spawned pool)
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-
-    if rank == 0:
-        d = config_pair("c2")
-    else:   # replicas: an independent CCD pair with the same recipe per rank
-        d = make_pair(4096, 2048, seed=2 + 1000 * rank, n_src=20000, fwhm_R=(1.0, 1.4), fwhm_S=(1.5, 2.1),
-                      shift=(0.1, 0.0), n_transients=50, snr=(5.0, 50.0), clip=SAT_CLIP_ADU,
-                      mask_saturated=True, bad_columns=(700, 1500))
+    B, Hs = len(pairs), pairs[0]["R"].shape[0]
+    batched = B > 1
 
     cpu_base = None
     if rank == 0 and not args.no_cpu_baseline:
-        dt, frac = oracle_strip_seconds(d, args.cpu_rows)
+        dt, frac = oracle_strip_seconds(pairs[0], args.cpu_rows)
         cpu_base = {"value": frac / dt, "unit": UNIT, "cores": _CORES, "kind": "oracle",
                     "sample": (f"FP64 NumPy/SciPy oracle (definition-form normal equations, Cholesky, FP64 apply) "
-                               f"on the first {args.cpu_rows} of 4096 rows, {dt:.1f} s, scaled to CCD-pairs/s"),
+                               f"on the first {args.cpu_rows} of 4096 rows of one CCD pair, {dt:.1f} s, "
+                               f"scaled to CCD-pairs/s"),
                     "cpu": cpu_model()}
 
     stream = torch.cuda.Stream(device=dev)
-    R = torch.from_numpy(d["R"]).to(dev)[None].contiguous()
-    S = torch.from_numpy(d["S"]).to(dev)[None].contiguous()
-    bad = torch.from_numpy(d["bad"]).to(dev)[None].contiguous()
+    R = torch.from_numpy(np.stack([p["R"] for p in pairs])).to(dev).contiguous()
+    S = torch.from_numpy(np.stack([p["S"] for p in pairs])).to(dev).contiguous()
+    bad = torch.from_numpy(np.stack([p["bad"] for p in pairs])).to(dev).contiguous()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize(dev)
     with torch.cuda.stream(stream):
-        plan = Plan(H, W, L, DK, DB, batch=1, prec="mixed", stream=stream, device=dev)
+        plan = Plan(Hs, W, L, DK, DB, batch=B, prec=args.prec, stream=stream, device=dev, d_batch=args.d_batch,
+                    graph=batched)
+        if batched:
+            # per-phase times and launch counts from an eager profiled pass of the same plan
+            eager = Plan(Hs, W, L, DK, DB, batch=B, prec=args.prec, stream=stream, device=dev, d_batch=args.d_batch)
+            eo = eager.subtract(R, S, bad, None, refine=REFINE)
+            eager.profile(True)
+            eager.profile_read(reset=True)
+            _subtract_steps(eager, R, S, bad, eo, 1, stream)
+            stream.synchronize()
+            prof1 = eager.profile_read(reset=True)
+            prof = {k: (v[0] * args.steps, v[1] * args.steps) for k, v in prof1.items()}
+            del eager, eo
         out = plan.subtract(R, S, bad, None, refine=REFINE)
-        for _ in range(max(args.warmup - 1, 0)):
-            plan.subtract(R, S, bad, None, refine=REFINE, out=out)
+        _subtract_steps(plan, R, S, bad, out, max(args.warmup - 1, 0), stream)
         stream.synchronize()
-        info = int(out["info"][0])
-        plan.profile(True)
-        plan.profile_read(reset=True)
+        info = [int(v) for v in out["info"].cpu()]
+        if not batched:
+            plan.profile(True)
+            plan.profile_read(reset=True)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize(dev)
         with ClockSampler(local) as clk:
             t0 = time.perf_counter()
-            for i in range(args.steps):
-                flush.fill_(i & 0xff)                        # evict L2 between timed steps
-                evs[i][0].record(stream)
-                plan.subtract(R, S, bad, None, refine=REFINE, out=out)
-                evs[i][1].record(stream)
+            _subtract_steps(plan, R, S, bad, out, args.steps, stream, flush, evs)
             stream.synchronize()
             wall = time.perf_counter() - t0
-        prof = plan.profile_read(reset=True)
-        plan.profile(False)
+        if not batched:
+            prof = plan.profile_read(reset=True)
+            plan.profile(False)
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    dev_s = sum(step_ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([dev_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_s = float(t.item())
-    value = world * args.steps / dev_s
+    dev_s = _max_over_ranks(dist, dev, sum(step_ms) / 1e3)
+    value = world * B * args.steps / dev_s
 
-    # end to end through the public API: pinned host inputs in, difference image and theta out
+    # end to end through the public API: pinned host inputs in, difference images and theta out
     e2e = None
     if not args.no_e2e:
-        hR = torch.from_numpy(d["R"]).pin_memory(); hS = torch.from_numpy(d["S"]).pin_memory()
-        hb = torch.from_numpy(d["bad"]).pin_memory()
-        hD = torch.empty((H, W), dtype=torch.float32).pin_memory()
-        hth = torch.empty((plan.N,), dtype=torch.float64).pin_memory()
-        hinfo = torch.empty((1,), dtype=torch.int32).pin_memory()
+        hR = torch.from_numpy(R.cpu().numpy()).pin_memory(); hS = torch.from_numpy(S.cpu().numpy()).pin_memory()
+        hb = torch.from_numpy(bad.cpu().numpy()).pin_memory()
+        hD = torch.empty(tuple(out["D"].shape), dtype=torch.float32).pin_memory()
+        hth = torch.empty(tuple(out["theta"].shape), dtype=torch.float64).pin_memory()
+        hinfo = torch.empty((B,), dtype=torch.int32).pin_memory()
         with torch.cuda.stream(stream):
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             for it in range(args.steps + 1):
                 if it == 1:
                     ev0.record(stream)
-                R[0].copy_(hR, non_blocking=True); S[0].copy_(hS, non_blocking=True); bad[0].copy_(hb, non_blocking=True)
+                R.copy_(hR, non_blocking=True); S.copy_(hS, non_blocking=True); bad.copy_(hb, non_blocking=True)
                 plan.subtract(R, S, bad, None, refine=REFINE, out=out)
-                hD.copy_(out["D"][0], non_blocking=True); hth.copy_(out["theta"][0], non_blocking=True)
+                hD.copy_(out["D"], non_blocking=True); hth.copy_(out["theta"], non_blocking=True)
                 hinfo.copy_(out["info"], non_blocking=True)
             ev1.record(stream)
             stream.synchronize()
-        e_s = ev0.elapsed_time(ev1) / 1e3
-        if dist is not None:
-            t = torch.tensor([e_s], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_s = float(t.item())
-        e2e = {"value": world * args.steps / e_s, "unit": UNIT,
+        e_s = _max_over_ranks(dist, dev, ev0.elapsed_time(ev1) / 1e3)
+        e2e = {"value": world * B * args.steps / e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(hR.numel() * 4 + hS.numel() * 4 + hb.numel()),
-               "d2h_bytes_per_step": int(hD.numel() * 4 + hth.numel() * 8 + 4)}
+               "d2h_bytes_per_step": int(hD.numel() * 4 + hth.numel() * 8 + hinfo.numel() * 4)}
+    del plan, out
+    torch.cuda.empty_cache()
+
+    # the plain FP64 GPU path on the same pairs, one CCD per call, for comparison
+    fp64 = None
+    if args.fp64_steps > 0 and args.prec == "mixed":
+        n64 = min(args.fp64_steps, B) if batched else args.fp64_steps
+        with torch.cuda.stream(stream):
+            p64 = Plan(Hs, W, L, DK, DB, batch=1, prec="fp64", stream=stream, device=dev)
+            o64 = p64.subtract(R[:1], S[:1], bad[:1], None, refine=REFINE)
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(n64):
+                j = i % B
+                p64.subtract(R[j:j + 1], S[j:j + 1], bad[j:j + 1], None, refine=REFINE, out=o64)
+            e1.record(stream)
+            stream.synchronize()
+        s64 = _max_over_ranks(dist, dev, e0.elapsed_time(e1) / 1e3)
+        fp64 = {"value": world * n64 / s64, "unit": UNIT, "ms_per_ccd": 1e3 * s64 / n64, "ccds_timed": n64,
+                "note": "plain FP64 GPU path (FP64 FFTs, products and contraction), sequential single-CCD calls"}
+        del p64, o64
 
     if rank != 0:
         if dist is not None:
@@ -270,23 +347,39 @@ def run_gpu(args):
     roof = None
     clocks = clk.summary()
     if kk_n:
-        per_launch_flop = kk_flops_per_ccd(H, W, L, DK) / (kk_n / args.steps)
-        avg_ms = kk_ms / kk_n
+        # one launch = k_contract over one batch of offset differences plus its
+        # k_contract_slot0 companion (the exact DC/Nyquist slot of the same sums)
+        n_launch = kk_n / 2
+        per_launch_flop = B * kk_flops_per_ccd(Hs, W, L, DK) / (n_launch / args.steps)
+        avg_ms = kk_ms / n_launch
         achieved = per_launch_flop / (avg_ms * 1e-3) / 1e12
         clock = 2070.0
         peak = fp32_alu_peak_tflops(clock)
         roof = {"bound": "alu", "kernel": "k_contract (product-spectrum lag contraction)", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": args.traffic,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": args.traffic if args.traffic is not None else (kk_traffic_bytes() if Hs == H else None),
                 "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz max SM clock (derived, not measured)",
-                "avg_launch_ms": avg_ms, "launches_per_step": kk_n / args.steps}
+                "avg_launch_ms": avg_ms, "launches_per_step": n_launch / args.steps,
+                "traffic_note": "DRAM read+write bytes per launch, ncu on a 512-row strip scaled by rows x differences"}
+        if batched:
+            roof["timing_note"] = "kernel durations from an eager profiled pass of the same plan (timed steps replay a CUDA graph)"
+    if batched:
+        workload = (f"{B} CCD pairs of one DECam exposure per GPU per step (2048x4096 FP32 each, independent PSF "
+                    f"gradients, masked fractions 2-30 %, cosmics, bleed trails) in one CUDA-graph-captured call; "
+                    f"L=11, D_K=D_B=2, {args.prec}, 1 refinement step")
+    elif Hs != H:
+        workload = f"profiling strip: {Hs}x{W} rows of the DECam pair recipe (not the headline workload)"
+    else:
+        workload = WORKLOAD
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "H": H, "W": W, "L": L, "DK": DK, "DB": DB, "prec": "mixed",
-                       "refine": REFINE, "ccd_pairs_per_gpu_per_step": 1, "parallelism": f"replicas x{world}",
-                       "l2": "256 MB buffer written between timed steps (L2 flushed)"},
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.prec == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": workload, "H": Hs, "W": W, "L": L, "DK": DK, "DB": DB, "prec": args.prec,
+                       "refine": REFINE, "ccd_pairs_per_gpu_per_step": B, "parallelism": f"replicas x{world}",
+                       "cuda_graph": batched, "l2": "256 MB buffer written between timed steps (L2 flushed)"},
             "roofline": roof, "cpu_baseline": cpu_base, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clocks, "status": info, "wall_s": wall,
+            "clocks": clocks, "status": info, "wall_s": wall, "fp64_path": fp64,
             "phases_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -305,6 +398,11 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=512, help="rows of the CCD the CPU oracle baseline runs on")
     ap.add_argument("--ref-rows", type=int, default=256, help="rows per reference-arm step")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per contraction launch, if known")
+    ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--batch", type=int, default=1, help="CCD pairs per call; > 1 runs the C4 exposure batch")
+    ap.add_argument("--rows", type=int, default=H, help="rows per CCD (4096; fewer only for profiling captures)")
+    ap.add_argument("--d-batch", type=int, default=0, help="offset differences per workspace slab (0: plan default)")
+    ap.add_argument("--fp64-steps", type=int, default=2, help="CCDs timed on the plain FP64 path for comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

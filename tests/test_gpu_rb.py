@@ -127,6 +127,27 @@ def test_normalisation_edge_cases():
     _check_logits(z, p, st)
 
 
+@pytest.mark.parametrize("ch,c1,c2,c3,pos", [(2, 0, 0, 0, 4), (0, 5, 17, 33, 0), (1, 31, 63, 63, 8)])
+def test_delta_filters_route_one_pixel_block(ch, c1, c2, c3, pos):
+    """Delta filters through every layer: the logit is exactly the maximum of
+    relu(normalised input) over one 8 x 8 input block (BF16 values, FP32 sums
+    of a single term), which pins the im2col, weight and flatten layouts."""
+    p = {k: np.zeros(C.SHAPES[k]) for k in C.ORDER}
+    p["w1"][c1, ch, 1, 1] = 1.0
+    p["w2"][c2, c1, 1, 1] = 1.0
+    p["w3"][c3, c2, 1, 1] = 1.0
+    p["w4"][7, c3 * 9 + pos] = 1.0
+    p["w5"][0, 7] = 1.0
+    d = make_stamps(6, seed=60 + ch)
+    m = _model(p, 8)
+    z = m.logits(_dev(d["stamps"])).cpu().numpy().astype(np.float64)
+    xn = _bf16(C.normalise(d["stamps"].astype(np.float64)))
+    i, j = divmod(pos, 3)
+    ref = np.maximum(xn[:, ch, 8 * i:8 * i + 8, 8 * j:8 * j + 8].reshape(6, -1).max(axis=1), 0.0)
+    assert np.all(np.abs(z - ref) <= 2.0 ** -8 * np.abs(ref)), (z, ref)
+    assert np.all(ref > 0)
+
+
 def test_gradients_match_oracle():
     d = make_stamps(48, seed=7)
     p = _params(13)
