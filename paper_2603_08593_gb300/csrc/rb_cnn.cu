@@ -50,8 +50,9 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
 }
 
 __global__ void __launch_bounds__(128)
-k_gemm_bf16(int M, int N, int K, const bf16* __restrict__ A, int lda, int transA, const bf16* __restrict__ B,
-            int ldb, int transB, float* __restrict__ C, int ldc, const float* __restrict__ bias) {
+k_gemm_bf16(int M, int N, int K, int kchunk, const bf16* __restrict__ A, int lda, int transA,
+            const bf16* __restrict__ B, int ldb, int transB, float* __restrict__ C, int ldc,
+            const float* __restrict__ bias) {
   __shared__ __align__(16) bf16 As[GBM][GBK + GPAD];
   __shared__ __align__(16) bf16 Bs[GBN][GBK + GPAD];   // [n][k]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -66,13 +67,16 @@ k_gemm_bf16(int M, int N, int K, const bf16* __restrict__ A, int lda, int transA
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
   const bf16 zero = __float2bfloat16(0.f);
-  for (int k0 = 0; k0 < K; k0 += GBK) {
+  // split-K: CTA z covers k in [z * kchunk, min(K, (z + 1) * kchunk)) and writes its own C slice
+  const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+  C += (int64_t)blockIdx.z * M * ldc;
+  for (int k0 = kbeg; k0 < kend; k0 += GBK) {
     for (int e = tid; e < GBM * GBK; e += 128) {
       int mm, kk;
       if (transA) { kk = e / GBM; mm = e % GBM; } else { mm = e / GBK; kk = e % GBK; }
       const int gm = m0 + mm, gk = k0 + kk;
       bf16 v = zero;
-      if (gm < M && gk < K) v = transA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk];
+      if (gm < M && gk < kend) v = transA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk];
       As[mm][kk] = v;
     }
     for (int e = tid; e < GBN * GBK; e += 128) {
@@ -80,7 +84,7 @@ k_gemm_bf16(int M, int N, int K, const bf16* __restrict__ A, int lda, int transA
       if (transB) { nn = e / GBK; kk = e % GBK; } else { kk = e / GBN; nn = e % GBN; }
       const int gn = n0 + nn, gk = k0 + kk;
       bf16 v = zero;
-      if (gn < N && gk < K) v = transB ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn];
+      if (gn < N && gk < kend) v = transB ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn];
       Bs[nn][kk] = v;
     }
     __syncthreads();
@@ -124,7 +128,36 @@ k_gemm_bf16(int M, int N, int K, const bf16* __restrict__ A, int lda, int transA
 cudaError_t gemm(cudaStream_t s, int M, int N, int K, const bf16* A, int lda, int transA, const bf16* B, int ldb,
                  int transB, float* C, int ldc, const float* bias) {
   dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
-  k_gemm_bf16<<<grid, 128, 0, s>>>(M, N, K, A, lda, transA, B, ldb, transB, C, ldc, bias);
+  k_gemm_bf16<<<grid, 128, 0, s>>>(M, N, K, K, A, lda, transA, B, ldb, transB, C, ldc, bias);
+  return cudaGetLastError();
+}
+
+constexpr int kMaxSplits = 64;
+
+__global__ void k_sum_splits(const float* __restrict__ part, int splits, int64_t mn, float* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < mn; e += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += part[z * mn + e];
+    out[e] = s;
+  }
+}
+
+// C[M][N] (contiguous, no bias) for a long reduction dimension: the K range is
+// split over CTAs into fixed slices of `part` (kMaxSplits * M * N floats) that a
+// second kernel sums in a fixed order, so results do not depend on scheduling.
+cudaError_t gemm_splitk(cudaStream_t s, int M, int N, int K, const bf16* A, int lda, int transA, const bf16* B,
+                        int ldb, int transB, float* C, float* part) {
+  const int tiles = ((N + GBN - 1) / GBN) * ((M + GBM - 1) / GBM);
+  int splits = std::min({(K + 2047) / 2048, kMaxSplits, std::max(1, 2 * 152 / tiles)});
+  splits = std::max(splits, 1);
+  if (splits == 1) return gemm(s, M, N, K, A, lda, transA, B, ldb, transB, C, N, nullptr);
+  int kchunk = (K + splits - 1) / splits;
+  kchunk = (kchunk + GBK - 1) / GBK * GBK;
+  splits = (K + kchunk - 1) / kchunk;
+  dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM, splits);
+  k_gemm_bf16<<<grid, 128, 0, s>>>(M, N, K, kchunk, A, lda, transA, B, ldb, transB, part, N, nullptr);
+  const int64_t mn = (int64_t)M * N;
+  k_sum_splits<<<(int)std::min<int64_t>((mn + 255) / 256, 1024), 256, 0, s>>>(part, splits, mn, C);
   return cudaGetLastError();
 }
 
@@ -438,7 +471,7 @@ struct rb_model_s {
   // activations / scratch for max_batch stamps
   bf16 *xn = nullptr, *cols = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *dzb = nullptr, *dz4 = nullptr;
   float *z1 = nullptr, *z2 = nullptr, *z3 = nullptr, *z4 = nullptr, *logit = nullptr, *dz5 = nullptr,
-        *dcols = nullptr, *da = nullptr;
+        *dcols = nullptr, *da = nullptr, *part = nullptr;
   uint8_t *i1 = nullptr, *i2 = nullptr, *i3 = nullptr;
   size_t cols_elems = 0;
 };
@@ -448,7 +481,7 @@ namespace {
 void free_model(rb_model_s* m) {
   void* ptrs[] = {m->params, m->grads, m->adam_m, m->adam_v, m->wbf, m->xn,  m->cols, m->a1,   m->a2,
                   m->a3,     m->dzb,    m->dz4,    m->z1,  m->z2,  m->z3,   m->z4,   m->logit,
-                  m->dz5,    m->dcols, m->da,     m->i1,     m->i2,  m->i3};
+                  m->dz5,    m->dcols, m->da,     m->part,     m->i1,     m->i2,  m->i3};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -489,27 +522,27 @@ cudaError_t backward(rb_model_s* m, int n, const float* labels, float* loss_dev,
   k_bce_head<<<1, 1024, 0, s>>>(m->logit, labels, n, m->z4, m->params + OW5, m->dz5, m->dz4, loss_dev);
   k_fc2_grad<<<1, F4, 0, s>>>(m->dz5, m->z4, n, G + OW5, G + OB5);
   // fc1: dW4 = a3^T dz4, db4 = colsum(dz4), da3 = dz4 W4^T
-  if ((e = gemm(s, K4, F4, n, m->a3, K4, 1, m->dz4, F4, 0, G + OW4, F4, nullptr))) return e;
+  if ((e = gemm_splitk(s, K4, F4, n, m->a3, K4, 1, m->dz4, F4, 0, G + OW4, m->part))) return e;
   k_colsum<<<F4, 256, 0, s>>>(m->dz4, n, F4, G + OB4);
   if ((e = gemm(s, n, K4, F4, m->dz4, F4, 0, W + OW4, F4, 1, m->da, K4, nullptr))) return e;
   // conv3
   k_pool_relu_back<<<grid1((int64_t)n * PIX3 * C3), 256, 0, s>>>(m->da, m->i3, m->z3, n, 7, 7, C3, m->dzb);
   k_im2col<<<grid1((int64_t)n * PIX3 * K3), 256, 0, s>>>(m->a2, n, 7, 7, C2, K3, m->cols);
-  if ((e = gemm(s, K3, C3, n * PIX3, m->cols, K3, 1, m->dzb, C3, 0, G + OW3, C3, nullptr))) return e;
+  if ((e = gemm_splitk(s, K3, C3, n * PIX3, m->cols, K3, 1, m->dzb, C3, 0, G + OW3, m->part))) return e;
   k_colsum<<<C3, 256, 0, s>>>(m->dzb, (int64_t)n * PIX3, C3, G + OB3);
   if ((e = gemm(s, n * PIX3, K3, C3, m->dzb, C3, 0, W + OW3, C3, 1, m->dcols, K3, nullptr))) return e;
   k_col2im<<<grid1((int64_t)n * PIX3 * C2), 256, 0, s>>>(m->dcols, n, 7, 7, C2, K3, m->da);
   // conv2
   k_pool_relu_back<<<grid1((int64_t)n * PIX2 * C2), 256, 0, s>>>(m->da, m->i2, m->z2, n, 15, 15, C2, m->dzb);
   k_im2col<<<grid1((int64_t)n * PIX2 * K2), 256, 0, s>>>(m->a1, n, 15, 15, C1, K2, m->cols);
-  if ((e = gemm(s, K2, C2, n * PIX2, m->cols, K2, 1, m->dzb, C2, 0, G + OW2, C2, nullptr))) return e;
+  if ((e = gemm_splitk(s, K2, C2, n * PIX2, m->cols, K2, 1, m->dzb, C2, 0, G + OW2, m->part))) return e;
   k_colsum<<<C2, 256, 0, s>>>(m->dzb, (int64_t)n * PIX2, C2, G + OB2);
   if ((e = gemm(s, n * PIX2, K2, C2, m->dzb, C2, 0, W + OW2, C2, 1, m->dcols, K2, nullptr))) return e;
   k_col2im<<<grid1((int64_t)n * PIX2 * C1), 256, 0, s>>>(m->dcols, n, 15, 15, C1, K2, m->da);
   // conv1 (no input gradient)
   k_pool_relu_back<<<grid1((int64_t)n * PIX1 * C1), 256, 0, s>>>(m->da, m->i1, m->z1, n, S31, S31, C1, m->dzb);
   k_im2col<<<grid1((int64_t)n * PIX1 * K1), 256, 0, s>>>(m->xn, n, S31, S31, 3, K1, m->cols);
-  if ((e = gemm(s, K1, C1, n * PIX1, m->cols, K1, 1, m->dzb, C1, 0, G + OW1, C1, nullptr))) return e;
+  if ((e = gemm_splitk(s, K1, C1, n * PIX1, m->cols, K1, 1, m->dzb, C1, 0, G + OW1, m->part))) return e;
   k_colsum<<<C1, 256, 0, s>>>(m->dzb, (int64_t)n * PIX1, C1, G + OB1);
   return cudaGetLastError();
 }
@@ -542,7 +575,7 @@ extern "C" sfft_status_t rb_create(const int32_t* desc, rb_model_t* out) {
             alloc(&m->z3, (size_t)B * PIX3 * C3) && alloc(&m->z4, (size_t)B * F4) && alloc(&m->logit, (size_t)B) &&
             alloc(&m->dz5, (size_t)B) && alloc(&m->dcols, cols) && alloc(&m->da, (size_t)B * PIX2 * C1 + B * K4) &&
             alloc(&m->i1, (size_t)B * PIX2 * C1) && alloc(&m->i2, (size_t)B * PIX3 * C2) &&
-            alloc(&m->i3, (size_t)B * PIX4 * C3);
+            alloc(&m->i3, (size_t)B * PIX4 * C3) && alloc(&m->part, (size_t)kMaxSplits * K4 * F4);
   if (!ok) {
     free_model(m);
     delete m;
