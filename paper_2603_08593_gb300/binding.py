@@ -95,6 +95,13 @@ def _check(st, what):
         raise SfftError(f"{what}: {msg} ({st}) {err}")
 
 
+def _device(device):
+    """A CUDA device with an explicit index (the current device when unspecified)."""
+    import torch
+    d = torch.device(device) if device is not None else torch.device("cuda")
+    return d if d.index is not None else torch.device(d.type, torch.cuda.current_device())
+
+
 def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
@@ -122,7 +129,7 @@ class Plan:
         self._torch = torch
         lib = load()
         self.lib = lib
-        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.device = _device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.desc = Desc(H, W, L, DK, DB, batch, PREC[prec], autotune, d_batch, rows_per_cta,
                          FLAG_GRAPH if graph else 0)
@@ -337,7 +344,7 @@ class Detector:
         import torch
         self.lib = load()
         self.H, self.W, self.batch, self.max_cand = H, W, batch, max_cand
-        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.device = _device(device)
         nb = int(self.lib.rb_detect_workspace_bytes(H, W, batch, max_cand))
         if nb == 0:
             raise SfftError("rb_detect_workspace_bytes: invalid sizes")

@@ -267,7 +267,8 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
   if (d.d_batch > 0) {
     p->d_batch = std::min(d.d_batch, p->n_hd);
   } else {
-    const size_t budget = size_t(4) << 30;
+    // product spectra of up to 24 GB per plan (GB300: 288 GB of HBM3e)
+    const size_t budget = size_t(24) << 30;
     size_t nb = budget / (slab * (size_t)d.batch);
     p->d_batch = (int)std::max<size_t>(1, std::min<size_t>(nb, (size_t)p->n_hd));
   }
@@ -300,7 +301,11 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
     if (st == SFFT_OK) st = upload(&p->twM, a);
     if (st == SFFT_OK) st = upload(&p->twN, b);
     if (st == SFFT_OK) st = upload(&p->twD, c);
-    std::vector<float> ypf(ypow.begin(), ypow.end());
+    // FP32 rows hold each power twice, (yt^0, yt^0, yt^1, yt^1, ...), so that the
+    // contraction loads them as ready-made operand pairs of the packed FP32 FMA
+    std::vector<float> ypf((size_t)d.H * 16, 0.0f);
+    for (int y = 0; y < d.H; ++y)
+      for (int b = 0; b < 5; ++b) ypf[(size_t)y * 16 + 2 * b] = ypf[(size_t)y * 16 + 2 * b + 1] = (float)ypow[(size_t)y * 8 + b];
     if (st == SFFT_OK) st = upload(&p->ytab, ypf);
   }
   if (st == SFFT_OK) st = upload((void**)&p->d_dlist, p->dlist);

@@ -103,7 +103,7 @@ template <typename T, int DM, int KT, int MU>
 struct Stage {
   c_t<T> P[kChunk + MU - 1][KT];
   c_t<T> V[DM + 1][kChunk][KT];
-  T ypw[kChunk][8];        // yt^b of the chunk's rows, b = 0..4 (from the plan's power table)
+  T ypw[kChunk][64 / sizeof(T)];   // yt^b of the chunk's rows, b = 0..4, in the power table's 64 B rows
   int rf[kChunk + 4];      // row flags from the 16-byte aligned row at or below the chunk start
 };
 
@@ -120,7 +120,7 @@ __device__ __forceinline__ void produce_chunk(Stage<T, DM, KT, MU>& st, uint64_t
   const int nv = (ye - yc);
   const int slots = min(KT, M - k0);                       // a tile wider than a tiny row copies less
   const unsigned seg = (unsigned)(slots * sizeof(c_t<T>)); // multiple of 256 bytes
-  const unsigned ybytes = (unsigned)(nv * 8 * sizeof(T));
+  const unsigned ybytes = (unsigned)(nv * 64);
   const unsigned fbytes = (unsigned)((kChunk + 4) * sizeof(int));
   const int ncopy = np + (DM + 1) * nv;
   const int t = threadIdx.x;
@@ -131,7 +131,7 @@ __device__ __forceinline__ void produce_chunk(Stage<T, DM, KT, MU>& st, uint64_t
     const int r2 = t - np, a = r2 / nv, yy = r2 - a * nv;
     bulk_copy_g2s(&st.V[a][yy][0], V + a * HM + (int64_t)(yc + yy) * M + k0, seg, full);
   } else if (t == ncopy) {
-    bulk_copy_g2s(&st.ypw[0][0], ytab + (int64_t)yc * 8, ybytes, full);
+    bulk_copy_g2s(&st.ypw[0][0], ytab + (int64_t)yc * (64 / sizeof(T)), ybytes, full);
   } else if (t == ncopy + 1) {
     bulk_copy_g2s(&st.rf[0], rowflag + (yc & ~3), fbytes, full);
   }
@@ -192,11 +192,6 @@ __device__ __forceinline__ float4 lds4(unsigned addr) {
   asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
   return v;
 }
-__device__ __forceinline__ float lds1(unsigned addr) {
-  float v;
-  asm volatile("ld.shared.f32 %0, [%1+16];" : "=f"(v) : "r"(addr));
-  return v;
-}
 
 template <int NLAG, int KT, int I>
 __device__ __forceinline__ float2 lag_load(unsigned p_lo) {
@@ -213,13 +208,16 @@ __device__ __forceinline__ void group_chunk_f32(c_t<float> (&acc)[MH][5], const 
   unsigned ypa = (unsigned)__cvta_generic_to_shared(&st.ypw[0][0]);
   // staged row of lag lag0 + NLAG - 1 for r = 0
   unsigned plo = (unsigned)__cvta_generic_to_shared(&st.P[nuy - 1 - lag0 - (NLAG - 1)][kk]);
-  for (int r = 0; r < nrow; ++r, vlo += KT * 8, vhi += KT * 8, ypa += 8 * 4, plo += KT * 8) {
+  for (int r = 0; r < nrow; ++r, vlo += KT * 8, vhi += KT * 8, ypa += 64, plo += KT * 8) {
     if (!rf[r]) continue;   // no fit pixel on this row: its weight spectra are zero
     const float2 vl = lds2<0>(vlo);
     float2 vh = vl;
     if constexpr (C::NHI > 0) vh = lds2<0>(vhi);
-    const float4 y4 = lds4(ypa);
-    const float yp[5] = {y4.x, y4.y, y4.z, y4.w, lds1(ypa)};
+    // the powers of yt arrive as duplicated pairs: operands of the packed FMA as loaded
+    const float4 y01 = lds4(ypa), y23 = lds4(ypa + 16);
+    const float2 yp[5] = {make_float2(y01.x, y01.y), make_float2(y01.z, y01.w), make_float2(y23.x, y23.y),
+                          make_float2(y23.z, y23.w), lds2<32>(ypa)};
+    const float2 vlx = make_float2(vl.x, vl.x), vhx = make_float2(vh.x, vh.x);
     float2 pv[NLAG];
 #pragma unroll
     for (int i = 0; i < NLAG; ++i) {
@@ -232,13 +230,18 @@ __device__ __forceinline__ void group_chunk_f32(c_t<float> (&acc)[MH][5], const 
     }
 #pragma unroll
     for (int i = 0; i < NLAG; ++i) {
-      const float xr = vl.x * pv[i].x + vl.y * pv[i].y, xi = vl.x * pv[i].y - vl.y * pv[i].x;
+      // conj(V) P = (vx px + vy py, vx py - vy px): one packed product and two FMAs
+      float2 x = __fmul2_rn(vlx, pv[i]);
+      x.x = fmaf(vl.y, pv[i].y, x.x);
+      x.y = fmaf(-vl.y, pv[i].x, x.y);
 #pragma unroll
-      for (int s = 0; s < C::NLO; ++s) { acc[i][s].x += yp[s] * xr; acc[i][s].y += yp[s] * xi; }
+      for (int s = 0; s < C::NLO; ++s) acc[i][s] = __ffma2_rn(yp[s], x, acc[i][s]);
       if constexpr (C::NHI > 0) {
-        const float hr = vh.x * pv[i].x + vh.y * pv[i].y, hi = vh.x * pv[i].y - vh.y * pv[i].x;
+        float2 h = __fmul2_rn(vhx, pv[i]);
+        h.x = fmaf(vh.y, pv[i].y, h.x);
+        h.y = fmaf(-vh.y, pv[i].x, h.y);
 #pragma unroll
-        for (int s = 0; s < C::NHI; ++s) { acc[i][C::NLO + s].x += yp[s] * hr; acc[i][C::NLO + s].y += yp[s] * hi; }
+        for (int s = 0; s < C::NHI; ++s) acc[i][C::NLO + s] = __ffma2_rn(yp[s], h, acc[i][C::NLO + s]);
       }
     }
   }
@@ -317,7 +320,7 @@ k_contract(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, int M, i
   St* stages = reinterpret_cast<St*>(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + 2 * sizeof(St));    // [2]
   T* red = reinterpret_cast<T*>(smem_raw + 2 * sizeof(St) + 32);              // [L][L][n_mono(DM)]
-  const CJob job = jobs[blockIdx.z];
+  const CJob job = jobs[blockIdx.y];
   const int nred = L * L * NMONO;
   for (int i = threadIdx.x; i < nred; i += blockDim.x) red[i] = (T)0;
   if (threadIdx.x == 0) {
@@ -331,7 +334,7 @@ k_contract(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, int M, i
   const int kk = threadIdx.x % KT, gh = threadIdx.x / KT;     // gh = group * kHalves + half (warp-uniform)
   const int g = gh / kHalves, half = gh % kHalves;
   const int k0 = blockIdx.x * KT, k = k0 + kk;
-  int y0 = blockIdx.y * rows_per_cta, y1 = y0 + rows_per_cta;
+  int y0 = blockIdx.z * rows_per_cta, y1 = y0 + rows_per_cta;
   if (y0 < w) y0 = w;
   if (y1 > H - w) y1 = H - w;
   const int64_t HM = (int64_t)H * M;
@@ -466,13 +469,18 @@ static cudaError_t contract_T(const sfft_plan_s* p, int job0, int njobs, int row
   auto kern = k_contract<T, DM, KT>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int nb = (H + rows_per_cta - 1) / rows_per_cta;
-  dim3 grid((p->M + KT - 1) / KT, nb, njobs);
-  kern<<<grid, cta_threads<T, DM, KT>(), smem, p->stream>>>(p->d_jobs + job0, (char*)ws, H, p->M, p->Nf,
-                                                                      L, rows_per_cta, (const c_t<T>*)p->twD,
-                                                                      (const T*)p->ytab);
+  // row bands vary slowest: the CTAs in flight share one band of the weight
+  // spectra (read by every job), which then stays in L2 across the jobs
+  for (int j0 = 0; j0 < njobs; j0 += 65535) {   // grid.y limit
+    dim3 grid((p->M + KT - 1) / KT, std::min(65535, njobs - j0), nb);
+    kern<<<grid, cta_threads<T, DM, KT>(), smem, p->stream>>>(p->d_jobs + job0 + j0, (char*)ws, H, p->M, p->Nf,
+                                                                        L, rows_per_cta, (const c_t<T>*)p->twD,
+                                                                        (const T*)p->ytab);
+    p->nlaunch += 1;
+  }
   k_contract_slot0<T, DM><<<dim3(njobs, max_uy<T>()), 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, H, p->M,
                                                                           p->Nf, L);
-  p->nlaunch += 2;
+  p->nlaunch += 1;
   return cudaGetLastError();
 }
 

@@ -43,7 +43,8 @@ struct sfft_plan_s {
   void* twM = nullptr;                // c_t [M]       exp(-2 pi i j / M)
   void* twN = nullptr;                // c_t [M]       exp(-2 pi i k / Nf)
   void* twD = nullptr;                // c_t [Nf]      (cos, sin)(2 pi j / Nf)
-  void* ytab = nullptr;               // T [H][8]      yt(y)^b, b = 0..4 (zero padded)
+  void* ytab = nullptr;               // 64 B per row: yt(y)^b, b = 0..4, as double [8] (FP64 path) or as
+                                      // duplicated pairs float [16] (FP32 path); zero padded
   int rf_stride = 0;                  // ints per CCD in the row-flag array (padded, multiple of 64)
   int2* d_dlist = nullptr;            // device copy of dlist
   int* d_hdidx = nullptr;             // [(2L-1)][(2L-1)] -> half-plane index or -1
