@@ -74,8 +74,11 @@ sfft_status_t rb_train_step(rb_model_t m, const float* stamps, const float* labe
  * over the good finite pixels at least 15 px from every edge after three
  * 3-sigma clipping passes (|D - mean| <= 3 RMS of the previous pass), divided
  * by sqrt(0.97334), the share of a Gaussian's variance inside +-3 sigma.
- * Candidates are pixels at least 15 px from every edge, not bad, with
- * SNR >= thresh and SNR >= every SNR in their 5 x 5 neighbourhood.  Per CCD,
+ * Candidates are pixels at least 15 px from every edge, with no bad pixel
+ * within Chebyshev distance `guard` (0 <= guard <= 15; 0: the pixel itself is
+ * not bad; a subtraction's kernel half-width keeps out pixels whose D drew on
+ * masked reference pixels), with SNR >= thresh and SNR >= every SNR in their
+ * 5 x 5 neighbourhood.  Per CCD,
  * up to max_cand candidates are written in row-major order: xy int32
  * [batch][max_cand][2] (x, y), snr float [batch][max_cand], count int32
  * [batch] (the number found, which may exceed max_cand), and stamps float
@@ -86,8 +89,8 @@ sfft_status_t rb_train_step(rb_model_t m, const float* stamps, const float* labe
  * rb_detect_workspace_bytes(H, W, batch, max_cand), 256-byte aligned. */
 size_t rb_detect_workspace_bytes(int32_t H, int32_t W, int32_t batch, int32_t max_cand);
 sfft_status_t rb_detect(int32_t H, int32_t W, int32_t batch, const float* D, const float* S, const float* R,
-                        const uint8_t* bad, float psf_sigma, float thresh, int32_t max_cand, int32_t* xy,
-                        float* snr, int32_t* count, float* stamps, void* ws, void* stream);
+                        const uint8_t* bad, float psf_sigma, float thresh, int32_t guard, int32_t max_cand,
+                        int32_t* xy, float* snr, int32_t* count, float* stamps, void* ws, void* stream);
 
 /* Plain SNR/shape cuts on difference stamps (the classifier's fallback):
  * pass[i] = 1 iff snr[i] >= snr_min, the second-moment FWHM of the positive

@@ -14,8 +14,10 @@ used here is a PSF matched filter:
               kept inside +-3 sigma)
   G(u)      = g(u_x) g(u_y), g(t) = exp(-t^2 / (2 s^2)), |u_x|, |u_y| <= r = ceil(3 s)
   SNR(x)    = sum_u G(u) D^(x - u) / (sigma_D ||G||_2)
-  candidate : >= 15 px from every edge, good, SNR >= thresh, SNR >= every SNR
-              in its 5 x 5 neighbourhood; reported in row-major order
+  candidate : >= 15 px from every edge, no bad pixel within Chebyshev
+              distance `guard` (guard 0: the pixel itself is good), SNR >=
+              thresh, SNR >= every SNR in its 5 x 5 neighbourhood; reported in
+              row-major order
   stamp     : 31 x 31 cut of (S, R, D) centred on the candidate, non-finite -> 0
 
 The matched-filter normalisation makes SNR unit-variance on white noise of
@@ -27,6 +29,7 @@ from __future__ import annotations
 import math
 
 import numpy as np
+from scipy import ndimage
 
 MARGIN = 15
 HALF = 15          # stamp half-size (31 x 31)
@@ -94,10 +97,20 @@ def matched_snr(D, bad, psf_sigma, sigma_D):
     return out / (sigma_D * norm)
 
 
-def candidates(snr, bad, thresh):
+def guard_mask(bad, guard):
+    """Pixels with a bad pixel within Chebyshev distance `guard` (max filter)."""
+    if bad is None:
+        return None
+    b = np.asarray(bad) != 0
+    if guard <= 0:
+        return b.astype(np.uint8)
+    return ndimage.maximum_filter(b.astype(np.uint8), size=2 * guard + 1, mode="constant", cval=0)
+
+
+def candidates(snr, bad, thresh, guard=0):
     """Row-major (y, x) of the local maxima at or above thresh."""
     H, W = snr.shape
-    ok = interior_mask(H, W, bad)
+    ok = interior_mask(H, W, guard_mask(bad, guard))
     ok &= np.isfinite(snr) & (snr >= thresh)
     P = np.full((H + 2 * NMS, W + 2 * NMS), -np.inf)
     P[NMS:NMS + H, NMS:NMS + W] = np.where(np.isfinite(snr), snr, -np.inf)
@@ -117,12 +130,12 @@ def cut_stamps(S, R, D, ys, xs):
     return out
 
 
-def detect(D, S, R, bad, psf_sigma, thresh, max_cand=None):
+def detect(D, S, R, bad, psf_sigma, thresh, max_cand=None, guard=0):
     """Full detection of one CCD: dict(sigma_D, snr_map, y, x, snr, stamps);
     the lists are truncated to max_cand (count is the untruncated number)."""
     mu, sigma_D = clipped_sigma(D, bad)
     snr = matched_snr(D, bad, psf_sigma, sigma_D)
-    ys, xs = candidates(snr, bad, thresh)
+    ys, xs = candidates(snr, bad, thresh, guard)
     count = len(ys)
     if max_cand is not None:
         ys, xs = ys[:max_cand], xs[:max_cand]

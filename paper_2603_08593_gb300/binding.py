@@ -57,7 +57,7 @@ SIGNATURES = {
     "rb_backward": (I32, [VP, VP, VP, I64, VP, VP]),
     "rb_train_step": (I32, [VP, VP, VP, I64, C.c_float, VP, VP]),
     "rb_detect_workspace_bytes": (SZ, [I32, I32, I32, I32]),
-    "rb_detect": (I32, [I32, I32, I32, VP, VP, VP, VP, C.c_float, C.c_float, I32, VP, VP, VP, VP, VP, VP]),
+    "rb_detect": (I32, [I32, I32, I32, VP, VP, VP, VP, C.c_float, C.c_float, I32, I32, VP, VP, VP, VP, VP, VP]),
     "rb_shape_cuts": (I32, [VP, VP, I64, C.c_float, C.c_float, VP, VP]),
 }
 
@@ -357,7 +357,7 @@ class Detector:
         self.stamps = torch.empty(batch, max_cand, 3, RB_STAMP, RB_STAMP, dtype=torch.float32, device=self.device)
         self.snr_map = self.ws_view[:batch * H * W * 4].view(torch.float32).view(batch, H, W)
 
-    def __call__(self, D, S, R, bad=None, psf_sigma=1.0, thresh=5.0, stream=None):
+    def __call__(self, D, S, R, bad=None, psf_sigma=1.0, thresh=5.0, guard=0, stream=None):
         import torch
         for t, name in ((D, "D"), (S, "S"), (R, "R")):
             _need(t, torch.float32, name)
@@ -366,7 +366,7 @@ class Detector:
         if bad is not None:
             _need(bad, torch.uint8, "bad")
         st = self.lib.rb_detect(self.H, self.W, self.batch, _ptr(D), _ptr(S), _ptr(R), _ptr(bad), float(psf_sigma),
-                                float(thresh), self.max_cand, _ptr(self.xy), _ptr(self.snr), _ptr(self.count),
+                                float(thresh), int(guard), self.max_cand, _ptr(self.xy), _ptr(self.snr), _ptr(self.count),
                                 _ptr(self.stamps), _ptr(self.ws_view), _stream(D, stream))
         _check(st, "rb_detect")
         return self.xy, self.snr, self.count, self.stamps

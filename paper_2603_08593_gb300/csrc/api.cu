@@ -264,15 +264,23 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
       }
   p->n_hd = (int)p->dlist.size();
   const size_t slab = (size_t)d.H * p->M * 2 * p->elem;
-  if (d.d_batch > 0) {
-    p->d_batch = std::min(d.d_batch, p->n_hd);
-  } else {
-    // product spectra of up to 24 GB per plan (GB300: 288 GB of HBM3e)
-    const size_t budget = size_t(24) << 30;
-    size_t nb = budget / (slab * (size_t)d.batch);
-    p->d_batch = (int)std::max<size_t>(1, std::min<size_t>(nb, (size_t)p->n_hd));
+  // product spectra of up to 24 GB per plan (GB300: 288 GB of HBM3e)
+  const size_t budget = size_t(24) << 30;
+  const int d_batch_max =
+      (int)std::max<size_t>(1, std::min<size_t>(budget / (slab * (size_t)d.batch), (size_t)p->n_hd));
+  int tuned_db = 0, tuned_rows = 0;
+  if (d.autotune && (d.d_batch == 0 || d.rows_per_cta == 0)) {
+    const sfft_status_t ts =
+        autotune_tiles(d, (cudaStream_t)cuda_stream, d_batch_max, &tuned_db, &tuned_rows, &p->tuned_ms);
+    if (ts != SFFT_OK) {
+      delete p;
+      return ts;
+    }
   }
-  p->rows_per_cta = d.rows_per_cta > 0 ? d.rows_per_cta : std::min(d.H, 1024);
+  if (d.d_batch > 0) p->d_batch = std::min(d.d_batch, p->n_hd);
+  else p->d_batch = tuned_db > 0 ? std::min(tuned_db, p->n_hd) : d_batch_max;
+  if (d.rows_per_cta > 0) p->rows_per_cta = d.rows_per_cta;
+  else p->rows_per_cta = tuned_rows > 0 ? tuned_rows : std::min(d.H, 1024);
   p->ktile = p->M >= 128 ? 128 : 64;
   // row flags are bulk-copied in 16-byte aligned runs of up to 20 ints past a chunk start
   p->rf_stride = ((d.H + 32) + 63) / 64 * 64;

@@ -38,6 +38,7 @@ struct sfft_plan_s {
   int n_hd = 0;                       // half-plane differences
   std::vector<int2> dlist;            // (dy, dx) per half-plane difference
   int d_batch = 0, rows_per_cta = 0, ktile = 128;
+  double tuned_ms = 0.0;              // autotuned build_normal time per CCD (0: not tuned)
   size_t elem = 4;                    // sizeof(T)
   // plan-owned constant device tables
   void* twM = nullptr;                // c_t [M]       exp(-2 pi i j / M)
@@ -98,6 +99,9 @@ cudaError_t launch_theta_units_raw(cudaStream_t s, const double* src, double* ds
 cudaError_t launch_apply_raw(cudaStream_t s, bool fp64, const float* R, const float* S, const double* theta_off,
                              const double* sky, float* D, int H, int W, int L, int DK, int DB, int batch);
 void set_last_error(const char* msg);
+// Times candidate (d_batch, rows_per_cta) on synthetic data (autotune.cu).
+sfft_status_t autotune_tiles(const sfft_desc_t& d, cudaStream_t s, int d_batch_max, int* d_batch, int* rows_per_cta,
+                             double* ms_per_ccd);
 
 template <typename T> inline T* ws_at(void* ws, const Region& r) {
   return reinterpret_cast<T*>(static_cast<char*>(ws) + r.off);

@@ -10,6 +10,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 
 #include "common.cuh"
@@ -30,12 +31,13 @@ struct Taps {
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct DetectLayout {
-  size_t snr, tmp, part, rowcnt, rowoff, total;
+  size_t snr, tmp, guard, part, rowcnt, rowoff, total;
   DetectLayout(int H, int W, int B) {
     const size_t img = (size_t)B * H * W * sizeof(float);
     snr = 0;
     tmp = snr + align256(img);
-    part = tmp + align256(img);
+    guard = tmp + align256(img);
+    part = guard + align256((size_t)B * H * W);
     rowcnt = part + align256((size_t)B * kStatPasses * (kStatBlocks * 3 + 1) * sizeof(double));
     rowoff = rowcnt + align256((size_t)B * H * sizeof(int));
     total = rowoff + align256((size_t)B * H * sizeof(int));
@@ -177,6 +179,30 @@ k_filter_cols(int H, int W, const float* __restrict__ T, Taps taps, const double
     float s = 0.f;
     for (int k = 0; k <= 2 * r; ++k) s = fmaf(g[k], tile[j + k][tx], s);
     snr[b * img + (int64_t)y * W + x] = s * scale;
+  }
+}
+
+// bad-pixel guard band, separable: rows then columns (Chebyshev distance <= g)
+__global__ void __launch_bounds__(256)
+k_dilate_rows(int H, int W, const uint8_t* __restrict__ bad, int g, uint8_t* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)H * W; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t base = (int64_t)blockIdx.y * H * W;
+    const int x = (int)(e % W);
+    const int64_t row = base + e - x;
+    uint8_t v = 0;
+    for (int dx = max(0, x - g); dx <= min(W - 1, x + g); ++dx) v |= bad[row + dx];
+    out[base + e] = v ? 1 : 0;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_dilate_cols(int H, int W, const uint8_t* __restrict__ in, int g, uint8_t* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)H * W; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t base = (int64_t)blockIdx.y * H * W;
+    const int x = (int)(e % W), y = (int)(e / W);
+    uint8_t v = 0;
+    for (int dy = max(0, y - g); dy <= min(H - 1, y + g); ++dy) v |= in[base + (int64_t)dy * W + x];
+    out[base + e] = v;
   }
 }
 
@@ -359,10 +385,11 @@ extern "C" size_t rb_detect_workspace_bytes(int32_t H, int32_t W, int32_t batch,
 
 extern "C" sfft_status_t rb_detect(int32_t H, int32_t W, int32_t batch, const float* D, const float* S,
                                    const float* R, const uint8_t* bad, float psf_sigma, float thresh,
-                                   int32_t max_cand, int32_t* xy, float* snr, int32_t* count, float* stamps, void* ws,
+                                   int32_t guard, int32_t max_cand, int32_t* xy, float* snr, int32_t* count, float* stamps, void* ws,
                                    void* stream) {
   if (H < 2 * kHalf + 1 || W < 2 * kHalf + 1 || batch < 1 || max_cand < 0 || !D || !S || !R || !count || !ws ||
-      (max_cand > 0 && (!xy || !snr || !stamps)) || !(psf_sigma > 0.f) || !(psf_sigma <= 5.f) ||
+      (max_cand > 0 && (!xy || !snr || !stamps)) || !(psf_sigma > 0.f) || !(psf_sigma <= 5.f) || guard < 0 ||
+      guard > kMargin ||
       (reinterpret_cast<uintptr_t>(ws) & 255))
     return SFFT_ERR_ARG;
   if (batch > 65535 || sizeof(float) * (W + 2 * kMaxR) > 48 * 1024) return SFFT_ERR_UNSUPPORTED;
@@ -386,10 +413,19 @@ extern "C" sfft_status_t rb_detect(int32_t H, int32_t W, int32_t batch, const fl
   k_filter_rows<<<dim3(std::min(H, 1024), batch), 256, row_smem, s>>>(H, W, D, bad, taps, tmp);
   k_filter_cols<<<dim3((W + 31) / 32, (H + kColTile - 1) / kColTile, batch), 256, 0, s>>>(H, W, tmp, taps, part,
                                                                                              snr_map);
-  k_cand_count<<<dim3(H, batch), 256, 0, s>>>(H, W, snr_map, bad, thresh, rowcnt);
+  const uint8_t* cbad = bad;   // the mask the candidate test reads
+  if (bad && guard > 0) {
+    uint8_t* rows = reinterpret_cast<uint8_t*>(base + L.tmp);    // the row-filtered image is consumed by now
+    uint8_t* gm = reinterpret_cast<uint8_t*>(base + L.guard);
+    const int gx = (int)std::min<int64_t>(((int64_t)H * W + 255) / 256, 2048);
+    k_dilate_rows<<<dim3(gx, batch), 256, 0, s>>>(H, W, bad, guard, rows);
+    k_dilate_cols<<<dim3(gx, batch), 256, 0, s>>>(H, W, rows, guard, gm);
+    cbad = gm;
+  }
+  k_cand_count<<<dim3(H, batch), 256, 0, s>>>(H, W, snr_map, cbad, thresh, rowcnt);
   k_cand_scan<<<batch, 1024, 0, s>>>(H, rowcnt, rowoff, count);
   if (max_cand > 0) {
-    k_cand_write<<<dim3(H, batch), 256, 0, s>>>(H, W, snr_map, bad, thresh, rowcnt, rowoff, max_cand, xy, snr);
+    k_cand_write<<<dim3(H, batch), 256, 0, s>>>(H, W, snr_map, cbad, thresh, rowcnt, rowoff, max_cand, xy, snr);
     k_stamps<<<dim3(max_cand, batch), 256, 0, s>>>(H, W, S, R, D, count, xy, max_cand, stamps);
   }
   const cudaError_t e = cudaGetLastError();

@@ -8,8 +8,10 @@ injection truth: training pairs (512 x 512) carry point transients at SNR
 3-100 and unmasked artifacts in the science frame (cosmic-ray hits, bad-column
 segments, stars misregistered by 0.3-1 px); every candidate the detector
 finds within 2 px of an injected transient is real, every other candidate is
-bogus.  The network is trained on the GPU by rb_train_step (BF16 tensor-core
-forward/backward, FP32 Adam) on a class-balanced 80/5/15 split, and then
+bogus.  Candidates stay a kernel half-width away from masked pixels, whose
+neighbourhood in D draws on masked reference pixels.  The network is trained
+on the GPU by rb_train_step (BF16 tensor-core forward/backward, FP32 Adam) on
+a class-balanced 80/5/15 split, and then
 judged on the candidates of one 60-CCD exposure of 2048 x 4096 pairs against
 the plain SNR/shape cuts (rb_shape_cuts).
 
@@ -32,6 +34,7 @@ import numpy as np
 
 L, DK, DB = 11, 2, 2
 MATCH_PX = 2.0
+GUARD = (L - 1) // 2    # candidates keep the kernel half-width away from masked pixels
 
 
 # ---------------------------------------------------------------- inputs (host, spawned pool)
@@ -51,7 +54,7 @@ def train_pair(seed):
     d = make_pair(512, 512, seed=seed, n_src=300, fwhm_R=(r_lo, r_hi), fwhm_S=(s_lo, s_hi),
                   grad_angle=float(rng.uniform(0, 2 * math.pi)), shift=(0.1, 0.0), n_transients=40,
                   snr=(3.0, 100.0), transient_sep=16.0, transient_margin=20, n_cosmics=25, n_colsegs=2,
-                  n_misreg=40, misreg_shift=(0.3, 1.0))
+                  n_misreg=40, misreg_shift=(0.3, 1.0), mask_fraction=float(rng.uniform(0.0, 0.15)))
     return _truth(d, 512, 512)
 
 
@@ -90,7 +93,7 @@ def candidates(pairs, chunk=16, max_cand=512, thresh=5.0, device="cuda"):
         out = plan.subtract(R, S, bad, None, refine=1)
         for i, p in enumerate(part):
             xyi, snri, cnt, st = det(out["D"][i:i + 1], S[i:i + 1], R[i:i + 1], bad[i:i + 1],
-                                     psf_sigma=p["psf_sigma"], thresh=thresh)
+                                     psf_sigma=p["psf_sigma"], thresh=thresh, guard=GUARD)
             n = min(int(cnt[0].item()), max_cand)
             stamps.append(st[0, :n].clone())
             snr.append(snri[0, :n].cpu().numpy())

@@ -159,6 +159,7 @@ def test_gradients_match_oracle():
     for k in C.ORDER:
         a, b = g[k].ravel().astype(np.float64), go[k].ravel()
         cos = float(a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30))
+        print(f"gradient {k}: cosine {cos:.6f}, relative L2 {_rel(a, b):.3e}")
         assert cos >= 0.99 and _rel(a, b) <= 0.1, (k, cos, _rel(a, b))
 
 
@@ -220,20 +221,21 @@ def _margins(snr, y, x, thresh):
     return min(abs(v - thresh), abs(v - np.nanmax(nb)))
 
 
-@pytest.mark.parametrize("H,W,batch,use_bad", [(64, 80, 1, True), (157, 203, 2, True), (300, 129, 3, False)])
-def test_detect_matches_oracle(H, W, batch, use_bad):
+@pytest.mark.parametrize("H,W,batch,use_bad,guard", [(64, 80, 1, True, 0), (157, 203, 2, True, 5),
+                                                     (300, 129, 3, False, 3)])
+def test_detect_matches_oracle(H, W, batch, use_bad, guard):
     from paper_2603_08593_gb300 import Detector
     imgs = [_det_image(H, W, 40 + b) for b in range(batch)]
     D = np.stack([i[0] for i in imgs]); S = np.stack([i[1] for i in imgs]); R = np.stack([i[2] for i in imgs])
     bad = np.stack([i[3] for i in imgs])
     det = Detector(H, W, batch=batch, max_cand=64)
     xy, snr, count, stamps = det(_dev(D), _dev(S), _dev(R), _dev(bad, torch.uint8) if use_bad else None,
-                                 psf_sigma=1.4, thresh=5.0)
+                                 psf_sigma=1.4, thresh=5.0, guard=guard)
     torch.cuda.synchronize()
     smap = det.snr_map.cpu().numpy()
     xy, snr, count, stamps = xy.cpu().numpy(), snr.cpu().numpy(), count.cpu().numpy(), stamps.cpu().numpy()
     for b in range(batch):
-        o = DO.detect(D[b], S[b], R[b], bad[b] if use_bad else None, 1.4, 5.0, max_cand=64)
+        o = DO.detect(D[b], S[b], R[b], bad[b] if use_bad else None, 1.4, 5.0, max_cand=64, guard=guard)
         ref = o["snr_map"]
         assert np.max(np.abs(smap[b] - ref)) <= 1e-5 * np.max(np.abs(ref)) + 1e-5
         got = set(map(tuple, xy[b, :min(count[b], 64)][:, ::-1].tolist()))

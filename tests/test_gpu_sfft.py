@@ -140,3 +140,30 @@ def test_nonfinite_pixels_are_masked_and_singular_is_reported():
     torch.cuda.synchronize()
     info = o["info"].cpu().numpy()
     assert info[0] == 4 and info[1] == 0
+
+
+def test_autotuned_plan_matches_default_and_is_cached(tmp_path, monkeypatch):
+    """The autotuner only picks (d_batch, rows_per_cta): A and theta match a
+    plan with fixed tiles, the choice lies in the candidate set, and a second
+    plan of the same shape reuses the cached choice (one cache line)."""
+    from paper_2603_08593_gb300 import Plan
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("SFFT_AUTOTUNE_CACHE", str(cache))
+    L, DK, DB = 5, 1, 1
+    d = small_pair(300, 200, seed=5001, mask_fraction=0.02)
+    H, W = d["R"].shape
+    R, S, bad = _dev(d["R"][None]), _dev(d["S"][None]), _dev(d["bad"][None])
+    pt = Plan(H, W, L, DK, DB, batch=1, prec="mixed", autotune=1)
+    pd = Plan(H, W, L, DK, DB, batch=1, prec="mixed", d_batch=7, rows_per_cta=128)
+    assert pt.tiles[1] in (256, H) and 1 <= pt.tiles[0] <= (2 * L - 1) * L
+    ot = pt.subtract(R, S, bad, None, refine=1)
+    od = pd.subtract(R, S, bad, None, refine=1)
+    torch.cuda.synchronize()
+    # FP32 band partial sums differ with the band height: mixed-path tolerances
+    assert torch.allclose(ot["A"], od["A"], rtol=0, atol=2e-5 * float(od["A"].abs().max()))
+    th_t, th_d = ot["theta"][0].cpu().numpy(), od["theta"][0].cpu().numpy()
+    assert O.kernel_coef_rel_err(th_t, th_d, L, DK, DB) <= 1e-5
+    pt2 = Plan(H, W, L, DK, DB, batch=1, prec="mixed", autotune=1)
+    assert pt2.tiles == pt.tiles
+    lines = cache.read_text().strip().splitlines()
+    assert len([ln for ln in lines if "_H300_W200_L5_" in ln]) == 1

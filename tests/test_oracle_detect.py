@@ -106,3 +106,25 @@ def test_detect_rules():
     # truncation keeps the first max_cand in row-major order and the full count
     t = O.detect(D, S, R, bad, s, 5.0, max_cand=2)
     assert t["count"] == len(got) and list(zip(t["y"], t["x"])) == got[:2]
+
+
+def test_guard_band_against_bad_pixels():
+    H, W = 80, 90
+    D = RNG.normal(0, 1.0, (H, W))
+    _blob(D, 40, 40, 60.0, 1.5)
+    _blob(D, 40, 70, 60.0, 1.5)
+    bad = np.zeros((H, W), np.uint8)
+    bad[43, 44] = 1                             # Chebyshev distance 4 from (40, 40)
+    bad[40, 64] = 1                             # distance 6 from (40, 70)
+    g0 = list(zip(*O.candidates(O.matched_snr(D, bad, 1.5, 1.0), bad, 5.0, 0)))
+    g5 = list(zip(*O.candidates(O.matched_snr(D, bad, 1.5, 1.0), bad, 5.0, 5)))
+    assert (40, 40) in g0 and (40, 70) in g0
+    assert (40, 40) not in g5 and (40, 70) in g5
+    # the guard mask is the brute-force Chebyshev neighbourhood
+    m = O.guard_mask(bad, 5)
+    ys, xs = np.nonzero(bad)
+    yy, xx = np.mgrid[0:H, 0:W]
+    brute = np.zeros((H, W), bool)
+    for y, x in zip(ys, xs):
+        brute |= (np.abs(yy - y) <= 5) & (np.abs(xx - x) <= 5)
+    assert np.array_equal(m.astype(bool), brute)
