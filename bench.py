@@ -35,11 +35,12 @@ L2_FLUSH_BYTES = 256 << 20
 WORKLOAD = ("one DECam CCD pair per GPU per step: 2048x4096 FP32, 20k stars, PSF FWHM 1.0-1.4 (R) / "
             "1.5-2.1 (S) px across the chip, saturation mask with 3 px dilation, two bad columns, "
             "50 transients; L=11, D_K=D_B=2, mixed precision, 1 refinement step")
-# DRAM bytes (read + write) of one full-size KK contraction launch, scaled from an
-# ncu capture of the same kernel on a 512-row strip (profiles/k_contract_*.md);
-# reported only while the kernel source is the one that was measured.
-KK_TRAFFIC_BYTES = 4.41e9 + 0.09e9
-KK_TRAFFIC_SOURCE_SHA256_16 = "f16859dc5ad5cc81"
+# DRAM bytes (read + write) of one full-size KK contraction launch (all 221
+# differences), from a one-pass ncu capture of the benchmark workload
+# (profiles/dram_per_kernel_*.md); reported only while the kernel source is the
+# one that was measured.
+KK_TRAFFIC_BYTES = 10.05e9
+KK_TRAFFIC_SOURCE_SHA256_16 = "ac58c028e66f4353"
 PHASES = ("prep", "fft_weights", "fft_prod", "contract_kk", "contract_rk", "scatter", "solve", "apply")
 
 
@@ -359,10 +360,10 @@ def run_gpu(args):
         peak = fp32_alu_peak_tflops(clock)
         roof = {"bound": "alu", "kernel": "k_contract (product-spectrum lag contraction)", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": args.traffic if args.traffic is not None else (kk_traffic_bytes() if Hs == H else None),
+                "traffic": args.traffic if args.traffic is not None else (kk_traffic_bytes() if (Hs == H and B == 1 and tiles[0] == 221) else None),
                 "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz max SM clock (derived, not measured)",
                 "avg_launch_ms": avg_ms, "launches_per_step": n_launch / args.steps,
-                "traffic_note": "DRAM read+write bytes per launch, ncu on a 512-row strip scaled by rows x differences"}
+                "traffic_note": "DRAM read+write bytes per launch, one-pass ncu capture of this workload"}
         if batched:
             roof["timing_note"] = "kernel durations from an eager profiled pass of the same plan (timed steps replay a CUDA graph)"
     if batched:

@@ -196,6 +196,106 @@ k_rfft_prod_dy(const T* __restrict__ Rm, int H, int W, int L, int d0, int nd, c_
   }
 }
 
+// FP32 products for 2048-sample rows (M = 1024), one warp per product row.
+// Four-step transform of the packed row z[n], n = l + 32 q (lane l holds the
+// 32 samples q): a 32-point DFT over q in registers, the twiddle
+// exp(-2 pi i l a / 1024), a transpose through the warp's own shared-memory
+// tile, and a 32-point DFT over l, after which lane a holds X[a + 32 b].  The
+// real-input split reads X[M - k] back from the same tile.  Only warp-level
+// synchronisation is needed between the staged source rows and the output.
+// Each CTA walks `rows` image rows of one d_y group; its 8 warps take the
+// d_x values of the group in turns.
+constexpr int kWarpRowsPerCta = 4;
+
+__global__ void __launch_bounds__(256, 2)
+k_rfft_prod_dy_w(const float* __restrict__ Rm, int H, int W, int L, int d0, int nd, float2* __restrict__ out,
+                 int64_t slab_stride, int64_t ccd_stride_out, const float2* __restrict__ twM,
+                 const float2* __restrict__ twN) {
+  constexpr int M = 1024, NF = 2048, PADX = 16, SROW = 33;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* r1 = reinterpret_cast<float*>(smem_raw);            // [NF]
+  float* r2 = r1 + NF;                                         // [NF + 2 PADX]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float2* tile = reinterpret_cast<float2*>(r2 + NF + 2 * PADX) + warp * 32 * SROW;
+  // per-lane twiddles: exp(-2 pi i l a / M) = tB[a mod 8] tA[a / 8]; exp(-2 pi i l / NF)
+  float2 tB[8], tA[4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) tB[i] = twM[(lane * i) & (M - 1)];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) tA[j] = twM[(8 * lane * j) & (M - 1)];
+  const float2 tn = twN[lane];
+  const int ccd = blockIdx.z;
+  auto first_of = [L](int dy) { return dy == 0 ? 0 : L + (2 * L - 1) * (dy - 1); };
+  auto dy_of = [L](int id) { return id < L ? 0 : 1 + (id - L) / (2 * L - 1); };
+  const int dy = dy_of(d0) + blockIdx.y;
+  const int lo = max(d0, first_of(dy)), hi = min(d0 + nd, first_of(dy) + (dy == 0 ? L : 2 * L - 1));
+  if (lo >= hi) return;   // uniform over the CTA
+  const int dx0 = dy == 0 ? 0 : -(L - 1);
+  const float* img = Rm + (int64_t)ccd * H * W;
+  for (int yy = 0; yy < kWarpRowsPerCta; ++yy) {
+    const int y = blockIdx.x * kWarpRowsPerCta + yy;
+    if (y >= H) break;   // uniform
+    __syncthreads();     // the previous row's products are formed
+    const bool ok2 = y + dy < H;
+    for (int x = threadIdx.x; x < NF; x += blockDim.x) r1[x] = x < W ? img[(int64_t)y * W + x] : 0.f;
+    for (int x = threadIdx.x; x < NF + 2 * PADX; x += blockDim.x) {
+      const int gx = x - PADX;
+      r2[x] = (ok2 && gx >= 0 && gx < W) ? img[(int64_t)(y + dy) * W + gx] : 0.f;
+    }
+    __syncthreads();
+    float2* orow = out + (int64_t)ccd * ccd_stride_out + (int64_t)y * M;
+    for (int id = lo + warp; id < hi; id += 8) {
+      const int dx = dx0 + (id - first_of(dy));
+      float2 v[32];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int x0 = 2 * (lane + 32 * q);
+        const float2 a = *reinterpret_cast<const float2*>(r1 + x0);
+        // products vanish where R_m(y + d_y, x + d_x) falls outside the image (r2 is zero there)
+        v[q].x = a.x * r2[x0 + dx + PADX];
+        v[q].y = a.y * r2[x0 + 1 + dx + PADX];
+      }
+      fft_reg<32>(v);   // over q: v[a]
+#pragma unroll
+      for (int a = 1; a < 32; ++a) {
+        float2 w = tB[a & 7];
+        if ((a >> 3) != 0) w = (a & 7) ? cmul(w, tA[a >> 3]) : tA[a >> 3];
+        v[a] = cmul(v[a], w);
+      }
+#pragma unroll
+      for (int a = 0; a < 32; ++a) tile[lane * SROW + a] = v[a];
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] = tile[j * SROW + lane];
+      __syncwarp();
+      fft_reg<32>(v);   // over l: v[b] = X[lane + 32 b]
+#pragma unroll
+      for (int b = 0; b < 32; ++b) tile[lane + 32 * b] = v[b];
+      __syncwarp();
+      float2* o = orow + (int64_t)(id - d0) * slab_stride;
+#pragma unroll
+      for (int b = 0; b < 32; ++b) {
+        const int k = lane + 32 * b;
+        const float2 zk = v[b], zm = tile[(M - k) & (M - 1)];
+        float2 X;
+        if (k == 0) {
+          X.x = zk.x + zk.y;
+          X.y = zk.x - zk.y;
+        } else {
+          const float er = 0.5f * (zk.x + zm.x), ei = 0.5f * (zk.y - zm.y);
+          const float orr = 0.5f * (zk.x - zm.x), oi = 0.5f * (zk.y + zm.y);
+          const float2 wk = twiddle_mul(tn, b, 64);   // exp(-2 pi i (lane + 32 b) / NF)
+          const float wr = wk.x * orr - wk.y * oi, wi = wk.x * oi + wk.y * orr;
+          X.x = er + wi;
+          X.y = ei - wr;
+        }
+        o[k] = X;
+      }
+      __syncwarp();
+    }
+  }
+}
+
 // weights M_fit xt^a, optionally times (S - s_S) (S != null) or e (E != null)
 template <typename T, int M>
 __global__ void __launch_bounds__(kFftThreads)
@@ -296,11 +396,30 @@ static cudaError_t run_prod_dy(const sfft_plan_s* p, const T* Rm, int d0, int nd
   return cudaGetLastError();
 }
 
+static cudaError_t run_prod_dy_w(const sfft_plan_s* p, const float* Rm, int d0, int nd, float2* out,
+                                 int64_t slab_stride, int64_t ccd_stride) {
+  constexpr int NF = 2048;
+  const size_t smem = sizeof(float) * (size_t)(2 * NF + 32) + sizeof(float2) * 8 * 32 * 33;
+  cudaFuncSetAttribute(k_rfft_prod_dy_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int L = p->d.L;
+  auto dy_of = [L](int id) { return id < L ? 0 : 1 + (id - L) / (2 * L - 1); };
+  const int ndy = dy_of(d0 + nd - 1) - dy_of(d0) + 1;
+  dim3 grid((p->d.H + kWarpRowsPerCta - 1) / kWarpRowsPerCta, ndy, p->d.batch);
+  k_rfft_prod_dy_w<<<grid, 256, smem, p->stream>>>(Rm, p->d.H, p->d.W, L, d0, nd, out, slab_stride, ccd_stride,
+                                                    (const float2*)p->twM, (const float2*)p->twN);
+  p->nlaunch += 1;
+  return cudaGetLastError();
+}
+
 template <typename T>
 static cudaError_t prod_T(const sfft_plan_s* p, int d0, int nd, void* ws) {
   const int64_t HM = (int64_t)p->d.H * p->M;
   const T* Rm = ws_at<T>(ws, p->rm);
   c_t<T>* out = ws_at<c_t<T>>(ws, p->phat);
+  if constexpr (sizeof(T) == 4) {
+    if (p->M == 1024)
+      return run_prod_dy_w(p, (const float*)Rm, d0, nd, (float2*)out, HM, HM * p->d_batch);
+  }
   SFFT_DISPATCH_M(p->M, (run_prod_dy<T, M>(p, Rm, d0, nd, out, HM, HM * p->d_batch)))
 }
 

@@ -12,8 +12,11 @@ rounded to BF16) must agree with the GPU to 5e-3 of the RMS (the GPU
 normalises in FP32, so a few inputs round to the neighbouring BF16 value),
 which separates layout or indexing mistakes from rounding.  Gradients add one more
 rounding of each back-propagated signal and sign flips of ReLU/max-pool
-decisions taken on slightly different values, so they are compared per tensor
-by cosine similarity (>= 0.99) and relative L2 error (<= 0.1).  The detector
+decisions taken on slightly different values: against FP64 the first layers'
+gradients differ by up to ~9 % (relative L2) at cosine >= 0.995, and the same
+happens to an FP64 model of the kernels' roundings.  The bars are cosine >=
+0.99 and relative L2 <= 0.15 against FP64, and relative L2 <= 2e-2 against the
+rounding model.  The detector
 filters in FP32 (31 taps per pass, two passes): its SNR map agrees with the
 FP64 map to 1e-5 of max |SNR| + 1e-5; candidate decisions may differ only where
 the oracle's margin (to the threshold or to a neighbour) is below 1e-3.  The
@@ -71,6 +74,38 @@ def _forward_bf16(p, xn):
         a = _bf16(C.maxpool2(np.maximum(C.conv_same(a, _bf16(p[wk]), p[bk]), 0.0))[0])
     h4 = np.maximum(a.reshape(a.shape[0], -1) @ _bf16(p["w4"]).T + p["b4"], 0.0)
     return (h4 @ p["w5"].T + p["b5"])[:, 0]
+
+
+def _grads_bf16(p, xn, t):
+    """Oracle backward with the kernels' BF16 roundings applied: operands of
+    every matrix product (activations, weights, back-propagated signals) are
+    BF16, sums and the dense head FP32-exact (modelled in FP64)."""
+    n = xn.shape[0]
+    a = _bf16(xn)
+    cache = []
+    for wk, bk in [("w1", "b1"), ("w2", "b2"), ("w3", "b3")]:
+        wb = _bf16(p[wk])
+        z = C.conv_same(a, wb, p[bk])
+        r = np.maximum(z, 0.0)
+        pooled, idx = C.maxpool2(r)
+        cache.append((a, wb, z, idx, r.shape))
+        a = _bf16(pooled)
+    flat = a.reshape(n, -1)
+    w4b = _bf16(p["w4"])
+    z4 = flat @ w4b.T + p["b4"]
+    h4 = np.maximum(z4, 0.0)
+    logit = (h4 @ p["w5"].T + p["b5"])[:, 0]
+    dz5 = (C.sigmoid(logit) - t) / n
+    g = {"w5": (dz5[:, None] * h4).sum(0)[None, :], "b5": np.array([dz5.sum()])}
+    dz4 = _bf16(dz5[:, None] * p["w5"] * (z4 > 0))
+    g["w4"], g["b4"] = dz4.T @ flat, dz4.sum(0)
+    da = (dz4 @ w4b).reshape(a.shape)
+    for li, (wk, bk) in reversed(list(enumerate([("w1", "b1"), ("w2", "b2"), ("w3", "b3")]))):
+        a_in, wb, z, idx, rshape = cache[li]
+        dz = _bf16(C.maxpool2_backward(da, idx, rshape) * (z > 0))
+        dx, g[wk], g[bk] = C.conv_same_backward(a_in, wb, dz)
+        da = dx
+    return g
 
 
 def _check_logits(z, p, stamps):
@@ -154,13 +189,17 @@ def test_gradients_match_oracle():
     m = _model(p, 64)
     loss = m.backward(_dev(d["stamps"]), _dev(d["labels"]))
     g = C.unflatten(m.get_grads())
-    lo, go = C.loss_and_grads(p, C.normalise(d["stamps"].astype(np.float64)), d["labels"].astype(np.float64))
+    xn = C.normalise(d["stamps"].astype(np.float64))
+    lo, go = C.loss_and_grads(p, xn, d["labels"].astype(np.float64))
+    gb = _grads_bf16(p, xn, d["labels"].astype(np.float64))
     assert abs(float(loss.item()) - lo) <= 2e-2 * abs(lo)
     for k in C.ORDER:
-        a, b = g[k].ravel().astype(np.float64), go[k].ravel()
+        a, b, c = g[k].ravel().astype(np.float64), go[k].ravel(), gb[k].ravel()
         cos = float(a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30))
-        print(f"gradient {k}: cosine {cos:.6f}, relative L2 {_rel(a, b):.3e}")
-        assert cos >= 0.99 and _rel(a, b) <= 0.1, (k, cos, _rel(a, b))
+        print(f"gradient {k}: vs FP64 cosine {cos:.6f}, relative L2 {_rel(a, b):.3e}; "
+              f"vs BF16 model relative L2 {_rel(a, c):.3e} (model vs FP64 {_rel(c, b):.3e})")
+        assert cos >= 0.99 and _rel(a, b) <= 0.15, (k, cos, _rel(a, b))
+        assert _rel(a, c) <= 2e-2, (k, _rel(a, c))
 
 
 def test_adam_step_and_checkpoint_resume():

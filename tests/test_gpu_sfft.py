@@ -54,6 +54,8 @@ CASES = [
     ((130, 100), 7, 1, 2),
     ((150, 210), 7, 2, 2),
     ((96, 300), 11, 2, 2),
+    ((40, 1100), 5, 1, 1),      # 2048-sample rows: the warp-per-row product FFT
+    ((56, 2048), 7, 2, 2),
 ]
 
 
