@@ -258,12 +258,12 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     with torch.cuda.stream(stream):
         plan = Plan(Hs, W, L, DK, DB, batch=B, prec=args.prec, stream=stream, device=dev, d_batch=args.d_batch,
-                    graph=batched, autotune=0 if args.no_autotune else 1)
+                    graph=batched, autotune=0 if args.no_autotune else 1, lag_parts=args.lag_parts)
         tiles = plan.tiles
         if batched:
             # per-phase times and launch counts from an eager profiled pass of the same plan
             eager = Plan(Hs, W, L, DK, DB, batch=B, prec=args.prec, stream=stream, device=dev,
-                         d_batch=tiles[0], rows_per_cta=tiles[1])
+                         d_batch=tiles[0], rows_per_cta=tiles[1], lag_parts=tiles[2])
             eo = eager.subtract(R, S, bad, None, refine=REFINE)
             eager.profile(True)
             eager.profile_read(reset=True)
@@ -381,7 +381,7 @@ def run_gpu(args):
             "config": {"workload": workload, "H": Hs, "W": W, "L": L, "DK": DK, "DB": DB, "prec": args.prec,
                        "refine": REFINE, "ccd_pairs_per_gpu_per_step": B, "parallelism": f"replicas x{world}",
                        "cuda_graph": batched, "autotune": not args.no_autotune,
-                       "tiles": {"d_batch": tiles[0], "rows_per_cta": tiles[1], "k_slots_per_cta": tiles[2]},
+                       "tiles": {"d_batch": tiles[0], "rows_per_cta": tiles[1], "lag_parts": tiles[2]},
                        "l2": "256 MB buffer written between timed steps (L2 flushed)"},
             "roofline": roof, "cpu_baseline": cpu_base, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "status": info, "wall_s": wall, "fp64_path": fp64,
@@ -409,6 +409,7 @@ def main():
     ap.add_argument("--d-batch", type=int, default=0, help="offset differences per workspace slab (0: plan default)")
     ap.add_argument("--fp64-steps", type=int, default=2, help="CCDs timed on the plain FP64 path for comparison")
     ap.add_argument("--no-autotune", action="store_true", help="plan defaults instead of plan-time tile tuning")
+    ap.add_argument("--lag-parts", type=int, default=0, choices=[0, 2, 3], help="contraction lag parts (0: plan's)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

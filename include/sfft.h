@@ -77,6 +77,8 @@ typedef struct {
   int32_t autotune;          /* 1: time contraction tile shapes at plan time and keep the fastest */
   int32_t d_batch;           /* kernel-offset differences per product/FFT pass (0 = auto) */
   int32_t rows_per_cta;      /* rows of one contraction partial sum (0 = auto) */
+  int32_t lag_parts;         /* threads sharing the lags of one contraction k-slot: 2 or 3 (0 = auto;
+                                FP32 path only, the FP64 path uses 2) */
   uint32_t flags;            /* SFFT_FLAG_* */
 } sfft_desc_t;
 
@@ -91,7 +93,7 @@ sfft_status_t sfft_plan_set_stream(sfft_plan_t plan, void* cuda_stream);
 int64_t       sfft_num_unknowns(sfft_plan_t plan);          /* N */
 size_t        sfft_workspace_bytes(sfft_plan_t plan);       /* bytes for `ws` */
 /* Chosen tile shape after planning: out[0] = d_batch, out[1] = rows_per_cta,
- * out[2] = k-slots per CTA. */
+ * out[2] = lag parts of the contraction. */
 sfft_status_t sfft_plan_tiles(sfft_plan_t plan, int32_t* out3);
 
 /* Normal-matrix assembly (the method's Fourier-domain normal equations):

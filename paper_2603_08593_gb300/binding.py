@@ -21,7 +21,7 @@ FLAG_GRAPH = 1
 class Desc(C.Structure):
     _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("L", C.c_int32), ("DK", C.c_int32), ("DB", C.c_int32),
                 ("batch", C.c_int32), ("prec", C.c_int32), ("autotune", C.c_int32), ("d_batch", C.c_int32),
-                ("rows_per_cta", C.c_int32), ("flags", C.c_uint32)]
+                ("rows_per_cta", C.c_int32), ("lag_parts", C.c_int32), ("flags", C.c_uint32)]
 
 
 VP, I32, I64, SZ, DBL = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t, C.c_double
@@ -124,14 +124,14 @@ class Plan:
     """A subtraction plan plus its workspace (a torch uint8 device tensor)."""
 
     def __init__(self, H, W, L, DK, DB, batch=1, prec="mixed", d_batch=0, rows_per_cta=0, autotune=0,
-                 graph=False, stream=None, device=None):
+                 graph=False, stream=None, device=None, lag_parts=0):
         import torch
         self._torch = torch
         lib = load()
         self.lib = lib
         self.device = _device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        self.desc = Desc(H, W, L, DK, DB, batch, PREC[prec], autotune, d_batch, rows_per_cta,
+        self.desc = Desc(H, W, L, DK, DB, batch, PREC[prec], autotune, d_batch, rows_per_cta, lag_parts,
                          FLAG_GRAPH if graph else 0)
         h = VP()
         with torch.cuda.device(self.device):

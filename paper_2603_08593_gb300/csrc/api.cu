@@ -132,6 +132,8 @@ static void build_layout(sfft_plan_s* p) {
   add_region(p->mom_b, cur, sizeof(double) * n_mono(p->d.DB) * B);
   add_region(p->lfac, cur, sizeof(double) * p->N * p->N * B);
   add_region(p->scale, cur, sizeof(double) * p->N * B);
+  add_region(p->dinv, cur, sizeof(double) * 1024 * ((p->N + 31) / 32) * B);   // inverted 32 x 32 diagonal blocks
+  add_region(p->gbar, cur, 64);                                               // grid barrier of the factorisation
   add_region(p->vec, cur, sizeof(double) * 4 * p->N * B);
   add_region(p->theta_off, cur, sizeof(double) * p->N * B);
   p->ws_bytes = cur;
@@ -231,6 +233,7 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
   if (d.H <= 0 || d.W <= 0 || d.batch <= 0 || d.L <= 0) return SFFT_ERR_ARG;
   if (d.prec != SFFT_PREC_FP64 && d.prec != SFFT_PREC_MIXED) return SFFT_ERR_ARG;
   if (d.DK < 0 || d.DB < 0 || d.d_batch < 0 || d.rows_per_cta < 0) return SFFT_ERR_ARG;
+  if (d.lag_parts != 0 && d.lag_parts != 2 && d.lag_parts != 3) return SFFT_ERR_ARG;
   if ((d.L & 1) == 0 || d.L > kMaxL) return SFFT_ERR_UNSUPPORTED;
   if (d.DK > kMaxD || d.DB > kMaxD || d.DB < d.DK) return SFFT_ERR_UNSUPPORTED;
   if (d.H < d.L || d.W < d.L || d.W < 16 || d.W > 2048) return SFFT_ERR_UNSUPPORTED;
@@ -268,10 +271,10 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
   const size_t budget = size_t(24) << 30;
   const int d_batch_max =
       (int)std::max<size_t>(1, std::min<size_t>(budget / (slab * (size_t)d.batch), (size_t)p->n_hd));
-  int tuned_db = 0, tuned_rows = 0;
-  if (d.autotune && (d.d_batch == 0 || d.rows_per_cta == 0)) {
-    const sfft_status_t ts =
-        autotune_tiles(d, (cudaStream_t)cuda_stream, d_batch_max, &tuned_db, &tuned_rows, &p->tuned_ms);
+  int tuned_db = 0, tuned_rows = 0, tuned_parts = 0;
+  if (d.autotune && (d.d_batch == 0 || d.rows_per_cta == 0 || d.lag_parts == 0)) {
+    const sfft_status_t ts = autotune_tiles(d, (cudaStream_t)cuda_stream, d_batch_max, &tuned_db, &tuned_rows,
+                                            &tuned_parts, &p->tuned_ms);
     if (ts != SFFT_OK) {
       delete p;
       return ts;
@@ -281,7 +284,9 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
   else p->d_batch = tuned_db > 0 ? std::min(tuned_db, p->n_hd) : d_batch_max;
   if (d.rows_per_cta > 0) p->rows_per_cta = d.rows_per_cta;
   else p->rows_per_cta = tuned_rows > 0 ? tuned_rows : std::min(d.H, 1024);
-  p->ktile = p->M >= 128 ? 128 : 64;
+  if (d.lag_parts > 0) p->csplit = d.lag_parts;
+  else p->csplit = tuned_parts > 0 ? tuned_parts : 2;
+  if (p->fp64) p->csplit = 2;
   // row flags are bulk-copied in 16-byte aligned runs of up to 20 ints past a chunk start
   p->rf_stride = ((d.H + 32) + 63) / 64 * 64;
   build_layout(p);
@@ -344,7 +349,7 @@ extern "C" int64_t sfft_num_unknowns(sfft_plan_t p) { return p ? p->N : -1; }
 extern "C" size_t sfft_workspace_bytes(sfft_plan_t p) { return p ? p->ws_bytes : 0; }
 extern "C" sfft_status_t sfft_plan_tiles(sfft_plan_t p, int32_t* o) {
   if (!p || !o) return SFFT_ERR_ARG;
-  o[0] = p->d_batch; o[1] = p->rows_per_cta; o[2] = p->ktile;
+  o[0] = p->d_batch; o[1] = p->rows_per_cta; o[2] = p->csplit;
   return SFFT_OK;
 }
 
@@ -371,8 +376,8 @@ static sfft_status_t build_normal_impl(sfft_plan_t p, const float* R, const floa
     CK(cudaMemsetAsync(ws_at<char>(ws, p->gkk), 0, p->gkk.bytes, st));
     CK(cudaMemsetAsync(ws_at<char>(ws, p->gkb), 0, p->gkb.bytes, st));
     CK(cudaMemsetAsync(ws_at<char>(ws, p->gbk), 0, p->gbk.bytes, st));
-    CK(launch_contract(p, p->DM_KB, p->kb_first, p->kb_count, p->rows_per_cta, p->ktile, ws));
-    CK(launch_contract(p, p->DM_bK, p->bk_first, p->bk_count, p->rows_per_cta, p->ktile, ws));
+    CK(launch_contract(p, p->DM_KB, p->kb_first, p->kb_count, p->rows_per_cta, p->csplit, ws));
+    CK(launch_contract(p, p->DM_bK, p->bk_first, p->bk_count, p->rows_per_cta, p->csplit, ws));
   }
   for (size_t ib = 0; ib < p->kk_first.size(); ++ib) {
     const int d0 = (int)ib * p->d_batch;
@@ -383,7 +388,7 @@ static sfft_status_t build_normal_impl(sfft_plan_t p, const float* R, const floa
     }
     {
       Phase ph(p, SFFT_PROF_CONTRACT_KK);
-      CK(launch_contract(p, p->DM_KK, p->kk_first[ib], p->kk_count[ib], p->rows_per_cta, p->ktile, ws));
+      CK(launch_contract(p, p->DM_KK, p->kk_first[ib], p->kk_count[ib], p->rows_per_cta, p->csplit, ws));
     }
   }
   {
@@ -419,7 +424,7 @@ static sfft_status_t solve_impl(sfft_plan_t p, const double* A, const double* b,
     {
       Phase ph(p, SFFT_PROF_CONTRACT_RK);
       CK(cudaMemsetAsync(ws_at<char>(ws, p->gbk), 0, p->gbk.bytes, p->stream));
-      CK(launch_contract(p, p->DM_bK, p->bk_first, p->bk_count, p->rows_per_cta, p->ktile, ws));
+      CK(launch_contract(p, p->DM_bK, p->bk_first, p->bk_count, p->rows_per_cta, p->csplit, ws));
     }
     {
       Phase ph(p, SFFT_PROF_PREP);

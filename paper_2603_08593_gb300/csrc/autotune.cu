@@ -1,14 +1,15 @@
 // Plan-time autotuning of the normal-matrix assembly's tile shape.
 //
 // Candidates are the number of kernel-offset differences per product/FFT pass
-// (d_batch: the memory-budget maximum and its half) and the rows of one
-// contraction partial sum (rows_per_cta: 256 .. 2048, at most H).  Each
+// (d_batch: the memory-budget maximum and its half), the rows of one
+// contraction partial sum (rows_per_cta: 256 .. 2048, at most H) and the lag
+// parts per contraction k-slot (2 or 3, FP32 path).  Each
 // candidate builds a temporary plan of the same shape with min(batch, 2) CCDs,
 // runs sfft_build_normal on synthetic images (every pixel good, so every row
 // carries work) once to warm up and twice timed with CUDA events, and the
 // fastest per-CCD time wins.  Results are kept per process, keyed by the
 // descriptor, and appended to the file named by SFFT_AUTOTUNE_CACHE (one line
-// "key d_batch rows_per_cta ms") when that variable is set; a later process
+// "key d_batch rows_per_cta lag_parts ms") when that variable is set; a later process
 // reads them back instead of timing again.
 #include <stdio.h>
 #include <stdlib.h>
@@ -26,7 +27,7 @@
 namespace sfft {
 namespace {
 
-struct Tuned { int d_batch, rows_per_cta; double ms; };
+struct Tuned { int d_batch, rows_per_cta, lag_parts; double ms; };
 
 std::mutex g_mu;
 std::map<std::string, Tuned> g_cache;
@@ -36,7 +37,7 @@ std::string tune_key(const sfft_desc_t& d, int device) {
   char buf[160];
   cudaDeviceProp prop{};
   cudaGetDeviceProperties(&prop, device);
-  snprintf(buf, sizeof(buf), "sm%d%d_%dSM_H%d_W%d_L%d_DK%d_DB%d_B%d_P%d", prop.major, prop.minor,
+  snprintf(buf, sizeof(buf), "v2_sm%d%d_%dSM_H%d_W%d_L%d_DK%d_DB%d_B%d_P%d", prop.major, prop.minor,
            prop.multiProcessorCount, d.H, d.W, d.L, d.DK, d.DB, d.batch, d.prec);
   return buf;
 }
@@ -50,7 +51,7 @@ void load_cache_file() {
   if (!f) return;
   char key[160];
   Tuned t{};
-  while (fscanf(f, "%159s %d %d %lf", key, &t.d_batch, &t.rows_per_cta, &t.ms) == 4) g_cache[key] = t;
+  while (fscanf(f, "%159s %d %d %d %lf", key, &t.d_batch, &t.rows_per_cta, &t.lag_parts, &t.ms) == 5) g_cache[key] = t;
   fclose(f);
 }
 
@@ -60,7 +61,7 @@ void store(const std::string& key, const Tuned& t) {
   if (!path || !*path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %d %d %.6f\n", key.c_str(), t.d_batch, t.rows_per_cta, t.ms);
+  fprintf(f, "%s %d %d %d %.6f\n", key.c_str(), t.d_batch, t.rows_per_cta, t.lag_parts, t.ms);
   fclose(f);
 }
 
@@ -84,13 +85,14 @@ struct DevBuf {
 };
 
 // time one candidate; returns ms per CCD or a negative value on failure
-double time_candidate(const sfft_desc_t& base, cudaStream_t s, int d_batch, int rows) {
+double time_candidate(const sfft_desc_t& base, cudaStream_t s, int d_batch, int rows, int parts) {
   sfft_desc_t d = base;
   d.autotune = 0;
   d.flags = 0;
   d.batch = std::min(base.batch, 2);
   d.d_batch = d_batch;
   d.rows_per_cta = rows;
+  d.lag_parts = parts;
   sfft_plan_t p = nullptr;
   if (sfft_plan(&d, s, &p) != SFFT_OK) return -1.0;
   const int64_t npx = (int64_t)d.H * d.W * d.batch;
@@ -130,7 +132,7 @@ double time_candidate(const sfft_desc_t& base, cudaStream_t s, int d_batch, int 
 }  // namespace
 
 sfft_status_t autotune_tiles(const sfft_desc_t& d, cudaStream_t s, int d_batch_max, int* d_batch, int* rows_per_cta,
-                             double* ms_per_ccd) {
+                             int* lag_parts, double* ms_per_ccd) {
   int dev = 0;
   cudaGetDevice(&dev);
   const std::string key = tune_key(d, dev);
@@ -141,6 +143,7 @@ sfft_status_t autotune_tiles(const sfft_desc_t& d, cudaStream_t s, int d_batch_m
     if (it != g_cache.end()) {
       *d_batch = it->second.d_batch;
       *rows_per_cta = it->second.rows_per_cta;
+      *lag_parts = it->second.lag_parts;
       if (ms_per_ccd) *ms_per_ccd = it->second.ms;
       return SFFT_OK;
     }
@@ -153,12 +156,16 @@ sfft_status_t autotune_tiles(const sfft_desc_t& d, cudaStream_t s, int d_batch_m
     if (r <= d.H) rows.push_back(r);
   if (rows.empty()) rows.push_back(d.H);
   if (d.rows_per_cta > 0) rows = {d.rows_per_cta};
-  Tuned best{0, 0, -1.0};
+  std::vector<int> parts = {2, 3};
+  if (d.prec == SFFT_PREC_FP64) parts = {2};
+  if (d.lag_parts > 0) parts = {d.lag_parts};
+  Tuned best{0, 0, 0, -1.0};
   for (int db : dbs)
-    for (int r : rows) {
-      const double t = time_candidate(d, s, db, r);
-      if (t > 0 && (best.ms < 0 || t < best.ms)) best = {db, r, t};
-    }
+    for (int r : rows)
+      for (int np : parts) {
+        const double t = time_candidate(d, s, db, r, np);
+        if (t > 0 && (best.ms < 0 || t < best.ms)) best = {db, r, np, t};
+      }
   if (best.ms < 0) return SFFT_ERR_CUDA;
   {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -166,6 +173,7 @@ sfft_status_t autotune_tiles(const sfft_desc_t& d, cudaStream_t s, int d_batch_m
   }
   *d_batch = best.d_batch;
   *rows_per_cta = best.rows_per_cta;
+  *lag_parts = best.lag_parts;
   if (ms_per_ccd) *ms_per_ccd = best.ms;
   return SFFT_OK;
 }

@@ -13,7 +13,7 @@
 // over the CTA's k-slots, a warp shuffle reduction, a shared-memory reduction
 // over warps and an FP64 global atomic add.
 //
-// Thread layout: one k-slot x one monomial group x one half of the lags.  A
+// Thread layout: one k-slot x one monomial group x one part of the lags.  A
 // monomial group is one or two exponents a with all their b (at most five
 // monomials), so one complex product conj(V^_a) P^ feeds up to five FMA
 // pairs; splitting the lags over two threads halves the accumulators per
@@ -47,13 +47,21 @@ template <> struct GroupCfg<0, 0> { static constexpr int ALO = 0, NLO = 1, AHI =
 
 template <int DM> constexpr int n_groups() { return DM >= 3 ? 3 : (DM == 2 ? 2 : 1); }
 template <typename T> constexpr int max_uy() { return sizeof(T) == 4 ? 11 : 6; }
-constexpr int kHalves = 2;                         // threads sharing the lags of one (k, group)
-template <typename T> constexpr int max_half() { return (max_uy<T>() + 1) / 2; }
+// NS threads share the lags of one (k, group): lags [p ceil(nuy / NS), ...) go to part p
+template <typename T, int NS> constexpr int max_part() { return (max_uy<T>() + NS - 1) / NS; }
+__device__ __forceinline__ void lag_part(int nuy, int ns, int part, int& lag0, int& nlag) {
+  const int per = (nuy + ns - 1) / ns;
+  lag0 = part * per;
+  nlag = max(0, min(per, nuy - lag0));
+}
 // k-slots per CTA: the five-monomial groups (DM >= 3) use 32-slot tiles so
 // that three CTAs fit on an SM; FP64 accumulators take one CTA per SM.
 template <typename T, int DM> constexpr int kt_for() { return DM >= 3 ? 32 : 64; }
-// register cap per thread: three CTAs of 192 threads (DM >= 3) or two of 256 fit in 64K registers
-template <typename T, int DM> constexpr int maxreg_for() { return sizeof(T) == 8 ? 255 : (DM >= 3 ? 96 : 112); }
+// register cap per thread: three CTAs of 192 threads (DM >= 3, two lag parts) or of 288
+// threads (three parts), two CTAs of 256 or 384 threads otherwise, fit in 64K registers
+template <typename T, int DM, int NS> constexpr int maxreg_for() {
+  return sizeof(T) == 8 ? 255 : (DM >= 3 ? (NS == 2 ? 96 : 72) : (NS == 2 ? 112 : 80));
+}
 
 // ---------------------------------------------------------------- shared-memory pipeline
 // A CTA walks its band of weight rows y in chunks of kChunk rows.  For each
@@ -288,9 +296,7 @@ __device__ __forceinline__ void group_flush(const c_t<T> (&acc)[MH][5], const CJ
 
 template <typename T, int DM, int KT, int MU, int MH, int G>
 __device__ __forceinline__ void chunk_dispatch(c_t<T> (&acc)[MH][5], const Stage<T, DM, KT, MU>& st, int kk,
-                                               int nrow, int nuy, int half, const int* rf) {
-  const int lag0 = half == 0 ? 0 : (nuy + 1) / 2;
-  const int nlag = half == 0 ? (nuy + 1) / 2 : nuy / 2;
+                                               int nrow, int nuy, int lag0, int nlag, const int* rf) {
   if constexpr (sizeof(T) == 4) {
     switch (nlag) {
 #define SFFT_NLAG_CASE(NV) \
@@ -304,15 +310,15 @@ __device__ __forceinline__ void chunk_dispatch(c_t<T> (&acc)[MH][5], const Stage
   }
 }
 
-template <typename T, int DM, int KT> constexpr int cta_threads() { return KT * n_groups<DM>() * kHalves; }
+template <typename T, int DM, int KT, int NS> constexpr int cta_threads() { return KT * n_groups<DM>() * NS; }
 
-template <typename T, int DM, int KT>
-__global__ void __launch_bounds__(cta_threads<T, DM, KT>()) __maxnreg__((maxreg_for<T, DM>()))
+template <typename T, int DM, int KT, int NS>
+__global__ void __launch_bounds__(cta_threads<T, DM, KT, NS>()) __maxnreg__((maxreg_for<T, DM, NS>()))
 k_contract(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, int M, int Nf, int L, int rows_per_cta,
            const c_t<T>* __restrict__ twD, const T* __restrict__ ytab) {
   using T2 = c_t<T>;
   constexpr int MU = max_uy<T>();
-  constexpr int MH = max_half<T>();
+  constexpr int MH = max_part<T, NS>();
   constexpr int NMONO = n_mono(DM);
   constexpr int NG = n_groups<DM>();
   using St = Stage<T, DM, KT, MU>;
@@ -331,8 +337,8 @@ k_contract(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, int M, i
   __syncthreads();
 
   const int w = (L - 1) / 2;
-  const int kk = threadIdx.x % KT, gh = threadIdx.x / KT;     // gh = group * kHalves + half (warp-uniform)
-  const int g = gh / kHalves, half = gh % kHalves;
+  const int kk = threadIdx.x % KT, gp = threadIdx.x / KT;     // gp = group * NS + part (warp-uniform)
+  const int g = gp / NS, part = gp % NS;
   const int k0 = blockIdx.x * KT, k = k0 + kk;
   int y0 = blockIdx.z * rows_per_cta, y1 = y0 + rows_per_cta;
   if (y0 < w) y0 = w;
@@ -342,6 +348,8 @@ k_contract(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, int M, i
   const T2* V = reinterpret_cast<const T2*>(ws + job.wts);
   const int* rowflag = reinterpret_cast<const int*>(ws + job.rowflag);
   const int nuy = job.uy_hi - job.uy_lo + 1;
+  int lag0, nlag;
+  lag_part(nuy, NS, part, lag0, nlag);
 
   T2 acc[MH][5];
 #pragma unroll
@@ -371,15 +379,13 @@ k_contract(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, int M, i
     }
     const St& st = stages[c & 1];
     const int* rf = st.rf + (yc & 3);
-    if (g == 0) chunk_dispatch<T, DM, KT, MU, MH, 0>(acc, st, kk, ye - yc, nuy, half, rf);
-    if constexpr (NG > 1) { if (g == 1) chunk_dispatch<T, DM, KT, MU, MH, 1>(acc, st, kk, ye - yc, nuy, half, rf); }
-    if constexpr (NG > 2) { if (g == 2) chunk_dispatch<T, DM, KT, MU, MH, 2>(acc, st, kk, ye - yc, nuy, half, rf); }
+    if (g == 0) chunk_dispatch<T, DM, KT, MU, MH, 0>(acc, st, kk, ye - yc, nuy, lag0, nlag, rf);
+    if constexpr (NG > 1) { if (g == 1) chunk_dispatch<T, DM, KT, MU, MH, 1>(acc, st, kk, ye - yc, nuy, lag0, nlag, rf); }
+    if constexpr (NG > 2) { if (g == 2) chunk_dispatch<T, DM, KT, MU, MH, 2>(acc, st, kk, ye - yc, nuy, lag0, nlag, rf); }
     __syncthreads();
   }
   // k-slots past the row (whole warps, since M and KT are multiples of 32) hold junk
   if (k < M) {
-    const int lag0 = half == 0 ? 0 : (nuy + 1) / 2;
-    const int nlag = half == 0 ? (nuy + 1) / 2 : nuy / 2;
     if (g == 0) group_flush<T, DM, MH, 0>(acc, job, k, Nf, L, lag0, nlag, red, twD);
     if constexpr (NG > 1) { if (g == 1) group_flush<T, DM, MH, 1>(acc, job, k, Nf, L, lag0, nlag, red, twD); }
     if constexpr (NG > 2) { if (g == 2) group_flush<T, DM, MH, 2>(acc, job, k, Nf, L, lag0, nlag, red, twD); }
@@ -460,22 +466,22 @@ k_contract_slot0(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, in
   }
 }
 
-template <typename T, int DM>
+template <typename T, int DM, int NS>
 static cudaError_t contract_T(const sfft_plan_s* p, int job0, int njobs, int rows_per_cta, void* ws) {
   constexpr int KT = kt_for<T, DM>();
   const int H = p->d.H, L = p->d.L;
   constexpr int MU = max_uy<T>();
   const size_t smem = 2 * sizeof(Stage<T, DM, KT, MU>) + 32 + sizeof(T) * L * L * n_mono(DM);
-  auto kern = k_contract<T, DM, KT>;
+  auto kern = k_contract<T, DM, KT, NS>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int nb = (H + rows_per_cta - 1) / rows_per_cta;
   // row bands vary slowest: the CTAs in flight share one band of the weight
   // spectra (read by every job), which then stays in L2 across the jobs
   for (int j0 = 0; j0 < njobs; j0 += 65535) {   // grid.y limit
     dim3 grid((p->M + KT - 1) / KT, std::min(65535, njobs - j0), nb);
-    kern<<<grid, cta_threads<T, DM, KT>(), smem, p->stream>>>(p->d_jobs + job0 + j0, (char*)ws, H, p->M, p->Nf,
-                                                                        L, rows_per_cta, (const c_t<T>*)p->twD,
-                                                                        (const T*)p->ytab);
+    kern<<<grid, cta_threads<T, DM, KT, NS>(), smem, p->stream>>>(p->d_jobs + job0 + j0, (char*)ws, H, p->M,
+                                                                            p->Nf, L, rows_per_cta,
+                                                                            (const c_t<T>*)p->twD, (const T*)p->ytab);
     p->nlaunch += 1;
   }
   k_contract_slot0<T, DM><<<dim3(njobs, max_uy<T>()), 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, H, p->M,
@@ -484,24 +490,26 @@ static cudaError_t contract_T(const sfft_plan_s* p, int job0, int njobs, int row
   return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, int NS>
 static cudaError_t contract_dm(const sfft_plan_s* p, int DM, int job0, int njobs, int rows_per_cta, void* ws) {
   switch (DM) {
-    case 0: return contract_T<T, 0>(p, job0, njobs, rows_per_cta, ws);
-    case 1: return contract_T<T, 1>(p, job0, njobs, rows_per_cta, ws);
-    case 2: return contract_T<T, 2>(p, job0, njobs, rows_per_cta, ws);
-    case 3: return contract_T<T, 3>(p, job0, njobs, rows_per_cta, ws);
-    case 4: return contract_T<T, 4>(p, job0, njobs, rows_per_cta, ws);
+    case 0: return contract_T<T, 0, NS>(p, job0, njobs, rows_per_cta, ws);
+    case 1: return contract_T<T, 1, NS>(p, job0, njobs, rows_per_cta, ws);
+    case 2: return contract_T<T, 2, NS>(p, job0, njobs, rows_per_cta, ws);
+    case 3: return contract_T<T, 3, NS>(p, job0, njobs, rows_per_cta, ws);
+    case 4: return contract_T<T, 4, NS>(p, job0, njobs, rows_per_cta, ws);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_contract(const sfft_plan_s* p, int DM, int job0, int njobs, int rows_per_cta, int ktile,
+// lag_parts: threads sharing the lags of one (k-slot, monomial group), 2 or 3
+// (FP32 only; the FP64 path always uses 2)
+cudaError_t launch_contract(const sfft_plan_s* p, int DM, int job0, int njobs, int rows_per_cta, int lag_parts,
                             void* ws) {
-  (void)ktile;
   if (njobs <= 0) return cudaSuccess;
-  return p->fp64 ? contract_dm<double>(p, DM, job0, njobs, rows_per_cta, ws)
-                 : contract_dm<float>(p, DM, job0, njobs, rows_per_cta, ws);
+  if (p->fp64) return contract_dm<double, 2>(p, DM, job0, njobs, rows_per_cta, ws);
+  return lag_parts == 3 ? contract_dm<float, 3>(p, DM, job0, njobs, rows_per_cta, ws)
+                        : contract_dm<float, 2>(p, DM, job0, njobs, rows_per_cta, ws);
 }
 
 }  // namespace sfft

@@ -6,10 +6,12 @@
 // M_fit psi_q psi_q', b_(j,p) = g^{bK}_p(u_j), b_q = moment of M_fit psi_q S'.
 //
 // Solve: Jacobi equilibration D_s = diag(A)^-1/2, right-looking blocked
-// Cholesky (32 x 32 blocks: one launch factors the diagonal block and solves
-// the panel below it, one launch applies the trailing update) of D_s A D_s,
-// blocked forward and backward substitution, theta = D_s y.
+// Cholesky of D_s A D_s (32 x 32 blocks, all block steps in one cooperative
+// launch), blocked forward and backward substitution with the inverted
+// diagonal blocks, theta = D_s y.
 // Per-CCD status flags (never a trap): 1 = not positive definite, 2 = non-finite.
+#include <algorithm>
+
 #include "common.cuh"
 #include "plan.h"
 
@@ -118,132 +120,222 @@ k_chol_init(const double* __restrict__ A, double* __restrict__ Lf, double* __res
   }
 }
 
-// Factor the diagonal block [kb, kb+nb) in shared memory (one warp, lane i
-// owns row i) and solve this CTA's 32 panel rows r >= kb + nb against it:
-// X = A_rk L_kk^-T.  Every panel CTA factors the small block itself, so one
-// launch per block column does both; CTA 0 writes the factor back and reports
-// a non-positive or non-finite pivot.  blockDim = 32.
-__global__ void __launch_bounds__(NBK)
-k_chol_panel(double* __restrict__ Lf, int* __restrict__ status, int N, int kb) {
-  __shared__ double blk[NBK][NBK + 1];
-  __shared__ double rdiag[NBK];   // 1 / L_cc
-  const int ccd = blockIdx.y, lane = threadIdx.x;
-  double* l = Lf + (int64_t)ccd * N * N;
-  const int nb = min(NBK, N - kb);
-  for (int i = 0; i < NBK; ++i) blk[i][lane] = (i < nb && lane <= i) ? l[(int64_t)(kb + i) * N + kb + lane] : 0.0;
-  __syncwarp();
-  bool bad = false, nonfinite = false;
-  for (int c = 0; c < nb; ++c) {
-    if (lane == c) {
-      double d = blk[c][c];
-      if (!(d > 0.0) || !isfinite(d)) { bad = true; nonfinite = !isfinite(d); d = 1.0; }
-      const double s = sqrt(d);
-      blk[c][c] = s;
-      rdiag[c] = 1.0 / s;
-    }
-    __syncwarp();
-    if (lane > c && lane < nb) blk[lane][c] *= rdiag[c];
-    __syncwarp();
-    if (lane > c && lane < nb) {
-      const double lic = blk[lane][c];
-      for (int j = c + 1; j <= lane; ++j) blk[lane][j] -= lic * blk[j][c];
-    }
-    __syncwarp();
-  }
-  if (blockIdx.x == 0) {
-    if (bad) atomicOr(&status[ccd], nonfinite ? 2 : 1);
-    for (int i = 0; i < nb; ++i)
-      if (lane <= i) l[(int64_t)(kb + i) * N + kb + lane] = blk[i][lane];
-  }
-  const int r = kb + nb + blockIdx.x * NBK + lane;
-  if (r >= N) return;
-  double x[NBK];
-  double* row = l + (int64_t)r * N + kb;
-#pragma unroll
-  for (int c = 0; c < NBK; ++c) x[c] = c < nb ? row[c] : 0.0;
-#pragma unroll
-  for (int c = 0; c < NBK; ++c) {
-    if (c < nb) {
-      // four independent partial sums keep the FP64 dependency chains short
-      double v0 = x[c], v1 = 0.0, v2 = 0.0, v3 = 0.0;
-#pragma unroll
-      for (int t = 0; t + 3 < c; t += 4) {
-        v0 -= x[t] * blk[c][t];
-        v1 -= x[t + 1] * blk[c][t + 1];
-        v2 -= x[t + 2] * blk[c][t + 2];
-        v3 -= x[t + 3] * blk[c][t + 3];
-      }
-#pragma unroll
-      for (int t = c & ~3; t < c; ++t) v0 -= x[t] * blk[c][t];
-      x[c] = ((v0 + v1) + (v2 + v3)) * rdiag[c];
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < NBK; ++c) if (c < nb) row[c] = x[c];
-}
+// ---------------------------------------------------------------- persistent blocked Cholesky
+// One cooperative launch factors every CCD's matrix.  For each 32-column
+// block k: (A) one CTA per CCD factors the diagonal block in shared memory and
+// inverts the factor; (B) all CTAs take 256-row slices of the panels below the
+// diagonal blocks and multiply them by the transposed inverse (the panel
+// triangular solve as a product); (C) all CTAs take 32 x 32 tiles of the
+// trailing lower triangles and subtract P_i P_j^T.  The phases are separated
+// by a grid-wide barrier whose waits are bounded: a barrier that gives up (or
+// sees another CTA give up) flags every CCD with bit 4 and the kernel returns.
+// The inverses of the diagonal blocks are kept for the substitutions.  Data
+// written by other CTAs is read with L2-coherent loads (ld.global.cg).
+struct GridBar { unsigned count, gen, abort, pad; };
 
-// trailing update of lower tiles (bi >= bj) below the panel: C -= P_i P_j^T
-__global__ void __launch_bounds__(256)
-k_chol_update(double* __restrict__ Lf, int N, int kb) {
-  __shared__ double Pi[NBK][NBK + 1], Pj[NBK][NBK + 1];
-  const int ccd = blockIdx.y;
-  double* l = Lf + (int64_t)ccd * N * N;
-  const int nb = min(NBK, N - kb);
-  const int r0 = kb + nb;
-  // linear tile index -> (bi, bj), bj <= bi
-  int t = blockIdx.x, bi = 0;
-  while (t > bi) { t -= bi + 1; ++bi; }
-  const int bj = t;
-  const int i0 = r0 + bi * NBK, j0 = r0 + bj * NBK;
-  for (int q = threadIdx.x; q < NBK * NBK; q += blockDim.x) {
-    const int i = q / NBK, c = q % NBK;
-    Pi[i][c] = (i0 + i < N && c < nb) ? l[(int64_t)(i0 + i) * N + kb + c] : 0.0;
-    Pj[i][c] = (j0 + i < N && c < nb) ? l[(int64_t)(j0 + i) * N + kb + c] : 0.0;
+constexpr int kBarSpin = 1 << 24;   // x >= 64 ns per try: about a second
+
+__device__ bool grid_sync_bounded(GridBar* bar, int* flag_sh) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &bar->gen;
+    volatile unsigned* vab = &bar->abort;
+    const unsigned g = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&bar->count, 1u) + 1u;
+    bool ok = true;
+    if (arrived == gridDim.x) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      for (int it = 0; *vgen == g; ++it) {
+        if (*vab != 0u || it > kBarSpin) { ok = false; break; }
+        __nanosleep(64);
+      }
+    }
+    if (!ok) atomicExch(&bar->abort, 1u);
+    __threadfence();
+    *flag_sh = ok ? 1 : 0;
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < NBK * NBK; q += blockDim.x) {
-    const int i = q / NBK, j = q % NBK;
-    const int gi = i0 + i, gj = j0 + j;
-    if (gi >= N || gj >= N || gj > gi) continue;
-    double s = 0.0;
-#pragma unroll 8
-    for (int c = 0; c < NBK; ++c) s += Pi[i][c] * Pj[j][c];
-    l[(int64_t)gi * N + gj] -= s;
+  return *flag_sh != 0;
+}
+
+// Factor the diagonal block [kb, kb + nb) of one CCD with the whole CTA
+// (identity-padded past nb), write the factor back and its inverse (32 x 32,
+// lower) to `inv_out`.  Pivots use the reciprocal square root, so neither a
+// square root nor a division sits on the column-to-column dependency chain.
+// A non-positive or non-finite pivot is replaced by 1 and reported in the
+// CCD's status word.
+__device__ void factor_diag(double* __restrict__ l, double* __restrict__ inv_out, int* __restrict__ st, int N, int kb,
+                            int nb, double (*blk)[NBK + 1], double (*inv)[NBK + 1], double* rinv) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NBK * NBK; e += blockDim.x) {
+    const int i = e / NBK, j = e % NBK;
+    blk[i][j] = (i < nb && j <= i) ? __ldcg(l + (int64_t)(kb + i) * N + kb + j) : (i == j ? 1.0 : 0.0);
+    inv[i][j] = i == j ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int c = 0; c < NBK; ++c) {
+    if (tid == 0) {
+      double d = blk[c][c];
+      if (!(d > 0.0) || !isfinite(d)) {
+        atomicOr(st, isfinite(d) ? 1 : 2);
+        d = 1.0;
+      }
+      const double r = rsqrt(d);
+      blk[c][c] = d * r;
+      rinv[c] = r;
+    }
+    __syncthreads();
+    if (tid > c && tid < NBK) blk[tid][c] *= rinv[c];
+    __syncthreads();
+    for (int e = tid; e < NBK * NBK; e += blockDim.x) {
+      const int i = e / NBK, j = e % NBK;
+      if (j > c && j <= i) blk[i][j] -= blk[i][c] * blk[j][c];
+    }
+    __syncthreads();
+  }
+  // L X = I by row elimination: row t is final once scaled, then removed below
+  for (int t = 0; t < NBK; ++t) {
+    if (tid <= t) inv[t][tid] *= rinv[t];
+    __syncthreads();
+    for (int e = tid; e < NBK * NBK; e += blockDim.x) {
+      const int i = e / NBK, j = e % NBK;
+      if (i > t && j <= t) inv[i][j] -= blk[i][t] * inv[t][j];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < NBK * NBK; e += blockDim.x) {
+    const int i = e / NBK, j = e % NBK;
+    inv_out[e] = inv[i][j];
+    if (i < nb && j <= i) l[(int64_t)(kb + i) * N + kb + j] = blk[i][j];
   }
 }
 
-// x = D_s (L L^T)^-1 D_s rhs, one CTA per CCD.  Blocked substitution: each
-// 32 x 32 diagonal block is solved by one warp from shared memory (lane i owns
-// unknown i, one shuffle per column), the coupling to the remaining unknowns
-// is applied by all threads, one unknown per thread.
+__global__ void __launch_bounds__(256)
+k_chol_coop(double* __restrict__ Lf, double* __restrict__ dinv, int* __restrict__ status, int N, int B,
+            GridBar* __restrict__ bar) {
+  __shared__ double sa[NBK][NBK + 1], sb[NBK][NBK + 1];
+  __shared__ double rinv[NBK];
+  __shared__ int flag;
+  const int nblk = (N + NBK - 1) / NBK;
+  const int64_t NN = (int64_t)N * N;
+  const int tid = threadIdx.x;
+  for (int k = 0; k < nblk; ++k) {
+    const int kb = k * NBK, nb = min(NBK, N - kb), rem = N - kb - nb;
+    // (A) diagonal blocks
+    for (int ccd = blockIdx.x; ccd < B; ccd += gridDim.x) {
+      __syncthreads();
+      factor_diag(Lf + ccd * NN, dinv + ((int64_t)ccd * nblk + k) * NBK * NBK, status + ccd, N, kb, nb, sa, sb, rinv);
+    }
+    if (!grid_sync_bounded(bar, &flag)) break;
+    // (B) panels, 32-row tiles: X = A inv(L_kk)^T; thread (row tid / 8, columns tid % 8 + 8 m)
+    if (rem > 0) {
+      const int T = (rem + NBK - 1) / NBK;
+      for (int item = blockIdx.x; item < B * T; item += gridDim.x) {
+        const int ccd = item / T, r0 = kb + nb + (item % T) * NBK;
+        double* l = Lf + ccd * NN;
+        const double* iv = dinv + ((int64_t)ccd * nblk + k) * NBK * NBK;
+        __syncthreads();
+        for (int e = tid; e < NBK * NBK; e += blockDim.x) {
+          const int i = e / NBK, c = e % NBK;
+          sb[i][c] = __ldcg(iv + e);
+          sa[i][c] = (r0 + i < N && c < nb) ? __ldcg(l + (int64_t)(r0 + i) * N + kb + c) : 0.0;
+        }
+        __syncthreads();
+        const int i = tid >> 3, c0 = tid & 7;
+        double out[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int c = c0 + 8 * m;
+          double s0 = 0.0, s1 = 0.0;
+          for (int t = 0; t + 1 <= c; t += 2) {
+            s0 += sa[i][t] * sb[c][t];
+            s1 += sa[i][t + 1] * sb[c][t + 1];
+          }
+          if ((c & 1) == 0) s0 += sa[i][c] * sb[c][c];
+          out[m] = s0 + s1;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < 4; ++m) sa[i][c0 + 8 * m] = out[m];
+        __syncthreads();
+        for (int e = tid; e < NBK * NBK; e += blockDim.x) {
+          const int ii = e / NBK, c = e % NBK;
+          if (r0 + ii < N && c < nb) l[(int64_t)(r0 + ii) * N + kb + c] = sa[ii][c];
+        }
+      }
+    }
+    if (!grid_sync_bounded(bar, &flag)) break;
+    // (C) trailing update of the lower tiles
+    if (rem > 0) {
+      const int T = (rem + NBK - 1) / NBK, ntile = T * (T + 1) / 2;
+      const int r0 = kb + nb;
+      for (int item = blockIdx.x; item < B * ntile; item += gridDim.x) {
+        const int ccd = item / ntile;
+        int t = item % ntile, bi = 0;
+        while (t > bi) { t -= bi + 1; ++bi; }
+        const int bj = t;
+        const int i0 = r0 + bi * NBK, j0 = r0 + bj * NBK;
+        double* l = Lf + ccd * NN;
+        __syncthreads();
+        for (int e = tid; e < NBK * NBK; e += blockDim.x) {
+          const int i = e / NBK, c = e % NBK;
+          sa[i][c] = (i0 + i < N && c < nb) ? __ldcg(l + (int64_t)(i0 + i) * N + kb + c) : 0.0;
+          sb[i][c] = (j0 + i < N && c < nb) ? __ldcg(l + (int64_t)(j0 + i) * N + kb + c) : 0.0;
+        }
+        __syncthreads();
+        for (int e = tid; e < NBK * NBK; e += blockDim.x) {
+          const int i = e / NBK, j = e % NBK;
+          const int gi = i0 + i, gj = j0 + j;
+          if (gi >= N || gj >= N || gj > gi) continue;
+          double s0 = 0.0, s1 = 0.0;
+#pragma unroll 8
+          for (int c = 0; c < NBK; c += 2) {
+            s0 += sa[i][c] * sb[j][c];
+            s1 += sa[i][c + 1] * sb[j][c + 1];
+          }
+          l[(int64_t)gi * N + gj] = __ldcg(l + (int64_t)gi * N + gj) - (s0 + s1);
+        }
+      }
+    }
+    if (!grid_sync_bounded(bar, &flag)) break;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && ((volatile GridBar*)bar)->abort != 0u)
+    for (int c = 0; c < B; ++c) atomicOr(&status[c], 4);
+}
+
+// x = D_s (L L^T)^-1 D_s rhs, one CTA per CCD, blocked substitution with the
+// inverted diagonal blocks: each block of unknowns is a 32 x 32 product by one
+// warp, the coupling to the remaining unknowns is applied by all threads.
 __global__ void __launch_bounds__(1024)
-k_chol_solve(const double* __restrict__ Lf, const double* __restrict__ scale, const double* __restrict__ rhs,
-             double* __restrict__ x, int N, int* __restrict__ status) {
+k_chol_solve(const double* __restrict__ Lf, const double* __restrict__ dinv, const double* __restrict__ scale,
+             const double* __restrict__ rhs, double* __restrict__ x, int N, int* __restrict__ status) {
   extern __shared__ double sh[];   // y[N]
-  __shared__ double ld[32][33];
+  __shared__ double ld[NBK][NBK + 1];
   const int ccd = blockIdx.x;
+  const int nblk = (N + NBK - 1) / NBK;
   const double* l = Lf + (int64_t)ccd * N * N;
   const double* s = scale + (int64_t)ccd * N;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < N; i += blockDim.x) sh[i] = rhs[(int64_t)ccd * N + i] * s[i];
-  const int nblk = (N + 31) / 32;
   // forward: L y = r
   for (int bi = 0; bi < nblk; ++bi) {
-    const int jb = bi * 32, nb = min(32, N - jb);
-    for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
-      const int i = t >> 5, j = t & 31;
-      ld[i][j] = (i < nb && j <= i) ? l[(int64_t)(jb + i) * N + jb + j] : 0.0;
-    }
+    const int jb = bi * NBK, nb = min(NBK, N - jb);
+    const double* inv = dinv + ((int64_t)ccd * nblk + bi) * NBK * NBK;
+    for (int e = threadIdx.x; e < NBK * NBK; e += blockDim.x) ld[e / NBK][e % NBK] = inv[e];
     __syncthreads();
     if (warp == 0) {
-      double y = lane < nb ? sh[jb + lane] : 0.0;
-      const double rd = lane < nb ? 1.0 / ld[lane][lane] : 0.0;
-      for (int c = 0; c < nb; ++c) {
-        if (lane == c) y *= rd;
-        const double yc = __shfl_sync(0xffffffffu, y, c);
-        if (lane > c) y -= ld[lane][c] * yc;
+      const double v = lane < nb ? sh[jb + lane] : 0.0;
+      double y0 = 0.0, y1 = 0.0;
+#pragma unroll
+      for (int t = 0; t < NBK; t += 2) {
+        y0 += ld[lane][t] * __shfl_sync(0xffffffffu, v, t);
+        y1 += ld[lane][t + 1] * __shfl_sync(0xffffffffu, v, t + 1);
       }
-      if (lane < nb) sh[jb + lane] = y;
+      if (lane < nb) sh[jb + lane] = y0 + y1;
     }
     __syncthreads();
     for (int i = jb + nb + threadIdx.x; i < N; i += blockDim.x) {
@@ -263,21 +355,19 @@ k_chol_solve(const double* __restrict__ Lf, const double* __restrict__ scale, co
   }
   // backward: L^T z = y
   for (int bi = nblk - 1; bi >= 0; --bi) {
-    const int jb = bi * 32, nb = min(32, N - jb);
-    for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
-      const int i = t >> 5, j = t & 31;
-      ld[i][j] = (i < nb && j <= i) ? l[(int64_t)(jb + i) * N + jb + j] : 0.0;
-    }
+    const int jb = bi * NBK, nb = min(NBK, N - jb);
+    const double* inv = dinv + ((int64_t)ccd * nblk + bi) * NBK * NBK;
+    for (int e = threadIdx.x; e < NBK * NBK; e += blockDim.x) ld[e / NBK][e % NBK] = inv[e];
     __syncthreads();
     if (warp == 0) {
-      double z = lane < nb ? sh[jb + lane] : 0.0;
-      const double rd = lane < nb ? 1.0 / ld[lane][lane] : 0.0;
-      for (int c = nb - 1; c >= 0; --c) {
-        if (lane == c) z *= rd;
-        const double zc = __shfl_sync(0xffffffffu, z, c);
-        if (lane < c) z -= ld[c][lane] * zc;
+      const double v = lane < nb ? sh[jb + lane] : 0.0;
+      double z0 = 0.0, z1 = 0.0;
+#pragma unroll
+      for (int t = 0; t < NBK; t += 2) {
+        z0 += ld[t][lane] * __shfl_sync(0xffffffffu, v, t);
+        z1 += ld[t + 1][lane] * __shfl_sync(0xffffffffu, v, t + 1);
       }
-      if (lane < nb) sh[jb + lane] = z;
+      if (lane < nb) sh[jb + lane] = z0 + z1;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < jb; i += blockDim.x) {
@@ -382,20 +472,33 @@ cudaError_t launch_cholesky(const sfft_plan_s* p, const double* A, void* ws) {
   double* Lf = ws_at<double>(ws, p->lfac);
   double* scale = ws_at<double>(ws, p->scale);
   int* status = ws_at<int>(ws, p->status);
+  double* dinv = ws_at<double>(ws, p->dinv);
+  GridBar* bar = ws_at<GridBar>(ws, p->gbar);
   dim3 gi(64, B);
   k_chol_init<<<gi, 256, 0, p->stream>>>(A, Lf, scale, status, N);
-  p->nlaunch += 1;
-  for (int kb = 0; kb < N; kb += NBK) {
-    const int nb = N - kb < NBK ? N - kb : NBK;
-    const int rem = N - kb - nb;
-    const int T = (rem + NBK - 1) / NBK;
-    k_chol_panel<<<dim3(T > 0 ? T : 1, B), NBK, 0, p->stream>>>(Lf, status, N, kb);
-    p->nlaunch += 1;
-    if (rem > 0) {
-      k_chol_update<<<dim3(T * (T + 1) / 2, B), 256, 0, p->stream>>>(Lf, N, kb);
-      p->nlaunch += 1;
-    }
-  }
+  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBar), p->stream);
+  if (e != cudaSuccess) return e;
+  // every CTA of the cooperative grid must be resident at once
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_coop, 256, 0);
+  const int T0 = (N - NBK + NBK - 1) / NBK;
+  const int want = std::max(B, B * T0 * (T0 + 1) / 2);
+  const int grid = std::max(1, std::min(want, sms * std::max(per_sm, 1)));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = p->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, k_chol_coop, Lf, dinv, status, N, B, bar);
+  p->nlaunch += 2;
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -403,8 +506,9 @@ cudaError_t launch_chol_solve(const sfft_plan_s* p, const double* rhs, double* x
   const int N = p->N;
   const size_t smem = sizeof(double) * N;
   cudaFuncSetAttribute(k_chol_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_chol_solve<<<p->d.batch, 1024, smem, p->stream>>>(ws_at<double>(ws, p->lfac), ws_at<double>(ws, p->scale), rhs,
-                                                      x, N, ws_at<int>(ws, p->status));
+  k_chol_solve<<<p->d.batch, 1024, smem, p->stream>>>(ws_at<double>(ws, p->lfac), ws_at<double>(ws, p->dinv),
+                                                      ws_at<double>(ws, p->scale), rhs, x, N,
+                                                      ws_at<int>(ws, p->status));
   p->nlaunch += 1;
   return cudaGetLastError();
 }

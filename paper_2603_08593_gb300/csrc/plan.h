@@ -37,7 +37,7 @@ struct sfft_plan_s {
   int n_wa = 0;                       // weight spectra a = 0 .. n_wa-1
   int n_hd = 0;                       // half-plane differences
   std::vector<int2> dlist;            // (dy, dx) per half-plane difference
-  int d_batch = 0, rows_per_cta = 0, ktile = 128;
+  int d_batch = 0, rows_per_cta = 0, csplit = 2;   // csplit: lag parts per (k-slot, group) in the contraction
   double tuned_ms = 0.0;              // autotuned build_normal time per CCD (0: not tuned)
   size_t elem = 4;                    // sizeof(T)
   // plan-owned constant device tables
@@ -56,7 +56,7 @@ struct sfft_plan_s {
   int kb_first = 0, kb_count = 0, bk_first = 0, bk_count = 0;
   // workspace regions (per-CCD strides where noted)
   sfft::Region sky, skyacc, good, gh, mfit, rowflag, rm, wspec, uspec, rhat, phat, gkk, gkb, gbk,
-      mom_bb, mom_b, eimg, lfac, scale, vec, theta_off, status;
+      mom_bb, mom_b, eimg, lfac, scale, dinv, gbar, vec, theta_off, status;
   size_t ws_bytes = 0;
   // graph cache for sfft_subtract
   std::map<std::vector<uintptr_t>, cudaGraphExec_t> graphs;
@@ -81,7 +81,8 @@ cudaError_t launch_rfft_rm(const sfft_plan_s* p, void* ws);
 cudaError_t launch_rfft_weights(const sfft_plan_s* p, const float* S, const void* eimg, int a0, int na,
                                 void* out, int nslab, void* ws);
 cudaError_t launch_rfft_prod(const sfft_plan_s* p, int d0, int nd, void* ws);
-cudaError_t launch_contract(const sfft_plan_s* p, int DM, int job0, int njobs, int rows_per_cta, int ktile, void* ws);
+cudaError_t launch_contract(const sfft_plan_s* p, int DM, int job0, int njobs, int rows_per_cta, int lag_parts,
+                            void* ws);
 cudaError_t launch_scatter(const sfft_plan_s* p, double* A, double* b, void* ws, bool rhs_only, double* rhs_out);
 cudaError_t launch_cholesky(const sfft_plan_s* p, const double* A, void* ws);
 cudaError_t launch_chol_solve(const sfft_plan_s* p, const double* rhs, double* x, void* ws);
@@ -101,7 +102,7 @@ cudaError_t launch_apply_raw(cudaStream_t s, bool fp64, const float* R, const fl
 void set_last_error(const char* msg);
 // Times candidate (d_batch, rows_per_cta) on synthetic data (autotune.cu).
 sfft_status_t autotune_tiles(const sfft_desc_t& d, cudaStream_t s, int d_batch_max, int* d_batch, int* rows_per_cta,
-                             double* ms_per_ccd);
+                             int* lag_parts, double* ms_per_ccd);
 
 template <typename T> inline T* ws_at(void* ws, const Region& r) {
   return reinterpret_cast<T*>(static_cast<char*>(ws) + r.off);
