@@ -224,6 +224,50 @@ def _max_over_ranks(dist, dev, x):
     return float(t.item())
 
 
+CNN_FWD_FLOP = 2.0 * (961 * 27 * 32 + 225 * 288 * 64 + 49 * 576 * 64 + 576 * 128 + 128)   # per stamp
+
+
+def time_classifier(dev, n_infer=32768, batch=256, steps=40):
+    """Stamp-classifier throughput on synthetic 31 x 31 x 3 stamps: inference
+    (normalise + forward + sigmoid) and training steps (forward, backward, Adam),
+    CUDA-event timed; flop rates count the network's multiply-adds only."""
+    import torch
+    from paper_2603_08593_gb300 import RBModel
+    from synth.stamps import make_stamps
+    d = make_stamps(4096, seed=77)
+    base = torch.from_numpy(d["stamps"]).to(dev)
+    lab = torch.from_numpy(d["labels"]).to(dev)
+    stamps = base.repeat((n_infer + 4095) // 4096, 1, 1, 1)[:n_infer].contiguous()
+    m = RBModel(max_batch=4096, seed=1)
+    out = torch.empty(n_infer, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream(dev)
+    m.score(stamps, out=out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(3):
+        m.score(stamps, out=out)
+    e1.record(st)
+    e1.synchronize()
+    inf_s = e0.elapsed_time(e1) / 1e3 / 3
+    tb = base[:batch].contiguous()
+    tl = lab[:batch].contiguous()
+    loss = torch.empty(1, dtype=torch.float32, device=dev)
+    m.train_step(tb, tl, 1e-3, loss=loss)
+    e0.record(st)
+    for _ in range(steps):
+        m.train_step(tb, tl, 1e-3, loss=loss)
+    e1.record(st)
+    e1.synchronize()
+    tr_s = e0.elapsed_time(e1) / 1e3 / steps
+    inf_rate = n_infer / inf_s
+    return {"inference_stamps_per_s": inf_rate, "train_stamps_per_s": batch / tr_s,
+            "inference_tflops": inf_rate * CNN_FWD_FLOP / 1e12,
+            "train_tflops": 3 * CNN_FWD_FLOP * batch / tr_s / 1e12,
+            "note": f"synthetic stamps; inference on {n_infer} stamps in batches of 4096, training batch {batch}; "
+                    "BF16 mma.sync GEMMs with FP32 accumulation, flops = network multiply-adds x 2 "
+                    "(training = 3 x forward)"}
+
+
 def run_gpu(args):
     import torch
     from paper_2603_08593_gb300 import Plan
@@ -341,6 +385,10 @@ def run_gpu(args):
                 "note": "plain FP64 GPU path (FP64 FFTs, products and contraction), sequential single-CCD calls"}
         del p64, o64
 
+    classifier = None
+    if not args.no_classifier and rank == 0:
+        classifier = time_classifier(dev)
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -384,7 +432,7 @@ def run_gpu(args):
                        "tiles": {"d_batch": tiles[0], "rows_per_cta": tiles[1], "lag_parts": tiles[2]},
                        "l2": "256 MB buffer written between timed steps (L2 flushed)"},
             "roofline": roof, "cpu_baseline": cpu_base, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clocks, "status": info, "wall_s": wall, "fp64_path": fp64,
+            "clocks": clocks, "status": info, "wall_s": wall, "fp64_path": fp64, "classifier": classifier,
             "phases_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -409,6 +457,7 @@ def main():
     ap.add_argument("--d-batch", type=int, default=0, help="offset differences per workspace slab (0: plan default)")
     ap.add_argument("--fp64-steps", type=int, default=2, help="CCDs timed on the plain FP64 path for comparison")
     ap.add_argument("--no-autotune", action="store_true", help="plan defaults instead of plan-time tile tuning")
+    ap.add_argument("--no-classifier", action="store_true", help="skip the stamp-classifier throughput figures")
     ap.add_argument("--lag-parts", type=int, default=0, choices=[0, 2, 3], help="contraction lag parts (0: plan's)")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -123,10 +123,12 @@ k_chol_init(const double* __restrict__ A, double* __restrict__ Lf, double* __res
 // ---------------------------------------------------------------- persistent blocked Cholesky
 // One cooperative launch factors every CCD's matrix.  For each 32-column
 // block k: (A) one CTA per CCD factors the diagonal block in shared memory and
-// inverts the factor; (B) all CTAs take 256-row slices of the panels below the
+// inverts the factor; (B) all CTAs take 32-row tiles of the panels below the
 // diagonal blocks and multiply them by the transposed inverse (the panel
 // triangular solve as a product); (C) all CTAs take 32 x 32 tiles of the
-// trailing lower triangles and subtract P_i P_j^T.  The phases are separated
+// trailing lower triangles and subtract P_i P_j^T, and the CTA that updates
+// the next diagonal block factors it at once (A of step k + 1, overlapped
+// with the rest of C).  The phases are separated
 // by a grid-wide barrier whose waits are bounded: a barrier that gives up (or
 // sees another CTA give up) flags every CCD with bit 4 and the kernel returns.
 // The inverses of the diagonal blocks are kept for the substitutions.  Data
@@ -223,85 +225,89 @@ k_chol_coop(double* __restrict__ Lf, double* __restrict__ dinv, int* __restrict_
   const int nblk = (N + NBK - 1) / NBK;
   const int64_t NN = (int64_t)N * N;
   const int tid = threadIdx.x;
-  for (int k = 0; k < nblk; ++k) {
+  // (A) of block 0; later diagonal blocks are factored as soon as their last
+  // trailing update lands (look-ahead inside phase C)
+  for (int ccd = blockIdx.x; ccd < B; ccd += gridDim.x) {
+    __syncthreads();
+    factor_diag(Lf + ccd * NN, dinv + (int64_t)ccd * nblk * NBK * NBK, status + ccd, N, 0, min(NBK, N), sa, sb, rinv);
+  }
+  bool ok = grid_sync_bounded(bar, &flag);
+  for (int k = 0; ok && k < nblk; ++k) {
     const int kb = k * NBK, nb = min(NBK, N - kb), rem = N - kb - nb;
-    // (A) diagonal blocks
-    for (int ccd = blockIdx.x; ccd < B; ccd += gridDim.x) {
-      __syncthreads();
-      factor_diag(Lf + ccd * NN, dinv + ((int64_t)ccd * nblk + k) * NBK * NBK, status + ccd, N, kb, nb, sa, sb, rinv);
-    }
-    if (!grid_sync_bounded(bar, &flag)) break;
+    if (rem <= 0) break;   // uniform: the last block has no panel
     // (B) panels, 32-row tiles: X = A inv(L_kk)^T; thread (row tid / 8, columns tid % 8 + 8 m)
-    if (rem > 0) {
-      const int T = (rem + NBK - 1) / NBK;
-      for (int item = blockIdx.x; item < B * T; item += gridDim.x) {
-        const int ccd = item / T, r0 = kb + nb + (item % T) * NBK;
-        double* l = Lf + ccd * NN;
-        const double* iv = dinv + ((int64_t)ccd * nblk + k) * NBK * NBK;
-        __syncthreads();
-        for (int e = tid; e < NBK * NBK; e += blockDim.x) {
-          const int i = e / NBK, c = e % NBK;
-          sb[i][c] = __ldcg(iv + e);
-          sa[i][c] = (r0 + i < N && c < nb) ? __ldcg(l + (int64_t)(r0 + i) * N + kb + c) : 0.0;
-        }
-        __syncthreads();
-        const int i = tid >> 3, c0 = tid & 7;
-        double out[4];
+    const int T = (rem + NBK - 1) / NBK;
+    for (int item = blockIdx.x; item < B * T; item += gridDim.x) {
+      const int ccd = item / T, r0 = kb + nb + (item % T) * NBK;
+      double* l = Lf + ccd * NN;
+      const double* iv = dinv + ((int64_t)ccd * nblk + k) * NBK * NBK;
+      __syncthreads();
+      for (int e = tid; e < NBK * NBK; e += blockDim.x) {
+        const int i = e / NBK, c = e % NBK;
+        sb[i][c] = __ldcg(iv + e);
+        sa[i][c] = (r0 + i < N && c < nb) ? __ldcg(l + (int64_t)(r0 + i) * N + kb + c) : 0.0;
+      }
+      __syncthreads();
+      const int i = tid >> 3, c0 = tid & 7;
+      double out[4];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const int c = c0 + 8 * m;
-          double s0 = 0.0, s1 = 0.0;
-          for (int t = 0; t + 1 <= c; t += 2) {
-            s0 += sa[i][t] * sb[c][t];
-            s1 += sa[i][t + 1] * sb[c][t + 1];
-          }
-          if ((c & 1) == 0) s0 += sa[i][c] * sb[c][c];
-          out[m] = s0 + s1;
+      for (int m = 0; m < 4; ++m) {
+        const int c = c0 + 8 * m;
+        double s0 = 0.0, s1 = 0.0;
+        for (int t = 0; t + 1 <= c; t += 2) {
+          s0 += sa[i][t] * sb[c][t];
+          s1 += sa[i][t + 1] * sb[c][t + 1];
         }
-        __syncthreads();
+        if ((c & 1) == 0) s0 += sa[i][c] * sb[c][c];
+        out[m] = s0 + s1;
+      }
+      __syncthreads();
 #pragma unroll
-        for (int m = 0; m < 4; ++m) sa[i][c0 + 8 * m] = out[m];
-        __syncthreads();
-        for (int e = tid; e < NBK * NBK; e += blockDim.x) {
-          const int ii = e / NBK, c = e % NBK;
-          if (r0 + ii < N && c < nb) l[(int64_t)(r0 + ii) * N + kb + c] = sa[ii][c];
-        }
+      for (int m = 0; m < 4; ++m) sa[i][c0 + 8 * m] = out[m];
+      __syncthreads();
+      for (int e = tid; e < NBK * NBK; e += blockDim.x) {
+        const int ii = e / NBK, c = e % NBK;
+        if (r0 + ii < N && c < nb) l[(int64_t)(r0 + ii) * N + kb + c] = sa[ii][c];
       }
     }
-    if (!grid_sync_bounded(bar, &flag)) break;
-    // (C) trailing update of the lower tiles
-    if (rem > 0) {
-      const int T = (rem + NBK - 1) / NBK, ntile = T * (T + 1) / 2;
-      const int r0 = kb + nb;
-      for (int item = blockIdx.x; item < B * ntile; item += gridDim.x) {
-        const int ccd = item / ntile;
-        int t = item % ntile, bi = 0;
-        while (t > bi) { t -= bi + 1; ++bi; }
-        const int bj = t;
-        const int i0 = r0 + bi * NBK, j0 = r0 + bj * NBK;
-        double* l = Lf + ccd * NN;
-        __syncthreads();
-        for (int e = tid; e < NBK * NBK; e += blockDim.x) {
-          const int i = e / NBK, c = e % NBK;
-          sa[i][c] = (i0 + i < N && c < nb) ? __ldcg(l + (int64_t)(i0 + i) * N + kb + c) : 0.0;
-          sb[i][c] = (j0 + i < N && c < nb) ? __ldcg(l + (int64_t)(j0 + i) * N + kb + c) : 0.0;
-        }
-        __syncthreads();
-        for (int e = tid; e < NBK * NBK; e += blockDim.x) {
-          const int i = e / NBK, j = e % NBK;
-          const int gi = i0 + i, gj = j0 + j;
-          if (gi >= N || gj >= N || gj > gi) continue;
-          double s0 = 0.0, s1 = 0.0;
+    if (!(ok = grid_sync_bounded(bar, &flag))) break;
+    // (C) trailing update of the lower tiles; the CTA holding tile (0, 0), the
+    // next diagonal block, factors it right after its update
+    const int ntile = T * (T + 1) / 2;
+    const int r0 = kb + nb;
+    for (int item = blockIdx.x; item < B * ntile; item += gridDim.x) {
+      const int ccd = item / ntile;
+      int t = item % ntile, bi = 0;
+      while (t > bi) { t -= bi + 1; ++bi; }
+      const int bj = t;
+      const int i0 = r0 + bi * NBK, j0 = r0 + bj * NBK;
+      double* l = Lf + ccd * NN;
+      __syncthreads();
+      for (int e = tid; e < NBK * NBK; e += blockDim.x) {
+        const int i = e / NBK, c = e % NBK;
+        sa[i][c] = (i0 + i < N && c < nb) ? __ldcg(l + (int64_t)(i0 + i) * N + kb + c) : 0.0;
+        sb[i][c] = (j0 + i < N && c < nb) ? __ldcg(l + (int64_t)(j0 + i) * N + kb + c) : 0.0;
+      }
+      __syncthreads();
+      for (int e = tid; e < NBK * NBK; e += blockDim.x) {
+        const int i = e / NBK, j = e % NBK;
+        const int gi = i0 + i, gj = j0 + j;
+        if (gi >= N || gj >= N || gj > gi) continue;
+        double s0 = 0.0, s1 = 0.0;
 #pragma unroll 8
-          for (int c = 0; c < NBK; c += 2) {
-            s0 += sa[i][c] * sb[j][c];
-            s1 += sa[i][c + 1] * sb[j][c + 1];
-          }
-          l[(int64_t)gi * N + gj] = __ldcg(l + (int64_t)gi * N + gj) - (s0 + s1);
+        for (int c = 0; c < NBK; c += 2) {
+          s0 += sa[i][c] * sb[j][c];
+          s1 += sa[i][c + 1] * sb[j][c + 1];
         }
+        l[(int64_t)gi * N + gj] = __ldcg(l + (int64_t)gi * N + gj) - (s0 + s1);
+      }
+      if (bi == 0) {   // tile (0, 0): the diagonal block of step k + 1 is final
+        __syncthreads();
+        factor_diag(l, dinv + ((int64_t)ccd * nblk + k + 1) * NBK * NBK, status + ccd, N, r0, min(NBK, N - r0),
+                    sa, sb, rinv);
       }
     }
-    if (!grid_sync_bounded(bar, &flag)) break;
+    ok = grid_sync_bounded(bar, &flag);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0 && ((volatile GridBar*)bar)->abort != 0u)
     for (int c = 0; c < B; ++c) atomicOr(&status[c], 4);
