@@ -39,8 +39,8 @@ WORKLOAD = ("one DECam CCD pair per GPU per step: 2048x4096 FP32, 20k stars, PSF
 # differences), from a one-pass ncu capture of the benchmark workload
 # (profiles/dram_per_kernel_*.md); reported only while the kernel source is the
 # one that was measured.
-KK_TRAFFIC_BYTES = 10.05e9
-KK_TRAFFIC_SOURCE_SHA256_16 = "ac58c028e66f4353"
+KK_TRAFFIC_BYTES = 10.066e9
+KK_TRAFFIC_SOURCE_SHA256_16 = "c6ab6cfcea4ede82"
 PHASES = ("prep", "fft_weights", "fft_prod", "contract_kk", "contract_rk", "scatter", "solve", "apply")
 
 
