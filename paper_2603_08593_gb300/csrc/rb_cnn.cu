@@ -1,14 +1,16 @@
 // Stamp real-bogus classifier: BF16 tensor-core training and inference.
 //
-// Activations are NHWC.  Every convolution is an explicit im2col followed by
-// one GEMM C[M][N] = A[M][K] B[K][N] (+ bias) on mma.sync m16n8k16 BF16 with
-// FP32 accumulation; the backward pass reuses the same GEMM with transposed
-// operands (weight gradients: cols^T dZ; input gradients: dZ W^T then a
-// gather col2im).  Master weights, gradients and Adam moments are FP32 and
-// stored in GEMM layout: conv weights as [(ky*3 + kx)*cin + ci][cout] (conv1
-// padded from K = 27 to 32 with zero rows), the 576 -> 128 layer as
-// [(i*3 + j)*64 + c][128]; rb_set/get_weights convert from/to the
-// [cout][cin][ky][kx] and channel-major flatten order of the C ABI.
+// Activations are NHWC.  Every convolution is an implicit GEMM (rb_gemm.cuh:
+// no im2col matrix is written) on mma.sync m16n8k16 BF16 with FP32
+// accumulation: forward  Z[pixel][co] = sum_k x(pixel + tap)[ci] W[k][co];
+// weight gradient  dW[k][co] = sum_pixel dZ[pixel][co] x(pixel + tap)[ci]
+// (split over pixels, partial sums added in a fixed order); input gradient
+// dX[pixel][ci] = sum_(tap, co) dZ(pixel - tap)[co] W[(tap, ci)][co].  Master
+// weights, gradients and Adam moments are FP32 and stored in GEMM layout:
+// conv weights as [(ky*3 + kx)*cin + ci][cout] (conv1 padded from K = 27 to
+// 32 with zero rows), the 576 -> 128 layer as [(i*3 + j)*64 + c][128];
+// rb_set/get_weights convert from/to the [cout][cin][ky][kx] and
+// channel-major flatten order of the C ABI.
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -23,6 +25,7 @@
 #include "common.cuh"
 #include "plan.h"
 #include "rb.h"
+#include "rb_gemm.cuh"
 
 namespace {
 
@@ -36,102 +39,7 @@ constexpr int OW1 = 0, OB1 = OW1 + K1 * C1, OW2 = OB1 + C1, OB2 = OW2 + K2 * C2,
               OB3 = OW3 + K3 * C3, OW4 = OB3 + C3, OB4 = OW4 + K4 * F4, OW5 = OB4 + F4, OB5 = OW5 + F4,
               NMASTER = OB5 + 1;
 
-// ---------------------------------------------------------------- GEMM
-// C[M][N] (FP32, row-major, ldc) = op(A)[M][K] op(B)[K][N] (+ bias[N]).
-// op(A)(m, k) = transA ? A[k * lda + m] : A[m * lda + k]; same for B.
-constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-__global__ void __launch_bounds__(128)
-k_gemm_bf16(int M, int N, int K, int kchunk, const bf16* __restrict__ A, int lda, int transA,
-            const bf16* __restrict__ B, int ldb, int transB, float* __restrict__ C, int ldc,
-            const float* __restrict__ bias) {
-  __shared__ __align__(16) bf16 As[GBM][GBK + GPAD];
-  __shared__ __align__(16) bf16 Bs[GBN][GBK + GPAD];   // [n][k]
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int g = lane >> 2, t = lane & 3;
-  const int wm = warp >> 1, wn = warp & 1;
-  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-  const bf16 zero = __float2bfloat16(0.f);
-  // split-K: CTA z covers k in [z * kchunk, min(K, (z + 1) * kchunk)) and writes its own C slice
-  const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
-  C += (int64_t)blockIdx.z * M * ldc;
-  for (int k0 = kbeg; k0 < kend; k0 += GBK) {
-    for (int e = tid; e < GBM * GBK; e += 128) {
-      int mm, kk;
-      if (transA) { kk = e / GBM; mm = e % GBM; } else { mm = e / GBK; kk = e % GBK; }
-      const int gm = m0 + mm, gk = k0 + kk;
-      bf16 v = zero;
-      if (gm < M && gk < kend) v = transA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk];
-      As[mm][kk] = v;
-    }
-    for (int e = tid; e < GBN * GBK; e += 128) {
-      int nn, kk;
-      if (transB) { nn = e / GBK; kk = e % GBK; } else { kk = e / GBN; nn = e % GBN; }
-      const int gn = n0 + nn, gk = k0 + kk;
-      bf16 v = zero;
-      if (gn < N && gk < kend) v = transB ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn];
-      Bs[nn][kk] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < GBK; kk += 16) {
-      uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r = wm * 32 + i * 16;
-        af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r + g][kk + 2 * t]);
-        af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + g + 8][kk + 2 * t]);
-        af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r + g][kk + 8 + 2 * t]);
-        af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + g + 8][kk + 8 + 2 * t]);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = wn * 32 + j * 8;
-        bfr[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[c + g][kk + 2 * t]);
-        bfr[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[c + g][kk + 8 + 2 * t]);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int r = m0 + wm * 32 + i * 16 + g, c = n0 + wn * 32 + j * 8 + 2 * t;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int rr = r + (q >= 2 ? 8 : 0), cc = c + (q & 1);
-        if (rr < M && cc < N) C[(int64_t)rr * ldc + cc] = acc[i][j][q] + (bias ? bias[cc] : 0.f);
-      }
-    }
-}
-
-cudaError_t gemm(cudaStream_t s, int M, int N, int K, const bf16* A, int lda, int transA, const bf16* B, int ldb,
-                 int transB, float* C, int ldc, const float* bias) {
-  dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
-  k_gemm_bf16<<<grid, 128, 0, s>>>(M, N, K, K, A, lda, transA, B, ldb, transB, C, ldc, bias);
-  return cudaGetLastError();
-}
-
+// ---------------------------------------------------------------- GEMM launchers
 constexpr int kMaxSplits = 64;
 
 __global__ void k_sum_splits(const float* __restrict__ part, int splits, int64_t mn, float* __restrict__ out) {
@@ -142,24 +50,45 @@ __global__ void k_sum_splits(const float* __restrict__ part, int splits, int64_t
   }
 }
 
-// C[M][N] (contiguous, no bias) for a long reduction dimension: the K range is
-// split over CTAs into fixed slices of `part` (kMaxSplits * M * N floats) that a
-// second kernel sums in a fixed order, so results do not depend on scheduling.
-cudaError_t gemm_splitk(cudaStream_t s, int M, int N, int K, const bf16* A, int lda, int transA, const bf16* B,
-                        int ldb, int transB, float* C, float* part) {
-  const int tiles = ((N + GBN - 1) / GBN) * ((M + GBM - 1) / GBM);
-  int splits = std::min({(K + 2047) / 2048, kMaxSplits, std::max(1, 2 * 152 / tiles)});
-  splits = std::max(splits, 1);
-  if (splits == 1) return gemm(s, M, N, K, A, lda, transA, B, ldb, transB, C, N, nullptr);
-  int kchunk = (K + splits - 1) / splits;
-  kchunk = (kchunk + GBK - 1) / GBK * GBK;
-  splits = (K + kchunk - 1) / kchunk;
-  dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM, splits);
-  k_gemm_bf16<<<grid, 128, 0, s>>>(M, N, K, kchunk, A, lda, transA, B, ldb, transB, part, N, nullptr);
-  const int64_t mn = (int64_t)M * N;
-  k_sum_splits<<<(int)std::min<int64_t>((mn + 255) / 256, 1024), 256, 0, s>>>(part, splits, mn, C);
+// C = A B (+ bias): A K-major (rows = M), B outer-major (rows = K) or K-major (rows = N)
+template <class LA, class LB, bool B_KM>
+cudaError_t igemm(cudaStream_t s, int M, int N, int K, const LA& la, const LB& lb, float* C, int ldc,
+                  const float* bias) {
+  dim3 grid((N + rbg::BN - 1) / rbg::BN, (M + rbg::BM - 1) / rbg::BM, 1);
+  rbg::k_igemm<LA, LB, true, B_KM, false><<<grid, 256, 0, s>>>(M, N, K, K, la, lb, C, ldc, 0, bias);
   return cudaGetLastError();
 }
+
+// Weight gradient G[n][m] (ldc = M) = sum_k A[k][m] B[k][n] over a long k
+// (pixels or stamps): both operands outer-major, split over k into fixed
+// slices of `part` (kMaxSplits * M * N floats) summed in a fixed order.
+template <class LA, class LB>
+cudaError_t igemm_wgrad(cudaStream_t s, int M, int N, int K, const LA& la, const LB& lb, float* G, float* part) {
+  const int tiles = ((N + rbg::BN - 1) / rbg::BN) * ((M + rbg::BM - 1) / rbg::BM);
+  int splits = std::min({(K + 1023) / 1024, kMaxSplits, std::max(1, 2 * 152 / tiles)});
+  splits = std::max(splits, 1);
+  int kchunk = (K + splits - 1) / splits;
+  kchunk = (kchunk + rbg::BK - 1) / rbg::BK * rbg::BK;
+  splits = (K + kchunk - 1) / kchunk;
+  dim3 grid((N + rbg::BN - 1) / rbg::BN, (M + rbg::BM - 1) / rbg::BM, splits);
+  const int64_t mn = (int64_t)M * N;
+  float* dst = splits == 1 ? G : part;
+  rbg::k_igemm<LA, LB, false, false, true><<<grid, 256, 0, s>>>(M, N, K, kchunk, la, lb, dst, M, mn, nullptr);
+  if (splits > 1)
+    k_sum_splits<<<(int)std::min<int64_t>((mn + 255) / 256, 1024), 256, 0, s>>>(part, splits, mn, G);
+  return cudaGetLastError();
+}
+
+// B operand of the input gradient: row = ci, k = (tap, co) -> W[(tap * cin + ci)][co .. co + 7]
+struct ConvW {
+  const bf16* w;
+  int cin, cout;
+  __device__ __forceinline__ uint4 row8(int ci, int k) const {
+    if (ci >= cin || k >= 9 * cout) return rbg::zero4();
+    const int tap = k / cout, co = k - tap * cout;
+    return *reinterpret_cast<const uint4*>(w + ((int64_t)tap * cin + ci) * cout + co);
+  }
+};
 
 // ---------------------------------------------------------------- elementwise kernels
 // per stamp: normalise the three channels (median, 1.4826 MAD, clip) -> NHWC bf16 [31][31][3]
@@ -210,41 +139,6 @@ k_normalise(const float* __restrict__ stamps, bf16* __restrict__ xn) {
       xn[((int64_t)n * PIX1 + i) * 3 + ch] = __float2bfloat16(x);
     }
     __syncthreads();
-  }
-}
-
-// im2col for a 3 x 3 'same' convolution: NHWC x [n][h][w][c] -> cols [n*h*w][kp], k = (ky*3 + kx)*c + ci
-__global__ void k_im2col(const bf16* __restrict__ x, int n, int h, int w, int c, int kp, bf16* __restrict__ cols) {
-  const int64_t total = (int64_t)n * h * w * kp;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int k = (int)(e % kp);
-    const int64_t row = e / kp;
-    bf16 v = __float2bfloat16(0.f);
-    if (k < 9 * c) {
-      const int tap = k / c, ci = k % c, ky = tap / 3, kx = tap % 3;
-      const int xx = (int)(row % w), yy = (int)((row / w) % h), nn = (int)(row / ((int64_t)w * h));
-      const int sy = yy + ky - 1, sx = xx + kx - 1;
-      if (sy >= 0 && sy < h && sx >= 0 && sx < w) v = x[(((int64_t)nn * h + sy) * w + sx) * c + ci];
-    }
-    cols[e] = v;
-  }
-}
-
-// gather col2im: dx[n][y][x][ci] = sum_taps dcols[(n, y-ky+1, x-kx+1)][(ky*3+kx)*c + ci]
-__global__ void k_col2im(const float* __restrict__ dcols, int n, int h, int w, int c, int kp, float* __restrict__ dx) {
-  const int64_t total = (int64_t)n * h * w * c;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int ci = (int)(e % c);
-    const int64_t pix = e / c;
-    const int xx = (int)(pix % w), yy = (int)((pix / w) % h), nn = (int)(pix / ((int64_t)w * h));
-    float s = 0.f;
-    for (int ky = 0; ky < 3; ++ky)
-      for (int kx = 0; kx < 3; ++kx) {
-        const int oy = yy - ky + 1, ox = xx - kx + 1;
-        if (oy >= 0 && oy < h && ox >= 0 && ox < w)
-          s += dcols[(((int64_t)nn * h + oy) * w + ox) * kp + (ky * 3 + kx) * c + ci];
-      }
-    dx[e] = s;
   }
 }
 
@@ -469,19 +363,18 @@ struct rb_model_s {
   float *params = nullptr, *grads = nullptr, *adam_m = nullptr, *adam_v = nullptr;
   bf16* wbf = nullptr;                         // bf16 copy of the master vector
   // activations / scratch for max_batch stamps
-  bf16 *xn = nullptr, *cols = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *dzb = nullptr, *dz4 = nullptr;
+  bf16 *xn = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *dzb = nullptr, *dz4 = nullptr;
   float *z1 = nullptr, *z2 = nullptr, *z3 = nullptr, *z4 = nullptr, *logit = nullptr, *dz5 = nullptr,
-        *dcols = nullptr, *da = nullptr, *part = nullptr;
+        *da = nullptr, *part = nullptr;
   uint8_t *i1 = nullptr, *i2 = nullptr, *i3 = nullptr;
-  size_t cols_elems = 0;
 };
 
 namespace {
 
 void free_model(rb_model_s* m) {
-  void* ptrs[] = {m->params, m->grads, m->adam_m, m->adam_v, m->wbf, m->xn,  m->cols, m->a1,   m->a2,
-                  m->a3,     m->dzb,    m->dz4,    m->z1,  m->z2,  m->z3,   m->z4,   m->logit,
-                  m->dz5,    m->dcols, m->da,     m->part,     m->i1,     m->i2,  m->i3};
+  void* ptrs[] = {m->params, m->grads, m->adam_m, m->adam_v, m->wbf, m->xn,  m->a1,   m->a2,   m->a3,
+                  m->dzb,    m->dz4,   m->z1,     m->z2,     m->z3,  m->z4, m->logit, m->dz5,  m->da,
+                  m->part,   m->i1,    m->i2,     m->i3};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -493,56 +386,74 @@ bool alloc(T** p, size_t n) {
 
 // forward for n <= max_batch normalised stamps in m->xn; logits to m->logit
 cudaError_t forward(rb_model_s* m, int n, cudaStream_t s, bool keep_idx) {
+  using rbg::ConvRows;
+  using rbg::Conv1Rows;
+  using rbg::Dense;
   const bf16* W = m->wbf;
   const float* P = m->params;
   cudaError_t e;
-  // conv1
-  k_im2col<<<grid1((int64_t)n * PIX1 * K1), 256, 0, s>>>(m->xn, n, S31, S31, 3, K1, m->cols);
-  if ((e = gemm(s, n * PIX1, C1, K1, m->cols, K1, 0, W + OW1, C1, 0, m->z1, C1, P + OB1))) return e;
+  // conv1 (3 -> 32): implicit GEMM over the 27 (padded 32) taps x channels
+  if ((e = igemm<Conv1Rows, Dense, false>(s, n * PIX1, C1, K1, Conv1Rows{m->xn, n, S31, S31},
+                                          Dense{W + OW1, K1, C1, C1}, m->z1, C1, P + OB1)))
+    return e;
   k_relu_pool<<<grid1((int64_t)n * PIX2 * C1), 256, 0, s>>>(m->z1, n, S31, S31, C1, m->a1, keep_idx ? m->i1 : nullptr);
-  // conv2
-  k_im2col<<<grid1((int64_t)n * PIX2 * K2), 256, 0, s>>>(m->a1, n, 15, 15, C1, K2, m->cols);
-  if ((e = gemm(s, n * PIX2, C2, K2, m->cols, K2, 0, W + OW2, C2, 0, m->z2, C2, P + OB2))) return e;
+  // conv2 (32 -> 64)
+  if ((e = igemm<ConvRows, Dense, false>(s, n * PIX2, C2, K2, ConvRows{m->a1, n, 15, 15, C1, 1},
+                                         Dense{W + OW2, K2, C2, C2}, m->z2, C2, P + OB2)))
+    return e;
   k_relu_pool<<<grid1((int64_t)n * PIX3 * C2), 256, 0, s>>>(m->z2, n, 15, 15, C2, m->a2, keep_idx ? m->i2 : nullptr);
-  // conv3
-  k_im2col<<<grid1((int64_t)n * PIX3 * K3), 256, 0, s>>>(m->a2, n, 7, 7, C2, K3, m->cols);
-  if ((e = gemm(s, n * PIX3, C3, K3, m->cols, K3, 0, W + OW3, C3, 0, m->z3, C3, P + OB3))) return e;
+  // conv3 (64 -> 64)
+  if ((e = igemm<ConvRows, Dense, false>(s, n * PIX3, C3, K3, ConvRows{m->a2, n, 7, 7, C2, 1},
+                                         Dense{W + OW3, K3, C3, C3}, m->z3, C3, P + OB3)))
+    return e;
   k_relu_pool<<<grid1((int64_t)n * PIX4 * C3), 256, 0, s>>>(m->z3, n, 7, 7, C3, m->a3, keep_idx ? m->i3 : nullptr);
   // fc1 (NHWC flatten of a3 matches the W4 rows) and fc2
-  if ((e = gemm(s, n, F4, K4, m->a3, K4, 0, W + OW4, F4, 0, m->z4, F4, P + OB4))) return e;
+  if ((e = igemm<Dense, Dense, false>(s, n, F4, K4, Dense{m->a3, n, K4, K4}, Dense{W + OW4, K4, F4, F4}, m->z4, F4,
+                                      P + OB4)))
+    return e;
   k_fc2<<<(n * 32 + 255) / 256, 256, 0, s>>>(m->z4, P + OW5, P + OB5, n, m->logit);
   return cudaGetLastError();
 }
 
 cudaError_t backward(rb_model_s* m, int n, const float* labels, float* loss_dev, cudaStream_t s) {
+  using rbg::ConvRows;
+  using rbg::Conv1Rows;
+  using rbg::Dense;
   const bf16* W = m->wbf;
   float* G = m->grads;
   cudaError_t e;
   cudaMemsetAsync(G, 0, sizeof(float) * NMASTER, s);
   k_bce_head<<<1, 1024, 0, s>>>(m->logit, labels, n, m->z4, m->params + OW5, m->dz5, m->dz4, loss_dev);
   k_fc2_grad<<<1, F4, 0, s>>>(m->dz5, m->z4, n, G + OW5, G + OB5);
-  // fc1: dW4 = a3^T dz4, db4 = colsum(dz4), da3 = dz4 W4^T
-  if ((e = gemm_splitk(s, K4, F4, n, m->a3, K4, 1, m->dz4, F4, 0, G + OW4, m->part))) return e;
+  // fc1: dW4[k][co] = sum_i a3[i][k] dz4[i][co], db4 = colsum(dz4), da3 = dz4 W4^T
+  if ((e = igemm_wgrad(s, F4, K4, n, Dense{m->dz4, n, F4, F4}, Dense{m->a3, n, K4, K4}, G + OW4, m->part))) return e;
   k_colsum<<<F4, 256, 0, s>>>(m->dz4, n, F4, G + OB4);
-  if ((e = gemm(s, n, K4, F4, m->dz4, F4, 0, W + OW4, F4, 1, m->da, K4, nullptr))) return e;
+  if ((e = igemm<Dense, Dense, true>(s, n, K4, F4, Dense{m->dz4, n, F4, F4}, Dense{W + OW4, K4, F4, F4}, m->da, K4,
+                                     nullptr)))
+    return e;
   // conv3
   k_pool_relu_back<<<grid1((int64_t)n * PIX3 * C3), 256, 0, s>>>(m->da, m->i3, m->z3, n, 7, 7, C3, m->dzb);
-  k_im2col<<<grid1((int64_t)n * PIX3 * K3), 256, 0, s>>>(m->a2, n, 7, 7, C2, K3, m->cols);
-  if ((e = gemm_splitk(s, K3, C3, n * PIX3, m->cols, K3, 1, m->dzb, C3, 0, G + OW3, m->part))) return e;
+  if ((e = igemm_wgrad(s, C3, K3, n * PIX3, Dense{m->dzb, n * PIX3, C3, C3}, ConvRows{m->a2, n, 7, 7, C2, 1},
+                       G + OW3, m->part)))
+    return e;
   k_colsum<<<C3, 256, 0, s>>>(m->dzb, (int64_t)n * PIX3, C3, G + OB3);
-  if ((e = gemm(s, n * PIX3, K3, C3, m->dzb, C3, 0, W + OW3, C3, 1, m->dcols, K3, nullptr))) return e;
-  k_col2im<<<grid1((int64_t)n * PIX3 * C2), 256, 0, s>>>(m->dcols, n, 7, 7, C2, K3, m->da);
+  if ((e = igemm<ConvRows, ConvW, true>(s, n * PIX3, C2, 9 * C3, ConvRows{m->dzb, n, 7, 7, C3, -1},
+                                        ConvW{W + OW3, C2, C3}, m->da, C2, nullptr)))
+    return e;
   // conv2
   k_pool_relu_back<<<grid1((int64_t)n * PIX2 * C2), 256, 0, s>>>(m->da, m->i2, m->z2, n, 15, 15, C2, m->dzb);
-  k_im2col<<<grid1((int64_t)n * PIX2 * K2), 256, 0, s>>>(m->a1, n, 15, 15, C1, K2, m->cols);
-  if ((e = gemm_splitk(s, K2, C2, n * PIX2, m->cols, K2, 1, m->dzb, C2, 0, G + OW2, m->part))) return e;
+  if ((e = igemm_wgrad(s, C2, K2, n * PIX2, Dense{m->dzb, n * PIX2, C2, C2}, ConvRows{m->a1, n, 15, 15, C1, 1},
+                       G + OW2, m->part)))
+    return e;
   k_colsum<<<C2, 256, 0, s>>>(m->dzb, (int64_t)n * PIX2, C2, G + OB2);
-  if ((e = gemm(s, n * PIX2, K2, C2, m->dzb, C2, 0, W + OW2, C2, 1, m->dcols, K2, nullptr))) return e;
-  k_col2im<<<grid1((int64_t)n * PIX2 * C1), 256, 0, s>>>(m->dcols, n, 15, 15, C1, K2, m->da);
+  if ((e = igemm<ConvRows, ConvW, true>(s, n * PIX2, C1, 9 * C2, ConvRows{m->dzb, n, 15, 15, C2, -1},
+                                        ConvW{W + OW2, C1, C2}, m->da, C1, nullptr)))
+    return e;
   // conv1 (no input gradient)
   k_pool_relu_back<<<grid1((int64_t)n * PIX1 * C1), 256, 0, s>>>(m->da, m->i1, m->z1, n, S31, S31, C1, m->dzb);
-  k_im2col<<<grid1((int64_t)n * PIX1 * K1), 256, 0, s>>>(m->xn, n, S31, S31, 3, K1, m->cols);
-  if ((e = gemm_splitk(s, K1, C1, n * PIX1, m->cols, K1, 1, m->dzb, C1, 0, G + OW1, m->part))) return e;
+  if ((e = igemm_wgrad(s, C1, K1, n * PIX1, Dense{m->dzb, n * PIX1, C1, C1}, Conv1Rows{m->xn, n, S31, S31},
+                       G + OW1, m->part)))
+    return e;
   k_colsum<<<C1, 256, 0, s>>>(m->dzb, (int64_t)n * PIX1, C1, G + OB1);
   return cudaGetLastError();
 }
@@ -564,16 +475,14 @@ extern "C" sfft_status_t rb_create(const int32_t* desc, rb_model_t* out) {
   if (!m) return SFFT_ERR_NOMEM;
   const int B = desc[0];
   m->max_batch = B;
-  const size_t cols = std::max<size_t>({(size_t)B * PIX1 * K1, (size_t)B * PIX2 * K2, (size_t)B * PIX3 * K3});
-  m->cols_elems = cols;
   bool ok = alloc(&m->params, NMASTER) && alloc(&m->grads, NMASTER) && alloc(&m->adam_m, NMASTER) &&
             alloc(&m->adam_v, NMASTER) && alloc(&m->wbf, NMASTER) && alloc(&m->xn, (size_t)B * PIX1 * 3) &&
-            alloc(&m->cols, cols) && alloc(&m->a1, (size_t)B * PIX2 * C1) && alloc(&m->a2, (size_t)B * PIX3 * C2) &&
+            alloc(&m->a1, (size_t)B * PIX2 * C1) && alloc(&m->a2, (size_t)B * PIX3 * C2) &&
             alloc(&m->a3, (size_t)B * PIX4 * C3) &&
             alloc(&m->dzb, (size_t)B * PIX1 * C1) && alloc(&m->dz4, (size_t)B * F4) &&
             alloc(&m->z1, (size_t)B * PIX1 * C1) && alloc(&m->z2, (size_t)B * PIX2 * C2) &&
             alloc(&m->z3, (size_t)B * PIX3 * C3) && alloc(&m->z4, (size_t)B * F4) && alloc(&m->logit, (size_t)B) &&
-            alloc(&m->dz5, (size_t)B) && alloc(&m->dcols, cols) && alloc(&m->da, (size_t)B * PIX2 * C1 + B * K4) &&
+            alloc(&m->dz5, (size_t)B) && alloc(&m->da, (size_t)B * PIX2 * C1 + B * K4) &&
             alloc(&m->i1, (size_t)B * PIX2 * C1) && alloc(&m->i2, (size_t)B * PIX3 * C2) &&
             alloc(&m->i3, (size_t)B * PIX4 * C3) && alloc(&m->part, (size_t)kMaxSplits * K4 * F4);
   if (!ok) {
