@@ -458,8 +458,13 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2, help="CCDs timed on the plain FP64 path for comparison")
     ap.add_argument("--no-autotune", action="store_true", help="plan defaults instead of plan-time tile tuning")
     ap.add_argument("--no-classifier", action="store_true", help="skip the stamp-classifier throughput figures")
+    ap.add_argument("--only-classifier", action="store_true", help="print only the stamp-classifier figures")
     ap.add_argument("--lag-parts", type=int, default=0, choices=[0, 2, 3], help="contraction lag parts (0: plan's)")
     args = ap.parse_args()
+    if args.only_classifier:   # classifier figures alone (profiling captures)
+        import torch
+        print(json.dumps({"classifier": time_classifier(torch.device("cuda", 0))}), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -91,54 +91,68 @@ struct ConvW {
 };
 
 // ---------------------------------------------------------------- elementwise kernels
-// per stamp: normalise the three channels (median, 1.4826 MAD, clip) -> NHWC bf16 [31][31][3]
-__device__ void bitonic_sort_1024(float* v) {
-  for (int k = 2; k <= 1024; k <<= 1)
+// Robust normalisation of one channel of one stamp per warp: the 961 values
+// (padded with +inf to 1024) are sorted in registers by a bitonic network
+// (position p = lane * 32 + r; partner positions in other lanes are reached by
+// shuffles), the median is position 480; the absolute deviations are sorted
+// the same way for the MAD.  x -> clip((x - median) / (1.4826 MAD), +-64),
+// scale 1 when the MAD is 0.  Output NHWC BF16 [n][31][31][3].
+__device__ __forceinline__ void warp_bitonic_1024(float (&v)[32], int lane) {
+#pragma unroll
+  for (int k = 2; k <= 1024; k <<= 1) {
+#pragma unroll
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
-        const int l = i ^ j;
-        if (l > i) {
-          const bool up = (i & k) == 0;
-          const float a = v[i], b = v[l];
-          if ((a > b) == up) { v[i] = b; v[l] = a; }
+      if (j >= 32) {
+        const int lj = j >> 5;
+        const bool lower = (lane & lj) == 0;
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+          const bool up = (((lane * 32 + r) & k) == 0);
+          const float o = __shfl_xor_sync(0xffffffffu, v[r], lj);
+          v[r] = (lower == up) ? fminf(v[r], o) : fmaxf(v[r], o);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+          const int rp = r ^ j;
+          if (rp > r) {
+            const bool up = (((lane * 32 + r) & k) == 0);
+            const float x = v[r], y = v[rp];
+            v[r] = up ? fminf(x, y) : fmaxf(x, y);
+            v[rp] = up ? fmaxf(x, y) : fminf(x, y);
+          }
         }
       }
-      __syncthreads();
     }
+  }
 }
 
 __global__ void __launch_bounds__(256)
-k_normalise(const float* __restrict__ stamps, bf16* __restrict__ xn) {
-  __shared__ float raw[PIX1], v[1024];
-  __shared__ float med_s, scale_s;
-  const int n = blockIdx.x;
-  for (int ch = 0; ch < 3; ++ch) {
-    const float* src = stamps + ((int64_t)n * 3 + ch) * PIX1;
-    for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
-      const float x = i < PIX1 ? src[i] : INFINITY;
-      if (i < PIX1) raw[i] = x;
-      v[i] = x;
-    }
-    __syncthreads();
-    bitonic_sort_1024(v);
-    if (threadIdx.x == 0) med_s = v[480];
-    __syncthreads();
-    const float med = med_s;
-    for (int i = threadIdx.x; i < 1024; i += blockDim.x) v[i] = i < PIX1 ? fabsf(raw[i] - med) : INFINITY;
-    __syncthreads();
-    bitonic_sort_1024(v);
-    if (threadIdx.x == 0) {
-      const float sc = 1.4826f * v[480];
-      scale_s = sc > 0.f ? sc : 1.f;
-    }
-    __syncthreads();
-    const float inv = 1.f / scale_s;
-    for (int i = threadIdx.x; i < PIX1; i += blockDim.x) {
-      float x = (raw[i] - med) * inv;
-      x = fminf(fmaxf(x, -64.f), 64.f);
-      xn[((int64_t)n * PIX1 + i) * 3 + ch] = __float2bfloat16(x);
-    }
-    __syncthreads();
+k_normalise(const float* __restrict__ stamps, int n, bf16* __restrict__ xn) {
+  const int lane = threadIdx.x & 31;
+  const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);   // (stamp, channel)
+  if (item >= 3 * n) return;                                              // whole warps
+  const int st = item / 3, ch = item - 3 * st;
+  const float* src = stamps + ((int64_t)st * 3 + ch) * PIX1;
+  float v[32];
+#pragma unroll
+  for (int r = 0; r < 32; ++r) {
+    const int i = r * 32 + lane;
+    v[r] = i < PIX1 ? src[i] : INFINITY;
+  }
+  warp_bitonic_1024(v, lane);
+  const float med = __shfl_sync(0xffffffffu, v[0], 15);   // position 480
+#pragma unroll
+  for (int r = 0; r < 32; ++r) {
+    const int i = r * 32 + lane;
+    v[r] = i < PIX1 ? fabsf(src[i] - med) : INFINITY;
+  }
+  warp_bitonic_1024(v, lane);
+  const float sc = 1.4826f * __shfl_sync(0xffffffffu, v[0], 15);
+  const float inv = 1.f / (sc > 0.f ? sc : 1.f);
+  for (int i = lane; i < PIX1; i += 32) {
+    const float x = fminf(fmaxf((src[i] - med) * inv, -64.f), 64.f);
+    xn[((int64_t)st * PIX1 + i) * 3 + ch] = __float2bfloat16(x);
   }
 }
 
@@ -241,20 +255,30 @@ __global__ void k_fc2_grad(const float* __restrict__ dz5, const float* __restric
   }
 }
 
-// column sums of a bf16 matrix [rows][cols] into FP32 (bias gradients)
-__global__ void k_colsum(const bf16* __restrict__ x, int64_t rows, int cols, float* __restrict__ out) {
-  const int c = blockIdx.x;
+// column sums of a bf16 matrix [rows][cols] into FP32 (bias gradients), cols
+// dividing 256: each CTA sums a band of rows with coalesced reads into
+// part[blockIdx.x][cols]; the bands are then added in a fixed order.
+__global__ void __launch_bounds__(256)
+k_colsum_part(const bf16* __restrict__ x, int64_t rows, int cols, int64_t band, float* __restrict__ part) {
+  __shared__ float red[256];
+  const int c = threadIdx.x % cols, rp = threadIdx.x / cols, nrp = blockDim.x / cols;
+  const int64_t r0 = blockIdx.x * band, r1 = min(rows, r0 + band);
   float s = 0.f;
-  for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) s += __bfloat162float(x[r * cols + c]);
-  s = sfft::warp_sum(s);
-  __shared__ float red[32];
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  for (int64_t r = r0 + rp; r < r1; r += nrp) s += __bfloat162float(x[r * cols + c]);
+  red[threadIdx.x] = s;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    float t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
-    t = sfft::warp_sum(t);
-    if (threadIdx.x == 0) out[c] = t;
+  if (rp == 0) {
+    for (int q = 1; q < nrp; ++q) s += red[q * cols + c];
+    part[(int64_t)blockIdx.x * cols + c] = s;
   }
+}
+
+cudaError_t colsum(cudaStream_t st, const bf16* x, int64_t rows, int cols, float* part, float* out) {
+  const int nb = (int)std::min<int64_t>(512, (rows + 255) / 256);
+  const int64_t band = (rows + nb - 1) / nb;
+  k_colsum_part<<<nb, 256, 0, st>>>(x, rows, cols, band, part);
+  k_sum_splits<<<1, 256, 0, st>>>(part, nb, cols, out);
+  return cudaGetLastError();
 }
 
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
@@ -427,7 +451,7 @@ cudaError_t backward(rb_model_s* m, int n, const float* labels, float* loss_dev,
   k_fc2_grad<<<1, F4, 0, s>>>(m->dz5, m->z4, n, G + OW5, G + OB5);
   // fc1: dW4[k][co] = sum_i a3[i][k] dz4[i][co], db4 = colsum(dz4), da3 = dz4 W4^T
   if ((e = igemm_wgrad(s, F4, K4, n, Dense{m->dz4, n, F4, F4}, Dense{m->a3, n, K4, K4}, G + OW4, m->part))) return e;
-  k_colsum<<<F4, 256, 0, s>>>(m->dz4, n, F4, G + OB4);
+  if ((e = colsum(s, m->dz4, n, F4, m->part, G + OB4))) return e;
   if ((e = igemm<Dense, Dense, true>(s, n, K4, F4, Dense{m->dz4, n, F4, F4}, Dense{W + OW4, K4, F4, F4}, m->da, K4,
                                      nullptr)))
     return e;
@@ -436,7 +460,7 @@ cudaError_t backward(rb_model_s* m, int n, const float* labels, float* loss_dev,
   if ((e = igemm_wgrad(s, C3, K3, n * PIX3, Dense{m->dzb, n * PIX3, C3, C3}, ConvRows{m->a2, n, 7, 7, C2, 1},
                        G + OW3, m->part)))
     return e;
-  k_colsum<<<C3, 256, 0, s>>>(m->dzb, (int64_t)n * PIX3, C3, G + OB3);
+  if ((e = colsum(s, m->dzb, (int64_t)n * PIX3, C3, m->part, G + OB3))) return e;
   if ((e = igemm<ConvRows, ConvW, true>(s, n * PIX3, C2, 9 * C3, ConvRows{m->dzb, n, 7, 7, C3, -1},
                                         ConvW{W + OW3, C2, C3}, m->da, C2, nullptr)))
     return e;
@@ -445,7 +469,7 @@ cudaError_t backward(rb_model_s* m, int n, const float* labels, float* loss_dev,
   if ((e = igemm_wgrad(s, C2, K2, n * PIX2, Dense{m->dzb, n * PIX2, C2, C2}, ConvRows{m->a1, n, 15, 15, C1, 1},
                        G + OW2, m->part)))
     return e;
-  k_colsum<<<C2, 256, 0, s>>>(m->dzb, (int64_t)n * PIX2, C2, G + OB2);
+  if ((e = colsum(s, m->dzb, (int64_t)n * PIX2, C2, m->part, G + OB2))) return e;
   if ((e = igemm<ConvRows, ConvW, true>(s, n * PIX2, C1, 9 * C2, ConvRows{m->dzb, n, 15, 15, C2, -1},
                                         ConvW{W + OW2, C1, C2}, m->da, C1, nullptr)))
     return e;
@@ -454,7 +478,7 @@ cudaError_t backward(rb_model_s* m, int n, const float* labels, float* loss_dev,
   if ((e = igemm_wgrad(s, C1, K1, n * PIX1, Dense{m->dzb, n * PIX1, C1, C1}, Conv1Rows{m->xn, n, S31, S31},
                        G + OW1, m->part)))
     return e;
-  k_colsum<<<C1, 256, 0, s>>>(m->dzb, (int64_t)n * PIX1, C1, G + OB1);
+  if ((e = colsum(s, m->dzb, (int64_t)n * PIX1, C1, m->part, G + OB1))) return e;
   return cudaGetLastError();
 }
 
@@ -586,7 +610,7 @@ extern "C" sfft_status_t rb_logits(rb_model_t m, const float* stamps, int64_t n,
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (int64_t i0 = 0; i0 < n; i0 += m->max_batch) {
     const int nb = (int)std::min<int64_t>(m->max_batch, n - i0);
-    k_normalise<<<nb, 256, 0, s>>>(stamps + i0 * 3 * PIX1, m->xn);
+    k_normalise<<<(3 * nb + 7) / 8, 256, 0, s>>>(stamps + i0 * 3 * PIX1, nb, m->xn);
     cudaError_t e = forward(m, nb, s, false);
     if (e == cudaSuccess) e = cudaMemcpyAsync(logit + i0, m->logit, sizeof(float) * nb, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return fail(e, "rb_logits");
@@ -607,7 +631,7 @@ extern "C" sfft_status_t rb_backward(rb_model_t m, const float* stamps, const fl
   if (!m || !stamps || !labels || n < 1 || n > m->max_batch) return SFFT_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int nb = (int)n;
-  k_normalise<<<nb, 256, 0, s>>>(stamps, m->xn);
+  k_normalise<<<(3 * nb + 7) / 8, 256, 0, s>>>(stamps, nb, m->xn);
   cudaError_t e = forward(m, nb, s, true);
   if (e == cudaSuccess) e = backward(m, nb, labels, loss_dev, s);
   return e == cudaSuccess ? SFFT_OK : fail(e, "rb_backward");
