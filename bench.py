@@ -459,7 +459,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="plan defaults instead of plan-time tile tuning")
     ap.add_argument("--no-classifier", action="store_true", help="skip the stamp-classifier throughput figures")
     ap.add_argument("--only-classifier", action="store_true", help="print only the stamp-classifier figures")
-    ap.add_argument("--lag-parts", type=int, default=0, choices=[0, 2, 3], help="contraction lag parts (0: plan's)")
+    ap.add_argument("--lag-parts", type=int, default=0, choices=[0, 1, 2, 3], help="contraction lag parts (0: plan's)")
     args = ap.parse_args()
     if args.only_classifier:   # classifier figures alone (profiling captures)
         import torch

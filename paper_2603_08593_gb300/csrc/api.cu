@@ -233,7 +233,7 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
   if (d.H <= 0 || d.W <= 0 || d.batch <= 0 || d.L <= 0) return SFFT_ERR_ARG;
   if (d.prec != SFFT_PREC_FP64 && d.prec != SFFT_PREC_MIXED) return SFFT_ERR_ARG;
   if (d.DK < 0 || d.DB < 0 || d.d_batch < 0 || d.rows_per_cta < 0) return SFFT_ERR_ARG;
-  if (d.lag_parts != 0 && d.lag_parts != 2 && d.lag_parts != 3) return SFFT_ERR_ARG;
+  if (d.lag_parts < 0 || d.lag_parts > 3) return SFFT_ERR_ARG;
   if ((d.L & 1) == 0 || d.L > kMaxL) return SFFT_ERR_UNSUPPORTED;
   if (d.DK > kMaxD || d.DB > kMaxD || d.DB < d.DK) return SFFT_ERR_UNSUPPORTED;
   if (d.H < d.L || d.W < d.L || d.W < 16 || d.W > 2048) return SFFT_ERR_UNSUPPORTED;

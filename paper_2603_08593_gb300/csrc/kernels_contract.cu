@@ -60,7 +60,7 @@ template <typename T, int DM> constexpr int kt_for() { return DM >= 3 ? 32 : 64;
 // register cap per thread: three CTAs of 192 threads (DM >= 3, two lag parts) or of 288
 // threads (three parts), two CTAs of 256 or 384 threads otherwise, fit in 64K registers
 template <typename T, int DM, int NS> constexpr int maxreg_for() {
-  return sizeof(T) == 8 ? 255 : (DM >= 3 ? (NS == 2 ? 96 : 72) : (NS == 2 ? 112 : 80));
+  return sizeof(T) == 8 ? 255 : (NS == 1 ? 168 : (DM >= 3 ? (NS == 2 ? 96 : 72) : (NS == 2 ? 112 : 80)));
 }
 
 // ---------------------------------------------------------------- shared-memory pipeline
@@ -131,17 +131,19 @@ __device__ __forceinline__ void produce_chunk(Stage<T, DM, KT, MU>& st, uint64_t
   const unsigned ybytes = (unsigned)(nv * 64);
   const unsigned fbytes = (unsigned)((kChunk + 4) * sizeof(int));
   const int ncopy = np + (DM + 1) * nv;
-  const int t = threadIdx.x;
-  if (t == 0) mbar_arrive_expect_tx(full, seg * (unsigned)ncopy + ybytes + fbytes);
-  if (t < np) {
-    bulk_copy_g2s(&st.P[t][0], P + (int64_t)(yc - uy_hi + t) * M + k0, seg, full);
-  } else if (t < ncopy) {
-    const int r2 = t - np, a = r2 / nv, yy = r2 - a * nv;
-    bulk_copy_g2s(&st.V[a][yy][0], V + a * HM + (int64_t)(yc + yy) * M + k0, seg, full);
-  } else if (t == ncopy) {
-    bulk_copy_g2s(&st.ypw[0][0], ytab + (int64_t)yc * (64 / sizeof(T)), ybytes, full);
-  } else if (t == ncopy + 1) {
-    bulk_copy_g2s(&st.rf[0], rowflag + (yc & ~3), fbytes, full);
+  if (threadIdx.x == 0) mbar_arrive_expect_tx(full, seg * (unsigned)ncopy + ybytes + fbytes);
+  // every copy registered above is issued, whatever the CTA size
+  for (int t = threadIdx.x; t < ncopy + 2; t += blockDim.x) {
+    if (t < np) {
+      bulk_copy_g2s(&st.P[t][0], P + (int64_t)(yc - uy_hi + t) * M + k0, seg, full);
+    } else if (t < ncopy) {
+      const int r2 = t - np, a = r2 / nv, yy = r2 - a * nv;
+      bulk_copy_g2s(&st.V[a][yy][0], V + a * HM + (int64_t)(yc + yy) * M + k0, seg, full);
+    } else if (t == ncopy) {
+      bulk_copy_g2s(&st.ypw[0][0], ytab + (int64_t)yc * (64 / sizeof(T)), ybytes, full);
+    } else {
+      bulk_copy_g2s(&st.rf[0], rowflag + (yc & ~3), fbytes, full);
+    }
   }
 }
 
@@ -207,6 +209,14 @@ __device__ __forceinline__ float2 lag_load(unsigned p_lo) {
   return lds2<(NLAG - 1 - I) * KT * 8>(p_lo);
 }
 
+template <int NLAG, int KT, int I>
+__device__ __forceinline__ void load_lags(float2 (&pv)[NLAG], unsigned plo) {
+  if constexpr (I < NLAG) {
+    pv[I] = lag_load<NLAG, KT, I>(plo);
+    load_lags<NLAG, KT, I + 1>(pv, plo);
+  }
+}
+
 template <int DM, int KT, int MU, int MH, int G, int NLAG>
 __device__ __forceinline__ void group_chunk_f32(c_t<float> (&acc)[MH][5], const Stage<float, DM, KT, MU>& st, int kk,
                                                 int nrow, int nuy, int lag0, const int* rf) {
@@ -227,15 +237,7 @@ __device__ __forceinline__ void group_chunk_f32(c_t<float> (&acc)[MH][5], const 
                           make_float2(y23.z, y23.w), lds2<32>(ypa)};
     const float2 vlx = make_float2(vl.x, vl.x), vhx = make_float2(vh.x, vh.x);
     float2 pv[NLAG];
-#pragma unroll
-    for (int i = 0; i < NLAG; ++i) {
-      if (i == 0) pv[i] = lag_load<NLAG, KT, 0>(plo);
-      if constexpr (NLAG > 1) { if (i == 1) pv[i] = lag_load<NLAG, KT, (NLAG > 1 ? 1 : 0)>(plo); }
-      if constexpr (NLAG > 2) { if (i == 2) pv[i] = lag_load<NLAG, KT, (NLAG > 2 ? 2 : 0)>(plo); }
-      if constexpr (NLAG > 3) { if (i == 3) pv[i] = lag_load<NLAG, KT, (NLAG > 3 ? 3 : 0)>(plo); }
-      if constexpr (NLAG > 4) { if (i == 4) pv[i] = lag_load<NLAG, KT, (NLAG > 4 ? 4 : 0)>(plo); }
-      if constexpr (NLAG > 5) { if (i == 5) pv[i] = lag_load<NLAG, KT, (NLAG > 5 ? 5 : 0)>(plo); }
-    }
+    load_lags<NLAG, KT, 0>(pv, plo);
 #pragma unroll
     for (int i = 0; i < NLAG; ++i) {
       // conj(V) P = (vx px + vy py, vx py - vy px): one packed product and two FMAs
@@ -302,9 +304,15 @@ __device__ __forceinline__ void chunk_dispatch(c_t<T> (&acc)[MH][5], const Stage
 #define SFFT_NLAG_CASE(NV) \
   case NV: group_chunk_f32<DM, KT, MU, MH, G, NV>(acc, st, kk, nrow, nuy, lag0, rf); break;
       SFFT_NLAG_CASE(1) SFFT_NLAG_CASE(2) SFFT_NLAG_CASE(3) SFFT_NLAG_CASE(4) SFFT_NLAG_CASE(5) SFFT_NLAG_CASE(6)
-#undef SFFT_NLAG_CASE
       default: break;
     }
+    if constexpr (MH > 6) {   // one lag part: up to 11 lags per thread
+      switch (nlag) {
+        SFFT_NLAG_CASE(7) SFFT_NLAG_CASE(8) SFFT_NLAG_CASE(9) SFFT_NLAG_CASE(10) SFFT_NLAG_CASE(11)
+        default: break;
+      }
+    }
+#undef SFFT_NLAG_CASE
   } else {
     if (nlag > 0) group_chunk<T, DM, KT, MU, MH, G, 0>(acc, st, kk, nrow, nuy, lag0, nlag, rf);
   }
@@ -508,6 +516,7 @@ cudaError_t launch_contract(const sfft_plan_s* p, int DM, int job0, int njobs, i
                             void* ws) {
   if (njobs <= 0) return cudaSuccess;
   if (p->fp64) return contract_dm<double, 2>(p, DM, job0, njobs, rows_per_cta, ws);
+  if (lag_parts == 1) return contract_dm<float, 1>(p, DM, job0, njobs, rows_per_cta, ws);
   return lag_parts == 3 ? contract_dm<float, 3>(p, DM, job0, njobs, rows_per_cta, ws)
                         : contract_dm<float, 2>(p, DM, job0, njobs, rows_per_cta, ws);
 }

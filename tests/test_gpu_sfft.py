@@ -83,10 +83,11 @@ def test_mixed_path_within_stated_error(shape, L, DK, DB):
     assert np.abs(D[0] - ref["D"]).max() <= 1e-3 * SIGMA_SKY
 
 
+@pytest.mark.parametrize("parts", [1, 3])
 @pytest.mark.parametrize("shape,L,DK,DB", [((150, 210), 7, 2, 2), ((96, 300), 11, 2, 2), ((56, 2048), 7, 2, 2)])
-def test_mixed_path_three_lag_parts(shape, L, DK, DB):
+def test_mixed_path_other_lag_parts(shape, L, DK, DB, parts):
     d = small_pair(*shape, seed=2500 + shape[1] + L, mask_fraction=0.03)
-    refs, A, b, th, info, D = _run(d, L, DK, DB, "mixed", lag_parts=3)
+    refs, A, b, th, info, D = _run(d, L, DK, DB, "mixed", lag_parts=parts)
     ref = refs[0]
     assert info[0] == 0
     assert np.abs(A[0] - ref["A"]).max() <= 2e-5 * np.abs(ref["A"]).max()
