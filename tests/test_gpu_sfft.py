@@ -181,3 +181,24 @@ def test_autotuned_plan_matches_default_and_is_cached(tmp_path, monkeypatch):
     assert pt2.tiles == pt.tiles
     lines = cache.read_text().strip().splitlines()
     assert len([ln for ln in lines if "_H300_W200_L5_" in ln]) == 1
+
+
+def test_config_c1_single_512_pair():
+    """The 512 x 512 workload (one transient at SNR 20, L = 7, D_K = D_B = 1, no
+    mask): the plain FP64 GPU path and the mixed path against the oracle."""
+    from synth import config_pair
+    d = config_pair("c1")
+    L, DK, DB = 7, 1, 1
+    refs, A, b, th, info, D = _run(d, L, DK, DB, "fp64")
+    ref = refs[0]
+    assert info[0] == 0
+    assert np.abs(th[0] - ref["theta_orig"]).max() <= 1e-8 * np.abs(ref["theta_orig"]).max()
+    assert np.all(np.abs(D[0] - ref["D"]) <= 2.0 ** -24 * np.abs(ref["D"]) + 1e-7 * SIGMA_SKY)
+    _, _, _, th2, info2, D2 = _run(d, L, DK, DB, "mixed")
+    assert info2[0] == 0
+    assert O.kernel_coef_rel_err(th2[0], ref["theta_orig"], L, DK, DB) <= 1e-5
+    assert np.abs(D2[0] - ref["D"]).max() <= 1e-3 * SIGMA_SKY
+    # the injected transient is recovered in D
+    x, y, f = d["transients"][0, :3]
+    half = int(np.ceil(3.0 * d["transients"][0, 4]))
+    assert abs(O.box_flux(D2[0], x, y, half) - O.box_flux(ref["D"], x, y, half)) <= 1e-4 * f
