@@ -1,4 +1,4 @@
-"""ctypes binding over the C ABI in include/sfft.h and include/rb.h.
+"""ctypes binding over the C ABI in include/sfft.h, include/rb.h and include/phot.h.
 
 Argument marshalling only: every step of the subtraction runs in the CUDA
 kernels of libsfft_gb300.so.  PyTorch provides device memory and the stream.
@@ -59,6 +59,11 @@ SIGNATURES = {
     "rb_detect_workspace_bytes": (SZ, [I32, I32, I32, I32]),
     "rb_detect": (I32, [I32, I32, I32, VP, VP, VP, VP, C.c_float, C.c_float, I32, I32, VP, VP, VP, VP, VP, VP]),
     "rb_shape_cuts": (I32, [VP, VP, I64, C.c_float, C.c_float, VP, VP]),
+    # differential photometry and multi-template combination (include/phot.h)
+    "phot_aperture_flux": (I32, [I32, I32, I32, VP, VP, VP, I32, DBL, VP, VP, VP]),
+    "phot_limiting_workspace_bytes": (SZ, [I32, I32]),
+    "phot_limiting_mag": (I32, [I32, I32, I32, VP, VP, VP, I32, DBL, DBL, VP, VP, VP, VP, VP]),
+    "phot_median_combine": (I32, [I32, I32, I32, VP, VP, VP, VP, VP]),
 }
 
 RB_STAMP = 31
@@ -381,4 +386,73 @@ def shape_cuts(stamps, snr, psf_fwhm, snr_min=5.0, out=None, stream=None):
     out = out if out is not None else torch.empty(n, dtype=torch.int32, device=stamps.device)
     _check(load().rb_shape_cuts(_ptr(stamps), _ptr(snr), n, float(psf_fwhm), float(snr_min), _ptr(out),
                                 _stream(stamps, stream)), "rb_shape_cuts")
+    return out
+
+
+# ---------------------------------------------------------------- differential photometry
+def aperture_flux(D, pos, radius, bad=None, stream=None):
+    """Forced aperture fluxes on D [batch][H][W] (float32) at pos [batch][n][2]
+    (float64 x, y): returns (flux float64 [batch][n], flag int32 [batch][n])."""
+    import torch
+    _need(D, torch.float32, "D")
+    _need(pos, torch.float64, "pos")
+    B, H, W = D.shape
+    n = pos.shape[1]
+    if bad is not None:
+        _need(bad, torch.uint8, "bad")
+    flux = torch.empty(B, n, dtype=torch.float64, device=D.device)
+    flag = torch.empty(B, n, dtype=torch.int32, device=D.device)
+    _check(load().phot_aperture_flux(H, W, B, _ptr(D), _ptr(bad), _ptr(pos), n, float(radius), _ptr(flux),
+                                     _ptr(flag), _stream(D, stream)), "phot_aperture_flux")
+    return flux, flag
+
+
+def random_positions(batch, H, W, n=1024, seed=0, margin=16.0, device="cuda"):
+    """The Monte Carlo's background positions, drawn on the host from a seeded
+    generator (uniform over the image, `margin` px from the edges)."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(seed)
+    xy = np.empty((batch, n, 2))
+    xy[..., 0] = rng.uniform(margin, W - 1 - margin, (batch, n))
+    xy[..., 1] = rng.uniform(margin, H - 1 - margin, (batch, n))
+    return torch.from_numpy(xy).to(device)
+
+
+def limiting_mag(D, radius, zp, pos=None, bad=None, n=1024, seed=0, stream=None):
+    """Per-CCD limiting magnitude from aperture fluxes at random positions:
+    returns (sigma, mlim, ngood), each a [batch] tensor."""
+    import torch
+    _need(D, torch.float32, "D")
+    B, H, W = D.shape
+    if pos is None:
+        pos = random_positions(B, H, W, n, seed, device=D.device)
+    _need(pos, torch.float64, "pos")
+    n = pos.shape[1]
+    lib = load()
+    nb = int(lib.phot_limiting_workspace_bytes(B, n))
+    ws = torch.empty(nb + 256, dtype=torch.uint8, device=D.device)
+    off = (-ws.data_ptr()) % 256
+    sigma = torch.empty(B, dtype=torch.float64, device=D.device)
+    mlim = torch.empty(B, dtype=torch.float64, device=D.device)
+    ngood = torch.empty(B, dtype=torch.int32, device=D.device)
+    if bad is not None:
+        _need(bad, torch.uint8, "bad")
+    _check(lib.phot_limiting_mag(H, W, B, _ptr(D), _ptr(bad), _ptr(pos), n, float(radius), float(zp), _ptr(sigma),
+                                 _ptr(mlim), _ptr(ngood), VP(ws.data_ptr() + off), _stream(D, stream)),
+           "phot_limiting_mag")
+    return sigma, mlim, ngood
+
+
+def median_combine(D, scale, bad=None, out=None, stream=None):
+    """Median over templates of scale[t] D[t] ([ntemp][H][W] float32) at good pixels."""
+    import torch
+    _need(D, torch.float32, "D")
+    _need(scale, torch.float32, "scale")
+    T, H, W = D.shape
+    if bad is not None:
+        _need(bad, torch.uint8, "bad")
+    out = out if out is not None else torch.empty(H, W, dtype=torch.float32, device=D.device)
+    _check(load().phot_median_combine(H, W, T, _ptr(D), _ptr(scale), _ptr(bad), _ptr(out), _stream(D, stream)),
+           "phot_median_combine")
     return out
