@@ -456,3 +456,21 @@ def median_combine(D, scale, bad=None, out=None, stream=None):
     _check(load().phot_median_combine(H, W, T, _ptr(D), _ptr(scale), _ptr(bad), _ptr(out), _stream(D, stream)),
            "phot_median_combine")
     return out
+
+
+def multi_template_difference(plan, R, S, bad=None, scale=None, refine=1):
+    """Difference one science image against N_TEMP templates and median-combine
+    the differences: R [T][H][W] templates, S [H][W] science (float32, on the
+    plan's device), bad [T][H][W] or None, scale [T] zero-point factors
+    (float32; ones when None).  The plan's batch must be T.  Returns the
+    combined difference [H][W] and the per-template outputs of Plan.subtract."""
+    import torch
+    T = R.shape[0]
+    if plan.batch != T:
+        raise ValueError("the plan's batch must equal the number of templates")
+    Sx = S.reshape(1, *S.shape).expand(T, -1, -1).contiguous()
+    out = plan.subtract(R, Sx, bad, None, refine=refine)
+    if scale is None:
+        scale = torch.ones(T, dtype=torch.float32, device=R.device)
+    comb = median_combine(out["D"], scale, bad)
+    return comb, out
