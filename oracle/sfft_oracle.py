@@ -29,7 +29,17 @@ Readings where the paper is silent (all listed in the design notes):
   * R_m = good ? R - s_R : 0 (fit), R~ = finite(R) ? R - s_R : 0 (apply,
     zero outside the image), S' = S - s_S, s = median of the good pixels;
   * the background is reported in original units,
-    B = B' + s_S - s_R sum_j K_j(x)  (requires D_B >= D_K).
+    B = B' + s_S - s_R sum_j K_j(x), keeping the terms psi_q can hold
+    (all of them when D_B >= D_K or when the kernel sum is constant; with
+    D_B < D_K and a varying kernel sum the fit is that of the sky-subtracted
+    images and the higher terms of s_R sum_j K_j are dropped).
+
+Constant photometric ratio (the constrained kernel of the delta-basis
+literature the paper cites in Sec. 1): the kernel sum sum_j K_j(x) is one
+constant a_0 over the chip.  Written in the basis
+    K(x) = a_0 delta_0 + sum_{u != 0} sum_p c[u, p] phi_p(x) (delta_u - delta_0)
+it has (L^2 - 1) N_K + 1 + N_B unknowns; fit_const_ratio solves the
+least-squares problem in that basis directly from its design rows.
 
 Two forms of the normal equations are provided:
   normal_definition  (O1) - A and b as the chunked sum of Phi Phi^T, the
@@ -323,14 +333,14 @@ def split_theta(theta, L, DK, DB):
 
 def background_to_original(theta_off, L, DK, DB, s_R, s_S):
     """theta with the background in original units:
-    beta_q + s_S [q == 0] - s_R sum_j theta[j, q]  (psi_q = phi_q for q < N_K)."""
-    if DB < DK:
-        raise ValueError("original-unit background needs D_B >= D_K")
+    beta_q + s_S [q == 0] - s_R sum_j theta[j, q] for q < min(N_K, N_B)
+    (psi_q = phi_q there); the terms of degree above D_B are dropped."""
     th = np.array(theta_off, dtype=np.float64)
     c, beta = split_theta(th, L, DK, DB)
     beta = beta.copy()
+    m = min(n_terms(DK), n_terms(DB))
     beta[0] += s_S
-    beta[:n_terms(DK)] -= s_R * c.sum(axis=0)
+    beta[:m] -= s_R * c.sum(axis=0)[:m]
     th[L * L * n_terms(DK):] = beta
     return th
 
@@ -339,8 +349,9 @@ def background_to_offset(theta_orig, L, DK, DB, s_R, s_S):
     th = np.array(theta_orig, dtype=np.float64)
     c, beta = split_theta(th, L, DK, DB)
     beta = beta.copy()
+    m = min(n_terms(DK), n_terms(DB))
     beta[0] -= s_S
-    beta[:n_terms(DK)] += s_R * c.sum(axis=0)
+    beta[:m] += s_R * c.sum(axis=0)[:m]
     th[L * L * n_terms(DK):] = beta
     return th
 
@@ -388,6 +399,104 @@ def fit(R, S, bad, L, DK, DB, sky=None, form="definition", refine_steps=0):
         theta, st = refine(prep, DK, DB, A, theta)
     out = {"A": A, "b": b, "theta": theta, "status": st, "prep": prep}
     if st == STATUS_OK:
+        out["theta_orig"] = background_to_original(theta, L, DK, DB, prep["s_R"], prep["s_S"])
+        out["D"] = apply(prep, theta, DK, DB)
+    return out
+
+
+# ---------------------------------------------------------------- constant photometric ratio
+def center_index(L):
+    """Index j of the zero offset u = (0, 0)."""
+    return (L * L - 1) // 2
+
+
+def n_unknowns_const_ratio(L, DK, DB):
+    return (L * L - 1) * n_terms(DK) + 1 + n_terms(DB)
+
+
+def const_ratio_design_rows(prep, DK, DB, ys, xs):
+    """Design rows in the constant-ratio basis at pixels (ys, xs): for each
+    offset u_j != 0 (j ascending) and p, phi_p(x) [R_m(x - u_j) - R_m(x)];
+    then R_m(x) (the coefficient a_0 of delta_0); then psi_q(x)."""
+    L, H, W = prep["L"], prep["H"], prep["W"]
+    img = prep["R_m"]
+    xt, yt = norm_coords(H, W)
+    xv, yv = xt[xs], yt[ys]
+    mK, mB = monomials(DK), monomials(DB)
+    NK = len(mK)
+    phi = np.stack([xv ** a * yv ** b for (a, b) in mK], axis=1)
+    psi = np.stack([xv ** a * yv ** b for (a, b) in mB], axis=1)
+    r0 = img[ys, xs]
+    X = np.empty((len(ys), n_unknowns_const_ratio(L, DK, DB)), dtype=np.float64)
+    col = 0
+    for j, (uy, ux) in enumerate(offsets(L)):
+        if j == center_index(L):
+            continue
+        yy, xx = ys - uy, xs - ux
+        inb = (yy >= 0) & (yy < H) & (xx >= 0) & (xx < W)
+        r = np.zeros(len(ys))
+        r[inb] = img[yy[inb], xx[inb]]
+        X[:, col:col + NK] = phi * (r - r0)[:, None]
+        col += NK
+    X[:, col] = r0
+    X[:, col + 1:] = psi
+    return X
+
+
+def normal_const_ratio(prep, DK, DB, chunk_px=1 << 15):
+    """A_c = sum_x M X_c X_c^T and b_c = sum_x M X_c S' in the constant-ratio
+    basis (the definition, chunked over fit pixels)."""
+    ys, xs = np.nonzero(prep["M"])
+    N = n_unknowns_const_ratio(prep["L"], DK, DB)
+    A = np.zeros((N, N))
+    b = np.zeros(N)
+    for s in range(0, len(ys), chunk_px):
+        X = const_ratio_design_rows(prep, DK, DB, ys[s:s + chunk_px], xs[s:s + chunk_px])
+        A += X.T @ X
+        b += X.T @ prep["S_p"][ys[s:s + chunk_px], xs[s:s + chunk_px]]
+    return A, b
+
+
+def const_ratio_to_full(theta_c, L, DK, DB):
+    """Coefficients of the constant-ratio basis -> the full layout theta[j, p]:
+    c[u, p] at u != 0, and at u = 0 the constant a_0 minus sum_{u != 0} c[u, p]."""
+    NK = n_terms(DK)
+    n = (L * L - 1) * NK
+    c = np.asarray(theta_c[:n]).reshape(L * L - 1, NK)
+    full = np.zeros((L * L, NK))
+    jc = center_index(L)
+    full[[j for j in range(L * L) if j != jc]] = c
+    full[jc] = -c.sum(axis=0)
+    full[jc, 0] += theta_c[n]
+    return np.concatenate([full.ravel(), np.asarray(theta_c[n + 1:])])
+
+
+def residual_rhs_const_ratio(prep, DK, DB, theta_c, chunk_px=1 << 15):
+    ys, xs = np.nonzero(prep["M"])
+    r = np.zeros(n_unknowns_const_ratio(prep["L"], DK, DB))
+    for s in range(0, len(ys), chunk_px):
+        X = const_ratio_design_rows(prep, DK, DB, ys[s:s + chunk_px], xs[s:s + chunk_px])
+        r += X.T @ (prep["S_p"][ys[s:s + chunk_px], xs[s:s + chunk_px]] - X @ theta_c)
+    return r
+
+
+def fit_const_ratio(R, S, bad, L, DK, DB, sky=None, refine_steps=0):
+    """The constant-photometric-ratio fit: assemble and solve in the
+    constrained basis, map to the full layout, apply.  Returns a dict with
+    A_c, b_c, theta_c, theta (offset units, full layout), theta_orig, D,
+    status, prep."""
+    prep = prepare(R, S, bad, L, sky)
+    A, b = normal_const_ratio(prep, DK, DB)
+    th, st = solve(A, b)
+    for _ in range(refine_steps):
+        if st != STATUS_OK:
+            break
+        delta, st = solve(A, residual_rhs_const_ratio(prep, DK, DB, th))
+        th = th + delta
+    out = {"A_c": A, "b_c": b, "theta_c": th, "status": st, "prep": prep}
+    if st == STATUS_OK:
+        theta = const_ratio_to_full(th, L, DK, DB)
+        out["theta"] = theta
         out["theta_orig"] = background_to_original(theta, L, DK, DB, prep["s_R"], prep["s_S"])
         out["D"] = apply(prep, theta, DK, DB)
     return out

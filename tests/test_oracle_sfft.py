@@ -312,3 +312,109 @@ def test_apply_matches_library_convolution_everywhere():
     D = O.apply(prep, theta, DK, DB)
     model = _exact_model_science(prep["R_t"], c, beta, L, DK, DB)
     assert np.abs(D - (prep["S_p"] - model)).max() < 1e-9
+
+
+# ------------------------------------------------------------------ constant photometric ratio
+def _kernel_sums(theta, L, DK, DB, H, W, pts):
+    return np.array([O.kernel_at(theta, L, DK, DB, H, W, x, y).sum() for (x, y) in pts])
+
+
+PTS = [(3.0, 4.0), (60.0, 10.0), (20.0, 50.0), (70.0, 60.0), (35.5, 31.0)]
+
+
+def test_const_ratio_with_constant_kernel_spans_the_full_basis():
+    """D_K = 0: delta_0 plus the differences delta_u - delta_0 span every
+    constant kernel, so the constrained and free fits are the same problem."""
+    H, W, L = 56, 64, 5
+    d = small_pair(H, W, seed=71, n_src=12, mask_fraction=0.02)
+    free = O.fit(d["R"], d["S"], d["bad"], L, 0, 1)
+    cpr = O.fit_const_ratio(d["R"], d["S"], d["bad"], L, 0, 1)
+    assert cpr["A_c"].shape[0] == O.n_unknowns(L, 0, 1)
+    assert np.abs(cpr["theta"] - free["theta"]).max() <= 1e-8 * np.abs(free["theta"]).max()
+    assert np.abs(cpr["D"] - free["D"]).max() <= 1e-8 * np.abs(d["S"]).max()
+
+
+@pytest.mark.parametrize("L,DK,DB", [(5, 2, 2), (7, 2, 0), (5, 1, 0)])
+def test_const_ratio_exact_model_recovered(L, DK, DB):
+    """S = K (x) R + B with a kernel whose shape varies over the chip but whose
+    sum is constant: the constrained fit returns it exactly, also for
+    D_B < D_K (the sky offset then only shifts the constant background)."""
+    H, W = 64, 72
+    d = small_pair(H, W, seed=81 + L + DB, n_src=10, mask_fraction=0.03)
+    R = d["R"].astype(np.float64)
+    rng = np.random.default_rng(82 + DK)
+    NK, NB = O.n_terms(DK), O.n_terms(DB)
+    c = rng.normal(0, 0.05, (L * L, NK))
+    c[:, 1:] -= c[:, 1:].mean(axis=0)              # sum_j c[j, p] = 0 for p >= 1
+    c[O.center_index(L), 0] += 0.8
+    beta = rng.normal(0, 3.0, NB); beta[0] = 900.0
+    S = _exact_model_science(R, c, beta, L, DK, DB)
+    out = O.fit_const_ratio(R, S, d["bad"], L, DK, DB)    # sky = medians
+    ct, bt = O.split_theta(out["theta_orig"], L, DK, DB)
+    assert np.abs(ct - c).max() <= 1e-9 * np.abs(c).max()
+    assert np.abs(bt - beta).max() <= 1e-9 * np.abs(beta).max()
+    w = (L - 1) // 2
+    assert np.abs(out["D"][w:H - w, w:W - w]).max() < 1e-8 * np.abs(S).max()
+
+
+def test_const_ratio_kernel_sum_is_constant_and_free_fit_is_not():
+    H, W, L, DK, DB = 64, 72, 5, 2, 2
+    d = small_pair(H, W, seed=91, n_src=25, mask_fraction=0.02, n_transients=1)
+    cpr = O.fit_const_ratio(d["R"], d["S"], d["bad"], L, DK, DB)
+    free = O.fit(d["R"], d["S"], d["bad"], L, DK, DB)
+    sc = _kernel_sums(cpr["theta"], L, DK, DB, H, W, PTS)
+    sf = _kernel_sums(free["theta"], L, DK, DB, H, W, PTS)
+    assert np.ptp(sc) <= 1e-12 * abs(sc[0])
+    n = (L * L - 1) * O.n_terms(DK)
+    assert abs(sc[0] - cpr["theta_c"][n]) <= 1e-12 * abs(sc[0])
+    assert np.ptp(sf) > 1e-6 * abs(sf[0])
+    # the constraint costs fit quality, never gains it
+    M = cpr["prep"]["M"]
+    assert np.sum(cpr["D"][M] ** 2) >= np.sum(free["D"][M] ** 2)
+
+
+def test_const_ratio_matches_lagrange_multipliers():
+    """The constrained optimum from the KKT system of the free normal
+    equations with the equality constraints sum_j theta[j, p] = 0 (p >= 1):
+    an independent formulation of the same least-squares problem."""
+    H, W, L, DK, DB = 60, 66, 5, 1, 2
+    d = small_pair(H, W, seed=93, n_src=20, mask_fraction=0.03)
+    free = O.fit(d["R"], d["S"], d["bad"], L, DK, DB)
+    A, b = free["A"], free["b"]
+    NK, N = O.n_terms(DK), A.shape[0]
+    C = np.zeros((NK - 1, N))
+    for p in range(1, NK):
+        C[p - 1, [j * NK + p for j in range(L * L)]] = 1.0
+    s = 1.0 / np.sqrt(np.diag(A))
+    K = np.block([[A * s[:, None] * s[None, :], (C * s[None, :]).T], [C * s[None, :], np.zeros((NK - 1, NK - 1))]])
+    sol = np.linalg.solve(K, np.concatenate([b * s, np.zeros(NK - 1)]))
+    theta_kkt = sol[:N] * s
+    cpr = O.fit_const_ratio(d["R"], d["S"], d["bad"], L, DK, DB)
+    assert np.abs(cpr["theta"] - theta_kkt).max() <= 1e-7 * np.abs(theta_kkt).max()
+
+
+def test_sky_dependence_below_kernel_degree():
+    """D_B < D_K: with a constant kernel sum the fit is independent of the sky
+    constants; with a free kernel sum it is not (the reading: the free fit is
+    that of the sky-subtracted images)."""
+    H, W, L, DK, DB = 56, 64, 5, 2, 0
+    d = small_pair(H, W, seed=95, n_src=15)
+    w = (L - 1) // 2
+    inner = (slice(w, H - w), slice(w, W - w))
+    sky0 = (float(np.median(d["R"])), float(np.median(d["S"])))
+    sky1 = (sky0[0] + 40.0, sky0[1] - 15.0)
+    a = O.fit_const_ratio(d["R"], d["S"], None, L, DK, DB, sky=sky0)
+    b = O.fit_const_ratio(d["R"], d["S"], None, L, DK, DB, sky=sky1)
+    assert np.abs(a["theta_orig"] - b["theta_orig"]).max() <= 1e-8 * np.abs(a["theta_orig"]).max()
+    assert np.abs(a["D"][inner] - b["D"][inner]).max() <= 1e-8 * np.abs(d["S"]).max()
+    fa = O.fit(d["R"], d["S"], None, L, DK, DB, sky=sky0)
+    fb = O.fit(d["R"], d["S"], None, L, DK, DB, sky=sky1)
+    assert np.abs(fa["D"][inner] - fb["D"][inner]).max() > 1e-6 * np.abs(d["S"]).max()
+
+
+def test_const_ratio_refinement_is_a_no_op_in_fp64():
+    H, W, L = 48, 52, 5
+    d = small_pair(H, W, seed=97, n_src=10)
+    a = O.fit_const_ratio(d["R"], d["S"], None, L, 1, 1)
+    b = O.fit_const_ratio(d["R"], d["S"], None, L, 1, 1, refine_steps=1)
+    assert np.abs(a["theta"] - b["theta"]).max() <= 1e-9 * np.abs(a["theta"]).max()
