@@ -31,8 +31,18 @@
  *  - No call allocates device memory after sfft_plan; scratch lives in the
  *    caller-allocated workspace `ws` of sfft_workspace_bytes() bytes (256-byte
  *    aligned).  A workspace must not be shared by calls that overlap on the GPU.
- *  - Requirements: L odd, 1 <= L <= 11; 0 <= D_K <= D_B <= 2 (D_B >= D_K makes
- *    the sky offsets exactly absorbed by the background); H >= L; 16 <= W <= 2048.
+ *  - Requirements: L odd, 1 <= L <= 11; 0 <= D_K, D_B <= 2; H >= L;
+ *    16 <= W <= 2048.  The sky offsets are absorbed exactly by the background
+ *    when D_B >= D_K or with SFFT_FLAG_CONST_RATIO; otherwise the fit is that
+ *    of the sky-subtracted images (see sfft_solve for the reported units).
+ *
+ * Constant photometric ratio (SFFT_FLAG_CONST_RATIO; the constrained
+ * delta-basis kernel of the literature cited in Sec. 1): the kernel sum
+ * sum_j K_j(x) is one constant a_0 over the chip.  The fit is solved in the
+ * basis K = a_0 delta_0 + sum_{u != 0} sum_p c[u,p] phi_p (delta_u - delta_0),
+ * (L^2 - 1) N_K + 1 + N_B unknowns, i.e. the normal equations
+ * (T A T^T) theta_c = T b with theta = T^T theta_c; A, b and theta keep the
+ * full N-term layout above.
  *
  * The paper gives no equations for the fit; the exact definition above, the
  * mask and sky-offset semantics and the polynomial coordinates are this
@@ -66,7 +76,8 @@ typedef enum {
   SFFT_PREC_MIXED = 1        /* FP32 FFTs/products/partials; FP64 accumulation, solve, refinement */
 } sfft_prec_t;
 
-#define SFFT_FLAG_GRAPH 1u   /* sfft_subtract replays a captured CUDA graph */
+#define SFFT_FLAG_GRAPH 1u        /* sfft_subtract replays a captured CUDA graph */
+#define SFFT_FLAG_CONST_RATIO 2u  /* kernel sum constant over the chip (constrained fit) */
 
 typedef struct {
   int32_t H, W;              /* image rows, columns */
@@ -113,13 +124,19 @@ sfft_status_t sfft_build_normal(sfft_plan_t plan, const float* R, const float* S
                                 const uint8_t* bad, const double* sky,
                                 double* A, double* b, void* ws);
 
-/* Solve A theta = b per CCD in FP64: Jacobi equilibration, Cholesky, two
- * triangular solves; then `refine_steps` steps of iterative refinement whose
- * residual r = sum_x M_fit Phi (S' - model) is formed in image space from R
- * and S.  theta : double [batch][N]; its background part is returned in
- * original (un-offset) units, B = B' + s_S - s_R sum_j K_j.  info : int32
- * [batch] (device) receives SFFT_OK / SFFT_ERR_SINGULAR / SFFT_ERR_NONFINITE.
- * Must follow sfft_build_normal with the same ws, R, S and bad. */
+/* Solve A theta = b per CCD in FP64 (with SFFT_FLAG_CONST_RATIO the
+ * projected system T A T^T theta_c = T b, theta = T^T theta_c): Jacobi
+ * equilibration, Cholesky, two triangular solves; then `refine_steps` steps of
+ * iterative refinement whose residual r = sum_x M_fit Phi (S' - model) is
+ * formed in image space from R and S.  theta : double [batch][N]; its
+ * background part is returned in original (un-offset) units,
+ * beta_q + s_S [q == 0] - s_R sum_j theta[j, q] for q < min(N_K, N_B), which
+ * is B = B' + s_S - s_R sum_j K_j exactly unless D_B < D_K with a free kernel
+ * sum (then the terms of degree above D_B are not representable and are left
+ * out; sfft_apply with the same sky still reproduces the fitted D).
+ * info : int32 [batch] (device) receives SFFT_OK / SFFT_ERR_SINGULAR /
+ * SFFT_ERR_NONFINITE.  Must follow sfft_build_normal with the same ws, R, S
+ * and bad. */
 sfft_status_t sfft_solve(sfft_plan_t plan, const double* A, const double* b, double* theta,
                          int32_t refine_steps, const float* R, const float* S,
                          const uint8_t* bad, int32_t* info, void* ws);

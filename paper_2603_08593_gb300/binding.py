@@ -16,6 +16,7 @@ SFFT_OK, SFFT_ERR_ARG, SFFT_ERR_CUDA, SFFT_ERR_NOMEM = 0, 1, 2, 3
 SFFT_ERR_SINGULAR, SFFT_ERR_NONFINITE, SFFT_ERR_TIMEOUT, SFFT_ERR_UNSUPPORTED = 4, 5, 6, 7
 PREC = {"fp64": 0, "mixed": 1}
 FLAG_GRAPH = 1
+FLAG_CONST_RATIO = 2
 
 
 class Desc(C.Structure):
@@ -126,10 +127,12 @@ def apply_noalloc(R, S, theta, sky, D, L, DK, DB, prec="mixed", stream=None):
 
 
 class Plan:
-    """A subtraction plan plus its workspace (a torch uint8 device tensor)."""
+    """A subtraction plan plus its workspace (a torch uint8 device tensor).
+    const_ratio=True holds the kernel sum constant over the chip
+    (SFFT_FLAG_CONST_RATIO); theta keeps the full N-term layout."""
 
     def __init__(self, H, W, L, DK, DB, batch=1, prec="mixed", d_batch=0, rows_per_cta=0, autotune=0,
-                 graph=False, stream=None, device=None, lag_parts=0):
+                 graph=False, stream=None, device=None, lag_parts=0, const_ratio=False):
         import torch
         self._torch = torch
         lib = load()
@@ -137,12 +140,13 @@ class Plan:
         self.device = _device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.desc = Desc(H, W, L, DK, DB, batch, PREC[prec], autotune, d_batch, rows_per_cta, lag_parts,
-                         FLAG_GRAPH if graph else 0)
+                         (FLAG_GRAPH if graph else 0) | (FLAG_CONST_RATIO if const_ratio else 0))
         h = VP()
         with torch.cuda.device(self.device):
             _check(lib.sfft_plan(C.byref(self.desc), VP(self.stream.cuda_stream), C.byref(h)), "sfft_plan")
         self.h = h
         self.H, self.W, self.L, self.DK, self.DB, self.batch = H, W, L, DK, DB, batch
+        self.const_ratio = bool(const_ratio)
         self.N = int(lib.sfft_num_unknowns(h))
         self.ws_bytes = int(lib.sfft_workspace_bytes(h))
         self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)

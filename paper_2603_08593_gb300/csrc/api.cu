@@ -235,7 +235,8 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
   if (d.DK < 0 || d.DB < 0 || d.d_batch < 0 || d.rows_per_cta < 0) return SFFT_ERR_ARG;
   if (d.lag_parts < 0 || d.lag_parts > 3) return SFFT_ERR_ARG;
   if ((d.L & 1) == 0 || d.L > kMaxL) return SFFT_ERR_UNSUPPORTED;
-  if (d.DK > kMaxD || d.DB > kMaxD || d.DB < d.DK) return SFFT_ERR_UNSUPPORTED;
+  if (d.flags & ~(SFFT_FLAG_GRAPH | SFFT_FLAG_CONST_RATIO)) return SFFT_ERR_ARG;
+  if (d.DK > kMaxD || d.DB > kMaxD) return SFFT_ERR_UNSUPPORTED;
   if (d.H < d.L || d.W < d.L || d.W < 16 || d.W > 2048) return SFFT_ERR_UNSUPPORTED;
 
   sfft_plan_s* p = new (std::nothrow) sfft_plan_s();
@@ -250,6 +251,8 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
   p->NB = n_mono(d.DB);
   p->NKK = d.L * d.L * p->NK;
   p->N = p->NKK + p->NB;
+  p->cpr = (d.flags & SFFT_FLAG_CONST_RATIO) != 0;
+  p->Nsol = p->cpr ? (d.L * d.L - 1) * p->NK + 1 + p->NB : p->N;
   p->Nf = std::max(64, next_pow2(d.W));
   p->M = p->Nf / 2;
   p->N2 = p->M / 32;
@@ -405,11 +408,26 @@ static sfft_status_t solve_impl(sfft_plan_t p, const double* A, const double* b,
   double* rhs = vec;
   double* x = vec + NBt;
   double* toff = ws_at<double>(ws, p->theta_off);
+  // constant-ratio fit: right-hand sides projected to, and solutions expanded
+  // from, the constrained basis (vec's third and fourth quarters)
+  double* rhs_c = vec + 2 * NBt;
+  double* x_c = vec + 3 * NBt;
+  auto solve_rhs = [&](const double* r, bool add) -> sfft_status_t {
+    if (p->cpr) {
+      CK(launch_cpr_rhs(p, r, rhs_c));
+      CK(launch_chol_solve(p, rhs_c, x_c, ws));
+      CK(launch_cpr_expand(p, x_c, toff, add));
+    } else {
+      CK(launch_chol_solve(p, r, x, ws));
+      CK(launch_theta_finish(p, x, toff, add));
+    }
+    return SFFT_OK;
+  };
   {
     Phase ph(p, SFFT_PROF_SOLVE);
     CK(launch_cholesky(p, A, ws));
-    CK(launch_chol_solve(p, b, x, ws));
-    CK(launch_theta_finish(p, x, toff, false));
+    const sfft_status_t s0 = solve_rhs(b, false);
+    if (s0 != SFFT_OK) return s0;
   }
   for (int r = 0; r < refine; ++r) {
     void* e = ws_at<char>(ws, p->eimg);
@@ -436,8 +454,8 @@ static sfft_status_t solve_impl(sfft_plan_t p, const double* A, const double* b,
     }
     {
       Phase ph(p, SFFT_PROF_SOLVE);
-      CK(launch_chol_solve(p, rhs, x, ws));
-      CK(launch_theta_finish(p, x, toff, true));
+      const sfft_status_t s1 = solve_rhs(rhs, true);
+      if (s1 != SFFT_OK) return s1;
     }
   }
   {

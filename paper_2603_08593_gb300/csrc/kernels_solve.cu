@@ -5,7 +5,8 @@
 // u_j'), A[(j,p), q] = g^{KB}_{phi_p psi_q}(u_j), A[q, q'] = moment of
 // M_fit psi_q psi_q', b_(j,p) = g^{bK}_p(u_j), b_q = moment of M_fit psi_q S'.
 //
-// Solve: Jacobi equilibration D_s = diag(A)^-1/2, right-looking blocked
+// Solve: optionally the constant-ratio projection T A T^T (below), then
+// Jacobi equilibration D_s = diag(A)^-1/2, right-looking blocked
 // Cholesky of D_s A D_s (32 x 32 blocks, all block steps in one cooperative
 // launch), blocked forward and backward substitution with the inverted
 // diagonal blocks, theta = D_s y.
@@ -92,28 +93,106 @@ k_scatter(ScatterArgs a, const double* __restrict__ gkk, const double* __restric
   }
 }
 
-// scale = diag(A)^-1/2; Lf (lower) = D_s A D_s; status flags
+// ---------------------------------------------------------------- constant photometric ratio
+// With the kernel sum held constant over the chip the solved unknowns are,
+// in order, c[u, p] for the offsets u != 0 (j ascending, p minor), the
+// constant a_0 of delta_0 and the N_B background terms, the basis
+// K = a_0 delta_0 + sum_{u != 0} sum_p c[u, p] phi_p (delta_u - delta_0).
+// The full-layout coefficients are theta = T^T theta_c, where T's row of
+// c[u, p] is e_(u,p) - e_(0,p), its row of a_0 is e_(0,0) and the background
+// rows are the identity, so the constrained normal equations are
+// (T A T^T) theta_c = T b.  Each row of T has at most two non-zeros.
+struct CprMap {
+  int on;    // 0: the free fit (T = identity)
+  int NK;    // kernel polynomial terms
+  int jc;    // index of the zero offset, (L^2 - 1) / 2
+  int nkc;   // (L^2 - 1) N_K
+};
+
+// Columns (full layout) and signs of row r of T; returns their count.
+__device__ __forceinline__ int cpr_row(const CprMap& m, int r, int* idx, double* sg) {
+  if (!m.on) { idx[0] = r; sg[0] = 1.0; return 1; }
+  if (r < m.nkc) {
+    const int jj = r / m.NK, p = r % m.NK;
+    idx[0] = (jj < m.jc ? jj : jj + 1) * m.NK + p; sg[0] = 1.0;
+    idx[1] = m.jc * m.NK + p; sg[1] = -1.0;
+    return 2;
+  }
+  idx[0] = r == m.nkc ? m.jc * m.NK : r - 1 + m.NK;
+  sg[0] = 1.0;
+  return 1;
+}
+
+// (T A T^T)[i][j] from the full matrix a (row stride N)
+__device__ __forceinline__ double cpr_entry(const double* a, int64_t N, const CprMap& m, int i, int j) {
+  int ii[2], jj[2];
+  double si[2], sj[2];
+  const int ni = cpr_row(m, i, ii, si), nj = cpr_row(m, j, jj, sj);
+  double v = 0.0;
+  for (int x = 0; x < ni; ++x)
+    for (int y = 0; y < nj; ++y) v += si[x] * sj[y] * a[(int64_t)ii[x] * N + jj[y]];
+  return v;
+}
+
+// out = T b (per CCD: b stride N, out stride Ns)
+__global__ void k_cpr_rhs(const double* __restrict__ b, double* __restrict__ out, int N, int Ns, CprMap m) {
+  const int ccd = blockIdx.y;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < Ns; r += gridDim.x * blockDim.x) {
+    int idx[2];
+    double sg[2];
+    const int n = cpr_row(m, r, idx, sg);
+    double v = 0.0;
+    for (int x = 0; x < n; ++x) v += sg[x] * b[(int64_t)ccd * N + idx[x]];
+    out[(int64_t)ccd * Ns + r] = v;
+  }
+}
+
+// theta_off (=|+=) T^T x (per CCD: x stride Ns, theta_off stride N)
+__global__ void k_cpr_expand(const double* __restrict__ x, double* __restrict__ theta_off, int N, int Ns, CprMap m,
+                             int add) {
+  const int ccd = blockIdx.y;
+  const double* xc = x + (int64_t)ccd * Ns;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    double v;
+    if (i >= m.nkc + m.NK) {
+      v = xc[i - m.NK + 1];                      // background
+    } else {
+      const int j = i / m.NK, p = i % m.NK;
+      if (j != m.jc) {
+        v = xc[(j < m.jc ? j : j - 1) * m.NK + p];
+      } else {
+        v = p == 0 ? xc[m.nkc] : 0.0;
+        for (int jj = 0; jj < m.nkc / m.NK; ++jj) v -= xc[jj * m.NK + p];
+      }
+    }
+    double* o = theta_off + (int64_t)ccd * N + i;
+    *o = add ? *o + v : v;
+  }
+}
+
+// scale = diag(A_s)^-1/2; Lf (lower) = D_s A_s D_s; status flags.  A_s is the
+// solved system: A itself (row stride N = Ns) or T A T^T (size Ns).
 __global__ void __launch_bounds__(256)
 k_chol_init(const double* __restrict__ A, double* __restrict__ Lf, double* __restrict__ scale,
-            int* __restrict__ status, int N) {
+            int* __restrict__ status, int N, int Ns, CprMap m) {
   const int ccd = blockIdx.y;
-  const int64_t NN = (int64_t)N * N;
-  const double* a = A + ccd * NN;
-  double* l = Lf + ccd * NN;
-  double* s = scale + (int64_t)ccd * N;
+  const int64_t NS2 = (int64_t)Ns * Ns;
+  const double* a = A + ccd * (int64_t)N * N;
+  double* l = Lf + ccd * NS2;
+  double* s = scale + (int64_t)ccd * Ns;
   if (blockIdx.x == 0) {
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-      const double d = a[(int64_t)i * N + i];
+    for (int i = threadIdx.x; i < Ns; i += blockDim.x) {
+      const double d = cpr_entry(a, N, m, i, i);
       if (!isfinite(d)) atomicOr(&status[ccd], 2);
       else if (!(d > 0.0)) atomicOr(&status[ccd], 1);
     }
   }
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < NN; t += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t / N), j = (int)(t % N);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < NS2; t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / Ns), j = (int)(t % Ns);
     if (j > i) continue;
-    const double di = a[(int64_t)i * N + i], dj = a[(int64_t)j * N + j];
+    const double di = cpr_entry(a, N, m, i, i), dj = cpr_entry(a, N, m, j, j);
     const double si = di > 0.0 ? rsqrt(di) : 0.0, sj = dj > 0.0 ? rsqrt(dj) : 0.0;
-    const double v = a[t];
+    const double v = cpr_entry(a, N, m, i, j);
     if (!isfinite(v)) atomicOr(&status[ccd], 2);
     l[t] = v * si * sj;
     if (i == j) s[i] = si;
@@ -473,15 +552,24 @@ cudaError_t launch_scatter(const sfft_plan_s* p, double* A, double* b, void* ws,
   return cudaGetLastError();
 }
 
+static CprMap cpr_map(const sfft_plan_s* p) {
+  CprMap m;
+  m.on = p->cpr ? 1 : 0;
+  m.NK = p->NK;
+  m.jc = (p->d.L * p->d.L - 1) / 2;
+  m.nkc = (p->d.L * p->d.L - 1) * p->NK;
+  return m;
+}
+
 cudaError_t launch_cholesky(const sfft_plan_s* p, const double* A, void* ws) {
-  const int N = p->N, B = p->d.batch;
+  const int N = p->Nsol, B = p->d.batch;
   double* Lf = ws_at<double>(ws, p->lfac);
   double* scale = ws_at<double>(ws, p->scale);
   int* status = ws_at<int>(ws, p->status);
   double* dinv = ws_at<double>(ws, p->dinv);
   GridBar* bar = ws_at<GridBar>(ws, p->gbar);
   dim3 gi(64, B);
-  k_chol_init<<<gi, 256, 0, p->stream>>>(A, Lf, scale, status, N);
+  k_chol_init<<<gi, 256, 0, p->stream>>>(A, Lf, scale, status, p->N, N, cpr_map(p));
   cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBar), p->stream);
   if (e != cudaSuccess) return e;
   // every CTA of the cooperative grid must be resident at once
@@ -509,7 +597,7 @@ cudaError_t launch_cholesky(const sfft_plan_s* p, const double* A, void* ws) {
 }
 
 cudaError_t launch_chol_solve(const sfft_plan_s* p, const double* rhs, double* x, void* ws) {
-  const int N = p->N;
+  const int N = p->Nsol;
   const size_t smem = sizeof(double) * N;
   cudaFuncSetAttribute(k_chol_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_chol_solve<<<p->d.batch, 1024, smem, p->stream>>>(ws_at<double>(ws, p->lfac), ws_at<double>(ws, p->dinv),
@@ -522,6 +610,20 @@ cudaError_t launch_chol_solve(const sfft_plan_s* p, const double* rhs, double* x
 cudaError_t launch_theta_finish(const sfft_plan_s* p, const double* x, double* theta_off, bool add) {
   const int64_t n = (int64_t)p->N * p->d.batch;
   k_theta_finish<<<(int)((n + 255) / 256), 256, 0, p->stream>>>(x, theta_off, p->N, p->d.batch, add ? 1 : 0);
+  p->nlaunch += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cpr_rhs(const sfft_plan_s* p, const double* b, double* out) {
+  dim3 grid((p->Nsol + 255) / 256, p->d.batch);
+  k_cpr_rhs<<<grid, 256, 0, p->stream>>>(b, out, p->N, p->Nsol, cpr_map(p));
+  p->nlaunch += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cpr_expand(const sfft_plan_s* p, const double* x, double* theta_off, bool add) {
+  dim3 grid((p->N + 255) / 256, p->d.batch);
+  k_cpr_expand<<<grid, 256, 0, p->stream>>>(x, theta_off, p->N, p->Nsol, cpr_map(p), add ? 1 : 0);
   p->nlaunch += 1;
   return cudaGetLastError();
 }

@@ -69,8 +69,9 @@ extern "C" sfft_status_t sfft_apply_noalloc(int32_t H, int32_t W, int32_t L, int
     sfft::set_last_error("sfft_apply_noalloc: invalid shape or precision");
     return SFFT_ERR_ARG;
   }
-  if ((L & 1) == 0 || L > sfft::kMaxL || DK < 0 || DB < DK || DB > sfft::kMaxD || H < L || W < L) {
-    sfft::set_last_error("sfft_apply_noalloc: L must be odd and <= 11, 0 <= D_K <= D_B <= 2, H and W >= L");
+  if ((L & 1) == 0 || L > sfft::kMaxL || DK < 0 || DB < 0 || DK > sfft::kMaxD || DB > sfft::kMaxD || H < L ||
+      W < L) {
+    sfft::set_last_error("sfft_apply_noalloc: L must be odd and <= 11, 0 <= D_K, D_B <= 2, H and W >= L");
     return SFFT_ERR_UNSUPPORTED;
   }
   const int NK = sfft::n_mono(DK), NB = sfft::n_mono(DB);

@@ -32,6 +32,8 @@ struct sfft_plan_s {
   bool fp64 = false;
   int device = 0;
   int w = 0, NK = 0, NB = 0, NKK = 0, N = 0;
+  bool cpr = false;                   // constant photometric ratio: solve in the constrained basis
+  int Nsol = 0;                       // unknowns of the solved system: N, or (L^2 - 1) N_K + 1 + N_B
   int Nf = 0, M = 0, N2 = 0;
   int DM_KK = 0, DM_KB = 0, DM_bK = 0, DM_BB = 0;
   int n_wa = 0;                       // weight spectra a = 0 .. n_wa-1
@@ -87,6 +89,8 @@ cudaError_t launch_scatter(const sfft_plan_s* p, double* A, double* b, void* ws,
 cudaError_t launch_cholesky(const sfft_plan_s* p, const double* A, void* ws);
 cudaError_t launch_chol_solve(const sfft_plan_s* p, const double* rhs, double* x, void* ws);
 cudaError_t launch_theta_finish(const sfft_plan_s* p, const double* x, double* theta_off, bool add);
+cudaError_t launch_cpr_rhs(const sfft_plan_s* p, const double* b, double* out);
+cudaError_t launch_cpr_expand(const sfft_plan_s* p, const double* x, double* theta_off, bool add);
 cudaError_t launch_theta_to_orig(const sfft_plan_s* p, const double* theta_off, double* theta, void* ws);
 cudaError_t launch_theta_to_off(const sfft_plan_s* p, const double* theta, const double* sky, double* theta_off, void* ws);
 cudaError_t launch_apply(const sfft_plan_s* p, const float* R, const float* S, const double* theta_off,

@@ -55,9 +55,11 @@ def test_status_strings_and_arg_errors_without_gpu(built_lib):
     h = ctypes.c_void_p()
     for desc in [binding.Desc(64, 64, 4, 1, 1, 1, 1, 0, 0, 0, 0),      # even L
                  binding.Desc(64, 64, 13, 1, 1, 1, 1, 0, 0, 0, 0),     # L too large
-                 binding.Desc(64, 64, 5, 2, 1, 1, 1, 0, 0, 0, 0),      # D_B < D_K
+                 binding.Desc(64, 64, 5, 3, 3, 1, 1, 0, 0, 0, 0),      # degree above 2
                  binding.Desc(64, 4096, 5, 1, 1, 1, 1, 0, 0, 0, 0)]:   # W too large
         assert lib.sfft_plan(ctypes.byref(desc), None, ctypes.byref(h)) == binding.SFFT_ERR_UNSUPPORTED
     bad = binding.Desc(0, 64, 5, 1, 1, 1, 1, 0, 0, 0, 0)
     assert lib.sfft_plan(ctypes.byref(bad), None, ctypes.byref(h)) == binding.SFFT_ERR_ARG
+    unknown_flag = binding.Desc(64, 64, 5, 1, 1, 1, 1, 0, 0, 0, 0, 4)
+    assert lib.sfft_plan(ctypes.byref(unknown_flag), None, ctypes.byref(h)) == binding.SFFT_ERR_ARG
     assert lib.sfft_build_normal(None, None, None, None, None, None, None, None) == binding.SFFT_ERR_ARG

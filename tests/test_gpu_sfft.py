@@ -36,7 +36,8 @@ def _run(d, L, DK, DB, prec, refine=1, sky_from_oracle=True, batch_imgs=None, **
     R = _dev(np.stack([x["R"] for x in imgs]))
     S = _dev(np.stack([x["S"] for x in imgs]))
     bad = _dev(np.stack([x["bad"] for x in imgs]))
-    refs = [O.fit(x["R"], x["S"], x["bad"], L, DK, DB) for x in imgs]
+    fit = O.fit_const_ratio if plan_kw.get("const_ratio") else O.fit
+    refs = [fit(x["R"], x["S"], x["bad"], L, DK, DB) for x in imgs]
     sky = None
     if sky_from_oracle:
         sky = torch.tensor([[r["prep"]["s_R"], r["prep"]["s_S"]] for r in refs], dtype=torch.float64, device=DEV)
@@ -202,3 +203,85 @@ def test_config_c1_single_512_pair():
     x, y, f = d["transients"][0, :3]
     half = int(np.ceil(3.0 * d["transients"][0, 4]))
     assert abs(O.box_flux(D2[0], x, y, half) - O.box_flux(ref["D"], x, y, half)) <= 1e-4 * f
+
+
+# ------------------------------------------------------------------ constant photometric ratio, D_B < D_K
+CPR_CASES = [
+    ((70, 90), 5, 1, 1),
+    ((150, 210), 7, 2, 2),
+    ((96, 300), 11, 2, 0),      # D_B < D_K: sky offsets absorbed through the constant kernel sum
+    ((40, 1100), 5, 2, 1),
+]
+
+
+@pytest.mark.parametrize("shape,L,DK,DB", CPR_CASES)
+def test_const_ratio_fp64_matches_oracle(shape, L, DK, DB):
+    d = small_pair(*shape, seed=4000 + shape[0] + L, mask_fraction=0.03, n_transients=1)
+    refs, A, b, th, info, D = _run(d, L, DK, DB, "fp64", const_ratio=True)
+    ref = refs[0]
+    assert info[0] == 0
+    assert np.abs(th[0] - ref["theta_orig"]).max() <= 1e-8 * np.abs(ref["theta_orig"]).max()
+    assert np.all(np.abs(D[0] - ref["D"]) <= 2.0 ** -24 * np.abs(ref["D"]) + 1e-7 * SIGMA_SKY)
+
+
+@pytest.mark.parametrize("shape,L,DK,DB", CPR_CASES)
+def test_const_ratio_mixed_within_stated_error(shape, L, DK, DB):
+    from paper_2603_08593_gb300 import Plan
+    d = small_pair(*shape, seed=4100 + shape[1] + L, mask_fraction=0.03, n_transients=1)
+    refs, A, b, th, info, D = _run(d, L, DK, DB, "mixed", const_ratio=True)
+    ref = refs[0]
+    assert info[0] == 0
+    assert O.kernel_coef_rel_err(th[0], ref["theta_orig"], L, DK, DB) <= 1e-5
+    assert np.abs(D[0] - ref["D"]).max() <= 1e-3 * SIGMA_SKY
+    # the kernel sum is one constant over the chip
+    plan = Plan(*shape, L, DK, DB, batch=1, prec="mixed", const_ratio=True)
+    t = _dev(th)
+    sums = [float(plan.kernel_at(t, x, y).sum()) for (x, y) in [(0, 0), (shape[1] - 1, 3), (7, shape[0] - 1),
+                                                                 (shape[1] / 2, shape[0] / 3)]]
+    assert np.ptp(sums) <= 1e-12 * abs(sums[0])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_free_fit_below_kernel_degree(prec):
+    """D_B < D_K without the constraint: the fit of the sky-subtracted images,
+    compared with the oracle at the same sky constants."""
+    shape, L, DK, DB = (90, 130), 7, 2, 1
+    d = small_pair(*shape, seed=4200, mask_fraction=0.03)
+    refs, A, b, th, info, D = _run(d, L, DK, DB, prec)
+    ref = refs[0]
+    assert info[0] == 0
+    if prec == "fp64":
+        assert np.abs(th[0] - ref["theta_orig"]).max() <= 1e-8 * np.abs(ref["theta_orig"]).max()
+        assert np.all(np.abs(D[0] - ref["D"]) <= 2.0 ** -24 * np.abs(ref["D"]) + 1e-7 * SIGMA_SKY)
+    else:
+        assert O.kernel_coef_rel_err(th[0], ref["theta_orig"], L, DK, DB) <= 1e-5
+        assert np.abs(D[0] - ref["D"]).max() <= 1e-3 * SIGMA_SKY
+
+
+def test_const_ratio_batched_graph_subtract():
+    """Three CCDs in one constrained plan through the captured-graph
+    subtraction with GPU sky estimates: every CCD against its own oracle fit
+    (same sky constants), compared away from the border."""
+    from paper_2603_08593_gb300 import Plan
+    L, DK, DB = 5, 2, 0
+    H, W = 72, 96
+    imgs = [small_pair(H, W, seed=4300 + i, mask_fraction=0.02 * i, n_transients=1) for i in range(3)]
+    R = _dev(np.stack([x["R"] for x in imgs])); S = _dev(np.stack([x["S"] for x in imgs]))
+    bad = _dev(np.stack([x["bad"] for x in imgs]))
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        plan = Plan(H, W, L, DK, DB, batch=3, prec="mixed", graph=True, stream=s, const_ratio=True)
+        out = plan.subtract(R, S, bad, None, refine=1)
+        out = plan.subtract(R, S, bad, None, refine=1, out=out)
+    s.synchronize()
+    assert np.all(out["info"].cpu().numpy() == 0)
+    th = out["theta"].cpu().numpy()
+    Dg = out["D"].cpu().numpy()
+    w = (L - 1) // 2
+    for i, x in enumerate(imgs):
+        ref = O.fit_const_ratio(x["R"], x["S"], x["bad"], L, DK, DB)
+        # the sky constant is absorbed exactly: K and D do not depend on it
+        assert O.kernel_coef_rel_err(th[i], ref["theta_orig"], L, DK, DB) <= 1e-5
+        fin = np.isfinite(ref["D"][w:-w, w:-w])
+        assert np.abs(Dg[i][w:-w, w:-w][fin] - ref["D"][w:-w, w:-w][fin]).max() <= 1e-3 * SIGMA_SKY
