@@ -73,11 +73,14 @@ typedef enum {
 
 typedef enum {
   SFFT_PREC_FP64 = 0,        /* FFTs, products, partial sums and apply in FP64 */
-  SFFT_PREC_MIXED = 1        /* FP32 FFTs/products/partials; FP64 accumulation, solve, refinement */
+  SFFT_PREC_MIXED = 1        /* FP32 FFTs/products/partials (KK products as three-term TF32 splits on
+                                the tensor cores); FP64 accumulation, solve, refinement */
 } sfft_prec_t;
 
 #define SFFT_FLAG_GRAPH 1u        /* sfft_subtract replays a captured CUDA graph */
 #define SFFT_FLAG_CONST_RATIO 2u  /* kernel sum constant over the chip (constrained fit) */
+#define SFFT_FLAG_FMA_CONTRACT 4u /* mixed path: KK contraction on the FP32 FMA pipes instead of the
+                                     three-term TF32 split on the tensor cores (the default) */
 
 typedef struct {
   int32_t H, W;              /* image rows, columns */

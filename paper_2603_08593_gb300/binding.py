@@ -17,6 +17,7 @@ SFFT_ERR_SINGULAR, SFFT_ERR_NONFINITE, SFFT_ERR_TIMEOUT, SFFT_ERR_UNSUPPORTED = 
 PREC = {"fp64": 0, "mixed": 1}
 FLAG_GRAPH = 1
 FLAG_CONST_RATIO = 2
+FLAG_FMA_CONTRACT = 4
 
 
 class Desc(C.Structure):
@@ -129,10 +130,12 @@ def apply_noalloc(R, S, theta, sky, D, L, DK, DB, prec="mixed", stream=None):
 class Plan:
     """A subtraction plan plus its workspace (a torch uint8 device tensor).
     const_ratio=True holds the kernel sum constant over the chip
-    (SFFT_FLAG_CONST_RATIO); theta keeps the full N-term layout."""
+    (SFFT_FLAG_CONST_RATIO); theta keeps the full N-term layout.
+    fma_contract=True runs the mixed path's KK contraction on the FP32 FMA
+    pipes instead of the tensor cores (SFFT_FLAG_FMA_CONTRACT)."""
 
     def __init__(self, H, W, L, DK, DB, batch=1, prec="mixed", d_batch=0, rows_per_cta=0, autotune=0,
-                 graph=False, stream=None, device=None, lag_parts=0, const_ratio=False):
+                 graph=False, stream=None, device=None, lag_parts=0, const_ratio=False, fma_contract=False):
         import torch
         self._torch = torch
         lib = load()
@@ -140,7 +143,8 @@ class Plan:
         self.device = _device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.desc = Desc(H, W, L, DK, DB, batch, PREC[prec], autotune, d_batch, rows_per_cta, lag_parts,
-                         (FLAG_GRAPH if graph else 0) | (FLAG_CONST_RATIO if const_ratio else 0))
+                         (FLAG_GRAPH if graph else 0) | (FLAG_CONST_RATIO if const_ratio else 0) |
+                         (FLAG_FMA_CONTRACT if fma_contract else 0))
         h = VP()
         with torch.cuda.device(self.device):
             _check(lib.sfft_plan(C.byref(self.desc), VP(self.stream.cuda_stream), C.byref(h)), "sfft_plan")

@@ -201,7 +201,74 @@ static void build_jobs(sfft_plan_s* p) {
   p->bk_count = (int)p->h_jobs.size() - p->bk_first;
 }
 
+// Pair lists and patterns of the tensor-core KK contraction: per d-batch the
+// (d, u_y) pairs in difference order, cut greedily into patterns of at most
+// 8 kTcNT pairs whose staged probe rows (kTcChunk + n_lag - 1 per difference)
+// fit kTcRowCap; one job per (CCD, pattern).
+static void build_tc_jobs(sfft_plan_s* p) {
+  const int L = p->d.L, w = p->w, B = p->d.batch, H = p->d.H;
+  const int LL = L * L, NP = 8 * kTcNT;
+  const size_t slab = (size_t)H * p->M * 2 * p->elem;
+  p->tc_first.clear();
+  p->tc_count.clear();
+  p->h_tcjobs.clear();
+  p->h_tcpairs.clear();
+  p->h_tcdj.clear();
+  for (int d0 = 0; d0 < p->n_hd; d0 += p->d_batch) {
+    const int nd = std::min(p->d_batch, p->n_hd - d0);
+    const int pair_base = (int)p->h_tcpairs.size();
+    for (int i = 0; i < nd; ++i) {
+      const int2 d = p->dlist[d0 + i];
+      const int ulo = std::max(-w, d.x - w), uhi = std::min(w, d.x + w);
+      const int xlo = std::max(-w, d.y - w), xhi = std::min(w, d.y + w);
+      for (int u = ulo; u <= uhi; ++u) p->h_tcpairs.push_back(int4{i, u, xlo, xhi});
+    }
+    struct Pat { int pair0, npair, dj0, nd; };
+    std::vector<Pat> pats;
+    const int npairs = (int)p->h_tcpairs.size() - pair_base;
+    int q = 0;
+    while (q < npairs) {
+      Pat pt{pair_base + q, 0, (int)p->h_tcdj.size(), 0};
+      int rows = 0;
+      while (q < npairs && pt.npair < NP) {
+        const int4 e = p->h_tcpairs[pair_base + q];
+        const bool new_d = pt.nd == 0 || p->h_tcdj.back().x != e.x;
+        const int add = new_d ? kTcChunk : 1;
+        if (rows + add > kTcRowCap) break;
+        if (new_d) {
+          p->h_tcdj.push_back(int4{e.x, e.y, e.y, rows});
+          ++pt.nd;
+        } else {
+          p->h_tcdj.back().z = e.y;
+        }
+        rows += add;
+        ++pt.npair;
+        ++q;
+      }
+      pats.push_back(pt);
+    }
+    p->tc_first.push_back((int)p->h_tcjobs.size());
+    for (int ccd = 0; ccd < B; ++ccd)
+      for (const Pat& pt : pats) {
+        TcJob j;
+        j.probe = (int64_t)(p->phat.off + (size_t)ccd * p->d_batch * slab);
+        j.wts = (int64_t)(p->wspec.off + (size_t)ccd * p->n_wa * slab);
+        j.out = (int64_t)(p->gkk.off + sizeof(double) * ((size_t)ccd * p->n_hd + d0) * LL * n_mono(p->DM_KK));
+        j.status = (int64_t)(p->status.off + sizeof(int) * (size_t)ccd);
+        j.pair0 = pt.pair0;
+        j.npair = pt.npair;
+        j.dj0 = pt.dj0;
+        j.nd = pt.nd;
+        p->h_tcjobs.push_back(j);
+      }
+    p->tc_count.push_back((int)p->h_tcjobs.size() - p->tc_first.back());
+  }
+}
+
 static void free_plan_device(sfft_plan_s* p) {
+  if (p->d_tcjobs) cudaFree(p->d_tcjobs);
+  if (p->d_tcpairs) cudaFree(p->d_tcpairs);
+  if (p->d_tcdj) cudaFree(p->d_tcdj);
   if (p->twM) cudaFree(p->twM);
   if (p->twN) cudaFree(p->twN);
   if (p->twD) cudaFree(p->twD);
@@ -235,7 +302,7 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
   if (d.DK < 0 || d.DB < 0 || d.d_batch < 0 || d.rows_per_cta < 0) return SFFT_ERR_ARG;
   if (d.lag_parts < 0 || d.lag_parts > 3) return SFFT_ERR_ARG;
   if ((d.L & 1) == 0 || d.L > kMaxL) return SFFT_ERR_UNSUPPORTED;
-  if (d.flags & ~(SFFT_FLAG_GRAPH | SFFT_FLAG_CONST_RATIO)) return SFFT_ERR_ARG;
+  if (d.flags & ~(SFFT_FLAG_GRAPH | SFFT_FLAG_CONST_RATIO | SFFT_FLAG_FMA_CONTRACT)) return SFFT_ERR_ARG;
   if (d.DK > kMaxD || d.DB > kMaxD) return SFFT_ERR_UNSUPPORTED;
   if (d.H < d.L || d.W < d.L || d.W < 16 || d.W > 2048) return SFFT_ERR_UNSUPPORTED;
 
@@ -292,8 +359,11 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
   if (p->fp64) p->csplit = 2;
   // row flags are bulk-copied in 16-byte aligned runs of up to 20 ints past a chunk start
   p->rf_stride = ((d.H + 32) + 63) / 64 * 64;
+  p->tc = !p->fp64 && !(d.flags & SFFT_FLAG_FMA_CONTRACT);
+  p->tc_rows = d.H;
   build_layout(p);
   build_jobs(p);
+  if (p->tc) build_tc_jobs(p);
 
   // yt(y)^b for b = 0..4 per row, FP64 on the host, stored in the path's precision
   std::vector<double> ypow((size_t)d.H * 8, 0.0);
@@ -327,6 +397,9 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
   if (st == SFFT_OK) st = upload((void**)&p->d_dlist, p->dlist);
   if (st == SFFT_OK) st = upload((void**)&p->d_hdidx, hdidx);
   if (st == SFFT_OK) st = upload((void**)&p->d_jobs, p->h_jobs);
+  if (st == SFFT_OK && p->tc) st = upload((void**)&p->d_tcjobs, p->h_tcjobs);
+  if (st == SFFT_OK && p->tc) st = upload((void**)&p->d_tcpairs, p->h_tcpairs);
+  if (st == SFFT_OK && p->tc) st = upload((void**)&p->d_tcdj, p->h_tcdj);
   if (st != SFFT_OK) {
     free_plan_device(p);
     delete p;
@@ -391,7 +464,12 @@ static sfft_status_t build_normal_impl(sfft_plan_t p, const float* R, const floa
     }
     {
       Phase ph(p, SFFT_PROF_CONTRACT_KK);
-      CK(launch_contract(p, p->DM_KK, p->kk_first[ib], p->kk_count[ib], p->rows_per_cta, p->csplit, ws));
+      if (p->tc) {
+        CK(launch_contract_tc(p, (int)ib, ws));
+        CK(launch_contract_slot0(p, p->DM_KK, p->kk_first[ib], p->kk_count[ib], ws));
+      } else {
+        CK(launch_contract(p, p->DM_KK, p->kk_first[ib], p->kk_count[ib], p->rows_per_cta, p->csplit, ws));
+      }
     }
   }
   {

@@ -23,6 +23,7 @@
 // treats it as an ordinary complex slot and drops it at the flush; the small
 // kernel k_contract_slot0 adds the two real-bin terms exactly, which keeps the
 // hot loop free of per-slot special cases.
+#include "bulk.cuh"
 #include "common.cuh"
 #include "plan.h"
 
@@ -71,41 +72,6 @@ template <typename T, int DM, int NS> constexpr int maxreg_for() {
 // k-slots), the powers of yt and the row flags.  The chunk after next is in
 // flight while a chunk is being consumed; the arithmetic reads shared memory only.
 constexpr int kChunk = 16;
-
-// Bulk (TMA-engine) row copies tracked by an mbarrier transaction count.
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(uint64_t* m, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* m, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* m) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(m))
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* m, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(m)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: every try_wait suspends for at most a hardware-defined
-// interval, so the loop gives up after a bounded time instead of hanging.
-constexpr int kMaxSpin = 1 << 22;
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, unsigned parity) {
-  for (int it = 0; it < kMaxSpin; ++it)
-    if (mbar_try_wait(m, parity)) return true;
-  return false;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* m) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(m)) : "memory");
-}
 
 template <typename T, int DM, int KT, int MU>
 struct Stage {
@@ -494,6 +460,19 @@ static cudaError_t contract_T(const sfft_plan_s* p, int job0, int njobs, int row
   }
   k_contract_slot0<T, DM><<<dim3(njobs, max_uy<T>()), 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, H, p->M,
                                                                           p->Nf, L);
+  p->nlaunch += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_contract_slot0(const sfft_plan_s* p, int DM, int job0, int njobs, void* ws) {
+  if (njobs <= 0) return cudaSuccess;
+  const dim3 grid(njobs, max_uy<float>());
+  switch (DM) {
+    case 0: k_contract_slot0<float, 0><<<grid, 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, p->d.H, p->M, p->Nf, p->d.L); break;
+    case 2: k_contract_slot0<float, 2><<<grid, 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, p->d.H, p->M, p->Nf, p->d.L); break;
+    case 4: k_contract_slot0<float, 4><<<grid, 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, p->d.H, p->M, p->Nf, p->d.L); break;
+    default: return cudaErrorInvalidValue;
+  }
   p->nlaunch += 1;
   return cudaGetLastError();
 }

@@ -24,6 +24,19 @@ struct CJob {
 
 struct Region { size_t off = 0, bytes = 0; };
 
+// One CTA row of the tensor-core KK contraction (kernels_contract_tc.cu): the
+// pairs [pair0, pair0 + npair) of the pair table (int4 (d_local, u_y, ux_lo,
+// ux_hi), d_local within the d-batch) and the differences [dj0, dj0 + nd) of
+// the pattern table (int4 (d_local, u_lo, u_hi, first staged row)).
+struct TcJob {
+  int64_t probe, wts, out, status;   // byte offsets: slab of d_local = 0, weight spectra, G of d_local = 0, status
+  int pair0, npair, dj0, nd;
+};
+constexpr int kTcKT = 8;        // k-slots per CTA (one warp each)
+constexpr int kTcNT = 8;        // 8-column tiles per warp: up to 64 (d, u_y) pairs per CTA
+constexpr int kTcChunk = 32;    // weight rows per stage
+constexpr int kTcRowCap = 448;  // staged probe rows per stage: sum over differences of (chunk + n_lag - 1)
+
 }  // namespace sfft
 
 struct sfft_plan_s {
@@ -40,6 +53,8 @@ struct sfft_plan_s {
   int n_hd = 0;                       // half-plane differences
   std::vector<int2> dlist;            // (dy, dx) per half-plane difference
   int d_batch = 0, rows_per_cta = 0, csplit = 2;   // csplit: lag parts per (k-slot, group) in the contraction
+  bool tc = false;                    // KK contraction on the tensor cores (FP32 path)
+  int tc_rows = 0;                    // weight rows per CTA of the tensor-core contraction
   double tuned_ms = 0.0;              // autotuned build_normal time per CCD (0: not tuned)
   size_t elem = 4;                    // sizeof(T)
   // plan-owned constant device tables
@@ -56,6 +71,13 @@ struct sfft_plan_s {
   // job table sections: KK jobs of d-batch i start at kk_first[i]
   std::vector<int> kk_first, kk_count;
   int kb_first = 0, kb_count = 0, bk_first = 0, bk_count = 0;
+  // tensor-core KK contraction: jobs of d-batch i start at tc_first[i]
+  std::vector<int> tc_first, tc_count;
+  std::vector<sfft::TcJob> h_tcjobs;
+  std::vector<int4> h_tcpairs, h_tcdj;
+  sfft::TcJob* d_tcjobs = nullptr;
+  int4* d_tcpairs = nullptr;
+  int4* d_tcdj = nullptr;
   // workspace regions (per-CCD strides where noted)
   sfft::Region sky, skyacc, good, gh, mfit, rowflag, rm, wspec, uspec, rhat, phat, gkk, gkb, gbk,
       mom_bb, mom_b, eimg, lfac, scale, dinv, gbar, vec, theta_off, status;
@@ -85,6 +107,8 @@ cudaError_t launch_rfft_weights(const sfft_plan_s* p, const float* S, const void
 cudaError_t launch_rfft_prod(const sfft_plan_s* p, int d0, int nd, void* ws);
 cudaError_t launch_contract(const sfft_plan_s* p, int DM, int job0, int njobs, int rows_per_cta, int lag_parts,
                             void* ws);
+cudaError_t launch_contract_tc(const sfft_plan_s* p, int batch_index, void* ws);
+cudaError_t launch_contract_slot0(const sfft_plan_s* p, int DM, int job0, int njobs, void* ws);
 cudaError_t launch_scatter(const sfft_plan_s* p, double* A, double* b, void* ws, bool rhs_only, double* rhs_out);
 cudaError_t launch_cholesky(const sfft_plan_s* p, const double* A, void* ws);
 cudaError_t launch_chol_solve(const sfft_plan_s* p, const double* rhs, double* x, void* ws);
