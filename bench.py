@@ -38,9 +38,11 @@ WORKLOAD = ("one DECam CCD pair per GPU per step: 2048x4096 FP32, 20k stars, PSF
 # DRAM bytes (read + write) of one full-size KK contraction launch (all 221
 # differences), from a one-pass ncu capture of the benchmark workload
 # (profiles/dram_per_kernel_*.md); reported only while the kernel source is the
-# one that was measured.
-KK_TRAFFIC_BYTES = 10.066e9
-KK_TRAFFIC_SOURCE_SHA256_16 = "c6ab6cfcea4ede82"
+# one that was measured.  Keys: the kernel's source file.
+KK_TRAFFIC = {
+    "kernels_contract.cu": (10.09e9, "1a847c15ebf73406"),      # FP32 FMA kernel (--fma-contract)
+    "kernels_contract_tc.cu": (None, ""),                      # tensor-core kernel (default)
+}
 PHASES = ("prep", "fft_weights", "fft_prod", "contract_kk", "contract_rk", "scatter", "solve", "apply")
 
 
@@ -61,14 +63,37 @@ def kk_flops_per_ccd(H, W, L, DK):
     return half_plane_lag_rows(L) * (H - (L - 1)) * M * per
 
 
-def kk_traffic_bytes():
+def kk_traffic_bytes(src):
     import hashlib
-    path = os.path.join(ROOT, "paper_2603_08593_gb300", "csrc", "kernels_contract.cu")
+    val, want = KK_TRAFFIC.get(src, (None, ""))
+    path = os.path.join(ROOT, "paper_2603_08593_gb300", "csrc", src)
     try:
         h = hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
     except OSError:
         return None
-    return KK_TRAFFIC_BYTES if h == KK_TRAFFIC_SOURCE_SHA256_16 else None
+    return val if (val is not None and h == want) else None
+
+
+def kk_gemm_flops_per_ccd(H, W, L, DK):
+    """Algorithmic work of the KK contraction in its matrix-product form, one
+    CCD: per k-slot a real product of (monomial x Re/Im) rows, (2 x rows x
+    re/im) inner dimension and (d, u_y) columns, i.e. 8 flop per complex
+    multiply-add conj(W_m) P over every monomial, (d, u_y) pair, interior
+    row and complex spectrum slot (the packed real slot excluded)."""
+    M = max(64, 1 << (W - 1).bit_length()) // 2
+    return 8 * n_mono(2 * DK) * half_plane_lag_rows(L) * (H - (L - 1)) * (M - 1)
+
+
+def n_mono(D):
+    return (D + 1) * (D + 2) // 2
+
+
+def tf32_peak_tflops(sustained=True):
+    """Dense TF32 tensor peak from the measured BF16 cuBLAS peak and the
+    nominal TF32 : BF16 ratio (1.1 : 2.25 PFLOP/s)."""
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    bf16 = peaks["bf16_tflops_sustained" if sustained else "bf16_tflops"]
+    return bf16 * 1.1 / 2.25
 
 
 def fp32_alu_peak_tflops(clock_mhz):
@@ -302,12 +327,13 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     with torch.cuda.stream(stream):
         plan = Plan(Hs, W, L, DK, DB, batch=B, prec=args.prec, stream=stream, device=dev, d_batch=args.d_batch,
-                    graph=batched, autotune=0 if args.no_autotune else 1, lag_parts=args.lag_parts)
+                    graph=batched, autotune=0 if args.no_autotune else 1, lag_parts=args.lag_parts,
+                    fma_contract=args.fma_contract)
         tiles = plan.tiles
         if batched:
             # per-phase times and launch counts from an eager profiled pass of the same plan
             eager = Plan(Hs, W, L, DK, DB, batch=B, prec=args.prec, stream=stream, device=dev,
-                         d_batch=tiles[0], rows_per_cta=tiles[1], lag_parts=tiles[2])
+                         d_batch=tiles[0], rows_per_cta=tiles[1], lag_parts=tiles[2], fma_contract=args.fma_contract)
             eo = eager.subtract(R, S, bad, None, refine=REFINE)
             eager.profile(True)
             eager.profile_read(reset=True)
@@ -398,20 +424,39 @@ def run_gpu(args):
     roof = None
     clocks = clk.summary()
     if kk_n:
-        # one launch = k_contract over one batch of offset differences plus its
-        # k_contract_slot0 companion (the exact DC/Nyquist slot of the same sums)
+        # one launch = the KK contraction over one batch of offset differences
+        # plus its k_contract_slot0 companion (the exact DC/Nyquist slot)
         n_launch = kk_n / 2
-        per_launch_flop = B * kk_flops_per_ccd(Hs, W, L, DK) / (n_launch / args.steps)
         avg_ms = kk_ms / n_launch
-        achieved = per_launch_flop / (avg_ms * 1e-3) / 1e12
-        clock = 2070.0
-        peak = fp32_alu_peak_tflops(clock)
-        roof = {"bound": "alu", "kernel": "k_contract (product-spectrum lag contraction)", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": args.traffic if args.traffic is not None else (kk_traffic_bytes() if (Hs == H and B == 1 and tiles[0] == 221) else None),
-                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz max SM clock (derived, not measured)",
-                "avg_launch_ms": avg_ms, "launches_per_step": n_launch / args.steps,
-                "traffic_note": "DRAM read+write bytes per launch, one-pass ncu capture of this workload"}
+        on_tc = args.prec == "mixed" and not args.fma_contract
+        full = Hs == H and B == 1 and tiles[0] == 221
+        if on_tc:
+            # the split-operand product runs the matrix product once in TF32
+            # (hi x hi) and once more as two BF16 corrections at twice the TF32
+            # rate: 2 x F at the TF32 rate is the time the tensor cores need
+            per_launch_flop = 2 * B * kk_gemm_flops_per_ccd(Hs, W, L, DK) / (n_launch / args.steps)
+            achieved = per_launch_flop / (avg_ms * 1e-3) / 1e12
+            peak = tf32_peak_tflops(sustained=True)
+            roof = {"bound": "tensor", "kernel": "k_contract_tc (lag contraction as split TF32/BF16 mma.sync products)",
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": args.traffic if args.traffic is not None else (kk_traffic_bytes("kernels_contract_tc.cu") if full else None),
+                    "peak_note": "dense TF32 tensor peak of measured = sustained cuBLAS BF16 (MEASURED_PEAKS.json) x 1.1/2.25 "
+                                 "(nominal TF32:BF16); achieved counts 2 x the matrix-product flops (TF32 hi*hi + two BF16 "
+                                 "corrections at twice the TF32 rate)",
+                    "useful_tflops": per_launch_flop / 2 / (avg_ms * 1e-3) / 1e12,
+                    "avg_launch_ms": avg_ms, "launches_per_step": n_launch / args.steps,
+                    "traffic_note": "DRAM read+write bytes per launch, one-pass ncu capture of this workload"}
+        else:
+            per_launch_flop = B * kk_flops_per_ccd(Hs, W, L, DK) / (n_launch / args.steps)
+            achieved = per_launch_flop / (avg_ms * 1e-3) / 1e12
+            clock = 2070.0
+            peak = fp32_alu_peak_tflops(clock)
+            roof = {"bound": "alu", "kernel": "k_contract (product-spectrum lag contraction, FP32 FMA)",
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": args.traffic if args.traffic is not None else (kk_traffic_bytes("kernels_contract.cu") if full else None),
+                    "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz max SM clock (derived, not measured)",
+                    "avg_launch_ms": avg_ms, "launches_per_step": n_launch / args.steps,
+                    "traffic_note": "DRAM read+write bytes per launch, one-pass ncu capture of this workload"}
         if batched:
             roof["timing_note"] = "kernel durations from an eager profiled pass of the same plan (timed steps replay a CUDA graph)"
     if batched:
@@ -460,6 +505,8 @@ def main():
     ap.add_argument("--no-classifier", action="store_true", help="skip the stamp-classifier throughput figures")
     ap.add_argument("--only-classifier", action="store_true", help="print only the stamp-classifier figures")
     ap.add_argument("--lag-parts", type=int, default=0, choices=[0, 1, 2, 3], help="contraction lag parts (0: plan's)")
+    ap.add_argument("--fma-contract", action="store_true",
+                    help="mixed path: KK contraction on the FP32 FMA pipes instead of the tensor cores")
     args = ap.parse_args()
     if args.only_classifier:   # classifier figures alone (profiling captures)
         import torch

@@ -41,9 +41,9 @@ constexpr int kChunkTC = kTcChunk;   // 4 mma k-steps of 4 rows
 template <int DM> __host__ __device__ constexpr int n_mtiles() { return (n_mono(DM) + 7) / 8; }
 
 // Probe rows per stage: sum over the pattern's differences of (kChunkTC + n_lag - 1).
-template <int KT> struct TcStage {
+template <int KT, int CAP> struct TcStage {
   static constexpr int RS = KT + 2;   // float2 per staged row: KT slots + 16 bytes of padding (bank spread)
-  float2 P[kTcRowCap][RS];
+  float2 P[CAP][RS];
   float2 V[kMaxWeightDeg + 1][kChunkTC][RS];
   float ypw[kChunkTC][16];            // yt^b as duplicated pairs (the FP32 power table's 64-byte rows)
 };
@@ -84,8 +84,8 @@ __device__ __forceinline__ void mono_ab(int m, int& a, int& b) {
 // Issue the bulk copies of rows [yc, ye) into stage `st`, counted on `full`:
 // warp w copies the probe rows of the pattern's differences w, w + nwarp, ...
 // (lane i row i), then all threads copy the weight rows and thread 0 the powers of yt.
-template <int DM, int KT>
-__device__ __forceinline__ void tc_produce(TcStage<KT>& st, uint64_t* full, const char* __restrict__ probe,
+template <int DM, int KT, int CAP>
+__device__ __forceinline__ void tc_produce(TcStage<KT, CAP>& st, uint64_t* full, const char* __restrict__ probe,
                                            int64_t slab, const float2* __restrict__ V, const float* __restrict__ ytab,
                                            const int4* __restrict__ dj, int nd, int npair, int64_t HM, int M, int k0,
                                            int yc, int ye) {
@@ -113,7 +113,7 @@ __device__ __forceinline__ void tc_produce(TcStage<KT>& st, uint64_t* full, cons
 
 }  // namespace
 
-template <int DM, int KT, int NT>
+template <int DM, int KT, int NT, int CAP>
 __global__ void __launch_bounds__(KT * 32, 2)
 k_contract_tc(const TcJob* __restrict__ jobs, const int4* __restrict__ pairs, const int4* __restrict__ djobs,
               char* __restrict__ ws, int H, int M, int Nf, int L, int rows_per_cta, int64_t slab,
@@ -121,7 +121,7 @@ k_contract_tc(const TcJob* __restrict__ jobs, const int4* __restrict__ pairs, co
   constexpr int NMT = n_mtiles<DM>();
   constexpr int NMONO = n_mono(DM);
   constexpr int NP = 8 * NT;
-  using St = TcStage<KT>;
+  using St = TcStage<KT, CAP>;
   constexpr int RS = St::RS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   St* stages = reinterpret_cast<St*>(smem_raw);
@@ -188,13 +188,13 @@ k_contract_tc(const TcJob* __restrict__ jobs, const int4* __restrict__ pairs, co
 
   const int nchunk = y1 > y0 ? (y1 - y0 + kChunkTC - 1) / kChunkTC : 0;
   if (nchunk > 0)
-    tc_produce<DM, KT>(stages[0], &full[0], probe, slab, V, ytab, dj, job.nd, job.npair, HM, M, k0, y0,
+    tc_produce<DM, KT, CAP>(stages[0], &full[0], probe, slab, V, ytab, dj, job.nd, job.npair, HM, M, k0, y0,
                        min(y0 + kChunkTC, y1));
   for (int c = 0; c < nchunk; ++c) {
     const int yc = y0 + c * kChunkTC, ye = min(yc + kChunkTC, y1);
     if (c + 1 < nchunk) {   // stage (c+1)&1 was released by the barrier that closed chunk c - 1
       const int yn = yc + kChunkTC;
-      tc_produce<DM, KT>(stages[(c + 1) & 1], &full[(c + 1) & 1], probe, slab, V, ytab, dj, job.nd, job.npair, HM,
+      tc_produce<DM, KT, CAP>(stages[(c + 1) & 1], &full[(c + 1) & 1], probe, slab, V, ytab, dj, job.nd, job.npair, HM,
                          M, k0, yn, min(yn + kChunkTC, y1));
     }
     const bool landed = mbar_wait_bounded(&full[c & 1], (unsigned)((c >> 1) & 1));
@@ -260,7 +260,8 @@ k_contract_tc(const TcJob* __restrict__ jobs, const int4* __restrict__ pairs, co
     __syncthreads();
   }
 
-  // ---- flush: lag DFT over the CTA's k-slots into shared FP32 sums, then FP64 atomics
+  // ---- flush: lag DFT over the CTA's k-slots into shared FP32 sums (fixed
+  // order), then FP64 atomics
   constexpr int RM = 8 * NMT + 1;   // monomials per (pair, u_x) entry, padded against bank conflicts
   const int nred = NP * L * RM;
   for (int i = threadIdx.x; i < nred; i += blockDim.x) red[i] = 0.f;
@@ -272,48 +273,55 @@ k_contract_tc(const TcJob* __restrict__ jobs, const int4* __restrict__ pairs, co
     tw[kk * kMaxL + lane] = make_float2(2.f * cs.x, 2.f * cs.y);
   }
   __syncthreads();
-  if (k != 0 && k < M) {   // slot 0: the packed real bins, summed by k_contract_slot0
+  // the warps add their k-slot's terms in turn (a fixed order, so the sums do
+  // not depend on scheduling); within a warp every lane owns distinct entries
+  for (int turn = 0; turn < KT; ++turn) {
+    if (warp == turn && k != 0 && k < M) {   // slot 0: the packed real bins, summed by k_contract_slot0
 #pragma unroll
-    for (int n = 0; n < NT; ++n) {
+      for (int n = 0; n < NT; ++n) {
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const int q = n * 8 + 2 * t + j;
-        if (q >= job.npair) continue;
-        const int4 pq = pr[q];
+        for (int j = 0; j < 2; ++j) {
+          const int q = n * 8 + 2 * t + j;
+          if (q >= job.npair) continue;
+          const int4 pq = pr[q];
 #pragma unroll
-        for (int m = 0; m < NMT; ++m) {
-          if (!vm[m]) continue;
-          const float cr = acc[m][n][j], ci = acc[m][n][2 + j];
-          float* dst = red + (q * L + w) * RM + m * 8 + g;
-          for (int ux = pq.z; ux <= pq.w; ++ux) {
-            const float2 c2 = tw[kk * kMaxL + ux + w];
-            atomicAdd(dst + ux * RM, cr * c2.x + ci * c2.y);
+          for (int m = 0; m < NMT; ++m) {
+            if (!vm[m]) continue;
+            const float cr = acc[m][n][j], ci = acc[m][n][2 + j];
+            float* dst = red + (q * L + w) * RM + m * 8 + g;
+            for (int ux = pq.z; ux <= pq.w; ++ux) {
+              const float2 c2 = tw[kk * kMaxL + ux + w];
+              atomicAdd(dst + ux * RM, cr * c2.x + ci * c2.y);   // one add per entry per turn
+            }
           }
         }
       }
     }
+    __syncthreads();
   }
-  __syncthreads();
   const double inv = 1.0 / (double)Nf;
   double* out = reinterpret_cast<double*>(ws + job.out);
   const int LL = L * L;
-  for (int i = threadIdx.x; i < NMONO * job.npair * L; i += blockDim.x) {
-    const int ux = i % L - w, q = (i / L) % job.npair, mono = i / (L * job.npair);
+  for (int q = warp; q < job.npair; q += KT) {   // one pair per warp: its (u_x, monomial) entries over the lanes
     const int4 pq = pr[q];
-    if (ux < pq.z || ux > pq.w) continue;
-    const float v = red[(q * L + ux + w) * RM + mono];
-    if (v != 0.f)
-      atomicAdd(out + ((int64_t)pq.x * LL + (pq.y + w) * L + (ux + w)) * NMONO + mono, (double)v * inv);
+    const int nval = (pq.w - pq.z + 1) * NMONO;
+    double* o = out + ((int64_t)pq.x * LL + (pq.y + w) * L + (pq.z + w)) * NMONO;
+    const float* rq = red + (q * L + pq.z + w) * RM;
+    for (int e = lane; e < nval; e += 32) {
+      const int iu = e / NMONO, mono = e - iu * NMONO;
+      const float v = rq[iu * RM + mono];
+      if (v != 0.f) atomicAdd(o + e, (double)v * inv);
+    }
   }
 }
 
-template <int DM>
+template <int DM, int NT, int CAP>
 static cudaError_t contract_tc_dm(const sfft_plan_s* p, int job0, int njobs, void* ws) {
-  constexpr int KT = kTcKT, NT = kTcNT;
-  const size_t smem = 2 * sizeof(TcStage<KT>) + 16 + sizeof(float2) * KT * kMaxL;
-  static_assert(sizeof(float) * (n_mtiles<DM>() * 8 + 1) * 8 * NT * kMaxL <= 2 * sizeof(TcStage<KT>),
+  constexpr int KT = kTcKT;
+  const size_t smem = 2 * sizeof(TcStage<KT, CAP>) + 16 + sizeof(float2) * KT * kMaxL;
+  static_assert(sizeof(float) * (n_mtiles<DM>() * 8 + 1) * 8 * NT * kMaxL <= 2 * sizeof(TcStage<KT, CAP>),
                 "flush sums must fit in the stage memory");
-  auto kern = k_contract_tc<DM, KT, NT>;
+  auto kern = k_contract_tc<DM, KT, NT, CAP>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);   // two CTAs per SM
   const int H = p->d.H;
@@ -334,9 +342,9 @@ cudaError_t launch_contract_tc(const sfft_plan_s* p, int batch_index, void* ws) 
   const int job0 = p->tc_first[batch_index], njobs = p->tc_count[batch_index];
   if (njobs <= 0) return cudaSuccess;
   switch (p->DM_KK) {
-    case 0: return contract_tc_dm<0>(p, job0, njobs, ws);
-    case 2: return contract_tc_dm<2>(p, job0, njobs, ws);
-    case 4: return contract_tc_dm<4>(p, job0, njobs, ws);
+    case 0: return contract_tc_dm<0, kTcNT, kTcRowCap>(p, job0, njobs, ws);
+    case 2: return contract_tc_dm<2, kTcNT, kTcRowCap>(p, job0, njobs, ws);
+    case 4: return contract_tc_dm<4, kTcNT, kTcRowCap>(p, job0, njobs, ws);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -32,10 +32,10 @@ struct TcJob {
   int64_t probe, wts, out, status;   // byte offsets: slab of d_local = 0, weight spectra, G of d_local = 0, status
   int pair0, npair, dj0, nd;
 };
-constexpr int kTcKT = 8;        // k-slots per CTA (one warp each)
-constexpr int kTcNT = 8;        // 8-column tiles per warp: up to 64 (d, u_y) pairs per CTA
-constexpr int kTcChunk = 32;    // weight rows per stage
-constexpr int kTcRowCap = 448;  // staged probe rows per stage: sum over differences of (chunk + n_lag - 1)
+constexpr int kTcKT = 8;         // k-slots per CTA (one warp each)
+constexpr int kTcNT = 8;         // 8-column tiles per warp: up to 64 (d, u_y) pairs per CTA
+constexpr int kTcChunk = 32;     // weight rows per stage
+constexpr int kTcRowCap = 448;   // staged probe rows per stage: sum over differences of (chunk + n_lag - 1)
 
 }  // namespace sfft
 
