@@ -41,7 +41,8 @@ WORKLOAD = ("one DECam CCD pair per GPU per step: 2048x4096 FP32, 20k stars, PSF
 # one that was measured.  Keys: the kernel's source file.
 KK_TRAFFIC = {
     "kernels_contract.cu": (10.09e9, "1a847c15ebf73406"),      # FP32 FMA kernel (--fma-contract)
-    "kernels_contract_tc.cu": (None, ""),                      # tensor-core kernel (default)
+    "kernels_contract_tc.cu": (None, ""),                      # mma.sync kernel (--mma-sync-contract)
+    "kernels_contract_umma.cu": (None, ""),                    # tcgen05 kernel (default)
 }
 PHASES = ("prep", "fft_weights", "fft_prod", "contract_kk", "contract_rk", "scatter", "solve", "apply")
 
@@ -328,12 +329,13 @@ def run_gpu(args):
     with torch.cuda.stream(stream):
         plan = Plan(Hs, W, L, DK, DB, batch=B, prec=args.prec, stream=stream, device=dev, d_batch=args.d_batch,
                     graph=batched, autotune=0 if args.no_autotune else 1, lag_parts=args.lag_parts,
-                    fma_contract=args.fma_contract)
+                    fma_contract=args.fma_contract, mma_sync_contract=args.mma_sync_contract)
         tiles = plan.tiles
         if batched:
             # per-phase times and launch counts from an eager profiled pass of the same plan
             eager = Plan(Hs, W, L, DK, DB, batch=B, prec=args.prec, stream=stream, device=dev,
-                         d_batch=tiles[0], rows_per_cta=tiles[1], lag_parts=tiles[2], fma_contract=args.fma_contract)
+                         d_batch=tiles[0], rows_per_cta=tiles[1], lag_parts=tiles[2], fma_contract=args.fma_contract,
+                         mma_sync_contract=args.mma_sync_contract)
             eo = eager.subtract(R, S, bad, None, refine=REFINE)
             eager.profile(True)
             eager.profile_read(reset=True)
@@ -437,9 +439,12 @@ def run_gpu(args):
             per_launch_flop = 2 * B * kk_gemm_flops_per_ccd(Hs, W, L, DK) / (n_launch / args.steps)
             achieved = per_launch_flop / (avg_ms * 1e-3) / 1e12
             peak = tf32_peak_tflops(sustained=True)
-            roof = {"bound": "tensor", "kernel": "k_contract_tc (lag contraction as split TF32/BF16 mma.sync products)",
+            kname = ("k_contract_tc (lag contraction as split TF32/BF16 mma.sync products)" if args.mma_sync_contract
+                     else "k_contract_umma (lag contraction as split TF32/BF16 tcgen05 products, accumulators in TMEM)")
+            ksrc = "kernels_contract_tc.cu" if args.mma_sync_contract else "kernels_contract_umma.cu"
+            roof = {"bound": "tensor", "kernel": kname,
                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": args.traffic if args.traffic is not None else (kk_traffic_bytes("kernels_contract_tc.cu") if full else None),
+                    "traffic": args.traffic if args.traffic is not None else (kk_traffic_bytes(ksrc) if full else None),
                     "peak_note": "dense TF32 tensor peak of measured = sustained cuBLAS BF16 (MEASURED_PEAKS.json) x 1.1/2.25 "
                                  "(nominal TF32:BF16); achieved counts 2 x the matrix-product flops (TF32 hi*hi + two BF16 "
                                  "corrections at twice the TF32 rate)",
@@ -507,6 +512,8 @@ def main():
     ap.add_argument("--lag-parts", type=int, default=0, choices=[0, 1, 2, 3], help="contraction lag parts (0: plan's)")
     ap.add_argument("--fma-contract", action="store_true",
                     help="mixed path: KK contraction on the FP32 FMA pipes instead of the tensor cores")
+    ap.add_argument("--mma-sync-contract", action="store_true",
+                    help="mixed path: tensor-core KK contraction through mma.sync instead of tcgen05")
     args = ap.parse_args()
     if args.only_classifier:   # classifier figures alone (profiling captures)
         import torch

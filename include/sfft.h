@@ -80,7 +80,9 @@ typedef enum {
 #define SFFT_FLAG_GRAPH 1u        /* sfft_subtract replays a captured CUDA graph */
 #define SFFT_FLAG_CONST_RATIO 2u  /* kernel sum constant over the chip (constrained fit) */
 #define SFFT_FLAG_FMA_CONTRACT 4u /* mixed path: KK contraction on the FP32 FMA pipes instead of the
-                                     three-term TF32 split on the tensor cores (the default) */
+                                     split TF32/BF16 products on the tensor cores (the default) */
+#define SFFT_FLAG_MMA_SYNC_CONTRACT 8u /* mixed path: the tensor-core KK contraction with warp-level
+                                          mma.sync instead of tcgen05 (the default) */
 
 typedef struct {
   int32_t H, W;              /* image rows, columns */

@@ -18,6 +18,7 @@ PREC = {"fp64": 0, "mixed": 1}
 FLAG_GRAPH = 1
 FLAG_CONST_RATIO = 2
 FLAG_FMA_CONTRACT = 4
+FLAG_MMA_SYNC_CONTRACT = 8
 
 
 class Desc(C.Structure):
@@ -132,10 +133,13 @@ class Plan:
     const_ratio=True holds the kernel sum constant over the chip
     (SFFT_FLAG_CONST_RATIO); theta keeps the full N-term layout.
     fma_contract=True runs the mixed path's KK contraction on the FP32 FMA
-    pipes instead of the tensor cores (SFFT_FLAG_FMA_CONTRACT)."""
+    pipes instead of the tensor cores (SFFT_FLAG_FMA_CONTRACT);
+    mma_sync_contract=True keeps it on the tensor cores through warp-level
+    mma.sync instead of tcgen05 (SFFT_FLAG_MMA_SYNC_CONTRACT)."""
 
     def __init__(self, H, W, L, DK, DB, batch=1, prec="mixed", d_batch=0, rows_per_cta=0, autotune=0,
-                 graph=False, stream=None, device=None, lag_parts=0, const_ratio=False, fma_contract=False):
+                 graph=False, stream=None, device=None, lag_parts=0, const_ratio=False, fma_contract=False,
+                 mma_sync_contract=False):
         import torch
         self._torch = torch
         lib = load()
@@ -144,7 +148,8 @@ class Plan:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.desc = Desc(H, W, L, DK, DB, batch, PREC[prec], autotune, d_batch, rows_per_cta, lag_parts,
                          (FLAG_GRAPH if graph else 0) | (FLAG_CONST_RATIO if const_ratio else 0) |
-                         (FLAG_FMA_CONTRACT if fma_contract else 0))
+                         (FLAG_FMA_CONTRACT if fma_contract else 0) |
+                         (FLAG_MMA_SYNC_CONTRACT if mma_sync_contract else 0))
         h = VP()
         with torch.cuda.device(self.device):
             _check(lib.sfft_plan(C.byref(self.desc), VP(self.stream.cuda_stream), C.byref(h)), "sfft_plan")

@@ -203,11 +203,11 @@ static void build_jobs(sfft_plan_s* p) {
 
 // Pair lists and patterns of the tensor-core KK contraction: per d-batch the
 // (d, u_y) pairs in difference order, cut greedily into patterns of at most
-// 8 kTcNT pairs whose staged probe rows (kTcChunk + n_lag - 1 per difference)
-// fit kTcRowCap; one job per (CCD, pattern).
-static void build_tc_jobs(sfft_plan_s* p) {
+// NP pairs from at most max_nd differences whose staged probe rows (chunk +
+// n_lag - 1 per difference) fit `cap`; one job per (CCD, pattern).
+static void build_tc_jobs(sfft_plan_s* p, int NP, int chunk, int cap, int max_nd) {
   const int L = p->d.L, w = p->w, B = p->d.batch, H = p->d.H;
-  const int LL = L * L, NP = 8 * kTcNT;
+  const int LL = L * L;
   const size_t slab = (size_t)H * p->M * 2 * p->elem;
   p->tc_first.clear();
   p->tc_count.clear();
@@ -233,8 +233,8 @@ static void build_tc_jobs(sfft_plan_s* p) {
       while (q < npairs && pt.npair < NP) {
         const int4 e = p->h_tcpairs[pair_base + q];
         const bool new_d = pt.nd == 0 || p->h_tcdj.back().x != e.x;
-        const int add = new_d ? kTcChunk : 1;
-        if (rows + add > kTcRowCap) break;
+        const int add = new_d ? chunk : 1;
+        if (rows + add > cap || (new_d && pt.nd == max_nd)) break;
         if (new_d) {
           p->h_tcdj.push_back(int4{e.x, e.y, e.y, rows});
           ++pt.nd;
@@ -302,7 +302,8 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
   if (d.DK < 0 || d.DB < 0 || d.d_batch < 0 || d.rows_per_cta < 0) return SFFT_ERR_ARG;
   if (d.lag_parts < 0 || d.lag_parts > 3) return SFFT_ERR_ARG;
   if ((d.L & 1) == 0 || d.L > kMaxL) return SFFT_ERR_UNSUPPORTED;
-  if (d.flags & ~(SFFT_FLAG_GRAPH | SFFT_FLAG_CONST_RATIO | SFFT_FLAG_FMA_CONTRACT)) return SFFT_ERR_ARG;
+  if (d.flags & ~(SFFT_FLAG_GRAPH | SFFT_FLAG_CONST_RATIO | SFFT_FLAG_FMA_CONTRACT | SFFT_FLAG_MMA_SYNC_CONTRACT))
+    return SFFT_ERR_ARG;
   if (d.DK > kMaxD || d.DB > kMaxD) return SFFT_ERR_UNSUPPORTED;
   if (d.H < d.L || d.W < d.L || d.W < 16 || d.W > 2048) return SFFT_ERR_UNSUPPORTED;
 
@@ -360,10 +361,12 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
   // row flags are bulk-copied in 16-byte aligned runs of up to 20 ints past a chunk start
   p->rf_stride = ((d.H + 32) + 63) / 64 * 64;
   p->tc = !p->fp64 && !(d.flags & SFFT_FLAG_FMA_CONTRACT);
+  p->umma = p->tc && !(d.flags & SFFT_FLAG_MMA_SYNC_CONTRACT);
   p->tc_rows = d.H;
   build_layout(p);
   build_jobs(p);
-  if (p->tc) build_tc_jobs(p);
+  if (p->umma) build_tc_jobs(p, kUmmaPairs, 1, 1 << 30, kUmmaMaxDiffs);
+  else if (p->tc) build_tc_jobs(p, 8 * kTcNT, kTcChunk, kTcRowCap, 1 << 30);
 
   // yt(y)^b for b = 0..4 per row, FP64 on the host, stored in the path's precision
   std::vector<double> ypow((size_t)d.H * 8, 0.0);
@@ -465,7 +468,7 @@ static sfft_status_t build_normal_impl(sfft_plan_t p, const float* R, const floa
     {
       Phase ph(p, SFFT_PROF_CONTRACT_KK);
       if (p->tc) {
-        CK(launch_contract_tc(p, (int)ib, ws));
+        CK(p->umma ? launch_contract_umma(p, (int)ib, ws) : launch_contract_tc(p, (int)ib, ws));
         CK(launch_contract_slot0(p, p->DM_KK, p->kk_first[ib], p->kk_count[ib], ws));
       } else {
         CK(launch_contract(p, p->DM_KK, p->kk_first[ib], p->kk_count[ib], p->rows_per_cta, p->csplit, ws));

@@ -1,0 +1,482 @@
+// Lag contraction of the product spectra on the fifth-generation tensor cores
+// (tcgen05, FP32 path, KK block).
+//
+// The arithmetic is that of kernels_contract_tc.cu: for one k-slot the y sum
+//   C[(d, u_y)][(m, Re|Im)] = sum_y conj(W_m(y)) P^_d(y - u_y),  W_m = yt^b V^_a,
+// is a real matrix product whose rows are the (d, u_y) pairs of a pattern (128
+// TMEM lanes), whose columns are the monomials (Re: 0..15, Im: 16..31) and whose
+// inner dimension runs over rows y and (re, im).  Each product x y is taken as
+// hi_x hi_y on the TF32 path (kind::tf32, K = 8 = four rows) plus
+// bf16(hi_x) bf16(lo_y) + bf16(lo_x) bf16(y) on the BF16 path (kind::f16,
+// K = 16), hi the TF32 truncation and lo = x - hi, as in the split-operand
+// scheme of Ootomo and Yokota (2022).  The accumulators of the CTA's eight
+// k-slots (32 FP32 columns each) stay in tensor memory for the whole band.
+//
+// Roles (320 threads, one CTA per SM):
+//   warps 0-3  A producers: lane l of warp w is pair 32 w + l; per unit
+//              (k-slot, four rows) it loads its four probe values from the
+//              staged rows, splits them and stores the 16 A columns of the
+//              unit to tensor memory (tcgen05.st); at the end they read the
+//              accumulators back (tcgen05.ld) for the lag DFT;
+//   warps 4-7  B producers: warp 4 + b builds the tiles of k-slots b and
+//              b + 4, forming W_m for the unit's four rows and writing the
+//              TF32 and BF16 operand tiles (32 x 32 bytes each, K-major, no
+//              swizzle) to shared memory;
+//   warp 8     MMA issuer: one elected lane issues the sixteen MMAs of a
+//              k-step group (two per k-slot) and one commit;
+//   warp 9     copy producer: stages, 32 weight rows at a time and into two
+//              alternating stages, one tensor-copy box of probe rows per
+//              difference of the pattern, one box of weight rows per exponent
+//              and the powers of yt.
+// A unit is one k-slot over four rows; the eight units of a k-step form a
+// group, and groups alternate between two slots (A: 128 TMEM columns, B: 16 KB
+// of shared memory) with mbarrier hand-offs (A written, B written, MMAs done),
+// so that the next group is built while the tensor cores run the current one; every wait
+// is bounded, and a wait that gives up flags the CCD (status bit 4) and makes
+// every role leave its loop, after which the issued copies and MMAs are
+// drained (bounded) and the tensor memory is freed.
+#include <cuda.h>
+
+#include "bulk.cuh"
+#include "common.cuh"
+#include "plan.h"
+
+namespace sfft {
+
+namespace {
+
+constexpr int KT = kUmmaKT;          // k-slots per CTA
+constexpr int CH = kUmmaChunk;       // weight rows per stage
+constexpr int GSLOT = 2;             // k-step groups in flight (A: 128 TMEM columns, B: 16 KB each)
+constexpr int PITCH = 80;            // bytes per staged row: 10 spectrum slots (the CTA's 8 and 2 more)
+constexpr int BOXW = PITCH / 4;      // floats per staged row (the tensor box's inner extent)
+constexpr int RBOX_MAX = CH + (kMaxL - 1) + 7;   // probe rows per box: chunk, lag range, bank shift
+constexpr int DSLOT = (RBOX_MAX * PITCH + 127) / 128 * 128;   // bytes per difference in a stage
+constexpr int NDMAX = kUmmaMaxDiffs; // differences per pattern
+constexpr int VSLOT = CH * PITCH;    // bytes per weight exponent in a stage
+constexpr int NTHREADS = 320;
+constexpr int TMEM_COLS = 512;       // D: KT x 32 columns, A: GSLOT x KT x 16 columns
+
+// One stage: a box of probe rows per difference (tensor copies; box i starts
+// i % 8 rows early so that the differences' rows fall on different banks),
+// a box of weight rows per exponent a, and the powers of yt.  Offsets are
+// multiples of 128 bytes, as the tensor copies require.
+struct UStage {
+  uint8_t P[NDMAX][DSLOT];
+  uint8_t V[kMaxWeightDeg + 1][VSLOT];
+  float ypw[CH][16];
+};
+static_assert(DSLOT % 128 == 0 && VSLOT % 128 == 0 && sizeof(UStage) % 128 == 0, "tensor copy alignment");
+
+struct USmem {
+  UStage st[2];
+  uint8_t btile[GSLOT][KT][2][1024];   // per group slot and k-slot: TF32 tile, BF16 tile (32 rows x 32 bytes,
+                                       // canonical K-major)
+  uint64_t raw_full[2], raw_empty[2];
+  uint64_t a_full[GSLOT], b_full[GSLOT], mma_done[GSLOT];
+  uint64_t done;
+  float2 tw[KT][kMaxL];
+  uint32_t tmem_base;
+  int abort;
+};
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  // canonical K-major layout without swizzle: core matrices of 8 rows x 16
+  // bytes, 128 bytes apart along K (leading byte offset) and 256 bytes apart
+  // along the 8-row groups (stride byte offset); descriptor version 1
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)(128u >> 4) << 16;
+  d |= (uint64_t)(256u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// instruction descriptor: D FP32, A and B of format `fmt` (1 = BF16 for
+// kind::f16, 2 = TF32 for kind::tf32), both K-major, M = 128, N = 32
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+// tiled tensor copy of a 3-D box (x innermost) into shared memory, counted on `bar`
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool elect_one() {
+  uint32_t pred = 0;
+  asm volatile("{\n .reg .pred P;\n elect.sync _|P, 0xffffffff;\n selp.u32 %0, 1, 0, P;\n}\n" : "=r"(pred));
+  return pred != 0;
+}
+
+__device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+__device__ __forceinline__ void mono_ab(int m, int& a, int& b) {
+  int n = 0;
+  while ((n + 1) * (n + 2) / 2 <= m) ++n;
+  b = m - n * (n + 1) / 2;
+  a = n - b;
+}
+
+// Bounded wait on a phase; gives up when the spin budget runs out or another
+// role has given up, and then raises the shared abort flag.
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, unsigned parity, volatile int* abort) {
+  for (int it = 0; it < kMaxSpin; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63) == 63 && *abort) return false;
+  }
+  *abort = 1;
+  return false;
+}
+
+}  // namespace
+
+template <int DM>
+__global__ void __launch_bounds__(NTHREADS, 1)
+k_contract_umma(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmV,
+                const TcJob* __restrict__ jobs, const int4* __restrict__ pairs, const int4* __restrict__ djobs,
+                char* __restrict__ ws, int H, int M, int Nf, int L, int rows_per_cta, int rbox,
+                const float2* __restrict__ twD, const float* __restrict__ ytab) {
+  constexpr int NMONO = n_mono(DM);
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  USmem& S = *reinterpret_cast<USmem*>(smem_raw);
+  volatile int* abort = &S.abort;
+
+  const TcJob job = jobs[blockIdx.y];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = (L - 1) / 2;
+  const int k0 = blockIdx.x * KT;
+  const int4* dj = djobs + job.dj0;
+  const int4* pr = pairs + job.pair0;
+  int y0 = blockIdx.z * rows_per_cta, y1 = y0 + rows_per_cta;
+  if (y0 < w) y0 = w;
+  if (y1 > H - w) y1 = H - w;
+  const int nchunk = y1 > y0 ? (y1 - y0 + CH - 1) / CH : 0;
+  const int ngroup = nchunk * (CH / 4);   // k-step groups: the eight k-slots' units of four rows
+  // ---- setup: zeroed stages, barriers, tensor memory, twiddles
+  for (int i = threadIdx.x; i < (int)(sizeof(UStage) * 2 / 16); i += NTHREADS)
+    reinterpret_cast<float4*>(&S.st[0])[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2; ++i) { mbar_init(&S.raw_full[i], 1); mbar_init(&S.raw_empty[i], 8); }
+    for (int i = 0; i < GSLOT; ++i) { mbar_init(&S.a_full[i], 4); mbar_init(&S.b_full[i], 4); mbar_init(&S.mma_done[i], 1); }
+    mbar_init(&S.done, 1);
+    S.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x < KT * kMaxL) {
+    const int kk = threadIdx.x / kMaxL, ux = threadIdx.x % kMaxL - w;
+    int idx = (int)(((int64_t)(k0 + kk) * ux) % Nf);
+    if (idx < 0) idx += Nf;
+    const float2 cs = twD[idx];
+    S.tw[kk][threadIdx.x % kMaxL] = make_float2(2.f * cs.x, 2.f * cs.y);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
+                 "n"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = S.tmem_base;
+  const uint32_t t_d = tbase;                   // accumulators: k-slot kk at columns 32 kk
+  const uint32_t t_a = tbase + 32 * KT;         // A: group slot g, k-slot kk at columns 128 g + 16 kk
+                                                // (TF32 0-7, BF16 8-15)
+
+  int issued_chunks = 0;   // bulk-copy warp: chunks whose copies were issued
+
+  if (warp == 9) {
+    // ---- copy producer: per chunk one tensor copy per difference and per
+    // weight exponent and one bulk copy of the powers of yt
+    for (int c = 0; c < nchunk; ++c) {
+      const int sidx = c & 1;
+      if (c >= 2 && !wait_phase(&S.raw_empty[sidx], (unsigned)(((c >> 1) - 1) & 1), abort)) break;
+      UStage& st = S.st[sidx];
+      const int yc = y0 + c * CH, ye = min(yc + CH, y1), nrow = ye - yc;
+      if (lane == 0)
+        mbar_arrive_expect_tx(&S.raw_full[sidx], (unsigned)(job.nd * rbox * PITCH + (DM + 1) * VSLOT + nrow * 64));
+      __syncwarp();
+      if (lane < job.nd) {
+        const int4 e = dj[lane];   // (d_local, u_lo, u_hi, -): rows yc - u_hi - lane % 8 ...
+        tma_load_3d(&st.P[lane][0], &tmP, 2 * k0, yc - e.z - lane % 8, e.x, &S.raw_full[sidx]);
+      } else if (lane < job.nd + DM + 1) {
+        const int a = lane - job.nd;
+        tma_load_3d(&st.V[a][0], &tmV, 2 * k0, yc, a, &S.raw_full[sidx]);
+      } else if (lane == 31) {
+        bulk_copy_g2s(&st.ypw[0][0], ytab + (int64_t)yc * 16, (unsigned)(nrow * 64), &S.raw_full[sidx]);
+      }
+      issued_chunks = c + 1;
+      __syncwarp();
+    }
+  } else if (warp == 8) {
+    // ---- MMA issuer: per k-step group, sixteen MMAs and one commit
+    constexpr uint32_t id_tf32 = instr_desc(2), id_bf16 = instr_desc(1);
+    for (int g = 0; g < ngroup; ++g) {
+      const int slot = g & 1;
+      const unsigned par = (unsigned)((g >> 1) & 1);
+      if (!wait_phase(&S.a_full[slot], par, abort) || !wait_phase(&S.b_full[slot], par, abort)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t acc = g > 0 ? 1u : 0u;   // the first group starts the accumulators
+      if (elect_one()) {
+#pragma unroll
+        for (int kk = 0; kk < KT; ++kk) {
+          const uint32_t dcol = t_d + 32 * kk, acol = t_a + 128 * slot + 16 * kk;
+          const uint64_t bt = smem_desc(smem_u32(&S.btile[slot][kk][0][0]));
+          const uint64_t bb = smem_desc(smem_u32(&S.btile[slot][kk][1][0]));
+          asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                       " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n"
+                       ::"r"(dcol), "r"(acol), "l"(bt), "r"(id_tf32), "r"(acc) : "memory");
+          asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                       " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n"
+                       ::"r"(dcol), "r"(acol + 8), "l"(bb), "r"(id_bf16), "r"(1u) : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     ::"r"(smem_u32(&S.mma_done[slot])) : "memory");
+      }
+      __syncwarp();
+    }
+    // every MMA issued so far completes before the accumulators are read or freed
+    if (elect_one())
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   ::"r"(smem_u32(&S.done)) : "memory");
+    __syncwarp();
+    for (int it = 0; it < kMaxSpin && !mbar_try_wait(&S.done, 0); ++it) {
+    }
+  } else if (warp < 4) {
+    // ---- A producers: pair q = 32 warp + lane; per group the eight k-slots'
+    // A columns, one store wait and one arrival
+    int q = 32 * warp + lane;
+    if (q >= job.npair) q = 0;   // lanes past the pattern mirror pair 0; their rows are dropped
+    const int4 pq = pr[q];
+    int off0 = 0;   // byte offset in a stage of (pair, weight row yc, slot 0)
+    for (int i = 0; i < job.nd; ++i)
+      if (dj[i].x == pq.x) off0 = i * DSLOT + (dj[i].z + i % 8 - pq.y) * PITCH;
+    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+    for (int c = 0; c < nchunk && !*abort; ++c) {
+      const int sidx = c & 1;
+      if (!wait_phase(&S.raw_full[sidx], (unsigned)((c >> 1) & 1), abort)) break;
+      const uint8_t* P = &S.st[sidx].P[0][0] + off0;
+      for (int s = 0; s < CH / 4; ++s) {
+        const int g = c * (CH / 4) + s, slot = g & 1;
+        if (g >= 2 && !wait_phase(&S.mma_done[slot], (unsigned)(((g >> 1) - 1) & 1), abort)) break;
+#pragma unroll 2
+        for (int kk = 0; kk < KT; ++kk) {
+          uint32_t v[16];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const float2 pv = *reinterpret_cast<const float2*>(P + (4 * s + r) * PITCH + kk * 8);
+            const float hr = tf32_trunc(pv.x), hi = tf32_trunc(pv.y);
+            v[2 * r] = __float_as_uint(hr);        // TF32 columns: k = 2 r + (re, im)
+            v[2 * r + 1] = __float_as_uint(hi);
+            v[8 + r] = pack_bf16(hr, hi);          // BF16 columns 0-3: hi(P) of row r
+            v[12 + r] = pack_bf16(pv.x - hr, pv.y - hi);   // BF16 columns 4-7: lo(P) of row r
+          }
+          asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                       "%12, %13, %14, %15, %16};"
+                       ::"r"(t_a + 128 * slot + 16 * kk + lane_off), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]),
+                         "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]),
+                         "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]) : "memory");
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.a_full[slot]);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.raw_empty[sidx]);
+    }
+  } else {
+    // ---- B producers: warp 4 + bw builds the tiles of k-slots bw and bw + 4 of
+    // every group; lane: monomial m = lane % 16, rows r = lane / 16 and + 2
+    const int bw = warp - 4;
+    const int m = lane & 15, r0 = lane >> 4;
+    int am = 0, bm = 0;
+    mono_ab(m < NMONO ? m : 0, am, bm);
+    const bool live = m < NMONO;
+    for (int c = 0; c < nchunk && !*abort; ++c) {
+      const int sidx = c & 1;
+      if (!wait_phase(&S.raw_full[sidx], (unsigned)((c >> 1) & 1), abort)) break;
+      const UStage& st = S.st[sidx];
+      const int yc = y0 + c * CH, ye = min(yc + CH, y1);
+      for (int s = 0; s < CH / 4; ++s) {
+        const int g = c * (CH / 4) + s, slot = g & 1;
+        if (g >= 2 && !wait_phase(&S.mma_done[slot], (unsigned)(((g >> 1) - 1) & 1), abort)) break;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int kk = bw + 4 * e;
+          uint8_t* tf = &S.btile[slot][kk][0][0];
+          uint8_t* tb = &S.btile[slot][kk][1][0];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int r = r0 + 2 * h, row = 4 * s + r;
+            const bool on = live && yc + row < ye;
+            const float2 vv = *reinterpret_cast<const float2*>(&st.V[am][row * PITCH + kk * 8]);
+            const float yp = st.ypw[row][2 * bm];
+            const float wr = on ? yp * vv.x : 0.f, wi = on ? yp * vv.y : 0.f;
+            const float hr = tf32_trunc(wr), hi = tf32_trunc(wi);
+            const float lr = wr - hr, li = wi - hi;
+            // rows n = m (Re) and 16 + m (Im); element (n, k) of the TF32 tile at
+            // (n / 8) 256 + (k / 4) 128 + (n % 8) 16 + (k % 4) 4, k = 2 r + (re, im)
+            const int kb = (2 * r / 4) * 128 + (2 * r % 4) * 4;
+            const int nre = (m / 8) * 256 + (m % 8) * 16, nim = ((16 + m) / 8) * 256 + (m % 8) * 16;
+            *reinterpret_cast<float2*>(tf + nre + kb) = make_float2(hr, hi);
+            *reinterpret_cast<float2*>(tf + nim + kb) = make_float2(-hi, hr);
+            // BF16 tile: element (n, k) at (n / 8) 256 + (k / 8) 128 + (n % 8) 16 + (k % 8) 2;
+            // k = 2 r + (re, im) multiplies hi(P), k = 8 + 2 r + (re, im) multiplies lo(P)
+            const int k1 = (2 * r % 8) * 2, k2 = 128 + (2 * r % 8) * 2;
+            *reinterpret_cast<uint32_t*>(tb + nre + k1) = pack_bf16(lr, li);
+            *reinterpret_cast<uint32_t*>(tb + nim + k1) = pack_bf16(-li, lr);
+            *reinterpret_cast<uint32_t*>(tb + nre + k2) = pack_bf16(wr, wi);
+            *reinterpret_cast<uint32_t*>(tb + nim + k2) = pack_bf16(-wi, wr);
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.b_full[slot]);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.raw_empty[sidx]);
+    }
+  }
+
+  // ---- drain: the copies of the last two chunks issued land before the
+  // stages are reused (earlier phases of a stage report complete at once)
+  if (warp == 9)
+    for (int c = issued_chunks - 2; c < issued_chunks; ++c) {
+      if (c < 0) continue;
+      for (int it = 0; it < kMaxSpin && !mbar_try_wait(&S.raw_full[c & 1], (unsigned)((c >> 1) & 1)); ++it) {
+      }
+    }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const bool ok = ngroup > 0 && !S.abort && mbar_try_wait(&S.done, 0);
+  if (threadIdx.x == 0 && !ok) atomicOr(reinterpret_cast<int*>(ws + job.status), 4);
+
+  // ---- epilogue: lag DFT over the CTA's k-slots, per pair in thread-private
+  // shared sums (fixed order), then FP64 atomics
+  constexpr int RSTRIDE = 16 * kMaxL + 1;
+  float* red = reinterpret_cast<float*>(&S.st[0]);   // [128][RSTRIDE], aliases the stages
+  if (ok && warp < 4) {
+    const int q = 32 * warp + lane;
+    const int4 pq = pr[q < job.npair ? q : 0];
+    float* rq = red + q * RSTRIDE;
+    for (int i = 0; i < 16 * kMaxL; ++i) rq[i] = 0.f;
+    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+    for (int kk = 0; kk < KT; ++kk) {
+      uint32_t c[32];
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                   "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+                   "[%32];"
+                   : "=r"(c[0]), "=r"(c[1]), "=r"(c[2]), "=r"(c[3]), "=r"(c[4]), "=r"(c[5]), "=r"(c[6]), "=r"(c[7]),
+                     "=r"(c[8]), "=r"(c[9]), "=r"(c[10]), "=r"(c[11]), "=r"(c[12]), "=r"(c[13]), "=r"(c[14]),
+                     "=r"(c[15]), "=r"(c[16]), "=r"(c[17]), "=r"(c[18]), "=r"(c[19]), "=r"(c[20]), "=r"(c[21]),
+                     "=r"(c[22]), "=r"(c[23]), "=r"(c[24]), "=r"(c[25]), "=r"(c[26]), "=r"(c[27]), "=r"(c[28]),
+                     "=r"(c[29]), "=r"(c[30]), "=r"(c[31])
+                   : "r"(t_d + 32 * kk + lane_off));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      const int k = k0 + kk;
+      if (k == 0 || k >= M) continue;   // slot 0: the packed real bins, summed by k_contract_slot0
+      for (int ux = pq.z; ux <= pq.w; ++ux) {
+        const float2 t2 = S.tw[kk][ux + w];
+#pragma unroll
+        for (int mm = 0; mm < NMONO; ++mm)
+          rq[mm * kMaxL + ux + w] += __uint_as_float(c[mm]) * t2.x + __uint_as_float(c[16 + mm]) * t2.y;
+      }
+    }
+    if (q < job.npair) {
+      const double inv = 1.0 / (double)Nf;
+      double* out = reinterpret_cast<double*>(ws + job.out) + ((int64_t)pq.x * L * L + (pq.y + w) * L) * NMONO;
+      for (int ux = pq.z; ux <= pq.w; ++ux)
+#pragma unroll
+        for (int mm = 0; mm < NMONO; ++mm) {
+          const float v = rq[mm * kMaxL + ux + w];
+          if (v != 0.f) atomicAdd(out + (ux + w) * NMONO + mm, (double)v * inv);
+        }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "n"(TMEM_COLS) : "memory");
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiled encode_fn() {
+  static EncodeTiled fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(f);
+  }
+  return fn;
+}
+
+// 3-D FP32 view (x: 2 M floats of one spectrum row, y: rows, z: spectra) of
+// `n` consecutive row spectra, with boxes of BOXW x rows x 1
+static bool make_map(CUtensorMap* m, void* base, int M, int H, int n, int rows) {
+  EncodeTiled fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * M, (cuuint64_t)H, (cuuint64_t)n};
+  const cuuint64_t strides[2] = {(cuuint64_t)2 * M * 4, (cuuint64_t)H * 2 * M * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)BOXW, (cuuint32_t)rows, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+template <int DM>
+static cudaError_t contract_umma_dm(const sfft_plan_s* p, int job0, int njobs, void* ws) {
+  const size_t smem = sizeof(USmem);
+  static_assert(sizeof(float) * 128 * (16 * kMaxL + 1) <= 2 * sizeof(UStage), "epilogue sums must fit the stages");
+  auto kern = k_contract_umma<DM>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int H = p->d.H, L = p->d.L, B = p->d.batch;
+  const int rows = p->tc_rows;
+  const int nb = (H + rows - 1) / rows;
+  const int rbox = CH + (L - 1) + 7;
+  const size_t slab = (size_t)H * p->M * sizeof(float2);
+  const int npat = njobs / B;   // jobs are ordered CCD-major
+  for (int ccd = 0; ccd < B; ++ccd) {
+    CUtensorMap mp, mv;
+    char* base = static_cast<char*>(ws);
+    if (!make_map(&mp, base + p->phat.off + (size_t)ccd * p->d_batch * slab, p->M, H, p->d_batch, rbox) ||
+        !make_map(&mv, base + p->wspec.off + (size_t)ccd * p->n_wa * slab, p->M, H, p->n_wa, CH))
+      return cudaErrorInvalidValue;
+    for (int j0 = 0; j0 < npat; j0 += 65535) {
+      dim3 grid(p->M / KT, std::min(65535, npat - j0), nb);
+      kern<<<grid, NTHREADS, smem, p->stream>>>(mp, mv, p->d_tcjobs + job0 + ccd * npat + j0, p->d_tcpairs,
+                                                p->d_tcdj, (char*)ws, H, p->M, p->Nf, L, rows, rbox,
+                                                (const float2*)p->twD, (const float*)p->ytab);
+      p->nlaunch += 1;
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_contract_umma(const sfft_plan_s* p, int batch_index, void* ws) {
+  const int job0 = p->tc_first[batch_index], njobs = p->tc_count[batch_index];
+  if (njobs <= 0) return cudaSuccess;
+  switch (p->DM_KK) {
+    case 0: return contract_umma_dm<0>(p, job0, njobs, ws);
+    case 2: return contract_umma_dm<2>(p, job0, njobs, ws);
+    case 4: return contract_umma_dm<4>(p, job0, njobs, ws);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace sfft

@@ -36,6 +36,12 @@ constexpr int kTcKT = 8;         // k-slots per CTA (one warp each)
 constexpr int kTcNT = 8;         // 8-column tiles per warp: up to 64 (d, u_y) pairs per CTA
 constexpr int kTcChunk = 32;     // weight rows per stage
 constexpr int kTcRowCap = 448;   // staged probe rows per stage: sum over differences of (chunk + n_lag - 1)
+// tcgen05 kernel (kernels_contract_umma.cu): 128 pairs per CTA (the MMA's M)
+// drawn from at most 16 differences
+constexpr int kUmmaKT = 8;
+constexpr int kUmmaChunk = 32;
+constexpr int kUmmaPairs = 128;
+constexpr int kUmmaMaxDiffs = 16;
 
 }  // namespace sfft
 
@@ -54,6 +60,7 @@ struct sfft_plan_s {
   std::vector<int2> dlist;            // (dy, dx) per half-plane difference
   int d_batch = 0, rows_per_cta = 0, csplit = 2;   // csplit: lag parts per (k-slot, group) in the contraction
   bool tc = false;                    // KK contraction on the tensor cores (FP32 path)
+  bool umma = false;                  // ... with tcgen05 (else mma.sync)
   int tc_rows = 0;                    // weight rows per CTA of the tensor-core contraction
   double tuned_ms = 0.0;              // autotuned build_normal time per CCD (0: not tuned)
   size_t elem = 4;                    // sizeof(T)
@@ -108,6 +115,7 @@ cudaError_t launch_rfft_prod(const sfft_plan_s* p, int d0, int nd, void* ws);
 cudaError_t launch_contract(const sfft_plan_s* p, int DM, int job0, int njobs, int rows_per_cta, int lag_parts,
                             void* ws);
 cudaError_t launch_contract_tc(const sfft_plan_s* p, int batch_index, void* ws);
+cudaError_t launch_contract_umma(const sfft_plan_s* p, int batch_index, void* ws);
 cudaError_t launch_contract_slot0(const sfft_plan_s* p, int DM, int job0, int njobs, void* ws);
 cudaError_t launch_scatter(const sfft_plan_s* p, double* A, double* b, void* ws, bool rhs_only, double* rhs_out);
 cudaError_t launch_cholesky(const sfft_plan_s* p, const double* A, void* ws);

@@ -86,12 +86,13 @@ def test_mixed_path_within_stated_error(shape, L, DK, DB):
     assert np.abs(D[0] - ref["D"]).max() <= 1e-3 * SIGMA_SKY
 
 
+@pytest.mark.parametrize("engine", ["fma_contract", "mma_sync_contract"])
 @pytest.mark.parametrize("shape,L,DK,DB", [((150, 210), 7, 2, 2), ((96, 300), 11, 2, 2), ((48, 64), 3, 0, 0)])
-def test_mixed_path_fma_contraction(shape, L, DK, DB):
-    """The KK contraction on the FP32 FMA pipes (the tensor-core split is the
-    default): same stated error bars."""
+def test_mixed_path_other_contraction_engines(shape, L, DK, DB, engine):
+    """The KK contraction on the FP32 FMA pipes or through warp-level mma.sync
+    (tcgen05 is the default): same stated error bars."""
     d = small_pair(*shape, seed=2300 + shape[1] + L, mask_fraction=0.03)
-    refs, A, b, th, info, D = _run(d, L, DK, DB, "mixed", fma_contract=True)
+    refs, A, b, th, info, D = _run(d, L, DK, DB, "mixed", **{engine: True})
     ref = refs[0]
     assert info[0] == 0
     assert np.abs(A[0] - ref["A"]).max() <= 2e-5 * np.abs(ref["A"]).max()
