@@ -12,29 +12,31 @@
 // scheme of Ootomo and Yokota (2022).  The accumulators of the CTA's eight
 // k-slots (32 FP32 columns each) stay in tensor memory for the whole band.
 //
-// Roles (320 threads, one CTA per SM):
-//   warps 0-3  A producers: lane l of warp w is pair 32 w + l; per unit
-//              (k-slot, four rows) it loads its four probe values from the
-//              staged rows, splits them and stores the 16 A columns of the
-//              unit to tensor memory (tcgen05.st); at the end they read the
-//              accumulators back (tcgen05.ld) for the lag DFT;
-//   warps 4-7  B producers: warp 4 + b builds the tiles of k-slots b and
-//              b + 4, forming W_m for the unit's four rows and writing the
-//              TF32 and BF16 operand tiles (32 x 32 bytes each, K-major, no
-//              swizzle) to shared memory;
-//   warp 8     MMA issuer: one elected lane issues the sixteen MMAs of a
-//              k-step group (two per k-slot) and one commit;
-//   warp 9     copy producer: stages, 32 weight rows at a time and into two
+// Roles (576 threads, one CTA per SM):
+//   warps 0-7  A producers: lane l of warp w is pair 32 (w % 4) + l (warp w
+//              reaches tensor-memory lanes 32 (w % 4) ...); per unit (k-slot,
+//              four rows) it loads its four probe values from the staged rows,
+//              splits them and stores the unit's 16 A columns to tensor memory
+//              (tcgen05.st), warps 0-3 for half of a group's units and
+//              warps 4-7 for the other half;
+//              warps 0-3 read the accumulators back (tcgen05.ld) at the end for
+//              the lag DFT;
+//   warps 8-15 B producers: warp 8 + e forms W_m for unit e's four rows and
+//              writes its TF32 and BF16 operand tiles (32 x 32 bytes each,
+//              K-major, no swizzle) to shared memory;
+//   warp 16    MMA issuer: one elected lane issues the sixteen MMAs of a
+//              group (two per unit) and one commit;
+//   warp 17    copy producer: stages, 32 weight rows at a time and into two
 //              alternating stages, one tensor-copy box of probe rows per
 //              difference of the pattern, one box of weight rows per exponent
 //              and the powers of yt.
-// A unit is one k-slot over four rows; the eight units of a k-step form a
-// group, and groups alternate between two slots (A: 128 TMEM columns, B: 16 KB
-// of shared memory) with mbarrier hand-offs (A written, B written, MMAs done),
-// so that the next group is built while the tensor cores run the current one; every wait
-// is bounded, and a wait that gives up flags the CCD (status bit 4) and makes
-// every role leave its loop, after which the issued copies and MMAs are
-// drained (bounded) and the tensor memory is freed.
+// A unit is one k-slot over four rows; a group holds the eight k-slots' units
+// of one k-step, and groups alternate between two slots (A: 128 TMEM columns,
+// B: 16 KB of shared memory) with mbarrier hand-offs (A written, B written,
+// MMAs done), so that one group is built while the tensor cores run the other.
+// Every wait is bounded, and a wait that gives up flags the CCD (status bit 4)
+// and makes every role leave its loop, after which the issued copies and MMAs
+// are drained (bounded) and the tensor memory is freed.
 #include <cuda.h>
 
 #include "bulk.cuh"
@@ -47,15 +49,20 @@ namespace {
 
 constexpr int KT = kUmmaKT;          // k-slots per CTA
 constexpr int CH = kUmmaChunk;       // weight rows per stage
-constexpr int GSLOT = 2;             // k-step groups in flight (A: 128 TMEM columns, B: 16 KB each)
-constexpr int PITCH = 80;            // bytes per staged row: 10 spectrum slots (the CTA's 8 and 2 more)
+constexpr int SPG = 1;               // k-steps (four rows each) per group
+constexpr int UPG = KT * SPG;        // units (k-slot, k-step) per group
+constexpr int GPC = CH / (4 * SPG);  // groups per staged chunk
+constexpr int GSLOT = 2;             // groups in flight (A: UPG x 16 TMEM columns, B: UPG x 2 KB each)
+constexpr int PITCH = (KT + 2) * 8;  // bytes per staged row: the CTA's KT spectrum slots and 2 more
 constexpr int BOXW = PITCH / 4;      // floats per staged row (the tensor box's inner extent)
 constexpr int RBOX_MAX = CH + (kMaxL - 1) + 7;   // probe rows per box: chunk, lag range, bank shift
 constexpr int DSLOT = (RBOX_MAX * PITCH + 127) / 128 * 128;   // bytes per difference in a stage
 constexpr int NDMAX = kUmmaMaxDiffs; // differences per pattern
 constexpr int VSLOT = CH * PITCH;    // bytes per weight exponent in a stage
-constexpr int NTHREADS = 320;
-constexpr int TMEM_COLS = 512;       // D: KT x 32 columns, A: GSLOT x KT x 16 columns
+constexpr int WARP_MMA = 16, WARP_COPY = 17;   // warps 0-7: A producers, 8-15: B producers
+constexpr int NTHREADS = 32 * 18;
+constexpr int TMEM_COLS = 512;       // D: KT x 32 columns, A: GSLOT x UPG x 16 columns
+static_assert(KT * 32 + GSLOT * UPG * 16 <= TMEM_COLS, "tensor memory budget");
 
 // One stage: a box of probe rows per difference (tensor copies; box i starts
 // i % 8 rows early so that the differences' rows fall on different banks),
@@ -70,7 +77,7 @@ static_assert(DSLOT % 128 == 0 && VSLOT % 128 == 0 && sizeof(UStage) % 128 == 0,
 
 struct USmem {
   UStage st[2];
-  uint8_t btile[GSLOT][KT][2][1024];   // per group slot and k-slot: TF32 tile, BF16 tile (32 rows x 32 bytes,
+  uint8_t btile[GSLOT][UPG][2][1024];  // per group slot and unit: TF32 tile, BF16 tile (32 rows x 32 bytes,
                                        // canonical K-major)
   uint64_t raw_full[2], raw_empty[2];
   uint64_t a_full[GSLOT], b_full[GSLOT], mma_done[GSLOT];
@@ -160,13 +167,13 @@ k_contract_umma(const __grid_constant__ CUtensorMap tmP, const __grid_constant__
   if (y0 < w) y0 = w;
   if (y1 > H - w) y1 = H - w;
   const int nchunk = y1 > y0 ? (y1 - y0 + CH - 1) / CH : 0;
-  const int ngroup = nchunk * (CH / 4);   // k-step groups: the eight k-slots' units of four rows
+  const int ngroup = nchunk * GPC;   // groups of UPG units (k-slot, four rows)
   // ---- setup: zeroed stages, barriers, tensor memory, twiddles
   for (int i = threadIdx.x; i < (int)(sizeof(UStage) * 2 / 16); i += NTHREADS)
     reinterpret_cast<float4*>(&S.st[0])[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 2; ++i) { mbar_init(&S.raw_full[i], 1); mbar_init(&S.raw_empty[i], 8); }
-    for (int i = 0; i < GSLOT; ++i) { mbar_init(&S.a_full[i], 4); mbar_init(&S.b_full[i], 4); mbar_init(&S.mma_done[i], 1); }
+    for (int i = 0; i < 2; ++i) { mbar_init(&S.raw_full[i], 1); mbar_init(&S.raw_empty[i], 16); }
+    for (int i = 0; i < GSLOT; ++i) { mbar_init(&S.a_full[i], 8); mbar_init(&S.b_full[i], 8); mbar_init(&S.mma_done[i], 1); }
     mbar_init(&S.done, 1);
     S.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -188,12 +195,12 @@ k_contract_umma(const __grid_constant__ CUtensorMap tmP, const __grid_constant__
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tbase = S.tmem_base;
   const uint32_t t_d = tbase;                   // accumulators: k-slot kk at columns 32 kk
-  const uint32_t t_a = tbase + 32 * KT;         // A: group slot g, k-slot kk at columns 128 g + 16 kk
+  const uint32_t t_a = tbase + 32 * KT;         // A: group slot g, unit e at columns 16 (UPG g + e)
                                                 // (TF32 0-7, BF16 8-15)
 
   int issued_chunks = 0;   // bulk-copy warp: chunks whose copies were issued
 
-  if (warp == 9) {
+  if (warp == WARP_COPY) {
     // ---- copy producer: per chunk one tensor copy per difference and per
     // weight exponent and one bulk copy of the powers of yt
     for (int c = 0; c < nchunk; ++c) {
@@ -216,21 +223,22 @@ k_contract_umma(const __grid_constant__ CUtensorMap tmP, const __grid_constant__
       issued_chunks = c + 1;
       __syncwarp();
     }
-  } else if (warp == 8) {
-    // ---- MMA issuer: per k-step group, sixteen MMAs and one commit
+  } else if (warp == WARP_MMA) {
+    // ---- MMA issuer: per group, two MMAs per unit and one commit
     constexpr uint32_t id_tf32 = instr_desc(2), id_bf16 = instr_desc(1);
     for (int g = 0; g < ngroup; ++g) {
-      const int slot = g & 1;
-      const unsigned par = (unsigned)((g >> 1) & 1);
+      const int slot = g % GSLOT;
+      const unsigned par = (unsigned)((g / GSLOT) & 1);
       if (!wait_phase(&S.a_full[slot], par, abort) || !wait_phase(&S.b_full[slot], par, abort)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t acc = g > 0 ? 1u : 0u;   // the first group starts the accumulators
       if (elect_one()) {
 #pragma unroll
-        for (int kk = 0; kk < KT; ++kk) {
-          const uint32_t dcol = t_d + 32 * kk, acol = t_a + 128 * slot + 16 * kk;
-          const uint64_t bt = smem_desc(smem_u32(&S.btile[slot][kk][0][0]));
-          const uint64_t bb = smem_desc(smem_u32(&S.btile[slot][kk][1][0]));
+        for (int e = 0; e < UPG; ++e) {   // unit e: k-slot e / SPG, k-step e % SPG of the group
+          const int kk = e / SPG;
+          const uint32_t acc = (g > 0 || e % SPG > 0) ? 1u : 0u;   // the first k-step starts the accumulators
+          const uint32_t dcol = t_d + 32 * kk, acol = t_a + 16 * (UPG * slot + e);
+          const uint64_t bt = smem_desc(smem_u32(&S.btile[slot][e][0][0]));
+          const uint64_t bb = smem_desc(smem_u32(&S.btile[slot][e][1][0]));
           asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n"
                        ::"r"(dcol), "r"(acol), "l"(bt), "r"(id_tf32), "r"(acc) : "memory");
@@ -250,25 +258,28 @@ k_contract_umma(const __grid_constant__ CUtensorMap tmP, const __grid_constant__
     __syncwarp();
     for (int it = 0; it < kMaxSpin && !mbar_try_wait(&S.done, 0); ++it) {
     }
-  } else if (warp < 4) {
-    // ---- A producers: pair q = 32 warp + lane; per group the eight k-slots'
-    // A columns, one store wait and one arrival
-    int q = 32 * warp + lane;
+  } else if (warp < 8) {
+    // ---- A producers: lanes of warp w hold pair q = 32 (w % 4) + lane (their
+    // tensor-memory lanes); warp w writes units UPG / 2 (w / 4) ... of every
+    // group, then waits for its stores once and arrives
+    const int quarter = warp & 3, e0 = (UPG / 2) * (warp >> 2);
+    int q = 32 * quarter + lane;
     if (q >= job.npair) q = 0;   // lanes past the pattern mirror pair 0; their rows are dropped
     const int4 pq = pr[q];
     int off0 = 0;   // byte offset in a stage of (pair, weight row yc, slot 0)
     for (int i = 0; i < job.nd; ++i)
       if (dj[i].x == pq.x) off0 = i * DSLOT + (dj[i].z + i % 8 - pq.y) * PITCH;
-    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+    const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
     for (int c = 0; c < nchunk && !*abort; ++c) {
       const int sidx = c & 1;
       if (!wait_phase(&S.raw_full[sidx], (unsigned)((c >> 1) & 1), abort)) break;
       const uint8_t* P = &S.st[sidx].P[0][0] + off0;
-      for (int s = 0; s < CH / 4; ++s) {
-        const int g = c * (CH / 4) + s, slot = g & 1;
-        if (g >= 2 && !wait_phase(&S.mma_done[slot], (unsigned)(((g >> 1) - 1) & 1), abort)) break;
+      for (int sp = 0; sp < GPC; ++sp) {
+        const int g = c * GPC + sp, slot = g % GSLOT;
+        if (g >= GSLOT && !wait_phase(&S.mma_done[slot], (unsigned)(((g / GSLOT) - 1) & 1), abort)) break;
 #pragma unroll 2
-        for (int kk = 0; kk < KT; ++kk) {
+        for (int e = e0; e < e0 + UPG / 2; ++e) {
+          const int kk = e / SPG, s = SPG * sp + e % SPG;   // k-slot and k-step (rows 4 s ..) of unit e
           uint32_t v[16];
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
@@ -281,7 +292,7 @@ k_contract_umma(const __grid_constant__ CUtensorMap tmP, const __grid_constant__
           }
           asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
                        "%12, %13, %14, %15, %16};"
-                       ::"r"(t_a + 128 * slot + 16 * kk + lane_off), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]),
+                       ::"r"(t_a + 16 * (UPG * slot + e) + lane_off), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]),
                          "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]),
                          "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]) : "memory");
         }
@@ -294,9 +305,10 @@ k_contract_umma(const __grid_constant__ CUtensorMap tmP, const __grid_constant__
       if (lane == 0) mbar_arrive(&S.raw_empty[sidx]);
     }
   } else {
-    // ---- B producers: warp 4 + bw builds the tiles of k-slots bw and bw + 4 of
-    // every group; lane: monomial m = lane % 16, rows r = lane / 16 and + 2
-    const int bw = warp - 4;
+    // ---- B producers: warp 8 + e builds the tiles of unit e (k-slot e / SPG,
+    // k-step e % SPG) of every group; lane: monomial m = lane % 16, rows
+    // r = lane / 16 and + 2
+    const int e = warp - 8, kk = e / SPG;
     const int m = lane & 15, r0 = lane >> 4;
     int am = 0, bm = 0;
     mono_ab(m < NMONO ? m : 0, am, bm);
@@ -306,14 +318,12 @@ k_contract_umma(const __grid_constant__ CUtensorMap tmP, const __grid_constant__
       if (!wait_phase(&S.raw_full[sidx], (unsigned)((c >> 1) & 1), abort)) break;
       const UStage& st = S.st[sidx];
       const int yc = y0 + c * CH, ye = min(yc + CH, y1);
-      for (int s = 0; s < CH / 4; ++s) {
-        const int g = c * (CH / 4) + s, slot = g & 1;
-        if (g >= 2 && !wait_phase(&S.mma_done[slot], (unsigned)(((g >> 1) - 1) & 1), abort)) break;
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int kk = bw + 4 * e;
-          uint8_t* tf = &S.btile[slot][kk][0][0];
-          uint8_t* tb = &S.btile[slot][kk][1][0];
+      for (int sp = 0; sp < GPC; ++sp) {
+        const int g = c * GPC + sp, slot = g % GSLOT, s = SPG * sp + e % SPG;
+        if (g >= GSLOT && !wait_phase(&S.mma_done[slot], (unsigned)(((g / GSLOT) - 1) & 1), abort)) break;
+        {
+          uint8_t* tf = &S.btile[slot][e][0][0];
+          uint8_t* tb = &S.btile[slot][e][1][0];
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int r = r0 + 2 * h, row = 4 * s + r;
@@ -349,7 +359,7 @@ k_contract_umma(const __grid_constant__ CUtensorMap tmP, const __grid_constant__
 
   // ---- drain: the copies of the last two chunks issued land before the
   // stages are reused (earlier phases of a stage report complete at once)
-  if (warp == 9)
+  if (warp == WARP_COPY)
     for (int c = issued_chunks - 2; c < issued_chunks; ++c) {
       if (c < 0) continue;
       for (int it = 0; it < kMaxSpin && !mbar_try_wait(&S.raw_full[c & 1], (unsigned)((c >> 1) & 1)); ++it) {
