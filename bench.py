@@ -42,7 +42,7 @@ WORKLOAD = ("one DECam CCD pair per GPU per step: 2048x4096 FP32, 20k stars, PSF
 KK_TRAFFIC = {
     "kernels_contract.cu": (10.09e9, "1a847c15ebf73406"),      # FP32 FMA kernel (--fma-contract)
     "kernels_contract_tc.cu": (None, ""),                      # mma.sync kernel (--mma-sync-contract)
-    "kernels_contract_umma.cu": (None, ""),                    # tcgen05 kernel (default)
+    "kernels_contract_umma.cu": (9.975e9, "0d3c235754a7a213"),  # tcgen05 kernel (default)
 }
 PHASES = ("prep", "fft_weights", "fft_prod", "contract_kk", "contract_rk", "scatter", "solve", "apply")
 
