@@ -20,6 +20,9 @@ the small network built here, which follows the project's stated design:
 
 Max-pool is 2 x 2 with stride 2 over the top-left even part (floor); its
 gradient goes to the first maximum in the order (0,0), (0,1), (1,0), (1,1).
+
+The paper's own architecture (a rotation-invariant network with residual
+connections) is the second model below (forward_ri, loss_and_grads_ri).
 """
 from __future__ import annotations
 
@@ -227,3 +230,123 @@ def shape_cuts(dstamp, snr, fwhm_psf, snr_min=5.0):
     neg_frac = np.abs(np.minimum(inner, 0)).sum() / max(np.abs(inner).sum(), 1e-12)
     ratio = np.sqrt(l1 / l2)
     return (0.5 * fwhm_psf <= fwhm <= 2.0 * fwhm_psf) and neg_frac < 0.3 and ratio < 2.5
+
+
+# ---------------------------------------------------------------- rotation-invariant residual network
+# The paper's classifier (Sec. 2.3.4) is a rotation-invariant CNN in the
+# framework of its cited DeepHiTS work with residual connections in the style
+# of ResNet-18; no layer sizes are given.  Reading implemented here: the
+# normalised stamp is presented in its four rotations by multiples of 90
+# degrees to one shared convolutional stack, and the four flattened feature
+# vectors are averaged (exact invariance under those rotations) before the
+# dense head:
+#   conv1  3 -> 32, ReLU, pool (31 -> 15)
+#   res1   relu(p1 + conv_b(relu(conv_a(p1))))           32 -> 32, 15 x 15
+#   conv2  32 -> 64, ReLU, pool (15 -> 7)
+#   res2   relu(p2 + conv_d(relu(conv_c(p2))))           64 -> 64, 7 x 7, then pool (7 -> 3)
+#   mean over the four rotations of the 576 features, fc1 576 -> 128 ReLU, fc2 128 -> 1
+SHAPES_RI = {
+    "w1": (32, 3, 3, 3), "b1": (32,),
+    "wa": (32, 32, 3, 3), "ba": (32,), "wb": (32, 32, 3, 3), "bb": (32,),
+    "w2": (64, 32, 3, 3), "b2": (64,),
+    "wc": (64, 64, 3, 3), "bc": (64,), "wd": (64, 64, 3, 3), "bd": (64,),
+    "w4": (128, 576), "b4": (128,),
+    "w5": (1, 128), "b5": (1,),
+}
+ORDER_RI = ["w1", "b1", "wa", "ba", "wb", "bb", "w2", "b2", "wc", "bc", "wd", "bd", "w4", "b4", "w5", "b5"]
+
+
+def n_params_ri():
+    return int(sum(np.prod(SHAPES_RI[k]) for k in ORDER_RI))
+
+
+def unflatten_ri(vec):
+    out, o = {}, 0
+    for k in ORDER_RI:
+        n = int(np.prod(SHAPES_RI[k]))
+        out[k] = np.asarray(vec[o:o + n], dtype=np.float64).reshape(SHAPES_RI[k])
+        o += n
+    return out
+
+
+def flatten_ri(params):
+    return np.concatenate([np.asarray(params[k], dtype=np.float64).ravel() for k in ORDER_RI])
+
+
+def init_params_ri(seed):
+    rng = np.random.default_rng(seed)
+    p = {}
+    for k in ORDER_RI:
+        shp = SHAPES_RI[k]
+        if k.startswith("b"):
+            p[k] = np.zeros(shp)
+        else:
+            lim = np.sqrt(6.0 / int(np.prod(shp[1:])))
+            p[k] = rng.uniform(-lim, lim, shp)
+    return p
+
+
+def rotations(xn):
+    """The four rotations by r x 90 degrees (counterclockwise, as np.rot90 over
+    rows and columns), stacked rotation-major: [4 n][3][31][31]."""
+    return np.concatenate([np.rot90(xn, r, axes=(2, 3)) for r in range(4)], axis=0)
+
+
+def forward_ri(params, xn, keep=False):
+    """Logits of the rotation-invariant residual network for normalised stamps."""
+    n = xn.shape[0]
+    x = rotations(np.asarray(xn, dtype=np.float64))
+    z1 = conv_same(x, params["w1"], params["b1"])
+    p1, i1 = maxpool2(np.maximum(z1, 0.0))
+    za = conv_same(p1, params["wa"], params["ba"])
+    ra = np.maximum(za, 0.0)
+    zb = conv_same(ra, params["wb"], params["bb"]) + p1
+    r1 = np.maximum(zb, 0.0)
+    z2 = conv_same(r1, params["w2"], params["b2"])
+    p2, i2 = maxpool2(np.maximum(z2, 0.0))
+    zc = conv_same(p2, params["wc"], params["bc"])
+    rc = np.maximum(zc, 0.0)
+    zd = conv_same(rc, params["wd"], params["bd"]) + p2
+    p3, i3 = maxpool2(np.maximum(zd, 0.0))
+    feats = p3.reshape(4, n, -1)
+    f = feats.mean(axis=0)
+    z4 = f @ params["w4"].T + params["b4"]
+    h4 = np.maximum(z4, 0.0)
+    logit = (h4 @ params["w5"].T + params["b5"])[:, 0]
+    if keep:
+        cache = dict(x=x, z1=z1, p1=p1, i1=i1, za=za, ra=ra, zb=zb, r1=r1, z2=z2, p2=p2, i2=i2, zc=zc, rc=rc,
+                     zd=zd, i3=i3, p3shape=p3.shape, f=f, z4=z4, h4=h4)
+        return logit, cache
+    return logit
+
+
+def loss_and_grads_ri(params, xn, target):
+    """BCE loss and its gradient for every parameter of the rotation-invariant network."""
+    logit, c = forward_ri(params, xn, keep=True)
+    n = logit.shape[0]
+    loss = bce_loss(logit, target)
+    dz5 = ((sigmoid(logit) - np.asarray(target, dtype=np.float64)) / n)[:, None]
+    g = {"w5": dz5.T @ c["h4"], "b5": dz5.sum(axis=0)}
+    dz4 = (dz5 @ params["w5"]) * (c["z4"] > 0)
+    g["w4"], g["b4"] = dz4.T @ c["f"], dz4.sum(axis=0)
+    df = dz4 @ params["w4"]
+    dp3 = np.broadcast_to(df[None] / 4.0, (4,) + df.shape).reshape(c["p3shape"])
+    dzd = maxpool2_backward(dp3, c["i3"], c["zd"].shape) * (c["zd"] > 0)
+    drc, g["wd"], g["bd"] = conv_same_backward(c["rc"], params["wd"], dzd)
+    dzc = drc * (c["zc"] > 0)
+    dp2, g["wc"], g["bc"] = conv_same_backward(c["p2"], params["wc"], dzc)
+    dp2 = dp2 + dzd                                   # the skip connection
+    dz2 = maxpool2_backward(dp2, c["i2"], c["z2"].shape) * (c["z2"] > 0)
+    dr1, g["w2"], g["b2"] = conv_same_backward(c["r1"], params["w2"], dz2)
+    dzb = dr1 * (c["zb"] > 0)
+    dra, g["wb"], g["bb"] = conv_same_backward(c["ra"], params["wb"], dzb)
+    dza = dra * (c["za"] > 0)
+    dp1, g["wa"], g["ba"] = conv_same_backward(c["p1"], params["wa"], dza)
+    dp1 = dp1 + dzb                                   # the skip connection
+    dz1 = maxpool2_backward(dp1, c["i1"], c["z1"].shape) * (c["z1"] > 0)
+    _, g["w1"], g["b1"] = conv_same_backward(c["x"], params["w1"], dz1)
+    return loss, g
+
+
+def score_ri(params, stamps):
+    return sigmoid(forward_ri(params, normalise(stamps)))

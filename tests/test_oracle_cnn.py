@@ -126,3 +126,82 @@ def test_training_reduces_loss_on_separable_toy():
         _, g = C.loss_and_grads(p, xn, t)
         p = opt.step(p, g)
     assert C.loss_and_grads(p, xn, t)[0] < 0.5 * l0
+
+
+# ------------------------------------------------------------------ rotation-invariant residual network
+def _ri_setup(n=4, seed=5):
+    p = C.init_params_ri(seed)
+    rng = np.random.default_rng(seed + 1)
+    for k in p:
+        if k.startswith("b"):
+            p[k] = rng.normal(0, 0.05, p[k].shape)
+    xn = rng.normal(0, 1.0, (n, 3, 31, 31))
+    t = (rng.random(n) < 0.5).astype(np.float64)
+    return p, xn, t
+
+
+def test_ri_parameter_count():
+    assert C.n_params_ri() == 185729
+    p = C.init_params_ri(1)
+    assert np.array_equal(C.flatten_ri(C.unflatten_ri(C.flatten_ri(p))), C.flatten_ri(p))
+
+
+def test_ri_rotations_follow_numpy_rot90():
+    x = np.arange(2 * 3 * 31 * 31, dtype=np.float64).reshape(2, 3, 31, 31)
+    r = C.rotations(x)
+    assert r.shape == (8, 3, 31, 31)
+    # one counterclockwise quarter turn: out[y][x] = in[x][30 - y]
+    assert r[2, 1, 5, 7] == x[0, 1, 7, 30 - 5]
+    assert r[4, 2, 5, 7] == x[0, 2, 30 - 5, 30 - 7]
+    assert r[6, 0, 5, 7] == x[0, 0, 30 - 7, 5]
+
+
+def test_ri_score_is_rotation_invariant_and_features_are_not():
+    p, xn, _ = _ri_setup()
+    z0 = C.forward_ri(p, xn)
+    for r in (1, 2, 3):
+        zr = C.forward_ri(p, np.rot90(xn, r, axes=(2, 3)).copy())
+        assert np.allclose(zr, z0, rtol=1e-12, atol=1e-12)
+    # mirroring is not one of the four rotations: the score moves
+    zm = C.forward_ri(p, xn[:, :, :, ::-1].copy())
+    assert np.max(np.abs(zm - z0)) > 1e-6
+    # each rotation's own feature vector differs (the average is what is invariant)
+    _, c = C.forward_ri(p, xn, keep=True)
+    p3 = C.maxpool2(np.maximum(c["zd"], 0.0))[0].reshape(4, xn.shape[0], -1)
+    assert np.max(np.abs(p3[1] - p3[0])) > 1e-6
+
+
+def test_ri_residual_block_with_zero_branch_is_identity():
+    """With the second convolution of each block zeroed the block returns its
+    (non-negative) input: the network equals the same network without the
+    residual branches, written out here without them."""
+    p, xn, _ = _ri_setup(n=3, seed=9)
+    for k in ("wb", "bb", "wd", "bd"):
+        p[k] = np.zeros_like(p[k])
+    z = C.forward_ri(p, xn)
+    x = C.rotations(xn)
+    a = C.maxpool2(np.maximum(C.conv_same(x, p["w1"], p["b1"]), 0))[0]
+    a = C.maxpool2(np.maximum(C.conv_same(a, p["w2"], p["b2"]), 0))[0]
+    a = C.maxpool2(a)[0]
+    f = a.reshape(4, xn.shape[0], -1).mean(axis=0)
+    zz = (np.maximum(f @ p["w4"].T + p["b4"], 0) @ p["w5"].T + p["b5"])[:, 0]
+    assert np.allclose(z, zz, rtol=1e-12, atol=1e-12)
+
+
+def test_ri_gradients_by_central_differences():
+    p, xn, t = _ri_setup(n=3, seed=11)
+    loss, g = C.loss_and_grads_ri(p, xn, t)
+    rng = np.random.default_rng(3)
+    h = 1e-6
+    for k in C.ORDER_RI:
+        flat = p[k].ravel()
+        for idx in rng.choice(flat.size, size=min(4, flat.size), replace=False):
+            old = flat[idx]
+            flat[idx] = old + h
+            lp = C.bce_loss(C.forward_ri(p, xn), t)
+            flat[idx] = old - h
+            lm = C.bce_loss(C.forward_ri(p, xn), t)
+            flat[idx] = old
+            num = (lp - lm) / (2 * h)
+            ana = g[k].ravel()[idx]
+            assert abs(num - ana) <= 1e-6 * max(1.0, abs(num)) + 1e-8, (k, idx, num, ana)
