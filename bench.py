@@ -251,20 +251,27 @@ def _max_over_ranks(dist, dev, x):
 
 
 CNN_FWD_FLOP = 2.0 * (961 * 27 * 32 + 225 * 288 * 64 + 49 * 576 * 64 + 576 * 128 + 128)   # per stamp
+# the rotation-invariant residual network: four rotations through conv1, two
+# 32 -> 32 convolutions, conv2 and two 64 -> 64 convolutions; one dense head
+CNN_RI_FWD_FLOP = 2.0 * (4 * (961 * 27 * 32 + 2 * 225 * 288 * 32 + 225 * 288 * 64 + 2 * 49 * 576 * 64)
+                         + 576 * 128 + 128)
 
 
-def time_classifier(dev, n_infer=32768, batch=256, steps=40):
+def time_classifier(dev, n_infer=32768, batch=256, steps=40, arch="small"):
     """Stamp-classifier throughput on synthetic 31 x 31 x 3 stamps: inference
     (normalise + forward + sigmoid) and training steps (forward, backward, Adam),
-    CUDA-event timed; flop rates count the network's multiply-adds only."""
+    CUDA-event timed; flop rates count the network's multiply-adds only.
+    arch "small": the three-convolution network; "ri": the paper's
+    rotation-invariant residual network."""
     import torch
-    from paper_2603_08593_gb300 import RBModel
+    from paper_2603_08593_gb300 import RBModel, RIModel
     from synth.stamps import make_stamps
     d = make_stamps(4096, seed=77)
     base = torch.from_numpy(d["stamps"]).to(dev)
     lab = torch.from_numpy(d["labels"]).to(dev)
     stamps = base.repeat((n_infer + 4095) // 4096, 1, 1, 1)[:n_infer].contiguous()
-    m = RBModel(max_batch=4096, seed=1)
+    m = RBModel(max_batch=4096, seed=1) if arch == "small" else RIModel(max_batch=1024, seed=1)
+    fwd = CNN_FWD_FLOP if arch == "small" else CNN_RI_FWD_FLOP
     out = torch.empty(n_infer, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream(dev)
     m.score(stamps, out=out)
@@ -287,10 +294,10 @@ def time_classifier(dev, n_infer=32768, batch=256, steps=40):
     tr_s = e0.elapsed_time(e1) / 1e3 / steps
     inf_rate = n_infer / inf_s
     return {"inference_stamps_per_s": inf_rate, "train_stamps_per_s": batch / tr_s,
-            "inference_tflops": inf_rate * CNN_FWD_FLOP / 1e12,
-            "train_tflops": 3 * CNN_FWD_FLOP * batch / tr_s / 1e12,
-            "note": f"synthetic stamps; inference on {n_infer} stamps in batches of 4096, training batch {batch}; "
-                    "BF16 mma.sync GEMMs with FP32 accumulation, flops = network multiply-adds x 2 "
+            "inference_tflops": inf_rate * fwd / 1e12,
+            "train_tflops": 3 * fwd * batch / tr_s / 1e12,
+            "note": f"synthetic stamps; inference on {n_infer} stamps in batches of {m.max_batch}, training batch "
+                    f"{batch}; BF16 mma.sync GEMMs with FP32 accumulation, flops = network multiply-adds x 2 "
                     "(training = 3 x forward)"}
 
 
@@ -416,6 +423,7 @@ def run_gpu(args):
     classifier = None
     if not args.no_classifier and rank == 0:
         classifier = time_classifier(dev)
+        classifier["rotation_invariant_residual"] = time_classifier(dev, n_infer=8192, arch="ri")
 
     if rank != 0:
         if dist is not None:
@@ -517,7 +525,9 @@ def main():
     args = ap.parse_args()
     if args.only_classifier:   # classifier figures alone (profiling captures)
         import torch
-        print(json.dumps({"classifier": time_classifier(torch.device("cuda", 0))}), flush=True)
+        dev = torch.device("cuda", 0)
+        print(json.dumps({"classifier": time_classifier(dev),
+                          "rotation_invariant_residual": time_classifier(dev, n_infer=8192, arch="ri")}), flush=True)
         return 0
     if args.impl == "reference":
         return run_reference(args)

@@ -66,6 +66,39 @@ sfft_status_t rb_backward(rb_model_t m, const float* stamps, const float* labels
 sfft_status_t rb_train_step(rb_model_t m, const float* stamps, const float* labels, int64_t n, float lr,
                             float* loss_dev, void* stream);
 
+/* The paper's classifier (Sec. 2.3.4: a rotation-invariant CNN in the cited
+ * DeepHiTS framework with ResNet-style residual connections; the layer sizes
+ * are this library's reading).  The normalised stamp passes in its four
+ * rotations by multiples of 90 degrees through one shared stack:
+ * conv1 3 -> 32 + ReLU + pool (31 -> 15); residual block relu(p1 +
+ * conv_b(relu(conv_a(p1)))) at 32 channels; conv2 32 -> 64 + ReLU + pool
+ * (15 -> 7); residual block relu(p2 + conv_d(relu(conv_c(p2)))) at 64
+ * channels and a pool (7 -> 3); the four 576-feature vectors are averaged
+ * (exact invariance under the rotations) and fed to fc1 576 -> 128 + ReLU and
+ * fc2 128 -> 1.  Normalisation, loss, optimiser, precision and the call
+ * semantics are those of the rb_* model above; desc[0] <= 2048.  Weights:
+ * RBRI_NPARAM floats in the order w1 [32][3][3][3], b1, wa [32][32][3][3], ba,
+ * wb [32][32][3][3], bb, w2 [64][32][3][3], b2, wc [64][64][3][3], bc,
+ * wd [64][64][3][3], bd, w4 [128][576] (input index channel * 9 + row * 3 +
+ * column), b4, w5 [1][128], b5. */
+#define RBRI_NPARAM 185729
+
+typedef struct rbri_model_s* rbri_model_t;
+
+sfft_status_t rbri_create(const int32_t* desc, rbri_model_t* out);
+sfft_status_t rbri_destroy(rbri_model_t m);
+sfft_status_t rbri_set_weights(rbri_model_t m, const void* host_buf, size_t bytes);
+sfft_status_t rbri_get_weights(rbri_model_t m, void* host_buf, size_t bytes);
+sfft_status_t rbri_get_grads(rbri_model_t m, void* host_buf, size_t bytes);
+sfft_status_t rbri_get_state(rbri_model_t m, void* host_buf, size_t bytes, int64_t* step);
+sfft_status_t rbri_set_state(rbri_model_t m, const void* host_buf, size_t bytes, int64_t step);
+sfft_status_t rbri_logits(rbri_model_t m, const float* stamps, int64_t n, float* logit, void* stream);
+sfft_status_t rbri_score(rbri_model_t m, const float* stamps, int64_t n, float* score, void* stream);
+sfft_status_t rbri_backward(rbri_model_t m, const float* stamps, const float* labels, int64_t n,
+                            float* loss_dev, void* stream);
+sfft_status_t rbri_train_step(rbri_model_t m, const float* stamps, const float* labels, int64_t n, float lr,
+                              float* loss_dev, void* stream);
+
 /* Candidate detection on difference images (Sec. 2.3.3's detection step,
  * here a matched filter): SNR(x) = sum_u G(u) D^(x - u) / (sigma_D ||G||_2)
  * with D^ = D at good finite pixels and 0 elsewhere (and outside the image),

@@ -7,5 +7,5 @@ include/sfft.h, include/rb.h and include/phot.h); `binding` marshals
 arguments to it through ctypes.
 """
 from . import binding  # noqa: F401
-from .binding import (Detector, Plan, RBModel, SfftError, aperture_flux, limiting_mag, load,  # noqa: F401
+from .binding import (Detector, Plan, RBModel, RIModel, SfftError, aperture_flux, limiting_mag, load,  # noqa: F401
                       median_combine, shape_cuts)

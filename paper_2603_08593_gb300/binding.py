@@ -59,6 +59,17 @@ SIGNATURES = {
     "rb_score": (I32, [VP, VP, I64, VP, VP]),
     "rb_backward": (I32, [VP, VP, VP, I64, VP, VP]),
     "rb_train_step": (I32, [VP, VP, VP, I64, C.c_float, VP, VP]),
+    "rbri_create": (I32, [VP, C.POINTER(VP)]),
+    "rbri_destroy": (I32, [VP]),
+    "rbri_set_weights": (I32, [VP, VP, SZ]),
+    "rbri_get_weights": (I32, [VP, VP, SZ]),
+    "rbri_get_grads": (I32, [VP, VP, SZ]),
+    "rbri_get_state": (I32, [VP, VP, SZ, C.POINTER(I64)]),
+    "rbri_set_state": (I32, [VP, VP, SZ, I64]),
+    "rbri_logits": (I32, [VP, VP, I64, VP, VP]),
+    "rbri_score": (I32, [VP, VP, I64, VP, VP]),
+    "rbri_backward": (I32, [VP, VP, VP, I64, VP, VP]),
+    "rbri_train_step": (I32, [VP, VP, VP, I64, C.c_float, VP, VP]),
     "rb_detect_workspace_bytes": (SZ, [I32, I32, I32, I32]),
     "rb_detect": (I32, [I32, I32, I32, VP, VP, VP, VP, C.c_float, C.c_float, I32, I32, VP, VP, VP, VP, VP, VP]),
     "rb_shape_cuts": (I32, [VP, VP, I64, C.c_float, C.c_float, VP, VP]),
@@ -71,6 +82,7 @@ SIGNATURES = {
 
 RB_STAMP = 31
 RB_NPARAM = 130305
+RBRI_NPARAM = 185729
 
 _LIB = None
 
@@ -273,58 +285,66 @@ class RBModel:
     BF16 tensor-core forward/backward.  Weight vectors use the layout of
     include/rb.h (w1 b1 ... w5 b5, RB_NPARAM floats)."""
 
+    PREFIX = "rb"
+    NPARAM = RB_NPARAM
+
     def __init__(self, max_batch=1024, seed=0):
         import numpy as np
         self._np = np
         self.lib = load()
         desc = (I32 * 2)(int(max_batch), int(seed))
         h = VP()
-        _check(self.lib.rb_create(desc, C.byref(h)), "rb_create")
+        _check(self._fn("create")(desc, C.byref(h)), f"{self.PREFIX}_create")
         self.h = h
         self.max_batch = int(max_batch)
+
+    def _fn(self, name):
+        return getattr(self.lib, f"{self.PREFIX}_{name}")
 
     def __del__(self):
         try:
             if getattr(self, "h", None):
-                self.lib.rb_destroy(self.h)
+                self._fn("destroy")(self.h)
                 self.h = None
         except Exception:
             pass
 
-    def _vec(self, fn, n=RB_NPARAM):
-        out = self._np.empty(n, dtype=self._np.float32)
-        _check(fn(self.h, out.ctypes.data_as(VP), out.nbytes), fn.__name__)
+    def _vec(self, name):
+        out = self._np.empty(self.NPARAM, dtype=self._np.float32)
+        _check(self._fn(name)(self.h, out.ctypes.data_as(VP), out.nbytes), f"{self.PREFIX}_{name}")
         return out
 
     def set_weights(self, w):
         w = self._np.ascontiguousarray(w, dtype=self._np.float32)
-        if w.size != RB_NPARAM:
-            raise ValueError(f"expected {RB_NPARAM} weights")
-        _check(self.lib.rb_set_weights(self.h, w.ctypes.data_as(VP), w.nbytes), "rb_set_weights")
+        if w.size != self.NPARAM:
+            raise ValueError(f"expected {self.NPARAM} weights")
+        _check(self._fn("set_weights")(self.h, w.ctypes.data_as(VP), w.nbytes), f"{self.PREFIX}_set_weights")
 
     def get_weights(self):
-        return self._vec(self.lib.rb_get_weights)
+        return self._vec("get_weights")
 
     def get_grads(self):
-        return self._vec(self.lib.rb_get_grads)
+        return self._vec("get_grads")
 
     def get_state(self):
-        """(weights, adam_m, adam_v) as one array of 3 * RB_NPARAM floats, and the step count."""
-        out = self._np.empty(3 * RB_NPARAM, dtype=self._np.float32)
+        """(weights, adam_m, adam_v) as one array of 3 * NPARAM floats, and the step count."""
+        out = self._np.empty(3 * self.NPARAM, dtype=self._np.float32)
         step = I64()
-        _check(self.lib.rb_get_state(self.h, out.ctypes.data_as(VP), out.nbytes, C.byref(step)), "rb_get_state")
+        _check(self._fn("get_state")(self.h, out.ctypes.data_as(VP), out.nbytes, C.byref(step)),
+               f"{self.PREFIX}_get_state")
         return out, int(step.value)
 
     def set_state(self, state, step):
         s = self._np.ascontiguousarray(state, dtype=self._np.float32)
-        _check(self.lib.rb_set_state(self.h, s.ctypes.data_as(VP), s.nbytes, int(step)), "rb_set_state")
+        _check(self._fn("set_state")(self.h, s.ctypes.data_as(VP), s.nbytes, int(step)), f"{self.PREFIX}_set_state")
 
     def logits(self, stamps, out=None, stream=None):
         import torch
         _need(stamps, torch.float32, "stamps")
         n = stamps.shape[0]
         out = out if out is not None else torch.empty(n, dtype=torch.float32, device=stamps.device)
-        _check(self.lib.rb_logits(self.h, _ptr(stamps), n, _ptr(out), _stream(stamps, stream)), "rb_logits")
+        _check(self._fn("logits")(self.h, _ptr(stamps), n, _ptr(out), _stream(stamps, stream)),
+               f"{self.PREFIX}_logits")
         return out
 
     def score(self, stamps, out=None, stream=None):
@@ -332,7 +352,7 @@ class RBModel:
         _need(stamps, torch.float32, "stamps")
         n = stamps.shape[0]
         out = out if out is not None else torch.empty(n, dtype=torch.float32, device=stamps.device)
-        _check(self.lib.rb_score(self.h, _ptr(stamps), n, _ptr(out), _stream(stamps, stream)), "rb_score")
+        _check(self._fn("score")(self.h, _ptr(stamps), n, _ptr(out), _stream(stamps, stream)), f"{self.PREFIX}_score")
         return out
 
     def backward(self, stamps, labels, loss=None, stream=None):
@@ -340,8 +360,8 @@ class RBModel:
         _need(stamps, torch.float32, "stamps")
         _need(labels, torch.float32, "labels")
         loss = loss if loss is not None else torch.empty(1, dtype=torch.float32, device=stamps.device)
-        _check(self.lib.rb_backward(self.h, _ptr(stamps), _ptr(labels), stamps.shape[0], _ptr(loss),
-                                    _stream(stamps, stream)), "rb_backward")
+        _check(self._fn("backward")(self.h, _ptr(stamps), _ptr(labels), stamps.shape[0], _ptr(loss),
+                                    _stream(stamps, stream)), f"{self.PREFIX}_backward")
         return loss
 
     def train_step(self, stamps, labels, lr, loss=None, stream=None):
@@ -349,9 +369,21 @@ class RBModel:
         _need(stamps, torch.float32, "stamps")
         _need(labels, torch.float32, "labels")
         loss = loss if loss is not None else torch.empty(1, dtype=torch.float32, device=stamps.device)
-        _check(self.lib.rb_train_step(self.h, _ptr(stamps), _ptr(labels), stamps.shape[0], float(lr), _ptr(loss),
-                                      _stream(stamps, stream)), "rb_train_step")
+        _check(self._fn("train_step")(self.h, _ptr(stamps), _ptr(labels), stamps.shape[0], float(lr), _ptr(loss),
+                                      _stream(stamps, stream)), f"{self.PREFIX}_train_step")
         return loss
+
+
+class RIModel(RBModel):
+    """The paper's rotation-invariant residual classifier (include/rb.h rbri_*):
+    the same interface as RBModel, RBRI_NPARAM weights in the order w1 b1 wa ba
+    wb bb w2 b2 wc bc wd bd w4 b4 w5 b5; at most 2048 stamps per internal batch."""
+
+    PREFIX = "rbri"
+    NPARAM = RBRI_NPARAM
+
+    def __init__(self, max_batch=512, seed=0):
+        super().__init__(max_batch=max_batch, seed=seed)
 
 
 class Detector:

@@ -222,9 +222,9 @@ def balanced_split(lab, seed=500, frac=(0.8, 0.05, 0.15)):
     return out
 
 
-def run(train_ccds=3000, epochs=5, batch=256, lr=1e-3, eval_ccds=60, seed=500, log=print):
+def run(train_ccds=3000, epochs=5, batch=256, lr=1e-3, eval_ccds=60, seed=500, log=print, arch="small"):
     import torch
-    from .binding import RBModel
+    from .binding import RBModel, RIModel
     t0 = time.time()
     tr_pairs = generate(train_pair, list(range(seed, seed + train_ccds)))
     ev_pairs = generate(exposure_pair, list(range(eval_ccds))) if eval_ccds else []
@@ -237,7 +237,8 @@ def run(train_ccds=3000, epochs=5, batch=256, lr=1e-3, eval_ccds=60, seed=500, l
     t_cand = time.time() - t1
     log(f"training candidates: {len(lab)} ({int(lab.sum())} real) in {t_cand:.1f} s")
     i_tr, i_va, i_te = balanced_split(lab, seed)
-    model = RBModel(max_batch=max(batch, 1024), seed=seed)
+    model = (RBModel(max_batch=max(batch, 1024), seed=seed) if arch == "small"
+             else RIModel(max_batch=max(batch, 512), seed=seed))
     st = ctr["stamps"]
     dev = st.device
     take = lambda idx: st.index_select(0, torch.as_tensor(idx, device=dev)).contiguous()   # noqa: E731
@@ -246,7 +247,7 @@ def run(train_ccds=3000, epochs=5, batch=256, lr=1e-3, eval_ccds=60, seed=500, l
     torch.cuda.synchronize()
     t_train = time.time() - t2
     steps = epochs * (len(i_tr) // batch)
-    report = {"train": {"ccds": train_ccds, "candidates": int(len(lab)), "real": int(lab.sum()),
+    report = {"arch": arch, "train": {"ccds": train_ccds, "candidates": int(len(lab)), "real": int(lab.sum()),
                         "split": [int(len(i_tr)), int(len(i_va)), int(len(i_te))], "epochs": epochs, "batch": batch,
                         "lr": lr, "steps": steps, "seconds": t_train, "stamps_per_s": steps * batch / t_train,
                         "loss_by_epoch": hist}}
@@ -282,9 +283,11 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=500)
     ap.add_argument("--out", default=None)
     ap.add_argument("--weights", default=None, help="save the trained weights (float32 .npy)")
+    ap.add_argument("--arch", choices=["small", "ri"], default="small",
+                    help="small: three-convolution network; ri: the paper's rotation-invariant residual network")
     a = ap.parse_args(argv)
     report, model = run(a.train_ccds, a.epochs, a.batch, a.lr, a.eval_ccds, a.seed,
-                        log=lambda s: print(s, file=sys.stderr, flush=True))
+                        log=lambda s: print(s, file=sys.stderr, flush=True), arch=a.arch)
     js = json.dumps(report, indent=1)
     print(js)
     if a.out:

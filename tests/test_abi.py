@@ -18,7 +18,7 @@ def declared_functions():
         src = re.sub(r"//[^\n]*", "", src)
         for m in re.finditer(r"\b([A-Za-z_][A-Za-z0-9_]*)\s*\(", src):
             name = m.group(1)
-            if name.startswith(("sfft_", "rb_", "phot_")) and not name.endswith("_t"):
+            if name.startswith(("sfft_", "rb_", "rbri_", "phot_")) and not name.endswith("_t"):
                 names.add(name)
     return sorted(names)
 
