@@ -134,6 +134,8 @@ static void build_layout(sfft_plan_s* p) {
   add_region(p->scale, cur, sizeof(double) * p->N * B);
   add_region(p->dinv, cur, sizeof(double) * 1024 * ((p->N + 31) / 32) * B);   // inverted 32 x 32 diagonal blocks
   add_region(p->gbar, cur, 64);                                               // grid barrier of the factorisation
+  // substitutions: the y and x vectors, read by other CTAs as they appear
+  add_region(p->swave, cur, sizeof(double) * 2 * p->N * B);
   add_region(p->vec, cur, sizeof(double) * 4 * p->N * B);
   add_region(p->theta_off, cur, sizeof(double) * p->N * B);
   p->ws_bytes = cur;
@@ -259,6 +261,8 @@ static void build_tc_jobs(sfft_plan_s* p, int NP, int chunk, int cap, int max_nd
         j.npair = pt.npair;
         j.dj0 = pt.dj0;
         j.nd = pt.nd;
+        j.zp = ccd * p->d_batch;
+        j.zw = ccd * p->n_wa;
         p->h_tcjobs.push_back(j);
       }
     p->tc_count.push_back((int)p->h_tcjobs.size() - p->tc_first.back());
@@ -338,8 +342,10 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
       }
   p->n_hd = (int)p->dlist.size();
   const size_t slab = (size_t)d.H * p->M * 2 * p->elem;
-  // product spectra of up to 24 GB per plan (GB300: 288 GB of HBM3e)
-  const size_t budget = size_t(24) << 30;
+  // product spectra of up to 64 GB per plan (GB300: 288 GB of HBM3e); a
+  // batch of CCDs then still takes a few dozen differences per pass, enough
+  // to fill the tensor-core contraction's 128-pair patterns
+  const size_t budget = size_t(64) << 30;
   const int d_batch_max =
       (int)std::max<size_t>(1, std::min<size_t>(budget / (slab * (size_t)d.batch), (size_t)p->n_hd));
   int tuned_db = 0, tuned_rows = 0, tuned_parts = 0;

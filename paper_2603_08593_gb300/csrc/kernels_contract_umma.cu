@@ -14,16 +14,18 @@
 //
 // Roles (576 threads, one CTA per SM):
 //   warps 0-7  A producers: lane l of warp w is pair 32 (w % 4) + l (warp w
-//              reaches tensor-memory lanes 32 (w % 4) ...); per unit (k-slot,
-//              four rows) it loads its four probe values from the staged rows,
-//              splits them and stores the unit's 16 A columns to tensor memory
-//              (tcgen05.st), warps 0-3 for half of a group's units and
-//              warps 4-7 for the other half;
+//              reaches tensor-memory lanes 32 (w % 4) ...); per two units
+//              (adjacent k-slots, four rows) it loads its probe values from
+//              the staged rows (one 16-byte load per row), splits them and
+//              stores each unit's 16 A columns to tensor memory (tcgen05.st),
+//              warps 0-3 for half of a group's units and warps 4-7 for the
+//              other half;
 //              warps 0-3 read the accumulators back (tcgen05.ld) at the end for
 //              the lag DFT;
 //   warps 8-15 B producers: warp 8 + e forms W_m for unit e's four rows and
 //              writes its TF32 and BF16 operand tiles (32 x 32 bytes each,
-//              K-major, no swizzle) to shared memory;
+//              K-major, no swizzle) to shared memory, each lane two rows of
+//              one monomial with 16- and 8-byte stores;
 //   warp 16    MMA issuer: one elected lane issues the sixteen MMAs of a
 //              group (two per unit) and one commit;
 //   warp 17    copy producer: stages, 32 weight rows at a time and into two
@@ -63,6 +65,7 @@ constexpr int WARP_MMA = 16, WARP_COPY = 17;   // warps 0-7: A producers, 8-15: 
 constexpr int NTHREADS = 32 * 18;
 constexpr int TMEM_COLS = 512;       // D: KT x 32 columns, A: GSLOT x UPG x 16 columns
 static_assert(KT * 32 + GSLOT * UPG * 16 <= TMEM_COLS, "tensor memory budget");
+static_assert(SPG == 1 && KT % 2 == 0 && UPG % 4 == 0, "A producers take two adjacent k-slots per 16-byte load");
 
 // One stage: a box of probe rows per difference (tensor copies; box i starts
 // i % 8 rows early so that the differences' rows fall on different banks),
@@ -213,10 +216,10 @@ k_contract_umma(const __grid_constant__ CUtensorMap tmP, const __grid_constant__
       __syncwarp();
       if (lane < job.nd) {
         const int4 e = dj[lane];   // (d_local, u_lo, u_hi, -): rows yc - u_hi - lane % 8 ...
-        tma_load_3d(&st.P[lane][0], &tmP, 2 * k0, yc - e.z - lane % 8, e.x, &S.raw_full[sidx]);
+        tma_load_3d(&st.P[lane][0], &tmP, 2 * k0, yc - e.z - lane % 8, job.zp + e.x, &S.raw_full[sidx]);
       } else if (lane < job.nd + DM + 1) {
         const int a = lane - job.nd;
-        tma_load_3d(&st.V[a][0], &tmV, 2 * k0, yc, a, &S.raw_full[sidx]);
+        tma_load_3d(&st.V[a][0], &tmV, 2 * k0, yc, job.zw + a, &S.raw_full[sidx]);
       } else if (lane == 31) {
         bulk_copy_g2s(&st.ypw[0][0], ytab + (int64_t)yc * 16, (unsigned)(nrow * 64), &S.raw_full[sidx]);
       }
@@ -277,24 +280,31 @@ k_contract_umma(const __grid_constant__ CUtensorMap tmP, const __grid_constant__
       for (int sp = 0; sp < GPC; ++sp) {
         const int g = c * GPC + sp, slot = g % GSLOT;
         if (g >= GSLOT && !wait_phase(&S.mma_done[slot], (unsigned)(((g / GSLOT) - 1) & 1), abort)) break;
-#pragma unroll 2
-        for (int e = e0; e < e0 + UPG / 2; ++e) {
-          const int kk = e / SPG, s = SPG * sp + e % SPG;   // k-slot and k-step (rows 4 s ..) of unit e
-          uint32_t v[16];
+#pragma unroll
+        for (int e = e0; e < e0 + UPG / 2; e += 2) {   // units e, e + 1: adjacent k-slots, one 16-byte load per row
+          const int kk = e, s = sp;
+          uint32_t v[2][16];
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
-            const float2 pv = *reinterpret_cast<const float2*>(P + (4 * s + r) * PITCH + kk * 8);
-            const float hr = tf32_trunc(pv.x), hi = tf32_trunc(pv.y);
-            v[2 * r] = __float_as_uint(hr);        // TF32 columns: k = 2 r + (re, im)
-            v[2 * r + 1] = __float_as_uint(hi);
-            v[8 + r] = pack_bf16(hr, hi);          // BF16 columns 0-3: hi(P) of row r
-            v[12 + r] = pack_bf16(pv.x - hr, pv.y - hi);   // BF16 columns 4-7: lo(P) of row r
+            const float4 pv = *reinterpret_cast<const float4*>(P + (4 * s + r) * PITCH + kk * 8);
+            const float px[2] = {pv.x, pv.z}, py[2] = {pv.y, pv.w};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const float hr = tf32_trunc(px[h]), hi = tf32_trunc(py[h]);
+              v[h][2 * r] = __float_as_uint(hr);        // TF32 columns: k = 2 r + (re, im)
+              v[h][2 * r + 1] = __float_as_uint(hi);
+              v[h][8 + r] = pack_bf16(hr, hi);          // BF16 columns 0-3: hi(P) of row r
+              v[h][12 + r] = pack_bf16(px[h] - hr, py[h] - hi);   // BF16 columns 4-7: lo(P) of row r
+            }
           }
-          asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-                       "%12, %13, %14, %15, %16};"
-                       ::"r"(t_a + 16 * (UPG * slot + e) + lane_off), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]),
-                         "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]),
-                         "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]) : "memory");
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                         "%12, %13, %14, %15, %16};"
+                         ::"r"(t_a + 16 * (UPG * slot + e + h) + lane_off), "r"(v[h][0]), "r"(v[h][1]), "r"(v[h][2]),
+                           "r"(v[h][3]), "r"(v[h][4]), "r"(v[h][5]), "r"(v[h][6]), "r"(v[h][7]), "r"(v[h][8]),
+                           "r"(v[h][9]), "r"(v[h][10]), "r"(v[h][11]), "r"(v[h][12]), "r"(v[h][13]), "r"(v[h][14]),
+                           "r"(v[h][15]) : "memory");
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -309,7 +319,7 @@ k_contract_umma(const __grid_constant__ CUtensorMap tmP, const __grid_constant__
     // k-step e % SPG) of every group; lane: monomial m = lane % 16, rows
     // r = lane / 16 and + 2
     const int e = warp - 8, kk = e / SPG;
-    const int m = lane & 15, r0 = lane >> 4;
+    const int m = lane & 15, rp = lane >> 4;
     int am = 0, bm = 0;
     mono_ab(m < NMONO ? m : 0, am, bm);
     const bool live = m < NMONO;
@@ -324,29 +334,34 @@ k_contract_umma(const __grid_constant__ CUtensorMap tmP, const __grid_constant__
         {
           uint8_t* tf = &S.btile[slot][e][0][0];
           uint8_t* tb = &S.btile[slot][e][1][0];
+          float wr[2], wi[2], hr[2], hi[2];
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
-            const int r = r0 + 2 * h, row = 4 * s + r;
+            const int row = 4 * s + 2 * rp + h;
             const bool on = live && yc + row < ye;
             const float2 vv = *reinterpret_cast<const float2*>(&st.V[am][row * PITCH + kk * 8]);
             const float yp = st.ypw[row][2 * bm];
-            const float wr = on ? yp * vv.x : 0.f, wi = on ? yp * vv.y : 0.f;
-            const float hr = tf32_trunc(wr), hi = tf32_trunc(wi);
-            const float lr = wr - hr, li = wi - hi;
-            // rows n = m (Re) and 16 + m (Im); element (n, k) of the TF32 tile at
-            // (n / 8) 256 + (k / 4) 128 + (n % 8) 16 + (k % 4) 4, k = 2 r + (re, im)
-            const int kb = (2 * r / 4) * 128 + (2 * r % 4) * 4;
-            const int nre = (m / 8) * 256 + (m % 8) * 16, nim = ((16 + m) / 8) * 256 + (m % 8) * 16;
-            *reinterpret_cast<float2*>(tf + nre + kb) = make_float2(hr, hi);
-            *reinterpret_cast<float2*>(tf + nim + kb) = make_float2(-hi, hr);
-            // BF16 tile: element (n, k) at (n / 8) 256 + (k / 8) 128 + (n % 8) 16 + (k % 8) 2;
-            // k = 2 r + (re, im) multiplies hi(P), k = 8 + 2 r + (re, im) multiplies lo(P)
-            const int k1 = (2 * r % 8) * 2, k2 = 128 + (2 * r % 8) * 2;
-            *reinterpret_cast<uint32_t*>(tb + nre + k1) = pack_bf16(lr, li);
-            *reinterpret_cast<uint32_t*>(tb + nim + k1) = pack_bf16(-li, lr);
-            *reinterpret_cast<uint32_t*>(tb + nre + k2) = pack_bf16(wr, wi);
-            *reinterpret_cast<uint32_t*>(tb + nim + k2) = pack_bf16(-wi, wr);
+            wr[h] = on ? yp * vv.x : 0.f;
+            wi[h] = on ? yp * vv.y : 0.f;
+            hr[h] = tf32_trunc(wr[h]);
+            hi[h] = tf32_trunc(wi[h]);
           }
+          // rows n = m (Re) and 16 + m (Im); element (n, k) of the TF32 tile at
+          // (n / 8) 256 + (k / 4) 128 + (n % 8) 16 + (k % 4) 4, k = 2 r + (re, im):
+          // this lane's rows 2 rp, 2 rp + 1 fill one 16-byte core-matrix row
+          const int nre = (m / 8) * 256 + (m % 8) * 16, nim = ((16 + m) / 8) * 256 + (m % 8) * 16;
+          *reinterpret_cast<float4*>(tf + nre + rp * 128) = make_float4(hr[0], hi[0], hr[1], hi[1]);
+          *reinterpret_cast<float4*>(tf + nim + rp * 128) = make_float4(-hi[0], hr[0], -hi[1], hr[1]);
+          // BF16 tile: element (n, k) at (n / 8) 256 + (k / 8) 128 + (n % 8) 16 + (k % 8) 2;
+          // k = 2 r + (re, im) multiplies hi(P), k = 8 + 2 r + (re, im) multiplies lo(P)
+          const float lr0 = wr[0] - hr[0], li0 = wi[0] - hi[0], lr1 = wr[1] - hr[1], li1 = wi[1] - hi[1];
+          const int kb1 = rp * 8;
+          *reinterpret_cast<uint2*>(tb + nre + kb1) = make_uint2(pack_bf16(lr0, li0), pack_bf16(lr1, li1));
+          *reinterpret_cast<uint2*>(tb + nim + kb1) = make_uint2(pack_bf16(-li0, lr0), pack_bf16(-li1, lr1));
+          *reinterpret_cast<uint2*>(tb + nre + 128 + kb1) =
+              make_uint2(pack_bf16(wr[0], wi[0]), pack_bf16(wr[1], wi[1]));
+          *reinterpret_cast<uint2*>(tb + nim + 128 + kb1) =
+              make_uint2(pack_bf16(-wi[0], wr[0]), pack_bf16(-wi[1], wr[1]));
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
@@ -459,21 +474,20 @@ static cudaError_t contract_umma_dm(const sfft_plan_s* p, int job0, int njobs, v
   const int rows = p->tc_rows;
   const int nb = (H + rows - 1) / rows;
   const int rbox = CH + (L - 1) + 7;
-  const size_t slab = (size_t)H * p->M * sizeof(float2);
-  const int npat = njobs / B;   // jobs are ordered CCD-major
-  for (int ccd = 0; ccd < B; ++ccd) {
-    CUtensorMap mp, mv;
-    char* base = static_cast<char*>(ws);
-    if (!make_map(&mp, base + p->phat.off + (size_t)ccd * p->d_batch * slab, p->M, H, p->d_batch, rbox) ||
-        !make_map(&mv, base + p->wspec.off + (size_t)ccd * p->n_wa * slab, p->M, H, p->n_wa, CH))
-      return cudaErrorInvalidValue;
-    for (int j0 = 0; j0 < npat; j0 += 65535) {
-      dim3 grid(p->M / KT, std::min(65535, npat - j0), nb);
-      kern<<<grid, NTHREADS, smem, p->stream>>>(mp, mv, p->d_tcjobs + job0 + ccd * npat + j0, p->d_tcpairs,
-                                                p->d_tcdj, (char*)ws, H, p->M, p->Nf, L, rows, rbox,
-                                                (const float2*)p->twD, (const float*)p->ytab);
-      p->nlaunch += 1;
-    }
+  // one launch for every CCD of the batch: the product and weight spectra of
+  // all CCDs are consecutive slabs, so one tensor map covers each kind and a
+  // job names its CCD's first slab
+  CUtensorMap mp, mv;
+  char* base = static_cast<char*>(ws);
+  if (!make_map(&mp, base + p->phat.off, p->M, H, p->d_batch * B, rbox) ||
+      !make_map(&mv, base + p->wspec.off, p->M, H, p->n_wa * B, CH))
+    return cudaErrorInvalidValue;
+  for (int j0 = 0; j0 < njobs; j0 += 65535) {
+    dim3 grid(p->M / KT, std::min(65535, njobs - j0), nb);
+    kern<<<grid, NTHREADS, smem, p->stream>>>(mp, mv, p->d_tcjobs + job0 + j0, p->d_tcpairs, p->d_tcdj, (char*)ws, H,
+                                              p->M, p->Nf, L, rows, rbox, (const float2*)p->twD,
+                                              (const float*)p->ytab);
+    p->nlaunch += 1;
   }
   return cudaGetLastError();
 }

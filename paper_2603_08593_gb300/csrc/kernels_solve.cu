@@ -9,7 +9,8 @@
 // Jacobi equilibration D_s = diag(A)^-1/2, right-looking blocked
 // Cholesky of D_s A D_s (32 x 32 blocks, all block steps in one cooperative
 // launch), blocked forward and backward substitution with the inverted
-// diagonal blocks, theta = D_s y.
+// diagonal blocks (one cooperative launch, blocks handed between CTAs by
+// flags), theta = D_s y.
 // Per-CCD status flags (never a trap): 1 = not positive definite, 2 = non-finite.
 #include <algorithm>
 
@@ -200,21 +201,27 @@ k_chol_init(const double* __restrict__ A, double* __restrict__ Lf, double* __res
 }
 
 // ---------------------------------------------------------------- persistent blocked Cholesky
-// One cooperative launch factors every CCD's matrix.  For each 32-column
-// block k: (A) one CTA per CCD factors the diagonal block in shared memory and
-// inverts the factor; (B) all CTAs take 32-row tiles of the panels below the
-// diagonal blocks and multiply them by the transposed inverse (the panel
-// triangular solve as a product); (C) all CTAs take 32 x 32 tiles of the
-// trailing lower triangles and subtract P_i P_j^T, and the CTA that updates
-// the next diagonal block factors it at once (A of step k + 1, overlapped
-// with the rest of C).  The phases are separated
-// by a grid-wide barrier whose waits are bounded: a barrier that gives up (or
-// sees another CTA give up) flags every CCD with bit 4 and the kernel returns.
-// The inverses of the diagonal blocks are kept for the substitutions.  Data
-// written by other CTAs is read with L2-coherent loads (ld.global.cg).
+// One cooperative launch (one CTA per SM for a few CCDs) factors every CCD's
+// matrix.  For each 32-column block k: (B) the CTAs take 8-row pieces of the
+// panels below the diagonal blocks and solve X L_kk^T = A by substitution
+// (a warp per row, a lane per column); (C) they take 8 x 32 pieces of the
+// trailing lower triangles and subtract P_i P_j^T, while one CTA per CCD
+// updates the next diagonal block in shared memory and factors it
+// (look-ahead).  GB300 retires about two FP64 FMAs per SM per clock, so the
+// pieces are small enough to spread each step over every SM, and the chain
+// from one diagonal block to the next is kept short: the block factor takes
+// one barrier per column and maps the threads onto the elements each column
+// step touches, and the inverses of the diagonal factors, which only the
+// substitutions need, are formed after the last step, all blocks at once.
+// The phases are separated by a grid-wide barrier whose waits are bounded:
+// a barrier that gives up (or sees another CTA give up) flags every CCD with
+// bit 4 and the kernel returns.  Data written by other CTAs is read with
+// L2-coherent loads (ld.global.cg).
 struct GridBar { unsigned count, gen, abort, pad; };
 
 constexpr int kBarSpin = 1 << 24;   // x >= 64 ns per try: about a second
+constexpr int PRW = 8;              // rows per piece of the panel and trailing updates
+constexpr int NTRI = NBK * (NBK + 1) / 2;
 
 __device__ bool grid_sync_bounded(GridBar* bar, int* flag_sh) {
   __syncthreads();
@@ -243,237 +250,366 @@ __device__ bool grid_sync_bounded(GridBar* bar, int* flag_sh) {
   return *flag_sh != 0;
 }
 
-// Factor the diagonal block [kb, kb + nb) of one CCD with the whole CTA
-// (identity-padded past nb), write the factor back and its inverse (32 x 32,
-// lower) to `inv_out`.  Pivots use the reciprocal square root, so neither a
-// square root nor a division sits on the column-to-column dependency chain.
-// A non-positive or non-finite pivot is replaced by 1 and reported in the
-// CCD's status word.
-__device__ void factor_diag(double* __restrict__ l, double* __restrict__ inv_out, int* __restrict__ st, int N, int kb,
-                            int nb, double (*blk)[NBK + 1], double (*inv)[NBK + 1], double* rinv) {
+struct CholSmem {
+  double blk[NBK][NBK + 1];   // diagonal block, or the rows of a piece
+  double aux[NBK][NBK + 1];   // a diagonal factor, panel rows, or an inverse
+  double pinv[NBK], prs[NBK], dgl[NBK];   // per pivot d: 1 / d, 1 / sqrt(d), sqrt(d)
+  unsigned char ti[NTRI], tj[NTRI];       // e -> (i, j), j <= i, e = i (i + 1) / 2 + j
+  int flag;
+};
+
+// Pivot c: a non-positive or non-finite d is replaced by 1 and reported in
+// the CCD's status word.
+__device__ __forceinline__ void set_pivot(CholSmem& S, int c, double d0, int* st) {
+  const bool bad = !(d0 > 0.0) || !isfinite(d0);
+  if (bad) atomicOr(st, isfinite(d0) ? 1 : 2);
+  const double d = bad ? 1.0 : d0;
+  const double r = rsqrt(d);
+  S.pinv[c] = r * r;
+  S.prs[c] = r;
+  S.dgl[c] = d * r;
+}
+
+// Factor S.blk (lower, identity past the block's size) in place: right-
+// looking on the unscaled Schur complement, a_ij -= a_ic a_jc / d_c for
+// c < j <= i, one barrier per column (the thread that updates the next
+// diagonal element forms its pivot at once), then l_ij = a_ij / sqrt(d_j).
+__device__ void factor_block(CholSmem& S, int* st) {
   const int tid = threadIdx.x;
-  for (int e = tid; e < NBK * NBK; e += blockDim.x) {
-    const int i = e / NBK, j = e % NBK;
-    blk[i][j] = (i < nb && j <= i) ? __ldcg(l + (int64_t)(kb + i) * N + kb + j) : (i == j ? 1.0 : 0.0);
-    inv[i][j] = i == j ? 1.0 : 0.0;
+  if (tid == 0) set_pivot(S, 0, S.blk[0][0], st);
+  __syncthreads();
+  for (int c = 0; c < NBK - 1; ++c) {
+    const double p = S.pinv[c];
+    const int m = NBK - 1 - c;
+    for (int e = tid; e < m * (m + 1) / 2; e += blockDim.x) {
+      const int i = c + 1 + S.ti[e], j = c + 1 + S.tj[e];
+      const double v = S.blk[i][j] - S.blk[i][c] * S.blk[j][c] * p;
+      S.blk[i][j] = v;
+      if (e == 0) set_pivot(S, c + 1, v, st);   // (i, j) = (c + 1, c + 1)
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < NTRI; e += blockDim.x) {
+    const int i = S.ti[e], j = S.tj[e];
+    S.blk[i][j] = i == j ? S.dgl[j] : S.blk[i][j] * S.prs[j];
   }
   __syncthreads();
-  for (int c = 0; c < NBK; ++c) {
-    if (tid == 0) {
-      double d = blk[c][c];
-      if (!(d > 0.0) || !isfinite(d)) {
-        atomicOr(st, isfinite(d) ? 1 : 2);
-        d = 1.0;
-      }
-      const double r = rsqrt(d);
-      blk[c][c] = d * r;
-      rinv[c] = r;
-    }
-    __syncthreads();
-    if (tid > c && tid < NBK) blk[tid][c] *= rinv[c];
-    __syncthreads();
-    for (int e = tid; e < NBK * NBK; e += blockDim.x) {
-      const int i = e / NBK, j = e % NBK;
-      if (j > c && j <= i) blk[i][j] -= blk[i][c] * blk[j][c];
-    }
-    __syncthreads();
+}
+
+// S.aux = inverse of the lower factor in S.blk (L X = I by row elimination:
+// row t is final once scaled, then removed below).
+__device__ void invert_block(CholSmem& S) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NBK * (NBK + 1); e += blockDim.x) {
+    const int i = e / (NBK + 1), j = e % (NBK + 1);
+    S.aux[i][j] = i == j ? 1.0 : 0.0;
   }
-  // L X = I by row elimination: row t is final once scaled, then removed below
+  if (tid < NBK) S.pinv[tid] = 1.0 / S.blk[tid][tid];
+  __syncthreads();
   for (int t = 0; t < NBK; ++t) {
-    if (tid <= t) inv[t][tid] *= rinv[t];
+    if (tid <= t) S.aux[t][tid] *= S.pinv[t];
     __syncthreads();
-    for (int e = tid; e < NBK * NBK; e += blockDim.x) {
-      const int i = e / NBK, j = e % NBK;
-      if (i > t && j <= t) inv[i][j] -= blk[i][t] * inv[t][j];
+    const int w = t + 1, n = (NBK - 1 - t) * w;
+    for (int e = tid; e < n; e += blockDim.x) {
+      const int i = t + 1 + e / w, j = e % w;
+      S.aux[i][j] -= S.blk[i][t] * S.aux[t][j];
     }
     __syncthreads();
   }
-  for (int e = tid; e < NBK * NBK; e += blockDim.x) {
+}
+
+// S.blk <- the factored diagonal block at rows/columns [r0, r0 + nb) of l
+// (identity past nb)
+__device__ void load_block(CholSmem& S, const double* __restrict__ l, int N, int r0, int nb, double (*dst)[NBK + 1]) {
+  for (int e = threadIdx.x; e < NBK * NBK; e += blockDim.x) {
     const int i = e / NBK, j = e % NBK;
-    inv_out[e] = inv[i][j];
-    if (i < nb && j <= i) l[(int64_t)(kb + i) * N + kb + j] = blk[i][j];
+    dst[i][j] = (i < nb && j <= i) ? __ldcg(l + (int64_t)(r0 + i) * N + r0 + j) : (i == j ? 1.0 : 0.0);
+  }
+}
+
+__device__ void store_block(const CholSmem& S, double* __restrict__ l, int N, int r0, int nb) {
+  for (int e = threadIdx.x; e < NTRI; e += blockDim.x) {
+    const int i = S.ti[e], j = S.tj[e];
+    if (i < nb) l[(int64_t)(r0 + i) * N + r0 + j] = S.blk[i][j];
   }
 }
 
 __global__ void __launch_bounds__(256)
 k_chol_coop(double* __restrict__ Lf, double* __restrict__ dinv, int* __restrict__ status, int N, int B,
             GridBar* __restrict__ bar) {
-  __shared__ double sa[NBK][NBK + 1], sb[NBK][NBK + 1];
-  __shared__ double rinv[NBK];
-  __shared__ int flag;
+  __shared__ CholSmem S;
   const int nblk = (N + NBK - 1) / NBK;
   const int64_t NN = (int64_t)N * N;
-  const int tid = threadIdx.x;
-  // (A) of block 0; later diagonal blocks are factored as soon as their last
-  // trailing update lands (look-ahead inside phase C)
-  for (int ccd = blockIdx.x; ccd < B; ccd += gridDim.x) {
-    __syncthreads();
-    factor_diag(Lf + ccd * NN, dinv + (int64_t)ccd * nblk * NBK * NBK, status + ccd, N, 0, min(NBK, N), sa, sb, rinv);
+  const int tid = threadIdx.x, G = gridDim.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int e = tid; e < NTRI; e += blockDim.x) {
+    int i = 0;
+    while ((i + 1) * (i + 2) / 2 <= e) ++i;
+    S.ti[e] = (unsigned char)i;
+    S.tj[e] = (unsigned char)(e - i * (i + 1) / 2);
   }
-  bool ok = grid_sync_bounded(bar, &flag);
+  // the first diagonal block of every CCD; later ones are factored as soon
+  // as their last trailing update lands (look-ahead inside phase C)
+  for (int ccd = blockIdx.x; ccd < B; ccd += G) {
+    __syncthreads();
+    load_block(S, Lf + ccd * NN, N, 0, min(NBK, N), S.blk);
+    __syncthreads();
+    factor_block(S, status + ccd);
+    store_block(S, Lf + ccd * NN, N, 0, min(NBK, N));
+  }
+  bool ok = grid_sync_bounded(bar, &S.flag);
   for (int k = 0; ok && k < nblk; ++k) {
     const int kb = k * NBK, nb = min(NBK, N - kb), rem = N - kb - nb;
     if (rem <= 0) break;   // uniform: the last block has no panel
-    // (B) panels, 32-row tiles: X = A inv(L_kk)^T; thread (row tid / 8, columns tid % 8 + 8 m)
-    const int T = (rem + NBK - 1) / NBK;
-    for (int item = blockIdx.x; item < B * T; item += gridDim.x) {
-      const int ccd = item / T, r0 = kb + nb + (item % T) * NBK;
+    const int T = (rem + NBK - 1) / NBK;   // block rows below the diagonal block
+    const int r0 = kb + nb;
+    // (B) panel pieces: X L_kk^T = A, warp = row of the piece, lane = column
+    for (int item = blockIdx.x; item < B * T * (NBK / PRW); item += G) {
+      const int ccd = item / (T * (NBK / PRW)), pc = item % (T * (NBK / PRW));
+      const int p0 = r0 + pc * PRW;
       double* l = Lf + ccd * NN;
-      const double* iv = dinv + ((int64_t)ccd * nblk + k) * NBK * NBK;
       __syncthreads();
-      for (int e = tid; e < NBK * NBK; e += blockDim.x) {
+      load_block(S, l, N, kb, nb, S.aux);
+      for (int e = tid; e < PRW * NBK; e += blockDim.x) {
         const int i = e / NBK, c = e % NBK;
-        sb[i][c] = __ldcg(iv + e);
-        sa[i][c] = (r0 + i < N && c < nb) ? __ldcg(l + (int64_t)(r0 + i) * N + kb + c) : 0.0;
+        S.blk[i][c] = (p0 + i < N && c < nb) ? __ldcg(l + (int64_t)(p0 + i) * N + kb + c) : 0.0;
       }
       __syncthreads();
-      const int i = tid >> 3, c0 = tid & 7;
-      double out[4];
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const int c = c0 + 8 * m;
-        double s0 = 0.0, s1 = 0.0;
-        for (int t = 0; t + 1 <= c; t += 2) {
-          s0 += sa[i][t] * sb[c][t];
-          s1 += sa[i][t + 1] * sb[c][t + 1];
+      if (warp < PRW) {
+        const double rd = 1.0 / S.aux[lane][lane];
+        double acc = S.blk[warp][lane], x = 0.0;
+#pragma unroll 4
+        for (int t = 0; t < NBK; ++t) {
+          if (lane == t) x = acc * rd;
+          const double xt = __shfl_sync(0xffffffffu, x, t);
+          if (lane > t) acc -= xt * S.aux[lane][t];
         }
-        if ((c & 1) == 0) s0 += sa[i][c] * sb[c][c];
-        out[m] = s0 + s1;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int m = 0; m < 4; ++m) sa[i][c0 + 8 * m] = out[m];
-      __syncthreads();
-      for (int e = tid; e < NBK * NBK; e += blockDim.x) {
-        const int ii = e / NBK, c = e % NBK;
-        if (r0 + ii < N && c < nb) l[(int64_t)(r0 + ii) * N + kb + c] = sa[ii][c];
+        if (p0 + warp < N && lane < nb) l[(int64_t)(p0 + warp) * N + kb + lane] = x;
       }
     }
-    if (!(ok = grid_sync_bounded(bar, &flag))) break;
-    // (C) trailing update of the lower tiles; the CTA holding tile (0, 0), the
-    // next diagonal block, factors it right after its update
+    if (!(ok = grid_sync_bounded(bar, &S.flag))) break;
+    // (C) the next diagonal block of every CCD (one CTA each: update and
+    // factor), then 8 x 32 pieces of the other trailing tiles
     const int ntile = T * (T + 1) / 2;
-    const int r0 = kb + nb;
-    for (int item = blockIdx.x; item < B * ntile; item += gridDim.x) {
-      const int ccd = item / ntile;
-      int t = item % ntile, bi = 0;
+    const int npiece = (ntile - 1) * (NBK / PRW);
+    for (int item = blockIdx.x; item < B + B * npiece; item += G) {
+      __syncthreads();
+      if (item < B) {
+        const int ccd = item, nb2 = min(NBK, rem);
+        double* l = Lf + ccd * NN;
+        for (int e = tid; e < NBK * NBK; e += blockDim.x) {
+          const int i = e / NBK, c = e % NBK;
+          S.aux[i][c] = (i < nb2 && c < nb) ? __ldcg(l + (int64_t)(r0 + i) * N + kb + c) : 0.0;
+        }
+        __syncthreads();
+        for (int e = tid; e < NTRI; e += blockDim.x) {
+          const int i = S.ti[e], j = S.tj[e];
+          double v = i == j ? 1.0 : 0.0;
+          if (i < nb2) {
+            double s0 = 0.0, s1 = 0.0;
+#pragma unroll 8
+            for (int c = 0; c < NBK; c += 2) {
+              s0 += S.aux[i][c] * S.aux[j][c];
+              s1 += S.aux[i][c + 1] * S.aux[j][c + 1];
+            }
+            v = __ldcg(l + (int64_t)(r0 + i) * N + r0 + j) - (s0 + s1);
+          }
+          S.blk[i][j] = v;
+        }
+        __syncthreads();
+        factor_block(S, status + ccd);
+        store_block(S, l, N, r0, nb2);
+        continue;
+      }
+      const int q = item - B, ccd = q / npiece, pc = q % npiece;
+      int t = 1 + pc / (NBK / PRW), bi = 0;
       while (t > bi) { t -= bi + 1; ++bi; }
       const int bj = t;
-      const int i0 = r0 + bi * NBK, j0 = r0 + bj * NBK;
+      const int i0 = r0 + bi * NBK + (pc % (NBK / PRW)) * PRW, j0 = r0 + bj * NBK;
       double* l = Lf + ccd * NN;
-      __syncthreads();
       for (int e = tid; e < NBK * NBK; e += blockDim.x) {
+        const int j = e / NBK, c = e % NBK;
+        S.aux[j][c] = (j0 + j < N && c < nb) ? __ldcg(l + (int64_t)(j0 + j) * N + kb + c) : 0.0;
+      }
+      for (int e = tid; e < PRW * NBK; e += blockDim.x) {
         const int i = e / NBK, c = e % NBK;
-        sa[i][c] = (i0 + i < N && c < nb) ? __ldcg(l + (int64_t)(i0 + i) * N + kb + c) : 0.0;
-        sb[i][c] = (j0 + i < N && c < nb) ? __ldcg(l + (int64_t)(j0 + i) * N + kb + c) : 0.0;
+        S.blk[i][c] = (i0 + i < N && c < nb) ? __ldcg(l + (int64_t)(i0 + i) * N + kb + c) : 0.0;
       }
       __syncthreads();
-      for (int e = tid; e < NBK * NBK; e += blockDim.x) {
-        const int i = e / NBK, j = e % NBK;
-        const int gi = i0 + i, gj = j0 + j;
-        if (gi >= N || gj >= N || gj > gi) continue;
+      const int i = tid / NBK, j = tid % NBK;
+      const int gi = i0 + i, gj = j0 + j;
+      if (i < PRW && gi < N && gj < N && gj <= gi) {
         double s0 = 0.0, s1 = 0.0;
 #pragma unroll 8
         for (int c = 0; c < NBK; c += 2) {
-          s0 += sa[i][c] * sb[j][c];
-          s1 += sa[i][c + 1] * sb[j][c + 1];
+          s0 += S.blk[i][c] * S.aux[j][c];
+          s1 += S.blk[i][c + 1] * S.aux[j][c + 1];
         }
         l[(int64_t)gi * N + gj] = __ldcg(l + (int64_t)gi * N + gj) - (s0 + s1);
       }
-      if (bi == 0) {   // tile (0, 0): the diagonal block of step k + 1 is final
-        __syncthreads();
-        factor_diag(l, dinv + ((int64_t)ccd * nblk + k + 1) * NBK * NBK, status + ccd, N, r0, min(NBK, N - r0),
-                    sa, sb, rinv);
-      }
     }
-    ok = grid_sync_bounded(bar, &flag);
+    ok = grid_sync_bounded(bar, &S.flag);
+  }
+  // inverses of the diagonal factors for the substitutions, all at once
+  for (int item = blockIdx.x; ok && item < B * nblk; item += G) {
+    const int ccd = item / nblk, b = item % nblk, jb = b * NBK;
+    __syncthreads();
+    load_block(S, Lf + ccd * NN, N, jb, min(NBK, N - jb), S.blk);
+    __syncthreads();
+    invert_block(S);
+    double* out = dinv + ((int64_t)ccd * nblk + b) * NBK * NBK;
+    for (int e = tid; e < NBK * NBK; e += blockDim.x) out[e] = S.aux[e / NBK][e % NBK];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0 && ((volatile GridBar*)bar)->abort != 0u)
     for (int c = 0; c < B; ++c) atomicOr(&status[c], 4);
 }
 
-// x = D_s (L L^T)^-1 D_s rhs, one CTA per CCD, blocked substitution with the
-// inverted diagonal blocks: each block of unknowns is a 32 x 32 product by one
-// warp, the coupling to the remaining unknowns is applied by all threads.
-__global__ void __launch_bounds__(1024)
+// ---------------------------------------------------------------- substitutions
+// x = D_s (L L^T)^-1 D_s rhs in one cooperative launch.  The unknowns come
+// in 32-blocks (CCD c, block b); item o = b B + c belongs to CTA o mod G.
+// Forward (increasing o): the owner gathers r_b - sum_{j<b} L_bj y_j as the
+// y_j appear, then publishes y_b = inv(L_bb) (...).  Backward (decreasing o):
+// z_b = y_b - sum_{j>b} L_jb^T x_j, x_b = inv(L_bb)^T z_b.  The y and x
+// buffers start as an all-ones bit pattern that no stored value has (a NaN
+// result is stored as the canonical NaN), so a thread waits for exactly the
+// values it reads, with the rows of L fetched before the wait.  Every item
+// waits only on items of smaller order, each CTA takes its items in that
+// order and the grid is co-resident, so the smallest unfinished item can
+// always run.  The waits are bounded; one that gives up marks the CCDs
+// (bit 4) and the CTA stops.
+constexpr long long kUnset = -1ll;   // all bits set
+
+struct SolveSmem {
+  double iv[NBK][NBK + 1];
+  double v[NBK];
+  double part[NBK][9];
+  int fail;
+};
+
+__device__ __forceinline__ double publishable(double v) {
+  return isnan(v) ? __longlong_as_double(0x7FF8000000000000ll) : v;
+}
+
+__device__ __forceinline__ bool wait_value(const double* p, double& v) {
+  for (int it = 0; it < kBarSpin; ++it) {
+    const double x = __ldcv(p);
+    if (__double_as_longlong(x) != kUnset) {
+      v = x;
+      return true;
+    }
+    if (it > 16) __nanosleep(32);
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(256)
 k_chol_solve(const double* __restrict__ Lf, const double* __restrict__ dinv, const double* __restrict__ scale,
-             const double* __restrict__ rhs, double* __restrict__ x, int N, int* __restrict__ status) {
-  extern __shared__ double sh[];   // y[N]
-  __shared__ double ld[NBK][NBK + 1];
-  const int ccd = blockIdx.x;
+             const double* __restrict__ rhs, double* __restrict__ x, int N, int B, double* __restrict__ ybuf,
+             double* __restrict__ xbuf, int* __restrict__ status) {
+  __shared__ SolveSmem S;
   const int nblk = (N + NBK - 1) / NBK;
-  const double* l = Lf + (int64_t)ccd * N * N;
-  const double* s = scale + (int64_t)ccd * N;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) sh[i] = rhs[(int64_t)ccd * N + i] * s[i];
-  // forward: L y = r
-  for (int bi = 0; bi < nblk; ++bi) {
-    const int jb = bi * NBK, nb = min(NBK, N - jb);
-    const double* inv = dinv + ((int64_t)ccd * nblk + bi) * NBK * NBK;
-    for (int e = threadIdx.x; e < NBK * NBK; e += blockDim.x) ld[e / NBK][e % NBK] = inv[e];
+  const int nitem = nblk * B, G = gridDim.x;
+  const int tid = threadIdx.x, row = tid >> 3, part = tid & 7;
+  if (tid == 0) S.fail = 0;
+  __syncthreads();
+  bool alive = true, waited = true;
+  // forward
+  for (int o = blockIdx.x; alive && o < nitem; o += G) {
+    const int b = o / B, ccd = o % B, jb = b * NBK, nb = min(NBK, N - jb);
+    const double* l = Lf + (int64_t)ccd * N * N;
+    const double* iv = dinv + ((int64_t)ccd * nblk + b) * NBK * NBK;
+    for (int e = tid; e < NBK * NBK; e += blockDim.x) S.iv[e / NBK][e % NBK] = iv[e];
+    double acc = 0.0;   // thread (row, part): columns part + 8 m of every block j < b
+    for (int j = 0; j < b && waited; ++j) {
+      double lv[NBK / 8], yv[NBK / 8];
+      const double* lr = l + (int64_t)(jb + min(row, nb - 1)) * N + j * NBK + part;
+#pragma unroll
+      for (int m = 0; m < NBK / 8; ++m) lv[m] = __ldcg(lr + 8 * m);
+      const double* y = ybuf + (int64_t)ccd * N + j * NBK + part;
+#pragma unroll
+      for (int m = 0; m < NBK / 8; ++m) waited = waited && wait_value(y + 8 * m, yv[m]);
+      if (waited && row < nb)
+#pragma unroll
+        for (int m = 0; m < NBK / 8; ++m) acc += lv[m] * yv[m];
+    }
+    if (!waited) S.fail = 1;
+    S.part[row][part] = acc;
     __syncthreads();
-    if (warp == 0) {
-      const double v = lane < nb ? sh[jb + lane] : 0.0;
-      double y0 = 0.0, y1 = 0.0;
+    if (S.fail) { alive = false; break; }
+    if (tid < NBK) {
+      double s = 0.0;
+#pragma unroll
+      for (int p = 0; p < 8; ++p) s += S.part[tid][p];
+      S.v[tid] = tid < nb ? rhs[(int64_t)ccd * N + jb + tid] * scale[(int64_t)ccd * N + jb + tid] - s : 0.0;
+    }
+    __syncthreads();
+    if (tid < nb) {
+      double s0 = 0.0, s1 = 0.0;
 #pragma unroll
       for (int t = 0; t < NBK; t += 2) {
-        y0 += ld[lane][t] * __shfl_sync(0xffffffffu, v, t);
-        y1 += ld[lane][t + 1] * __shfl_sync(0xffffffffu, v, t + 1);
+        s0 += S.iv[tid][t] * S.v[t];
+        s1 += S.iv[tid][t + 1] * S.v[t + 1];
       }
-      if (lane < nb) sh[jb + lane] = y0 + y1;
-    }
-    __syncthreads();
-    for (int i = jb + nb + threadIdx.x; i < N; i += blockDim.x) {
-      const double* row = l + (int64_t)i * N + jb;
-      double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-      int c = 0;
-      for (; c + 3 < nb; c += 4) {
-        v0 += row[c] * sh[jb + c];
-        v1 += row[c + 1] * sh[jb + c + 1];
-        v2 += row[c + 2] * sh[jb + c + 2];
-        v3 += row[c + 3] * sh[jb + c + 3];
-      }
-      for (; c < nb; ++c) v0 += row[c] * sh[jb + c];
-      sh[i] -= (v0 + v1) + (v2 + v3);
+      ybuf[(int64_t)ccd * N + jb + tid] = publishable(s0 + s1);
     }
     __syncthreads();
   }
-  // backward: L^T z = y
-  for (int bi = nblk - 1; bi >= 0; --bi) {
-    const int jb = bi * NBK, nb = min(NBK, N - jb);
-    const double* inv = dinv + ((int64_t)ccd * nblk + bi) * NBK * NBK;
-    for (int e = threadIdx.x; e < NBK * NBK; e += blockDim.x) ld[e / NBK][e % NBK] = inv[e];
+  // backward
+  const int last = (alive && (int)blockIdx.x < nitem) ? (nitem - 1 - (int)blockIdx.x) / G * G + (int)blockIdx.x : -1;
+  for (int o = last; alive && o >= 0; o -= G) {
+    const int b = o / B, ccd = o % B, jb = b * NBK, nb = min(NBK, N - jb);
+    const double* l = Lf + (int64_t)ccd * N * N;
+    const double* iv = dinv + ((int64_t)ccd * nblk + b) * NBK * NBK;
+    for (int e = tid; e < NBK * NBK; e += blockDim.x) S.iv[e / NBK][e % NBK] = iv[e];
+    double acc = 0.0;   // thread (column row, part): rows part + 8 m of every block j > b
+    for (int j = nblk - 1; j > b && waited; --j) {
+      const int nj = min(NBK, N - j * NBK);
+      double lv[NBK / 8], xv[NBK / 8];
+#pragma unroll
+      for (int m = 0; m < NBK / 8; ++m) {
+        const int r = min(part + 8 * m, nj - 1);
+        lv[m] = __ldcg(l + (int64_t)(j * NBK + r) * N + jb + min(row, nb - 1));
+      }
+      const double* xs = xbuf + (int64_t)ccd * N + j * NBK;
+#pragma unroll
+      for (int m = 0; m < NBK / 8; ++m) {
+        const int r = part + 8 * m;
+        xv[m] = 0.0;
+        if (r < nj) waited = waited && wait_value(xs + r, xv[m]);
+      }
+      if (waited && row < nb)
+#pragma unroll
+        for (int m = 0; m < NBK / 8; ++m)
+          if (part + 8 * m < nj) acc += lv[m] * xv[m];
+    }
+    if (!waited) S.fail = 1;
+    S.part[row][part] = acc;
     __syncthreads();
-    if (warp == 0) {
-      const double v = lane < nb ? sh[jb + lane] : 0.0;
-      double z0 = 0.0, z1 = 0.0;
+    if (S.fail) { alive = false; break; }
+    if (tid < NBK) {
+      double s = 0.0;
+#pragma unroll
+      for (int p = 0; p < 8; ++p) s += S.part[tid][p];
+      S.v[tid] = tid < nb ? __ldcg(ybuf + (int64_t)ccd * N + jb + tid) - s : 0.0;
+    }
+    __syncthreads();
+    if (tid < nb) {
+      double s0 = 0.0, s1 = 0.0;
 #pragma unroll
       for (int t = 0; t < NBK; t += 2) {
-        z0 += ld[t][lane] * __shfl_sync(0xffffffffu, v, t);
-        z1 += ld[t + 1][lane] * __shfl_sync(0xffffffffu, v, t + 1);
+        s0 += S.iv[t][tid] * S.v[t];
+        s1 += S.iv[t + 1][tid] * S.v[t + 1];
       }
-      if (lane < nb) sh[jb + lane] = z0 + z1;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < jb; i += blockDim.x) {
-      double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-      int c = 0;
-      for (; c + 3 < nb; c += 4) {
-        v0 += l[(int64_t)(jb + c) * N + i] * sh[jb + c];
-        v1 += l[(int64_t)(jb + c + 1) * N + i] * sh[jb + c + 1];
-        v2 += l[(int64_t)(jb + c + 2) * N + i] * sh[jb + c + 2];
-        v3 += l[(int64_t)(jb + c + 3) * N + i] * sh[jb + c + 3];
-      }
-      for (; c < nb; ++c) v0 += l[(int64_t)(jb + c) * N + i] * sh[jb + c];
-      sh[i] -= (v0 + v1) + (v2 + v3);
+      const double z = s0 + s1;
+      xbuf[(int64_t)ccd * N + jb + tid] = publishable(z);
+      const double v = z * scale[(int64_t)ccd * N + jb + tid];
+      if (!isfinite(v)) atomicOr(&status[ccd], 2);
+      x[(int64_t)ccd * N + jb + tid] = v;
     }
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const double v = sh[i] * s[i];
-    if (!isfinite(v)) atomicOr(&status[ccd], 2);
-    x[(int64_t)ccd * N + i] = v;
-  }
+  if (!alive && tid == 0)
+    for (int c = 0; c < B; ++c) atomicOr(&status[c], 4);
 }
 
 __global__ void k_theta_finish(const double* __restrict__ x, double* __restrict__ theta_off, int N, int batch, int add) {
@@ -561,8 +697,34 @@ static CprMap cpr_map(const sfft_plan_s* p) {
   return m;
 }
 
+// Cooperative grid size: one CTA per SM for a few CCDs (the FP64 pipe of an
+// SM is shared by its CTAs, and a smaller grid makes the grid-wide barriers
+// cheaper); for a batch of 8 or more, as many as fit, to hide load latency.
+static int coop_grid(const void* fn, int want, int batch) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
+  if (per_sm < 1) return 1;
+  return std::max(1, std::min(want, sms * (batch >= 8 ? per_sm : 1)));
+}
+
+static cudaError_t launch_coop(const void* fn, int grid, cudaStream_t s, void** args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
 cudaError_t launch_cholesky(const sfft_plan_s* p, const double* A, void* ws) {
-  const int N = p->Nsol, B = p->d.batch;
+  int N = p->Nsol, B = p->d.batch;
   double* Lf = ws_at<double>(ws, p->lfac);
   double* scale = ws_at<double>(ws, p->scale);
   int* status = ws_at<int>(ws, p->status);
@@ -573,37 +735,33 @@ cudaError_t launch_cholesky(const sfft_plan_s* p, const double* A, void* ws) {
   cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBar), p->stream);
   if (e != cudaSuccess) return e;
   // every CTA of the cooperative grid must be resident at once
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_coop, 256, 0);
   const int T0 = (N - NBK + NBK - 1) / NBK;
-  const int want = std::max(B, B * T0 * (T0 + 1) / 2);
-  const int grid = std::max(1, std::min(want, sms * std::max(per_sm, 1)));
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(256);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = p->stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, k_chol_coop, Lf, dinv, status, N, B, bar);
+  const int want = std::max(B, B + B * std::max(T0 * (T0 + 1) / 2 - 1, 1) * (NBK / PRW));
+  const int grid = coop_grid((const void*)k_chol_coop, want, B);
+  void* args[] = {&Lf, &dinv, &status, &N, &B, &bar};
+  e = launch_coop((const void*)k_chol_coop, grid, p->stream, args);
   p->nlaunch += 2;
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 cudaError_t launch_chol_solve(const sfft_plan_s* p, const double* rhs, double* x, void* ws) {
-  const int N = p->Nsol;
-  const size_t smem = sizeof(double) * N;
-  cudaFuncSetAttribute(k_chol_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_chol_solve<<<p->d.batch, 1024, smem, p->stream>>>(ws_at<double>(ws, p->lfac), ws_at<double>(ws, p->dinv),
-                                                      ws_at<double>(ws, p->scale), rhs, x, N,
-                                                      ws_at<int>(ws, p->status));
+  int N = p->Nsol, B = p->d.batch;
+  const int nitem = ((N + NBK - 1) / NBK) * B;
+  double* Lf = ws_at<double>(ws, p->lfac);
+  double* dinv = ws_at<double>(ws, p->dinv);
+  double* scale = ws_at<double>(ws, p->scale);
+  double* ybuf = ws_at<double>(ws, p->swave);
+  double* xbuf = ybuf + (size_t)p->N * B;
+  int* status = ws_at<int>(ws, p->status);
+  // y and x start unset (all bits one)
+  cudaError_t e = cudaMemsetAsync(ybuf, 0xFF, sizeof(double) * 2 * (size_t)p->N * B, p->stream);
+  if (e != cudaSuccess) return e;
+  const int grid = coop_grid((const void*)k_chol_solve, nitem, B);
+  void* args[] = {&Lf, &dinv, &scale, &rhs, &x, &N, &B, &ybuf, &xbuf, &status};
+  e = launch_coop((const void*)k_chol_solve, grid, p->stream, args);
   p->nlaunch += 1;
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

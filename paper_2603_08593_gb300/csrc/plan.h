@@ -31,6 +31,7 @@ struct Region { size_t off = 0, bytes = 0; };
 struct TcJob {
   int64_t probe, wts, out, status;   // byte offsets: slab of d_local = 0, weight spectra, G of d_local = 0, status
   int pair0, npair, dj0, nd;
+  int zp, zw;                        // the CCD's first product / weight spectrum in the batch-wide tensor maps
 };
 constexpr int kTcKT = 8;         // k-slots per CTA (one warp each)
 constexpr int kTcNT = 8;         // 8-column tiles per warp: up to 64 (d, u_y) pairs per CTA
@@ -87,7 +88,7 @@ struct sfft_plan_s {
   int4* d_tcdj = nullptr;
   // workspace regions (per-CCD strides where noted)
   sfft::Region sky, skyacc, good, gh, mfit, rowflag, rm, wspec, uspec, rhat, phat, gkk, gkb, gbk,
-      mom_bb, mom_b, eimg, lfac, scale, dinv, gbar, vec, theta_off, status;
+      mom_bb, mom_b, eimg, lfac, scale, dinv, gbar, swave, vec, theta_off, status;
   size_t ws_bytes = 0;
   // graph cache for sfft_subtract
   std::map<std::vector<uintptr_t>, cudaGraphExec_t> graphs;
