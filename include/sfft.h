@@ -83,6 +83,11 @@ typedef enum {
                                      split TF32/BF16 products on the tensor cores (the default) */
 #define SFFT_FLAG_MMA_SYNC_CONTRACT 8u /* mixed path: the tensor-core KK contraction with warp-level
                                           mma.sync instead of tcgen05 (the default) */
+#define SFFT_FLAG_PAIR_LANE_CONTRACT 16u /* mixed path: the tcgen05 KK contraction with one tensor-memory
+                                            lane per (difference, u_y) pair instead of one lane per
+                                            difference with the u_y shifts taken from the weight rows
+                                            (the default when a difference batch holds at least
+                                            min(96, all) differences) */
 
 typedef struct {
   int32_t H, W;              /* image rows, columns */

@@ -19,6 +19,7 @@ FLAG_GRAPH = 1
 FLAG_CONST_RATIO = 2
 FLAG_FMA_CONTRACT = 4
 FLAG_MMA_SYNC_CONTRACT = 8
+FLAG_PAIR_LANE_CONTRACT = 16
 
 
 class Desc(C.Structure):
@@ -147,11 +148,13 @@ class Plan:
     fma_contract=True runs the mixed path's KK contraction on the FP32 FMA
     pipes instead of the tensor cores (SFFT_FLAG_FMA_CONTRACT);
     mma_sync_contract=True keeps it on the tensor cores through warp-level
-    mma.sync instead of tcgen05 (SFFT_FLAG_MMA_SYNC_CONTRACT)."""
+    mma.sync instead of tcgen05 (SFFT_FLAG_MMA_SYNC_CONTRACT);
+    pair_lane_contract=True runs the tcgen05 contraction with one tensor-memory
+    lane per (difference, u_y) pair (SFFT_FLAG_PAIR_LANE_CONTRACT)."""
 
     def __init__(self, H, W, L, DK, DB, batch=1, prec="mixed", d_batch=0, rows_per_cta=0, autotune=0,
                  graph=False, stream=None, device=None, lag_parts=0, const_ratio=False, fma_contract=False,
-                 mma_sync_contract=False):
+                 mma_sync_contract=False, pair_lane_contract=False):
         import torch
         self._torch = torch
         lib = load()
@@ -161,7 +164,8 @@ class Plan:
         self.desc = Desc(H, W, L, DK, DB, batch, PREC[prec], autotune, d_batch, rows_per_cta, lag_parts,
                          (FLAG_GRAPH if graph else 0) | (FLAG_CONST_RATIO if const_ratio else 0) |
                          (FLAG_FMA_CONTRACT if fma_contract else 0) |
-                         (FLAG_MMA_SYNC_CONTRACT if mma_sync_contract else 0))
+                         (FLAG_MMA_SYNC_CONTRACT if mma_sync_contract else 0) |
+                         (FLAG_PAIR_LANE_CONTRACT if pair_lane_contract else 0))
         h = VP()
         with torch.cuda.device(self.device):
             _check(lib.sfft_plan(C.byref(self.desc), VP(self.stream.cuda_stream), C.byref(h)), "sfft_plan")

@@ -137,6 +137,8 @@ static void build_layout(sfft_plan_s* p) {
   // substitutions: the y and x vectors, read by other CTAs as they appear
   add_region(p->swave, cur, sizeof(double) * 2 * p->N * B);
   add_region(p->vec, cur, sizeof(double) * 4 * p->N * B);
+  // lane-per-difference contraction: k-slot products C[k][d_local][u_y][32] per CCD
+  add_region(p->cbuf, cur, p->dl ? sizeof(float) * (size_t)p->M * p->d_batch * p->d.L * 32 * B : 0);
   add_region(p->theta_off, cur, sizeof(double) * p->N * B);
   p->ws_bytes = cur;
 }
@@ -269,7 +271,62 @@ static void build_tc_jobs(sfft_plan_s* p, int NP, int chunk, int cap, int max_nd
   }
 }
 
+// Jobs of the lane-per-difference tensor-core contraction: per d-batch and
+// CCD, tiles of up to 128 consecutive differences, each with its u_y range
+// (the union over its differences) cut into runs of at most kDlMaxU; and
+// the (d_local, u_y, ux_lo, ux_hi) pairs whose lags k_lag_dft forms.
+static void build_dl_jobs(sfft_plan_s* p) {
+  const int w = p->w, B = p->d.batch;
+  const size_t cb_ccd = sizeof(float) * (size_t)p->M * p->d_batch * p->d.L * 32;
+  p->dl_first.clear();
+  p->dl_count.clear();
+  p->dlp_first.clear();
+  p->dlp_count.clear();
+  p->h_dljobs.clear();
+  p->h_dlpairs.clear();
+  for (int d0 = 0; d0 < p->n_hd; d0 += p->d_batch) {
+    const int nd = std::min(p->d_batch, p->n_hd - d0);
+    p->dlp_first.push_back((int)p->h_dlpairs.size());
+    for (int i = 0; i < nd; ++i) {
+      const int2 d = p->dlist[d0 + i];
+      const int ulo = std::max(-w, d.x - w), uhi = std::min(w, d.x + w);
+      const int xlo = std::max(-w, d.y - w), xhi = std::min(w, d.y + w);
+      for (int u = ulo; u <= uhi; ++u) p->h_dlpairs.push_back(int4{i, u, xlo, xhi});
+    }
+    p->dlp_count.push_back((int)p->h_dlpairs.size() - p->dlp_first.back());
+    p->dl_first.push_back((int)p->h_dljobs.size());
+    for (int ccd = 0; ccd < B; ++ccd)
+      for (int t0 = 0; t0 < nd; t0 += 128) {
+        const int nl = std::min(128, nd - t0);
+        int ulo = w, uhi = -w;
+        for (int i = t0; i < t0 + nl; ++i) {
+          const int2 d = p->dlist[d0 + i];
+          ulo = std::min(ulo, std::max(-w, d.x - w));
+          uhi = std::max(uhi, std::min(w, d.x + w));
+        }
+        const int nrun = (uhi - ulo + kDlMaxU) / kDlMaxU;
+        for (int r = 0; r < nrun; ++r) {
+          // runs of near-equal length
+          const int a = ulo + (uhi - ulo + 1) * r / nrun, b = ulo + (uhi - ulo + 1) * (r + 1) / nrun;
+          DlJob j;
+          j.cbuf = (int64_t)(p->cbuf.off + (size_t)ccd * cb_ccd);
+          j.status = (int64_t)(p->status.off + sizeof(int) * (size_t)ccd);
+          j.zp = ccd * p->d_batch;
+          j.zw = ccd * p->n_wa;
+          j.d_first = t0;
+          j.nlanes = nl;
+          j.u_lo = a;
+          j.nu = b - a;
+          p->h_dljobs.push_back(j);
+        }
+      }
+    p->dl_count.push_back((int)p->h_dljobs.size() - p->dl_first.back());
+  }
+}
+
 static void free_plan_device(sfft_plan_s* p) {
+  if (p->d_dljobs) cudaFree(p->d_dljobs);
+  if (p->d_dlpairs) cudaFree(p->d_dlpairs);
   if (p->d_tcjobs) cudaFree(p->d_tcjobs);
   if (p->d_tcpairs) cudaFree(p->d_tcpairs);
   if (p->d_tcdj) cudaFree(p->d_tcdj);
@@ -306,7 +363,8 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
   if (d.DK < 0 || d.DB < 0 || d.d_batch < 0 || d.rows_per_cta < 0) return SFFT_ERR_ARG;
   if (d.lag_parts < 0 || d.lag_parts > 3) return SFFT_ERR_ARG;
   if ((d.L & 1) == 0 || d.L > kMaxL) return SFFT_ERR_UNSUPPORTED;
-  if (d.flags & ~(SFFT_FLAG_GRAPH | SFFT_FLAG_CONST_RATIO | SFFT_FLAG_FMA_CONTRACT | SFFT_FLAG_MMA_SYNC_CONTRACT))
+  if (d.flags & ~(SFFT_FLAG_GRAPH | SFFT_FLAG_CONST_RATIO | SFFT_FLAG_FMA_CONTRACT | SFFT_FLAG_MMA_SYNC_CONTRACT |
+                  SFFT_FLAG_PAIR_LANE_CONTRACT))
     return SFFT_ERR_ARG;
   if (d.DK > kMaxD || d.DB > kMaxD) return SFFT_ERR_UNSUPPORTED;
   if (d.H < d.L || d.W < d.L || d.W < 16 || d.W > 2048) return SFFT_ERR_UNSUPPORTED;
@@ -368,9 +426,14 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
   p->rf_stride = ((d.H + 32) + 63) / 64 * 64;
   p->tc = !p->fp64 && !(d.flags & SFFT_FLAG_FMA_CONTRACT);
   p->umma = p->tc && !(d.flags & SFFT_FLAG_MMA_SYNC_CONTRACT);
+  // one lane per difference needs two whole k-slots per CTA and difference
+  // batches that fill most of the 128 lanes
+  p->dl = p->umma && !(d.flags & SFFT_FLAG_PAIR_LANE_CONTRACT) && p->M % 8 == 0 && d.H >= 32 &&
+          p->d_batch >= std::min(p->n_hd, 96);
   p->tc_rows = d.H;
   build_layout(p);
   build_jobs(p);
+  if (p->dl) build_dl_jobs(p);
   if (p->umma) build_tc_jobs(p, kUmmaPairs, 1, 1 << 30, kUmmaMaxDiffs);
   else if (p->tc) build_tc_jobs(p, 8 * kTcNT, kTcChunk, kTcRowCap, 1 << 30);
 
@@ -409,6 +472,8 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
   if (st == SFFT_OK && p->tc) st = upload((void**)&p->d_tcjobs, p->h_tcjobs);
   if (st == SFFT_OK && p->tc) st = upload((void**)&p->d_tcpairs, p->h_tcpairs);
   if (st == SFFT_OK && p->tc) st = upload((void**)&p->d_tcdj, p->h_tcdj);
+  if (st == SFFT_OK && p->dl) st = upload((void**)&p->d_dljobs, p->h_dljobs);
+  if (st == SFFT_OK && p->dl) st = upload((void**)&p->d_dlpairs, p->h_dlpairs);
   if (st != SFFT_OK) {
     free_plan_device(p);
     delete p;
@@ -474,7 +539,8 @@ static sfft_status_t build_normal_impl(sfft_plan_t p, const float* R, const floa
     {
       Phase ph(p, SFFT_PROF_CONTRACT_KK);
       if (p->tc) {
-        CK(p->umma ? launch_contract_umma(p, (int)ib, ws) : launch_contract_tc(p, (int)ib, ws));
+        if (p->dl) CK(launch_contract_dlane(p, (int)ib, ws));
+        else CK(p->umma ? launch_contract_umma(p, (int)ib, ws) : launch_contract_tc(p, (int)ib, ws));
         CK(launch_contract_slot0(p, p->DM_KK, p->kk_first[ib], p->kk_count[ib], ws));
       } else {
         CK(launch_contract(p, p->DM_KK, p->kk_first[ib], p->kk_count[ib], p->rows_per_cta, p->csplit, ws));

@@ -382,7 +382,7 @@ k_contract(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, int M, i
 // One CTA per (job, lag u_y); FP32 per-thread partial sums over rows, FP64 block sums.
 template <typename T, int DM>
 __global__ void __launch_bounds__(256)
-k_contract_slot0(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, int M, int Nf, int L) {
+k_contract_slot0(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, int M, int Nf, int L, int rs) {
   using T2 = c_t<T>;
   constexpr int NMONO = n_mono(DM);
   __shared__ double red[8][2 * NMONO];
@@ -402,7 +402,7 @@ k_contract_slot0(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, in
   for (int m = 0; m < NMONO; ++m) { dc[m] = 0; nq[m] = 0; }
   for (int y = w + (int)threadIdx.x; y < H - w; y += blockDim.x) {
     if (!rowflag[y]) continue;
-    const T2 p = P[(int64_t)(y - uy) * M];
+    const T2 p = P[(int64_t)(y - uy) * rs];   // slot 0 of row y - u_y (rs: row stride of the probe slab)
     const T yt = (T)y * ysc - (T)1;
 #pragma unroll
     for (int a = 0; a <= DM; ++a) {
@@ -459,7 +459,7 @@ static cudaError_t contract_T(const sfft_plan_s* p, int job0, int njobs, int row
     p->nlaunch += 1;
   }
   k_contract_slot0<T, DM><<<dim3(njobs, max_uy<T>()), 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, H, p->M,
-                                                                          p->Nf, L);
+                                                                          p->Nf, L, p->M);
   p->nlaunch += 1;
   return cudaGetLastError();
 }
@@ -468,9 +468,9 @@ cudaError_t launch_contract_slot0(const sfft_plan_s* p, int DM, int job0, int nj
   if (njobs <= 0) return cudaSuccess;
   const dim3 grid(njobs, max_uy<float>());
   switch (DM) {
-    case 0: k_contract_slot0<float, 0><<<grid, 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, p->d.H, p->M, p->Nf, p->d.L); break;
-    case 2: k_contract_slot0<float, 2><<<grid, 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, p->d.H, p->M, p->Nf, p->d.L); break;
-    case 4: k_contract_slot0<float, 4><<<grid, 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, p->d.H, p->M, p->Nf, p->d.L); break;
+    case 0: k_contract_slot0<float, 0><<<grid, 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, p->d.H, p->M, p->Nf, p->d.L, p->dl ? 8 : p->M); break;
+    case 2: k_contract_slot0<float, 2><<<grid, 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, p->d.H, p->M, p->Nf, p->d.L, p->dl ? 8 : p->M); break;
+    case 4: k_contract_slot0<float, 4><<<grid, 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, p->d.H, p->M, p->Nf, p->d.L, p->dl ? 8 : p->M); break;
     default: return cudaErrorInvalidValue;
   }
   p->nlaunch += 1;

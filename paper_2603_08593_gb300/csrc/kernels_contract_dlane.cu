@@ -1,0 +1,457 @@
+// Lag contraction of the product spectra on the tcgen05 tensor cores with one
+// tensor-memory lane per offset difference (FP32 path, KK block).
+//
+// For one k-slot the y sum
+//   C[d][u_y][(m, Re|Im)] = sum_y conj(W_m(y)) P^_d(y - u_y)
+//                         = sum_{y'} P^_d(y') conj(W_m(y' + u_y))
+// is, for each u_y, a real matrix product whose rows are the differences d
+// of a tile (128 lanes), whose columns are the monomials (Re 0..15, Im
+// 16..31) and whose inner dimension runs over the rows y' and (re, im).  The
+// A operand (the probe rows) is the same for every u_y; only the weight rows
+// shift.  So each probe value is split and stored to tensor memory once, and
+// each u_y reads the B operand from a strip of weight rows at its own start:
+// the strips hold two rows per 16-byte core-matrix column, one strip for
+// each row parity, so that every start falls on a column.  The products are
+// split as in kernels_contract_umma.cu (hi_x hi_y on kind::tf32, K = 8 = four
+// rows, plus bf16(hi_x) bf16(lo_y) + bf16(lo_x) bf16(y) on kind::f16, K = 16;
+// Ootomo and Yokota, 2022), with the BF16 inner order (row pair, row parity,
+// hi/lo part, re/im) so that a row pair is one 16-byte column there too.
+//
+// A CTA takes two adjacent k-slots and up to NU consecutive u_y of one tile
+// over all weight rows of the band; its 2 x NU accumulators (32 FP32 columns
+// each) stay in tensor memory and go to an HBM buffer C[k][d][u_y][32] at the
+// end.  k_lag_dft then forms the lags u_x of every (d, u_y) pair, summing the
+// k-slots in FP32 runs of 32 and FP64 across runs.
+//
+// Roles (320 threads, one CTA per SM):
+//   warps 0-3  A producers: lane l of warp w is difference 32 w + l of the
+//              tile (tensor-memory lane 32 w + l); per k-step (four rows y')
+//              one 16-byte load per row gives both k-slots' probe values,
+//              split into 2 x 16 A columns (tcgen05.st); then the epilogue;
+//   warps 4-7  B producers: the four strips (TF32 and BF16, two parities) of
+//              both k-slots for each staged chunk of 16 rows y';
+//   warp 8     MMA issuer: per k-step 2 x nu x (TF32 + BF16) MMAs;
+//   warp 9     copy producer: per chunk one tensor-map box of probe rows
+//              (128 differences x 17 rows x 2 slots, from the k-slot-blocked
+//              product spectra [d][k / 8][y][k % 8]) and one box of weight
+//              rows per exponent.
+// Every wait is bounded; a wait that gives up flags the CCD (status bit 4)
+// and makes every role leave its loop, after which the issued copies and
+// MMAs are drained (bounded) and the tensor memory is freed.
+#include <cuda.h>
+
+#include "bulk.cuh"
+#include "common.cuh"
+#include "plan.h"
+#include "umma_common.cuh"
+
+namespace sfft {
+
+namespace {
+
+constexpr int CH = kDlChunk;          // rows y' per staged chunk
+constexpr int KSC = CH / 4;           // k-steps per chunk
+constexpr int NU = kDlMaxU;           // u_y per CTA at most
+constexpr int GA = 4;                 // k-steps of A operands in flight
+constexpr int PBR = CH + 1;           // probe rows per box: a spare row staggers the lanes' banks
+constexpr int PBYTES = 128 * PBR * 16;
+constexpr int VR = CH + NU;           // weight rows per box (CH + NU - 1 used)
+constexpr int VSLOT = (VR * 16 + 127) / 128 * 128;
+constexpr int NQ = (4 * (KSC - 1) + NU - 1) / 2 + 2;   // 16-byte columns (row pairs) per strip
+constexpr int SBO = NQ * 128 + 16;    // bytes between the strips' 8-row groups (16 more to shift banks)
+constexpr int STRIP = 4 * SBO;        // 32 rows n
+constexpr int WARP_MMA = 8, WARP_COPY = 9;
+constexpr int NTHREADS = 32 * 10;
+constexpr int TMEM_COLS = 512;        // D: 2 x NU x 32 columns, A: GA x 32 columns
+static_assert(2 * NU * 32 + GA * 32 <= TMEM_COLS, "tensor memory budget");
+static_assert(CH % 4 == 0 && VR % 2 == 0, "chunk geometry");
+
+struct DStage {
+  uint8_t P[PBYTES];                       // [difference][row y'][2 slots]
+  uint8_t V[kMaxWeightDeg + 1][VSLOT];     // per exponent a: [row][2 slots]
+  float ypw[VR][16];                       // yt^b of the weight rows (pairs (yt^b, yt^b), b = 0..4)
+};
+static_assert(PBYTES % 128 == 0 && sizeof(DStage) % 128 == 0, "tensor copy alignment");
+
+struct DSmem {
+  DStage st[2];
+  uint8_t strip[2][2][4][STRIP];   // [stage][slot][TF32 even, TF32 odd, BF16 even, BF16 odd]
+  uint64_t raw_full[2], raw_empty[2], strip_full[2], strip_empty[2];
+  uint64_t a_full[GA], a_empty[GA], done;
+  uint32_t tmem_base;
+  int abort;
+};
+
+}  // namespace
+
+template <int DM>
+__global__ void __launch_bounds__(NTHREADS, 1)
+k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmV,
+                 const DlJob* __restrict__ jobs, char* __restrict__ ws, int H, int L, int dstride, int pz,
+                 const float* __restrict__ ytab) {
+  constexpr int NMONO = n_mono(DM);
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  DSmem& S = *reinterpret_cast<DSmem*>(smem_raw);
+  volatile int* abort = &S.abort;
+
+  // grid (job within the CCD, slot pair, CCD): the CTAs of one k-slot block
+  // (four slot pairs) and of both u_y runs of a tile run side by side and
+  // share the block rows in L2
+  const DlJob job = jobs[blockIdx.z * gridDim.x + blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = (L - 1) / 2;
+  const int k0 = 2 * blockIdx.y;
+  const int y0 = w, y1 = H - w;                 // weight rows of the band (M_fit vanishes within w of the edges)
+  const int ulo = job.u_lo, nu = job.nu;
+  const int Ys = y0 - (ulo + nu - 1);           // first row y' any u_y of the CTA needs
+  const int nchunk = y1 > y0 ? (y1 - ulo - Ys + CH - 1) / CH : 0;
+  const int nstep = nchunk * KSC;
+  // ---- setup: zeroed stages (lanes past the tile read zeros), barriers, tensor memory
+  for (int i = threadIdx.x; i < (int)(sizeof(DStage) * 2 / 16); i += NTHREADS)
+    reinterpret_cast<float4*>(&S.st[0])[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&S.raw_full[i], 1);
+      mbar_init(&S.raw_empty[i], 8);
+      mbar_init(&S.strip_full[i], 4);
+      mbar_init(&S.strip_empty[i], 1);
+    }
+    for (int i = 0; i < GA; ++i) { mbar_init(&S.a_full[i], 4); mbar_init(&S.a_empty[i], 1); }
+    mbar_init(&S.done, 1);
+    S.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
+                 "n"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = S.tmem_base;
+  const uint32_t t_d = tbase;                  // accumulators: (slot s, u index i) at columns 32 (NU s + i)
+  const uint32_t t_a = tbase + 2 * NU * 32;    // A: k-step slot g at columns 32 g + 16 s (TF32 0-7, BF16 8-15)
+
+  int issued_chunks = 0;   // copy warp: chunks whose copies were issued
+
+  if (warp == WARP_COPY) {
+    for (int c = 0; c < nchunk; ++c) {
+      const int sidx = c & 1;
+      if (c >= 2 && !wait_phase(&S.raw_empty[sidx], (unsigned)(((c >> 1) - 1) & 1), abort)) break;
+      DStage& st = S.st[sidx];
+      const int yc = Ys + c * CH;
+      // powers of yt for the weight rows inside the image (the others are masked)
+      const int ylo = max(yc + ulo, 0), yhi = min(yc + ulo + VR, H);
+      const unsigned ybytes = yhi > ylo ? (unsigned)(yhi - ylo) * 64u : 0u;
+      if (lane == 0)
+        mbar_arrive_expect_tx(&S.raw_full[sidx], (unsigned)(pz * PBR * 16 + (DM + 1) * VR * 16) + ybytes);
+      __syncwarp();
+      if (lane == 0) {
+        tma_load_4d(&st.P[0], &tmP, 2 * (k0 & 7), yc, k0 >> 3, job.zp + job.d_first, &S.raw_full[sidx]);
+      } else if (lane <= DM + 1) {
+        const int a = lane - 1;
+        tma_load_3d(&st.V[a][0], &tmV, 2 * k0, yc + ulo, job.zw + a, &S.raw_full[sidx]);
+      } else if (lane == 31 && ybytes > 0) {
+        bulk_copy_g2s(&st.ypw[ylo - (yc + ulo)][0], ytab + (int64_t)ylo * 16, ybytes, &S.raw_full[sidx]);
+      }
+      issued_chunks = c + 1;
+      __syncwarp();
+    }
+  } else if (warp == WARP_MMA) {
+    constexpr uint32_t id_tf32 = instr_desc(2), id_bf16 = instr_desc(1);
+    // descriptor of a strip start: the address field (bits 0-13, 16-byte units)
+    // advances by 8 per 128-byte row pair
+    const uint64_t dstrip0 = smem_desc(smem_u32(&S.strip[0][0][0][0]), SBO);
+    for (int c = 0; c < nchunk && !*abort; ++c) {
+      const int sidx = c & 1;
+      if (!wait_phase(&S.strip_full[sidx], (unsigned)((c >> 1) & 1), abort)) break;
+      bool live = true;
+      for (int j = 0; j < KSC; ++j) {
+        const int g = c * KSC + j, as = g % GA;
+        if (!wait_phase(&S.a_full[as], (unsigned)((g / GA) & 1), abort)) { live = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (elect_one()) {
+#pragma unroll
+          for (int s = 0; s < 2; ++s) {
+#pragma unroll
+            for (int i = 0; i < NU; ++i) {
+              if (i >= nu) break;
+              const int o = 4 * j + i, par = o & 1, qc = (o - par) >> 1;   // strip row of the step's first weight row
+              const uint32_t dcol = t_d + 32 * (NU * s + i), acol = t_a + 32 * as + 16 * s;
+              const uint64_t bt = dstrip0 + (uint64_t)((((sidx * 2 + s) * 4 + par) * STRIP + qc * 128) >> 4);
+              const uint64_t bb = dstrip0 + (uint64_t)((((sidx * 2 + s) * 4 + 2 + par) * STRIP + qc * 128) >> 4);
+              const uint32_t acc = g > 0 ? 1u : 0u;
+              asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                           " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n"
+                           ::"r"(dcol), "r"(acol), "l"(bt), "r"(id_tf32), "r"(acc) : "memory");
+              asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                           " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n"
+                           ::"r"(dcol), "r"(acol + 8), "l"(bb), "r"(id_bf16), "r"(1u) : "memory");
+            }
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                       ::"r"(smem_u32(&S.a_empty[as])) : "memory");
+        }
+        __syncwarp();
+      }
+      if (!live) break;
+      if (elect_one())
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     ::"r"(smem_u32(&S.strip_empty[sidx])) : "memory");
+      __syncwarp();
+    }
+    // every MMA issued so far completes before the accumulators are read or freed
+    if (elect_one())
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   ::"r"(smem_u32(&S.done)) : "memory");
+    __syncwarp();
+    for (int it = 0; it < kMaxSpin && !mbar_try_wait(&S.done, 0); ++it) {
+    }
+  } else if (warp < 4) {
+    // ---- A producers
+    const int q = 32 * warp + lane;
+    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+    for (int c = 0; c < nchunk && !*abort; ++c) {
+      const int sidx = c & 1;
+      if (!wait_phase(&S.raw_full[sidx], (unsigned)((c >> 1) & 1), abort)) break;
+      const uint8_t* P = &S.st[sidx].P[q * PBR * 16];
+      for (int j = 0; j < KSC; ++j) {
+        const int g = c * KSC + j, as = g % GA;
+        if (g >= GA && !wait_phase(&S.a_empty[as], (unsigned)(((g / GA) - 1) & 1), abort)) break;
+        uint32_t v[2][16];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const float4 pv = *reinterpret_cast<const float4*>(P + (4 * j + r) * 16);
+          const float px[2] = {pv.x, pv.z}, py[2] = {pv.y, pv.w};
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const float hr = tf32_trunc(px[h]), hi = tf32_trunc(py[h]);
+            v[h][2 * r] = __float_as_uint(hr);                      // TF32: k = 2 r + (re, im)
+            v[h][2 * r + 1] = __float_as_uint(hi);
+            v[h][8 + 2 * r] = pack_bf16(hr, hi);                    // BF16 pair 2 r: hi(P) of row r
+            v[h][9 + 2 * r] = pack_bf16(px[h] - hr, py[h] - hi);    // BF16 pair 2 r + 1: lo(P) of row r
+          }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                       "%12, %13, %14, %15, %16};"
+                       ::"r"(t_a + 32 * as + 16 * h + lane_off), "r"(v[h][0]), "r"(v[h][1]), "r"(v[h][2]),
+                         "r"(v[h][3]), "r"(v[h][4]), "r"(v[h][5]), "r"(v[h][6]), "r"(v[h][7]), "r"(v[h][8]),
+                         "r"(v[h][9]), "r"(v[h][10]), "r"(v[h][11]), "r"(v[h][12]), "r"(v[h][13]), "r"(v[h][14]),
+                         "r"(v[h][15]) : "memory");
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.a_full[as]);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.raw_empty[sidx]);
+    }
+  } else if (warp < 8) {
+    // ---- B producers: thread (monomial m, slot s, first row r0) writes
+    // W_m(y) for y = yc + u_lo + s_row, s_row = r0, r0 + 4, ..., into the
+    // rows n = m (Re) and 16 + m (Im) of both parities' strips.  TF32 strip element (n, k) at
+    // (n / 8) SBO + (k / 4) 128 + (n % 8) 16 + (k % 4) 4 with k = 2 (row % 2)
+    // + (re, im) inside the row pair k / 4; the BF16 strip holds per (n, row)
+    // four values (hi(P)-part re, im: lo(W); lo(P)-part re, im: W) at
+    // (row % 2) 8 bytes of the same 16-byte column.
+    const int bt = threadIdx.x - 128;
+    const int m = bt & 15, s = (bt >> 4) & 1, r0 = bt >> 5;   // strip rows r0, r0 + 4, ... of each chunk
+    int am = 0, bm = 0;
+    mono_ab(m < NMONO ? m : 0, am, bm);
+    const bool live = m < NMONO;
+    const int nre = (m / 8) * SBO + (m % 8) * 16, nim = ((16 + m) / 8) * SBO + (m % 8) * 16;
+    for (int c = 0; c < nchunk && !*abort; ++c) {
+      const int sidx = c & 1;
+      if (!wait_phase(&S.raw_full[sidx], (unsigned)((c >> 1) & 1), abort)) break;
+      if (c >= 2 && !wait_phase(&S.strip_empty[sidx], (unsigned)(((c >> 1) - 1) & 1), abort)) break;
+      const DStage& st = S.st[sidx];
+      const int ybase = Ys + c * CH + ulo;
+      uint8_t* tf0 = &S.strip[sidx][s][0][0];
+      uint8_t* bf0 = &S.strip[sidx][s][2][0];
+#pragma unroll 2
+      for (int srow = r0; srow < VR - 1; srow += 4) {
+        const int y = ybase + srow;
+        const bool on = live && y >= y0 && y < y1;
+        const float2 vv = *reinterpret_cast<const float2*>(&st.V[am][srow * 16 + s * 8]);
+        const float yp = st.ypw[srow][2 * bm];
+        const float wr = on ? yp * vv.x : 0.f, wi = on ? yp * vv.y : 0.f;
+        const float hr = tf32_trunc(wr), hi = tf32_trunc(wi);
+        const float lr = wr - hr, li = wi - hi;
+        const float2 tre = make_float2(hr, hi), tim = make_float2(-hi, hr);
+        const uint2 bre = make_uint2(pack_bf16(lr, li), pack_bf16(wr, wi));
+        const uint2 bim = make_uint2(pack_bf16(-li, lr), pack_bf16(-wi, wr));
+#pragma unroll
+        for (int par = 0; par < 2; ++par) {
+          const int rr = srow - par;
+          if (rr < 0 || (rr >> 1) >= NQ) continue;
+          const int off = (rr >> 1) * 128 + (rr & 1) * 8 + par * STRIP;
+          *reinterpret_cast<float2*>(tf0 + nre + off) = tre;
+          *reinterpret_cast<float2*>(tf0 + nim + off) = tim;
+          *reinterpret_cast<uint2*>(bf0 + nre + off) = bre;
+          *reinterpret_cast<uint2*>(bf0 + nim + off) = bim;
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&S.strip_full[sidx]);
+        mbar_arrive(&S.raw_empty[sidx]);
+      }
+    }
+  }
+
+  // ---- drain: the copies of the last two chunks issued land before the
+  // stages are reused (earlier phases of a stage report complete at once)
+  if (warp == WARP_COPY)
+    for (int c = issued_chunks - 2; c < issued_chunks; ++c) {
+      if (c < 0) continue;
+      for (int it = 0; it < kMaxSpin && !mbar_try_wait(&S.raw_full[c & 1], (unsigned)((c >> 1) & 1)); ++it) {
+      }
+    }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const bool ok = nstep > 0 && !S.abort && mbar_try_wait(&S.done, 0);
+  if (threadIdx.x == 0 && !ok) atomicOr(reinterpret_cast<int*>(ws + job.status), 4);
+
+  // ---- epilogue: the accumulators of lane q (difference d_first + q) to C[k][d][u_y][32]
+  if (ok && warp < 4) {
+    const int q = 32 * warp + lane;
+    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+    float* cb = reinterpret_cast<float*>(ws + job.cbuf);
+    for (int s = 0; s < 2; ++s)
+      for (int i = 0; i < nu; ++i) {
+        uint32_t c[32];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                     "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+                     "[%32];"
+                     : "=r"(c[0]), "=r"(c[1]), "=r"(c[2]), "=r"(c[3]), "=r"(c[4]), "=r"(c[5]), "=r"(c[6]), "=r"(c[7]),
+                       "=r"(c[8]), "=r"(c[9]), "=r"(c[10]), "=r"(c[11]), "=r"(c[12]), "=r"(c[13]), "=r"(c[14]),
+                       "=r"(c[15]), "=r"(c[16]), "=r"(c[17]), "=r"(c[18]), "=r"(c[19]), "=r"(c[20]), "=r"(c[21]),
+                       "=r"(c[22]), "=r"(c[23]), "=r"(c[24]), "=r"(c[25]), "=r"(c[26]), "=r"(c[27]), "=r"(c[28]),
+                       "=r"(c[29]), "=r"(c[30]), "=r"(c[31])
+                     : "r"(t_d + 32 * (NU * s + i) + lane_off));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (q < job.nlanes) {
+          float4* o = reinterpret_cast<float4*>(
+              cb + (((int64_t)(k0 + s) * dstride + job.d_first + q) * L + (ulo + i + w)) * 32);
+#pragma unroll
+          for (int t = 0; t < 8; ++t)
+            o[t] = make_float4(__uint_as_float(c[4 * t]), __uint_as_float(c[4 * t + 1]), __uint_as_float(c[4 * t + 2]),
+                               __uint_as_float(c[4 * t + 3]));
+        }
+      }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "n"(TMEM_COLS) : "memory");
+}
+
+// Lags u_x of the k-slot products: for pair (d, u_y) of the difference batch,
+// G[d][u_y][u_x][m] += (1/N_f) sum_{k=1}^{M-1} (C_Re 2 cos(2 pi k u_x / N_f)
+// + C_Im 2 sin(2 pi k u_x / N_f)); slot 0 (the packed real bins) is summed by
+// k_contract_slot0.  Thread (m, g) takes the k-slots k = 1 + g (mod 16) for
+// every u_x (cos is even and sin odd in u_x), in FP32 runs of 16 slots added
+// to FP64; the 16 groups are then summed in FP64 in a fixed order.
+template <int DM>
+__global__ void __launch_bounds__(256)
+k_lag_dft(const int4* __restrict__ pairs, const char* __restrict__ cbuf0, size_t cbuf_ccd, double* __restrict__ g0,
+          size_t g_ccd, int M, int Nf, int L, int dstride, const float2* __restrict__ twD) {
+  constexpr int NMONO = n_mono(DM);
+  constexpr int NG = 16, W5 = (kMaxL - 1) / 2;
+  __shared__ double red[NG][16][kMaxL];
+  const int4 pq = pairs[blockIdx.x];
+  const int ccd = blockIdx.y, w = (L - 1) / 2;
+  const int m = threadIdx.x & 15, grp = threadIdx.x >> 4;
+  const float* C = reinterpret_cast<const float*>(cbuf0 + (size_t)ccd * cbuf_ccd) +
+                   ((int64_t)pq.x * L + (pq.y + w)) * 32;
+  const int64_t kstride = (int64_t)dstride * L * 32;
+  double sp[W5 + 1], sn[W5 + 1];   // u_x = +v and -v
+  float fp[W5 + 1], fn[W5 + 1];
+#pragma unroll
+  for (int v = 0; v <= W5; ++v) { sp[v] = sn[v] = 0.0; fp[v] = fn[v] = 0.f; }
+  int run = 0;
+  for (int k = 1 + grp; k < M; k += NG) {
+    const float* ck = C + k * kstride;
+    const float cr = __ldg(ck + m), ci = __ldg(ck + 16 + m);
+#pragma unroll
+    for (int v = 0; v <= W5; ++v) {
+      if (v > w) break;
+      const float2 t = __ldg(twD + ((k * v) & (Nf - 1)));
+      const float a = cr * t.x, b = ci * t.y;
+      fp[v] += 2.f * (a + b);
+      fn[v] += 2.f * (a - b);
+    }
+    if (++run == 16) {
+#pragma unroll
+      for (int v = 0; v <= W5; ++v) { sp[v] += fp[v]; sn[v] += fn[v]; fp[v] = fn[v] = 0.f; }
+      run = 0;
+    }
+  }
+#pragma unroll
+  for (int v = 0; v <= W5; ++v) {
+    sp[v] += fp[v];
+    sn[v] += fn[v];
+    if (v <= w) {
+      red[grp][m][w + v] = sp[v];
+      red[grp][m][w - v] = sn[v];   // u_x = 0 writes the same value twice
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 16 * L; t += blockDim.x) {
+    const int mm = t % 16, xi = t / 16, ux = xi - w;
+    if (mm >= NMONO || ux < pq.z || ux > pq.w) continue;
+    double s = 0.0;
+    for (int g = 0; g < NG; ++g) s += red[g][mm][xi];
+    g0[(size_t)ccd * g_ccd + (((int64_t)pq.x * L + (pq.y + w)) * L + xi) * NMONO + mm] += s / (double)Nf;
+  }
+}
+
+template <int DM>
+static cudaError_t contract_dlane_dm(const sfft_plan_s* p, int batch_index, void* ws) {
+  const int job0 = p->dl_first[batch_index], njobs = p->dl_count[batch_index];
+  const int pair0 = p->dlp_first[batch_index], npair = p->dlp_count[batch_index];
+  const int H = p->d.H, L = p->d.L, B = p->d.batch;
+  const size_t smem = sizeof(DSmem);
+  auto kern = k_contract_dlane<DM>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int ntot = p->d_batch * B;
+  const int pz = std::min(128, ntot);   // differences per probe box
+  CUtensorMap mp, mv;
+  char* base = static_cast<char*>(ws);
+  if (!make_map_blk(&mp, base + p->phat.off, p->M, H, ntot, 4, PBR, pz) ||
+      !make_map(&mv, base + p->wspec.off, p->M, H, p->n_wa * B, 4, VR, 1))
+    return cudaErrorInvalidValue;
+  if (njobs > 0) {
+    const int per_ccd = njobs / B;   // jobs are ordered CCD-major, the same count per CCD
+    dim3 grid(per_ccd, p->M / 2, B);
+    kern<<<grid, NTHREADS, smem, p->stream>>>(mp, mv, p->d_dljobs + job0, (char*)ws, H, L, p->d_batch, pz,
+                                              (const float*)p->ytab);
+    p->nlaunch += 1;
+  }
+  if (npair > 0) {
+    const size_t cbuf_ccd = (size_t)p->M * p->d_batch * L * 32 * sizeof(float);
+    const size_t g_ccd = (size_t)p->n_hd * L * L * n_mono(DM);
+    double* g0 = ws_at<double>(ws, p->gkk) + (size_t)batch_index * p->d_batch * L * L * n_mono(DM);
+    dim3 grid(npair, B);
+    k_lag_dft<DM><<<grid, 256, 0, p->stream>>>(p->d_dlpairs + pair0, base + p->cbuf.off, cbuf_ccd, g0, g_ccd, p->M,
+                                               p->Nf, L, p->d_batch, (const float2*)p->twD);
+    p->nlaunch += 1;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_contract_dlane(const sfft_plan_s* p, int batch_index, void* ws) {
+  switch (p->DM_KK) {
+    case 0: return contract_dlane_dm<0>(p, batch_index, ws);
+    case 2: return contract_dlane_dm<2>(p, batch_index, ws);
+    case 4: return contract_dlane_dm<4>(p, batch_index, ws);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace sfft

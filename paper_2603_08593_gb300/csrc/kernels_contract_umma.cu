@@ -44,6 +44,7 @@
 #include "bulk.cuh"
 #include "common.cuh"
 #include "plan.h"
+#include "umma_common.cuh"
 
 namespace sfft {
 
@@ -89,63 +90,6 @@ struct USmem {
   uint32_t tmem_base;
   int abort;
 };
-
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-  // canonical K-major layout without swizzle: core matrices of 8 rows x 16
-  // bytes, 128 bytes apart along K (leading byte offset) and 256 bytes apart
-  // along the 8-row groups (stride byte offset); descriptor version 1
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)(128u >> 4) << 16;
-  d |= (uint64_t)(256u >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;
-}
-
-// instruction descriptor: D FP32, A and B of format `fmt` (1 = BF16 for
-// kind::f16, 2 = TF32 for kind::tf32), both K-major, M = 128, N = 32
-__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
-}
-
-// tiled tensor copy of a 3-D box (x innermost) into shared memory, counted on `bar`
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ bool elect_one() {
-  uint32_t pred = 0;
-  asm volatile("{\n .reg .pred P;\n elect.sync _|P, 0xffffffff;\n selp.u32 %0, 1, 0, P;\n}\n" : "=r"(pred));
-  return pred != 0;
-}
-
-__device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  uint32_t r;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-  return r;
-}
-
-__device__ __forceinline__ void mono_ab(int m, int& a, int& b) {
-  int n = 0;
-  while ((n + 1) * (n + 2) / 2 <= m) ++n;
-  b = m - n * (n + 1) / 2;
-  a = n - b;
-}
-
-// Bounded wait on a phase; gives up when the spin budget runs out or another
-// role has given up, and then raises the shared abort flag.
-__device__ __forceinline__ bool wait_phase(uint64_t* bar, unsigned parity, volatile int* abort) {
-  for (int it = 0; it < kMaxSpin; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 63) == 63 && *abort) return false;
-  }
-  *abort = 1;
-  return false;
-}
 
 }  // namespace
 
@@ -434,36 +378,6 @@ k_contract_umma(const __grid_constant__ CUtensorMap tmP, const __grid_constant__
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "n"(TMEM_COLS) : "memory");
 }
 
-using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiled encode_fn() {
-  static EncodeTiled fn = nullptr;
-  if (!fn) {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q{};
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiled>(f);
-  }
-  return fn;
-}
-
-// 3-D FP32 view (x: 2 M floats of one spectrum row, y: rows, z: spectra) of
-// `n` consecutive row spectra, with boxes of BOXW x rows x 1
-static bool make_map(CUtensorMap* m, void* base, int M, int H, int n, int rows) {
-  EncodeTiled fn = encode_fn();
-  if (!fn) return false;
-  const cuuint64_t dims[3] = {(cuuint64_t)2 * M, (cuuint64_t)H, (cuuint64_t)n};
-  const cuuint64_t strides[2] = {(cuuint64_t)2 * M * 4, (cuuint64_t)H * 2 * M * 4};
-  const cuuint32_t box[3] = {(cuuint32_t)BOXW, (cuuint32_t)rows, 1};
-  const cuuint32_t es[3] = {1, 1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
-         CUDA_SUCCESS;
-}
-
 template <int DM>
 static cudaError_t contract_umma_dm(const sfft_plan_s* p, int job0, int njobs, void* ws) {
   const size_t smem = sizeof(USmem);
@@ -479,8 +393,8 @@ static cudaError_t contract_umma_dm(const sfft_plan_s* p, int job0, int njobs, v
   // job names its CCD's first slab
   CUtensorMap mp, mv;
   char* base = static_cast<char*>(ws);
-  if (!make_map(&mp, base + p->phat.off, p->M, H, p->d_batch * B, rbox) ||
-      !make_map(&mv, base + p->wspec.off, p->M, H, p->n_wa * B, CH))
+  if (!make_map(&mp, base + p->phat.off, p->M, H, p->d_batch * B, BOXW, rbox, 1) ||
+      !make_map(&mv, base + p->wspec.off, p->M, H, p->n_wa * B, BOXW, CH, 1))
     return cudaErrorInvalidValue;
   for (int j0 = 0; j0 < njobs; j0 += 65535) {
     dim3 grid(p->M / KT, std::min(65535, njobs - j0), nb);

@@ -72,8 +72,11 @@ struct RowFFT {
   }
 
   // v[r] = z[t + TPR r] (the first pass's inputs, radix 16, span 1) -> spectrum row `out`
+  // (X[k] is stored at out[k], or with BLK at out[(k / 8) kb + k % 8] for the
+  // k-slot-blocked product spectra, kb = 8 H)
+  template <bool BLK = false>
   __device__ static void run(T2 (&v)[16], T2* buf, int t, bool valid, const T2* __restrict__ twM,
-                             const T2* __restrict__ twN, T2* __restrict__ out) {
+                             const T2* __restrict__ twN, T2* __restrict__ out, int kb = 0) {
     // first pass straight from registers
     fft_reg<16>(v);
 #pragma unroll
@@ -99,7 +102,8 @@ struct RowFFT {
           X.x = er + wi;
           X.y = ei - wr;
         }
-        out[k] = X;
+        if constexpr (BLK) out[(k >> 3) * kb + (k & 7)] = X;
+        else out[k] = X;
       }
     }
     __syncthreads();
@@ -150,7 +154,7 @@ k_rfft_prod(const T* __restrict__ Rm, int H, int W, const int2* __restrict__ dl,
 // 16 on each side for the d_x shift), then forms RPB products at a time -- one
 // per d_x of this d_y in the batch -- and transforms them side by side.
 // grid = (H, number of d_y values met by the batch [d0, d0 + nd), batch).
-template <typename T, int M>
+template <typename T, int M, bool BLK>
 __global__ void __launch_bounds__(kFftThreads)
 k_rfft_prod_dy(const T* __restrict__ Rm, int H, int W, int L, int d0, int nd, c_t<T>* __restrict__ out,
                int64_t slab_stride, int64_t ccd_stride_out, const c_t<T>* __restrict__ twM,
@@ -179,7 +183,7 @@ k_rfft_prod_dy(const T* __restrict__ Rm, int H, int W, int L, int d0, int nd, c_
   }
   __syncthreads();
   const int dx0 = dy == 0 ? 0 : -(L - 1);
-  c_t<T>* obase = out + (int64_t)ccd * ccd_stride_out + (int64_t)y * M;
+  c_t<T>* obase = out + (int64_t)ccd * ccd_stride_out + (int64_t)y * (BLK ? 8 : M);
   for (int id0 = lo; id0 < hi; id0 += F::RPB) {
     const int id = id0 + rloc;
     const bool valid = id < hi;
@@ -192,7 +196,7 @@ k_rfft_prod_dy(const T* __restrict__ Rm, int H, int W, int L, int d0, int nd, c_
       v[r].x = valid ? r1[x0] * r2[x0 + dx + PADX] : (T)0;
       v[r].y = valid ? r1[x0 + 1] * r2[x0 + 1 + dx + PADX] : (T)0;
     }
-    F::run(v, buf, t, valid, twM, twN, obase + (int64_t)(valid ? id - d0 : 0) * slab_stride);
+    F::template run<BLK>(v, buf, t, valid, twM, twN, obase + (int64_t)(valid ? id - d0 : 0) * slab_stride, 8 * H);
   }
 }
 
@@ -207,6 +211,7 @@ k_rfft_prod_dy(const T* __restrict__ Rm, int H, int W, int L, int d0, int nd, c_
 // d_x values of the group in turns.
 constexpr int kWarpRowsPerCta = 4;
 
+template <bool BLK>
 __global__ void __launch_bounds__(256, 2)
 k_rfft_prod_dy_w(const float* __restrict__ Rm, int H, int W, int L, int d0, int nd, float2* __restrict__ out,
                  int64_t slab_stride, int64_t ccd_stride_out, const float2* __restrict__ twM,
@@ -243,7 +248,7 @@ k_rfft_prod_dy_w(const float* __restrict__ Rm, int H, int W, int L, int d0, int 
       r2[x] = (ok2 && gx >= 0 && gx < W) ? img[(int64_t)(y + dy) * W + gx] : 0.f;
     }
     __syncthreads();
-    float2* orow = out + (int64_t)ccd * ccd_stride_out + (int64_t)y * M;
+    float2* orow = out + (int64_t)ccd * ccd_stride_out + (int64_t)y * (BLK ? 8 : M);
     for (int id = lo + warp; id < hi; id += 8) {
       const int dx = dx0 + (id - first_of(dy));
       float2 v[32];
@@ -289,7 +294,8 @@ k_rfft_prod_dy_w(const float* __restrict__ Rm, int H, int W, int L, int d0, int 
           X.x = er + wi;
           X.y = ei - wr;
         }
-        o[k] = X;
+        if constexpr (BLK) o[(int64_t)(k >> 3) * (8 * H) + (k & 7)] = X;   // [k / 8][y][k % 8]
+        else o[k] = X;
       }
       __syncwarp();
     }
@@ -384,7 +390,9 @@ static cudaError_t run_prod_dy(const sfft_plan_s* p, const T* Rm, int d0, int nd
                                int64_t ccd_stride) {
   using F = RowFFT<T, M>;
   const size_t smem = F::smem_bytes() + sizeof(T) * (size_t)(2 * (2 * M) + 32);
-  auto kern = k_rfft_prod_dy<T, M>;
+  // product spectra [d][y][k], or k-slot-blocked [d][k / 8][y][k % 8] for the
+  // lane-per-difference contraction
+  auto kern = p->dl ? k_rfft_prod_dy<T, M, true> : k_rfft_prod_dy<T, M, false>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int L = p->d.L;
   auto dy_of = [L](int id) { return id < L ? 0 : 1 + (id - L) / (2 * L - 1); };
@@ -400,13 +408,14 @@ static cudaError_t run_prod_dy_w(const sfft_plan_s* p, const float* Rm, int d0, 
                                  int64_t slab_stride, int64_t ccd_stride) {
   constexpr int NF = 2048;
   const size_t smem = sizeof(float) * (size_t)(2 * NF + 32) + sizeof(float2) * 8 * 32 * 33;
-  cudaFuncSetAttribute(k_rfft_prod_dy_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = p->dl ? k_rfft_prod_dy_w<true> : k_rfft_prod_dy_w<false>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int L = p->d.L;
   auto dy_of = [L](int id) { return id < L ? 0 : 1 + (id - L) / (2 * L - 1); };
   const int ndy = dy_of(d0 + nd - 1) - dy_of(d0) + 1;
   dim3 grid((p->d.H + kWarpRowsPerCta - 1) / kWarpRowsPerCta, ndy, p->d.batch);
-  k_rfft_prod_dy_w<<<grid, 256, smem, p->stream>>>(Rm, p->d.H, p->d.W, L, d0, nd, out, slab_stride, ccd_stride,
-                                                    (const float2*)p->twM, (const float2*)p->twN);
+  kern<<<grid, 256, smem, p->stream>>>(Rm, p->d.H, p->d.W, L, d0, nd, out, slab_stride, ccd_stride,
+                                       (const float2*)p->twM, (const float2*)p->twN);
   p->nlaunch += 1;
   return cudaGetLastError();
 }

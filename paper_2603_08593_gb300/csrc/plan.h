@@ -43,6 +43,17 @@ constexpr int kUmmaKT = 8;
 constexpr int kUmmaChunk = 32;
 constexpr int kUmmaPairs = 128;
 constexpr int kUmmaMaxDiffs = 16;
+// tcgen05 kernel with one lane per difference (kernels_contract_dlane.cu):
+// one CTA per (two k-slots, tile of up to 128 differences, up to kDlMaxU
+// consecutive u_y); its accumulators go to C[k][d_local][u_y][32]
+struct DlJob {
+  int64_t cbuf, status;   // byte offsets: the CCD's C buffer of the d-batch, status
+  int zp, zw;             // the CCD's first product / weight spectrum in the batch-wide tensor maps
+  int d_first, nlanes;    // the tile: differences [d_first, d_first + nlanes) of the d-batch
+  int u_lo, nu;           // u_y = u_lo .. u_lo + nu - 1
+};
+constexpr int kDlChunk = 16;
+constexpr int kDlMaxU = 6;
 
 }  // namespace sfft
 
@@ -62,6 +73,7 @@ struct sfft_plan_s {
   int d_batch = 0, rows_per_cta = 0, csplit = 2;   // csplit: lag parts per (k-slot, group) in the contraction
   bool tc = false;                    // KK contraction on the tensor cores (FP32 path)
   bool umma = false;                  // ... with tcgen05 (else mma.sync)
+  bool dl = false;                    // ... with one tensor-memory lane per difference (else per (d, u_y) pair)
   int tc_rows = 0;                    // weight rows per CTA of the tensor-core contraction
   double tuned_ms = 0.0;              // autotuned build_normal time per CCD (0: not tuned)
   size_t elem = 4;                    // sizeof(T)
@@ -86,9 +98,15 @@ struct sfft_plan_s {
   sfft::TcJob* d_tcjobs = nullptr;
   int4* d_tcpairs = nullptr;
   int4* d_tcdj = nullptr;
+  // lane-per-difference engine: jobs and (d_local, u_y, ux_lo, ux_hi) pairs of d-batch i
+  std::vector<int> dl_first, dl_count, dlp_first, dlp_count;
+  std::vector<sfft::DlJob> h_dljobs;
+  std::vector<int4> h_dlpairs;
+  sfft::DlJob* d_dljobs = nullptr;
+  int4* d_dlpairs = nullptr;
   // workspace regions (per-CCD strides where noted)
   sfft::Region sky, skyacc, good, gh, mfit, rowflag, rm, wspec, uspec, rhat, phat, gkk, gkb, gbk,
-      mom_bb, mom_b, eimg, lfac, scale, dinv, gbar, swave, vec, theta_off, status;
+      mom_bb, mom_b, eimg, lfac, scale, dinv, gbar, swave, vec, theta_off, status, cbuf;
   size_t ws_bytes = 0;
   // graph cache for sfft_subtract
   std::map<std::vector<uintptr_t>, cudaGraphExec_t> graphs;
@@ -117,6 +135,7 @@ cudaError_t launch_contract(const sfft_plan_s* p, int DM, int job0, int njobs, i
                             void* ws);
 cudaError_t launch_contract_tc(const sfft_plan_s* p, int batch_index, void* ws);
 cudaError_t launch_contract_umma(const sfft_plan_s* p, int batch_index, void* ws);
+cudaError_t launch_contract_dlane(const sfft_plan_s* p, int batch_index, void* ws);
 cudaError_t launch_contract_slot0(const sfft_plan_s* p, int DM, int job0, int njobs, void* ws);
 cudaError_t launch_scatter(const sfft_plan_s* p, double* A, double* b, void* ws, bool rhs_only, double* rhs_out);
 cudaError_t launch_cholesky(const sfft_plan_s* p, const double* A, void* ws);

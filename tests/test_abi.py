@@ -60,6 +60,6 @@ def test_status_strings_and_arg_errors_without_gpu(built_lib):
         assert lib.sfft_plan(ctypes.byref(desc), None, ctypes.byref(h)) == binding.SFFT_ERR_UNSUPPORTED
     bad = binding.Desc(0, 64, 5, 1, 1, 1, 1, 0, 0, 0, 0)
     assert lib.sfft_plan(ctypes.byref(bad), None, ctypes.byref(h)) == binding.SFFT_ERR_ARG
-    unknown_flag = binding.Desc(64, 64, 5, 1, 1, 1, 1, 0, 0, 0, 0, 16)
+    unknown_flag = binding.Desc(64, 64, 5, 1, 1, 1, 1, 0, 0, 0, 0, 32)
     assert lib.sfft_plan(ctypes.byref(unknown_flag), None, ctypes.byref(h)) == binding.SFFT_ERR_ARG
     assert lib.sfft_build_normal(None, None, None, None, None, None, None, None) == binding.SFFT_ERR_ARG

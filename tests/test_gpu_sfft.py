@@ -86,11 +86,12 @@ def test_mixed_path_within_stated_error(shape, L, DK, DB):
     assert np.abs(D[0] - ref["D"]).max() <= 1e-3 * SIGMA_SKY
 
 
-@pytest.mark.parametrize("engine", ["fma_contract", "mma_sync_contract"])
+@pytest.mark.parametrize("engine", ["fma_contract", "mma_sync_contract", "pair_lane_contract"])
 @pytest.mark.parametrize("shape,L,DK,DB", [((150, 210), 7, 2, 2), ((96, 300), 11, 2, 2), ((48, 64), 3, 0, 0)])
 def test_mixed_path_other_contraction_engines(shape, L, DK, DB, engine):
-    """The KK contraction on the FP32 FMA pipes or through warp-level mma.sync
-    (tcgen05 is the default): same stated error bars."""
+    """The KK contraction on the FP32 FMA pipes, through warp-level mma.sync,
+    or on tcgen05 with one tensor-memory lane per (difference, u_y) pair (the
+    default takes one lane per difference): same stated error bars."""
     d = small_pair(*shape, seed=2300 + shape[1] + L, mask_fraction=0.03)
     refs, A, b, th, info, D = _run(d, L, DK, DB, "mixed", **{engine: True})
     ref = refs[0]
