@@ -428,7 +428,7 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
   p->umma = p->tc && !(d.flags & SFFT_FLAG_MMA_SYNC_CONTRACT);
   // one lane per difference needs two whole k-slots per CTA and difference
   // batches that fill most of the 128 lanes
-  p->dl = p->umma && !(d.flags & SFFT_FLAG_PAIR_LANE_CONTRACT) && p->M % 8 == 0 && d.H >= 32 &&
+  p->dl = p->umma && !(d.flags & SFFT_FLAG_PAIR_LANE_CONTRACT) && p->M % 16 == 0 && d.H >= 32 &&
           p->d_batch >= std::min(p->n_hd, 96);
   p->tc_rows = d.H;
   build_layout(p);

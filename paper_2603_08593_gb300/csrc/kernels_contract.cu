@@ -468,9 +468,9 @@ cudaError_t launch_contract_slot0(const sfft_plan_s* p, int DM, int job0, int nj
   if (njobs <= 0) return cudaSuccess;
   const dim3 grid(njobs, max_uy<float>());
   switch (DM) {
-    case 0: k_contract_slot0<float, 0><<<grid, 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, p->d.H, p->M, p->Nf, p->d.L, p->dl ? 8 : p->M); break;
-    case 2: k_contract_slot0<float, 2><<<grid, 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, p->d.H, p->M, p->Nf, p->d.L, p->dl ? 8 : p->M); break;
-    case 4: k_contract_slot0<float, 4><<<grid, 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, p->d.H, p->M, p->Nf, p->d.L, p->dl ? 8 : p->M); break;
+    case 0: k_contract_slot0<float, 0><<<grid, 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, p->d.H, p->M, p->Nf, p->d.L, p->dl ? 16 : p->M); break;
+    case 2: k_contract_slot0<float, 2><<<grid, 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, p->d.H, p->M, p->Nf, p->d.L, p->dl ? 16 : p->M); break;
+    case 4: k_contract_slot0<float, 4><<<grid, 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, p->d.H, p->M, p->Nf, p->d.L, p->dl ? 16 : p->M); break;
     default: return cudaErrorInvalidValue;
   }
   p->nlaunch += 1;

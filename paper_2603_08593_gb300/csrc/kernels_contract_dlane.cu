@@ -23,18 +23,23 @@
 // end.  k_lag_dft then forms the lags u_x of every (d, u_y) pair, summing the
 // k-slots in FP32 runs of 32 and FP64 across runs.
 //
-// Roles (320 threads, one CTA per SM):
-//   warps 0-3  A producers: lane l of warp w is difference 32 w + l of the
-//              tile (tensor-memory lane 32 w + l); per k-step (four rows y')
-//              one 16-byte load per row gives both k-slots' probe values,
-//              split into 2 x 16 A columns (tcgen05.st); then the epilogue;
-//   warps 4-7  B producers: the four strips (TF32 and BF16, two parities) of
-//              both k-slots for each staged chunk of 16 rows y';
-//   warp 8     MMA issuer: per k-step 2 x nu x (TF32 + BF16) MMAs;
-//   warp 9     copy producer: per chunk one tensor-map box of probe rows
+// Roles (448 threads, one CTA per SM):
+//   warps 0-7  A producers: lane l of warp w is difference 32 (w % 4) + l of
+//              the tile (tensor-memory lane 32 (w % 4) + l); warps 0-3 take
+//              the even k-steps (four rows y') and warps 4-7 the odd ones; one
+//              16-byte load per row gives both k-slots' probe values, split
+//              into 2 x 16 A columns (tcgen05.st); warps 0-3 then run the
+//              epilogue;
+//   warps 8-11 B producers: the four strips (TF32 and BF16, two parities) of
+//              both k-slots for each staged chunk of 16 rows y', a half-warp
+//              filling one 128-byte core matrix per store;
+//   warp 12    MMA issuer: per pair of k-steps 2 x nu accumulators, each
+//              taking its four MMAs (TF32 and BF16 of both k-steps) back to
+//              back;
+//   warp 13    copy producer: per chunk one tensor-map box of probe rows
 //              (128 differences x 17 rows x 2 slots, from the k-slot-blocked
-//              product spectra [d][k / 8][y][k % 8]) and one box of weight
-//              rows per exponent.
+//              product spectra [d][k / 16][y][k % 16]), one box of weight rows
+//              per exponent and the powers of yt.
 // Every wait is bounded; a wait that gives up flags the CCD (status bit 4)
 // and makes every role leave its loop, after which the issued copies and
 // MMAs are drained (bounded) and the tensor memory is freed.
@@ -60,11 +65,12 @@ constexpr int VSLOT = (VR * 16 + 127) / 128 * 128;
 constexpr int NQ = (4 * (KSC - 1) + NU - 1) / 2 + 2;   // 16-byte columns (row pairs) per strip
 constexpr int SBO = NQ * 128 + 16;    // bytes between the strips' 8-row groups (16 more to shift banks)
 constexpr int STRIP = 4 * SBO;        // 32 rows n
-constexpr int WARP_MMA = 8, WARP_COPY = 9;
-constexpr int NTHREADS = 32 * 10;
+constexpr int WARP_BP = 8;            // first B-producer warp
+constexpr int WARP_MMA = 12, WARP_COPY = 13;
+constexpr int NTHREADS = 32 * 14;
 constexpr int TMEM_COLS = 512;        // D: 2 x NU x 32 columns, A: GA x 32 columns
 static_assert(2 * NU * 32 + GA * 32 <= TMEM_COLS, "tensor memory budget");
-static_assert(CH % 4 == 0 && VR % 2 == 0, "chunk geometry");
+static_assert(CH % 8 == 0 && VR % 2 == 0 && GA % 2 == 0, "chunk geometry: k-steps in pairs");
 
 struct DStage {
   uint8_t P[PBYTES];                       // [difference][row y'][2 slots]
@@ -112,7 +118,7 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
   if (threadIdx.x == 0) {
     for (int i = 0; i < 2; ++i) {
       mbar_init(&S.raw_full[i], 1);
-      mbar_init(&S.raw_empty[i], 8);
+      mbar_init(&S.raw_empty[i], 12);
       mbar_init(&S.strip_full[i], 4);
       mbar_init(&S.strip_empty[i], 1);
     }
@@ -148,7 +154,7 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
         mbar_arrive_expect_tx(&S.raw_full[sidx], (unsigned)(pz * PBR * 16 + (DM + 1) * VR * 16) + ybytes);
       __syncwarp();
       if (lane == 0) {
-        tma_load_4d(&st.P[0], &tmP, 2 * (k0 & 7), yc, k0 >> 3, job.zp + job.d_first, &S.raw_full[sidx]);
+        tma_load_4d(&st.P[0], &tmP, 2 * (k0 & 15), yc, k0 >> 4, job.zp + job.d_first, &S.raw_full[sidx]);
       } else if (lane <= DM + 1) {
         const int a = lane - 1;
         tma_load_3d(&st.V[a][0], &tmV, 2 * k0, yc + ulo, job.zw + a, &S.raw_full[sidx]);
@@ -166,32 +172,51 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
     for (int c = 0; c < nchunk && !*abort; ++c) {
       const int sidx = c & 1;
       if (!wait_phase(&S.strip_full[sidx], (unsigned)((c >> 1) & 1), abort)) break;
+      uint64_t dtf[2][4];   // descriptors of the stage's strips: [slot][TF32 even, odd, BF16 even, odd]
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int kd = 0; kd < 4; ++kd) dtf[s][kd] = dstrip0 + (uint64_t)((((sidx * 2 + s) * 4 + kd) * STRIP) >> 4);
       bool live = true;
-      for (int j = 0; j < KSC; ++j) {
-        const int g = c * KSC + j, as = g % GA;
-        if (!wait_phase(&S.a_full[as], (unsigned)((g / GA) & 1), abort)) { live = false; break; }
+      // k-steps in pairs: each accumulator takes TF32 (j), BF16 (j), TF32
+      // (j + 1), BF16 (j + 1) back to back, which halves the switches between
+      // accumulators (each switch costs the tensor pipe a TMEM turnaround)
+      for (int j = 0; j < KSC; j += 2) {
+        const int g = c * KSC + j, as = g % GA;   // k-steps g, g + 1 in A slots as, as + 1
+        if (!wait_phase(&S.a_full[as], (unsigned)((g / GA) & 1), abort) ||
+            !wait_phase(&S.a_full[as + 1], (unsigned)(((g + 1) / GA) & 1), abort)) {
+          live = false;
+          break;
+        }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (elect_one()) {
+          const uint32_t acc = g > 0 ? 1u : 0u;   // the first k-step starts the accumulators
 #pragma unroll
           for (int s = 0; s < 2; ++s) {
 #pragma unroll
             for (int i = 0; i < NU; ++i) {
-              if (i >= nu) break;
-              const int o = 4 * j + i, par = o & 1, qc = (o - par) >> 1;   // strip row of the step's first weight row
-              const uint32_t dcol = t_d + 32 * (NU * s + i), acol = t_a + 32 * as + 16 * s;
-              const uint64_t bt = dstrip0 + (uint64_t)((((sidx * 2 + s) * 4 + par) * STRIP + qc * 128) >> 4);
-              const uint64_t bb = dstrip0 + (uint64_t)((((sidx * 2 + s) * 4 + 2 + par) * STRIP + qc * 128) >> 4);
-              const uint32_t acc = g > 0 ? 1u : 0u;
-              asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                           " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n"
-                           ::"r"(dcol), "r"(acol), "l"(bt), "r"(id_tf32), "r"(acc) : "memory");
-              asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                           " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n"
-                           ::"r"(dcol), "r"(acol + 8), "l"(bb), "r"(id_bf16), "r"(1u) : "memory");
+              if (i < nu) {
+                const uint32_t dcol = t_d + 32 * (NU * s + i);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  const int o = 4 * (j + h) + i, par = o & 1, qc = (o - par) >> 1;   // strip row of the first weight row
+                  const uint32_t acol = t_a + 32 * (as + h) + 16 * s;
+                  const uint64_t bt = dtf[s][par] + (uint64_t)(qc * 8);
+                  const uint64_t bb = dtf[s][2 + par] + (uint64_t)(qc * 8);
+                  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                               " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n"
+                               ::"r"(dcol), "r"(acol), "l"(bt), "r"(id_tf32), "r"(h ? 1u : acc) : "memory");
+                  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                               " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n"
+                               ::"r"(dcol), "r"(acol + 8), "l"(bb), "r"(id_bf16), "r"(1u) : "memory");
+                }
+              }
             }
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                        ::"r"(smem_u32(&S.a_empty[as])) : "memory");
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                       ::"r"(smem_u32(&S.a_empty[as + 1])) : "memory");
         }
         __syncwarp();
       }
@@ -208,15 +233,15 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
     __syncwarp();
     for (int it = 0; it < kMaxSpin && !mbar_try_wait(&S.done, 0); ++it) {
     }
-  } else if (warp < 4) {
-    // ---- A producers
-    const int q = 32 * warp + lane;
-    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+  } else if (warp < WARP_BP) {
+    // ---- A producers: warp w takes the k-steps j = w / 4 (mod 2)
+    const int q = 32 * (warp & 3) + lane;
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
     for (int c = 0; c < nchunk && !*abort; ++c) {
       const int sidx = c & 1;
       if (!wait_phase(&S.raw_full[sidx], (unsigned)((c >> 1) & 1), abort)) break;
       const uint8_t* P = &S.st[sidx].P[q * PBR * 16];
-      for (int j = 0; j < KSC; ++j) {
+      for (int j = warp >> 2; j < KSC; j += 2) {
         const int g = c * KSC + j, as = g % GA;
         if (g >= GA && !wait_phase(&S.a_empty[as], (unsigned)(((g / GA) - 1) & 1), abort)) break;
         uint32_t v[2][16];
@@ -249,16 +274,19 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
       __syncwarp();
       if (lane == 0) mbar_arrive(&S.raw_empty[sidx]);
     }
-  } else if (warp < 8) {
-    // ---- B producers: thread (monomial m, slot s, first row r0) writes
-    // W_m(y) for y = yc + u_lo + s_row, s_row = r0, r0 + 4, ..., into the
-    // rows n = m (Re) and 16 + m (Im) of both parities' strips.  TF32 strip element (n, k) at
-    // (n / 8) SBO + (k / 4) 128 + (n % 8) 16 + (k % 4) 4 with k = 2 (row % 2)
+  } else if (warp < WARP_MMA) {
+    // ---- B producers: warp e (slot e % 2) takes the row pairs e / 2, e / 2
+    // + 2, ...; lane (m % 8, row parity, m / 8) writes W_m(y) for
+    // y = yc + u_lo + s_row into the rows n = m (Re) and 16 + m (Im) of
+    // both parities' strips, so that the 16 lanes of a half-warp fill one
+    // 128-byte core matrix (8 rows n x 2 rows y) per store.  TF32 strip
+    // element (n, k) at (n / 8) SBO + (k / 4) 128 + (n % 8) 16 + (k % 4) 4
+    // with k = 2 (row % 2)
     // + (re, im) inside the row pair k / 4; the BF16 strip holds per (n, row)
     // four values (hi(P)-part re, im: lo(W); lo(P)-part re, im: W) at
     // (row % 2) 8 bytes of the same 16-byte column.
-    const int bt = threadIdx.x - 128;
-    const int m = bt & 15, s = (bt >> 4) & 1, r0 = bt >> 5;   // strip rows r0, r0 + 4, ... of each chunk
+    const int e = warp - WARP_BP;
+    const int m = 8 * ((lane >> 4) & 1) + (lane & 7), rpar = (lane >> 3) & 1, s = e & 1;
     int am = 0, bm = 0;
     mono_ab(m < NMONO ? m : 0, am, bm);
     const bool live = m < NMONO;
@@ -272,7 +300,7 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
       uint8_t* tf0 = &S.strip[sidx][s][0][0];
       uint8_t* bf0 = &S.strip[sidx][s][2][0];
 #pragma unroll 2
-      for (int srow = r0; srow < VR - 1; srow += 4) {
+      for (int srow = 2 * (e >> 1) + rpar; srow < VR - 1; srow += 4) {
         const int y = ybase + srow;
         const bool on = live && y >= y0 && y < y1;
         const float2 vv = *reinterpret_cast<const float2*>(&st.V[am][srow * 16 + s * 8]);

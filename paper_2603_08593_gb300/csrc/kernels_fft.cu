@@ -72,8 +72,8 @@ struct RowFFT {
   }
 
   // v[r] = z[t + TPR r] (the first pass's inputs, radix 16, span 1) -> spectrum row `out`
-  // (X[k] is stored at out[k], or with BLK at out[(k / 8) kb + k % 8] for the
-  // k-slot-blocked product spectra, kb = 8 H)
+  // (X[k] is stored at out[k], or with BLK at out[(k / 16) kb + k % 16] for
+  // the k-slot-blocked product spectra, kb = 16 H)
   template <bool BLK = false>
   __device__ static void run(T2 (&v)[16], T2* buf, int t, bool valid, const T2* __restrict__ twM,
                              const T2* __restrict__ twN, T2* __restrict__ out, int kb = 0) {
@@ -102,7 +102,7 @@ struct RowFFT {
           X.x = er + wi;
           X.y = ei - wr;
         }
-        if constexpr (BLK) out[(k >> 3) * kb + (k & 7)] = X;
+        if constexpr (BLK) out[(k >> 4) * kb + (k & 15)] = X;
         else out[k] = X;
       }
     }
@@ -183,7 +183,7 @@ k_rfft_prod_dy(const T* __restrict__ Rm, int H, int W, int L, int d0, int nd, c_
   }
   __syncthreads();
   const int dx0 = dy == 0 ? 0 : -(L - 1);
-  c_t<T>* obase = out + (int64_t)ccd * ccd_stride_out + (int64_t)y * (BLK ? 8 : M);
+  c_t<T>* obase = out + (int64_t)ccd * ccd_stride_out + (int64_t)y * (BLK ? 16 : M);
   for (int id0 = lo; id0 < hi; id0 += F::RPB) {
     const int id = id0 + rloc;
     const bool valid = id < hi;
@@ -196,7 +196,7 @@ k_rfft_prod_dy(const T* __restrict__ Rm, int H, int W, int L, int d0, int nd, c_
       v[r].x = valid ? r1[x0] * r2[x0 + dx + PADX] : (T)0;
       v[r].y = valid ? r1[x0 + 1] * r2[x0 + 1 + dx + PADX] : (T)0;
     }
-    F::template run<BLK>(v, buf, t, valid, twM, twN, obase + (int64_t)(valid ? id - d0 : 0) * slab_stride, 8 * H);
+    F::template run<BLK>(v, buf, t, valid, twM, twN, obase + (int64_t)(valid ? id - d0 : 0) * slab_stride, 16 * H);
   }
 }
 
@@ -248,7 +248,7 @@ k_rfft_prod_dy_w(const float* __restrict__ Rm, int H, int W, int L, int d0, int 
       r2[x] = (ok2 && gx >= 0 && gx < W) ? img[(int64_t)(y + dy) * W + gx] : 0.f;
     }
     __syncthreads();
-    float2* orow = out + (int64_t)ccd * ccd_stride_out + (int64_t)y * (BLK ? 8 : M);
+    float2* orow = out + (int64_t)ccd * ccd_stride_out + (int64_t)y * (BLK ? 16 : M);
     for (int id = lo + warp; id < hi; id += 8) {
       const int dx = dx0 + (id - first_of(dy));
       float2 v[32];
@@ -294,7 +294,7 @@ k_rfft_prod_dy_w(const float* __restrict__ Rm, int H, int W, int L, int d0, int 
           X.x = er + wi;
           X.y = ei - wr;
         }
-        if constexpr (BLK) o[(int64_t)(k >> 3) * (8 * H) + (k & 7)] = X;   // [k / 8][y][k % 8]
+        if constexpr (BLK) o[(int64_t)(k >> 4) * (16 * H) + (k & 15)] = X;   // [k / 16][y][k % 16]
         else o[k] = X;
       }
       __syncwarp();
@@ -390,8 +390,8 @@ static cudaError_t run_prod_dy(const sfft_plan_s* p, const T* Rm, int d0, int nd
                                int64_t ccd_stride) {
   using F = RowFFT<T, M>;
   const size_t smem = F::smem_bytes() + sizeof(T) * (size_t)(2 * (2 * M) + 32);
-  // product spectra [d][y][k], or k-slot-blocked [d][k / 8][y][k % 8] for the
-  // lane-per-difference contraction
+  // product spectra [d][y][k], or k-slot-blocked [d][k / 16][y][k % 16] for
+  // the lane-per-difference contraction
   auto kern = p->dl ? k_rfft_prod_dy<T, M, true> : k_rfft_prod_dy<T, M, false>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int L = p->d.L;

@@ -108,14 +108,14 @@ inline bool make_map(CUtensorMap* m, void* base, int M, int H, int n, int bx, in
 }
 
 
-// 4-D FP32 view of k-slot-blocked spectra [n][M / 8][H][8 complex] (x: the
-// 16 floats of one block row, y: rows, z: blocks, v: spectra), with boxes of
+// 4-D FP32 view of k-slot-blocked spectra [n][M / 16][H][16 complex] (x: the
+// 32 floats of one block row, y: rows, z: blocks, v: spectra), with boxes of
 // bx floats x by rows x 1 block x bv spectra
 inline bool make_map_blk(CUtensorMap* m, void* base, int M, int H, int n, int bx, int by, int bv) {
   EncodeTiled fn = encode_fn();
   if (!fn) return false;
-  const cuuint64_t dims[4] = {16, (cuuint64_t)H, (cuuint64_t)(M / 8), (cuuint64_t)n};
-  const cuuint64_t strides[3] = {64, (cuuint64_t)H * 64, (cuuint64_t)H * 64 * (M / 8)};
+  const cuuint64_t dims[4] = {32, (cuuint64_t)H, (cuuint64_t)(M / 16), (cuuint64_t)n};
+  const cuuint64_t strides[3] = {128, (cuuint64_t)H * 128, (cuuint64_t)H * 128 * (M / 16)};
   const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, (cuuint32_t)bv};
   const cuuint32_t es[4] = {1, 1, 1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
