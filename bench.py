@@ -42,9 +42,10 @@ WORKLOAD = ("one DECam CCD pair per GPU per step: 2048x4096 FP32, 20k stars, PSF
 KK_TRAFFIC = {
     "kernels_contract.cu": (10.09e9, "1a847c15ebf73406"),      # FP32 FMA kernel (--fma-contract)
     "kernels_contract_tc.cu": (None, ""),                      # mma.sync kernel (--mma-sync-contract)
-    "kernels_contract_umma.cu": (9.975e9, "0d3c235754a7a213"),  # tcgen05 kernel (default)
+    "kernels_contract_umma.cu": (9.975e9, "0d3c235754a7a213"),  # tcgen05, one lane per (d, u_y) pair
+    "kernels_contract_dlane.cu": (None, ""),                    # tcgen05, one lane per difference (default)
 }
-PHASES = ("prep", "fft_weights", "fft_prod", "contract_kk", "contract_rk", "scatter", "solve", "apply")
+PHASES = ("prep", "fft_weights", "fft_prod", "contract_kk", "contract_rk", "scatter", "solve", "apply", "lag_dft")
 
 
 def half_plane_lag_rows(L):
@@ -336,13 +337,15 @@ def run_gpu(args):
     with torch.cuda.stream(stream):
         plan = Plan(Hs, W, L, DK, DB, batch=B, prec=args.prec, stream=stream, device=dev, d_batch=args.d_batch,
                     graph=batched, autotune=0 if args.no_autotune else 1, lag_parts=args.lag_parts,
-                    fma_contract=args.fma_contract, mma_sync_contract=args.mma_sync_contract)
+                    fma_contract=args.fma_contract, mma_sync_contract=args.mma_sync_contract,
+                    pair_lane_contract=args.pair_lane_contract)
         tiles = plan.tiles
+        engine = plan.engine
         if batched:
             # per-phase times and launch counts from an eager profiled pass of the same plan
             eager = Plan(Hs, W, L, DK, DB, batch=B, prec=args.prec, stream=stream, device=dev,
                          d_batch=tiles[0], rows_per_cta=tiles[1], lag_parts=tiles[2], fma_contract=args.fma_contract,
-                         mma_sync_contract=args.mma_sync_contract)
+                         mma_sync_contract=args.mma_sync_contract, pair_lane_contract=args.pair_lane_contract)
             eo = eager.subtract(R, S, bad, None, refine=REFINE)
             eager.profile(True)
             eager.profile_read(reset=True)
@@ -434,11 +437,13 @@ def run_gpu(args):
     roof = None
     clocks = clk.summary()
     if kk_n:
-        # one launch = the KK contraction over one batch of offset differences
-        # plus its k_contract_slot0 companion (the exact DC/Nyquist slot)
-        n_launch = kk_n / 2
-        avg_ms = kk_ms / n_launch
         on_tc = args.prec == "mixed" and not args.fma_contract
+        # the contract_kk phase holds one contraction launch per batch of offset
+        # differences on the tensor-core engines (their lag DFT and exact
+        # slot-0 sums are the lag_dft phase); the FP32 FMA engine adds its
+        # k_contract_slot0 companion to the same phase
+        n_launch = kk_n if on_tc else kk_n / 2
+        avg_ms = kk_ms / n_launch
         full = Hs == H and B == 1 and tiles[0] == 221
         if on_tc:
             # the split-operand product runs the matrix product once in TF32
@@ -447,9 +452,15 @@ def run_gpu(args):
             per_launch_flop = 2 * B * kk_gemm_flops_per_ccd(Hs, W, L, DK) / (n_launch / args.steps)
             achieved = per_launch_flop / (avg_ms * 1e-3) / 1e12
             peak = tf32_peak_tflops(sustained=True)
-            kname = ("k_contract_tc (lag contraction as split TF32/BF16 mma.sync products)" if args.mma_sync_contract
-                     else "k_contract_umma (lag contraction as split TF32/BF16 tcgen05 products, accumulators in TMEM)")
-            ksrc = "kernels_contract_tc.cu" if args.mma_sync_contract else "kernels_contract_umma.cu"
+            kname, ksrc = {
+                "mma_sync": ("k_contract_tc (lag contraction as split TF32/BF16 mma.sync products)",
+                             "kernels_contract_tc.cu"),
+                "tcgen05_pair_lane": ("k_contract_umma (lag contraction as split TF32/BF16 tcgen05 products, one "
+                                      "TMEM lane per (d, u_y) pair)", "kernels_contract_umma.cu"),
+                "tcgen05_difference_lane": ("k_contract_dlane (lag contraction as split TF32/BF16 tcgen05 products, "
+                                            "one TMEM lane per difference, u_y shifts from weight-row strips)",
+                                            "kernels_contract_dlane.cu"),
+            }[engine]
             roof = {"bound": "tensor", "kernel": kname,
                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                     "traffic": args.traffic if args.traffic is not None else (kk_traffic_bytes(ksrc) if full else None),
@@ -488,6 +499,7 @@ def run_gpu(args):
                        "refine": REFINE, "ccd_pairs_per_gpu_per_step": B, "parallelism": f"replicas x{world}",
                        "cuda_graph": batched, "autotune": not args.no_autotune,
                        "tiles": {"d_batch": tiles[0], "rows_per_cta": tiles[1], "lag_parts": tiles[2]},
+                       "kk_engine": engine,
                        "l2": "256 MB buffer written between timed steps (L2 flushed)"},
             "roofline": roof, "cpu_baseline": cpu_base, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "status": info, "wall_s": wall, "fp64_path": fp64, "classifier": classifier,
@@ -522,6 +534,8 @@ def main():
                     help="mixed path: KK contraction on the FP32 FMA pipes instead of the tensor cores")
     ap.add_argument("--mma-sync-contract", action="store_true",
                     help="mixed path: tensor-core KK contraction through mma.sync instead of tcgen05")
+    ap.add_argument("--pair-lane-contract", action="store_true",
+                    help="tcgen05 contraction with one TMEM lane per (difference, u_y) pair")
     args = ap.parse_args()
     if args.only_classifier:   # classifier figures alone (profiling captures)
         import torch

@@ -113,6 +113,11 @@ void          sfft_plan_destroy(sfft_plan_t plan);
 sfft_status_t sfft_plan_set_stream(sfft_plan_t plan, void* cuda_stream);
 int64_t       sfft_num_unknowns(sfft_plan_t plan);          /* N */
 size_t        sfft_workspace_bytes(sfft_plan_t plan);       /* bytes for `ws` */
+/* KK-contraction engine the plan runs: 0 FP64 FMA (FP64 path), 1 FP32 FMA,
+ * 2 tensor cores through mma.sync, 3 tcgen05 with one tensor-memory lane per
+ * (difference, u_y) pair, 4 tcgen05 with one lane per difference; -1 for a
+ * null plan. */
+int32_t       sfft_plan_engine(sfft_plan_t plan);
 /* Chosen tile shape after planning: out[0] = d_batch, out[1] = rows_per_cta,
  * out[2] = lag parts of the contraction. */
 sfft_status_t sfft_plan_tiles(sfft_plan_t plan, int32_t* out3);
@@ -209,7 +214,9 @@ enum {
   SFFT_PROF_SCATTER = 5,     /* assembly of A and b from the accumulators */
   SFFT_PROF_SOLVE = 6,       /* Cholesky and triangular solves */
   SFFT_PROF_APPLY = 7,       /* convolve-and-subtract and refinement residual */
-  SFFT_PROF_N = 8
+  SFFT_PROF_LAG_DFT = 8,     /* tensor-core KK paths: lags u_x over the k-slot products and the
+                                exact slot-0 sums */
+  SFFT_PROF_N = 9
 };
 sfft_status_t sfft_profile_enable(sfft_plan_t plan, int32_t enable);
 sfft_status_t sfft_profile_read(sfft_plan_t plan, double* ms, int64_t* launches, int32_t reset);

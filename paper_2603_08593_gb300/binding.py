@@ -37,6 +37,7 @@ SIGNATURES = {
     "sfft_plan_set_stream": (I32, [VP, VP]),
     "sfft_num_unknowns": (I64, [VP]),
     "sfft_workspace_bytes": (SZ, [VP]),
+    "sfft_plan_engine": (I32, [VP]),
     "sfft_plan_tiles": (I32, [VP, C.POINTER(I32)]),
     "sfft_build_normal": (I32, [VP, VP, VP, VP, VP, VP, VP, VP]),
     "sfft_solve": (I32, [VP, VP, VP, VP, I32, VP, VP, VP, VP, VP]),
@@ -174,6 +175,7 @@ class Plan:
         self.const_ratio = bool(const_ratio)
         self.N = int(lib.sfft_num_unknowns(h))
         self.ws_bytes = int(lib.sfft_workspace_bytes(h))
+        self.engine = self.ENGINES[int(lib.sfft_plan_engine(h))]
         self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
         off = (-self.ws.data_ptr()) % 256
         self.ws_view = self.ws[off:off + self.ws_bytes]
@@ -254,7 +256,9 @@ class Plan:
         _check(st, "sfft_subtract")
         return o
 
-    PROF_PHASES = ("prep", "fft_weights", "fft_prod", "contract_kk", "contract_rk", "scatter", "solve", "apply")
+    PROF_PHASES = ("prep", "fft_weights", "fft_prod", "contract_kk", "contract_rk", "scatter", "solve", "apply",
+                   "lag_dft")
+    ENGINES = ("fp64_fma", "fp32_fma", "mma_sync", "tcgen05_pair_lane", "tcgen05_difference_lane")
 
     def profile(self, enable=True):
         _check(self.lib.sfft_profile_enable(self.h, 1 if enable else 0), "sfft_profile_enable")

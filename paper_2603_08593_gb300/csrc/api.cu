@@ -497,6 +497,13 @@ extern "C" sfft_status_t sfft_plan_set_stream(sfft_plan_t p, void* s) {
 
 extern "C" int64_t sfft_num_unknowns(sfft_plan_t p) { return p ? p->N : -1; }
 extern "C" size_t sfft_workspace_bytes(sfft_plan_t p) { return p ? p->ws_bytes : 0; }
+extern "C" int32_t sfft_plan_engine(sfft_plan_t p) {
+  if (!p) return -1;
+  if (p->fp64) return 0;
+  if (!p->tc) return 1;
+  if (!p->umma) return 2;
+  return p->dl ? 4 : 3;
+}
 extern "C" sfft_status_t sfft_plan_tiles(sfft_plan_t p, int32_t* o) {
   if (!p || !o) return SFFT_ERR_ARG;
   o[0] = p->d_batch; o[1] = p->rows_per_cta; o[2] = p->csplit;
@@ -541,10 +548,14 @@ static sfft_status_t build_normal_impl(sfft_plan_t p, const float* R, const floa
       if (p->tc) {
         if (p->dl) CK(launch_contract_dlane(p, (int)ib, ws));
         else CK(p->umma ? launch_contract_umma(p, (int)ib, ws) : launch_contract_tc(p, (int)ib, ws));
-        CK(launch_contract_slot0(p, p->DM_KK, p->kk_first[ib], p->kk_count[ib], ws));
       } else {
         CK(launch_contract(p, p->DM_KK, p->kk_first[ib], p->kk_count[ib], p->rows_per_cta, p->csplit, ws));
       }
+    }
+    if (p->tc) {
+      Phase ph(p, SFFT_PROF_LAG_DFT);
+      if (p->dl) CK(launch_lag_dft(p, (int)ib, ws));
+      CK(launch_contract_slot0(p, p->DM_KK, p->kk_first[ib], p->kk_count[ib], ws));
     }
   }
   {

@@ -21,7 +21,7 @@
 // over all weight rows of the band; its 2 x NU accumulators (32 FP32 columns
 // each) stay in tensor memory and go to an HBM buffer C[k][d][u_y][32] at the
 // end.  k_lag_dft then forms the lags u_x of every (d, u_y) pair, summing the
-// k-slots in FP32 runs of 32 and FP64 across runs.
+// k-slots in FP32 runs of 16 and FP64 across runs.
 //
 // Roles (448 threads, one CTA per SM):
 //   warps 0-7  A producers: lane l of warp w is difference 32 (w % 4) + l of
@@ -442,7 +442,7 @@ k_lag_dft(const int4* __restrict__ pairs, const char* __restrict__ cbuf0, size_t
 template <int DM>
 static cudaError_t contract_dlane_dm(const sfft_plan_s* p, int batch_index, void* ws) {
   const int job0 = p->dl_first[batch_index], njobs = p->dl_count[batch_index];
-  const int pair0 = p->dlp_first[batch_index], npair = p->dlp_count[batch_index];
+  if (njobs <= 0) return cudaSuccess;
   const int H = p->d.H, L = p->d.L, B = p->d.batch;
   const size_t smem = sizeof(DSmem);
   auto kern = k_contract_dlane<DM>;
@@ -454,22 +454,26 @@ static cudaError_t contract_dlane_dm(const sfft_plan_s* p, int batch_index, void
   if (!make_map_blk(&mp, base + p->phat.off, p->M, H, ntot, 4, PBR, pz) ||
       !make_map(&mv, base + p->wspec.off, p->M, H, p->n_wa * B, 4, VR, 1))
     return cudaErrorInvalidValue;
-  if (njobs > 0) {
-    const int per_ccd = njobs / B;   // jobs are ordered CCD-major, the same count per CCD
-    dim3 grid(per_ccd, p->M / 2, B);
-    kern<<<grid, NTHREADS, smem, p->stream>>>(mp, mv, p->d_dljobs + job0, (char*)ws, H, L, p->d_batch, pz,
-                                              (const float*)p->ytab);
-    p->nlaunch += 1;
-  }
-  if (npair > 0) {
-    const size_t cbuf_ccd = (size_t)p->M * p->d_batch * L * 32 * sizeof(float);
-    const size_t g_ccd = (size_t)p->n_hd * L * L * n_mono(DM);
-    double* g0 = ws_at<double>(ws, p->gkk) + (size_t)batch_index * p->d_batch * L * L * n_mono(DM);
-    dim3 grid(npair, B);
-    k_lag_dft<DM><<<grid, 256, 0, p->stream>>>(p->d_dlpairs + pair0, base + p->cbuf.off, cbuf_ccd, g0, g_ccd, p->M,
-                                               p->Nf, L, p->d_batch, (const float2*)p->twD);
-    p->nlaunch += 1;
-  }
+  const int per_ccd = njobs / B;   // jobs are ordered CCD-major, the same count per CCD
+  dim3 grid(per_ccd, p->M / 2, B);
+  kern<<<grid, NTHREADS, smem, p->stream>>>(mp, mv, p->d_dljobs + job0, (char*)ws, H, L, p->d_batch, pz,
+                                            (const float*)p->ytab);
+  p->nlaunch += 1;
+  return cudaGetLastError();
+}
+
+template <int DM>
+static cudaError_t lag_dft_dm(const sfft_plan_s* p, int batch_index, void* ws) {
+  const int pair0 = p->dlp_first[batch_index], npair = p->dlp_count[batch_index];
+  if (npair <= 0) return cudaSuccess;
+  const int L = p->d.L, B = p->d.batch;
+  const size_t cbuf_ccd = (size_t)p->M * p->d_batch * L * 32 * sizeof(float);
+  const size_t g_ccd = (size_t)p->n_hd * L * L * n_mono(DM);
+  double* g0 = ws_at<double>(ws, p->gkk) + (size_t)batch_index * p->d_batch * L * L * n_mono(DM);
+  dim3 grid(npair, B);
+  k_lag_dft<DM><<<grid, 256, 0, p->stream>>>(p->d_dlpairs + pair0, static_cast<char*>(ws) + p->cbuf.off, cbuf_ccd,
+                                             g0, g_ccd, p->M, p->Nf, L, p->d_batch, (const float2*)p->twD);
+  p->nlaunch += 1;
   return cudaGetLastError();
 }
 
@@ -478,6 +482,15 @@ cudaError_t launch_contract_dlane(const sfft_plan_s* p, int batch_index, void* w
     case 0: return contract_dlane_dm<0>(p, batch_index, ws);
     case 2: return contract_dlane_dm<2>(p, batch_index, ws);
     case 4: return contract_dlane_dm<4>(p, batch_index, ws);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_lag_dft(const sfft_plan_s* p, int batch_index, void* ws) {
+  switch (p->DM_KK) {
+    case 0: return lag_dft_dm<0>(p, batch_index, ws);
+    case 2: return lag_dft_dm<2>(p, batch_index, ws);
+    case 4: return lag_dft_dm<4>(p, batch_index, ws);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -136,6 +136,7 @@ cudaError_t launch_contract(const sfft_plan_s* p, int DM, int job0, int njobs, i
 cudaError_t launch_contract_tc(const sfft_plan_s* p, int batch_index, void* ws);
 cudaError_t launch_contract_umma(const sfft_plan_s* p, int batch_index, void* ws);
 cudaError_t launch_contract_dlane(const sfft_plan_s* p, int batch_index, void* ws);
+cudaError_t launch_lag_dft(const sfft_plan_s* p, int batch_index, void* ws);
 cudaError_t launch_contract_slot0(const sfft_plan_s* p, int DM, int job0, int njobs, void* ws);
 cudaError_t launch_scatter(const sfft_plan_s* p, double* A, double* b, void* ws, bool rhs_only, double* rhs_out);
 cudaError_t launch_cholesky(const sfft_plan_s* p, const double* A, void* ws);

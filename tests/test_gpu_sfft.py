@@ -302,3 +302,15 @@ def test_const_ratio_batched_graph_subtract():
         assert O.kernel_coef_rel_err(th[i], ref["theta_orig"], L, DK, DB) <= 1e-5
         fin = np.isfinite(ref["D"][w:-w, w:-w])
         assert np.abs(Dg[i][w:-w, w:-w][fin] - ref["D"][w:-w, w:-w][fin]).max() <= 1e-3 * SIGMA_SKY
+
+
+def test_contraction_engine_selection():
+    """One tensor-memory lane per difference is the default when a difference
+    batch fills most of the 128 lanes; the pair-lane engine is kept for small
+    batches and on request; the FP64 path contracts on the FMA pipes."""
+    from paper_2603_08593_gb300 import Plan
+    assert Plan(96, 300, 11, 2, 2, prec="mixed").engine == "tcgen05_difference_lane"
+    assert Plan(96, 300, 11, 2, 2, prec="mixed", pair_lane_contract=True).engine == "tcgen05_pair_lane"
+    assert Plan(96, 300, 11, 2, 2, prec="mixed", d_batch=7).engine == "tcgen05_pair_lane"
+    assert Plan(96, 300, 11, 2, 2, prec="mixed", mma_sync_contract=True).engine == "mma_sync"
+    assert Plan(96, 300, 11, 2, 2, prec="fp64").engine == "fp64_fma"
