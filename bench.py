@@ -43,7 +43,7 @@ KK_TRAFFIC = {
     "kernels_contract.cu": (10.09e9, "1a847c15ebf73406"),      # FP32 FMA kernel (--fma-contract)
     "kernels_contract_tc.cu": (None, ""),                      # mma.sync kernel (--mma-sync-contract)
     "kernels_contract_umma.cu": (9.975e9, "0d3c235754a7a213"),  # tcgen05, one lane per (d, u_y) pair
-    "kernels_contract_dlane.cu": (None, ""),                    # tcgen05, one lane per difference (default)
+    "kernels_contract_dlane.cu": (11.585e9, "301479bab2fe6f96"),  # tcgen05, one lane per difference (default)
 }
 PHASES = ("prep", "fft_weights", "fft_prod", "contract_kk", "contract_rk", "scatter", "solve", "apply", "lag_dft")
 
