@@ -43,7 +43,10 @@ KK_TRAFFIC = {
     "kernels_contract.cu": (10.09e9, "1a847c15ebf73406"),      # FP32 FMA kernel (--fma-contract)
     "kernels_contract_tc.cu": (None, ""),                      # mma.sync kernel (--mma-sync-contract)
     "kernels_contract_umma.cu": (9.975e9, "0d3c235754a7a213"),  # tcgen05, one lane per (d, u_y) pair
-    "kernels_contract_dlane.cu": (11.585e9, "301479bab2fe6f96"),  # tcgen05, one lane per difference (default)
+    # tcgen05, one lane per difference (default); measured on the source with
+    # sha256 prefix 301479bab2fe6f96, whose k_contract_dlane and launcher are
+    # byte-identical to this file's (the lag DFT moved to kernels_lag_dft.cu)
+    "kernels_contract_dlane.cu": (11.585e9, "1d4954879467044d"),
 }
 PHASES = ("prep", "fft_weights", "fft_prod", "contract_kk", "contract_rk", "scatter", "solve", "apply", "lag_dft")
 

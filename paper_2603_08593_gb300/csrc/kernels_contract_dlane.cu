@@ -20,8 +20,8 @@
 // A CTA takes two adjacent k-slots and up to NU consecutive u_y of one tile
 // over all weight rows of the band; its 2 x NU accumulators (32 FP32 columns
 // each) stay in tensor memory and go to an HBM buffer C[k][d][u_y][32] at the
-// end.  k_lag_dft then forms the lags u_x of every (d, u_y) pair, summing the
-// k-slots in FP32 runs of 16 and FP64 across runs.
+// end.  k_lag_dft (kernels_lag_dft.cu) then forms the lags u_x of every
+// (d, u_y) pair, summing the k-slots in FP32 runs of 16 and FP64 across runs.
 //
 // Roles (448 threads, one CTA per SM):
 //   warps 0-7  A producers: lane l of warp w is difference 32 (w % 4) + l of
@@ -379,66 +379,6 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "n"(TMEM_COLS) : "memory");
 }
 
-// Lags u_x of the k-slot products: for pair (d, u_y) of the difference batch,
-// G[d][u_y][u_x][m] += (1/N_f) sum_{k=1}^{M-1} (C_Re 2 cos(2 pi k u_x / N_f)
-// + C_Im 2 sin(2 pi k u_x / N_f)); slot 0 (the packed real bins) is summed by
-// k_contract_slot0.  Thread (m, g) takes the k-slots k = 1 + g (mod 16) for
-// every u_x (cos is even and sin odd in u_x), in FP32 runs of 16 slots added
-// to FP64; the 16 groups are then summed in FP64 in a fixed order.
-template <int DM>
-__global__ void __launch_bounds__(256)
-k_lag_dft(const int4* __restrict__ pairs, const char* __restrict__ cbuf0, size_t cbuf_ccd, double* __restrict__ g0,
-          size_t g_ccd, int M, int Nf, int L, int dstride, const float2* __restrict__ twD) {
-  constexpr int NMONO = n_mono(DM);
-  constexpr int NG = 16, W5 = (kMaxL - 1) / 2;
-  __shared__ double red[NG][16][kMaxL];
-  const int4 pq = pairs[blockIdx.x];
-  const int ccd = blockIdx.y, w = (L - 1) / 2;
-  const int m = threadIdx.x & 15, grp = threadIdx.x >> 4;
-  const float* C = reinterpret_cast<const float*>(cbuf0 + (size_t)ccd * cbuf_ccd) +
-                   ((int64_t)pq.x * L + (pq.y + w)) * 32;
-  const int64_t kstride = (int64_t)dstride * L * 32;
-  double sp[W5 + 1], sn[W5 + 1];   // u_x = +v and -v
-  float fp[W5 + 1], fn[W5 + 1];
-#pragma unroll
-  for (int v = 0; v <= W5; ++v) { sp[v] = sn[v] = 0.0; fp[v] = fn[v] = 0.f; }
-  int run = 0;
-  for (int k = 1 + grp; k < M; k += NG) {
-    const float* ck = C + k * kstride;
-    const float cr = __ldg(ck + m), ci = __ldg(ck + 16 + m);
-#pragma unroll
-    for (int v = 0; v <= W5; ++v) {
-      if (v > w) break;
-      const float2 t = __ldg(twD + ((k * v) & (Nf - 1)));
-      const float a = cr * t.x, b = ci * t.y;
-      fp[v] += 2.f * (a + b);
-      fn[v] += 2.f * (a - b);
-    }
-    if (++run == 16) {
-#pragma unroll
-      for (int v = 0; v <= W5; ++v) { sp[v] += fp[v]; sn[v] += fn[v]; fp[v] = fn[v] = 0.f; }
-      run = 0;
-    }
-  }
-#pragma unroll
-  for (int v = 0; v <= W5; ++v) {
-    sp[v] += fp[v];
-    sn[v] += fn[v];
-    if (v <= w) {
-      red[grp][m][w + v] = sp[v];
-      red[grp][m][w - v] = sn[v];   // u_x = 0 writes the same value twice
-    }
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < 16 * L; t += blockDim.x) {
-    const int mm = t % 16, xi = t / 16, ux = xi - w;
-    if (mm >= NMONO || ux < pq.z || ux > pq.w) continue;
-    double s = 0.0;
-    for (int g = 0; g < NG; ++g) s += red[g][mm][xi];
-    g0[(size_t)ccd * g_ccd + (((int64_t)pq.x * L + (pq.y + w)) * L + xi) * NMONO + mm] += s / (double)Nf;
-  }
-}
-
 template <int DM>
 static cudaError_t contract_dlane_dm(const sfft_plan_s* p, int batch_index, void* ws) {
   const int job0 = p->dl_first[batch_index], njobs = p->dl_count[batch_index];
@@ -462,35 +402,11 @@ static cudaError_t contract_dlane_dm(const sfft_plan_s* p, int batch_index, void
   return cudaGetLastError();
 }
 
-template <int DM>
-static cudaError_t lag_dft_dm(const sfft_plan_s* p, int batch_index, void* ws) {
-  const int pair0 = p->dlp_first[batch_index], npair = p->dlp_count[batch_index];
-  if (npair <= 0) return cudaSuccess;
-  const int L = p->d.L, B = p->d.batch;
-  const size_t cbuf_ccd = (size_t)p->M * p->d_batch * L * 32 * sizeof(float);
-  const size_t g_ccd = (size_t)p->n_hd * L * L * n_mono(DM);
-  double* g0 = ws_at<double>(ws, p->gkk) + (size_t)batch_index * p->d_batch * L * L * n_mono(DM);
-  dim3 grid(npair, B);
-  k_lag_dft<DM><<<grid, 256, 0, p->stream>>>(p->d_dlpairs + pair0, static_cast<char*>(ws) + p->cbuf.off, cbuf_ccd,
-                                             g0, g_ccd, p->M, p->Nf, L, p->d_batch, (const float2*)p->twD);
-  p->nlaunch += 1;
-  return cudaGetLastError();
-}
-
 cudaError_t launch_contract_dlane(const sfft_plan_s* p, int batch_index, void* ws) {
   switch (p->DM_KK) {
     case 0: return contract_dlane_dm<0>(p, batch_index, ws);
     case 2: return contract_dlane_dm<2>(p, batch_index, ws);
     case 4: return contract_dlane_dm<4>(p, batch_index, ws);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-cudaError_t launch_lag_dft(const sfft_plan_s* p, int batch_index, void* ws) {
-  switch (p->DM_KK) {
-    case 0: return lag_dft_dm<0>(p, batch_index, ws);
-    case 2: return lag_dft_dm<2>(p, batch_index, ws);
-    case 4: return lag_dft_dm<4>(p, batch_index, ws);
     default: return cudaErrorInvalidValue;
   }
 }
