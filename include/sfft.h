@@ -73,8 +73,9 @@ typedef enum {
 
 typedef enum {
   SFFT_PREC_FP64 = 0,        /* FFTs, products, partial sums and apply in FP64 */
-  SFFT_PREC_MIXED = 1        /* FP32 FFTs/products/partials (KK products as three-term TF32 splits on
-                                the tensor cores); FP64 accumulation, solve, refinement */
+  SFFT_PREC_MIXED = 1        /* FP32 FFTs/products/partials (KK products with split operands on the
+                                tensor cores: hi x hi in TF32 plus two BF16 corrections, about
+                                2^-18 per product); FP64 accumulation, solve, refinement */
 } sfft_prec_t;
 
 #define SFFT_FLAG_GRAPH 1u        /* sfft_subtract replays a captured CUDA graph */
