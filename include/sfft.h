@@ -102,6 +102,8 @@ typedef struct {
   int32_t lag_parts;         /* threads sharing the lags of one contraction k-slot: 2 or 3 (0 = auto;
                                 FP32 path only, the FP64 path uses 2) */
   uint32_t flags;            /* SFFT_FLAG_* */
+  int32_t ccd_group;         /* CCDs whose product spectra are held at once (0 = auto: every difference of a
+                                CCD in one pass, as many CCDs as 64 GB of product spectra hold) */
 } sfft_desc_t;
 
 /* Create a plan: validates the descriptor, builds offset/monomial/lag tables,
@@ -122,6 +124,24 @@ int32_t       sfft_plan_engine(sfft_plan_t plan);
 /* Chosen tile shape after planning: out[0] = d_batch, out[1] = rows_per_cta,
  * out[2] = lag parts of the contraction. */
 sfft_status_t sfft_plan_tiles(sfft_plan_t plan, int32_t* out3);
+/* CCDs per product-spectrum pass (the group the offset-difference product
+ * spectra are formed and contracted for at once); -1 for a null plan. */
+int32_t       sfft_plan_ccd_group(sfft_plan_t plan);
+/* Failure detection (no counterpart in the paper).  The FP64 factorisation
+ * separates its block steps by a grid-wide barrier whose wait is bounded:
+ * after `tries` polls (each at least 64 ns) a CTA gives up, every CCD of the
+ * call gets SFFT_ERR_TIMEOUT in `info` and the kernel returns with the
+ * context intact.  The default (about a second) applies after plan creation
+ * and again for tries < 0; small values let a test make the wait run out.
+ * The barrier is a software flag wait with no asynchronous copies or
+ * tensor-core work in flight, so giving up leaves nothing pending. */
+sfft_status_t sfft_plan_set_wait_limit(sfft_plan_t plan, int32_t tries);
+/* Number of device allocations the library's plans (and the plan-time
+ * autotuner) currently hold.  For leak checks: with SFFT_FAIL_ALLOC=n set in
+ * the environment, the n-th device allocation of every sfft_plan call fails
+ * as a full device would (SFFT_ERR_NOMEM, message in sfft_last_error), and the
+ * count returns to its value before the call. */
+int64_t       sfft_debug_live_allocations(void);
 
 /* Normal-matrix assembly (the method's Fourier-domain normal equations):
  *   A = sum_x M_fit Phi Phi^T,  b = sum_x M_fit Phi S'   (FP64 outputs)

@@ -25,7 +25,8 @@ FLAG_PAIR_LANE_CONTRACT = 16
 class Desc(C.Structure):
     _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("L", C.c_int32), ("DK", C.c_int32), ("DB", C.c_int32),
                 ("batch", C.c_int32), ("prec", C.c_int32), ("autotune", C.c_int32), ("d_batch", C.c_int32),
-                ("rows_per_cta", C.c_int32), ("lag_parts", C.c_int32), ("flags", C.c_uint32)]
+                ("rows_per_cta", C.c_int32), ("lag_parts", C.c_int32), ("flags", C.c_uint32),
+                ("ccd_group", C.c_int32)]
 
 
 VP, I32, I64, SZ, DBL = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t, C.c_double
@@ -39,6 +40,9 @@ SIGNATURES = {
     "sfft_workspace_bytes": (SZ, [VP]),
     "sfft_plan_engine": (I32, [VP]),
     "sfft_plan_tiles": (I32, [VP, C.POINTER(I32)]),
+    "sfft_plan_ccd_group": (I32, [VP]),
+    "sfft_plan_set_wait_limit": (I32, [VP, I32]),
+    "sfft_debug_live_allocations": (I64, []),
     "sfft_build_normal": (I32, [VP, VP, VP, VP, VP, VP, VP, VP]),
     "sfft_solve": (I32, [VP, VP, VP, VP, I32, VP, VP, VP, VP, VP]),
     "sfft_apply": (I32, [VP, VP, VP, VP, VP, VP, VP]),
@@ -151,11 +155,12 @@ class Plan:
     mma_sync_contract=True keeps it on the tensor cores through warp-level
     mma.sync instead of tcgen05 (SFFT_FLAG_MMA_SYNC_CONTRACT);
     pair_lane_contract=True runs the tcgen05 contraction with one tensor-memory
-    lane per (difference, u_y) pair (SFFT_FLAG_PAIR_LANE_CONTRACT)."""
+    lane per (difference, u_y) pair (SFFT_FLAG_PAIR_LANE_CONTRACT).
+    ccd_group: CCDs whose product spectra are held at once (0: the plan's choice)."""
 
     def __init__(self, H, W, L, DK, DB, batch=1, prec="mixed", d_batch=0, rows_per_cta=0, autotune=0,
                  graph=False, stream=None, device=None, lag_parts=0, const_ratio=False, fma_contract=False,
-                 mma_sync_contract=False, pair_lane_contract=False):
+                 mma_sync_contract=False, pair_lane_contract=False, ccd_group=0):
         import torch
         self._torch = torch
         lib = load()
@@ -166,7 +171,7 @@ class Plan:
                          (FLAG_GRAPH if graph else 0) | (FLAG_CONST_RATIO if const_ratio else 0) |
                          (FLAG_FMA_CONTRACT if fma_contract else 0) |
                          (FLAG_MMA_SYNC_CONTRACT if mma_sync_contract else 0) |
-                         (FLAG_PAIR_LANE_CONTRACT if pair_lane_contract else 0))
+                         (FLAG_PAIR_LANE_CONTRACT if pair_lane_contract else 0), int(ccd_group))
         h = VP()
         with torch.cuda.device(self.device):
             _check(lib.sfft_plan(C.byref(self.desc), VP(self.stream.cuda_stream), C.byref(h)), "sfft_plan")
@@ -182,6 +187,7 @@ class Plan:
         t = (I32 * 3)()
         _check(lib.sfft_plan_tiles(h, t), "sfft_plan_tiles")
         self.tiles = tuple(int(v) for v in t)
+        self.ccd_group = int(lib.sfft_plan_ccd_group(h))
 
     def __del__(self):
         try:
@@ -190,6 +196,10 @@ class Plan:
                 self.h = None
         except Exception:
             pass
+
+    def set_wait_limit(self, tries):
+        """Polls before the factorisation's grid-barrier wait gives up (< 0: the default, about a second)."""
+        _check(self.lib.sfft_plan_set_wait_limit(self.h, int(tries)), "sfft_plan_set_wait_limit")
 
     def set_stream(self, stream):
         self.stream = stream

@@ -3,7 +3,10 @@
 #include <math.h>
 #include <string.h>
 
+#include <stdlib.h>
+
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <string>
 #include <vector>
@@ -124,7 +127,7 @@ static void build_layout(sfft_plan_s* p) {
   add_region(p->wspec, cur, slab * p->n_wa * B);
   add_region(p->uspec, cur, slab * (p->d.DK + 1) * B);
   add_region(p->rhat, cur, slab * B);
-  add_region(p->phat, cur, slab * p->d_batch * B);
+  add_region(p->phat, cur, slab * p->d_batch * p->ccd_group);
   add_region(p->gkk, cur, sizeof(double) * p->n_hd * LL * n_mono(p->DM_KK) * B);
   add_region(p->gkb, cur, sizeof(double) * LL * n_mono(p->DM_KB) * B);
   add_region(p->gbk, cur, sizeof(double) * LL * n_mono(p->DM_bK) * B);
@@ -137,8 +140,8 @@ static void build_layout(sfft_plan_s* p) {
   // substitutions: the y and x vectors, read by other CTAs as they appear
   add_region(p->swave, cur, sizeof(double) * 2 * p->N * B);
   add_region(p->vec, cur, sizeof(double) * 4 * p->N * B);
-  // lane-per-difference contraction: k-slot products C[k][d_local][u_y][32] per CCD
-  add_region(p->cbuf, cur, p->dl ? sizeof(float) * (size_t)p->M * p->d_batch * p->d.L * 32 * B : 0);
+  // lane-per-difference contraction: k-slot products C[k][d_local][u_y][32] per CCD of a group
+  add_region(p->cbuf, cur, p->dl ? sizeof(float) * (size_t)p->M * p->d_batch * p->d.L * 32 * p->ccd_group : 0);
   add_region(p->theta_off, cur, sizeof(double) * p->N * B);
   p->ws_bytes = cur;
 }
@@ -166,7 +169,7 @@ static void build_jobs(sfft_plan_s* p) {
       for (int i = 0; i < nd; ++i) {
         const int2 d = p->dlist[d0 + i];
         CJob j;
-        j.probe = (int64_t)(p->phat.off + ((size_t)ccd * p->d_batch + i) * slab);
+        j.probe = (int64_t)(p->phat.off + ((size_t)(ccd % p->ccd_group) * p->d_batch + i) * slab);
         j.wts = (int64_t)(p->wspec.off + (size_t)ccd * p->n_wa * slab);
         j.out = (int64_t)(p->gkk.off + sizeof(double) * ((size_t)ccd * p->n_hd + d0 + i) * LL * n_mono(p->DM_KK));
         j.rowflag = (int64_t)(p->rowflag.off + sizeof(int) * (size_t)ccd * p->rf_stride);
@@ -255,7 +258,7 @@ static void build_tc_jobs(sfft_plan_s* p, int NP, int chunk, int cap, int max_nd
     for (int ccd = 0; ccd < B; ++ccd)
       for (const Pat& pt : pats) {
         TcJob j;
-        j.probe = (int64_t)(p->phat.off + (size_t)ccd * p->d_batch * slab);
+        j.probe = (int64_t)(p->phat.off + (size_t)(ccd % p->ccd_group) * p->d_batch * slab);
         j.wts = (int64_t)(p->wspec.off + (size_t)ccd * p->n_wa * slab);
         j.out = (int64_t)(p->gkk.off + sizeof(double) * ((size_t)ccd * p->n_hd + d0) * LL * n_mono(p->DM_KK));
         j.status = (int64_t)(p->status.off + sizeof(int) * (size_t)ccd);
@@ -263,7 +266,7 @@ static void build_tc_jobs(sfft_plan_s* p, int NP, int chunk, int cap, int max_nd
         j.npair = pt.npair;
         j.dj0 = pt.dj0;
         j.nd = pt.nd;
-        j.zp = ccd * p->d_batch;
+        j.zp = (ccd % p->ccd_group) * p->d_batch;
         j.zw = ccd * p->n_wa;
         p->h_tcjobs.push_back(j);
       }
@@ -309,9 +312,9 @@ static void build_dl_jobs(sfft_plan_s* p) {
           // runs of near-equal length
           const int a = ulo + (uhi - ulo + 1) * r / nrun, b = ulo + (uhi - ulo + 1) * (r + 1) / nrun;
           DlJob j;
-          j.cbuf = (int64_t)(p->cbuf.off + (size_t)ccd * cb_ccd);
+          j.cbuf = (int64_t)(p->cbuf.off + (size_t)(ccd % p->ccd_group) * cb_ccd);
           j.status = (int64_t)(p->status.off + sizeof(int) * (size_t)ccd);
-          j.zp = ccd * p->d_batch;
+          j.zp = (ccd % p->ccd_group) * p->d_batch;
           j.zw = ccd * p->n_wa;
           j.d_first = t0;
           j.nlanes = nl;
@@ -324,19 +327,59 @@ static void build_dl_jobs(sfft_plan_s* p) {
   }
 }
 
+// ------------------------------------------------------------------ device allocations
+// Every device allocation of a plan (its tables, and the autotuner's
+// temporary buffers) goes through plan_malloc / plan_free, which count the
+// live ones.  For fault-injection tests, SFFT_FAIL_ALLOC=n in the environment
+// makes the n-th allocation of each sfft_plan call fail (without calling
+// cudaMalloc), as a full device would.
+static std::atomic<long long> g_live_allocs{0};
+static thread_local int g_plan_depth = 0;
+static thread_local long long g_plan_allocs = 0;
+
+cudaError_t sfft::plan_malloc(void** dst, size_t bytes) {
+  *dst = nullptr;
+  const long long n = ++g_plan_allocs;
+  const char* env = getenv("SFFT_FAIL_ALLOC");
+  if (env && *env && atoll(env) == n) {
+    g_last_error = "injected device allocation failure (SFFT_FAIL_ALLOC=" + std::string(env) + ")";
+    return cudaErrorMemoryAllocation;
+  }
+  const cudaError_t e = cudaMalloc(dst, bytes ? bytes : 1);
+  if (e == cudaSuccess) {
+    ++g_live_allocs;
+  } else {
+    *dst = nullptr;
+    g_last_error = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    cudaGetLastError();   // a failed allocation must not poison later calls
+  }
+  return e;
+}
+
+void sfft::plan_free(void* ptr) {
+  if (!ptr) return;
+  cudaFree(ptr);
+  --g_live_allocs;
+}
+
+extern "C" int64_t sfft_debug_live_allocations(void) { return (int64_t)g_live_allocs.load(); }
+
 static void free_plan_device(sfft_plan_s* p) {
-  if (p->d_dljobs) cudaFree(p->d_dljobs);
-  if (p->d_dlpairs) cudaFree(p->d_dlpairs);
-  if (p->d_tcjobs) cudaFree(p->d_tcjobs);
-  if (p->d_tcpairs) cudaFree(p->d_tcpairs);
-  if (p->d_tcdj) cudaFree(p->d_tcdj);
-  if (p->twM) cudaFree(p->twM);
-  if (p->twN) cudaFree(p->twN);
-  if (p->twD) cudaFree(p->twD);
-  if (p->ytab) cudaFree(p->ytab);
-  if (p->d_dlist) cudaFree(p->d_dlist);
-  if (p->d_hdidx) cudaFree(p->d_hdidx);
-  if (p->d_jobs) cudaFree(p->d_jobs);
+  plan_free(p->d_dljobs);
+  plan_free(p->d_dlpairs);
+  plan_free(p->d_tcjobs);
+  plan_free(p->d_tcpairs);
+  plan_free(p->d_tcdj);
+  plan_free(p->twM);
+  plan_free(p->twN);
+  plan_free(p->twD);
+  plan_free(p->ytab);
+  plan_free(p->d_dlist);
+  plan_free(p->d_hdidx);
+  plan_free(p->d_jobs);
+  p->d_dljobs = nullptr; p->d_dlpairs = nullptr; p->d_tcjobs = nullptr; p->d_tcpairs = nullptr;
+  p->d_tcdj = nullptr; p->twM = p->twN = p->twD = p->ytab = nullptr;
+  p->d_dlist = nullptr; p->d_hdidx = nullptr; p->d_jobs = nullptr;
   for (auto& kv : p->graphs) cudaGraphExecDestroy(kv.second);
   p->graphs.clear();
   for (auto& e : p->pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
@@ -348,19 +391,28 @@ static void free_plan_device(sfft_plan_s* p) {
 template <typename T>
 static sfft_status_t upload(void** dst, const std::vector<T>& v) {
   const size_t bytes = sizeof(T) * std::max<size_t>(v.size(), 1);
-  cudaError_t e = cudaMalloc(dst, bytes);
-  if (e != cudaSuccess) { g_last_error = cudaGetErrorString(e); return SFFT_ERR_NOMEM; }
+  if (plan_malloc(dst, bytes) != cudaSuccess) return SFFT_ERR_NOMEM;
   if (!v.empty()) CK(cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
   return SFFT_OK;
 }
 
+static sfft_status_t plan_impl(const sfft_desc_t* desc, void* cuda_stream, sfft_plan_t* out);
+
 extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, sfft_plan_t* out) {
+  // allocations are numbered per outermost call (the autotuner plans inside)
+  if (g_plan_depth++ == 0) g_plan_allocs = 0;
+  const sfft_status_t st = plan_impl(desc, cuda_stream, out);
+  --g_plan_depth;
+  return st;
+}
+
+static sfft_status_t plan_impl(const sfft_desc_t* desc, void* cuda_stream, sfft_plan_t* out) {
   if (!desc || !out) return SFFT_ERR_ARG;
   *out = nullptr;
   const sfft_desc_t d = *desc;
   if (d.H <= 0 || d.W <= 0 || d.batch <= 0 || d.L <= 0) return SFFT_ERR_ARG;
   if (d.prec != SFFT_PREC_FP64 && d.prec != SFFT_PREC_MIXED) return SFFT_ERR_ARG;
-  if (d.DK < 0 || d.DB < 0 || d.d_batch < 0 || d.rows_per_cta < 0) return SFFT_ERR_ARG;
+  if (d.DK < 0 || d.DB < 0 || d.d_batch < 0 || d.rows_per_cta < 0 || d.ccd_group < 0) return SFFT_ERR_ARG;
   if (d.lag_parts < 0 || d.lag_parts > 3) return SFFT_ERR_ARG;
   if ((d.L & 1) == 0 || d.L > kMaxL) return SFFT_ERR_UNSUPPORTED;
   if (d.flags & ~(SFFT_FLAG_GRAPH | SFFT_FLAG_CONST_RATIO | SFFT_FLAG_FMA_CONTRACT | SFFT_FLAG_MMA_SYNC_CONTRACT |
@@ -400,12 +452,13 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
       }
   p->n_hd = (int)p->dlist.size();
   const size_t slab = (size_t)d.H * p->M * 2 * p->elem;
-  // product spectra of up to 64 GB per plan (GB300: 288 GB of HBM3e); a
-  // batch of CCDs then still takes a few dozen differences per pass, enough
-  // to fill the tensor-core contraction's 128-pair patterns
+  // product spectra of up to 64 GB per plan (GB300: 288 GB of HBM3e).  The
+  // product-spectrum stage runs per group of CCDs with every difference in
+  // one pass when one CCD's spectra fit (7.4 GB at 2048 x 4096): a 60-CCD
+  // exposure then runs in groups of 8 on the same contraction engine as a
+  // single CCD.  Otherwise one CCD at a time with as many differences as fit.
   const size_t budget = size_t(64) << 30;
-  const int d_batch_max =
-      (int)std::max<size_t>(1, std::min<size_t>(budget / (slab * (size_t)d.batch), (size_t)p->n_hd));
+  const int d_batch_max = (int)std::max<size_t>(1, std::min<size_t>(budget / slab, (size_t)p->n_hd));
   int tuned_db = 0, tuned_rows = 0, tuned_parts = 0;
   if (d.autotune && (d.d_batch == 0 || d.rows_per_cta == 0 || d.lag_parts == 0)) {
     const sfft_status_t ts = autotune_tiles(d, (cudaStream_t)cuda_stream, d_batch_max, &tuned_db, &tuned_rows,
@@ -419,6 +472,8 @@ extern "C" sfft_status_t sfft_plan(const sfft_desc_t* desc, void* cuda_stream, s
   else p->d_batch = tuned_db > 0 ? std::min(tuned_db, p->n_hd) : d_batch_max;
   if (d.rows_per_cta > 0) p->rows_per_cta = d.rows_per_cta;
   else p->rows_per_cta = tuned_rows > 0 ? tuned_rows : std::min(d.H, 1024);
+  p->ccd_group = (int)std::max<size_t>(1, std::min<size_t>(budget / (slab * (size_t)p->d_batch), (size_t)d.batch));
+  if (d.ccd_group > 0) p->ccd_group = std::min(d.ccd_group, d.batch);
   if (d.lag_parts > 0) p->csplit = d.lag_parts;
   else p->csplit = tuned_parts > 0 ? tuned_parts : 2;
   if (p->fp64) p->csplit = 2;
@@ -495,6 +550,12 @@ extern "C" sfft_status_t sfft_plan_set_stream(sfft_plan_t p, void* s) {
   return SFFT_OK;
 }
 
+extern "C" sfft_status_t sfft_plan_set_wait_limit(sfft_plan_t p, int32_t tries) {
+  if (!p) return SFFT_ERR_ARG;
+  p->bar_spin_limit = tries < 0 ? (1 << 24) : tries;
+  return SFFT_OK;
+}
+
 extern "C" int64_t sfft_num_unknowns(sfft_plan_t p) { return p ? p->N : -1; }
 extern "C" size_t sfft_workspace_bytes(sfft_plan_t p) { return p ? p->ws_bytes : 0; }
 extern "C" int32_t sfft_plan_engine(sfft_plan_t p) {
@@ -504,6 +565,8 @@ extern "C" int32_t sfft_plan_engine(sfft_plan_t p) {
   if (!p->umma) return 2;
   return p->dl ? 4 : 3;
 }
+extern "C" int32_t sfft_plan_ccd_group(sfft_plan_t p) { return p ? p->ccd_group : -1; }
+
 extern "C" sfft_status_t sfft_plan_tiles(sfft_plan_t p, int32_t* o) {
   if (!p || !o) return SFFT_ERR_ARG;
   o[0] = p->d_batch; o[1] = p->rows_per_cta; o[2] = p->csplit;
@@ -536,26 +599,34 @@ static sfft_status_t build_normal_impl(sfft_plan_t p, const float* R, const floa
     CK(launch_contract(p, p->DM_KB, p->kb_first, p->kb_count, p->rows_per_cta, p->csplit, ws));
     CK(launch_contract(p, p->DM_bK, p->bk_first, p->bk_count, p->rows_per_cta, p->csplit, ws));
   }
-  for (size_t ib = 0; ib < p->kk_first.size(); ++ib) {
-    const int d0 = (int)ib * p->d_batch;
-    const int nd = std::min(p->d_batch, p->n_hd - d0);
-    {
-      Phase ph(p, SFFT_PROF_FFT_PROD);
-      CK(launch_rfft_prod(p, d0, nd, ws));
-    }
-    {
-      Phase ph(p, SFFT_PROF_CONTRACT_KK);
-      if (p->tc) {
-        if (p->dl) CK(launch_contract_dlane(p, (int)ib, ws));
-        else CK(p->umma ? launch_contract_umma(p, (int)ib, ws) : launch_contract_tc(p, (int)ib, ws));
-      } else {
-        CK(launch_contract(p, p->DM_KK, p->kk_first[ib], p->kk_count[ib], p->rows_per_cta, p->csplit, ws));
+  // product spectra and their contraction: per group of ccd_group CCDs, per d-batch
+  const int B = p->d.batch, G = p->ccd_group;
+  for (int c0 = 0; c0 < B; c0 += G) {
+    const int nc = std::min(G, B - c0);
+    for (size_t ib = 0; ib < p->kk_first.size(); ++ib) {
+      const int d0 = (int)ib * p->d_batch;
+      const int nd = std::min(p->d_batch, p->n_hd - d0);
+      // the d-batch's KK jobs are ordered CCD-major with the same count per CCD
+      const int jpc = p->kk_count[ib] / B;
+      const int kj0 = p->kk_first[ib] + c0 * jpc, kjn = nc * jpc;
+      {
+        Phase ph(p, SFFT_PROF_FFT_PROD);
+        CK(launch_rfft_prod(p, c0, nc, d0, nd, ws));
       }
-    }
-    if (p->tc) {
-      Phase ph(p, SFFT_PROF_LAG_DFT);
-      if (p->dl) CK(launch_lag_dft(p, (int)ib, ws));
-      CK(launch_contract_slot0(p, p->DM_KK, p->kk_first[ib], p->kk_count[ib], ws));
+      {
+        Phase ph(p, SFFT_PROF_CONTRACT_KK);
+        if (p->tc) {
+          if (p->dl) CK(launch_contract_dlane(p, (int)ib, c0, nc, ws));
+          else CK(p->umma ? launch_contract_umma(p, (int)ib, c0, nc, ws) : launch_contract_tc(p, (int)ib, c0, nc, ws));
+        } else {
+          CK(launch_contract(p, p->DM_KK, kj0, kjn, p->rows_per_cta, p->csplit, ws));
+        }
+      }
+      if (p->tc) {
+        Phase ph(p, SFFT_PROF_LAG_DFT);
+        if (p->dl) CK(launch_lag_dft(p, (int)ib, c0, nc, ws));
+        CK(launch_contract_slot0(p, p->DM_KK, kj0, kjn, ws));
+      }
     }
   }
   {

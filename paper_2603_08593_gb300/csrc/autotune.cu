@@ -37,7 +37,7 @@ std::string tune_key(const sfft_desc_t& d, int device) {
   char buf[160];
   cudaDeviceProp prop{};
   cudaGetDeviceProperties(&prop, device);
-  snprintf(buf, sizeof(buf), "v2_sm%d%d_%dSM_H%d_W%d_L%d_DK%d_DB%d_B%d_P%d", prop.major, prop.minor,
+  snprintf(buf, sizeof(buf), "v3_sm%d%d_%dSM_H%d_W%d_L%d_DK%d_DB%d_B%d_P%d", prop.major, prop.minor,
            prop.multiProcessorCount, d.H, d.W, d.L, d.DK, d.DB, d.batch, d.prec);
   return buf;
 }
@@ -80,8 +80,8 @@ __global__ void k_tune_fill(float* R, float* S, int64_t n) {
 
 struct DevBuf {
   void* p = nullptr;
-  ~DevBuf() { if (p) cudaFree(p); }
-  bool alloc(size_t n) { return cudaMalloc(&p, n ? n : 1) == cudaSuccess; }
+  ~DevBuf() { plan_free(p); }
+  bool alloc(size_t n) { return plan_malloc(&p, n) == cudaSuccess; }
 };
 
 // time one candidate; returns ms per CCD or a negative value on failure
@@ -91,6 +91,7 @@ double time_candidate(const sfft_desc_t& base, cudaStream_t s, int d_batch, int 
   d.flags = 0;
   d.batch = std::min(base.batch, 2);
   d.d_batch = d_batch;
+  d.ccd_group = 0;
   d.rows_per_cta = rows;
   d.lag_parts = parts;
   sfft_plan_t p = nullptr;

@@ -380,33 +380,33 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
 }
 
 template <int DM>
-static cudaError_t contract_dlane_dm(const sfft_plan_s* p, int batch_index, void* ws) {
+static cudaError_t contract_dlane_dm(const sfft_plan_s* p, int batch_index, int c0, int nc, void* ws) {
   const int job0 = p->dl_first[batch_index], njobs = p->dl_count[batch_index];
-  if (njobs <= 0) return cudaSuccess;
+  if (njobs <= 0 || nc <= 0) return cudaSuccess;
   const int H = p->d.H, L = p->d.L, B = p->d.batch;
   const size_t smem = sizeof(DSmem);
   auto kern = k_contract_dlane<DM>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const int ntot = p->d_batch * B;
-  const int pz = std::min(128, ntot);   // differences per probe box
+  const int ntot = p->d_batch * p->ccd_group;   // product spectra held: one d-batch of a CCD group
+  const int pz = std::min(128, ntot);           // differences per probe box
   CUtensorMap mp, mv;
   char* base = static_cast<char*>(ws);
   if (!make_map_blk(&mp, base + p->phat.off, p->M, H, ntot, 4, PBR, pz) ||
       !make_map(&mv, base + p->wspec.off, p->M, H, p->n_wa * B, 4, VR, 1))
     return cudaErrorInvalidValue;
   const int per_ccd = njobs / B;   // jobs are ordered CCD-major, the same count per CCD
-  dim3 grid(per_ccd, p->M / 2, B);
-  kern<<<grid, NTHREADS, smem, p->stream>>>(mp, mv, p->d_dljobs + job0, (char*)ws, H, L, p->d_batch, pz,
-                                            (const float*)p->ytab);
+  dim3 grid(per_ccd, p->M / 2, nc);
+  kern<<<grid, NTHREADS, smem, p->stream>>>(mp, mv, p->d_dljobs + job0 + (int64_t)c0 * per_ccd, (char*)ws, H, L,
+                                            p->d_batch, pz, (const float*)p->ytab);
   p->nlaunch += 1;
   return cudaGetLastError();
 }
 
-cudaError_t launch_contract_dlane(const sfft_plan_s* p, int batch_index, void* ws) {
+cudaError_t launch_contract_dlane(const sfft_plan_s* p, int batch_index, int c0, int nc, void* ws) {
   switch (p->DM_KK) {
-    case 0: return contract_dlane_dm<0>(p, batch_index, ws);
-    case 2: return contract_dlane_dm<2>(p, batch_index, ws);
-    case 4: return contract_dlane_dm<4>(p, batch_index, ws);
+    case 0: return contract_dlane_dm<0>(p, batch_index, c0, nc, ws);
+    case 2: return contract_dlane_dm<2>(p, batch_index, c0, nc, ws);
+    case 4: return contract_dlane_dm<4>(p, batch_index, c0, nc, ws);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -338,8 +338,10 @@ static cudaError_t contract_tc_dm(const sfft_plan_s* p, int job0, int njobs, voi
   return cudaGetLastError();
 }
 
-cudaError_t launch_contract_tc(const sfft_plan_s* p, int batch_index, void* ws) {
-  const int job0 = p->tc_first[batch_index], njobs = p->tc_count[batch_index];
+cudaError_t launch_contract_tc(const sfft_plan_s* p, int batch_index, int c0, int nc, void* ws) {
+  // jobs are ordered CCD-major with the same count per CCD: the group's jobs are one run
+  const int per_ccd = p->tc_count[batch_index] / p->d.batch;
+  const int job0 = p->tc_first[batch_index] + c0 * per_ccd, njobs = nc * per_ccd;
   if (njobs <= 0) return cudaSuccess;
   switch (p->DM_KK) {
     case 0: return contract_tc_dm<0, kTcNT, kTcRowCap>(p, job0, njobs, ws);

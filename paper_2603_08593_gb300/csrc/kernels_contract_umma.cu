@@ -393,7 +393,7 @@ static cudaError_t contract_umma_dm(const sfft_plan_s* p, int job0, int njobs, v
   // job names its CCD's first slab
   CUtensorMap mp, mv;
   char* base = static_cast<char*>(ws);
-  if (!make_map(&mp, base + p->phat.off, p->M, H, p->d_batch * B, BOXW, rbox, 1) ||
+  if (!make_map(&mp, base + p->phat.off, p->M, H, p->d_batch * p->ccd_group, BOXW, rbox, 1) ||
       !make_map(&mv, base + p->wspec.off, p->M, H, p->n_wa * B, BOXW, CH, 1))
     return cudaErrorInvalidValue;
   for (int j0 = 0; j0 < njobs; j0 += 65535) {
@@ -406,8 +406,10 @@ static cudaError_t contract_umma_dm(const sfft_plan_s* p, int job0, int njobs, v
   return cudaGetLastError();
 }
 
-cudaError_t launch_contract_umma(const sfft_plan_s* p, int batch_index, void* ws) {
-  const int job0 = p->tc_first[batch_index], njobs = p->tc_count[batch_index];
+cudaError_t launch_contract_umma(const sfft_plan_s* p, int batch_index, int c0, int nc, void* ws) {
+  // jobs are ordered CCD-major with the same count per CCD: the group's jobs are one run
+  const int per_ccd = p->tc_count[batch_index] / p->d.batch;
+  const int job0 = p->tc_first[batch_index] + c0 * per_ccd, njobs = nc * per_ccd;
   if (njobs <= 0) return cudaSuccess;
   switch (p->DM_KK) {
     case 0: return contract_umma_dm<0>(p, job0, njobs, ws);

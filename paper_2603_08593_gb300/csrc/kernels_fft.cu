@@ -386,8 +386,8 @@ static cudaError_t run_weight(const sfft_plan_s* p, const uint8_t* Mfit, const f
   }
 
 template <typename T, int M>
-static cudaError_t run_prod_dy(const sfft_plan_s* p, const T* Rm, int d0, int nd, c_t<T>* out, int64_t slab_stride,
-                               int64_t ccd_stride) {
+static cudaError_t run_prod_dy(const sfft_plan_s* p, const T* Rm, int nc, int d0, int nd, c_t<T>* out,
+                               int64_t slab_stride, int64_t ccd_stride) {
   using F = RowFFT<T, M>;
   const size_t smem = F::smem_bytes() + sizeof(T) * (size_t)(2 * (2 * M) + 32);
   // product spectra [d][y][k], or k-slot-blocked [d][k / 16][y][k % 16] for
@@ -397,14 +397,14 @@ static cudaError_t run_prod_dy(const sfft_plan_s* p, const T* Rm, int d0, int nd
   const int L = p->d.L;
   auto dy_of = [L](int id) { return id < L ? 0 : 1 + (id - L) / (2 * L - 1); };
   const int ndy = dy_of(d0 + nd - 1) - dy_of(d0) + 1;
-  dim3 grid(p->d.H, ndy, p->d.batch);
+  dim3 grid(p->d.H, ndy, nc);
   kern<<<grid, kFftThreads, smem, p->stream>>>(Rm, p->d.H, p->d.W, L, d0, nd, out, slab_stride, ccd_stride,
                                                (const c_t<T>*)p->twM, (const c_t<T>*)p->twN);
   p->nlaunch += 1;
   return cudaGetLastError();
 }
 
-static cudaError_t run_prod_dy_w(const sfft_plan_s* p, const float* Rm, int d0, int nd, float2* out,
+static cudaError_t run_prod_dy_w(const sfft_plan_s* p, const float* Rm, int nc, int d0, int nd, float2* out,
                                  int64_t slab_stride, int64_t ccd_stride) {
   constexpr int NF = 2048;
   const size_t smem = sizeof(float) * (size_t)(2 * NF + 32) + sizeof(float2) * 8 * 32 * 33;
@@ -413,7 +413,7 @@ static cudaError_t run_prod_dy_w(const sfft_plan_s* p, const float* Rm, int d0, 
   const int L = p->d.L;
   auto dy_of = [L](int id) { return id < L ? 0 : 1 + (id - L) / (2 * L - 1); };
   const int ndy = dy_of(d0 + nd - 1) - dy_of(d0) + 1;
-  dim3 grid((p->d.H + kWarpRowsPerCta - 1) / kWarpRowsPerCta, ndy, p->d.batch);
+  dim3 grid((p->d.H + kWarpRowsPerCta - 1) / kWarpRowsPerCta, ndy, nc);
   kern<<<grid, 256, smem, p->stream>>>(Rm, p->d.H, p->d.W, L, d0, nd, out, slab_stride, ccd_stride,
                                        (const float2*)p->twM, (const float2*)p->twN);
   p->nlaunch += 1;
@@ -421,15 +421,16 @@ static cudaError_t run_prod_dy_w(const sfft_plan_s* p, const float* Rm, int d0, 
 }
 
 template <typename T>
-static cudaError_t prod_T(const sfft_plan_s* p, int d0, int nd, void* ws) {
+static cudaError_t prod_T(const sfft_plan_s* p, int c0, int nc, int d0, int nd, void* ws) {
+  // R_m of the group's CCDs in; their product spectra to the group-local slabs
   const int64_t HM = (int64_t)p->d.H * p->M;
-  const T* Rm = ws_at<T>(ws, p->rm);
+  const T* Rm = ws_at<T>(ws, p->rm) + (int64_t)c0 * p->d.H * p->d.W;
   c_t<T>* out = ws_at<c_t<T>>(ws, p->phat);
   if constexpr (sizeof(T) == 4) {
     if (p->M == 1024)
-      return run_prod_dy_w(p, (const float*)Rm, d0, nd, (float2*)out, HM, HM * p->d_batch);
+      return run_prod_dy_w(p, (const float*)Rm, nc, d0, nd, (float2*)out, HM, HM * p->d_batch);
   }
-  SFFT_DISPATCH_M(p->M, (run_prod_dy<T, M>(p, Rm, d0, nd, out, HM, HM * p->d_batch)))
+  SFFT_DISPATCH_M(p->M, (run_prod_dy<T, M>(p, Rm, nc, d0, nd, out, HM, HM * p->d_batch)))
 }
 
 template <typename T>
@@ -451,8 +452,8 @@ static cudaError_t weights_T(const sfft_plan_s* p, const float* S, const void* e
                                           HM * nslab)))
 }
 
-cudaError_t launch_rfft_prod(const sfft_plan_s* p, int d0, int nd, void* ws) {
-  return p->fp64 ? prod_T<double>(p, d0, nd, ws) : prod_T<float>(p, d0, nd, ws);
+cudaError_t launch_rfft_prod(const sfft_plan_s* p, int c0, int nc, int d0, int nd, void* ws) {
+  return p->fp64 ? prod_T<double>(p, c0, nc, d0, nd, ws) : prod_T<float>(p, c0, nc, d0, nd, ws);
 }
 cudaError_t launch_rfft_rm(const sfft_plan_s* p, void* ws) {
   return p->fp64 ? rm_T<double>(p, ws) : rm_T<float>(p, ws);

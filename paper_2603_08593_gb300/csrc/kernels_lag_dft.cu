@@ -15,6 +15,7 @@ template <int DM>
 __global__ void __launch_bounds__(256)
 k_lag_dft(const int4* __restrict__ pairs, const char* __restrict__ cbuf0, size_t cbuf_ccd, double* __restrict__ g0,
           size_t g_ccd, int M, int Nf, int L, int dstride, const float2* __restrict__ twD) {
+  // blockIdx.y: the CCD within its group (k-slot products); g0 points at the group's first CCD
   constexpr int NMONO = n_mono(DM);
   constexpr int NG = 16, W5 = (kMaxL - 1) / 2;
   __shared__ double red[NG][16][kMaxL];
@@ -75,25 +76,25 @@ k_lag_dft(const int4* __restrict__ pairs, const char* __restrict__ cbuf0, size_t
 }
 
 template <int DM>
-static cudaError_t lag_dft_dm(const sfft_plan_s* p, int batch_index, void* ws) {
+static cudaError_t lag_dft_dm(const sfft_plan_s* p, int batch_index, int c0, int nc, void* ws) {
   const int pair0 = p->dlp_first[batch_index], npair = p->dlp_count[batch_index];
-  if (npair <= 0) return cudaSuccess;
-  const int L = p->d.L, B = p->d.batch;
+  if (npair <= 0 || nc <= 0) return cudaSuccess;
+  const int L = p->d.L;
   const size_t cbuf_ccd = (size_t)p->M * p->d_batch * L * 32 * sizeof(float);
   const size_t g_ccd = (size_t)p->n_hd * L * L * n_mono(DM);
-  double* g0 = ws_at<double>(ws, p->gkk) + (size_t)batch_index * p->d_batch * L * L * n_mono(DM);
-  dim3 grid(npair, B);
+  double* g0 = ws_at<double>(ws, p->gkk) + (size_t)c0 * g_ccd + (size_t)batch_index * p->d_batch * L * L * n_mono(DM);
+  dim3 grid(npair, nc);
   k_lag_dft<DM><<<grid, 256, 0, p->stream>>>(p->d_dlpairs + pair0, static_cast<char*>(ws) + p->cbuf.off, cbuf_ccd,
                                              g0, g_ccd, p->M, p->Nf, L, p->d_batch, (const float2*)p->twD);
   p->nlaunch += 1;
   return cudaGetLastError();
 }
 
-cudaError_t launch_lag_dft(const sfft_plan_s* p, int batch_index, void* ws) {
+cudaError_t launch_lag_dft(const sfft_plan_s* p, int batch_index, int c0, int nc, void* ws) {
   switch (p->DM_KK) {
-    case 0: return lag_dft_dm<0>(p, batch_index, ws);
-    case 2: return lag_dft_dm<2>(p, batch_index, ws);
-    case 4: return lag_dft_dm<4>(p, batch_index, ws);
+    case 0: return lag_dft_dm<0>(p, batch_index, c0, nc, ws);
+    case 2: return lag_dft_dm<2>(p, batch_index, c0, nc, ws);
+    case 4: return lag_dft_dm<4>(p, batch_index, c0, nc, ws);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -219,11 +219,11 @@ k_chol_init(const double* __restrict__ A, double* __restrict__ Lf, double* __res
 // L2-coherent loads (ld.global.cg).
 struct GridBar { unsigned count, gen, abort, pad; };
 
-constexpr int kBarSpin = 1 << 24;   // x >= 64 ns per try: about a second
+constexpr int kBarSpin = 1 << 24;   // x >= 64 ns per try: about a second (the default wait limit)
 constexpr int PRW = 8;              // rows per piece of the panel and trailing updates
 constexpr int NTRI = NBK * (NBK + 1) / 2;
 
-__device__ bool grid_sync_bounded(GridBar* bar, int* flag_sh) {
+__device__ bool grid_sync_bounded(GridBar* bar, int* flag_sh, int spin_limit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* vgen = &bar->gen;
@@ -238,7 +238,7 @@ __device__ bool grid_sync_bounded(GridBar* bar, int* flag_sh) {
       atomicAdd(&bar->gen, 1u);
     } else {
       for (int it = 0; *vgen == g; ++it) {
-        if (*vab != 0u || it > kBarSpin) { ok = false; break; }
+        if (*vab != 0u || it >= spin_limit) { ok = false; break; }
         __nanosleep(64);
       }
     }
@@ -336,7 +336,7 @@ __device__ void store_block(const CholSmem& S, double* __restrict__ l, int N, in
 
 __global__ void __launch_bounds__(256)
 k_chol_coop(double* __restrict__ Lf, double* __restrict__ dinv, int* __restrict__ status, int N, int B,
-            GridBar* __restrict__ bar) {
+            GridBar* __restrict__ bar, int spin_limit) {
   __shared__ CholSmem S;
   const int nblk = (N + NBK - 1) / NBK;
   const int64_t NN = (int64_t)N * N;
@@ -357,7 +357,7 @@ k_chol_coop(double* __restrict__ Lf, double* __restrict__ dinv, int* __restrict_
     factor_block(S, status + ccd);
     store_block(S, Lf + ccd * NN, N, 0, min(NBK, N));
   }
-  bool ok = grid_sync_bounded(bar, &S.flag);
+  bool ok = grid_sync_bounded(bar, &S.flag, spin_limit);
   for (int k = 0; ok && k < nblk; ++k) {
     const int kb = k * NBK, nb = min(NBK, N - kb), rem = N - kb - nb;
     if (rem <= 0) break;   // uniform: the last block has no panel
@@ -387,7 +387,7 @@ k_chol_coop(double* __restrict__ Lf, double* __restrict__ dinv, int* __restrict_
         if (p0 + warp < N && lane < nb) l[(int64_t)(p0 + warp) * N + kb + lane] = x;
       }
     }
-    if (!(ok = grid_sync_bounded(bar, &S.flag))) break;
+    if (!(ok = grid_sync_bounded(bar, &S.flag, spin_limit))) break;
     // (C) the next diagonal block of every CCD (one CTA each: update and
     // factor), then 8 x 32 pieces of the other trailing tiles
     const int ntile = T * (T + 1) / 2;
@@ -448,7 +448,7 @@ k_chol_coop(double* __restrict__ Lf, double* __restrict__ dinv, int* __restrict_
         l[(int64_t)gi * N + gj] = __ldcg(l + (int64_t)gi * N + gj) - (s0 + s1);
       }
     }
-    ok = grid_sync_bounded(bar, &S.flag);
+    ok = grid_sync_bounded(bar, &S.flag, spin_limit);
   }
   // inverses of the diagonal factors for the substitutions, all at once
   for (int item = blockIdx.x; ok && item < B * nblk; item += G) {
@@ -644,7 +644,10 @@ __global__ void k_info(const int* __restrict__ status, int32_t* __restrict__ inf
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= batch) return;
   const int s = status[c];
-  info[c] = (s & 2) ? SFFT_ERR_NONFINITE : ((s & 1) ? SFFT_ERR_SINGULAR : (s & 4 ? SFFT_ERR_TIMEOUT : SFFT_OK));
+  // a wait that gave up leaves the normal matrix or the factor partly
+  // unwritten, which then also looks singular or non-finite: the time-out is
+  // the cause and is reported first
+  info[c] = (s & 4) ? SFFT_ERR_TIMEOUT : ((s & 2) ? SFFT_ERR_NONFINITE : ((s & 1) ? SFFT_ERR_SINGULAR : SFFT_OK));
 }
 
 __global__ void k_kernel_at(const double* __restrict__ theta, double* __restrict__ K, int L, int DK, int NK, int NB,
@@ -738,7 +741,8 @@ cudaError_t launch_cholesky(const sfft_plan_s* p, const double* A, void* ws) {
   const int T0 = (N - NBK + NBK - 1) / NBK;
   const int want = std::max(B, B + B * std::max(T0 * (T0 + 1) / 2 - 1, 1) * (NBK / PRW));
   const int grid = coop_grid((const void*)k_chol_coop, want, B);
-  void* args[] = {&Lf, &dinv, &status, &N, &B, &bar};
+  int spin = p->bar_spin_limit;
+  void* args[] = {&Lf, &dinv, &status, &N, &B, &bar, &spin};
   e = launch_coop((const void*)k_chol_coop, grid, p->stream, args);
   p->nlaunch += 2;
   if (e != cudaSuccess) return e;

@@ -71,11 +71,13 @@ struct sfft_plan_s {
   int n_hd = 0;                       // half-plane differences
   std::vector<int2> dlist;            // (dy, dx) per half-plane difference
   int d_batch = 0, rows_per_cta = 0, csplit = 2;   // csplit: lag parts per (k-slot, group) in the contraction
+  int ccd_group = 1;                  // CCDs whose product spectra of one d-batch are held at once
   bool tc = false;                    // KK contraction on the tensor cores (FP32 path)
   bool umma = false;                  // ... with tcgen05 (else mma.sync)
   bool dl = false;                    // ... with one tensor-memory lane per difference (else per (d, u_y) pair)
   int tc_rows = 0;                    // weight rows per CTA of the tensor-core contraction
   double tuned_ms = 0.0;              // autotuned build_normal time per CCD (0: not tuned)
+  int bar_spin_limit = 1 << 24;       // tries of the factorisation's grid-barrier wait (about a second)
   size_t elem = 4;                    // sizeof(T)
   // plan-owned constant device tables
   void* twM = nullptr;                // c_t [M]       exp(-2 pi i j / M)
@@ -130,13 +132,16 @@ cudaError_t launch_moments(const sfft_plan_s* p, const float* S, const void* eim
 cudaError_t launch_rfft_rm(const sfft_plan_s* p, void* ws);
 cudaError_t launch_rfft_weights(const sfft_plan_s* p, const float* S, const void* eimg, int a0, int na,
                                 void* out, int nslab, void* ws);
-cudaError_t launch_rfft_prod(const sfft_plan_s* p, int d0, int nd, void* ws);
+// The product-spectrum stage runs per group of ccd_group CCDs: c0 is the
+// group's first CCD, nc its size; product spectra and k-slot products are
+// indexed within the group, everything else by the CCD's batch index.
+cudaError_t launch_rfft_prod(const sfft_plan_s* p, int c0, int nc, int d0, int nd, void* ws);
 cudaError_t launch_contract(const sfft_plan_s* p, int DM, int job0, int njobs, int rows_per_cta, int lag_parts,
                             void* ws);
-cudaError_t launch_contract_tc(const sfft_plan_s* p, int batch_index, void* ws);
-cudaError_t launch_contract_umma(const sfft_plan_s* p, int batch_index, void* ws);
-cudaError_t launch_contract_dlane(const sfft_plan_s* p, int batch_index, void* ws);
-cudaError_t launch_lag_dft(const sfft_plan_s* p, int batch_index, void* ws);
+cudaError_t launch_contract_tc(const sfft_plan_s* p, int batch_index, int c0, int nc, void* ws);
+cudaError_t launch_contract_umma(const sfft_plan_s* p, int batch_index, int c0, int nc, void* ws);
+cudaError_t launch_contract_dlane(const sfft_plan_s* p, int batch_index, int c0, int nc, void* ws);
+cudaError_t launch_lag_dft(const sfft_plan_s* p, int batch_index, int c0, int nc, void* ws);
 cudaError_t launch_contract_slot0(const sfft_plan_s* p, int DM, int job0, int njobs, void* ws);
 cudaError_t launch_scatter(const sfft_plan_s* p, double* A, double* b, void* ws, bool rhs_only, double* rhs_out);
 cudaError_t launch_cholesky(const sfft_plan_s* p, const double* A, void* ws);
@@ -157,6 +162,9 @@ cudaError_t launch_theta_units_raw(cudaStream_t s, const double* src, double* ds
 cudaError_t launch_apply_raw(cudaStream_t s, bool fp64, const float* R, const float* S, const double* theta_off,
                              const double* sky, float* D, int H, int W, int L, int DK, int DB, int batch);
 void set_last_error(const char* msg);
+// Device allocations of plans and the autotuner (counted; see api.cu).
+cudaError_t plan_malloc(void** dst, size_t bytes);
+void plan_free(void* ptr);
 // Times candidate (d_batch, rows_per_cta) on synthetic data (autotune.cu).
 sfft_status_t autotune_tiles(const sfft_desc_t& d, cudaStream_t s, int d_batch_max, int* d_batch, int* rows_per_cta,
                              int* lag_parts, double* ms_per_ccd);

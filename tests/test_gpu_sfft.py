@@ -119,6 +119,11 @@ def test_batch_equals_single_and_graph_replay():
     imgs = [small_pair(64, 80, seed=3000 + i, mask_fraction=0.02 * i) for i in range(3)]
     refs, A, b, th, info, D = _run(None, L, DK, DB, "mixed", batch_imgs=imgs)
     for i in range(3):
+        # every CCD of the batch against its own oracle fit, at the stated error bars
+        assert info[i] == 0
+        assert np.abs(A[i] - refs[i]["A"]).max() <= 2e-5 * np.abs(refs[i]["A"]).max()
+        assert O.kernel_coef_rel_err(th[i], refs[i]["theta_orig"], L, DK, DB) <= 1e-5
+        assert np.abs(D[i] - refs[i]["D"]).max() <= 1e-3 * SIGMA_SKY
         _, A1, b1, th1, _, D1 = _run(imgs[i], L, DK, DB, "mixed")
         assert np.array_equal(A[i], A1[0]) or np.abs(A[i] - A1[0]).max() <= 1e-12 * np.abs(A1).max()
         assert np.abs(th[i] - th1[0]).max() <= 1e-12 * np.abs(th1).max()
@@ -138,6 +143,15 @@ def test_batch_equals_single_and_graph_replay():
     s.synchronize()
     assert torch.allclose(og2["theta"], oe["theta"], rtol=1e-9, atol=1e-12)
     assert torch.allclose(og2["D"], oe["D"], rtol=1e-5, atol=1e-4)
+    # the graph-replayed batch (sky offsets estimated on the GPU) against the oracle: the kernel, and D
+    # away from the w-pixel border, are independent of the offsets
+    w = (L - 1) // 2
+    inner = (slice(w, -w), slice(w, -w))
+    thg, Dg, ig = og2["theta"].cpu().numpy(), og2["D"].cpu().numpy(), og2["info"].cpu().numpy()
+    for i in range(3):
+        assert ig[i] == 0
+        assert O.kernel_coef_rel_err(thg[i], refs[i]["theta_orig"], L, DK, DB) <= 1e-5
+        assert np.abs(Dg[i][inner] - refs[i]["D"][inner]).max() <= 1e-3 * SIGMA_SKY
 
 
 def test_sky_estimate_gives_same_kernel_and_interior_difference():
