@@ -93,6 +93,40 @@ def n_mono(D):
     return (D + 1) * (D + 2) // 2
 
 
+def phase_bytes(H, W, L, DK, DB, refine=1):
+    """Algorithmic HBM bytes per CCD of each streaming phase: every kernel's
+    inputs read once and its outputs written once (FP32 path).  A spectrum
+    slab is H x M complex64 with M = max(64, 2^ceil(log2 W)) / 2."""
+    M = max(64, 1 << (W - 1).bit_length()) // 2
+    px, slab = H * W, H * M * 8
+    n_hd = half_plane_differences(L)
+    n_wa = 2 * DK + 1
+    return {
+        # sky sums (R, S, bad), masks and R_m (R, S, bad in; good, R_m out), two
+        # erosion passes (1 B in, 1 B out each), background moments (M_fit, S;
+        # and M_fit, e per refinement step)
+        "prep": px * (9 + 14 + 4 + 5 + 5 * refine),
+        # weight spectra (M_fit in), right-hand-side spectra (M_fit, S in),
+        # R_m spectrum, refinement right-hand sides (M_fit, e in)
+        "fft_weights": px * (1 + 5 + 4 + 5 * refine) + slab * (n_wa + (DK + 1) * (1 + refine) + 1),
+        # R_m in, one spectrum slab per half-plane difference out
+        "fft_prod": px * 4 + slab * n_hd,
+        # product and weight spectra in, k-slot products C[k][d][u_y][32] FP32 out
+        "contract_kk": slab * (n_hd + n_wa) + M * n_hd * L * 32 * 4,
+        # k-slot products in
+        "lag_dft": M * n_hd * L * 32 * 4,
+        # R_m spectrum against the weight spectra (KB) and the right-hand-side
+        # spectra (b_K, and again per refinement step)
+        "contract_rk": slab * ((1 + n_wa) + (1 + DK + 1) * (1 + refine)),
+        # residual pass (R, S, M_fit in; e out) and the final pass (R, S in; D out)
+        "apply": px * (13 * refine + 12),
+    }
+
+
+def half_plane_differences(L):
+    return L + (L - 1) * (2 * L - 1)
+
+
 def tf32_peak_tflops(sustained=True):
     """Dense TF32 tensor peak from the measured BF16 cuBLAS peak and the
     nominal TF32 : BF16 ratio (1.1 : 2.25 PFLOP/s)."""
@@ -305,6 +339,81 @@ def time_classifier(dev, n_infer=32768, batch=256, steps=40, arch="small"):
                     "(training = 3 x forward)"}
 
 
+def time_fma_engine(dev, stream, R, S, bad, Hs, args, steps=3):
+    """The same subtraction with the KK contraction on the FP32 FMA pipes:
+    CCD-pairs/s and the contraction's FP32 ALU roofline (derived peak)."""
+    import torch
+    from paper_2603_08593_gb300 import Plan
+    with torch.cuda.stream(stream):
+        p = Plan(Hs, W, L, DK, DB, batch=1, prec="mixed", stream=stream, device=dev, fma_contract=True)
+        o = p.subtract(R, S, bad, None, refine=REFINE)
+        stream.synchronize()
+        p.profile(True)
+        p.profile_read(reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            p.subtract(R, S, bad, None, refine=REFINE, out=o)
+        e1.record(stream)
+        stream.synchronize()
+        prof = p.profile_read(reset=True)
+    sec = e0.elapsed_time(e1) / 1e3 / steps
+    kk_ms = prof["contract_kk"][0] / steps
+    flop = kk_flops_per_ccd(Hs, W, L, DK)
+    peak = fp32_alu_peak_tflops(2070.0)
+    out = {"value": 1.0 / sec, "unit": UNIT, "ms_per_step": sec * 1e3, "steps": steps,
+           "contract_kk_ms": kk_ms, "alu_tflops": flop / (kk_ms * 1e-3) / 1e12,
+           "alu_frac": flop / (kk_ms * 1e-3) / 1e12 / peak,
+           "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)",
+           "status": [int(v) for v in o["info"].cpu()],
+           "note": "the KK lag contraction on the FP32 FMA pipes (SFFT_FLAG_FMA_CONTRACT), tensor cores used by "
+                   "the stamp classifier only; phase timing adds events inside the step"}
+    del p, o
+    torch.cuda.empty_cache()
+    return out
+
+
+def time_exposure(dev, stream, pairs, args, dist, steps=3, warmup=2):
+    """A whole exposure (len(pairs) CCD pairs of the 60-CCD recipe) per GPU in
+    one graph-captured sfft_subtract call, plan autotuned at creation."""
+    import torch
+    from paper_2603_08593_gb300 import Plan
+    B = len(pairs)
+    R = torch.from_numpy(np.stack([p["R"] for p in pairs])).to(dev).contiguous()
+    S = torch.from_numpy(np.stack([p["S"] for p in pairs])).to(dev).contiguous()
+    bad = torch.from_numpy(np.stack([p["bad"] for p in pairs])).to(dev).contiguous()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    with torch.cuda.stream(stream):
+        plan = Plan(H, W, L, DK, DB, batch=B, prec="mixed", stream=stream, device=dev, graph=True, autotune=1)
+        out = plan.subtract(R, S, bad, None, refine=REFINE)
+        for _ in range(warmup - 1):
+            plan.subtract(R, S, bad, None, refine=REFINE, out=out)
+        stream.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        with ClockSampler(dev.index) as clk:
+            _subtract_steps(plan, R, S, bad, out, steps, stream, flush, evs)
+            stream.synchronize()
+    sec = _max_over_ranks(dist, dev, sum(a.elapsed_time(b) for a, b in evs) / 1e3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rec = {"value": world * B * steps / sec, "unit": UNIT, "ccd_pairs_per_gpu_per_step": B, "steps": steps,
+           "warmup": warmup, "ms_per_step": 1e3 * sec / steps, "ms_per_ccd": 1e3 * sec / steps / B,
+           "tiles": {"d_batch": plan.tiles[0], "rows_per_cta": plan.tiles[1], "lag_parts": plan.tiles[2],
+                     "ccd_group": plan.ccd_group},
+           "kk_engine": plan.engine, "clocks": clk.summary(),
+           "status": [int(v) for v in out["info"].cpu()],
+           "masked_fraction": [float(p["masked_fraction"]) for p in pairs],
+           "workload": (f"{B} CCD pairs of one DECam exposure (2048x4096 FP32 each, seeds 100+, independent PSF "
+                        "gradients, masked fractions 2-30 %, cosmics, bleed trails) in one CUDA-graph-captured "
+                        "sfft_subtract call; L=11, D_K=D_B=2, mixed, 1 refinement step; 256 MB L2 flush between "
+                        "steps")}
+    del plan, out, R, S, bad, flush
+    torch.cuda.empty_cache()
+    return rec
+
+
 def run_gpu(args):
     import torch
     from paper_2603_08593_gb300 import Plan
@@ -313,6 +422,12 @@ def run_gpu(args):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     pairs = load_pairs(args, rank)                          # before the first CUDA call (spawned pool)
+    expo_pairs = None
+    if args.batch == 1 and args.rows == H and args.exposure_ccds > 0:
+        import multiprocessing as mp
+        idx = [60 * rank + i for i in range(args.exposure_ccds)]
+        with mp.get_context("spawn").Pool(max(1, min(16, _CORES))) as pool:
+            expo_pairs = pool.map(_c4_pair, idx)
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -426,6 +541,16 @@ def run_gpu(args):
                 "note": "plain FP64 GPU path (FP64 FFTs, products and contraction), sequential single-CCD calls"}
         del p64, o64
 
+    # the KK contraction on the FP32 FMA pipes (tensor cores left to the stamp classifier), same pair
+    fma_rec = None
+    if not batched and not args.no_fma_engine and args.prec == "mixed" and not args.fma_contract:
+        fma_rec = time_fma_engine(dev, stream, R, S, bad, Hs, args)
+    # the 60-CCD exposure in one graph-captured call, per GPU
+    expo = None
+    if expo_pairs is not None:
+        expo = time_exposure(dev, stream, expo_pairs, args, dist)
+        del expo_pairs
+
     classifier = None
     if not args.no_classifier and rank == 0:
         classifier = time_classifier(dev)
@@ -488,6 +613,18 @@ def run_gpu(args):
                     "traffic_note": "DRAM read+write bytes per launch, one-pass ncu capture of this workload"}
         if batched:
             roof["timing_note"] = "kernel durations from an eager profiled pass of the same plan (timed steps replay a CUDA graph)"
+    hbm = None
+    if prof and not batched and args.prec == "mixed":
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        pk = peaks["hbm_gbs"]
+        hbm = {"peak_gbs": pk, "peak_note": "STREAM-style copy of measured (MEASURED_PEAKS.json)",
+               "note": "per CCD: algorithmic bytes (each kernel's inputs read once, outputs written once) / phase "
+                       "time (CUDA events around the phase's kernels)"}
+        for k, nbytes in phase_bytes(Hs, W, L, DK, DB, REFINE).items():
+            ms = prof[k][0] / args.steps
+            if ms > 0:
+                gbs = nbytes / (ms * 1e-3) / 1e9
+                hbm[k] = {"bytes": nbytes, "ms": ms, "gbs": gbs, "frac": gbs / pk}
     if batched:
         workload = (f"{B} CCD pairs of one DECam exposure per GPU per step (2048x4096 FP32 each, independent PSF "
                     f"gradients, masked fractions 2-30 %, cosmics, bleed trails) in one CUDA-graph-captured call; "
@@ -508,6 +645,7 @@ def run_gpu(args):
                        "l2": "256 MB buffer written between timed steps (L2 flushed)"},
             "roofline": roof, "cpu_baseline": cpu_base, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "status": info, "wall_s": wall, "fp64_path": fp64, "classifier": classifier,
+            "hbm": hbm, "fma_engine": fma_rec, "exposure": expo,
             "phases_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -533,6 +671,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2, help="CCDs timed on the plain FP64 path for comparison")
     ap.add_argument("--no-autotune", action="store_true", help="plan defaults instead of plan-time tile tuning")
     ap.add_argument("--no-classifier", action="store_true", help="skip the stamp-classifier throughput figures")
+    ap.add_argument("--no-fma-engine", action="store_true", help="skip the FP32 FMA contraction engine figure")
+    ap.add_argument("--exposure-ccds", type=int, default=60,
+                    help="CCDs of the exposure sub-record (one graph-captured call; 0 skips it)")
     ap.add_argument("--only-classifier", action="store_true", help="print only the stamp-classifier figures")
     ap.add_argument("--lag-parts", type=int, default=0, choices=[0, 1, 2, 3], help="contraction lag parts (0: plan's)")
     ap.add_argument("--fma-contract", action="store_true",

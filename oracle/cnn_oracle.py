@@ -256,6 +256,71 @@ SHAPES_RI = {
 ORDER_RI = ["w1", "b1", "wa", "ba", "wb", "bb", "w2", "b2", "wc", "bc", "wd", "bd", "w4", "b4", "w5", "b5"]
 
 
+# ---------------------------------------------------------------- the network with BF16 operands
+# The GPU kernels compute the same network with every matrix-product operand
+# in BF16 (the normalised input, the weights of the convolutions and of fc1,
+# every pooled activation, and in the backward pass every back-propagated
+# signal dz) and FP32 sums; fc2 and the biases stay FP32.  The functions below
+# are that network with exact sums (modelled in FP64): the reference for how
+# much of a kernel's departure from the FP64 network is the operands' rounding.
+
+def round_bf16(x):
+    """Round to the nearest BF16 value, ties to even.  BF16 keeps the sign,
+    the 8 exponent bits and the top 7 of the 23 fraction bits of an IEEE
+    single, so the value is first rounded to FP32 and then to 8 significant
+    bits: add half a unit of the 16 dropped bits (minus one when the kept
+    part is even, so that an exact half goes to the even neighbour) and clear
+    them.  Finite inputs only."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    keep_odd = (u >> 16) & 1
+    u = ((u + 0x7FFF + keep_odd) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward_bf16(params, xn):
+    """Logits of the network with the kernels' BF16 operands (see above)."""
+    a = round_bf16(xn)
+    for wk, bk in (("w1", "b1"), ("w2", "b2"), ("w3", "b3")):
+        z = conv_same(a, round_bf16(params[wk]), params[bk])
+        a = round_bf16(maxpool2(np.maximum(z, 0.0))[0])
+    h4 = np.maximum(a.reshape(a.shape[0], -1) @ round_bf16(params["w4"]).T + params["b4"], 0.0)
+    return (h4 @ params["w5"].T + params["b5"])[:, 0]
+
+
+def loss_and_grads_bf16(params, xn, target):
+    """BCE loss and parameter gradients of the network with the kernels' BF16
+    operands: the forward of forward_bf16, then the backward of
+    loss_and_grads with each back-propagated signal dz (fc1's, and each
+    convolution's after its ReLU and pool) rounded to BF16 before it enters a
+    matrix product."""
+    n = xn.shape[0]
+    a = round_bf16(xn)
+    cache = []
+    for wk, bk in (("w1", "b1"), ("w2", "b2"), ("w3", "b3")):
+        wb = round_bf16(params[wk])
+        z = conv_same(a, wb, params[bk])
+        r = np.maximum(z, 0.0)
+        pooled, idx = maxpool2(r)
+        cache.append((a, wb, z, idx, r.shape))
+        a = round_bf16(pooled)
+    flat = a.reshape(n, -1)
+    w4b = round_bf16(params["w4"])
+    z4 = flat @ w4b.T + params["b4"]
+    h4 = np.maximum(z4, 0.0)
+    logit = (h4 @ params["w5"].T + params["b5"])[:, 0]
+    loss = bce_loss(logit, target)
+    dz5 = (sigmoid(logit) - target) / n
+    g = {"w5": (dz5[:, None] * h4).sum(0)[None, :], "b5": np.array([dz5.sum()])}
+    dz4 = round_bf16(dz5[:, None] * params["w5"] * (z4 > 0))
+    g["w4"], g["b4"] = dz4.T @ flat, dz4.sum(0)
+    da = (dz4 @ w4b).reshape(a.shape)
+    for li, (wk, bk) in reversed(list(enumerate((("w1", "b1"), ("w2", "b2"), ("w3", "b3"))))):
+        a_in, wb, z, idx, rshape = cache[li]
+        dz = round_bf16(maxpool2_backward(da, idx, rshape) * (z > 0))
+        da, g[wk], g[bk] = conv_same_backward(a_in, wb, dz)
+    return loss, g
+
+
 def n_params_ri():
     return int(sum(np.prod(SHAPES_RI[k]) for k in ORDER_RI))
 

@@ -9,9 +9,14 @@
 // 16..31) and whose inner dimension runs over the rows y' and (re, im).  The
 // A operand (the probe rows) is the same for every u_y; only the weight rows
 // shift.  So each probe value is split and stored to tensor memory once, and
-// each u_y reads the B operand from a strip of weight rows at its own start:
-// the strips hold two rows per 16-byte core-matrix column, one strip for
-// each row parity, so that every start falls on a column.  The products are
+// one MMA of N = 32 nu columns covers all nu u_y of a CTA: its B operand is
+// read from weight-row blocks laid out so that the n-groups of consecutive
+// u_y are consecutive 128-byte core matrices.  Block q (1024 bytes) holds the
+// row pair (2q, 2q + 1) for the 32 columns n (four 128-byte core matrices,
+// "even") and then the pair (2q + 1, 2q + 2) (four more, "odd"); with the
+// n-group stride at 128 bytes and the K stride (one row pair) at 1024 bytes,
+// the n-groups of u_y index i start at row 4 j + i of the k-step j (even
+// part of block 2 j + i / 2 for even i, odd part for odd i).  The products are
 // split as in kernels_contract_umma.cu (hi_x hi_y on kind::tf32, K = 8 = four
 // rows, plus bf16(hi_x) bf16(lo_y) + bf16(lo_x) bf16(y) on kind::f16, K = 16;
 // Ootomo and Yokota, 2022), with the BF16 inner order (row pair, row parity,
@@ -30,12 +35,12 @@
 //              16-byte load per row gives both k-slots' probe values, split
 //              into 2 x 16 A columns (tcgen05.st); warps 0-3 then run the
 //              epilogue;
-//   warps 8-11 B producers: the four strips (TF32 and BF16, two parities) of
-//              both k-slots for each staged chunk of 16 rows y', a half-warp
-//              filling one 128-byte core matrix per store;
-//   warp 12    MMA issuer: per pair of k-steps 2 x nu accumulators, each
-//              taking its four MMAs (TF32 and BF16 of both k-steps) back to
-//              back;
+//   warps 8-11 B producers: the weight-row blocks (TF32 and BF16) of both
+//              k-slots for each staged chunk of 16 rows y', every row written
+//              to its even and its odd block, a half-warp filling one 128-byte
+//              core matrix per store;
+//   warp 12    MMA issuer: per pair of k-steps and k-slot, four MMAs of
+//              N = 32 nu (TF32 and BF16 of both k-steps) back to back;
 //   warp 13    copy producer: per chunk one tensor-map box of probe rows
 //              (128 differences x 17 rows x 2 slots, from the k-slot-blocked
 //              product spectra [d][k / 16][y][k % 16]), one box of weight rows
@@ -62,9 +67,9 @@ constexpr int PBR = CH + 1;           // probe rows per box: a spare row stagger
 constexpr int PBYTES = 128 * PBR * 16;
 constexpr int VR = CH + NU;           // weight rows per box (CH + NU - 1 used)
 constexpr int VSLOT = (VR * 16 + 127) / 128 * 128;
-constexpr int NQ = (4 * (KSC - 1) + NU - 1) / 2 + 2;   // 16-byte columns (row pairs) per strip
-constexpr int SBO = NQ * 128 + 16;    // bytes between the strips' 8-row groups (16 more to shift banks)
-constexpr int STRIP = 4 * SBO;        // 32 rows n
+constexpr int NQ = (4 * (KSC - 1) + NU - 1) / 2 + 2;   // weight-row blocks (row pairs) per chunk
+constexpr int QB = 1024;              // bytes per block: even and odd row pairs of the 32 columns n
+constexpr int WBLK = NQ * QB;         // bytes of one chunk's blocks per k-slot and operand format
 constexpr int WARP_BP = 8;            // first B-producer warp
 constexpr int WARP_MMA = 12, WARP_COPY = 13;
 constexpr int NTHREADS = 32 * 14;
@@ -81,7 +86,7 @@ static_assert(PBYTES % 128 == 0 && sizeof(DStage) % 128 == 0, "tensor copy align
 
 struct DSmem {
   DStage st[2];
-  uint8_t strip[2][2][4][STRIP];   // [stage][slot][TF32 even, TF32 odd, BF16 even, BF16 odd]
+  uint8_t wblk[2][2][2][WBLK];     // [stage][slot][TF32, BF16] weight-row blocks
   uint64_t raw_full[2], raw_empty[2], strip_full[2], strip_empty[2];
   uint64_t a_full[GA], a_empty[GA], done;
   uint32_t tmem_base;
@@ -165,22 +170,21 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
       __syncwarp();
     }
   } else if (warp == WARP_MMA) {
-    constexpr uint32_t id_tf32 = instr_desc(2), id_bf16 = instr_desc(1);
-    // descriptor of a strip start: the address field (bits 0-13, 16-byte units)
-    // advances by 8 per 128-byte row pair
-    const uint64_t dstrip0 = smem_desc(smem_u32(&S.strip[0][0][0][0]), SBO);
+    // one MMA per k-step, k-slot and operand format covers the nu u_y of the
+    // CTA: N = 32 nu columns, n-groups 128 bytes apart, row pairs 1024 apart
+    const uint32_t id_tf32 = instr_desc(2, 32 * nu), id_bf16 = instr_desc(1, 32 * nu);
+    const uint64_t dblk0 = smem_desc_kn(smem_u32(&S.wblk[0][0][0][0]), QB, 128);
     for (int c = 0; c < nchunk && !*abort; ++c) {
       const int sidx = c & 1;
       if (!wait_phase(&S.strip_full[sidx], (unsigned)((c >> 1) & 1), abort)) break;
-      uint64_t dtf[2][4];   // descriptors of the stage's strips: [slot][TF32 even, odd, BF16 even, odd]
+      uint64_t dw[2][2];   // descriptors of the stage's blocks: [slot][TF32, BF16]
 #pragma unroll
       for (int s = 0; s < 2; ++s)
 #pragma unroll
-        for (int kd = 0; kd < 4; ++kd) dtf[s][kd] = dstrip0 + (uint64_t)((((sidx * 2 + s) * 4 + kd) * STRIP) >> 4);
+        for (int f = 0; f < 2; ++f) dw[s][f] = dblk0 + (uint64_t)((((sidx * 2 + s) * 2 + f) * WBLK) >> 4);
       bool live = true;
-      // k-steps in pairs: each accumulator takes TF32 (j), BF16 (j), TF32
-      // (j + 1), BF16 (j + 1) back to back, which halves the switches between
-      // accumulators (each switch costs the tensor pipe a TMEM turnaround)
+      // k-steps in pairs: each k-slot's accumulators take TF32 (j), BF16 (j),
+      // TF32 (j + 1), BF16 (j + 1) back to back
       for (int j = 0; j < KSC; j += 2) {
         const int g = c * KSC + j, as = g % GA;   // k-steps g, g + 1 in A slots as, as + 1
         if (!wait_phase(&S.a_full[as], (unsigned)((g / GA) & 1), abort) ||
@@ -193,24 +197,17 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
           const uint32_t acc = g > 0 ? 1u : 0u;   // the first k-step starts the accumulators
 #pragma unroll
           for (int s = 0; s < 2; ++s) {
+            const uint32_t dcol = t_d + 32 * NU * s;
 #pragma unroll
-            for (int i = 0; i < NU; ++i) {
-              if (i < nu) {
-                const uint32_t dcol = t_d + 32 * (NU * s + i);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                  const int o = 4 * (j + h) + i, par = o & 1, qc = (o - par) >> 1;   // strip row of the first weight row
-                  const uint32_t acol = t_a + 32 * (as + h) + 16 * s;
-                  const uint64_t bt = dtf[s][par] + (uint64_t)(qc * 8);
-                  const uint64_t bb = dtf[s][2 + par] + (uint64_t)(qc * 8);
-                  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                               " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n"
-                               ::"r"(dcol), "r"(acol), "l"(bt), "r"(id_tf32), "r"(h ? 1u : acc) : "memory");
-                  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                               " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n"
-                               ::"r"(dcol), "r"(acol + 8), "l"(bb), "r"(id_bf16), "r"(1u) : "memory");
-                }
-              }
+            for (int h = 0; h < 2; ++h) {
+              const uint32_t acol = t_a + 32 * (as + h) + 16 * s;
+              const uint64_t koff = (uint64_t)((2 * (j + h) * QB) >> 4);   // block 2 (j + h): rows 4 (j + h) ..
+              asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                           " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n"
+                           ::"r"(dcol), "r"(acol), "l"(dw[s][0] + koff), "r"(id_tf32), "r"(h ? 1u : acc) : "memory");
+              asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                           " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n"
+                           ::"r"(dcol), "r"(acol + 8), "l"(dw[s][1] + koff), "r"(id_bf16), "r"(1u) : "memory");
             }
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
@@ -277,28 +274,28 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
   } else if (warp < WARP_MMA) {
     // ---- B producers: warp e (slot e % 2) takes the row pairs e / 2, e / 2
     // + 2, ...; lane (m % 8, row parity, m / 8) writes W_m(y) for
-    // y = yc + u_lo + s_row into the rows n = m (Re) and 16 + m (Im) of
-    // both parities' strips, so that the 16 lanes of a half-warp fill one
-    // 128-byte core matrix (8 rows n x 2 rows y) per store.  TF32 strip
-    // element (n, k) at (n / 8) SBO + (k / 4) 128 + (n % 8) 16 + (k % 4) 4
-    // with k = 2 (row % 2)
-    // + (re, im) inside the row pair k / 4; the BF16 strip holds per (n, row)
-    // four values (hi(P)-part re, im: lo(W); lo(P)-part re, im: W) at
-    // (row % 2) 8 bytes of the same 16-byte column.
+    // y = yc + u_lo + s_row into the columns n = m (Re) and 16 + m (Im) of
+    // the row's even block (s_row / 2) and odd block ((s_row - 1) / 2), so
+    // that the 16 lanes of a half-warp fill one 128-byte core matrix (8
+    // columns n x 2 rows y) per store.  TF32 element (n, row r of the pair
+    // starting at row 2 q + par) at q QB + par 512 + (n / 8) 128 + (n % 8) 16
+    // + r 8 + (re, im) 4; the BF16 blocks hold per (n, row) four values
+    // (hi(P)-part re, im: lo(W); lo(P)-part re, im: W) at r 8 bytes of the
+    // same 16-byte column.
     const int e = warp - WARP_BP;
     const int m = 8 * ((lane >> 4) & 1) + (lane & 7), rpar = (lane >> 3) & 1, s = e & 1;
     int am = 0, bm = 0;
     mono_ab(m < NMONO ? m : 0, am, bm);
     const bool live = m < NMONO;
-    const int nre = (m / 8) * SBO + (m % 8) * 16, nim = ((16 + m) / 8) * SBO + (m % 8) * 16;
+    const int nre = (m / 8) * 128 + (m % 8) * 16, nim = ((16 + m) / 8) * 128 + (m % 8) * 16;
     for (int c = 0; c < nchunk && !*abort; ++c) {
       const int sidx = c & 1;
       if (!wait_phase(&S.raw_full[sidx], (unsigned)((c >> 1) & 1), abort)) break;
       if (c >= 2 && !wait_phase(&S.strip_empty[sidx], (unsigned)(((c >> 1) - 1) & 1), abort)) break;
       const DStage& st = S.st[sidx];
       const int ybase = Ys + c * CH + ulo;
-      uint8_t* tf0 = &S.strip[sidx][s][0][0];
-      uint8_t* bf0 = &S.strip[sidx][s][2][0];
+      uint8_t* tf0 = &S.wblk[sidx][s][0][0];
+      uint8_t* bf0 = &S.wblk[sidx][s][1][0];
 #pragma unroll 2
       for (int srow = 2 * (e >> 1) + rpar; srow < VR - 1; srow += 4) {
         const int y = ybase + srow;
@@ -315,7 +312,7 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
         for (int par = 0; par < 2; ++par) {
           const int rr = srow - par;
           if (rr < 0 || (rr >> 1) >= NQ) continue;
-          const int off = (rr >> 1) * 128 + (rr & 1) * 8 + par * STRIP;
+          const int off = (rr >> 1) * QB + (rr & 1) * 8 + par * 512;
           *reinterpret_cast<float2*>(tf0 + nre + off) = tre;
           *reinterpret_cast<float2*>(tf0 + nim + off) = tim;
           *reinterpret_cast<uint2*>(bf0 + nre + off) = bre;

@@ -20,10 +20,22 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t sbo = 256
   return d;
 }
 
+// canonical K-major layout without swizzle with both strides given: core
+// matrices (8 rows x 16 bytes) `lbo` bytes apart along K and `sbo` bytes
+// apart along the 8-row groups; descriptor version 1
+__device__ __forceinline__ uint64_t smem_desc_kn(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
 // instruction descriptor: D FP32, A and B of format `fmt` (1 = BF16 for
-// kind::f16, 2 = TF32 for kind::tf32), both K-major, M = 128, N = 32
-__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+// kind::f16, 2 = TF32 for kind::tf32), both K-major, M = 128, N columns
+// (a multiple of 16 up to 256; 32 by default)
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt, uint32_t n = 32) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
 }
 
 // tiled tensor copy of a 3-D box (x innermost) into shared memory, counted on `bar`

@@ -328,3 +328,30 @@ def test_contraction_engine_selection():
     assert Plan(96, 300, 11, 2, 2, prec="mixed", d_batch=7).engine == "tcgen05_pair_lane"
     assert Plan(96, 300, 11, 2, 2, prec="mixed", mma_sync_contract=True).engine == "mma_sync"
     assert Plan(96, 300, 11, 2, 2, prec="fp64").engine == "fp64_fma"
+
+
+@pytest.mark.parametrize("engine,d_batch", [("default", 0), ("pair_lane_contract", 0), ("fma_contract", 7),
+                                            ("mma_sync_contract", 0), ("pair_lane_contract", 9)])
+def test_ccd_groups_each_ccd_matches_oracle(engine, d_batch):
+    """A batch whose product spectra are formed and contracted in groups of
+    two CCDs (groups {0, 1} and {2}), also with several difference batches
+    per group: every CCD against its own oracle fit."""
+    L, DK, DB = 5, 1, 2
+    imgs = [small_pair(72, 120, seed=3300 + i, mask_fraction=0.03 * (i + 1)) for i in range(3)]
+    kw = {} if engine == "default" else {engine: True}
+    refs, A, b, th, info, D = _run(None, L, DK, DB, "mixed", batch_imgs=imgs, ccd_group=2, d_batch=d_batch, **kw)
+    for i in range(3):
+        assert info[i] == 0
+        assert np.abs(A[i] - refs[i]["A"]).max() <= 2e-5 * np.abs(refs[i]["A"]).max()
+        assert O.kernel_coef_rel_err(th[i], refs[i]["theta_orig"], L, DK, DB) <= 1e-5
+        assert np.abs(D[i] - refs[i]["D"]).max() <= 1e-3 * SIGMA_SKY
+
+
+def test_plan_groups_and_engine_choice():
+    """The plan holds every difference of a CCD per pass and groups CCDs by
+    the product-spectrum budget; a forced group size is kept."""
+    from paper_2603_08593_gb300 import Plan
+    p = Plan(72, 120, 5, 1, 2, batch=5, prec="mixed")
+    assert p.tiles[0] == 41 and p.ccd_group == 5 and p.engine == "tcgen05_difference_lane"
+    p = Plan(72, 120, 5, 1, 2, batch=5, prec="mixed", ccd_group=2)
+    assert p.ccd_group == 2 and p.engine == "tcgen05_difference_lane"

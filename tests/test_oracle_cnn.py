@@ -205,3 +205,84 @@ def test_ri_gradients_by_central_differences():
             num = (lp - lm) / (2 * h)
             ana = g[k].ravel()[idx]
             assert abs(num - ana) <= 1e-6 * max(1.0, abs(num)) + 1e-8, (k, idx, num, ana)
+
+
+# ---------------------------------------------------------------- the BF16 operand model
+def test_round_bf16_hand_computed_ties_to_even():
+    e8, e7, e6 = 2.0 ** -8, 2.0 ** -7, 2.0 ** -6
+    cases = [
+        (1.0, 1.0),
+        (3.0, 3.0),                       # representable: unchanged
+        (1 + e8, 1.0),                    # exact half between 1 and 1 + 2^-7: to the even 1
+        (1 + 3 * e8, 1 + e6),             # exact half between 1 + 2^-7 (odd) and 1 + 2^-6 (even)
+        (1 + e8 + 2.0 ** -20, 1 + e7),    # just above the half: up
+        (1 + e8 - 2.0 ** -20, 1.0),       # just below: down
+        (-(1 + 3 * e8), -(1 + e6)),       # sign kept
+        (255.5, 256.0),                   # 8 significant bits: 255.5 is the half between 255 and 256 (even)
+        (254.5, 254.0),                   # half between 254 (even) and 255
+        (0.0, 0.0),
+    ]
+    for x, want in cases:
+        assert C.round_bf16(np.array([x]))[0] == want, (x, C.round_bf16(np.array([x]))[0], want)
+
+
+def test_round_bf16_matches_library_conversion():
+    torch = pytest.importorskip("torch")
+    x = np.concatenate([RNG.normal(0, 1, 20000), RNG.normal(0, 1e6, 2000), RNG.normal(0, 1e-6, 2000)])
+    x = x.astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+    assert np.array_equal(C.round_bf16(x), ref)
+
+
+def _sparse_integer_net():
+    """Delta-like filters with weights +-1, small integer inputs and a large
+    fc2 bias: every operand and every sum is a small integer, exact in BF16;
+    with the targets below every back-propagated signal is a multiple of 2^-4."""
+    p = {k: np.zeros(C.SHAPES[k]) for k in C.ORDER}
+    for o in range(32):
+        p["w1"][o, o % 3, 1, 1] = 1.0 if o % 2 == 0 else -1.0
+    for o in range(64):
+        p["w2"][o, o % 32, 1, 1] = 1.0
+        p["w3"][o, o, 1, 1] = 1.0
+    for o in range(128):
+        p["w4"][o, (7 * o) % 576] = 1.0
+    p["w5"][0, :] = np.where(np.arange(128) % 3 == 0, 1.0, -1.0)
+    p["b5"][0] = 1000.0                   # sigmoid(logit) = 1 in FP64
+    xn = RNG.integers(-4, 5, size=(8, 3, 31, 31)).astype(np.float64)
+    return p, xn
+
+
+def test_bf16_model_equals_fp64_network_when_operands_are_exact():
+    p, xn = _sparse_integer_net()
+    z = C.forward(p, xn)
+    assert np.array_equal(C.forward_bf16(p, xn), z)
+    assert np.all(z > 100)
+    # targets 1/2: (sigmoid - t) / n = 2^-4 exactly, so every dz is exact in BF16
+    t = np.full(8, 0.5)
+    lo, go = C.loss_and_grads(p, xn, t)
+    lb, gb = C.loss_and_grads_bf16(p, xn, t)
+    assert lb == lo
+    for k in C.ORDER:
+        assert np.array_equal(gb[k], go[k]), k
+        assert np.any(go[k] != 0), k
+
+
+def test_bf16_model_rounds_inputs_weights_and_activations():
+    """Delta filters route one pixel to the logit: the FP64 network returns
+    the pixel times the weights; the BF16 model returns the pixel rounded, the
+    rounded weights, and each product rounded again at every pooled layer."""
+    p = {k: np.zeros(C.SHAPES[k]) for k in C.ORDER}
+    w = 1 + 3 * 2.0 ** -8                 # rounds to 1 + 2^-6
+    p["w1"][0, 0, 1, 1] = w
+    p["w2"][0, 0, 1, 1] = 1.0
+    p["w3"][0, 0, 1, 1] = 1.0
+    p["w4"][0, 0] = 1.0
+    p["w5"][0, 0] = 1.0
+    xn = np.zeros((1, 3, 31, 31))
+    xn[0, 0, 0, 0] = 1 + 2.0 ** -8        # rounds to 1
+    assert C.forward(p, xn)[0] == (1 + 2.0 ** -8) * w
+    # 1 * (1 + 2^-6) is exact in BF16: nothing more is lost after the first layer
+    assert C.forward_bf16(p, xn)[0] == 1 + 2.0 ** -6
+    xn[0, 0, 0, 0] = 1 + 2.0 ** -7        # exact; the product (1 + 2^-7)(1 + 2^-6) = 1 + 3 * 2^-7 + 2^-13
+    assert C.forward_bf16(p, xn)[0] == C.round_bf16(np.array([(1 + 2.0 ** -7) * (1 + 2.0 ** -6)]))[0]
+    assert C.forward_bf16(p, xn)[0] == 1 + 3 * 2.0 ** -7  # the 2^-13 is below half a unit (2^-8): dropped
