@@ -385,6 +385,26 @@ def forward_ri(params, xn, keep=False):
     return logit
 
 
+def forward_ri_bf16(params, xn):
+    """Logits of the rotation-invariant network with the kernels' BF16
+    operands: the input, the weights of every convolution and of fc1, and
+    every activation that enters a matrix product (each pooled or residual
+    output and the rotation-averaged features) rounded to BF16; fc2, the
+    biases and the sums exact."""
+    q = {k: (round_bf16(v) if k.startswith("w") and k != "w5" else v) for k, v in params.items()}
+    n = xn.shape[0]
+    x = rotations(round_bf16(xn))
+    p1 = round_bf16(maxpool2(np.maximum(conv_same(x, q["w1"], q["b1"]), 0.0))[0])
+    ra = round_bf16(np.maximum(conv_same(p1, q["wa"], q["ba"]), 0.0))
+    r1 = round_bf16(np.maximum(conv_same(ra, q["wb"], q["bb"]) + p1, 0.0))
+    p2 = round_bf16(maxpool2(np.maximum(conv_same(r1, q["w2"], q["b2"]), 0.0))[0])
+    rc = round_bf16(np.maximum(conv_same(p2, q["wc"], q["bc"]), 0.0))
+    p3 = round_bf16(maxpool2(np.maximum(conv_same(rc, q["wd"], q["bd"]) + p2, 0.0))[0])
+    f = round_bf16(p3.reshape(4, n, -1).mean(axis=0))
+    h4 = np.maximum(f @ q["w4"].T + q["b4"], 0.0)
+    return (h4 @ params["w5"].T + params["b5"])[:, 0]
+
+
 def loss_and_grads_ri(params, xn, target):
     """BCE loss and its gradient for every parameter of the rotation-invariant network."""
     logit, c = forward_ri(params, xn, keep=True)

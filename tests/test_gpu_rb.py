@@ -3,20 +3,21 @@
 
 Tolerances.  The classifier rounds its normalised inputs, weights and every
 hidden activation to BF16 (relative rounding error <= 2^-9) and accumulates in
-FP32.  Against the FP64 oracle that gives, on these inputs, a relative L2
-error of 2e-3 to 7e-3 in the logits with single logits off by up to ~4 % of
-the logits' RMS (an FP64 model of the same roundings reproduces these errors);
-the bars are 1.5e-2 (L2) and 6e-2 of the RMS (max).  The same oracle layers
-with the kernel's roundings applied (inputs, weights and pooled activations
-rounded to BF16) must agree with the GPU to 5e-3 of the RMS (the GPU
-normalises in FP32, so a few inputs round to the neighbouring BF16 value),
-which separates layout or indexing mistakes from rounding.  Gradients add one more
-rounding of each back-propagated signal and sign flips of ReLU/max-pool
-decisions taken on slightly different values: against FP64 the first layers'
-gradients differ by up to ~9 % (relative L2) at cosine >= 0.995, and the same
-happens to an FP64 model of the kernels' roundings.  The bars are cosine >=
-0.99 and relative L2 <= 0.15 against FP64, and relative L2 <= 2e-2 against the
-rounding model.  The detector
+FP32.  The oracle's BF16 operand model (cnn_oracle.forward_bf16 and
+loss_and_grads_bf16: the FP64 network with the same operands rounded) must
+agree with the GPU to 5e-3 of the logits' RMS and to relative L2 2e-2 and
+cosine 0.999 in every gradient (the GPU normalises in FP32, so a few inputs
+round to the neighbouring BF16 value), which separates layout or indexing
+mistakes from rounding.  Against the plain FP64 network the logits are held
+to relative L2 1e-2 where the logits are not dominated by cancellation (the
+detector-stamp test below); on the synthetic stamps with small random-network
+logits the rounding model itself departs by up to ~1 % with single logits off
+by ~4 % of the RMS, and the bars there are 1.5e-2 (L2) and 6e-2 of the RMS
+(max).  Gradients add one more rounding of each back-propagated signal and
+sign flips of ReLU/max-pool decisions taken on slightly different values:
+against FP64 the rounding model's own first-layer gradients differ by up to
+~9 % (relative L2) at cosine >= 0.996, so against FP64 the bars are cosine >=
+0.99 and relative L2 <= 0.15.  The detector
 filters in FP32 (31 taps per pass, two passes): its SNR map agrees with the
 FP64 map to 1e-5 of max |SNR| + 1e-5; candidate decisions may differ only where
 the oracle's margin (to the threshold or to a neighbour) is below 1e-3.  The
@@ -59,62 +60,13 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
-def _bf16(x):
-    """Round to the nearest BF16 (ties to even), as the kernels store operands."""
-    a = np.ascontiguousarray(x, dtype=np.float32)
-    u = a.view(np.uint32).astype(np.uint64)
-    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
-    return u.astype(np.uint32).view(np.float32).astype(np.float64)
-
-
-def _forward_bf16(p, xn):
-    """Oracle layers with the kernels' BF16 roundings applied."""
-    a = _bf16(xn)
-    for wk, bk in [("w1", "b1"), ("w2", "b2"), ("w3", "b3")]:
-        a = _bf16(C.maxpool2(np.maximum(C.conv_same(a, _bf16(p[wk]), p[bk]), 0.0))[0])
-    h4 = np.maximum(a.reshape(a.shape[0], -1) @ _bf16(p["w4"]).T + p["b4"], 0.0)
-    return (h4 @ p["w5"].T + p["b5"])[:, 0]
-
-
-def _grads_bf16(p, xn, t):
-    """Oracle backward with the kernels' BF16 roundings applied: operands of
-    every matrix product (activations, weights, back-propagated signals) are
-    BF16, sums and the dense head FP32-exact (modelled in FP64)."""
-    n = xn.shape[0]
-    a = _bf16(xn)
-    cache = []
-    for wk, bk in [("w1", "b1"), ("w2", "b2"), ("w3", "b3")]:
-        wb = _bf16(p[wk])
-        z = C.conv_same(a, wb, p[bk])
-        r = np.maximum(z, 0.0)
-        pooled, idx = C.maxpool2(r)
-        cache.append((a, wb, z, idx, r.shape))
-        a = _bf16(pooled)
-    flat = a.reshape(n, -1)
-    w4b = _bf16(p["w4"])
-    z4 = flat @ w4b.T + p["b4"]
-    h4 = np.maximum(z4, 0.0)
-    logit = (h4 @ p["w5"].T + p["b5"])[:, 0]
-    dz5 = (C.sigmoid(logit) - t) / n
-    g = {"w5": (dz5[:, None] * h4).sum(0)[None, :], "b5": np.array([dz5.sum()])}
-    dz4 = _bf16(dz5[:, None] * p["w5"] * (z4 > 0))
-    g["w4"], g["b4"] = dz4.T @ flat, dz4.sum(0)
-    da = (dz4 @ w4b).reshape(a.shape)
-    for li, (wk, bk) in reversed(list(enumerate([("w1", "b1"), ("w2", "b2"), ("w3", "b3")]))):
-        a_in, wb, z, idx, rshape = cache[li]
-        dz = _bf16(C.maxpool2_backward(da, idx, rshape) * (z > 0))
-        dx, g[wk], g[bk] = C.conv_same_backward(a_in, wb, dz)
-        da = dx
-    return g
-
-
 def _check_logits(z, p, stamps):
     xn = C.normalise(stamps.astype(np.float64))
     zo = C.forward(p, xn)
     rms = max(np.sqrt(np.mean(zo ** 2)), 1e-3)
     assert _rel(z, zo) <= 1.5e-2, _rel(z, zo)
     assert np.max(np.abs(z - zo)) <= 6e-2 * rms + 1e-4, (np.max(np.abs(z - zo)), rms)
-    zb = _forward_bf16(p, xn)
+    zb = C.forward_bf16(p, xn)
     assert np.max(np.abs(z - zb)) <= 5e-3 * rms + 1e-4, (np.max(np.abs(z - zb)), rms)
 
 
@@ -176,7 +128,7 @@ def test_delta_filters_route_one_pixel_block(ch, c1, c2, c3, pos):
     d = make_stamps(6, seed=60 + ch)
     m = _model(p, 8)
     z = m.logits(_dev(d["stamps"])).cpu().numpy().astype(np.float64)
-    xn = _bf16(C.normalise(d["stamps"].astype(np.float64)))
+    xn = C.round_bf16(C.normalise(d["stamps"].astype(np.float64)))
     i, j = divmod(pos, 3)
     ref = np.maximum(xn[:, ch, 8 * i:8 * i + 8, 8 * j:8 * j + 8].reshape(6, -1).max(axis=1), 0.0)
     assert np.all(np.abs(z - ref) <= 2.0 ** -8 * np.abs(ref)), (z, ref)
@@ -191,7 +143,7 @@ def test_gradients_match_oracle():
     g = C.unflatten(m.get_grads())
     xn = C.normalise(d["stamps"].astype(np.float64))
     lo, go = C.loss_and_grads(p, xn, d["labels"].astype(np.float64))
-    gb = _grads_bf16(p, xn, d["labels"].astype(np.float64))
+    gb = C.loss_and_grads_bf16(p, xn, d["labels"].astype(np.float64))[1]
     assert abs(float(loss.item()) - lo) <= 2e-2 * abs(lo)
     for k in C.ORDER:
         a, b, c = g[k].ravel().astype(np.float64), go[k].ravel(), gb[k].ravel()
@@ -200,6 +152,55 @@ def test_gradients_match_oracle():
               f"vs BF16 model relative L2 {_rel(a, c):.3e} (model vs FP64 {_rel(c, b):.3e})")
         assert cos >= 0.99 and _rel(a, b) <= 0.15, (k, cos, _rel(a, b))
         assert _rel(a, c) <= 2e-2, (k, _rel(a, c))
+
+
+def _detector_stamps():
+    """Stamps as the pipeline produces them: the oracle's subtraction of a
+    256 x 256 pair (stars, injected transients, cosmic-ray hits) and the
+    oracle's matched-filter detection at 3 sigma on its difference image."""
+    from oracle import sfft_oracle as O
+    from synth import make_pair
+    d = make_pair(256, 256, seed=11, n_src=120, fwhm_R=(1.2, 1.2), fwhm_S=(1.8, 1.8), shift=(0.1, 0.0),
+                  n_transients=12, snr=(5.0, 40.0), n_cosmics=20, transient_margin=20)
+    f = O.fit(d["R"], d["S"], d["bad"], 7, 1, 1)
+    o = DO.detect(f["D"], d["S"], d["R"], d["bad"], 1.8 / 2.3548, 3.0)
+    assert o["count"] >= 64
+    return o["stamps"].astype(np.float32)
+
+
+@pytest.mark.parametrize("seed", [5, 13])
+def test_detector_stamps_logits_and_gradients(seed):
+    """Parity on detector-produced stamps, the classifier's real input.  Logits
+    against the FP64 network: relative L2 <= 1e-2; against the BF16 operand
+    model: 5e-3 of the RMS.  Gradients against the BF16 operand model: cosine
+    >= 0.999 and relative L2 <= 2e-2 for every parameter; against plain FP64
+    (where the model itself departs by up to ~9 %), cosine >= 0.99 and
+    relative L2 <= 0.15."""
+    st = _detector_stamps()
+    n = st.shape[0]
+    p = _params(seed)
+    m = _model(p, 128)
+    z = m.logits(_dev(st)).cpu().numpy().astype(np.float64)
+    xn = C.normalise(st.astype(np.float64))
+    zo, zb = C.forward(p, xn), C.forward_bf16(p, xn)
+    rms = np.sqrt(np.mean(zo ** 2))
+    print(f"logits: vs FP64 {_rel(z, zo):.2e} (model vs FP64 {_rel(zb, zo):.2e}); "
+          f"vs model max {np.max(np.abs(z - zb)) / rms:.2e} of the RMS")
+    assert _rel(z, zo) <= 1e-2
+    assert np.max(np.abs(z - zb)) <= 5e-3 * rms
+    t = (np.arange(n) % 2).astype(np.float32)
+    m.backward(_dev(st), _dev(t))
+    g = C.unflatten(m.get_grads())
+    _, go = C.loss_and_grads(p, xn, t.astype(np.float64))
+    _, gb = C.loss_and_grads_bf16(p, xn, t.astype(np.float64))
+    for k in C.ORDER:
+        a, b, c = g[k].ravel().astype(np.float64), go[k].ravel(), gb[k].ravel()
+        cb = float(a @ c / max(np.linalg.norm(a) * np.linalg.norm(c), 1e-30))
+        co = float(a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30))
+        print(f"gradient {k}: vs model cosine {cb:.6f} rel {_rel(a, c):.2e}; vs FP64 cosine {co:.6f} "
+              f"rel {_rel(a, b):.2e}")
+        assert cb >= 0.999 and _rel(a, c) <= 2e-2, (k, cb, _rel(a, c))
+        assert co >= 0.99 and _rel(a, b) <= 0.15, (k, co, _rel(a, b))
 
 
 def test_adam_step_and_checkpoint_resume():

@@ -48,29 +48,6 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
-def _bf16(x):
-    a = np.ascontiguousarray(x, dtype=np.float32)
-    u = a.view(np.uint32).astype(np.uint64)
-    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
-    return u.astype(np.uint32).view(np.float32).astype(np.float64)
-
-
-def _forward_bf16(p, xn):
-    """The oracle's layers with the kernels' BF16 roundings applied."""
-    q = {k: (_bf16(v) if k.startswith("w") and k != "w5" else v) for k, v in p.items()}
-    n = xn.shape[0]
-    x = C.rotations(_bf16(xn))
-    p1 = _bf16(C.maxpool2(np.maximum(C.conv_same(x, q["w1"], q["b1"]), 0))[0])
-    ra = _bf16(np.maximum(C.conv_same(p1, q["wa"], q["ba"]), 0))
-    r1 = _bf16(np.maximum(C.conv_same(ra, q["wb"], q["bb"]) + p1, 0))
-    p2 = _bf16(C.maxpool2(np.maximum(C.conv_same(r1, q["w2"], q["b2"]), 0))[0])
-    rc = _bf16(np.maximum(C.conv_same(p2, q["wc"], q["bc"]), 0))
-    p3 = _bf16(C.maxpool2(np.maximum(C.conv_same(rc, q["wd"], q["bd"]) + p2, 0))[0])
-    f = _bf16(p3.reshape(4, n, -1).mean(axis=0))
-    h4 = np.maximum(f @ q["w4"].T + q["b4"], 0)
-    return (h4 @ p["w5"].T + p["b5"])[:, 0]
-
-
 def test_ri_weights_roundtrip_exact():
     p = _params(3)
     m = _model(p, 8)
@@ -87,7 +64,7 @@ def test_ri_logits_match_oracle(n, max_batch):
     z = m.logits(_dev(d["stamps"])).cpu().numpy().astype(np.float64)
     xn = C.normalise(d["stamps"].astype(np.float64))
     zo = C.forward_ri(p, xn)
-    zb = _forward_bf16(p, xn)
+    zb = C.forward_ri_bf16(p, xn)
     rms = float(np.sqrt(np.mean(zo ** 2)))
     print(f"logits: vs BF16 model max {np.abs(z - zb).max() / rms:.3e} RMS; vs FP64 relative L2 {_rel(z, zo):.3e}, "
           f"max {np.abs(z - zo).max() / rms:.3e} RMS")

@@ -286,3 +286,24 @@ def test_bf16_model_rounds_inputs_weights_and_activations():
     xn[0, 0, 0, 0] = 1 + 2.0 ** -7        # exact; the product (1 + 2^-7)(1 + 2^-6) = 1 + 3 * 2^-7 + 2^-13
     assert C.forward_bf16(p, xn)[0] == C.round_bf16(np.array([(1 + 2.0 ** -7) * (1 + 2.0 ** -6)]))[0]
     assert C.forward_bf16(p, xn)[0] == 1 + 3 * 2.0 ** -7  # the 2^-13 is below half a unit (2^-8): dropped
+
+
+def test_ri_bf16_model_equals_fp64_network_when_operands_are_exact():
+    """Integer weights and inputs with every sum a small integer (and the
+    rotation mean of a value repeated four times): the BF16 model of the
+    rotation-invariant network equals the FP64 network exactly."""
+    p = {k: np.zeros(v.shape) for k, v in C.init_params_ri(0).items()}
+    for o in range(32):
+        p["w1"][o, o % 3, 1, 1] = 1.0
+        p["wa"][o, o, 1, 1] = -1.0 if o % 2 else 1.0
+        p["wb"][o, o, 1, 1] = 1.0
+    for o in range(64):
+        p["w2"][o, o % 32, 1, 1] = 1.0
+        p["wc"][o, o, 1, 1] = 1.0
+        p["wd"][o, o, 1, 1] = -1.0
+    for o in range(128):
+        p["w4"][o, (5 * o) % 576] = 1.0
+    p["w5"][0, :] = 1.0
+    xn = RNG.integers(0, 5, size=(3, 3, 31, 31)).astype(np.float64)
+    xn = xn + np.rot90(xn, 1, axes=(2, 3)) + np.rot90(xn, 2, axes=(2, 3)) + np.rot90(xn, 3, axes=(2, 3))
+    assert np.array_equal(C.forward_ri_bf16(p, xn), C.forward_ri(p, xn))
