@@ -339,7 +339,15 @@ def time_classifier(dev, n_infer=32768, batch=256, steps=40, arch="small"):
                     "(training = 3 x forward)"}
 
 
-def time_fma_engine(dev, stream, R, S, bad, Hs, args, steps=3):
+def measured_alu_peaks():
+    """FP32 and FP64 FMA peaks of this GPU in TFLOP/s, measured by the
+    library's FMA-chain probe (sfft_probe_fma_peak)."""
+    from paper_2603_08593_gb300 import binding
+    return {"fp32_tflops": binding.probe_fma_peak(False), "fp64_tflops": binding.probe_fma_peak(True),
+            "how": "sfft_probe_fma_peak: 8 independent FMA chains per thread, 8 x 256 threads per SM, CUDA events"}
+
+
+def time_fma_engine(dev, stream, R, S, bad, Hs, args, alu_peaks, steps=3):
     """The same subtraction with the KK contraction on the FP32 FMA pipes:
     CCD-pairs/s and the contraction's FP32 ALU roofline (derived peak)."""
     import torch
@@ -360,11 +368,11 @@ def time_fma_engine(dev, stream, R, S, bad, Hs, args, steps=3):
     sec = e0.elapsed_time(e1) / 1e3 / steps
     kk_ms = prof["contract_kk"][0] / steps
     flop = kk_flops_per_ccd(Hs, W, L, DK)
-    peak = fp32_alu_peak_tflops(2070.0)
+    peak = alu_peaks["fp32_tflops"]
     out = {"value": 1.0 / sec, "unit": UNIT, "ms_per_step": sec * 1e3, "steps": steps,
            "contract_kk_ms": kk_ms, "alu_tflops": flop / (kk_ms * 1e-3) / 1e12,
-           "alu_frac": flop / (kk_ms * 1e-3) / 1e12 / peak,
-           "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)",
+           "alu_frac": flop / (kk_ms * 1e-3) / 1e12 / peak, "alu_peak_tflops": peak,
+           "peak_note": "FP32 FMA peak of measured (sfft_probe_fma_peak, this run)",
            "status": [int(v) for v in o["info"].cpu()],
            "note": "the KK lag contraction on the FP32 FMA pipes (SFFT_FLAG_FMA_CONTRACT), tensor cores used by "
                    "the stamp classifier only; phase timing adds events inside the step"}
@@ -447,6 +455,7 @@ def run_gpu(args):
                     "cpu": cpu_model()}
 
     stream = torch.cuda.Stream(device=dev)
+    alu_peaks = measured_alu_peaks()
     R = torch.from_numpy(np.stack([p["R"] for p in pairs])).to(dev).contiguous()
     S = torch.from_numpy(np.stack([p["S"] for p in pairs])).to(dev).contiguous()
     bad = torch.from_numpy(np.stack([p["bad"] for p in pairs])).to(dev).contiguous()
@@ -544,7 +553,7 @@ def run_gpu(args):
     # the KK contraction on the FP32 FMA pipes (tensor cores left to the stamp classifier), same pair
     fma_rec = None
     if not batched and not args.no_fma_engine and args.prec == "mixed" and not args.fma_contract:
-        fma_rec = time_fma_engine(dev, stream, R, S, bad, Hs, args)
+        fma_rec = time_fma_engine(dev, stream, R, S, bad, Hs, args, alu_peaks)
     # the 60-CCD exposure in one graph-captured call, per GPU
     expo = None
     if expo_pairs is not None:
@@ -603,12 +612,11 @@ def run_gpu(args):
         else:
             per_launch_flop = B * kk_flops_per_ccd(Hs, W, L, DK) / (n_launch / args.steps)
             achieved = per_launch_flop / (avg_ms * 1e-3) / 1e12
-            clock = 2070.0
-            peak = fp32_alu_peak_tflops(clock)
+            peak = alu_peaks["fp32_tflops"]
             roof = {"bound": "alu", "kernel": "k_contract (product-spectrum lag contraction, FP32 FMA)",
                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                     "traffic": args.traffic if args.traffic is not None else (kk_traffic_bytes("kernels_contract.cu") if full else None),
-                    "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz max SM clock (derived, not measured)",
+                    "peak_note": "FP32 FMA peak of measured (sfft_probe_fma_peak, this run)",
                     "avg_launch_ms": avg_ms, "launches_per_step": n_launch / args.steps,
                     "traffic_note": "DRAM read+write bytes per launch, one-pass ncu capture of this workload"}
         if batched:
@@ -625,6 +633,17 @@ def run_gpu(args):
             if ms > 0:
                 gbs = nbytes / (ms * 1e-3) / 1e9
                 hbm[k] = {"bytes": nbytes, "ms": ms, "gbs": gbs, "frac": gbs / pk}
+    solve_rec = None
+    if prof.get("solve") and prof["solve"][0] > 0:
+        Nn = L * L * n_mono(DK) + n_mono(DB)
+        # Cholesky N^3 / 3 multiply-adds, and two triangular solves (N^2 each) for the
+        # solution and for the refinement step
+        flop = B * (2.0 * Nn ** 3 / 3.0 + (1 + REFINE) * 2 * 2.0 * Nn * Nn)
+        ms = prof["solve"][0] / args.steps
+        solve_rec = {"ms": ms, "flop": flop, "fp64_tflops": flop / (ms * 1e-3) / 1e12,
+                     "fp64_frac": flop / (ms * 1e-3) / 1e12 / alu_peaks["fp64_tflops"],
+                     "note": "FP64 solve phase (factorisation, substitutions, units) against the measured FP64 "
+                             "FMA peak"}
     if batched:
         workload = (f"{B} CCD pairs of one DECam exposure per GPU per step (2048x4096 FP32 each, independent PSF "
                     f"gradients, masked fractions 2-30 %, cosmics, bleed trails) in one CUDA-graph-captured call; "
@@ -645,7 +664,7 @@ def run_gpu(args):
                        "l2": "256 MB buffer written between timed steps (L2 flushed)"},
             "roofline": roof, "cpu_baseline": cpu_base, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "status": info, "wall_s": wall, "fp64_path": fp64, "classifier": classifier,
-            "hbm": hbm, "fma_engine": fma_rec, "exposure": expo,
+            "hbm": hbm, "fma_engine": fma_rec, "exposure": expo, "alu_peaks": alu_peaks, "solve": solve_rec,
             "phases_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
     print(json.dumps(line), flush=True)
     if dist is not None:

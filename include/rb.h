@@ -131,6 +131,18 @@ sfft_status_t rb_detect(int32_t H, int32_t W, int32_t batch, const float* D, con
  * central 7 x 7 is below 0.3 and the axis ratio is below 2.5. */
 sfft_status_t rb_shape_cuts(const float* stamps, const float* snr, int64_t n, float psf_fwhm, float snr_min,
                             int32_t* pass, void* stream);
+/* The same cuts with a noise-robust size estimate (the paper's Sec. 2.3.4
+ * fallback reading: SNR and PSF-shape cuts; the estimator is this library's
+ * choice): the FWHM and axis ratio come from Gaussian-weighted adaptive
+ * second moments of the difference channel over the central 15 x 15 (40
+ * iterations of w = exp(-(r - mu)^T M^-1 (r - mu) / 2), mu = sum w I r / sum w I,
+ * M = 2 sum w I (r - mu)(r - mu)^T / sum w I, starting from the PSF width at the
+ * centre), which converge to a Gaussian source's own covariance and give
+ * distant noise no weight.  A candidate fails when its weighted flux is not
+ * positive, M is not positive definite, the centroid moves more than 3 px or
+ * M grows past 25 px^2.  Same arguments and layouts as rb_shape_cuts. */
+sfft_status_t rb_shape_cuts_adaptive(const float* stamps, const float* snr, int64_t n, float psf_fwhm,
+                                     float snr_min, int32_t* pass, void* stream);
 
 #ifdef __cplusplus
 }

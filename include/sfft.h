@@ -136,6 +136,12 @@ int32_t       sfft_plan_ccd_group(sfft_plan_t plan);
  * The barrier is a software flag wait with no asynchronous copies or
  * tensor-core work in flight, so giving up leaves nothing pending. */
 sfft_status_t sfft_plan_set_wait_limit(sfft_plan_t plan, int32_t tries);
+/* Measured FMA peak of this GPU for roofline reports (no counterpart in the
+ * paper): FP32 (fp64 = 0) or FP64 (fp64 = 1) TFLOP/s = 2 x FMAs / time of a
+ * kernel of independent FMA chains, 8 CTAs of 256 threads per SM, timed with
+ * CUDA events on `cuda_stream` after one warm-up launch (synchronizes the
+ * stream).  Allocates and frees a small device buffer for the results. */
+sfft_status_t sfft_probe_fma_peak(int32_t fp64, double* tflops, void* cuda_stream);
 /* Number of device allocations the library's plans (and the plan-time
  * autotuner) currently hold.  For leak checks: with SFFT_FAIL_ALLOC=n set in
  * the environment, the n-th device allocation of every sfft_plan call fails

@@ -43,6 +43,7 @@ SIGNATURES = {
     "sfft_plan_ccd_group": (I32, [VP]),
     "sfft_plan_set_wait_limit": (I32, [VP, I32]),
     "sfft_debug_live_allocations": (I64, []),
+    "sfft_probe_fma_peak": (I32, [I32, C.POINTER(C.c_double), VP]),
     "sfft_build_normal": (I32, [VP, VP, VP, VP, VP, VP, VP, VP]),
     "sfft_solve": (I32, [VP, VP, VP, VP, I32, VP, VP, VP, VP, VP]),
     "sfft_apply": (I32, [VP, VP, VP, VP, VP, VP, VP]),
@@ -79,6 +80,7 @@ SIGNATURES = {
     "rb_detect_workspace_bytes": (SZ, [I32, I32, I32, I32]),
     "rb_detect": (I32, [I32, I32, I32, VP, VP, VP, VP, C.c_float, C.c_float, I32, I32, VP, VP, VP, VP, VP, VP]),
     "rb_shape_cuts": (I32, [VP, VP, I64, C.c_float, C.c_float, VP, VP]),
+    "rb_shape_cuts_adaptive": (I32, [VP, VP, I64, C.c_float, C.c_float, VP, VP]),
     # differential photometry and multi-template combination (include/phot.h)
     "phot_aperture_flux": (I32, [I32, I32, I32, VP, VP, VP, I32, DBL, VP, VP, VP]),
     "phot_limiting_workspace_bytes": (SZ, [I32, I32]),
@@ -130,6 +132,16 @@ def _device(device):
 
 def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def probe_fma_peak(fp64=False, stream=None):
+    """Measured FMA peak of the current GPU in TFLOP/s (FP32 or FP64)."""
+    import torch
+    lib = load()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    v = C.c_double()
+    _check(lib.sfft_probe_fma_peak(1 if fp64 else 0, C.byref(v), VP(s.cuda_stream)), "sfft_probe_fma_peak")
+    return float(v.value)
 
 
 def apply_noalloc(R, S, theta, sky, D, L, DK, DB, prec="mixed", stream=None):
@@ -440,15 +452,18 @@ class Detector:
         return self.xy, self.snr, self.count, self.stamps
 
 
-def shape_cuts(stamps, snr, psf_fwhm, snr_min=5.0, out=None, stream=None):
-    """Plain SNR/shape cuts on [n][3][31][31] stamps: int32 pass flags."""
+def shape_cuts(stamps, snr, psf_fwhm, snr_min=5.0, out=None, stream=None, adaptive=False):
+    """Plain SNR/shape cuts on [n][3][31][31] stamps: int32 pass flags.
+    adaptive=True takes the size and axis ratio from Gaussian-weighted adaptive
+    moments (rb_shape_cuts_adaptive) instead of the positive 9 x 9's moments."""
     import torch
     _need(stamps, torch.float32, "stamps")
     _need(snr, torch.float32, "snr")
     n = stamps.shape[0]
     out = out if out is not None else torch.empty(n, dtype=torch.int32, device=stamps.device)
-    _check(load().rb_shape_cuts(_ptr(stamps), _ptr(snr), n, float(psf_fwhm), float(snr_min), _ptr(out),
-                                _stream(stamps, stream)), "rb_shape_cuts")
+    fn = load().rb_shape_cuts_adaptive if adaptive else load().rb_shape_cuts
+    _check(fn(_ptr(stamps), _ptr(snr), n, float(psf_fwhm), float(snr_min), _ptr(out), _stream(stamps, stream)),
+           "rb_shape_cuts_adaptive" if adaptive else "rb_shape_cuts")
     return out
 
 

@@ -28,20 +28,21 @@
 // end.  k_lag_dft (kernels_lag_dft.cu) then forms the lags u_x of every
 // (d, u_y) pair, summing the k-slots in FP32 runs of 16 and FP64 across runs.
 //
-// Roles (448 threads, one CTA per SM):
-//   warps 0-7  A producers: lane l of warp w is difference 32 (w % 4) + l of
-//              the tile (tensor-memory lane 32 (w % 4) + l); warps 0-3 take
-//              the even k-steps (four rows y') and warps 4-7 the odd ones; one
+// Roles (704 threads, one CTA per SM):
+//   warps 0-15 A producers: lane l of warp w is difference 32 (w % 4) + l of
+//              the tile (tensor-memory lane 32 (w % 4) + l); warp group w / 4
+//              takes k-step w / 4 (four rows y') of every chunk, so that four
+//              k-steps' stores to tensor memory are in flight at once; one
 //              16-byte load per row gives both k-slots' probe values, split
 //              into 2 x 16 A columns (tcgen05.st); warps 0-3 then run the
 //              epilogue;
-//   warps 8-11 B producers: the weight-row blocks (TF32 and BF16) of both
+//   warps 16-19 B producers: the weight-row blocks (TF32 and BF16) of both
 //              k-slots for each staged chunk of 16 rows y', every row written
 //              to its even and its odd block, a half-warp filling one 128-byte
 //              core matrix per store;
-//   warp 12    MMA issuer: per pair of k-steps and k-slot, four MMAs of
+//   warp 20    MMA issuer: per pair of k-steps and k-slot, four MMAs of
 //              N = 32 nu (TF32 and BF16 of both k-steps) back to back;
-//   warp 13    copy producer: per chunk one tensor-map box of probe rows
+//   warp 21    copy producer: per chunk one tensor-map box of probe rows
 //              (128 differences x 17 rows x 2 slots, from the k-slot-blocked
 //              product spectra [d][k / 16][y][k % 16]), one box of weight rows
 //              per exponent and the powers of yt.
@@ -63,6 +64,7 @@ constexpr int CH = kDlChunk;          // rows y' per staged chunk
 constexpr int KSC = CH / 4;           // k-steps per chunk
 constexpr int NU = kDlMaxU;           // u_y per CTA at most
 constexpr int GA = 4;                 // k-steps of A operands in flight
+constexpr int NST = 3;                // staged chunks of probe and weight rows in flight
 constexpr int PBR = CH + 1;           // probe rows per box: a spare row staggers the lanes' banks
 constexpr int PBYTES = 128 * PBR * 16;
 constexpr int VR = CH + NU;           // weight rows per box (CH + NU - 1 used)
@@ -70,9 +72,10 @@ constexpr int VSLOT = (VR * 16 + 127) / 128 * 128;
 constexpr int NQ = (4 * (KSC - 1) + NU - 1) / 2 + 2;   // weight-row blocks (row pairs) per chunk
 constexpr int QB = 1024;              // bytes per block: even and odd row pairs of the 32 columns n
 constexpr int WBLK = NQ * QB;         // bytes of one chunk's blocks per k-slot and operand format
-constexpr int WARP_BP = 8;            // first B-producer warp
-constexpr int WARP_MMA = 12, WARP_COPY = 13;
-constexpr int NTHREADS = 32 * 14;
+constexpr int WARP_BP = 16;           // first B-producer warp (warps 0-15: A producers, one k-step of a chunk each)
+constexpr int WARP_MMA = 20, WARP_COPY = 21;
+constexpr int NTHREADS = 32 * 22;
+static_assert(WARP_BP / 4 == KSC, "one A-producer warp group per k-step of a chunk");
 constexpr int TMEM_COLS = 512;        // D: 2 x NU x 32 columns, A: GA x 32 columns
 static_assert(2 * NU * 32 + GA * 32 <= TMEM_COLS, "tensor memory budget");
 static_assert(CH % 8 == 0 && VR % 2 == 0 && GA % 2 == 0, "chunk geometry: k-steps in pairs");
@@ -85,9 +88,9 @@ struct DStage {
 static_assert(PBYTES % 128 == 0 && sizeof(DStage) % 128 == 0, "tensor copy alignment");
 
 struct DSmem {
-  DStage st[2];
+  DStage st[NST];
   uint8_t wblk[2][2][2][WBLK];     // [stage][slot][TF32, BF16] weight-row blocks
-  uint64_t raw_full[2], raw_empty[2], strip_full[2], strip_empty[2];
+  uint64_t raw_full[NST], raw_empty[NST], strip_full[2], strip_empty[2];
   uint64_t a_full[GA], a_empty[GA], done;
   uint32_t tmem_base;
   int abort;
@@ -118,12 +121,14 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
   const int nchunk = y1 > y0 ? (y1 - ulo - Ys + CH - 1) / CH : 0;
   const int nstep = nchunk * KSC;
   // ---- setup: zeroed stages (lanes past the tile read zeros), barriers, tensor memory
-  for (int i = threadIdx.x; i < (int)(sizeof(DStage) * 2 / 16); i += NTHREADS)
+  for (int i = threadIdx.x; i < (int)(sizeof(DStage) * NST / 16); i += NTHREADS)
     reinterpret_cast<float4*>(&S.st[0])[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < NST; ++i) {
       mbar_init(&S.raw_full[i], 1);
-      mbar_init(&S.raw_empty[i], 12);
+      mbar_init(&S.raw_empty[i], WARP_BP + 4);
+    }
+    for (int i = 0; i < 2; ++i) {
       mbar_init(&S.strip_full[i], 4);
       mbar_init(&S.strip_empty[i], 1);
     }
@@ -148,8 +153,8 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
 
   if (warp == WARP_COPY) {
     for (int c = 0; c < nchunk; ++c) {
-      const int sidx = c & 1;
-      if (c >= 2 && !wait_phase(&S.raw_empty[sidx], (unsigned)(((c >> 1) - 1) & 1), abort)) break;
+      const int sidx = c % NST;
+      if (c >= NST && !wait_phase(&S.raw_empty[sidx], (unsigned)(((c / NST) - 1) & 1), abort)) break;
       DStage& st = S.st[sidx];
       const int yc = Ys + c * CH;
       // powers of yt for the weight rows inside the image (the others are masked)
@@ -231,14 +236,14 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
     for (int it = 0; it < kMaxSpin && !mbar_try_wait(&S.done, 0); ++it) {
     }
   } else if (warp < WARP_BP) {
-    // ---- A producers: warp w takes the k-steps j = w / 4 (mod 2)
+    // ---- A producers: warp w takes the k-step j = w / 4 of every chunk
     const int q = 32 * (warp & 3) + lane;
     const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
     for (int c = 0; c < nchunk && !*abort; ++c) {
-      const int sidx = c & 1;
-      if (!wait_phase(&S.raw_full[sidx], (unsigned)((c >> 1) & 1), abort)) break;
+      const int sidx = c % NST;
+      if (!wait_phase(&S.raw_full[sidx], (unsigned)((c / NST) & 1), abort)) break;
       const uint8_t* P = &S.st[sidx].P[q * PBR * 16];
-      for (int j = warp >> 2; j < KSC; j += 2) {
+      for (int j = warp >> 2; j < KSC; j += WARP_BP / 4) {
         const int g = c * KSC + j, as = g % GA;
         if (g >= GA && !wait_phase(&S.a_empty[as], (unsigned)(((g / GA) - 1) & 1), abort)) break;
         uint32_t v[2][16];
@@ -289,13 +294,13 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
     const bool live = m < NMONO;
     const int nre = (m / 8) * 128 + (m % 8) * 16, nim = ((16 + m) / 8) * 128 + (m % 8) * 16;
     for (int c = 0; c < nchunk && !*abort; ++c) {
-      const int sidx = c & 1;
-      if (!wait_phase(&S.raw_full[sidx], (unsigned)((c >> 1) & 1), abort)) break;
-      if (c >= 2 && !wait_phase(&S.strip_empty[sidx], (unsigned)(((c >> 1) - 1) & 1), abort)) break;
+      const int sidx = c % NST, widx = c & 1;   // raw stage, weight-block stage
+      if (!wait_phase(&S.raw_full[sidx], (unsigned)((c / NST) & 1), abort)) break;
+      if (c >= 2 && !wait_phase(&S.strip_empty[widx], (unsigned)(((c >> 1) - 1) & 1), abort)) break;
       const DStage& st = S.st[sidx];
       const int ybase = Ys + c * CH + ulo;
-      uint8_t* tf0 = &S.wblk[sidx][s][0][0];
-      uint8_t* bf0 = &S.wblk[sidx][s][1][0];
+      uint8_t* tf0 = &S.wblk[widx][s][0][0];
+      uint8_t* bf0 = &S.wblk[widx][s][1][0];
 #pragma unroll 2
       for (int srow = 2 * (e >> 1) + rpar; srow < VR - 1; srow += 4) {
         const int y = ybase + srow;
@@ -322,18 +327,18 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) {
-        mbar_arrive(&S.strip_full[sidx]);
+        mbar_arrive(&S.strip_full[widx]);
         mbar_arrive(&S.raw_empty[sidx]);
       }
     }
   }
 
-  // ---- drain: the copies of the last two chunks issued land before the
+  // ---- drain: the copies of the last NST chunks issued land before the
   // stages are reused (earlier phases of a stage report complete at once)
   if (warp == WARP_COPY)
-    for (int c = issued_chunks - 2; c < issued_chunks; ++c) {
+    for (int c = issued_chunks - NST; c < issued_chunks; ++c) {
       if (c < 0) continue;
-      for (int it = 0; it < kMaxSpin && !mbar_try_wait(&S.raw_full[c & 1], (unsigned)((c >> 1) & 1)); ++it) {
+      for (int it = 0; it < kMaxSpin && !mbar_try_wait(&S.raw_full[c % NST], (unsigned)((c / NST) & 1)); ++it) {
       }
     }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -370,6 +370,74 @@ __global__ void k_shape_cuts(const float* __restrict__ stamps, const float* __re
   pass[i] = (0.5 * psf_fwhm <= fwhm && fwhm <= 2.0 * psf_fwhm && neg_frac < 0.3 && ratio < 2.5) ? 1 : 0;
 }
 
+// The same cuts with the size and axis ratio from Gaussian-weighted adaptive
+// moments of the difference channel over the central 15 x 15: from a round
+// weight of the PSF's width at the centre, 40 times w = exp(-(r - mu)^T M^-1
+// (r - mu) / 2), mu = sum w I r / sum w I, M = 2 sum w I (r - mu)(r - mu)^T /
+// sum w I (a Gaussian source of covariance C is the fixed point M = C); a
+// candidate whose weighted flux is not positive, whose M is not positive
+// definite, whose centroid moves more than 3 px or whose M grows past
+// 25 px^2 fails.  One thread per stamp, FP64.
+constexpr int kAmHalf = 7, kAmIters = 40;
+
+__global__ void k_shape_cuts_adaptive(const float* __restrict__ stamps, const float* __restrict__ snr, int64_t n,
+                                      double psf_fwhm, double snr_min, int32_t* __restrict__ pass) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int side = 2 * kHalf + 1;
+  const float* d = stamps + (i * 3 + 2) * side * side;
+  const int c = kHalf;
+  const double fw2s = 2.0 * sqrt(2.0 * log(2.0));
+  const double s0w = psf_fwhm / fw2s;
+  double mxx = s0w * s0w, myy = s0w * s0w, mxy = 0.0, mx = 0.0, my = 0.0;
+  bool ok = (double)snr[i] >= snr_min;
+  for (int it = 0; ok && it < kAmIters; ++it) {
+    const double det = mxx * myy - mxy * mxy;
+    if (!(det > 0.0 && mxx > 0.0 && myy > 0.0)) { ok = false; break; }
+    const double ia = myy / det, ib = -mxy / det, ic = mxx / det;   // M^-1 = [[ia, ib], [ib, ic]]
+    double s0 = 0.0, sx = 0.0, sy = 0.0, sxx = 0.0, syy = 0.0, sxy = 0.0;
+    for (int yy = -kAmHalf; yy <= kAmHalf; ++yy)
+      for (int xx = -kAmHalf; xx <= kAmHalf; ++xx) {
+        const double dx = xx - mx, dy = yy - my;
+        const double wv = exp(-0.5 * (ia * dx * dx + 2.0 * ib * dx * dy + ic * dy * dy)) *
+                          (double)d[(c + yy) * side + c + xx];
+        s0 += wv;
+        sx += wv * xx;
+        sy += wv * yy;
+        sxx += wv * xx * xx;
+        syy += wv * yy * yy;
+        sxy += wv * xx * yy;
+      }
+    if (!(s0 > 0.0)) { ok = false; break; }
+    mx = sx / s0;
+    my = sy / s0;
+    // central moments about the new centroid from the raw sums
+    mxx = 2.0 * (sxx / s0 - mx * mx);
+    myy = 2.0 * (syy / s0 - my * my);
+    mxy = 2.0 * (sxy / s0 - mx * my);
+    if (fabs(mx) > 3.0 || fabs(my) > 3.0 || mxx > 25.0 || myy > 25.0) ok = false;
+  }
+  if (ok && !(mxx * myy - mxy * mxy > 0.0 && mxx > 0.0 && myy > 0.0)) ok = false;
+  if (!ok) {
+    pass[i] = 0;
+    return;
+  }
+  const double tr = mxx + myy, det = mxx * myy - mxy * mxy;
+  const double disc = sqrt(fmax(tr * tr / 4.0 - det, 0.0));
+  const double l1 = tr / 2.0 + disc, l2 = fmax(tr / 2.0 - disc, 1e-12);
+  const double fwhm = fw2s * sqrt(0.5 * (l1 + l2));
+  double neg = 0.0, absum = 0.0;
+  for (int yy = -3; yy <= 3; ++yy)
+    for (int xx = -3; xx <= 3; ++xx) {
+      const double v = (double)d[(c + yy) * side + c + xx];
+      neg += fabs(fmin(v, 0.0));
+      absum += fabs(v);
+    }
+  const double neg_frac = neg / fmax(absum, 1e-12);
+  const double ratio = sqrt(l1 / l2);
+  pass[i] = (0.5 * psf_fwhm <= fwhm && fwhm <= 2.0 * psf_fwhm && neg_frac < 0.3 && ratio < 2.5) ? 1 : 0;
+}
+
 sfft_status_t fail(cudaError_t e, const char* where) {
   sfft::set_last_error((std::string(where) + ": " + cudaGetErrorString(e)).c_str());
   return SFFT_ERR_CUDA;
@@ -440,4 +508,14 @@ extern "C" sfft_status_t rb_shape_cuts(const float* stamps, const float* snr, in
                                                                                              snr_min, pass);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SFFT_OK : fail(e, "rb_shape_cuts");
+}
+
+extern "C" sfft_status_t rb_shape_cuts_adaptive(const float* stamps, const float* snr, int64_t n, float psf_fwhm,
+                                                float snr_min, int32_t* pass, void* stream) {
+  if (n < 0 || (n > 0 && (!stamps || !snr || !pass)) || !(psf_fwhm > 0.f)) return SFFT_ERR_ARG;
+  if (n == 0) return SFFT_OK;
+  k_shape_cuts_adaptive<<<(unsigned)((n + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(
+      stamps, snr, n, psf_fwhm, snr_min, pass);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SFFT_OK : fail(e, "rb_shape_cuts_adaptive");
 }

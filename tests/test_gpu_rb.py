@@ -343,3 +343,32 @@ def test_shape_cuts_match_oracle():
     exp = np.array([C.shape_cuts(st[i, 2], float(snr[i]), 1.8, 5.0) for i in range(400)], np.int32)
     assert np.array_equal(out, exp)
     assert 0 < exp.sum() < 400
+
+
+def test_adaptive_shape_cuts_match_oracle():
+    """The adaptive-moment cuts: the GPU's 40 FP64 iterations against the
+    oracle's on the same stamps.  exp and the sums round differently on the
+    two sides, so a decision may differ only where the oracle's own size,
+    axis ratio or negative fraction lies within 1e-6 (relative) of a cut."""
+    from paper_2603_08593_gb300 import shape_cuts
+    d = make_stamps(400, seed=18)
+    rng = np.random.default_rng(3)
+    snr = rng.uniform(2, 60, 400).astype(np.float32)
+    st = d["stamps"].copy()
+    st[:5, 2] = 0.0                          # no flux: the weighted flux is not positive
+    out = shape_cuts(_dev(st), _dev(snr), psf_fwhm=1.8, snr_min=5.0, adaptive=True).cpu().numpy()
+    exp = np.array([C.shape_cuts_adaptive(st[i, 2], float(snr[i]), 1.8, 5.0) for i in range(400)], np.int32)
+    diff = np.nonzero(out != exp)[0]
+    for i in diff:
+        res = C.adaptive_moments(st[i, 2].astype(np.float64), 1.8 / 2.3548200450309493)
+        assert res is not None, i
+        (mxx, myy, mxy), _ = res
+        tr, det = mxx + myy, mxx * myy - mxy * mxy
+        disc = np.sqrt(max(tr * tr / 4 - det, 0.0))
+        l1, l2 = tr / 2 + disc, tr / 2 - disc
+        fw = 2.3548200450309493 * np.sqrt(0.5 * (l1 + l2))
+        margins = [abs(fw / (0.5 * 1.8) - 1), abs(fw / (2.0 * 1.8) - 1), abs(np.sqrt(l1 / l2) / 2.5 - 1)]
+        assert min(margins) < 1e-6, (i, margins)
+    assert len(diff) <= 2
+    assert 0 < exp.sum() < 400
+    assert not out[:5].any()
