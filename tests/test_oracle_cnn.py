@@ -310,7 +310,7 @@ def test_ri_bf16_model_equals_fp64_network_when_operands_are_exact():
 
 
 # ---------------------------------------------------------------- noise-robust shape cuts
-def _gauss_stamp(cov, flux=1000.0, centre=(0.0, 0.0)):
+def _gauss_cov_stamp(cov, flux=1000.0, centre=(0.0, 0.0)):
     yy, xx = np.mgrid[-15:16, -15:16].astype(np.float64)
     ci = np.linalg.inv(np.asarray(cov, dtype=np.float64))
     dx, dy = xx - centre[0], yy - centre[1]
@@ -321,21 +321,21 @@ def test_adaptive_moments_recover_a_gaussian():
     """A noiseless round Gaussian of sigma 1.5 sampled at the pixel centres:
     the moments of a sampled Gaussian equal the continuous ones up to
     exp(-2 pi^2 sigma^2) (Poisson summation), so M = sigma^2 I to 1e-6."""
-    (mxx, myy, mxy), (mx, my) = C.adaptive_moments(_gauss_stamp(np.eye(2) * 2.25), 1.0)
+    (mxx, myy, mxy), (mx, my) = C.adaptive_moments(_gauss_cov_stamp(np.eye(2) * 2.25), 1.0)
     assert abs(mxx - 2.25) < 1e-6 * 2.25 and abs(myy - 2.25) < 1e-6 * 2.25 and abs(mxy) < 1e-9
     assert abs(mx) < 1e-12 and abs(my) < 1e-12
     # an elliptical, rotated, off-centre Gaussian: its covariance and centre
     th = 0.5
     rot = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
     cov = rot @ np.diag([4.0, 1.0]) @ rot.T
-    (mxx, myy, mxy), (mx, my) = C.adaptive_moments(_gauss_stamp(cov, centre=(0.4, -0.7)), 1.0)
+    (mxx, myy, mxy), (mx, my) = C.adaptive_moments(_gauss_cov_stamp(cov, centre=(0.4, -0.7)), 1.0)
     # (the 15 x 15 window cuts the weighted profile of the 2 px major axis at ~4.5 of its widths)
     assert np.allclose([mxx, myy, mxy], [cov[0, 0], cov[1, 1], cov[0, 1]], rtol=0, atol=1e-5)
     assert abs(mx - 0.4) < 1e-5 and abs(my + 0.7) < 1e-5
 
 
 def test_adaptive_moments_ignore_distant_noise_and_reject_hits():
-    g = _gauss_stamp(np.eye(2) * 2.25)
+    g = _gauss_cov_stamp(np.eye(2) * 2.25)
     noisy = g.copy()
     noisy[0:3, :] += 200.0          # a bright band 12 px away: negligible weight
     (mxx, _, _), _ = C.adaptive_moments(noisy, 1.0)
@@ -347,4 +347,4 @@ def test_adaptive_moments_ignore_distant_noise_and_reject_hits():
     assert C.shape_cuts_adaptive(g, 20.0, fw)
     assert not C.shape_cuts_adaptive(hit, 20.0, fw)
     assert not C.shape_cuts_adaptive(g, 4.0, fw)                      # below the SNR cut
-    assert not C.shape_cuts_adaptive(_gauss_stamp(np.diag([9.0, 1.0])), 20.0, fw)   # axis ratio 3
+    assert not C.shape_cuts_adaptive(_gauss_cov_stamp(np.diag([9.0, 1.0])), 20.0, fw)   # axis ratio 3
