@@ -136,6 +136,18 @@ int32_t       sfft_plan_ccd_group(sfft_plan_t plan);
  * The barrier is a software flag wait with no asynchronous copies or
  * tensor-core work in flight, so giving up leaves nothing pending. */
 sfft_status_t sfft_plan_set_wait_limit(sfft_plan_t plan, int32_t tries);
+/* Wait attribution of the difference-lane contraction kernel (a profiling
+ * aid; no counterpart in the paper).  In a library built with
+ * -DSFFT_DLANE_WAIT_PROFILE, lane 0 of every warp of k_contract_dlane adds the
+ * clock cycles it spent in each kind of wait to a device array: out[0] copy
+ * warp waiting for a free stage of probe rows, [1] A producers waiting for
+ * probe rows, [2] A producers waiting for a free A slot, [3] A producers
+ * waiting for their tensor-memory stores, [4] B producers waiting for weight
+ * rows, [5] B producers waiting for a free stage of weight-row blocks, [6] MMA
+ * issuer waiting for weight-row blocks, [7] MMA issuer waiting for A operands,
+ * [8] cycles of whole CTAs (thread 0).  Synchronizes the device; reset != 0
+ * clears the array.  SFFT_ERR_UNSUPPORTED in the default build. */
+sfft_status_t sfft_debug_contract_waits(uint64_t* out9, int32_t reset);
 /* Measured FMA peak of this GPU for roofline reports (no counterpart in the
  * paper): FP32 (fp64 = 0) or FP64 (fp64 = 1) TFLOP/s = 2 x FMAs / time of a
  * kernel of independent FMA chains, 8 CTAs of 256 threads per SM, timed with

@@ -44,6 +44,7 @@ SIGNATURES = {
     "sfft_plan_set_wait_limit": (I32, [VP, I32]),
     "sfft_debug_live_allocations": (I64, []),
     "sfft_probe_fma_peak": (I32, [I32, C.POINTER(C.c_double), VP]),
+    "sfft_debug_contract_waits": (I32, [C.POINTER(C.c_uint64), I32]),
     "sfft_build_normal": (I32, [VP, VP, VP, VP, VP, VP, VP, VP]),
     "sfft_solve": (I32, [VP, VP, VP, VP, I32, VP, VP, VP, VP, VP]),
     "sfft_apply": (I32, [VP, VP, VP, VP, VP, VP, VP]),

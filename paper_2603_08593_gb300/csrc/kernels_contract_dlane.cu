@@ -96,13 +96,42 @@ struct DSmem {
   int abort;
 };
 
+// Wait attribution (compile with -DSFFT_DLANE_WAIT_PROFILE): lane 0 of every
+// warp adds the cycles it spends in each kind of wait, and the CTA's total
+// cycles, to a device array that sfft_debug_contract_waits reads.  The
+// default build compiles none of it.
+enum WaitKind {
+  W_COPY_RAW_EMPTY = 0,   // copy warp: a stage of probe rows to be released
+  W_A_RAW_FULL,           // A producers: probe rows to land
+  W_A_SLOT_EMPTY,         // A producers: an A slot in tensor memory to be consumed
+  W_A_STORE,              // A producers: their tensor-memory stores to complete
+  W_B_RAW_FULL,           // B producers: weight rows to land
+  W_B_BLK_EMPTY,          // B producers: a stage of weight-row blocks to be consumed
+  W_MMA_BLK_FULL,         // MMA issuer: weight-row blocks
+  W_MMA_A_FULL,           // MMA issuer: A operands
+  W_CTA_CYCLES,           // per CTA: cycles from setup to the epilogue
+  W_NKIND
+};
+#ifdef SFFT_DLANE_WAIT_PROFILE
+__device__ unsigned long long g_dl_wait[W_NKIND];
+#define DL_T0() long long dl_t0_ = clock64()
+#define DL_ACC(acc, kind) (acc)[kind] += clock64() - dl_t0_
+#else
+#define DL_T0() \
+  do {          \
+  } while (0)
+#define DL_ACC(acc, kind) \
+  do {                    \
+  } while (0)
+#endif
+
 }  // namespace
 
 template <int DM>
 __global__ void __launch_bounds__(NTHREADS, 1)
-k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmV,
-                 const DlJob* __restrict__ jobs, char* __restrict__ ws, int H, int L, int dstride, int pz,
-                 const float* __restrict__ ytab) {
+k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmPs,
+                 const __grid_constant__ CUtensorMap tmV, const DlJob* __restrict__ jobs, char* __restrict__ ws,
+                 int H, int L, int dstride, int pz, int pzs, const float* __restrict__ ytab) {
   constexpr int NMONO = n_mono(DM);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   DSmem& S = *reinterpret_cast<DSmem*>(smem_raw);
@@ -115,7 +144,10 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int w = (L - 1) / 2;
   const int k0 = 2 * blockIdx.y;
-  const int y0 = w, y1 = H - w;                 // weight rows of the band (M_fit vanishes within w of the edges)
+  // weight rows of the CTA's part of the band (M_fit vanishes within w of the
+  // edges); the parts of a job's band go to separate partial-sum buffers
+  const int y0 = job.y_lo, y1 = job.y_hi;
+  (void)w;
   const int ulo = job.u_lo, nu = job.nu;
   const int Ys = y0 - (ulo + nu - 1);           // first row y' any u_y of the CTA needs
   const int nchunk = y1 > y0 ? (y1 - ulo - Ys + CH - 1) / CH : 0;
@@ -150,21 +182,35 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
   const uint32_t t_a = tbase + 2 * NU * 32;    // A: k-step slot g at columns 32 g + 16 s (TF32 0-7, BF16 8-15)
 
   int issued_chunks = 0;   // copy warp: chunks whose copies were issued
+#ifdef SFFT_DLANE_WAIT_PROFILE
+  long long wt[W_NKIND] = {};
+  const long long cta_t0 = clock64();
+#endif
+  // a tile of at most pzs differences takes the smaller probe box (its other
+  // lanes keep the zeros of the setup)
+  const bool small_box = job.nlanes <= pzs;
+  const int pzj = small_box ? pzs : pz;
 
   if (warp == WARP_COPY) {
     for (int c = 0; c < nchunk; ++c) {
       const int sidx = c % NST;
-      if (c >= NST && !wait_phase(&S.raw_empty[sidx], (unsigned)(((c / NST) - 1) & 1), abort)) break;
+      {
+        DL_T0();
+        const bool ok_w = c < NST || wait_phase(&S.raw_empty[sidx], (unsigned)(((c / NST) - 1) & 1), abort);
+        DL_ACC(wt, W_COPY_RAW_EMPTY);
+        if (!ok_w) break;
+      }
       DStage& st = S.st[sidx];
       const int yc = Ys + c * CH;
       // powers of yt for the weight rows inside the image (the others are masked)
       const int ylo = max(yc + ulo, 0), yhi = min(yc + ulo + VR, H);
       const unsigned ybytes = yhi > ylo ? (unsigned)(yhi - ylo) * 64u : 0u;
       if (lane == 0)
-        mbar_arrive_expect_tx(&S.raw_full[sidx], (unsigned)(pz * PBR * 16 + (DM + 1) * VR * 16) + ybytes);
+        mbar_arrive_expect_tx(&S.raw_full[sidx], (unsigned)(pzj * PBR * 16 + (DM + 1) * VR * 16) + ybytes);
       __syncwarp();
       if (lane == 0) {
-        tma_load_4d(&st.P[0], &tmP, 2 * (k0 & 15), yc, k0 >> 4, job.zp + job.d_first, &S.raw_full[sidx]);
+        tma_load_4d(&st.P[0], small_box ? &tmPs : &tmP, 2 * (k0 & 15), yc, k0 >> 4, job.zp + job.d_first,
+                    &S.raw_full[sidx]);
       } else if (lane <= DM + 1) {
         const int a = lane - 1;
         tma_load_3d(&st.V[a][0], &tmV, 2 * k0, yc + ulo, job.zw + a, &S.raw_full[sidx]);
@@ -181,7 +227,12 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
     const uint64_t dblk0 = smem_desc_kn(smem_u32(&S.wblk[0][0][0][0]), QB, 128);
     for (int c = 0; c < nchunk && !*abort; ++c) {
       const int sidx = c & 1;
-      if (!wait_phase(&S.strip_full[sidx], (unsigned)((c >> 1) & 1), abort)) break;
+      {
+        DL_T0();
+        const bool ok_w = wait_phase(&S.strip_full[sidx], (unsigned)((c >> 1) & 1), abort);
+        DL_ACC(wt, W_MMA_BLK_FULL);
+        if (!ok_w) break;
+      }
       uint64_t dw[2][2];   // descriptors of the stage's blocks: [slot][TF32, BF16]
 #pragma unroll
       for (int s = 0; s < 2; ++s)
@@ -192,8 +243,11 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
       // TF32 (j + 1), BF16 (j + 1) back to back
       for (int j = 0; j < KSC; j += 2) {
         const int g = c * KSC + j, as = g % GA;   // k-steps g, g + 1 in A slots as, as + 1
-        if (!wait_phase(&S.a_full[as], (unsigned)((g / GA) & 1), abort) ||
-            !wait_phase(&S.a_full[as + 1], (unsigned)(((g + 1) / GA) & 1), abort)) {
+        DL_T0();
+        const bool ok_a = wait_phase(&S.a_full[as], (unsigned)((g / GA) & 1), abort) &&
+                          wait_phase(&S.a_full[as + 1], (unsigned)(((g + 1) / GA) & 1), abort);
+        DL_ACC(wt, W_MMA_A_FULL);
+        if (!ok_a) {
           live = false;
           break;
         }
@@ -241,11 +295,21 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
     const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
     for (int c = 0; c < nchunk && !*abort; ++c) {
       const int sidx = c % NST;
-      if (!wait_phase(&S.raw_full[sidx], (unsigned)((c / NST) & 1), abort)) break;
+      {
+        DL_T0();
+        const bool ok_w = wait_phase(&S.raw_full[sidx], (unsigned)((c / NST) & 1), abort);
+        DL_ACC(wt, W_A_RAW_FULL);
+        if (!ok_w) break;
+      }
       const uint8_t* P = &S.st[sidx].P[q * PBR * 16];
       for (int j = warp >> 2; j < KSC; j += WARP_BP / 4) {
         const int g = c * KSC + j, as = g % GA;
-        if (g >= GA && !wait_phase(&S.a_empty[as], (unsigned)(((g / GA) - 1) & 1), abort)) break;
+        {
+          DL_T0();
+          const bool ok_w = g < GA || wait_phase(&S.a_empty[as], (unsigned)(((g / GA) - 1) & 1), abort);
+          DL_ACC(wt, W_A_SLOT_EMPTY);
+          if (!ok_w) break;
+        }
         uint32_t v[2][16];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -268,7 +332,11 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
                          "r"(v[h][3]), "r"(v[h][4]), "r"(v[h][5]), "r"(v[h][6]), "r"(v[h][7]), "r"(v[h][8]),
                          "r"(v[h][9]), "r"(v[h][10]), "r"(v[h][11]), "r"(v[h][12]), "r"(v[h][13]), "r"(v[h][14]),
                          "r"(v[h][15]) : "memory");
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        {
+          DL_T0();
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+          DL_ACC(wt, W_A_STORE);
+        }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.a_full[as]);
@@ -295,8 +363,18 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
     const int nre = (m / 8) * 128 + (m % 8) * 16, nim = ((16 + m) / 8) * 128 + (m % 8) * 16;
     for (int c = 0; c < nchunk && !*abort; ++c) {
       const int sidx = c % NST, widx = c & 1;   // raw stage, weight-block stage
-      if (!wait_phase(&S.raw_full[sidx], (unsigned)((c / NST) & 1), abort)) break;
-      if (c >= 2 && !wait_phase(&S.strip_empty[widx], (unsigned)(((c >> 1) - 1) & 1), abort)) break;
+      {
+        DL_T0();
+        const bool ok_w = wait_phase(&S.raw_full[sidx], (unsigned)((c / NST) & 1), abort);
+        DL_ACC(wt, W_B_RAW_FULL);
+        if (!ok_w) break;
+      }
+      {
+        DL_T0();
+        const bool ok_w = c < 2 || wait_phase(&S.strip_empty[widx], (unsigned)(((c >> 1) - 1) & 1), abort);
+        DL_ACC(wt, W_B_BLK_EMPTY);
+        if (!ok_w) break;
+      }
       const DStage& st = S.st[sidx];
       const int ybase = Ys + c * CH + ulo;
       uint8_t* tf0 = &S.wblk[widx][s][0][0];
@@ -345,6 +423,12 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const bool ok = nstep > 0 && !S.abort && mbar_try_wait(&S.done, 0);
+#ifdef SFFT_DLANE_WAIT_PROFILE
+  if (threadIdx.x == 0) wt[W_CTA_CYCLES] = clock64() - cta_t0;
+  if (lane == 0)
+    for (int k = 0; k < W_NKIND; ++k)
+      if (wt[k]) atomicAdd(&g_dl_wait[k], (unsigned long long)wt[k]);
+#endif
   if (threadIdx.x == 0 && !ok) atomicOr(reinterpret_cast<int*>(ws + job.status), 4);
 
   // ---- epilogue: the accumulators of lane q (difference d_first + q) to C[k][d][u_y][32]
@@ -391,15 +475,20 @@ static cudaError_t contract_dlane_dm(const sfft_plan_s* p, int batch_index, int 
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int ntot = p->d_batch * p->ccd_group;   // product spectra held: one d-batch of a CCD group
   const int pz = std::min(128, ntot);           // differences per probe box
-  CUtensorMap mp, mv;
+  // the last tile of a d-batch (93 differences at L = 11) copies a box of its
+  // own size rounded up to 8 differences: 27 % fewer copy lines for its CTAs
+  const int last_tile = p->d_batch - 128 * ((p->d_batch - 1) / 128);
+  const int pzs = std::min(pz, (last_tile + 7) / 8 * 8);
+  CUtensorMap mp, mps, mv;
   char* base = static_cast<char*>(ws);
   if (!make_map_blk(&mp, base + p->phat.off, p->M, H, ntot, 4, PBR, pz) ||
+      !make_map_blk(&mps, base + p->phat.off, p->M, H, ntot, 4, PBR, pzs) ||
       !make_map(&mv, base + p->wspec.off, p->M, H, p->n_wa * B, 4, VR, 1))
     return cudaErrorInvalidValue;
   const int per_ccd = njobs / B;   // jobs are ordered CCD-major, the same count per CCD
   dim3 grid(per_ccd, p->M / 2, nc);
-  kern<<<grid, NTHREADS, smem, p->stream>>>(mp, mv, p->d_dljobs + job0 + (int64_t)c0 * per_ccd, (char*)ws, H, L,
-                                            p->d_batch, pz, (const float*)p->ytab);
+  kern<<<grid, NTHREADS, smem, p->stream>>>(mp, mps, mv, p->d_dljobs + job0 + (int64_t)c0 * per_ccd, (char*)ws, H, L,
+                                            p->d_batch, pz, pzs, (const float*)p->ytab);
   p->nlaunch += 1;
   return cudaGetLastError();
 }
@@ -414,3 +503,21 @@ cudaError_t launch_contract_dlane(const sfft_plan_s* p, int batch_index, int c0,
 }
 
 }  // namespace sfft
+
+extern "C" sfft_status_t sfft_debug_contract_waits(uint64_t* out, int32_t reset) {
+#ifdef SFFT_DLANE_WAIT_PROFILE
+  if (!out) return SFFT_ERR_ARG;
+  unsigned long long h[sfft::W_NKIND];
+  if (cudaMemcpyFromSymbol(h, sfft::g_dl_wait, sizeof(h)) != cudaSuccess) return SFFT_ERR_CUDA;
+  for (int k = 0; k < sfft::W_NKIND; ++k) out[k] = h[k];
+  if (reset) {
+    const unsigned long long z[sfft::W_NKIND] = {};
+    if (cudaMemcpyToSymbol(sfft::g_dl_wait, z, sizeof(z)) != cudaSuccess) return SFFT_ERR_CUDA;
+  }
+  return SFFT_OK;
+#else
+  (void)out;
+  (void)reset;
+  return SFFT_ERR_UNSUPPORTED;
+#endif
+}
