@@ -141,8 +141,7 @@ static void build_layout(sfft_plan_s* p) {
   add_region(p->swave, cur, sizeof(double) * 2 * p->N * B);
   add_region(p->vec, cur, sizeof(double) * 4 * p->N * B);
   // lane-per-difference contraction: k-slot products C[k][d_local][u_y][32] per CCD of a group
-  add_region(p->cbuf, cur,
-             p->dl ? sizeof(float) * (size_t)p->M * p->d_batch * p->d.L * 32 * p->ccd_group * kDlBandParts : 0);
+  add_region(p->cbuf, cur, p->dl ? sizeof(float) * (size_t)p->M * p->d_batch * p->d.L * 32 * p->ccd_group : 0);
   add_region(p->theta_off, cur, sizeof(double) * p->N * B);
   p->ws_bytes = cur;
 }
@@ -309,13 +308,13 @@ static void build_dl_jobs(sfft_plan_s* p) {
           uhi = std::max(uhi, std::min(w, d.x + w));
         }
         const int nrun = (uhi - ulo + kDlMaxU) / kDlMaxU;
-        for (int part = 0; part < kDlBandParts; ++part) {
-          const int y_lo = w + (H - 2 * w) * part / kDlBandParts, y_hi = w + (H - 2 * w) * (part + 1) / kDlBandParts;
+        {
+          const int y_lo = w, y_hi = H - w;
           for (int r = 0; r < nrun; ++r) {
             // runs of near-equal length
             const int a = ulo + (uhi - ulo + 1) * r / nrun, b = ulo + (uhi - ulo + 1) * (r + 1) / nrun;
             DlJob j;
-            j.cbuf = (int64_t)(p->cbuf.off + ((size_t)part * p->ccd_group + (size_t)(ccd % p->ccd_group)) * cb_ccd);
+            j.cbuf = (int64_t)(p->cbuf.off + (size_t)(ccd % p->ccd_group) * cb_ccd);
             j.status = (int64_t)(p->status.off + sizeof(int) * (size_t)ccd);
             j.zp = (ccd % p->ccd_group) * p->d_batch;
             j.zw = ccd * p->n_wa;

@@ -144,8 +144,7 @@ k_contract_dlane(const __grid_constant__ CUtensorMap tmP, const __grid_constant_
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int w = (L - 1) / 2;
   const int k0 = 2 * blockIdx.y;
-  // weight rows of the CTA's part of the band (M_fit vanishes within w of the
-  // edges); the parts of a job's band go to separate partial-sum buffers
+  // weight rows of the band (M_fit vanishes within w of the edges)
   const int y0 = job.y_lo, y1 = job.y_hi;
   (void)w;
   const int ulo = job.u_lo, nu = job.nu;

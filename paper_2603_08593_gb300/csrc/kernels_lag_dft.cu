@@ -13,8 +13,8 @@ namespace sfft {
 // to FP64; the 16 groups are then summed in FP64 in a fixed order.
 template <int DM>
 __global__ void __launch_bounds__(256)
-k_lag_dft(const int4* __restrict__ pairs, const char* __restrict__ cbuf0, size_t cbuf_ccd, size_t cbuf_part,
-          double* __restrict__ g0, size_t g_ccd, int M, int Nf, int L, int dstride, const float2* __restrict__ twD) {
+k_lag_dft(const int4* __restrict__ pairs, const char* __restrict__ cbuf0, size_t cbuf_ccd, double* __restrict__ g0,
+          size_t g_ccd, int M, int Nf, int L, int dstride, const float2* __restrict__ twD) {
   // blockIdx.y: the CCD within its group (k-slot products); g0 points at the group's first CCD
   constexpr int NMONO = n_mono(DM);
   constexpr int NG = 16, W5 = (kMaxL - 1) / 2;
@@ -37,16 +37,9 @@ k_lag_dft(const int4* __restrict__ pairs, const char* __restrict__ cbuf0, size_t
 #pragma unroll
     for (int t = 0; t < RUN; ++t) {
       const int k = kb + NG * t;
-      // the partial sums of the band's parts, added in FP32
       const float* ck = C + (int64_t)(k < M ? k : 0) * kstride;
-      float sr = 0.f, si = 0.f;
-#pragma unroll
-      for (int part = 0; part < kDlBandParts; ++part) {
-        sr += k < M ? __ldg(ck + part * cbuf_part + m) : 0.f;
-        si += k < M ? __ldg(ck + part * cbuf_part + 16 + m) : 0.f;
-      }
-      cr[t] = sr;
-      ci[t] = si;
+      cr[t] = k < M ? __ldg(ck + m) : 0.f;
+      ci[t] = k < M ? __ldg(ck + 16 + m) : 0.f;
     }
 #pragma unroll
     for (int t = 0; t < RUN; ++t) {
@@ -91,10 +84,8 @@ static cudaError_t lag_dft_dm(const sfft_plan_s* p, int batch_index, int c0, int
   const size_t g_ccd = (size_t)p->n_hd * L * L * n_mono(DM);
   double* g0 = ws_at<double>(ws, p->gkk) + (size_t)c0 * g_ccd + (size_t)batch_index * p->d_batch * L * L * n_mono(DM);
   dim3 grid(npair, nc);
-  const size_t cbuf_part = cbuf_ccd / sizeof(float) * p->ccd_group;   // floats between band parts
   k_lag_dft<DM><<<grid, 256, 0, p->stream>>>(p->d_dlpairs + pair0, static_cast<char*>(ws) + p->cbuf.off, cbuf_ccd,
-                                             cbuf_part, g0, g_ccd, p->M, p->Nf, L, p->d_batch,
-                                             (const float2*)p->twD);
+                                             g0, g_ccd, p->M, p->Nf, L, p->d_batch, (const float2*)p->twD);
   p->nlaunch += 1;
   return cudaGetLastError();
 }

@@ -47,18 +47,14 @@ constexpr int kUmmaMaxDiffs = 16;
 // one CTA per (two k-slots, tile of up to 128 differences, up to kDlMaxU
 // consecutive u_y); its accumulators go to C[k][d_local][u_y][32]
 struct DlJob {
-  int64_t cbuf, status;   // byte offsets: the CCD's C buffer of the d-batch (of the job's band part), status
+  int64_t cbuf, status;   // byte offsets: the CCD's C buffer of the d-batch, status
   int zp, zw;             // the CCD's first product / weight spectrum in the batch-wide tensor maps
   int d_first, nlanes;    // the tile: differences [d_first, d_first + nlanes) of the d-batch
   int u_lo, nu;           // u_y = u_lo .. u_lo + nu - 1
-  int y_lo, y_hi;         // weight rows [y_lo, y_hi): one part of the band [w, H - w)
+  int y_lo, y_hi;         // weight rows [y_lo, y_hi): the band [w, H - w)
 };
 constexpr int kDlChunk = 16;
 constexpr int kDlMaxU = 6;
-// the weight-row band of every tile and u_y run is cut into this many parts,
-// each its own CTA with its own partial k-slot products (summed by the lag
-// DFT): twice as many, half as long CTAs shorten the grid's last wave
-constexpr int kDlBandParts = 1;
 
 }  // namespace sfft
 

@@ -6,7 +6,7 @@ whose wait is bounded.  With the limit set to zero polls, every CTA that is
 not the last to arrive gives up at once (the CTA that factors the first
 diagonal block arrives microseconds after the others), so every CCD reports
 SFFT_ERR_TIMEOUT, the kernels return, and the next call on the same plan,
-with the default limit, gives the oracle's answer.  The tensor-core and
+with the default limit, gives the oracle's answer (one CCD and a batch).  The tensor-core and
 bulk-copy waits are not made to expire here: copies or MMAs could still be
 in flight when a CTA leaves."""
 import ctypes
@@ -21,25 +21,26 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def test_barrier_wait_runs_out_then_plan_recovers():
+@pytest.mark.parametrize("batch", [1, 2])
+def test_barrier_wait_runs_out_then_plan_recovers(batch):
     from paper_2603_08593_gb300 import Plan, binding
     L, DK, DB = 7, 2, 2
-    imgs = [small_pair(150, 210, seed=6100 + i, mask_fraction=0.03) for i in range(2)]
+    imgs = [small_pair(150, 210, seed=6100 + i, mask_fraction=0.03) for i in range(batch)]
     refs = [O.fit(x["R"], x["S"], x["bad"], L, DK, DB) for x in imgs]
     dev = torch.device("cuda", torch.cuda.current_device())
     R = torch.from_numpy(np.stack([x["R"] for x in imgs])).to(dev)
     S = torch.from_numpy(np.stack([x["S"] for x in imgs])).to(dev)
     bad = torch.from_numpy(np.stack([x["bad"] for x in imgs])).to(dev)
     sky = torch.tensor([[r["prep"]["s_R"], r["prep"]["s_S"]] for r in refs], dtype=torch.float64, device=dev)
-    plan = Plan(150, 210, L, DK, DB, batch=2, prec="mixed", device=dev)
+    plan = Plan(150, 210, L, DK, DB, batch=batch, prec="mixed", device=dev)
     plan.set_wait_limit(0)
     o = plan.subtract(R, S, bad, sky, refine=1)
     torch.cuda.synchronize()
-    assert [int(v) for v in o["info"].cpu()] == [binding.SFFT_ERR_TIMEOUT] * 2
+    assert [int(v) for v in o["info"].cpu()] == [binding.SFFT_ERR_TIMEOUT] * batch
     plan.set_wait_limit(-1)
     o = plan.subtract(R, S, bad, sky, refine=1, out=o)
     torch.cuda.synchronize()
-    assert [int(v) for v in o["info"].cpu()] == [0, 0]
+    assert [int(v) for v in o["info"].cpu()] == [0] * batch
     th, D = o["theta"].cpu().numpy(), o["D"].cpu().numpy()
     for i, r in enumerate(refs):
         assert O.kernel_coef_rel_err(th[i], r["theta_orig"], L, DK, DB) <= 1e-5
