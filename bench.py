@@ -37,16 +37,14 @@ WORKLOAD = ("one DECam CCD pair per GPU per step: 2048x4096 FP32, 20k stars, PSF
             "50 transients; L=11, D_K=D_B=2, mixed precision, 1 refinement step")
 # DRAM bytes (read + write) of one full-size KK contraction launch (all 221
 # differences), from a one-pass ncu capture of the benchmark workload
-# (profiles/dram_per_kernel_*.md); reported only while the kernel source is the
+# (profiles/k_contract_*.md); reported only while the kernel source is the
 # one that was measured.  Keys: the kernel's source file.
 KK_TRAFFIC = {
     "kernels_contract.cu": (10.09e9, "1a847c15ebf73406"),      # FP32 FMA kernel (--fma-contract)
     "kernels_contract_tc.cu": (None, ""),                      # mma.sync kernel (--mma-sync-contract)
     "kernels_contract_umma.cu": (9.975e9, "0d3c235754a7a213"),  # tcgen05, one lane per (d, u_y) pair
-    # tcgen05, one lane per difference (default); measured on the source with
-    # sha256 prefix 301479bab2fe6f96, whose k_contract_dlane and launcher are
-    # byte-identical to this file's (the lag DFT moved to kernels_lag_dft.cu)
-    "kernels_contract_dlane.cu": (11.585e9, "1d4954879467044d"),
+    # tcgen05, one lane per difference (default)
+    "kernels_contract_dlane.cu": (8.786e9, "3b64716d63df8ddd"),
 }
 PHASES = ("prep", "fft_weights", "fft_prod", "contract_kk", "contract_rk", "scatter", "solve", "apply", "lag_dft")
 

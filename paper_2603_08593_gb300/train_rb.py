@@ -166,7 +166,9 @@ def scores(model, stamps):
     return model.score(stamps.contiguous()).cpu().numpy()
 
 
-def cut_flags(stamps, snr, fwhm, ccd, snr_min=5.0):
+def cut_flags(stamps, snr, fwhm, ccd, snr_min=5.0, adaptive=False):
+    """The SNR/shape cuts per CCD (its PSF FWHM); adaptive=True sizes the
+    sources with Gaussian-weighted adaptive moments."""
     import torch
     from .binding import shape_cuts
     out = np.zeros(len(snr), np.int32)
@@ -175,7 +177,7 @@ def cut_flags(stamps, snr, fwhm, ccd, snr_min=5.0):
         sel = np.nonzero(ccd == c)[0]
         idx = torch.as_tensor(sel, device=stamps.device)
         out[sel] = shape_cuts(stamps.index_select(0, idx).contiguous(), snr_t.index_select(0, idx).contiguous(),
-                              float(fwhm[sel[0]]), snr_min).cpu().numpy()
+                              float(fwhm[sel[0]]), snr_min, adaptive=adaptive).cpu().numpy()
     return out
 
 
@@ -186,8 +188,17 @@ def rates(flag, lab):
             "n_real": int(real.sum()), "n_bogus": int(bogus.sum())}
 
 
-def judge(sc, cuts, lab, kind):
-    """Rates at 0.3 / 0.6, the cuts' rates, and the gain at matched operating points."""
+def judge(sc, cuts, lab, kind, cuts_adaptive=None):
+    """Rates at 0.3 / 0.6, the cuts' rates, and the gain at matched operating
+    points; with cuts_adaptive, the same comparison against the cuts whose
+    size comes from adaptive moments (under "adaptive_cuts")."""
+    if cuts_adaptive is not None:
+        out = judge(sc, cuts, lab, kind)
+        alt = judge(sc, cuts_adaptive, lab, kind)
+        out["adaptive_cuts"] = {k: alt[k] for k in ("cuts", "cnn_fpr_at_cuts_completeness",
+                                                     "cnn_completeness_at_cuts_fpr", "cuts_rejection_by_kind")
+                                if k in alt}
+        return out
     out = {"cnn_0.3": rates(sc >= 0.3, lab), "cnn_0.6": rates(sc >= 0.6, lab), "cuts": rates(cuts == 1, lab)}
     real, bogus = sc[lab == 1], sc[lab == 0]
     cc, cf = out["cuts"]["completeness"], out["cuts"]["fpr"]
@@ -254,7 +265,8 @@ def run(train_ccds=3000, epochs=5, batch=256, lr=1e-3, eval_ccds=60, seed=500, l
     for name, idx in (("validation", i_va), ("test", i_te)):
         sc = scores(model, take(idx))
         cuts = cut_flags(take(idx), ctr["snr"][idx], ctr["fwhm"][idx], ctr["ccd"][idx])
-        report[name] = judge(sc, cuts, lab[idx], kind[idx])
+        cuts_a = cut_flags(take(idx), ctr["snr"][idx], ctr["fwhm"][idx], ctr["ccd"][idx], adaptive=True)
+        report[name] = judge(sc, cuts, lab[idx], kind[idx], cuts_a)
     if ev_pairs:
         t3 = time.time()
         cev = candidates(ev_pairs, chunk=10, max_cand=4096)
@@ -264,7 +276,8 @@ def run(train_ccds=3000, epochs=5, batch=256, lr=1e-3, eval_ccds=60, seed=500, l
         torch.cuda.synchronize()
         t_inf = time.time() - t4
         cuts = cut_flags(cev["stamps"], cev["snr"], cev["fwhm"], cev["ccd"])
-        report["exposure"] = judge(sc, cuts, lab_e, kind_e)
+        cuts_a = cut_flags(cev["stamps"], cev["snr"], cev["fwhm"], cev["ccd"], adaptive=True)
+        report["exposure"] = judge(sc, cuts, lab_e, kind_e, cuts_a)
         report["exposure"]["ccds"] = eval_ccds
         report["exposure"]["candidates"] = int(len(lab_e))
         report["exposure"]["subtract_detect_seconds"] = t4 - t3

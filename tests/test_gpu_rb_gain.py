@@ -1,4 +1,5 @@
-"""What the trained classifier gains over the plain SNR/shape cuts, on
+"""What the trained classifier gains over the plain SNR/shape cuts (and over
+the same cuts with a noise-robust adaptive-moment size), on
 candidates that the GPU subtraction and detector produce from synthetic pairs
 (injection truth labels).  A reduced version of the classifier experiment:
 300 training pairs of 512 x 512, three epochs, judged on the held-out 15 %."""
@@ -20,3 +21,10 @@ def test_trained_network_beats_cuts():
     assert te["cnn_completeness_at_cuts_fpr"] > te["cuts"]["completeness"], te
     assert te["cnn_auc"] > 0.95, te
     assert report["train"]["loss_by_epoch"][-1] < report["train"]["loss_by_epoch"][0]
+    # the same gain against the noise-robust (adaptive-moment) cuts, which keep
+    # more real transients than the plain cuts
+    ad = te["adaptive_cuts"]
+    print("plain cuts", te["cuts"], "adaptive cuts", ad["cuts"])
+    assert ad["cuts"]["completeness"] > te["cuts"]["completeness"], (ad, te["cuts"])
+    assert ad["cnn_fpr_at_cuts_completeness"] < ad["cuts"]["fpr"], ad
+    assert ad["cnn_completeness_at_cuts_fpr"] > ad["cuts"]["completeness"], ad
