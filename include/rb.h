@@ -58,6 +58,28 @@ sfft_status_t rb_set_state(rb_model_t m, const void* host_buf, size_t bytes, int
 sfft_status_t rb_logits(rb_model_t m, const float* stamps, int64_t n, float* logit, void* stream);
 sfft_status_t rb_score(rb_model_t m, const float* stamps, int64_t n, float* score, void* stream);
 
+/* One fused inference convolution of the model, the step rb_logits runs per
+ * layer: 3 x 3 'same' convolution with the model's weights rounded to BF16,
+ * FP32 bias, ReLU and 2 x 2 max-pool (floor), BF16 output, on the tcgen05
+ * tensor cores with FP32 accumulation.
+ *   layer 1: in  = normalised stamps, BF16 NHWC [n][31][31][3];
+ *            out = the conv2 input planes, (CB, HP, WO) = (4, 18, 16)
+ *   layer 2: in  = those planes;  out = the conv3 input planes, (8, 10, 8)
+ *   layer 3: in  = those planes;  out = BF16 NHWC [n][3][3][64]
+ * Planes are BF16 [CB][n_alloc][HP][WO][8]: for channel block cb and stamp i,
+ * record (r, c) holds channels 8 cb .. 8 cb + 7 of pixel (r - 1, c - 1) and
+ * every other record must be zero; the layer reads whole planes of stamps < n
+ * and writes only the interiors of stamps < n.  Device pointers, 16-byte
+ * aligned; 0 <= n <= n_alloc <= 2^24 (n = 0 does nothing).  SFFT_ERR_ARG for
+ * a bad layer, sizes, alignment or null pointers.  Asynchronous on `stream`;
+ * a bounded wait that gave up sets the flag that rb_get_error reads. */
+sfft_status_t rb_conv_layer(rb_model_t m, int32_t layer, const void* in, int64_t n, int64_t n_alloc, void* out,
+                            void* stream);
+/* Error flags of the model's tensor-core kernels (synchronous): 0 none, bit 0
+ * a bounded wait gave up.  Sticky for the model's lifetime; while set,
+ * rb_logits and rb_score return NaN logits and scores. */
+sfft_status_t rb_get_error(rb_model_t m, int32_t* flags);
+
 /* Mean BCE loss (written to loss_dev, float) and parameter gradients of one
  * batch of n <= max stamps with labels (float 0/1); no parameter update. */
 sfft_status_t rb_backward(rb_model_t m, const float* stamps, const float* labels, int64_t n, float* loss_dev,

@@ -65,6 +65,8 @@ SIGNATURES = {
     "rb_set_state": (I32, [VP, VP, SZ, I64]),
     "rb_logits": (I32, [VP, VP, I64, VP, VP]),
     "rb_score": (I32, [VP, VP, I64, VP, VP]),
+    "rb_conv_layer": (I32, [VP, I32, VP, I64, I64, VP, VP]),
+    "rb_get_error": (I32, [VP, C.POINTER(I32)]),
     "rb_backward": (I32, [VP, VP, VP, I64, VP, VP]),
     "rb_train_step": (I32, [VP, VP, VP, I64, C.c_float, VP, VP]),
     "rbri_create": (I32, [VP, C.POINTER(VP)]),
@@ -385,6 +387,27 @@ class RBModel:
         out = out if out is not None else torch.empty(n, dtype=torch.float32, device=stamps.device)
         _check(self._fn("score")(self.h, _ptr(stamps), n, _ptr(out), _stream(stamps, stream)), f"{self.PREFIX}_score")
         return out
+
+    def conv_layer(self, layer, inp, n, n_alloc, out, stream=None):
+        """One fused inference convolution (include/rb.h rb_conv_layer) on
+        BF16 CUDA tensors: layer 1 reads NHWC stamps, layers 2 and 3 read
+        channel-block planes of n_alloc stamps; writes `out` in place."""
+        import torch
+        if self.PREFIX != "rb":
+            raise NotImplementedError("conv_layer: the three-convolution classifier only")
+        _need(inp, torch.bfloat16, "inp")
+        _need(out, torch.bfloat16, "out")
+        _check(self._fn("conv_layer")(self.h, int(layer), _ptr(inp), int(n), int(n_alloc), _ptr(out),
+                                      _stream(inp, stream)), "rb_conv_layer")
+        return out
+
+    def error_flags(self):
+        """Sticky error flags of the model's tensor-core kernels (synchronous)."""
+        if self.PREFIX != "rb":
+            raise NotImplementedError("error_flags: the three-convolution classifier only")
+        v = I32()
+        _check(self._fn("get_error")(self.h, C.byref(v)), "rb_get_error")
+        return int(v.value)
 
     def backward(self, stamps, labels, loss=None, stream=None):
         import torch

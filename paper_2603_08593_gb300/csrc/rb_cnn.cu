@@ -1,8 +1,12 @@
 // Stamp real-bogus classifier: BF16 tensor-core training and inference.
 //
-// Activations are NHWC.  Every convolution is an implicit GEMM (rb_gemm.cuh:
-// no im2col matrix is written) on mma.sync m16n8k16 BF16 with FP32
-// accumulation: forward  Z[pixel][co] = sum_k x(pixel + tap)[ci] W[k][co];
+// Inference (rb_logits / rb_score) runs the three convolutions on the tcgen05
+// tensor cores, each fused with its bias, ReLU and max-pool (rb_conv_tc.cu:
+// channel-block planes, no FP32 pre-activations in memory).  Training keeps
+// the FP32 pre-activations and pool indices its backward pass needs and runs
+// on the path below.  Activations are NHWC.  Every training convolution is an
+// implicit GEMM (rb_gemm.cuh: no im2col matrix is written) on mma.sync
+// m16n8k16 BF16 with FP32 accumulation: forward  Z[pixel][co] = sum_k x(pixel + tap)[ci] W[k][co];
 // weight gradient  dW[k][co] = sum_pixel dZ[pixel][co] x(pixel + tap)[ci]
 // (split over pixels, partial sums added in a fixed order); input gradient
 // dX[pixel][ci] = sum_(tap, co) dZ(pixel - tap)[co] W[(tap, ci)][co].  Master
@@ -27,6 +31,7 @@
 #include "rb.h"
 #include "rb_gemm.cuh"
 #include "rb_layers.cuh"
+#include "rb_tc.h"
 
 namespace {
 
@@ -115,6 +120,11 @@ struct rb_model_s {
   float *z1 = nullptr, *z2 = nullptr, *z3 = nullptr, *z4 = nullptr, *logit = nullptr, *dz5 = nullptr,
         *da = nullptr, *part = nullptr;
   uint8_t *i1 = nullptr, *i2 = nullptr, *i3 = nullptr;
+  // inference: BF16 weight images of the convolutions and the zero-bordered
+  // channel-block planes of the conv2 and conv3 inputs; error word of the
+  // tensor-core kernels (sticky: logits are NaN once a wait gave up)
+  bf16 *img1 = nullptr, *img2 = nullptr, *img3 = nullptr, *p2 = nullptr, *p3 = nullptr;
+  int* err = nullptr;
 };
 
 namespace {
@@ -122,7 +132,8 @@ namespace {
 void free_model(rb_model_s* m) {
   void* ptrs[] = {m->params, m->grads, m->adam_m, m->adam_v, m->wbf, m->xn,  m->a1,   m->a2,   m->a3,
                   m->dzb,    m->dz4,   m->z1,     m->z2,     m->z3,  m->z4, m->logit, m->dz5,  m->da,
-                  m->part,   m->i1,    m->i2,     m->i3};
+                  m->part,   m->i1,    m->i2,     m->i3,  m->img1, m->img2, m->img3, m->p2,   m->p3,
+                  m->err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -132,8 +143,26 @@ bool alloc(T** p, size_t n) {
   return cudaMalloc((void**)p, sizeof(T) * (n > 0 ? n : 1)) == cudaSuccess;
 }
 
-// forward for n <= max_batch normalised stamps in m->xn; logits to m->logit
-cudaError_t forward(rb_model_s* m, int n, cudaStream_t s, bool keep_idx) {
+// inference forward for n <= max_batch normalised stamps in m->xn: fused
+// tcgen05 convolutions, then the dense layers; logits to m->logit
+cudaError_t forward_infer(rb_model_s* m, int n, cudaStream_t s) {
+  using rbg::Dense;
+  const float* P = m->params;
+  cudaError_t e;
+  if ((e = rbtc::conv1_tc(m->xn, n, m->img1, P + OB1, m->p2, m->max_batch, m->err, s))) return e;
+  if ((e = rbtc::conv2_tc(m->p2, n, m->img2, P + OB2, m->p3, m->max_batch, m->err, s))) return e;
+  if ((e = rbtc::conv3_tc(m->p3, n, m->img3, P + OB3, m->a3, m->max_batch, m->err, s))) return e;
+  if ((e = igemm<Dense, Dense, false>(s, n, F4, K4, Dense{m->a3, n, K4, K4}, Dense{m->wbf + OW4, K4, F4, F4}, m->z4,
+                                      F4, P + OB4)))
+    return e;
+  k_fc2<<<(n * 32 + 255) / 256, 256, 0, s>>>(m->z4, P + OW5, P + OB5, n, m->logit, m->err);
+  return cudaGetLastError();
+}
+
+// training forward for n <= max_batch normalised stamps in m->xn (FP32
+// pre-activations and pool indices kept for the backward pass); logits to
+// m->logit
+cudaError_t forward(rb_model_s* m, int n, cudaStream_t s) {
   using rbg::ConvRows;
   using rbg::Conv1Rows;
   using rbg::Dense;
@@ -144,17 +173,17 @@ cudaError_t forward(rb_model_s* m, int n, cudaStream_t s, bool keep_idx) {
   if ((e = igemm<Conv1Rows, Dense, false>(s, n * PIX1, C1, K1, Conv1Rows{m->xn, n, S31, S31},
                                           Dense{W + OW1, K1, C1, C1}, m->z1, C1, P + OB1)))
     return e;
-  k_relu_pool<<<grid1((int64_t)n * PIX2 * C1), 256, 0, s>>>(m->z1, n, S31, S31, C1, m->a1, keep_idx ? m->i1 : nullptr);
+  k_relu_pool<<<grid1((int64_t)n * PIX2 * C1), 256, 0, s>>>(m->z1, n, S31, S31, C1, m->a1, m->i1);
   // conv2 (32 -> 64)
   if ((e = igemm<ConvRows, Dense, false>(s, n * PIX2, C2, K2, ConvRows{m->a1, n, 15, 15, C1, 1},
                                          Dense{W + OW2, K2, C2, C2}, m->z2, C2, P + OB2)))
     return e;
-  k_relu_pool<<<grid1((int64_t)n * PIX3 * C2), 256, 0, s>>>(m->z2, n, 15, 15, C2, m->a2, keep_idx ? m->i2 : nullptr);
+  k_relu_pool<<<grid1((int64_t)n * PIX3 * C2), 256, 0, s>>>(m->z2, n, 15, 15, C2, m->a2, m->i2);
   // conv3 (64 -> 64)
   if ((e = igemm<ConvRows, Dense, false>(s, n * PIX3, C3, K3, ConvRows{m->a2, n, 7, 7, C2, 1},
                                          Dense{W + OW3, K3, C3, C3}, m->z3, C3, P + OB3)))
     return e;
-  k_relu_pool<<<grid1((int64_t)n * PIX4 * C3), 256, 0, s>>>(m->z3, n, 7, 7, C3, m->a3, keep_idx ? m->i3 : nullptr);
+  k_relu_pool<<<grid1((int64_t)n * PIX4 * C3), 256, 0, s>>>(m->z3, n, 7, 7, C3, m->a3, m->i3);
   // fc1 (NHWC flatten of a3 matches the W4 rows) and fc2
   if ((e = igemm<Dense, Dense, false>(s, n, F4, K4, Dense{m->a3, n, K4, K4}, Dense{W + OW4, K4, F4, F4}, m->z4, F4,
                                       P + OB4)))
@@ -206,7 +235,10 @@ cudaError_t backward(rb_model_s* m, int n, const float* labels, float* loss_dev,
   return cudaGetLastError();
 }
 
-void refresh_bf16(rb_model_s* m, cudaStream_t s) { k_to_bf16<<<grid1(NMASTER), 256, 0, s>>>(m->params, NMASTER, m->wbf); }
+void refresh_bf16(rb_model_s* m, cudaStream_t s) {
+  k_to_bf16<<<grid1(NMASTER), 256, 0, s>>>(m->params, NMASTER, m->wbf);
+  rbtc::build_weight_images(m->params + OW1, m->params + OW2, m->params + OW3, m->img1, m->img2, m->img3, s);
+}
 
 sfft_status_t fail(cudaError_t e, const char* where) {
   sfft::set_last_error((std::string(where) + ": " + cudaGetErrorString(e)).c_str());
@@ -232,7 +264,10 @@ extern "C" sfft_status_t rb_create(const int32_t* desc, rb_model_t* out) {
             alloc(&m->z3, (size_t)B * PIX3 * C3) && alloc(&m->z4, (size_t)B * F4) && alloc(&m->logit, (size_t)B) &&
             alloc(&m->dz5, (size_t)B) && alloc(&m->da, (size_t)B * PIX2 * C1 + B * K4) &&
             alloc(&m->i1, (size_t)B * PIX2 * C1) && alloc(&m->i2, (size_t)B * PIX3 * C2) &&
-            alloc(&m->i3, (size_t)B * PIX4 * C3) && alloc(&m->part, (size_t)kMaxSplits * K4 * F4);
+            alloc(&m->i3, (size_t)B * PIX4 * C3) && alloc(&m->part, (size_t)kMaxSplits * K4 * F4) &&
+            alloc(&m->img1, rbtc::kWImg1) && alloc(&m->img2, rbtc::kWImg2) && alloc(&m->img3, rbtc::kWImg3) &&
+            alloc(&m->p2, (size_t)B * rbtc::kP2.CB * rbtc::kP2.per_stamp_elems()) &&
+            alloc(&m->p3, (size_t)B * rbtc::kP3.CB * rbtc::kP3.per_stamp_elems()) && alloc(&m->err, 1);
   if (!ok) {
     free_model(m);
     delete m;
@@ -255,6 +290,10 @@ extern "C" sfft_status_t rb_create(const int32_t* desc, rb_model_t* out) {
   if (e == cudaSuccess) e = cudaMemset(m->adam_m, 0, sizeof(float) * NMASTER);
   if (e == cudaSuccess) e = cudaMemset(m->adam_v, 0, sizeof(float) * NMASTER);
   if (e == cudaSuccess) e = cudaMemset(m->grads, 0, sizeof(float) * NMASTER);
+  // the planes' borders stay zero: the convolutions write interiors only
+  if (e == cudaSuccess) e = cudaMemset(m->p2, 0, sizeof(bf16) * (size_t)B * rbtc::kP2.CB * rbtc::kP2.per_stamp_elems());
+  if (e == cudaSuccess) e = cudaMemset(m->p3, 0, sizeof(bf16) * (size_t)B * rbtc::kP3.CB * rbtc::kP3.per_stamp_elems());
+  if (e == cudaSuccess) e = cudaMemset(m->err, 0, sizeof(int));
   if (e == cudaSuccess) {
     refresh_bf16(m, nullptr);
     e = cudaDeviceSynchronize();
@@ -335,7 +374,7 @@ extern "C" sfft_status_t rb_logits(rb_model_t m, const float* stamps, int64_t n,
   for (int64_t i0 = 0; i0 < n; i0 += m->max_batch) {
     const int nb = (int)std::min<int64_t>(m->max_batch, n - i0);
     k_normalise<<<(3 * nb + 7) / 8, 256, 0, s>>>(stamps + i0 * 3 * PIX1, nb, m->xn);
-    cudaError_t e = forward(m, nb, s, false);
+    cudaError_t e = forward_infer(m, nb, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(logit + i0, m->logit, sizeof(float) * nb, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return fail(e, "rb_logits");
   }
@@ -350,13 +389,40 @@ extern "C" sfft_status_t rb_score(rb_model_t m, const float* stamps, int64_t n, 
   return e == cudaSuccess ? SFFT_OK : fail(e, "rb_score");
 }
 
+extern "C" sfft_status_t rb_conv_layer(rb_model_t m, int32_t layer, const void* in, int64_t n, int64_t n_alloc,
+                                       void* out, void* stream) {
+  if (!m || layer < 1 || layer > 3 || n < 0 || n > n_alloc || n_alloc < 1 || n_alloc > (1 << 24))
+    return SFFT_ERR_ARG;
+  if (n == 0) return SFFT_OK;
+  if (!in || !out || ((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return SFFT_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bf16* x = static_cast<const bf16*>(in);
+  bf16* y = static_cast<bf16*>(out);
+  const float* P = m->params;
+  const int nn = (int)n, na = (int)n_alloc;
+  cudaError_t e = layer == 1   ? rbtc::conv1_tc(x, nn, m->img1, P + OB1, y, na, m->err, s)
+                  : layer == 2 ? rbtc::conv2_tc(x, nn, m->img2, P + OB2, y, na, m->err, s)
+                               : rbtc::conv3_tc(x, nn, m->img3, P + OB3, y, na, m->err, s);
+  return e == cudaSuccess ? SFFT_OK : fail(e, "rb_conv_layer");
+}
+
+extern "C" sfft_status_t rb_get_error(rb_model_t m, int32_t* flags) {
+  if (!m || !flags) return SFFT_ERR_ARG;
+  int v = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&v, m->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(e, "rb_get_error");
+  *flags = v;
+  return SFFT_OK;
+}
+
 extern "C" sfft_status_t rb_backward(rb_model_t m, const float* stamps, const float* labels, int64_t n,
                                      float* loss_dev, void* stream) {
   if (!m || !stamps || !labels || n < 1 || n > m->max_batch) return SFFT_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int nb = (int)n;
   k_normalise<<<(3 * nb + 7) / 8, 256, 0, s>>>(stamps, nb, m->xn);
-  cudaError_t e = forward(m, nb, s, true);
+  cudaError_t e = forward(m, nb, s);
   if (e == cudaSuccess) e = backward(m, nb, labels, loss_dev, s);
   return e == cudaSuccess ? SFFT_OK : fail(e, "rb_backward");
 }

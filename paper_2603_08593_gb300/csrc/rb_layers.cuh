@@ -178,15 +178,16 @@ __global__ void k_pool_relu_back(const float* __restrict__ da, const uint8_t* __
   }
 }
 
-// dense layer: z5 = relu(z4) . w5 + b5 (FP32, one warp per sample)
+// dense layer: z5 = relu(z4) . w5 + b5 (FP32, one warp per sample); NaN
+// logits when `err` (optional) reports a failed step earlier in the forward
 __global__ void k_fc2(const float* __restrict__ z4, const float* __restrict__ w5, const float* __restrict__ b5,
-                      int n, float* __restrict__ logit) {
+                      int n, float* __restrict__ logit, const int* __restrict__ err = nullptr) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= n) return;
   float s = 0.f;
   for (int i = lane; i < F4; i += 32) s += fmaxf(z4[(int64_t)warp * F4 + i], 0.f) * w5[i];
   s = sfft::warp_sum(s);
-  if (lane == 0) logit[warp] = s + b5[0];
+  if (lane == 0) logit[warp] = (err && *err) ? __int_as_float(0x7fc00000) : s + b5[0];
 }
 
 __global__ void k_sigmoid(const float* __restrict__ z, int64_t n, float* __restrict__ s) {
