@@ -62,7 +62,8 @@ sfft_status_t rb_score(rb_model_t m, const float* stamps, int64_t n, float* scor
  * layer: 3 x 3 'same' convolution with the model's weights rounded to BF16,
  * FP32 bias, ReLU and 2 x 2 max-pool (floor), BF16 output, on the tcgen05
  * tensor cores with FP32 accumulation.
- *   layer 1: in  = normalised stamps, BF16 NHWC [n][31][31][3];
+ *   layer 1: in  = normalised stamps, BF16 [n][2888]: NHWC 31 x 31 x 3
+ *            values, then 5 unused ones (a stamp is 5776 bytes);
  *            out = the conv2 input planes, (CB, HP, WO) = (4, 18, 16)
  *   layer 2: in  = those planes;  out = the conv3 input planes, (8, 10, 8)
  *   layer 3: in  = those planes;  out = BF16 NHWC [n][3][3][64]

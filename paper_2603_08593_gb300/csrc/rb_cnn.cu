@@ -170,7 +170,7 @@ cudaError_t forward(rb_model_s* m, int n, cudaStream_t s) {
   const float* P = m->params;
   cudaError_t e;
   // conv1 (3 -> 32): implicit GEMM over the 27 (padded 32) taps x channels
-  if ((e = igemm<Conv1Rows, Dense, false>(s, n * PIX1, C1, K1, Conv1Rows{m->xn, n, S31, S31},
+  if ((e = igemm<Conv1Rows, Dense, false>(s, n * PIX1, C1, K1, Conv1Rows{m->xn, n, S31, S31, rbtc::kXnStride},
                                           Dense{W + OW1, K1, C1, C1}, m->z1, C1, P + OB1)))
     return e;
   k_relu_pool<<<grid1((int64_t)n * PIX2 * C1), 256, 0, s>>>(m->z1, n, S31, S31, C1, m->a1, m->i1);
@@ -228,7 +228,8 @@ cudaError_t backward(rb_model_s* m, int n, const float* labels, float* loss_dev,
     return e;
   // conv1 (no input gradient)
   k_pool_relu_back<<<grid1((int64_t)n * PIX1 * C1), 256, 0, s>>>(m->da, m->i1, m->z1, n, S31, S31, C1, m->dzb);
-  if ((e = igemm_wgrad(s, C1, K1, n * PIX1, Dense{m->dzb, n * PIX1, C1, C1}, Conv1Rows{m->xn, n, S31, S31},
+  if ((e = igemm_wgrad(s, C1, K1, n * PIX1, Dense{m->dzb, n * PIX1, C1, C1},
+                       Conv1Rows{m->xn, n, S31, S31, rbtc::kXnStride},
                        G + OW1, m->part)))
     return e;
   if ((e = colsum(s, m->dzb, (int64_t)n * PIX1, C1, m->part, G + OB1))) return e;
@@ -256,7 +257,7 @@ extern "C" sfft_status_t rb_create(const int32_t* desc, rb_model_t* out) {
   const int B = desc[0];
   m->max_batch = B;
   bool ok = alloc(&m->params, NMASTER) && alloc(&m->grads, NMASTER) && alloc(&m->adam_m, NMASTER) &&
-            alloc(&m->adam_v, NMASTER) && alloc(&m->wbf, NMASTER) && alloc(&m->xn, (size_t)B * PIX1 * 3) &&
+            alloc(&m->adam_v, NMASTER) && alloc(&m->wbf, NMASTER) && alloc(&m->xn, (size_t)B * rbtc::kXnStride) &&
             alloc(&m->a1, (size_t)B * PIX2 * C1) && alloc(&m->a2, (size_t)B * PIX3 * C2) &&
             alloc(&m->a3, (size_t)B * PIX4 * C3) &&
             alloc(&m->dzb, (size_t)B * PIX1 * C1) && alloc(&m->dz4, (size_t)B * F4) &&
@@ -373,7 +374,7 @@ extern "C" sfft_status_t rb_logits(rb_model_t m, const float* stamps, int64_t n,
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (int64_t i0 = 0; i0 < n; i0 += m->max_batch) {
     const int nb = (int)std::min<int64_t>(m->max_batch, n - i0);
-    k_normalise<<<(3 * nb + 7) / 8, 256, 0, s>>>(stamps + i0 * 3 * PIX1, nb, m->xn);
+    k_normalise<<<nb, 96, 0, s>>>(stamps + i0 * 3 * PIX1, nb, m->xn, rbtc::kXnStride);
     cudaError_t e = forward_infer(m, nb, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(logit + i0, m->logit, sizeof(float) * nb, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return fail(e, "rb_logits");
@@ -421,7 +422,7 @@ extern "C" sfft_status_t rb_backward(rb_model_t m, const float* stamps, const fl
   if (!m || !stamps || !labels || n < 1 || n > m->max_batch) return SFFT_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int nb = (int)n;
-  k_normalise<<<(3 * nb + 7) / 8, 256, 0, s>>>(stamps, nb, m->xn);
+  k_normalise<<<nb, 96, 0, s>>>(stamps, nb, m->xn, rbtc::kXnStride);
   cudaError_t e = forward(m, nb, s);
   if (e == cudaSuccess) e = backward(m, nb, labels, loss_dev, s);
   return e == cudaSuccess ? SFFT_OK : fail(e, "rb_backward");

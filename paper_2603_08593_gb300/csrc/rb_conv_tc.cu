@@ -131,12 +131,10 @@ struct Geo {
   static constexpr int PAD = 2 * C::WO + 8;                // records past the last slot a tap may read
   static constexpr int STK = C::S * HPWO + PAD;            // records per channel-block stack
   static constexpr int IMG = C::NTAP * KS * 32 * C::N;     // weight-image bytes
-  static constexpr int STAGE = LAYER == 1 ? (C::S * 2883 * 2 + 15) / 16 * 16 : 0;   // conv1: NHWC stamps (bytes)
+  static constexpr int STAGE = LAYER == 1 ? C::S * kXnStride * 2 : 0;   // conv1: normalised stamps (bytes)
   static constexpr int XCH = C::WO == 32 ? 16 * 128 * 4 : 0;        // cross-warp pool exchange (bytes)
-  static constexpr int XS = STAGE > XCH ? STAGE : XCH;
-  static constexpr size_t SMEM = (size_t)C::CB * STK * 16 + IMG + XS;
+  static constexpr size_t SMEM = (size_t)C::CB * STK * 16 + IMG + XCH + STAGE;
   static_assert((C::S * HPWO) % 128 == 0, "whole tiles per group");
-  static_assert(LAYER != 1 || C::S % 2 == 0, "conv1 groups start on a 4-byte boundary of the NHWC stamps");
   static_assert(C::HP % 2 == 0 && 128 % C::WO == 0 && (128 / C::WO) % 2 == 0, "pool windows inside a tile");
   static_assert(C::TACC * C::N <= C::TCOLS && STK < 16384, "tensor memory and descriptor ranges");
   static_assert((C::CB * STK * 16) % 128 == 0 && IMG % 128 == 0, "shared-memory alignment");
@@ -156,22 +154,12 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 __device__ __forceinline__ uint32_t bf_bits(bf16 v) { return (uint32_t)__bfloat16_as_ushort(v); }
 
 // conv1 planes of the group's stamps s0 .. s0 + ns - 1 from the normalised
-// NHWC stamps (staged through shared memory); record (r, c) of block 0 holds
-// channels 0-2 of input pixels (r - 1, c - 2), (r - 1, c - 1) and channels 0-1
-// of (r - 1, c); block 1 holds channel 2 of (r - 1, c); zero outside the image
-// and for stamps past ns.
-__device__ __forceinline__ void build_conv1_planes(const bf16* __restrict__ xn, int s0, int ns, uint4* planes,
-                                                   uint32_t* stage) {
+// stamps staged in shared memory (kXnStride values each); record (r, c) of
+// block 0 holds channels 0-2 of input pixels (r - 1, c - 2), (r - 1, c - 1)
+// and channels 0-1 of (r - 1, c); block 1 holds channel 2 of (r - 1, c);
+// zero outside the image and for stamps past ns.
+__device__ __forceinline__ void build_conv1_planes(int ns, uint4* planes, const bf16* sb) {
   using G = Geo<1>;
-  // a stamp is 961 x 3 BF16 = 5766 bytes; s0 is even, so the group starts on
-  // a 4-byte boundary: whole words, then the odd last value of a single stamp
-  const int nval = ns * 2883;
-  const uint32_t* src = reinterpret_cast<const uint32_t*>(xn + (size_t)s0 * 2883);
-  for (int i = threadIdx.x; i < nval / 2; i += kThreads) stage[i] = __ldg(src + i);
-  if ((nval & 1) && threadIdx.x == 0)
-    reinterpret_cast<bf16*>(stage)[nval - 1] = xn[(size_t)s0 * 2883 + nval - 1];
-  __syncthreads();
-  const bf16* sb = reinterpret_cast<const bf16*>(stage);
   for (int idx = threadIdx.x; idx < Cfg<1>::S * G::HPWO; idx += kThreads) {
     const int s = idx / G::HPWO, rem = idx - s * G::HPWO, r = rem >> 5, c = rem & 31;
     uint32_t k[9];
@@ -183,7 +171,7 @@ __device__ __forceinline__ void build_conv1_planes(const bf16* __restrict__ xn, 
       for (int dxi = 0; dxi < 3; ++dxi) {
         const int col = c - 2 + dxi;
         if (col >= 0 && col < 31) {
-          const bf16* p = sb + (s * 961 + row * 31 + col) * 3;
+          const bf16* p = sb + s * kXnStride + (row * 31 + col) * 3;
 #pragma unroll
           for (int ci = 0; ci < 3; ++ci) k[dxi * 3 + ci] = bf_bits(p[ci]);
         }
@@ -229,9 +217,34 @@ __device__ __forceinline__ void pool_chunk(const float (&v)[32], float (&q)[8], 
   }
 }
 
+// Copies of group g's input into shared memory, counted on `bar` (thread 0):
+// conv1 the normalised stamps, the other layers their channel-block planes.
+template <int LAYER>
+__device__ __forceinline__ void issue_group_copy(const bf16* in, int g, int n, int n_alloc, uint4* planes,
+                                                 uint8_t* stage, uint64_t* bar) {
+  using C = Cfg<LAYER>;
+  using G = Geo<LAYER>;
+  const int s0 = g * C::S, ns = min(C::S, n - s0);
+  if constexpr (LAYER == 1) {
+    const unsigned bytes = (unsigned)(ns * kXnStride * 2);
+    mbar_arrive_expect_tx(bar, bytes);
+    bulk_g2s(stage, in + (size_t)s0 * kXnStride, bytes, bar);
+  } else {
+    const unsigned bytes = (unsigned)(ns * G::HPWO * 16);
+    mbar_arrive_expect_tx(bar, (unsigned)C::CB * bytes);
+    for (int cb = 0; cb < C::CB; ++cb)
+      bulk_g2s(planes + cb * G::STK, in + ((size_t)cb * n_alloc + s0) * G::HPWO * 8, bytes, bar);
+  }
+}
+
 // One convolution layer (see the file comment).  in: conv1 the normalised
-// NHWC stamps, else the layer's input planes ([cb][n_alloc][HP WO] records);
-// out: the next layer's planes (same n_alloc) or NHWC [n][3][3][64].
+// stamps ([n][kXnStride]), else the layer's input planes ([cb][n_alloc][HP WO]
+// records); out: the next layer's planes (same n_alloc) or NHWC [n][3][3][64].
+// The next group's copy is issued as soon as its buffer is free: for conv1
+// right after the planes are built from the staged stamps (it overlaps the
+// MMAs and the epilogue), for the other layers after the last round's MMAs
+// (it overlaps that round's epilogue; the remainder round goes first so that
+// the last round is a full one).
 template <int LAYER>
 __global__ void __launch_bounds__(kThreads, 1)
 k_conv_tc(const bf16* __restrict__ in, int n, int n_alloc, const bf16* __restrict__ img,
@@ -242,6 +255,7 @@ k_conv_tc(const bf16* __restrict__ in, int n, int n_alloc, const bf16* __restric
   uint4* planes = reinterpret_cast<uint4*>(smem);
   uint8_t* bimg = smem + (size_t)C::CB * G::STK * 16;
   float* xs = reinterpret_cast<float*>(bimg + G::IMG);
+  uint8_t* stage = bimg + G::IMG + G::XCH;
   __shared__ uint64_t load_bar, mma_bar, w_bar;
   __shared__ uint32_t tmem_base;
 
@@ -268,40 +282,49 @@ k_conv_tc(const bf16* __restrict__ in, int n, int n_alloc, const bf16* __restric
   const uint32_t tbase = tmem_base;
   const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
 
+  // this thread's epilogue channels (pool_chunk's reduce-scatter): 32 ch +
+  // 16 h + 8 v + i; their biases stay in registers
+  const int h_me = lane & 1;
+  const int v_me = C::WO == 32 ? (warp & 1) : ((lane / (C::WO == 16 ? 16 : 8)) & 1);
+  float breg[C::N / 32][8];
+#pragma unroll
+  for (int ch = 0; ch < C::N / 32; ++ch)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) breg[ch][i] = __ldg(bias + 32 * ch + 16 * h_me + 8 * v_me + i);
+
   if (tid == 0) {
     mbar_arrive_expect_tx(&w_bar, (unsigned)G::IMG);
     bulk_g2s(bimg, img, (unsigned)G::IMG, &w_bar);
+    if (blockIdx.x < ngroups) issue_group_copy<LAYER>(in, blockIdx.x, n, n_alloc, planes, stage, &load_bar);
   }
+  bool load_pending = (int)blockIdx.x < ngroups, mma_pending = false;
   bool ok = __syncthreads_and(wait_bounded(&w_bar, 0));
-  bool w_pending = !ok, load_pending = false, mma_pending = false;
+  const bool w_pending = !ok;
   unsigned lphase = 0, mphase = 0;
   constexpr uint32_t idesc = instr_desc(1, C::N);
   const uint64_t bdesc0 = smem_desc_kn(smem_u32(bimg), 16 * C::N, 128);
   const uint64_t adesc0 = smem_desc_kn(smem_u32(planes), G::STK * 16, 128);
 
   for (int g = blockIdx.x; ok && g < ngroups; g += gridDim.x) {
-    const int s0 = g * C::S, ns = min(C::S, n - s0);
-    // ---- the group's input planes
+    const int s0 = g * C::S, ns = min(C::S, n - s0), gn = g + (int)gridDim.x;
+    // ---- the group's input
+    ok = __syncthreads_and(wait_bounded(&load_bar, lphase));
+    if (!ok) break;
+    load_pending = false;
+    lphase ^= 1u;
     if constexpr (LAYER == 1) {
-      build_conv1_planes(in, s0, ns, planes, reinterpret_cast<uint32_t*>(xs));
+      build_conv1_planes(ns, planes, reinterpret_cast<const bf16*>(stage));
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
-    } else {
-      if (tid == 0) {
-        const unsigned bytes = (unsigned)(ns * G::HPWO * 16);
-        mbar_arrive_expect_tx(&load_bar, (unsigned)C::CB * bytes);
-        for (int cb = 0; cb < C::CB; ++cb)
-          bulk_g2s(planes + cb * G::STK, in + ((size_t)cb * n_alloc + s0) * G::HPWO * 8, bytes, &load_bar);
+      if (gn < ngroups) {   // the stage is free: fetch the next group's stamps
+        if (tid == 0) issue_group_copy<LAYER>(in, gn, n, n_alloc, planes, stage, &load_bar);
+        load_pending = true;
       }
-      load_pending = true;
-      ok = __syncthreads_and(wait_bounded(&load_bar, lphase));
-      if (!ok) break;
-      load_pending = false;
-      lphase ^= 1u;
     }
-    // ---- rounds of TACC tiles: MMAs into tensor memory, then the epilogue
-    for (int t0 = 0; t0 < G::T; t0 += C::TACC) {
-      const int nt = min(C::TACC, G::T - t0);
+    // ---- rounds of up to TACC tiles (the remainder first): MMAs into tensor
+    // memory, then the epilogue
+    for (int t0 = 0; t0 < G::T;) {
+      const int nt = (t0 == 0 && G::T % C::TACC) ? G::T % C::TACC : C::TACC;
       if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         for (int tt = 0; tt < nt; ++tt) {
@@ -325,6 +348,10 @@ k_conv_tc(const bf16* __restrict__ in, int n, int n_alloc, const bf16* __restric
       mma_pending = false;
       mphase ^= 1u;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (LAYER != 1 && t0 + nt == G::T && gn < ngroups) {   // planes no longer read: fetch the next group's
+        if (tid == 0) issue_group_copy<LAYER>(in, gn, n, n_alloc, planes, stage, &load_bar);
+        load_pending = true;
+      }
       for (int tt = 0; tt < nt; ++tt) {
         const int m = (t0 + tt) * 128 + 32 * warp + lane;   // this thread's slot (tensor-memory lane)
         const int R = m / C::WO, s = R / C::HP, yo = (R % C::HP) >> 1, xo = (m % C::WO) >> 1;
@@ -338,7 +365,7 @@ k_conv_tc(const bf16* __restrict__ in, int n, int n_alloc, const bf16* __restric
           const int c0 = 32 * ch + 16 * h + 8 * vb;
           float o[8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) o[i] = fmaxf(q[i] + __ldg(bias + c0 + i), 0.f);
+          for (int i = 0; i < 8; ++i) o[i] = fmaxf(q[i] + breg[ch][i], 0.f);
           const uint4 rec = make_uint4(pack2(o[0], o[1]), pack2(o[2], o[3]), pack2(o[4], o[5]), pack2(o[6], o[7]));
           if (keep) {
             size_t at;   // record index of the output
@@ -352,6 +379,7 @@ k_conv_tc(const bf16* __restrict__ in, int n, int n_alloc, const bf16* __restric
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();
+      t0 += nt;
     }
   }
 
@@ -411,14 +439,22 @@ cudaError_t launch(const bf16* in, int n, int n_alloc, const bf16* img, const fl
   if (n <= 0) return cudaSuccess;
   static int grid_cap = 0;
   if (grid_cap == 0) {
+    // CTAs per SM: as many as the SM's shared memory holds (the carveout set
+    // to its maximum), at most as many as share its 512 tensor-memory columns
     cudaError_t e = cudaFuncSetAttribute(k_conv_tc<LAYER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
-    int dev = 0, sms = 0, occ = 0;
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_conv_tc<LAYER>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
+    int dev = 0, sms = 0, smem_sm = 0, reserved = 0;
+    cudaFuncAttributes fa{};
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv_tc<LAYER>, kThreads, G::SMEM);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_conv_tc<LAYER>);
     if (e != cudaSuccess) return e;
-    // co-resident CTAs share the SM's 512 tensor-memory columns
-    occ = std::max(1, std::min(occ, 512 / C::TCOLS));
+    const int per_cta = (int)G::SMEM + (int)fa.sharedSizeBytes + reserved;
+    const int occ = std::max(1, std::min(smem_sm / per_cta, 512 / C::TCOLS));
     grid_cap = occ * sms;
   }
   const int ngroups = (n + C::S - 1) / C::S;

@@ -50,8 +50,8 @@ struct ConvRows {   // c % 8 == 0
 };
 
 struct Conv1Rows {   // c = 3, k = (ky * 3 + kx) * 3 + ci < 27, padded to 32
-  const bf16* x;
-  int n, h, w;
+  const bf16* x;       // NHWC stamps, sstride values apart
+  int n, h, w, sstride;
   __device__ __forceinline__ uint4 row8(int pix, int k) const {
     __align__(16) bf16 v[8];
     const bool okp = pix < n * h * w;
@@ -63,7 +63,7 @@ struct Conv1Rows {   // c = 3, k = (ky * 3 + kx) * 3 + ci < 27, padded to 32
       if (okp && kk < 27) {
         const int tap = kk / 3, ci = kk - tap * 3;
         const int sy = yy + tap / 3 - 1, sx = xx + tap % 3 - 1;
-        if (sy >= 0 && sy < h && sx >= 0 && sx < w) e = x[(((int64_t)nn * h + sy) * w + sx) * 3 + ci];
+        if (sy >= 0 && sy < h && sx >= 0 && sx < w) e = x[(int64_t)nn * sstride + (sy * w + sx) * 3 + ci];
       }
       v[j] = e;
     }

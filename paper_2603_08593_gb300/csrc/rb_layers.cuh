@@ -72,68 +72,118 @@ struct ConvW {
 };
 
 // ---------------------------------------------------------------- elementwise kernels
-// Robust normalisation of one channel of one stamp per warp: the 961 values
-// (padded with +inf to 1024) are sorted in registers by a bitonic network
-// (position p = lane * 32 + r; partner positions in other lanes are reached by
-// shuffles), the median is position 480; the absolute deviations are sorted
-// the same way for the MAD.  x -> clip((x - median) / (1.4826 MAD), +-64),
-// scale 1 when the MAD is 0.  Output NHWC BF16 [n][31][31][3].
-__device__ __forceinline__ void warp_bitonic_1024(float (&v)[32], int lane) {
+// Robust normalisation: x -> clip((x - median) / (1.4826 MAD), +-64) per
+// stamp and channel (scale 1 when the MAD is 0), output NHWC BF16 with
+// `stride` values per stamp (961 x 3 = 2883, or 2888 so that every stamp
+// starts on a 16-byte boundary; the pad is zero).  One block of three warps
+// per stamp, one warp per channel.  The median and the MAD are exact order
+// statistics (the 481st smallest of 961 values) found without a full sort:
+// each lane sorts its 31 values (padded with +inf to 32) in registers, and a
+// bisection over the order-preserving integer image of the FP32 values
+// counts, per probe, the values <= the probe in every lane's sorted column
+// (a 5-step search in shared memory) until the smallest value with at least
+// 481 values <= it is found.  The absolute deviations of a sorted column
+// fall and then rise, so one bitonic merge sorts them for the second search.
+__device__ __forceinline__ void sort32(float (&v)[32]) {
 #pragma unroll
-  for (int k = 2; k <= 1024; k <<= 1) {
+  for (int k = 2; k <= 32; k <<= 1)
 #pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      if (j >= 32) {
-        const int lj = j >> 5;
-        const bool lower = (lane & lj) == 0;
+    for (int j = k >> 1; j > 0; j >>= 1)
 #pragma unroll
-        for (int r = 0; r < 32; ++r) {
-          const bool up = (((lane * 32 + r) & k) == 0);
-          const float o = __shfl_xor_sync(0xffffffffu, v[r], lj);
-          v[r] = (lower == up) ? fminf(v[r], o) : fmaxf(v[r], o);
-        }
-      } else {
-#pragma unroll
-        for (int r = 0; r < 32; ++r) {
-          const int rp = r ^ j;
-          if (rp > r) {
-            const bool up = (((lane * 32 + r) & k) == 0);
-            const float x = v[r], y = v[rp];
-            v[r] = up ? fminf(x, y) : fmaxf(x, y);
-            v[rp] = up ? fmaxf(x, y) : fminf(x, y);
-          }
+      for (int i = 0; i < 32; ++i) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool up = (i & k) == 0;
+          const float a = v[i], b = v[l];
+          v[i] = up ? fminf(a, b) : fmaxf(a, b);
+          v[l] = up ? fmaxf(a, b) : fminf(a, b);
         }
       }
-    }
-  }
 }
 
-__global__ void __launch_bounds__(256)
-k_normalise(const float* __restrict__ stamps, int n, bf16* __restrict__ xn) {
+// ascending sort of a sequence that first falls and then rises (bitonic)
+__device__ __forceinline__ void merge32(float (&v)[32]) {
+#pragma unroll
+  for (int j = 16; j > 0; j >>= 1)
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const int l = i ^ j;
+      if (l > i) {
+        const float a = v[i], b = v[l];
+        v[i] = fminf(a, b);
+        v[l] = fmaxf(a, b);
+      }
+    }
+}
+
+__device__ __forceinline__ uint32_t order_key(float x) {
+  const uint32_t b = __float_as_uint(x);
+  return b ^ ((b >> 31) ? 0xffffffffu : 0x80000000u);
+}
+__device__ __forceinline__ float key_value(uint32_t k) {
+  return __uint_as_float(k ^ ((k >> 31) ? 0x80000000u : 0xffffffffu));
+}
+
+// The (rank + 1)-th smallest of the warp's finite values: v is the lane's
+// sorted column (finite entries first, nfin of them, then +inf), col the
+// lane's column in shared memory ([32][32], entry r of lane l at r * 32 + l).
+__device__ __forceinline__ float warp_select(const float (&v)[32], int nfin, float* col, int rank) {
   const int lane = threadIdx.x & 31;
-  const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);   // (stamp, channel)
-  if (item >= 3 * n) return;                                              // whole warps
-  const int st = item / 3, ch = item - 3 * st;
+#pragma unroll
+  for (int r = 0; r < 32; ++r) col[r * 32 + lane] = v[r];
+  __syncwarp();
+  float vmax = v[0];
+#pragma unroll
+  for (int r = 1; r < 32; ++r) vmax = r < nfin ? v[r] : vmax;
+  uint32_t lo = __reduce_min_sync(0xffffffffu, order_key(v[0]));
+  uint32_t hi = __reduce_max_sync(0xffffffffu, order_key(vmax));
+  while (lo < hi) {   // smallest key with more than `rank` values <= it
+    const uint32_t mid = lo + ((hi - lo) >> 1);
+    const float p = key_value(mid);
+    int pos = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) pos += col[(pos + step - 1) * 32 + lane] <= p ? step : 0;
+    const int c = (int)__reduce_add_sync(0xffffffffu, (unsigned)pos);
+    if (c > rank) hi = mid;
+    else lo = mid + 1;
+  }
+  __syncwarp();
+  return key_value(hi);
+}
+
+__global__ void __launch_bounds__(96)
+k_normalise(const float* __restrict__ stamps, int n, bf16* __restrict__ xn, int stride) {
+  __shared__ float cols[3][32 * 32];
+  __shared__ __align__(16) bf16 stage[2888];
+  const int st = blockIdx.x, ch = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (st >= n) return;
   const float* src = stamps + ((int64_t)st * 3 + ch) * PIX1;
   float v[32];
 #pragma unroll
   for (int r = 0; r < 32; ++r) {
     const int i = r * 32 + lane;
-    v[r] = i < PIX1 ? src[i] : INFINITY;
+    v[r] = (r < 31 && i < PIX1) ? src[i] : INFINITY;
   }
-  warp_bitonic_1024(v, lane);
-  const float med = __shfl_sync(0xffffffffu, v[0], 15);   // position 480
+  const int nfin = lane == 0 ? 31 : 30;   // 961 = 30 x 32 + 1
+  sort32(v);
+  const float med = warp_select(v, nfin, cols[ch], 480);
 #pragma unroll
-  for (int r = 0; r < 32; ++r) {
-    const int i = r * 32 + lane;
-    v[r] = i < PIX1 ? fabsf(src[i] - med) : INFINITY;
-  }
-  warp_bitonic_1024(v, lane);
-  const float sc = 1.4826f * __shfl_sync(0xffffffffu, v[0], 15);
+  for (int r = 0; r < 32; ++r) v[r] = fabsf(v[r] - med);   // +inf stays +inf, at the end
+  merge32(v);
+  const float sc = 1.4826f * warp_select(v, nfin, cols[ch], 480);
   const float inv = 1.f / (sc > 0.f ? sc : 1.f);
   for (int i = lane; i < PIX1; i += 32) {
     const float x = fminf(fmaxf((src[i] - med) * inv, -64.f), 64.f);
-    xn[((int64_t)st * PIX1 + i) * 3 + ch] = __float2bfloat16(x);
+    stage[i * 3 + ch] = __float2bfloat16(x);
+  }
+  if (threadIdx.x < stride - 3 * PIX1) stage[3 * PIX1 + threadIdx.x] = __float2bfloat16(0.f);
+  __syncthreads();
+  bf16* dst = xn + (int64_t)st * stride;
+  if (stride % 8 == 0) {
+    for (int i = threadIdx.x; i < stride / 8; i += blockDim.x)
+      reinterpret_cast<uint4*>(dst)[i] = reinterpret_cast<const uint4*>(stage)[i];
+  } else {
+    for (int i = threadIdx.x; i < stride; i += blockDim.x) dst[i] = stage[i];
   }
 }
 

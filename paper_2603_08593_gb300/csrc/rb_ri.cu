@@ -196,7 +196,7 @@ cudaError_t forward(rbri_model_s* m, int n, cudaStream_t s, bool keep_idx) {
   cudaError_t e;
   k_rotate<<<grid1((int64_t)n4 * PIX1 * 3), 256, 0, s>>>(m->xn, n, m->xr);
   // conv1 + ReLU + pool
-  if ((e = igemm<Conv1Rows, Dense, false>(s, n4 * PIX1, C1, K1, Conv1Rows{m->xr, n4, S31, S31},
+  if ((e = igemm<Conv1Rows, Dense, false>(s, n4 * PIX1, C1, K1, Conv1Rows{m->xr, n4, S31, S31, 3 * PIX1},
                                           Dense{W + QW1, K1, C1, C1}, m->z1, C1, P + QB1)))
     return e;
   k_relu_pool<<<grid1((int64_t)n4 * PIX2 * C1), 256, 0, s>>>(m->z1, n4, S31, S31, C1, m->a1, keep_idx ? m->i1 : nullptr);
@@ -292,7 +292,8 @@ cudaError_t backward(rbri_model_s* m, int n, const float* labels, float* loss_de
   k_add_grad<<<grid1(m1), 256, 0, s>>>(m->da, m->dzA, m1);   // the skip path
   // conv1 (no input gradient)
   k_pool_relu_back<<<grid1((int64_t)n4 * PIX1 * C1), 256, 0, s>>>(m->da, m->i1, m->z1, n4, S31, S31, C1, m->dzA);
-  if ((e = igemm_wgrad(s, C1, K1, n4 * PIX1, Dense{m->dzA, n4 * PIX1, C1, C1}, Conv1Rows{m->xr, n4, S31, S31},
+  if ((e = igemm_wgrad(s, C1, K1, n4 * PIX1, Dense{m->dzA, n4 * PIX1, C1, C1},
+                       Conv1Rows{m->xr, n4, S31, S31, 3 * PIX1},
                        G + QW1, m->part)))
     return e;
   if ((e = colsum(s, m->dzA, (int64_t)n4 * PIX1, C1, m->part, G + QB1))) return e;
@@ -433,7 +434,7 @@ extern "C" sfft_status_t rbri_logits(rbri_model_t m, const float* stamps, int64_
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (int64_t i0 = 0; i0 < n; i0 += m->max_batch) {
     const int nb = (int)std::min<int64_t>(m->max_batch, n - i0);
-    k_normalise<<<(3 * nb + 7) / 8, 256, 0, s>>>(stamps + i0 * 3 * PIX1, nb, m->xn);
+    k_normalise<<<nb, 96, 0, s>>>(stamps + i0 * 3 * PIX1, nb, m->xn, 3 * PIX1);
     cudaError_t e = forward(m, nb, s, false);
     if (e == cudaSuccess) e = cudaMemcpyAsync(logit + i0, m->logit, sizeof(float) * nb, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return fail(e, "rbri_logits");
@@ -454,7 +455,7 @@ extern "C" sfft_status_t rbri_backward(rbri_model_t m, const float* stamps, cons
   if (!m || !stamps || !labels || n < 1 || n > m->max_batch) return SFFT_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int nb = (int)n;
-  k_normalise<<<(3 * nb + 7) / 8, 256, 0, s>>>(stamps, nb, m->xn);
+  k_normalise<<<nb, 96, 0, s>>>(stamps, nb, m->xn, 3 * PIX1);
   cudaError_t e = forward(m, nb, s, true);
   if (e == cudaSuccess) e = backward(m, nb, labels, loss_dev, s);
   return e == cudaSuccess ? SFFT_OK : fail(e, "rbri_backward");

@@ -14,6 +14,9 @@ struct Planes {
   int CB, HP, WO;
   size_t per_stamp_elems() const { return (size_t)HP * WO * 8; }
 };
+// normalised stamps: NHWC 31 x 31 x 3 BF16, then 5 zero values, so that a
+// stamp is 5776 bytes and starts on a 16-byte boundary
+constexpr int kXnStride = 2888;
 constexpr Planes kP2{4, 18, 16};   // conv2 input: 15 x 15 x 32
 constexpr Planes kP3{8, 10, 8};    // conv3 input: 7 x 7 x 64
 
@@ -29,7 +32,7 @@ constexpr int kWImg1 = 3 * 1 * 16 * 32, kWImg2 = 9 * 2 * 16 * 64, kWImg3 = 9 * 4
 cudaError_t build_weight_images(const float* w1, const float* w2, const float* w3, __nv_bfloat16* img1,
                                 __nv_bfloat16* img2, __nv_bfloat16* img3, cudaStream_t s);
 
-// conv1 + bias + ReLU + pool: xn NHWC [n][31][31][3] -> conv2 planes p2
+// conv1 + bias + ReLU + pool: xn [n][kXnStride] -> conv2 planes p2
 // (n_alloc stamps per channel block); conv2 ... -> conv3 planes p3; conv3 ...
 // -> a3 NHWC [n][3][3][64].  err: device word that a wait that gives up sets.
 cudaError_t conv1_tc(const __nv_bfloat16* xn, int n, const __nv_bfloat16* img1, const float* b1, __nv_bfloat16* p2,

@@ -243,7 +243,9 @@ def test_fused_conv_layers_elementwise(n, n_alloc):
     x = C.round_bf16(rng.normal(0, 1.5, (n, 31, 31, 3)))
     # conv1: NHWC stamps -> conv2 planes
     out = _dev(_to_planes(np.zeros((n, 15, 15, 32)), 2, n_alloc, fill_tail=7.0), torch.bfloat16)
-    m.conv_layer(1, _dev(x, torch.bfloat16), n, n_alloc, out)
+    xin = np.zeros((n, 2888))
+    xin[:, :2883] = x.reshape(n, -1)
+    m.conv_layer(1, _dev(xin, torch.bfloat16), n, n_alloc, out)
     got = out.float().cpu().numpy().astype(np.float64).reshape(4, n_alloc, 18, 16, 8)
     exact, scale = _layer_oracle(x, p["w1"], p["b1"])
     border = np.ones((18, 16), bool)
@@ -277,7 +279,7 @@ def test_fused_conv_layers_elementwise(n, n_alloc):
 
 def test_fused_conv_layer_arguments():
     m = _model(_params(1), 4)
-    x = torch.zeros(4 * 961 * 3, dtype=torch.bfloat16, device=DEV)
+    x = torch.zeros(4 * 2888, dtype=torch.bfloat16, device=DEV)
     y = torch.zeros(4 * 4 * 288 * 8, dtype=torch.bfloat16, device=DEV)
     from paper_2603_08593_gb300.binding import SfftError
     for layer, n, na in ((0, 1, 1), (4, 1, 1), (1, 5, 4), (1, 1, 0), (1, -1, 4)):
