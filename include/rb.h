@@ -64,22 +64,35 @@ sfft_status_t rb_score(rb_model_t m, const float* stamps, int64_t n, float* scor
  * tensor cores with FP32 accumulation.
  *   layer 1: in  = normalised stamps, BF16 [n][2888]: NHWC 31 x 31 x 3
  *            values, then 5 unused ones (a stamp is 5776 bytes);
- *            out = the conv2 input planes, (CB, HP, WO) = (4, 18, 16)
- *   layer 2: in  = those planes;  out = the conv3 input planes, (8, 10, 8)
+ *            out = the conv2 input planes, (CB, WS) = (4, 8)
+ *   layer 2: in  = those planes;  out = the conv3 input planes, (8, 4)
  *   layer 3: in  = those planes;  out = BF16 NHWC [n][3][3][64]
- * Planes are BF16 [CB][n_alloc][HP][WO][8]: for channel block cb and stamp i,
- * record (r, c) holds channels 8 cb .. 8 cb + 7 of pixel (r - 1, c - 1) and
- * every other record must be zero; the layer reads whole planes of stamps < n
- * and writes only the interiors of stamps < n.  Device pointers, 16-byte
- * aligned; 0 <= n <= n_alloc <= 2^24 (n = 0 does nothing).  SFFT_ERR_ARG for
- * a bad layer, sizes, alignment or null pointers.  Asynchronous on `stream`;
- * a bounded wait that gave up sets the flag that rb_get_error reads. */
+ * Planes are BF16 [CB][4][n_alloc][WS][WS][8]: the image is padded with a
+ * zero border (padded pixel (r, c) = pixel (r - 1, c - 1)) and split by the
+ * parities of r and c; record (r >> 1, c >> 1) of parity plane
+ * 2 (r & 1) + (c & 1) holds channels 8 cb .. 8 cb + 7 of padded pixel (r, c),
+ * and every record that holds no pixel must be zero.  The layer reads whole
+ * planes of stamps < n and writes only the pixel records of stamps < n.
+ * Device pointers, 16-byte aligned; 0 <= n <= n_alloc <= 2^24 (n = 0 does
+ * nothing).  SFFT_ERR_ARG for a bad layer, sizes, alignment or null pointers.
+ * Asynchronous on `stream`; a bounded wait that gave up sets the flag that
+ * rb_get_error reads. */
 sfft_status_t rb_conv_layer(rb_model_t m, int32_t layer, const void* in, int64_t n, int64_t n_alloc, void* out,
                             void* stream);
 /* Error flags of the model's tensor-core kernels (synchronous): 0 none, bit 0
  * a bounded wait gave up.  Sticky for the model's lifetime; while set,
  * rb_logits and rb_score return NaN logits and scores. */
 sfft_status_t rb_get_error(rb_model_t m, int32_t* flags);
+
+/* Time attribution of the fused inference convolutions (a diagnostic): in a
+ * build compiled with -DRBTC_WAIT_PROFILE, out[0 .. 9] receive the summed
+ * cycles of layer `layer` (1-3) since the last reset: the CTAs' runs, the
+ * copy warp's waits for a free buffer, conv1's plane builders waiting for
+ * staged stamps / a free buffer / working, the MMA warp waiting for a full
+ * buffer / a free accumulator slot / issuing, the epilogue warps waiting for
+ * accumulators / working (lane 0 of each warp adds its own time).  reset != 0
+ * zeroes the counters.  Synchronous.  SFFT_ERR_UNSUPPORTED in other builds. */
+sfft_status_t rb_debug_conv_waits(int32_t layer, uint64_t* out, int32_t reset);
 
 /* Mean BCE loss (written to loss_dev, float) and parameter gradients of one
  * batch of n <= max stamps with labels (float 0/1); no parameter update. */

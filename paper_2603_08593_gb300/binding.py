@@ -67,6 +67,7 @@ SIGNATURES = {
     "rb_score": (I32, [VP, VP, I64, VP, VP]),
     "rb_conv_layer": (I32, [VP, I32, VP, I64, I64, VP, VP]),
     "rb_get_error": (I32, [VP, C.POINTER(I32)]),
+    "rb_debug_conv_waits": (I32, [I32, C.POINTER(C.c_uint64), I32]),
     "rb_backward": (I32, [VP, VP, VP, I64, VP, VP]),
     "rb_train_step": (I32, [VP, VP, VP, I64, C.c_float, VP, VP]),
     "rbri_create": (I32, [VP, C.POINTER(VP)]),

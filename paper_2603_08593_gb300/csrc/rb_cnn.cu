@@ -267,8 +267,8 @@ extern "C" sfft_status_t rb_create(const int32_t* desc, rb_model_t* out) {
             alloc(&m->i1, (size_t)B * PIX2 * C1) && alloc(&m->i2, (size_t)B * PIX3 * C2) &&
             alloc(&m->i3, (size_t)B * PIX4 * C3) && alloc(&m->part, (size_t)kMaxSplits * K4 * F4) &&
             alloc(&m->img1, rbtc::kWImg1) && alloc(&m->img2, rbtc::kWImg2) && alloc(&m->img3, rbtc::kWImg3) &&
-            alloc(&m->p2, (size_t)B * rbtc::kP2.CB * rbtc::kP2.per_stamp_elems()) &&
-            alloc(&m->p3, (size_t)B * rbtc::kP3.CB * rbtc::kP3.per_stamp_elems()) && alloc(&m->err, 1);
+            alloc(&m->p2, (size_t)B * rbtc::kP2.per_stamp_elems()) &&
+            alloc(&m->p3, (size_t)B * rbtc::kP3.per_stamp_elems()) && alloc(&m->err, 1);
   if (!ok) {
     free_model(m);
     delete m;
@@ -292,8 +292,8 @@ extern "C" sfft_status_t rb_create(const int32_t* desc, rb_model_t* out) {
   if (e == cudaSuccess) e = cudaMemset(m->adam_v, 0, sizeof(float) * NMASTER);
   if (e == cudaSuccess) e = cudaMemset(m->grads, 0, sizeof(float) * NMASTER);
   // the planes' borders stay zero: the convolutions write interiors only
-  if (e == cudaSuccess) e = cudaMemset(m->p2, 0, sizeof(bf16) * (size_t)B * rbtc::kP2.CB * rbtc::kP2.per_stamp_elems());
-  if (e == cudaSuccess) e = cudaMemset(m->p3, 0, sizeof(bf16) * (size_t)B * rbtc::kP3.CB * rbtc::kP3.per_stamp_elems());
+  if (e == cudaSuccess) e = cudaMemset(m->p2, 0, sizeof(bf16) * (size_t)B * rbtc::kP2.per_stamp_elems());
+  if (e == cudaSuccess) e = cudaMemset(m->p3, 0, sizeof(bf16) * (size_t)B * rbtc::kP3.per_stamp_elems());
   if (e == cudaSuccess) e = cudaMemset(m->err, 0, sizeof(int));
   if (e == cudaSuccess) {
     refresh_bf16(m, nullptr);

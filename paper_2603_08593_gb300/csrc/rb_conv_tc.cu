@@ -3,39 +3,52 @@
 // max-pool, in one kernel that reads BF16 activations and writes the next
 // layer's BF16 activations (no FP32 pre-activation image reaches memory).
 //
-// Layout.  A layer's input is held, per stamp, as channel-block planes: for
-// each block of 8 channels a plane of HP rows x WO columns of 16-byte records
-// (8 BF16 channels), where plane row r and column c hold the input pixel
-// (r - 1, c - 1) and every other record (the border) is zero.  WO is a power
-// of two at least W + 1, and HP = H + 2 rounded up to an even number.  The
-// convolution's output slots are the same HP x WO grid: slot m = y WO + x is
-// output pixel (y, x), and for the tap (dy, dx) it reads the record at slot
-// m + (dy + 1) WO + dx + 1 of the plane, i.e. the input pixel (y + dy, x + dx)
-// or the zero border; slots with y >= H or x >= W compute values nobody reads.
-// So the A operand of one MMA (M = 128 consecutive slots x K = 16 channels of
-// one tap) is a plain strided view of the planes: core matrices of 8 slots x
-// 8 channels are 128 contiguous bytes (stride byte offset 128) and the second
-// 8 channels are the next channel block's plane (leading byte offset = the
-// distance between planes).  No im2col matrix is built anywhere.  The B
-// operand (the tap's weights, N = C_out rows x K = 16) is a K-major image in
-// shared memory, copied once per launch from an image built when the
-// weights change.  conv1 has 3 input channels only: its records hold, for the
-// input pixel row of the plane row, the 3 channels of three horizontally
-// adjacent pixels (9 of 16 K entries, the rest zero), so one MMA covers a
-// whole kernel row and a tile takes 3 MMAs instead of 9.
+// Layout.  A layer's input is held as parity-split channel-block planes.  Pad
+// the H x H image with a zero border (padded pixel (r, c) = input pixel
+// (r - 1, c - 1)) and split the padded pixels by the parities of r and c into
+// four sub-planes of WS x WS records (16-byte records of 8 BF16 channels):
+// record (r >> 1, c >> 1) of sub-plane 2 (r & 1) + (c & 1).  Every record
+// that is no input pixel is zero.  The MMA rows are pool windows, not
+// pixels: window (wy, wx) covers the outputs (2 wy + a, 2 wx + b), a, b in
+// {0, 1}, and for window position (a, b) and tap (dy, dx) it reads padded
+// pixel (2 wy + a + dy + 1, 2 wx + b + dx + 1), that is record
+// (wy + i, wx + j) of sub-plane (p, q) with a + dy + 1 = 2 i + p and
+// b + dx + 1 = 2 j + q.  For fixed (a, b, dy, dx) consecutive windows read
+// consecutive records, so the A operand of one MMA (M = 128 windows x K = 16
+// channels) is a plain strided view of shared memory: core matrices of 8
+// windows x 8 channels are 128 contiguous bytes (stride byte offset 128),
+// the other 8 channels sit in the next channel block (leading byte offset).
+// Each window position accumulates into its own N columns of tensor memory,
+// so one thread (tensor-memory lane = window) holds all four outputs of its
+// window: the 2 x 2 max-pool, bias and ReLU are register arithmetic.  No
+// im2col matrix is built anywhere.  The B operand (a tap's weights, N = C_out
+// x K = 16) is a K-major image in shared memory, copied once per launch from
+// an image built when the weights change.
 //
-// A CTA takes S stamps at a time (S HP WO is a multiple of 128): it copies
-// their planes to shared memory (conv1 builds them from the normalised NHWC
-// stamp), issues per 128-slot tile 9 taps x (channel blocks / 2) MMAs into
-// tensor memory, TACC tiles per round, and its four warps read the
-// accumulators back (tcgen05.ld, one slot per thread), take the 2 x 2 maximum
-// with the neighbouring slots (lane shuffles, or through shared memory when a
-// warp holds one image row), add the bias, apply the ReLU and store the
-// pooled BF16 values: into the next layer's planes, or (after the last
-// convolution) into the NHWC [n][3][3][64] activations of the dense layers.
-// Pool windows never straddle a tile: a tile is 128 / WO whole image rows and
-// HP is even.  Every wait is bounded; a wait that gives up sets the model's
-// error word and the CTA leaves after draining its MMAs.
+// conv1 has 3 input channels.  Its record for padded row r and window column
+// wx holds the 3 channels of the four input pixels (r - 1, 2 wx - 1 .. 2 wx + 2)
+// that the window's two output columns and three kernel columns touch (12 of
+// 16 K entries), so the records are split by row parity only, and the A
+// operand for padded-row offset ro = a + dy + 1 (0 .. 3) is shared by every
+// window position and kernel row that reads it: one MMA per offset with
+// N = 4 positions x 32 channels, whose weight image holds, for position
+// (a, b), the weights of kernel row ro - a and columns e - b for pixel e (zero
+// where that tap does not exist).  4 MMAs of N = 128 per tile instead of 36
+// of N = 32: the MMAs run at the tensor cores' arithmetic rate instead of the
+// shared-memory operand rate.  conv1 expands these records in shared memory
+// from the normalised NHWC stamps.
+//
+// Windows of stamp s occupy rows s WS^2 + wy WS + wx of a group of S stamps
+// (the sub-planes of the group's stamps are contiguous); windows with wy or
+// wx beyond the pooled size compute values nobody reads.  The kernel is
+// persistent and warp-specialised: warps 0-3 read the accumulators back
+// (tcgen05.ld) and write the pooled outputs, warp 4 issues the MMAs (one
+// elected lane), warp 5 copies the inputs (bulk copies), and for conv1 warps
+// 6-9 expand the staged stamps into planes.  Input buffers and accumulator
+// slots are double-buffered and handed over by mbarriers, so copies, plane
+// expansion, MMAs and epilogues of consecutive groups overlap.  Every wait is
+// bounded; a wait that gives up raises the CTA's abort flag and the model's
+// error word, and every role leaves after draining what it issued.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -43,28 +56,22 @@
 
 #include "bulk.cuh"
 #include "common.cuh"
+#include "rb.h"
 #include "rb_tc.h"
 #include "umma_common.cuh"
 
 namespace rbtc {
 
 using bf16 = __nv_bfloat16;
-using sfft::elect_one;
 using sfft::instr_desc;
 using sfft::kMaxSpin;
+using sfft::mbar_arrive;
 using sfft::mbar_arrive_expect_tx;
 using sfft::mbar_init;
 using sfft::mbar_try_wait;
 using sfft::smem_desc_kn;
 using sfft::smem_u32;
-
-constexpr int kThreads = 128;
-
-__device__ __forceinline__ bool wait_bounded(uint64_t* bar, unsigned parity) {
-  for (int it = 0; it < kMaxSpin; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
+using sfft::wait_phase;
 
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
@@ -78,67 +85,48 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
   return r;
 }
 
-// 32 consecutive FP32 accumulator columns of this thread's tensor-memory lane
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-               "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
-               "[%32];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                 "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                 "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                 "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-               : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+// Four groups of 32 FP32 accumulator columns of this thread's tensor-memory
+// lane, starting at taddr + q * stride (q = 0 .. 3), with one wait for all
+__device__ __forceinline__ void tmem_ld4x32(uint32_t taddr, uint32_t stride, float (&v)[128]) {
+  uint32_t r[128];
+  asm volatile(
+      "{\n"
+      ".reg .b32 a1, a2, a3;\n"
+      "add.u32 a1, %128, %129;\n"
+      "add.u32 a2, a1, %129;\n"
+      "add.u32 a3, a2, %129;\n"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%128];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, "
+      "%46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [a1];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%64, %65, %66, %67, %68, %69, %70, %71, %72, %73, %74, %75, %76, %77, "
+      "%78, %79, %80, %81, %82, %83, %84, %85, %86, %87, %88, %89, %90, %91, %92, %93, %94, %95}, [a2];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%96, %97, %98, %99, %100, %101, %102, %103, %104, %105, %106, %107, "
+      "%108, %109, %110, %111, %112, %113, %114, %115, %116, %117, %118, %119, %120, %121, %122, %123, %124, %125, "
+      "%126, %127}, [a3];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      "}\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]),
+        "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]),
+        "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]),
+        "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]),
+        "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63]), "=r"(r[64]),
+        "=r"(r[65]), "=r"(r[66]), "=r"(r[67]), "=r"(r[68]), "=r"(r[69]), "=r"(r[70]), "=r"(r[71]), "=r"(r[72]),
+        "=r"(r[73]), "=r"(r[74]), "=r"(r[75]), "=r"(r[76]), "=r"(r[77]), "=r"(r[78]), "=r"(r[79]), "=r"(r[80]),
+        "=r"(r[81]), "=r"(r[82]), "=r"(r[83]), "=r"(r[84]), "=r"(r[85]), "=r"(r[86]), "=r"(r[87]), "=r"(r[88]),
+        "=r"(r[89]), "=r"(r[90]), "=r"(r[91]), "=r"(r[92]), "=r"(r[93]), "=r"(r[94]), "=r"(r[95]), "=r"(r[96]),
+        "=r"(r[97]), "=r"(r[98]), "=r"(r[99]), "=r"(r[100]), "=r"(r[101]), "=r"(r[102]), "=r"(r[103]),
+        "=r"(r[104]), "=r"(r[105]), "=r"(r[106]), "=r"(r[107]), "=r"(r[108]), "=r"(r[109]), "=r"(r[110]),
+        "=r"(r[111]), "=r"(r[112]), "=r"(r[113]), "=r"(r[114]), "=r"(r[115]), "=r"(r[116]), "=r"(r[117]),
+        "=r"(r[118]), "=r"(r[119]), "=r"(r[120]), "=r"(r[121]), "=r"(r[122]), "=r"(r[123]), "=r"(r[124]),
+        "=r"(r[125]), "=r"(r[126]), "=r"(r[127])
+      : "r"(taddr), "r"(stride));
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 128; ++i) v[i] = __uint_as_float(r[i]);
 }
-
-
-// Per-layer geometry.  Input planes: CB channel blocks, HP x WO records per
-// stamp, an H x H image; S stamps per group (S HP WO a multiple of 128);
-// N output channels; NTAP MMA taps per tile of K = 16 per channel-block pair;
-// TACC tiles accumulated per round in TCOLS tensor-memory columns.  Output:
-// the next layer's planes (CBO x HPO x WOO) or, after conv3, NHWC rows.
-template <int LAYER>
-struct Cfg;
-template <>
-struct Cfg<1> {
-  static constexpr int CB = 2, HP = 34, WO = 32, H = 31, S = 2, N = 32, NTAP = 3, TACC = 8, TCOLS = 256;
-  static constexpr int HPO = 18, WOO = 16;
-  static constexpr bool NHWC = false;
-};
-template <>
-struct Cfg<2> {
-  static constexpr int CB = 4, HP = 18, WO = 16, H = 15, S = 4, N = 64, NTAP = 9, TACC = 4, TCOLS = 256;
-  static constexpr int HPO = 10, WOO = 8;
-  static constexpr bool NHWC = false;
-};
-template <>
-struct Cfg<3> {
-  static constexpr int CB = 8, HP = 10, WO = 8, H = 7, S = 8, N = 64, NTAP = 9, TACC = 5, TCOLS = 512;
-  static constexpr int HPO = 0, WOO = 0;
-  static constexpr bool NHWC = true;
-};
-
-template <int LAYER>
-struct Geo {
-  using C = Cfg<LAYER>;
-  static constexpr int HPWO = C::HP * C::WO;
-  static constexpr int T = C::S * HPWO / 128;              // tiles per group
-  static constexpr int KS = C::CB / 2;                     // K = 16 slices per tap
-  static constexpr int PAD = 2 * C::WO + 8;                // records past the last slot a tap may read
-  static constexpr int STK = C::S * HPWO + PAD;            // records per channel-block stack
-  static constexpr int IMG = C::NTAP * KS * 32 * C::N;     // weight-image bytes
-  static constexpr int STAGE = LAYER == 1 ? C::S * kXnStride * 2 : 0;   // conv1: normalised stamps (bytes)
-  static constexpr int XCH = C::WO == 32 ? 16 * 128 * 4 : 0;        // cross-warp pool exchange (bytes)
-  static constexpr size_t SMEM = (size_t)C::CB * STK * 16 + IMG + XCH + STAGE;
-  static_assert((C::S * HPWO) % 128 == 0, "whole tiles per group");
-  static_assert(C::HP % 2 == 0 && 128 % C::WO == 0 && (128 / C::WO) % 2 == 0, "pool windows inside a tile");
-  static_assert(C::TACC * C::N <= C::TCOLS && STK < 16384, "tensor memory and descriptor ranges");
-  static_assert((C::CB * STK * 16) % 128 == 0 && IMG % 128 == 0, "shared-memory alignment");
-};
 
 __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -153,74 +141,122 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 
 __device__ __forceinline__ uint32_t bf_bits(bf16 v) { return (uint32_t)__bfloat16_as_ushort(v); }
 
-// conv1 planes of the group's stamps s0 .. s0 + ns - 1 from the normalised
-// stamps staged in shared memory (kXnStride values each); record (r, c) of
-// block 0 holds channels 0-2 of input pixels (r - 1, c - 2), (r - 1, c - 1)
-// and channels 0-1 of (r - 1, c); block 1 holds channel 2 of (r - 1, c);
-// zero outside the image and for stamps past ns.
-__device__ __forceinline__ void build_conv1_planes(int ns, uint4* planes, const bf16* sb) {
+// Per-layer geometry.  CB input channel blocks, NPAR parity sub-planes (conv1:
+// row parity only) of WS x WS records (= window grid), PH pooled outputs per
+// side (valid windows), S stamps per group, N output channels, NTAP taps per
+// window position (conv1: the 4 row offsets, each one MMA over all positions);
+// WSO the sub-plane width of the output planes.
+template <int LAYER>
+struct Cfg;
+template <>
+struct Cfg<1> {
+  static constexpr int CB = 2, NPAR = 2, WS = 16, PH = 15, S = 2, N = 32, NTAP = 4, WSO = 8;
+  static constexpr bool NHWC = false;
+};
+template <>
+struct Cfg<2> {
+  static constexpr int CB = 4, NPAR = 4, WS = 8, PH = 7, S = 4, N = 64, NTAP = 9, WSO = 4;
+  static constexpr bool NHWC = false;
+};
+template <>
+struct Cfg<3> {
+  static constexpr int CB = 8, NPAR = 4, WS = 4, PH = 3, S = 8, N = 64, NTAP = 9, WSO = 0;
+  static constexpr bool NHWC = true;
+};
+
+template <int LAYER>
+struct Geo {
+  using C = Cfg<LAYER>;
+  static constexpr int SP = C::WS * C::WS;                  // records per sub-plane and stamp
+  static constexpr int GW = C::S * SP;                      // windows (MMA rows) per group
+  static constexpr int T = GW / 128;                        // tiles per group
+  static constexpr int KS = C::CB / 2;                      // K = 16 slices per tap
+  static constexpr int CBS = C::NPAR * GW;                  // records per channel block
+  static constexpr int PAD = (C::WS + 8) & ~7;              // >= WS + 1 records a tap may read past the end
+  static constexpr int BUF = C::CB * CBS + PAD;             // records per input buffer
+  static constexpr int ACC = 4 * C::N;                      // accumulator columns per tile
+  static constexpr int NSLOT = 512 / ACC;                   // accumulator slots
+  static constexpr int NMMA = LAYER == 1 ? 4 * C::N : C::N;   // N of one MMA
+  static constexpr int IMG = C::NTAP * KS * 32 * NMMA;      // weight-image bytes
+  static constexpr int STAGE = LAYER == 1 ? C::S * kXnStride * 2 : 0;   // conv1: normalised stamps (bytes)
+  static constexpr int NWARP = LAYER == 1 ? 10 : 6;
+  static constexpr size_t SMEM_USED = 2 * (size_t)BUF * 16 + IMG + 2 * (size_t)STAGE;
+  // requested shared memory: at least enough that no two CTAs share an SM
+  // (each allocates all 512 tensor-memory columns)
+  static constexpr size_t SMEM = SMEM_USED > 120 * 1024 ? SMEM_USED : 120 * 1024;
+  static_assert(GW % 128 == 0 && CBS < 16384, "whole tiles per group, descriptor range");
+  static_assert(NSLOT >= 2 && SMEM <= 227 * 1024, "double buffering");
+  static_assert((BUF * 16) % 128 == 0 && IMG % 128 == 0 && STAGE % 16 == 0, "shared-memory alignment");
+};
+
+constexpr int WARP_MMA = 4, WARP_COPY = 5, WARP_BUILD = 6;
+
+// Time attribution (compile with -DRBTC_WAIT_PROFILE): lane 0 of every warp
+// adds the cycles its role spends in each wait and work phase to a per-layer
+// device array that rb_debug_conv_waits reads.  The default build compiles
+// none of it.
+enum ConvTime {
+  CT_CTA = 0,         // warp 0: the CTA's whole run
+  CT_COPY_EMPTY,      // copy warp: an input buffer (or stamp stage) to be released
+  CT_BUILD_STAGE,     // conv1 builders: staged stamps to land
+  CT_BUILD_EMPTY,     // conv1 builders: an input buffer to be released by the MMAs
+  CT_BUILD_WORK,      // conv1 builders: expanding records
+  CT_MMA_FULL,        // MMA warp: an input buffer to be filled
+  CT_MMA_ACC_EMPTY,   // MMA warp: an accumulator slot to be released
+  CT_MMA_ISSUE,       // MMA warp: issuing a tile's MMAs
+  CT_EPI_FULL,        // epilogue warps: a tile's accumulators
+  CT_EPI_WORK,        // epilogue warps: reading, pooling and storing a tile
+  CT_NKIND
+};
+#ifdef RBTC_WAIT_PROFILE
+__device__ unsigned long long g_conv_time[3][CT_NKIND];
+#define CT_T0() long long ct_t0_ = clock64()
+#define CT_ACC(kind) ct_acc_[kind] += clock64() - ct_t0_
+#else
+#define CT_T0() \
+  do {          \
+  } while (0)
+#define CT_ACC(kind) \
+  do {               \
+  } while (0)
+#endif
+
+// conv1 records of the group's stamps (ns of S) in input buffer `dst` from
+// the staged normalised stamps: for padded row r < 32 and window column wx,
+// K entry 3 e + c (e = 0 .. 3, c = 0 .. 2) is channel c of input pixel
+// (r - 1, 2 wx - 1 + e), entries 12 .. 15 zero; block 0 holds entries 0-7,
+// block 1 entries 8-15.  Zero outside the image and for stamps past ns.  `t`
+// counts the 128 building threads.
+__device__ __forceinline__ void build_conv1(int ns, uint4* dst, const bf16* sb, int t) {
   using G = Geo<1>;
-  for (int idx = threadIdx.x; idx < Cfg<1>::S * G::HPWO; idx += kThreads) {
-    const int s = idx / G::HPWO, rem = idx - s * G::HPWO, r = rem >> 5, c = rem & 31;
-    uint32_t k[9];
+  for (int idx = t; idx < Cfg<1>::S * 512; idx += 128) {
+    const int s = idx >> 9, r = (idx >> 4) & 31, wx = idx & 15;
+    uint32_t k[12];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) k[i] = 0;
+    for (int i = 0; i < 12; ++i) k[i] = 0;
     const int row = r - 1;
     if (s < ns && row >= 0 && row < 31) {
 #pragma unroll
-      for (int dxi = 0; dxi < 3; ++dxi) {
-        const int col = c - 2 + dxi;
+      for (int e = 0; e < 4; ++e) {
+        const int col = 2 * wx - 1 + e;
         if (col >= 0 && col < 31) {
           const bf16* p = sb + s * kXnStride + (row * 31 + col) * 3;
 #pragma unroll
-          for (int ci = 0; ci < 3; ++ci) k[dxi * 3 + ci] = bf_bits(p[ci]);
+          for (int c = 0; c < 3; ++c) k[3 * e + c] = bf_bits(p[c]);
         }
       }
     }
-    planes[idx] = make_uint4(k[0] | (k[1] << 16), k[2] | (k[3] << 16), k[4] | (k[5] << 16), k[6] | (k[7] << 16));
-    planes[G::STK + idx] = make_uint4(k[8], 0u, 0u, 0u);
+    const int at = (r & 1) * G::GW + s * G::SP + (r >> 1) * Cfg<1>::WS + wx;
+    dst[at] = make_uint4(k[0] | (k[1] << 16), k[2] | (k[3] << 16), k[4] | (k[5] << 16), k[6] | (k[7] << 16));
+    dst[G::CBS + at] = make_uint4(k[8] | (k[9] << 16), k[10] | (k[11] << 16), 0u, 0u);
   }
 }
 
-// 2 x 2 max of one 32-column chunk over the four slots of a pool window as a
-// reduce-scatter: the horizontal partner (lane ^ 1) and the vertical partner
-// (lane ^ 16 for WO = 16, lane ^ 8 for WO = 8, the same lane of warp ^ 1 for
-// WO = 32, through `xs`) each keep half of what they hold, so every thread
-// ends with the maximum of 8 channels: 32 ch + 16 h + 8 v + i, i = 0 .. 7.
-template <int WO>
-__device__ __forceinline__ void pool_chunk(const float (&v)[32], float (&q)[8], float* xs, int& h, int& vb) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  h = lane & 1;
-  float r[16];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    const float send = h ? v[i] : v[16 + i], keep = h ? v[16 + i] : v[i];
-    r[i] = fmaxf(keep, __shfl_xor_sync(0xffffffffu, send, 1));
-  }
-  if constexpr (WO == 32) {
-    vb = warp & 1;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) xs[i * 128 + threadIdx.x] = r[i];
-    __syncthreads();
-    const int partner = threadIdx.x ^ 32;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) q[i] = fmaxf(vb ? r[8 + i] : r[i], xs[(8 * vb + i) * 128 + partner]);
-    __syncthreads();
-  } else {
-    constexpr int X = WO == 16 ? 16 : 8;
-    vb = (lane / X) & 1;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const float send = vb ? r[i] : r[8 + i], keep = vb ? r[8 + i] : r[i];
-      q[i] = fmaxf(keep, __shfl_xor_sync(0xffffffffu, send, X));
-    }
-  }
-}
-
-// Copies of group g's input into shared memory, counted on `bar` (thread 0):
-// conv1 the normalised stamps, the other layers their channel-block planes.
+// Bulk copies of group g's input (thread 0 of the copy warp): conv1 the
+// normalised stamps into `stage`, the other layers their planes ([cb][parity]
+// [n_alloc][SP] records in memory, [cb][parity][S][SP] in `buf`).
 template <int LAYER>
-__device__ __forceinline__ void issue_group_copy(const bf16* in, int g, int n, int n_alloc, uint4* planes,
+__device__ __forceinline__ void issue_group_copy(const bf16* in, int g, int n, int n_alloc, uint4* buf,
                                                  uint8_t* stage, uint64_t* bar) {
   using C = Cfg<LAYER>;
   using G = Geo<LAYER>;
@@ -230,201 +266,300 @@ __device__ __forceinline__ void issue_group_copy(const bf16* in, int g, int n, i
     mbar_arrive_expect_tx(bar, bytes);
     bulk_g2s(stage, in + (size_t)s0 * kXnStride, bytes, bar);
   } else {
-    const unsigned bytes = (unsigned)(ns * G::HPWO * 16);
-    mbar_arrive_expect_tx(bar, (unsigned)C::CB * bytes);
-    for (int cb = 0; cb < C::CB; ++cb)
-      bulk_g2s(planes + cb * G::STK, in + ((size_t)cb * n_alloc + s0) * G::HPWO * 8, bytes, bar);
+    const unsigned bytes = (unsigned)(ns * G::SP * 16);
+    mbar_arrive_expect_tx(bar, (unsigned)(C::NPAR * C::CB) * bytes);
+    for (int cp = 0; cp < C::NPAR * C::CB; ++cp)   // (channel block, parity)
+      bulk_g2s(buf + (cp / C::NPAR) * G::CBS + (cp % C::NPAR) * G::GW, in + ((size_t)cp * n_alloc + s0) * G::SP * 8,
+               bytes, bar);
   }
 }
 
 // One convolution layer (see the file comment).  in: conv1 the normalised
-// stamps ([n][kXnStride]), else the layer's input planes ([cb][n_alloc][HP WO]
-// records); out: the next layer's planes (same n_alloc) or NHWC [n][3][3][64].
-// The next group's copy is issued as soon as its buffer is free: for conv1
-// right after the planes are built from the staged stamps (it overlaps the
-// MMAs and the epilogue), for the other layers after the last round's MMAs
-// (it overlaps that round's epilogue; the remainder round goes first so that
-// the last round is a full one).
+// stamps ([n][kXnStride]), else the layer's input planes; out: the next
+// layer's planes ([cb][parity][n_alloc][WSO^2] records) or, after conv3, NHWC
+// [n][3][3][64].
 template <int LAYER>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(32 * Geo<LAYER>::NWARP, 1)
 k_conv_tc(const bf16* __restrict__ in, int n, int n_alloc, const bf16* __restrict__ img,
           const float* __restrict__ bias, bf16* __restrict__ out, int* __restrict__ err) {
   using C = Cfg<LAYER>;
   using G = Geo<LAYER>;
   extern __shared__ __align__(128) uint8_t smem[];
-  uint4* planes = reinterpret_cast<uint4*>(smem);
-  uint8_t* bimg = smem + (size_t)C::CB * G::STK * 16;
-  float* xs = reinterpret_cast<float*>(bimg + G::IMG);
-  uint8_t* stage = bimg + G::IMG + G::XCH;
-  __shared__ uint64_t load_bar, mma_bar, w_bar;
+  uint4* buf0 = reinterpret_cast<uint4*>(smem);                 // input buffers 0 and 1
+  uint8_t* bimg = smem + 2 * (size_t)G::BUF * 16;
+  uint8_t* stage0 = bimg + G::IMG;                             // conv1: staged stamps 0 and 1
+  __shared__ uint64_t in_full[2], in_empty[2], st_full[2], st_empty[2], acc_full[G::NSLOT], acc_empty[G::NSLOT];
+  __shared__ uint64_t w_bar, done_bar;
   __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  __shared__ float sbias[C::N];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ngroups = (n + C::S - 1) / C::S;
+  const int nloc = (int)blockIdx.x < ngroups ? (ngroups - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   if (tid == 0) {
-    mbar_init(&load_bar, 1);
-    mbar_init(&mma_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&in_full[b], LAYER == 1 ? 128 : 1);
+      mbar_init(&in_empty[b], 1);
+      mbar_init(&st_full[b], 1);
+      mbar_init(&st_empty[b], 128);
+    }
+    for (int i = 0; i < G::NSLOT; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], 128);
+    }
     mbar_init(&w_bar, 1);
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // the stacks' pads are read only for output slots nobody keeps; zero them
-  for (int i = tid; i < C::CB * G::PAD; i += kThreads)
-    planes[(i / G::PAD) * G::STK + C::S * G::HPWO + i % G::PAD] = make_uint4(0u, 0u, 0u, 0u);
+  for (int i = tid; i < C::N; i += blockDim.x) sbias[i] = bias[i];
+  // the buffers' pads are read only for windows nobody keeps; zero them
+  for (int i = tid; i < 2 * G::PAD; i += blockDim.x)
+    buf0[(i / G::PAD) * G::BUF + C::CB * G::CBS + i % G::PAD] = make_uint4(0u, 0u, 0u, 0u);
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "n"(C::TCOLS) : "memory");
+  if (warp == WARP_MMA) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_base))
+                 : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tbase = tmem_base;
-  const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+  volatile int* abort = &abort_flag;
+#ifdef RBTC_WAIT_PROFILE
+  long long ct_acc_[CT_NKIND] = {};
+  const long long ct_start_ = clock64();
+#endif
 
-  // this thread's epilogue channels (pool_chunk's reduce-scatter): 32 ch +
-  // 16 h + 8 v + i; their biases stay in registers
-  const int h_me = lane & 1;
-  const int v_me = C::WO == 32 ? (warp & 1) : ((lane / (C::WO == 16 ? 16 : 8)) & 1);
-  float breg[C::N / 32][8];
-#pragma unroll
-  for (int ch = 0; ch < C::N / 32; ++ch)
-#pragma unroll
-    for (int i = 0; i < 8; ++i) breg[ch][i] = __ldg(bias + 32 * ch + 16 * h_me + 8 * v_me + i);
-
-  if (tid == 0) {
-    mbar_arrive_expect_tx(&w_bar, (unsigned)G::IMG);
-    bulk_g2s(bimg, img, (unsigned)G::IMG, &w_bar);
-    if (blockIdx.x < ngroups) issue_group_copy<LAYER>(in, blockIdx.x, n, n_alloc, planes, stage, &load_bar);
-  }
-  bool load_pending = (int)blockIdx.x < ngroups, mma_pending = false;
-  bool ok = __syncthreads_and(wait_bounded(&w_bar, 0));
-  const bool w_pending = !ok;
-  unsigned lphase = 0, mphase = 0;
-  constexpr uint32_t idesc = instr_desc(1, C::N);
-  const uint64_t bdesc0 = smem_desc_kn(smem_u32(bimg), 16 * C::N, 128);
-  const uint64_t adesc0 = smem_desc_kn(smem_u32(planes), G::STK * 16, 128);
-
-  for (int g = blockIdx.x; ok && g < ngroups; g += gridDim.x) {
-    const int s0 = g * C::S, ns = min(C::S, n - s0), gn = g + (int)gridDim.x;
-    // ---- the group's input
-    ok = __syncthreads_and(wait_bounded(&load_bar, lphase));
-    if (!ok) break;
-    load_pending = false;
-    lphase ^= 1u;
-    if constexpr (LAYER == 1) {
-      build_conv1_planes(ns, planes, reinterpret_cast<const bf16*>(stage));
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (gn < ngroups) {   // the stage is free: fetch the next group's stamps
-        if (tid == 0) issue_group_copy<LAYER>(in, gn, n, n_alloc, planes, stage, &load_bar);
-        load_pending = true;
+  if (warp == WARP_COPY) {
+    // ---- copies: the weight image once, then every group's input
+    if (lane == 0) {
+      mbar_arrive_expect_tx(&w_bar, (unsigned)G::IMG);
+      bulk_g2s(bimg, img, (unsigned)G::IMG, &w_bar);
+      int k = 0;
+      for (; k < nloc; ++k) {
+        const int b = k & 1, g = (int)blockIdx.x + k * (int)gridDim.x;
+        uint64_t* empty = LAYER == 1 ? &st_empty[b] : &in_empty[b];
+        CT_T0();
+        const bool ok_e = k < 2 || wait_phase(empty, (unsigned)(((k >> 1) - 1) & 1), abort);
+        CT_ACC(CT_COPY_EMPTY);
+        if (!ok_e) break;
+        issue_group_copy<LAYER>(in, g, n, n_alloc, buf0 + b * G::BUF, stage0 + b * G::STAGE,
+                                LAYER == 1 ? &st_full[b] : &in_full[b]);
+      }
+      // what was issued lands before the shared memory goes
+      for (int j = std::max(0, k - 2); j < k; ++j) {
+        uint64_t* full = LAYER == 1 ? &st_full[j & 1] : &in_full[j & 1];
+        for (int it = 0; it < kMaxSpin && !mbar_try_wait(full, (unsigned)((j >> 1) & 1)); ++it) {
+        }
+      }
+      for (int it = 0; it < kMaxSpin && !mbar_try_wait(&w_bar, 0); ++it) {
       }
     }
-    // ---- rounds of up to TACC tiles (the remainder first): MMAs into tensor
-    // memory, then the epilogue
-    for (int t0 = 0; t0 < G::T;) {
-      const int nt = (t0 == 0 && G::T % C::TACC) ? G::T % C::TACC : C::TACC;
-      if (tid == 0) {
+  } else if (LAYER == 1 && warp >= WARP_BUILD) {
+    // ---- conv1: staged stamps -> input buffer records
+    const int t = tid - 32 * WARP_BUILD;
+    for (int k = 0; k < nloc; ++k) {
+      const int b = k & 1, g = (int)blockIdx.x + k * (int)gridDim.x, ns = min(C::S, n - g * C::S);
+      {
+        CT_T0();
+        const bool ok_s = wait_phase(&st_full[b], (unsigned)((k >> 1) & 1), abort);
+        CT_ACC(CT_BUILD_STAGE);
+        if (!ok_s) break;
+      }
+      {
+        CT_T0();
+        const bool ok_e = k < 2 || wait_phase(&in_empty[b], (unsigned)(((k >> 1) - 1) & 1), abort);
+        CT_ACC(CT_BUILD_EMPTY);
+        if (!ok_e) break;
+      }
+      CT_T0();
+      build_conv1(ns, buf0 + b * G::BUF, reinterpret_cast<const bf16*>(stage0 + b * G::STAGE), t);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      CT_ACC(CT_BUILD_WORK);
+      mbar_arrive(&in_full[b]);
+      mbar_arrive(&st_empty[b]);
+    }
+  } else if (warp == WARP_MMA) {
+    // ---- MMAs: per tile, 4 window positions x NTAP taps x KS slices (conv1:
+    // 4 row offsets, each over all positions)
+    constexpr uint32_t idesc = instr_desc(1, G::NMMA);
+    const uint64_t bdesc0 = smem_desc_kn(smem_u32(bimg), 16 * G::NMMA, 128);
+    bool live = __all_sync(0xffffffffu, wait_phase(&w_bar, 0, abort));   // warp-uniform: .aligned ops follow
+    int tc = 0;
+    for (int k = 0; live && k < nloc; ++k) {
+      const int b = k & 1;
+      {
+        CT_T0();
+        const bool ok_f = __all_sync(0xffffffffu, wait_phase(&in_full[b], (unsigned)((k >> 1) & 1), abort));
+        CT_ACC(CT_MMA_FULL);
+        if (!ok_f) break;
+      }
+      const uint64_t adesc0 = smem_desc_kn(smem_u32(buf0 + b * G::BUF), G::CBS * 16, 128);
+      for (int t = 0; t < G::T; ++t, ++tc) {
+        const int slot = tc % G::NSLOT;
+        {
+          CT_T0();
+          const unsigned par = (unsigned)((tc / G::NSLOT - 1) & 1);
+          const bool ok_a = tc < G::NSLOT || __all_sync(0xffffffffu, wait_phase(&acc_empty[slot], par, abort));
+          CT_ACC(CT_MMA_ACC_EMPTY);
+          if (!ok_a) {
+            live = false;
+            break;
+          }
+        }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (int tt = 0; tt < nt; ++tt) {
-          const uint32_t dcol = tbase + (uint32_t)(tt * C::N);
+        CT_T0();
+        if (lane == 0) {
+          if constexpr (LAYER == 1) {
+            // one MMA per padded-row offset over all four window positions
+            const uint32_t dcol = tbase + (uint32_t)(slot * G::ACC);
 #pragma unroll
-          for (int j = 0; j < C::NTAP; ++j) {
-            const int off = C::NTAP == 9 ? (j / 3) * C::WO + j % 3 : j * C::WO + 1;   // record of the tap
+            for (int ro = 0; ro < 4; ++ro) {
+              const int rec = (ro & 1) * G::GW + t * 128 + (ro >> 1) * C::WS;
+              mma_bf16(dcol, adesc0 + (uint64_t)rec, bdesc0 + (uint64_t)(ro * 2 * G::NMMA), idesc, ro ? 1u : 0u);
+            }
+          } else {
+#pragma unroll 1
+            for (int pos = 0; pos < 4; ++pos) {
+              const int a = pos >> 1, bb = pos & 1;
+              const uint32_t dcol = tbase + (uint32_t)(slot * G::ACC + pos * C::N);
 #pragma unroll
-            for (int ks = 0; ks < G::KS; ++ks) {
-              const uint64_t a = adesc0 + (uint64_t)(2 * ks * G::STK + (t0 + tt) * 128 + off);
-              const uint64_t b = bdesc0 + (uint64_t)((j * G::KS + ks) * 2 * C::N);
-              mma_bf16(dcol, a, b, idesc, (j | ks) ? 1u : 0u);
+              for (int j = 0; j < C::NTAP; ++j) {
+                // padded offsets of the tap: rows a + dy + 1, columns b + dx + 1
+                const int ro = a + j / 3, co = bb + j % 3;
+                const int rec = ((ro & 1) * 2 + (co & 1)) * G::GW + t * 128 + (ro >> 1) * C::WS + (co >> 1);
+#pragma unroll
+                for (int ks = 0; ks < G::KS; ++ks) {
+                  const uint64_t ad = adesc0 + (uint64_t)(2 * ks * G::CBS + rec);
+                  const uint64_t bd = bdesc0 + (uint64_t)((j * G::KS + ks) * 2 * C::N);
+                  mma_bf16(dcol, ad, bd, idesc, (j | ks) ? 1u : 0u);
+                }
+              }
+            }
+          }
+          mma_commit(&acc_full[slot]);
+        }
+        __syncwarp();
+        CT_ACC(CT_MMA_ISSUE);
+      }
+      if (!live) break;
+      if (lane == 0) mma_commit(&in_empty[b]);   // the buffer is free once these MMAs complete
+      __syncwarp();
+    }
+    // every MMA issued completes before the tensor memory is freed
+    if (lane == 0) mma_commit(&done_bar);
+    __syncwarp();
+    for (int it = 0; it < kMaxSpin && !mbar_try_wait(&done_bar, 0); ++it) {
+    }
+  } else if (warp < 4) {
+    // ---- epilogue: thread = window (tensor-memory lane); max over the four
+    // window positions, bias, ReLU, BF16 records of the next layer
+    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+    int tc = 0;
+    for (int k = 0; k < nloc; ++k) {
+      const int g = (int)blockIdx.x + k * (int)gridDim.x, s0 = g * C::S, ns = min(C::S, n - s0);
+      bool live = true;
+      for (int t = 0; t < G::T; ++t, ++tc) {
+        const int slot = tc % G::NSLOT;
+        {
+          CT_T0();
+          const unsigned par = (unsigned)((tc / G::NSLOT) & 1);
+          const bool ok_f = __all_sync(0xffffffffu, wait_phase(&acc_full[slot], par, abort));
+          CT_ACC(CT_EPI_FULL);
+          if (!ok_f) {
+            live = false;
+            break;
+          }
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        CT_T0();
+        const int m = t * 128 + 32 * warp + lane, s = m / G::SP, wy = (m % G::SP) / C::WS, wx = m % C::WS;
+        const bool keep = s < ns && wy < C::PH && wx < C::PH;
+        const uint32_t col0 = tbase + lane_off + (uint32_t)(slot * G::ACC);
+#pragma unroll 1
+        for (int ch = 0; ch < C::N / 32; ++ch) {
+          float u[128], v[32];   // the chunk's 32 channels at the four window positions, one wait
+          tmem_ld4x32(col0 + 32 * ch, C::N, u);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] = fmaxf(fmaxf(u[i], u[32 + i]), fmaxf(u[64 + i], u[96 + i]));
+          if (keep) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {   // channel block 4 ch + q
+              float o[8];
+#pragma unroll
+              for (int i = 0; i < 8; ++i) o[i] = fmaxf(v[8 * q + i] + sbias[32 * ch + 8 * q + i], 0.f);
+              const uint4 rec =
+                  make_uint4(pack2(o[0], o[1]), pack2(o[2], o[3]), pack2(o[4], o[5]), pack2(o[6], o[7]));
+              const int cbo = 4 * ch + q;
+              size_t at;   // record index of the output
+              if constexpr (C::NHWC) {
+                at = ((size_t)(s0 + s) * 9 + wy * 3 + wx) * 8 + cbo;
+              } else {
+                const int r = wy + 1, c = wx + 1;   // padded output pixel
+                at = ((size_t)(cbo * 4 + (r & 1) * 2 + (c & 1)) * n_alloc + (s0 + s)) * (C::WSO * C::WSO) +
+                     (r >> 1) * C::WSO + (c >> 1);
+              }
+              reinterpret_cast<uint4*>(out)[at] = rec;
             }
           }
         }
-        mma_commit(&mma_bar);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(&acc_empty[slot]);
+        CT_ACC(CT_EPI_WORK);
       }
-      mma_pending = true;
-      ok = __syncthreads_and(wait_bounded(&mma_bar, mphase));
-      if (!ok) break;
-      mma_pending = false;
-      mphase ^= 1u;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (LAYER != 1 && t0 + nt == G::T && gn < ngroups) {   // planes no longer read: fetch the next group's
-        if (tid == 0) issue_group_copy<LAYER>(in, gn, n, n_alloc, planes, stage, &load_bar);
-        load_pending = true;
-      }
-      for (int tt = 0; tt < nt; ++tt) {
-        const int m = (t0 + tt) * 128 + 32 * warp + lane;   // this thread's slot (tensor-memory lane)
-        const int R = m / C::WO, s = R / C::HP, yo = (R % C::HP) >> 1, xo = (m % C::WO) >> 1;
-        const bool keep = s < ns && yo < C::H / 2 && xo < C::H / 2;
-#pragma unroll
-        for (int ch = 0; ch < C::N / 32; ++ch) {
-          float v[32], q[8];
-          int h, vb;
-          tmem_ld32(tbase + lane_off + (uint32_t)(tt * C::N + 32 * ch), v);
-          pool_chunk<C::WO>(v, q, xs, h, vb);
-          const int c0 = 32 * ch + 16 * h + 8 * vb;
-          float o[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) o[i] = fmaxf(q[i] + breg[ch][i], 0.f);
-          const uint4 rec = make_uint4(pack2(o[0], o[1]), pack2(o[2], o[3]), pack2(o[4], o[5]), pack2(o[6], o[7]));
-          if (keep) {
-            size_t at;   // record index of the output
-            if constexpr (C::NHWC)
-              at = (((size_t)(s0 + s) * 9 + yo * 3 + xo) * 64 + c0) / 8;
-            else
-              at = ((size_t)(c0 / 8) * n_alloc + (s0 + s)) * (C::HPO * C::WOO) + (yo + 1) * C::WOO + xo + 1;
-            reinterpret_cast<uint4*>(out)[at] = rec;
-          }
-        }
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();
-      t0 += nt;
+      if (!live) break;
     }
   }
 
-  // ---- teardown: a wait that gave up flags the error; copies or MMAs still
-  // in flight are waited for (bounded) before the shared and tensor memory go
-  if (tid == 0) {
-    if (!ok) atomicOr(err, 1);
-    if (w_pending) wait_bounded(&w_bar, 0);
-    if (load_pending) wait_bounded(&load_bar, lphase);
-    if (mma_pending) wait_bounded(&mma_bar, mphase);
-  }
+  // ---- teardown
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "n"(C::TCOLS) : "memory");
+#ifdef RBTC_WAIT_PROFILE
+  if (tid == 0) ct_acc_[CT_CTA] = clock64() - ct_start_;
+  if (lane == 0)
+    for (int k = 0; k < CT_NKIND; ++k)
+      if (ct_acc_[k]) atomicAdd(&g_conv_time[LAYER - 1][k], (unsigned long long)ct_acc_[k]);
+#endif
+  if (tid == 0 && *abort) atomicOr(err, 1);
+  if (warp == WARP_MMA)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase) : "memory");
 }
 
-// Weight images: element (j, ks, kc, co, e) of a layer with N output channels
-// sits at (((j KS + ks) 2 + kc) N + co) 8 + e and holds the weight of input
-// channel (2 ks + kc) 8 + e of tap j (conv1: K entry k = 8 kc + e, k < 9, is
-// tap (j, k / 3), channel k % 3; entries k >= 9 are zero).  Masters in GEMM
-// layout [(tap cin + ci)][cout].
+// Weight images.  conv2 and conv3: element (j, ks, kc, co, e) sits at
+// (((j KS + ks) 2 + kc) N + co) 8 + e and holds the weight of input channel
+// (2 ks + kc) 8 + e of tap j.  conv1: element (ro, kc, n, e), n = 32 pos + co,
+// sits at ((ro 2 + kc) 128 + n) 8 + e; for window position pos = 2 a + b and
+// K entry k = 8 kc + e = 3 px + c (k < 12) it holds the weight of kernel row
+// ro - a, column px - b, channel c when both lie in 0 .. 2, else zero.
+// Masters in GEMM layout [(tap cin + ci)][cout].
 __global__ void k_weight_images(const float* __restrict__ w1, const float* __restrict__ w2,
                                 const float* __restrict__ w3, bf16* __restrict__ img1, bf16* __restrict__ img2,
                                 bf16* __restrict__ img3) {
   const int total = kWImg1 + kWImg2 + kWImg3;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-    int i = idx, N, KS, cin;
-    const float* w;
+    int i = idx;
+    float v = 0.f;
     bf16* img;
     if (i < kWImg1) {
-      N = 32, KS = 1, cin = 3, w = w1, img = img1;
-    } else if ((i -= kWImg1) < kWImg2) {
-      N = 64, KS = 2, cin = 32, w = w2, img = img2;
+      img = img1;
+      const int e = i & 7, n = (i >> 3) & 127, kc = (i >> 10) & 1, ro = i >> 11;
+      const int pos = n >> 5, co = n & 31, a = pos >> 1, b = pos & 1, k = 8 * kc + e;
+      const int px = k / 3, c = k % 3, ky = ro - a, kx = px - b;
+      if (k < 12 && ky >= 0 && ky < 3 && kx >= 0 && kx < 3) v = w1[((ky * 3 + kx) * 3 + c) * 32 + co];
     } else {
-      i -= kWImg2;
-      N = 64, KS = 4, cin = 64, w = w3, img = img3;
-    }
-    const int e = i & 7, co = (i >> 3) % N, kc = (i / (8 * N)) & 1, jks = i / (16 * N);
-    const int ks = jks % KS, j = jks / KS;
-    float v;
-    if (cin == 3) {
-      const int k = 8 * kc + e;   // kernel row j, column k / 3, channel k % 3: GEMM row 9 j + k
-      v = k < 9 ? w[(j * 9 + k) * 32 + co] : 0.f;
-    } else {
+      int N, KS, cin;
+      const float* w;
+      if ((i -= kWImg1) < kWImg2) {
+        N = 64, KS = 2, cin = 32, w = w2, img = img2;
+      } else {
+        i -= kWImg2;
+        N = 64, KS = 4, cin = 64, w = w3, img = img3;
+      }
+      const int e = i & 7, co = (i >> 3) % N, kc = (i / (8 * N)) & 1, jks = i / (16 * N);
+      const int ks = jks % KS, j = jks / KS;
       v = w[(j * cin + (2 * ks + kc) * 8 + e) * N + co];
     }
     img[i] = __float2bfloat16(v);
@@ -434,31 +569,19 @@ __global__ void k_weight_images(const float* __restrict__ w1, const float* __res
 template <int LAYER>
 cudaError_t launch(const bf16* in, int n, int n_alloc, const bf16* img, const float* bias, bf16* out, int* err,
                    cudaStream_t s) {
-  using C = Cfg<LAYER>;
   using G = Geo<LAYER>;
   if (n <= 0) return cudaSuccess;
-  static int grid_cap = 0;
-  if (grid_cap == 0) {
-    // CTAs per SM: as many as the SM's shared memory holds (the carveout set
-    // to its maximum), at most as many as share its 512 tensor-memory columns
+  static int sms = 0;
+  if (sms == 0) {   // one persistent CTA per SM (its shared memory and 512 tensor-memory columns)
     cudaError_t e = cudaFuncSetAttribute(k_conv_tc<LAYER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_conv_tc<LAYER>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                               (int)cudaSharedmemCarveoutMaxShared);
-    int dev = 0, sms = 0, smem_sm = 0, reserved = 0;
-    cudaFuncAttributes fa{};
+    int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_conv_tc<LAYER>);
     if (e != cudaSuccess) return e;
-    const int per_cta = (int)G::SMEM + (int)fa.sharedSizeBytes + reserved;
-    const int occ = std::max(1, std::min(smem_sm / per_cta, 512 / C::TCOLS));
-    grid_cap = occ * sms;
   }
-  const int ngroups = (n + C::S - 1) / C::S;
-  k_conv_tc<LAYER><<<std::min(ngroups, grid_cap), kThreads, G::SMEM, s>>>(in, n, n_alloc, img, bias, out, err);
+  static_assert(2 * (G::SMEM + 2048) > 228 * 1024, "one CTA per SM: each holds all 512 tensor-memory columns");
+  const int ngroups = (n + Cfg<LAYER>::S - 1) / Cfg<LAYER>::S;
+  k_conv_tc<LAYER><<<std::min(ngroups, sms), 32 * G::NWARP, G::SMEM, s>>>(in, n, n_alloc, img, bias, out, err);
   return cudaGetLastError();
 }
 
@@ -482,3 +605,23 @@ cudaError_t conv3_tc(const bf16* p3, int n, const bf16* img3, const float* b3, b
 }
 
 }  // namespace rbtc
+
+extern "C" sfft_status_t rb_debug_conv_waits(int32_t layer, uint64_t* out, int32_t reset) {
+#ifdef RBTC_WAIT_PROFILE
+  if (!out || layer < 1 || layer > 3) return SFFT_ERR_ARG;
+  unsigned long long h[3][rbtc::CT_NKIND];
+  if (cudaMemcpyFromSymbol(h, rbtc::g_conv_time, sizeof(h)) != cudaSuccess) return SFFT_ERR_CUDA;
+  for (int k = 0; k < rbtc::CT_NKIND; ++k) out[k] = h[layer - 1][k];
+  if (reset) {
+    const unsigned long long z[rbtc::CT_NKIND] = {};
+    if (cudaMemcpyToSymbol(rbtc::g_conv_time, z, sizeof(z), sizeof(z) * (layer - 1)) != cudaSuccess)
+      return SFFT_ERR_CUDA;
+  }
+  return SFFT_OK;
+#else
+  (void)layer;
+  (void)out;
+  (void)reset;
+  return SFFT_ERR_UNSUPPORTED;
+#endif
+}

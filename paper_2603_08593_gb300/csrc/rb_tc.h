@@ -7,25 +7,27 @@
 
 namespace rbtc {
 
-// Input planes of a layer: CB blocks of 8 channels, each a plane of HP rows x
-// WO columns of 16-byte records holding pixel (row - 1, column - 1); border
-// records are zero.  Global layout [cb][stamp][HP * WO][8] (BF16).
+// Input planes of conv2 and conv3: CB blocks of 8 channels; the image padded
+// with a zero border (padded pixel (r, c) = pixel (r - 1, c - 1)) and split by
+// the parities of r and c into four WS x WS sub-planes of 16-byte records
+// (record (r >> 1, c >> 1) of sub-plane 2 (r & 1) + (c & 1)); every record
+// that holds no pixel is zero.  Memory layout [cb][parity][stamp][WS][WS][8]
+// BF16, stamps 0 .. n_alloc - 1.
 struct Planes {
-  int CB, HP, WO;
-  size_t per_stamp_elems() const { return (size_t)HP * WO * 8; }
+  int CB, WS;
+  size_t per_stamp_elems() const { return (size_t)CB * 4 * WS * WS * 8; }
 };
 // normalised stamps: NHWC 31 x 31 x 3 BF16, then 5 zero values, so that a
 // stamp is 5776 bytes and starts on a 16-byte boundary
 constexpr int kXnStride = 2888;
-constexpr Planes kP2{4, 18, 16};   // conv2 input: 15 x 15 x 32
-constexpr Planes kP3{8, 10, 8};    // conv3 input: 7 x 7 x 64
+constexpr Planes kP2{4, 8};   // conv2 input: 15 x 15 x 32
+constexpr Planes kP3{8, 4};   // conv3 input: 7 x 7 x 64
 
-// BF16 weight images of the three convolutions, one K = 16 slice per tap and
-// pair of channel blocks (C_out rows x 16, K-major core matrices), built from
-// the FP32 master weights in GEMM layout.  conv1 packs the three horizontal
-// taps of a kernel row and the three input channels into one slice (9 of its
-// 16 K entries; three slices); conv2 has 9 taps x 2 slices, conv3 9 x 4.
-constexpr int kWImg1 = 3 * 1 * 16 * 32, kWImg2 = 9 * 2 * 16 * 64, kWImg3 = 9 * 4 * 16 * 64;
+// BF16 weight images of the three convolutions (K-major core matrices, one
+// K = 16 slice per MMA), built from the FP32 master weights in GEMM layout:
+// conv1 4 row offsets x 128 (4 window positions x 32 channels) x 16, conv2
+// 9 taps x 2 slices x 64 x 16, conv3 9 x 4 x 64 x 16 values.
+constexpr int kWImg1 = 4 * 128 * 16, kWImg2 = 9 * 2 * 16 * 64, kWImg3 = 9 * 4 * 16 * 64;
 
 // Build the three weight images (one launch).  w1, w2, w3: master weights in
 // GEMM layout [(tap * cin + ci)][cout] (conv1 with its 32 padded rows).

@@ -188,18 +188,39 @@ def test_inference_full_batch_sampled():
     _check_logits(z[idx], p, st[idx])
 
 
-_PLANES = {2: (4, 18, 16, 15), 3: (8, 10, 8, 7)}   # layer input planes: CB, HP, WO, image size
+_PLANES = {2: (4, 8, 15), 3: (8, 4, 7)}   # layer input planes: CB, WS, image size
 
 
 def _to_planes(a, layer, n_alloc, fill_tail=0.0):
-    """NHWC [n][H][H][8 CB] -> channel-block planes [CB][n_alloc][HP][WO][8]
-    with zero borders; interiors of stamps >= n hold `fill_tail`."""
-    CB, HP, WO, H = _PLANES[layer]
+    """NHWC [n][H][H][8 CB] -> parity-split planes [CB][4][n_alloc][WS][WS][8]:
+    padded pixel (r, c) = pixel (r - 1, c - 1) is record (r >> 1, c >> 1) of
+    parity plane 2 (r & 1) + (c & 1), the zero border elsewhere; the pixels of
+    stamps >= n hold `fill_tail`."""
+    CB, WS, H = _PLANES[layer]
     n = a.shape[0]
-    p = np.zeros((CB, n_alloc, HP, WO, 8))
-    p[:, n:, 1:H + 1, 1:H + 1] = fill_tail
-    p[:, :n, 1:H + 1, 1:H + 1] = a.reshape(n, H, H, CB, 8).transpose(3, 0, 1, 2, 4)
-    return p
+    padded = np.zeros((n_alloc, 2 * WS, 2 * WS, CB * 8))
+    padded[n:, 1:H + 1, 1:H + 1] = fill_tail
+    padded[:n, 1:H + 1, 1:H + 1] = a
+    p = padded.reshape(n_alloc, WS, 2, WS, 2, CB, 8).transpose(5, 2, 4, 0, 1, 3, 6)
+    return p.reshape(CB, 4, n_alloc, WS, WS, 8)
+
+
+def _from_planes(t, layer, n_alloc):
+    """Inverse of _to_planes: the padded images [n_alloc][2 WS][2 WS][8 CB]."""
+    CB, WS, H = _PLANES[layer]
+    p = t.float().cpu().numpy().astype(np.float64).reshape(CB, 2, 2, n_alloc, WS, WS, 8)
+    return p.transpose(3, 4, 1, 5, 2, 0, 6).reshape(n_alloc, 2 * WS, 2 * WS, CB * 8)
+
+
+def _check_planes_out(t, layer, n, n_alloc):
+    """Output planes of a layer: border records still zero, the pixels of
+    stamps >= n untouched (7.0); returns the pixels of stamps < n (NHWC)."""
+    CB, WS, H = _PLANES[layer]
+    q = _from_planes(t, layer, n_alloc)
+    border = np.ones((2 * WS, 2 * WS), bool)
+    border[1:H + 1, 1:H + 1] = False
+    assert not np.any(q[:, border]) and np.all(q[n:, 1:H + 1, 1:H + 1] == 7.0)
+    return q[:n, 1:H + 1, 1:H + 1]
 
 
 def _layer_oracle(x_nhwc, w, b):
@@ -241,32 +262,22 @@ def test_fused_conv_layers_elementwise(n, n_alloc):
     p = _params(3 + n, bias_sd=0.1)
     m = _model(p, 8)
     x = C.round_bf16(rng.normal(0, 1.5, (n, 31, 31, 3)))
-    # conv1: NHWC stamps -> conv2 planes
+    # conv1: normalised stamps -> conv2 planes
     out = _dev(_to_planes(np.zeros((n, 15, 15, 32)), 2, n_alloc, fill_tail=7.0), torch.bfloat16)
     xin = np.zeros((n, 2888))
     xin[:, :2883] = x.reshape(n, -1)
     m.conv_layer(1, _dev(xin, torch.bfloat16), n, n_alloc, out)
-    got = out.float().cpu().numpy().astype(np.float64).reshape(4, n_alloc, 18, 16, 8)
     exact, scale = _layer_oracle(x, p["w1"], p["b1"])
-    border = np.ones((18, 16), bool)
-    border[1:16, 1:16] = False
-    assert not np.any(got[:, :, border]) and np.all(got[:, n:, 1:16, 1:16] == 7.0)
-    _check_layer(got[:, :n, 1:16, 1:16].transpose(1, 2, 3, 0, 4).reshape(n, 15, 15, 32), exact, scale)
+    _check_layer(_check_planes_out(out, 2, n, n_alloc), exact, scale)
     # conv2 and conv3 on non-negative BF16 activations of their own
-    for layer, (cin, cout, H) in ((2, (32, 64, 15)), (3, (64, 64, 7))):
+    for layer, (cin, H) in ((2, (32, 15)), (3, (64, 7))):
         a = C.round_bf16(np.abs(rng.normal(0, 1.0, (n, H, H, cin))) * (rng.random((n, H, H, cin)) < 0.6))
         inp = _dev(_to_planes(a, layer, n_alloc), torch.bfloat16)
-        w, b = p[f"w{layer}"], p[f"b{layer}"]
-        exact, scale = _layer_oracle(a, w, b)
-        Ho = H // 2
+        exact, scale = _layer_oracle(a, p[f"w{layer}"], p[f"b{layer}"])
         if layer == 2:
             out = _dev(_to_planes(np.zeros((n, 7, 7, 64)), 3, n_alloc, fill_tail=7.0), torch.bfloat16)
             m.conv_layer(2, inp, n, n_alloc, out)
-            got = out.float().cpu().numpy().astype(np.float64).reshape(8, n_alloc, 10, 8, 8)
-            border = np.ones((10, 8), bool)
-            border[1:8, 1:8] = False
-            assert not np.any(got[:, :, border]) and np.all(got[:, n:, 1:8, 1:8] == 7.0)
-            got = got[:, :n, 1:8, 1:8].transpose(1, 2, 3, 0, 4).reshape(n, Ho, Ho, cout)
+            got = _check_planes_out(out, 3, n, n_alloc)
         else:
             out = torch.full((n * 9 * 64 + 64,), 7.0, dtype=torch.bfloat16, device=DEV)
             m.conv_layer(3, inp, n, n_alloc, out)
@@ -280,7 +291,7 @@ def test_fused_conv_layers_elementwise(n, n_alloc):
 def test_fused_conv_layer_arguments():
     m = _model(_params(1), 4)
     x = torch.zeros(4 * 2888, dtype=torch.bfloat16, device=DEV)
-    y = torch.zeros(4 * 4 * 288 * 8, dtype=torch.bfloat16, device=DEV)
+    y = torch.zeros(4 * 4 * 4 * 64 * 8, dtype=torch.bfloat16, device=DEV)
     from paper_2603_08593_gb300.binding import SfftError
     for layer, n, na in ((0, 1, 1), (4, 1, 1), (1, 5, 4), (1, 1, 0), (1, -1, 4)):
         with pytest.raises(SfftError):
