@@ -293,6 +293,29 @@ CNN_RI_FWD_FLOP = 2.0 * (4 * (961 * 27 * 32 + 2 * 225 * 288 * 32 + 225 * 288 * 6
                          + 576 * 128 + 128)
 
 
+CONV_TIME_KINDS = ("cta", "copy_wait_empty", "build_wait_stage", "build_wait_empty", "build_work", "mma_wait_full",
+                   "mma_wait_acc_empty", "mma_issue", "epilogue_wait_full", "epilogue_work")
+CONV_TIME_WARPS = (1, 1, 4, 4, 4, 1, 1, 1, 4, 4)   # warps whose lane 0 adds to each counter
+
+
+def conv_waits(reset):
+    """Time attribution of the fused classifier convolutions per layer, as
+    fractions of the CTAs' run per warp of each role; None unless the library
+    was built with -DRBTC_WAIT_PROFILE (rb_debug_conv_waits)."""
+    import ctypes
+    from paper_2603_08593_gb300 import binding
+    lib = binding.load()
+    buf = (ctypes.c_uint64 * 16)()
+    res = {}
+    for layer in (1, 2, 3):
+        if lib.rb_debug_conv_waits(layer, buf, 1 if reset else 0) != 0:
+            return None
+        cta = max(int(buf[0]), 1)
+        res[f"conv{layer}"] = {k: round(int(buf[i]) / (cta * CONV_TIME_WARPS[i]), 4)
+                               for i, k in enumerate(CONV_TIME_KINDS) if i and buf[i]}
+    return res
+
+
 def time_classifier(dev, n_infer=32768, batch=256, steps=40, arch="small"):
     """Stamp-classifier throughput on synthetic 31 x 31 x 3 stamps: inference
     (normalise + forward + sigmoid) and training steps (forward, backward, Adam),
@@ -311,6 +334,7 @@ def time_classifier(dev, n_infer=32768, batch=256, steps=40, arch="small"):
     out = torch.empty(n_infer, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream(dev)
     m.score(stamps, out=out)
+    waits = conv_waits(reset=True) if arch == "small" else None
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
     for _ in range(3):
@@ -318,6 +342,8 @@ def time_classifier(dev, n_infer=32768, batch=256, steps=40, arch="small"):
     e1.record(st)
     e1.synchronize()
     inf_s = e0.elapsed_time(e1) / 1e3 / 3
+    if waits is not None:   # a build with the convolutions' time attribution compiled in
+        waits = conv_waits(reset=True)
     tb = base[:batch].contiguous()
     tl = lab[:batch].contiguous()
     loss = torch.empty(1, dtype=torch.float32, device=dev)
@@ -329,12 +355,26 @@ def time_classifier(dev, n_infer=32768, batch=256, steps=40, arch="small"):
     e1.synchronize()
     tr_s = e0.elapsed_time(e1) / 1e3 / steps
     inf_rate = n_infer / inf_s
-    return {"inference_stamps_per_s": inf_rate, "train_stamps_per_s": batch / tr_s,
-            "inference_tflops": inf_rate * fwd / 1e12,
-            "train_tflops": 3 * fwd * batch / tr_s / 1e12,
-            "note": f"synthetic stamps; inference on {n_infer} stamps in batches of {m.max_batch}, training batch "
-                    f"{batch}; BF16 mma.sync GEMMs with FP32 accumulation, flops = network multiply-adds x 2 "
-                    "(training = 3 x forward)"}
+    out = {"inference_stamps_per_s": inf_rate, "train_stamps_per_s": batch / tr_s,
+           "inference_tflops": inf_rate * fwd / 1e12,
+           "train_tflops": 3 * fwd * batch / tr_s / 1e12}
+    if arch == "small":
+        from paper_2603_08593_gb300 import binding
+        out["note"] = (f"synthetic stamps; inference on {n_infer} stamps in batches of {m.max_batch}: exact-median "
+                       "normalisation, the three convolutions fused with bias, ReLU and max-pool on tcgen05 "
+                       "(BF16, FP32 accumulation in tensor memory), the dense layers on mma.sync; training batch "
+                       f"{batch} on mma.sync; flops = network multiply-adds x 2 (training = 3 x forward)")
+        # the convolutions' MMAs read both operands from shared memory: their
+        # cost by N bounds the fused kernels (conv1 issues N = 128, conv2 and
+        # conv3 N = 64)
+        out["umma_cycles_per_mma"] = {str(n): binding.probe_umma_cycles(n) for n in (32, 64, 128, 256)}
+        if waits is not None:
+            out["conv_time_attribution"] = waits
+    else:
+        out["note"] = (f"synthetic stamps; inference on {n_infer} stamps in batches of {m.max_batch}, training batch "
+                       f"{batch}; BF16 mma.sync GEMMs with FP32 accumulation, flops = network multiply-adds x 2 "
+                       "(training = 3 x forward)")
+    return out
 
 
 def measured_alu_peaks():

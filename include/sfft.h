@@ -154,6 +154,15 @@ sfft_status_t sfft_debug_contract_waits(uint64_t* out9, int32_t reset);
  * CUDA events on `cuda_stream` after one warm-up launch (synchronizes the
  * stream).  Allocates and frees a small device buffer for the results. */
 sfft_status_t sfft_probe_fma_peak(int32_t fp64, double* tflops, void* cuda_stream);
+/* Measured cost of one tcgen05 MMA with both operands in shared memory (no
+ * counterpart in the paper; it bounds the stamp classifier's convolutions):
+ * clock cycles per kind::f16 BF16 MMA of M = 128, K = 16 and N = n columns
+ * (16 <= n <= 256, n % 16 == 0, else SFFT_ERR_ARG), canonical K-major layout
+ * without swizzle, 2000 issued back to back by one thread per CTA, one CTA per
+ * SM, averaged over the SMs after a warm-up launch.  SFFT_ERR_TIMEOUT if a
+ * bounded completion wait gave up.  Synchronizes the stream; allocates and
+ * frees a small device buffer. */
+sfft_status_t sfft_probe_umma_cycles(int32_t n, double* cycles_per_mma, void* cuda_stream);
 /* Number of device allocations the library's plans (and the plan-time
  * autotuner) currently hold.  For leak checks: with SFFT_FAIL_ALLOC=n set in
  * the environment, the n-th device allocation of every sfft_plan call fails

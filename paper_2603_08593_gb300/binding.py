@@ -44,6 +44,7 @@ SIGNATURES = {
     "sfft_plan_set_wait_limit": (I32, [VP, I32]),
     "sfft_debug_live_allocations": (I64, []),
     "sfft_probe_fma_peak": (I32, [I32, C.POINTER(C.c_double), VP]),
+    "sfft_probe_umma_cycles": (I32, [I32, C.POINTER(C.c_double), VP]),
     "sfft_debug_contract_waits": (I32, [C.POINTER(C.c_uint64), I32]),
     "sfft_build_normal": (I32, [VP, VP, VP, VP, VP, VP, VP, VP]),
     "sfft_solve": (I32, [VP, VP, VP, VP, I32, VP, VP, VP, VP, VP]),
@@ -136,6 +137,17 @@ def _device(device):
 
 def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def probe_umma_cycles(n, stream=None):
+    """Clock cycles per tcgen05 MMA (BF16, M = 128, K = 16, N = n) with both
+    operands in shared memory (include/sfft.h sfft_probe_umma_cycles)."""
+    import torch
+    lib = load()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = C.c_double()
+    _check(lib.sfft_probe_umma_cycles(int(n), C.byref(out), VP(s.cuda_stream)), "sfft_probe_umma_cycles")
+    return float(out.value)
 
 
 def probe_fma_peak(fp64=False, stream=None):

@@ -539,3 +539,17 @@ def test_adaptive_shape_cuts_match_oracle():
     assert len(diff) <= 2
     assert 0 < exp.sum() < 400
     assert not out[:5].any()
+
+
+def test_umma_probe_rates():
+    """The MMA-rate probe (sfft_probe_umma_cycles): finite positive cycle
+    counts, wider MMAs no cheaper than narrower ones and at least the
+    arithmetic time at N = 256; invalid N rejected."""
+    from paper_2603_08593_gb300 import binding
+    c = {n: binding.probe_umma_cycles(n) for n in (64, 256)}
+    assert all(0 < v < 1e4 for v in c.values()), c
+    assert c[256] >= c[64]
+    assert c[256] >= 0.9 * 128 * 256 * 16 / 4096   # 2 x 128 x 256 x 16 flop at <= 8192 flop per clock
+    for bad in (0, 8, 264):
+        with pytest.raises(binding.SfftError):
+            binding.probe_umma_cycles(bad)
