@@ -678,10 +678,15 @@ def run_gpu(args):
         # solution and for the refinement step
         flop = B * (2.0 * Nn ** 3 / 3.0 + (1 + REFINE) * 2 * 2.0 * Nn * Nn)
         ms = prof["solve"][0] / args.steps
-        solve_rec = {"ms": ms, "flop": flop, "fp64_tflops": flop / (ms * 1e-3) / 1e12,
-                     "fp64_frac": flop / (ms * 1e-3) / 1e12 / alu_peaks["fp64_tflops"],
-                     "note": "FP64 solve phase (factorisation, substitutions, units) against the measured FP64 "
-                             "FMA peak"}
+        fp64_solve = args.prec == "fp64"
+        peak = alu_peaks["fp64_tflops"] if fp64_solve else alu_peaks["fp32_tflops"]
+        solve_rec = {"ms": ms, "flop": flop, "tflops": flop / (ms * 1e-3) / 1e12,
+                     "frac": flop / (ms * 1e-3) / 1e12 / peak, "peak_tflops": peak,
+                     "note": ("FP64 solve phase (factorisation, substitutions, units) against the measured FP64 FMA "
+                              "peak" if fp64_solve else
+                              "solve phase of the mixed path: Cholesky of the Jacobi-scaled system and the "
+                              "substitutions in FP32, the solution refined against the FP64 system by the "
+                              "image-space refinement step; against the measured FP32 FMA peak (latency-bound)")}
     if batched:
         workload = (f"{B} CCD pairs of one DECam exposure per GPU per step (2048x4096 FP32 each, independent PSF "
                     f"gradients, masked fractions 2-30 %, cosmics, bleed trails) in one CUDA-graph-captured call; "

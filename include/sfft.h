@@ -75,7 +75,9 @@ typedef enum {
   SFFT_PREC_FP64 = 0,        /* FFTs, products, partial sums and apply in FP64 */
   SFFT_PREC_MIXED = 1        /* FP32 FFTs/products/partials (KK products with split operands on the
                                 tensor cores: hi x hi in TF32 plus two BF16 corrections, about
-                                2^-18 per product); FP64 accumulation, solve, refinement */
+                                2^-18 per product); FP64 accumulation and refinement; Cholesky
+                                factor and substitutions in FP32, every solution refined against
+                                the FP64 system (see sfft_solve) */
 } sfft_prec_t;
 
 #define SFFT_FLAG_GRAPH 1u        /* sfft_subtract replays a captured CUDA graph */
@@ -103,7 +105,8 @@ typedef struct {
                                 FP32 path only, the FP64 path uses 2) */
   uint32_t flags;            /* SFFT_FLAG_* */
   int32_t ccd_group;         /* CCDs whose product spectra are held at once (0 = auto: every difference of a
-                                CCD in one pass, as many CCDs as 64 GB of product spectra hold) */
+                                CCD in one pass when its spectra fit 64 GB, as many CCDs as 32 GB of
+                                product spectra hold) */
 } sfft_desc_t;
 
 /* Create a plan: validates the descriptor, builds offset/monomial/lag tables,
@@ -187,11 +190,15 @@ sfft_status_t sfft_build_normal(sfft_plan_t plan, const float* R, const float* S
                                 const uint8_t* bad, const double* sky,
                                 double* A, double* b, void* ws);
 
-/* Solve A theta = b per CCD in FP64 (with SFFT_FLAG_CONST_RATIO the
- * projected system T A T^T theta_c = T b, theta = T^T theta_c): Jacobi
- * equilibration, Cholesky, two triangular solves; then `refine_steps` steps of
- * iterative refinement whose residual r = sum_x M_fit Phi (S' - model) is
- * formed in image space from R and S.  theta : double [batch][N]; its
+/* Solve A theta = b per CCD (with SFFT_FLAG_CONST_RATIO the projected
+ * system T A T^T theta_c = T b, theta = T^T theta_c): Jacobi equilibration,
+ * Cholesky, two triangular solves; then `refine_steps` steps of iterative
+ * refinement whose residual r = sum_x M_fit Phi (S' - model) is formed in
+ * image space from R and S.  The FP64 plan factors and substitutes in FP64.
+ * The mixed plan factors the equilibrated matrix and substitutes in FP32; the
+ * refinement steps refine that solution (their residual is b - A theta), and
+ * with refine_steps = 0 one normal-equations step r = b - A theta in FP64
+ * does.  theta : double [batch][N]; its
  * background part is returned in original (un-offset) units,
  * beta_q + s_S [q == 0] - s_R sum_j theta[j, q] for q < min(N_K, N_B), which
  * is B = B' + s_S - s_R sum_j K_j exactly unless D_B < D_K with a free kernel
@@ -260,7 +267,8 @@ enum {
   SFFT_PROF_CONTRACT_KK = 3, /* lag contraction of the product spectra (KK block) */
   SFFT_PROF_CONTRACT_RK = 4, /* lag contraction against R_m spectra (KB, b_K, refinement) */
   SFFT_PROF_SCATTER = 5,     /* assembly of A and b from the accumulators */
-  SFFT_PROF_SOLVE = 6,       /* Cholesky and triangular solves */
+  SFFT_PROF_SOLVE = 6,       /* Cholesky, triangular solves (and, mixed with no refinement steps,
+                                one FP64 residual step) */
   SFFT_PROF_APPLY = 7,       /* convolve-and-subtract and refinement residual */
   SFFT_PROF_LAG_DFT = 8,     /* tensor-core KK paths: lags u_x over the k-slot products and the
                                 exact slot-0 sums */

@@ -457,12 +457,14 @@ static sfft_status_t plan_impl(const sfft_desc_t* desc, void* cuda_stream, sfft_
       }
   p->n_hd = (int)p->dlist.size();
   const size_t slab = (size_t)d.H * p->M * 2 * p->elem;
-  // product spectra of up to 64 GB per plan (GB300: 288 GB of HBM3e).  The
-  // product-spectrum stage runs per group of CCDs with every difference in
-  // one pass when one CCD's spectra fit (7.4 GB at 2048 x 4096): a 60-CCD
-  // exposure then runs in groups of 8 on the same contraction engine as a
-  // single CCD.  Otherwise one CCD at a time with as many differences as fit.
-  const size_t budget = size_t(64) << 30;
+  // product spectra of up to 64 GB per CCD pass (GB300: 288 GB of HBM3e).
+  // The product-spectrum stage runs per group of CCDs with every difference
+  // in one pass when one CCD's spectra fit (7.4 GB at 2048 x 4096), on the
+  // same contraction engine as a single CCD; otherwise one CCD at a time with
+  // as many differences as fit.  A group holds at most 32 GB of spectra: the
+  // difference-lane contraction measured 3.47 / 3.33 / 3.30 / 3.30 ms per
+  // CCD with groups of 1 / 2 / 3 / 4 CCDs, but 5.2 ms with 9 (67 GB).
+  const size_t budget = size_t(64) << 30, group_budget = size_t(32) << 30;
   const int d_batch_max = (int)std::max<size_t>(1, std::min<size_t>(budget / slab, (size_t)p->n_hd));
   int tuned_db = 0, tuned_rows = 0, tuned_parts = 0;
   if (d.autotune && (d.d_batch == 0 || d.rows_per_cta == 0 || d.lag_parts == 0)) {
@@ -477,7 +479,8 @@ static sfft_status_t plan_impl(const sfft_desc_t* desc, void* cuda_stream, sfft_
   else p->d_batch = tuned_db > 0 ? std::min(tuned_db, p->n_hd) : d_batch_max;
   if (d.rows_per_cta > 0) p->rows_per_cta = d.rows_per_cta;
   else p->rows_per_cta = tuned_rows > 0 ? tuned_rows : std::min(d.H, 1024);
-  p->ccd_group = (int)std::max<size_t>(1, std::min<size_t>(budget / (slab * (size_t)p->d_batch), (size_t)d.batch));
+  p->ccd_group =
+      (int)std::max<size_t>(1, std::min<size_t>(group_budget / (slab * (size_t)p->d_batch), (size_t)d.batch));
   if (d.ccd_group > 0) p->ccd_group = std::min(d.ccd_group, d.batch);
   if (d.lag_parts > 0) p->csplit = d.lag_parts;
   else p->csplit = tuned_parts > 0 ? tuned_parts : 2;
@@ -668,6 +671,13 @@ static sfft_status_t solve_impl(sfft_plan_t p, const double* A, const double* b,
     CK(launch_cholesky(p, A, ws));
     const sfft_status_t s0 = solve_rhs(b, false);
     if (s0 != SFFT_OK) return s0;
+    if (!p->fp64 && refine == 0) {
+      // the FP32 factor's solution, refined once against the FP64 system
+      // (the image-space steps below refine it otherwise)
+      CK(launch_residual(p, A, b, toff, rhs));
+      const sfft_status_t s1 = solve_rhs(rhs, true);
+      if (s1 != SFFT_OK) return s1;
+    }
   }
   for (int r = 0; r < refine; ++r) {
     void* e = ws_at<char>(ws, p->eimg);

@@ -173,13 +173,14 @@ __global__ void k_cpr_expand(const double* __restrict__ x, double* __restrict__ 
 
 // scale = diag(A_s)^-1/2; Lf (lower) = D_s A_s D_s; status flags.  A_s is the
 // solved system: A itself (row stride N = Ns) or T A T^T (size Ns).
+template <typename T>
 __global__ void __launch_bounds__(256)
-k_chol_init(const double* __restrict__ A, double* __restrict__ Lf, double* __restrict__ scale,
+k_chol_init(const double* __restrict__ A, T* __restrict__ Lf, double* __restrict__ scale,
             int* __restrict__ status, int N, int Ns, CprMap m) {
   const int ccd = blockIdx.y;
   const int64_t NS2 = (int64_t)Ns * Ns;
   const double* a = A + ccd * (int64_t)N * N;
-  double* l = Lf + ccd * NS2;
+  T* l = Lf + ccd * NS2;
   double* s = scale + (int64_t)ccd * Ns;
   if (blockIdx.x == 0) {
     for (int i = threadIdx.x; i < Ns; i += blockDim.x) {
@@ -195,7 +196,7 @@ k_chol_init(const double* __restrict__ A, double* __restrict__ Lf, double* __res
     const double si = di > 0.0 ? rsqrt(di) : 0.0, sj = dj > 0.0 ? rsqrt(dj) : 0.0;
     const double v = cpr_entry(a, N, m, i, j);
     if (!isfinite(v)) atomicOr(&status[ccd], 2);
-    l[t] = v * si * sj;
+    l[t] = (T)(v * si * sj);
     if (i == j) s[i] = si;
   }
 }
@@ -250,21 +251,26 @@ __device__ bool grid_sync_bounded(GridBar* bar, int* flag_sh, int spin_limit) {
   return *flag_sh != 0;
 }
 
+template <typename T>
 struct CholSmem {
-  double blk[NBK][NBK + 1];   // diagonal block, or the rows of a piece
-  double aux[NBK][NBK + 1];   // a diagonal factor, panel rows, or an inverse
-  double pinv[NBK], prs[NBK], dgl[NBK];   // per pivot d: 1 / d, 1 / sqrt(d), sqrt(d)
+  T blk[NBK][NBK + 1];   // diagonal block, or the rows of a piece
+  T aux[NBK][NBK + 1];   // a diagonal factor, panel rows, or an inverse
+  T pinv[NBK], prs[NBK], dgl[NBK];   // per pivot d: 1 / d, 1 / sqrt(d), sqrt(d)
   unsigned char ti[NTRI], tj[NTRI];       // e -> (i, j), j <= i, e = i (i + 1) / 2 + j
   int flag;
 };
 
 // Pivot c: a non-positive or non-finite d is replaced by 1 and reported in
 // the CCD's status word.
-__device__ __forceinline__ void set_pivot(CholSmem& S, int c, double d0, int* st) {
-  const bool bad = !(d0 > 0.0) || !isfinite(d0);
+__device__ __forceinline__ double rsq(double d) { return rsqrt(d); }
+__device__ __forceinline__ float rsq(float d) { return rsqrtf(d); }
+
+template <typename T>
+__device__ __forceinline__ void set_pivot(CholSmem<T>& S, int c, T d0, int* st) {
+  const bool bad = !(d0 > T(0)) || !isfinite(d0);
   if (bad) atomicOr(st, isfinite(d0) ? 1 : 2);
-  const double d = bad ? 1.0 : d0;
-  const double r = rsqrt(d);
+  const T d = bad ? T(1) : d0;
+  const T r = rsq(d);
   S.pinv[c] = r * r;
   S.prs[c] = r;
   S.dgl[c] = d * r;
@@ -274,16 +280,17 @@ __device__ __forceinline__ void set_pivot(CholSmem& S, int c, double d0, int* st
 // looking on the unscaled Schur complement, a_ij -= a_ic a_jc / d_c for
 // c < j <= i, one barrier per column (the thread that updates the next
 // diagonal element forms its pivot at once), then l_ij = a_ij / sqrt(d_j).
-__device__ void factor_block(CholSmem& S, int* st) {
+template <typename T>
+__device__ void factor_block(CholSmem<T>& S, int* st) {
   const int tid = threadIdx.x;
   if (tid == 0) set_pivot(S, 0, S.blk[0][0], st);
   __syncthreads();
   for (int c = 0; c < NBK - 1; ++c) {
-    const double p = S.pinv[c];
+    const T p = S.pinv[c];
     const int m = NBK - 1 - c;
     for (int e = tid; e < m * (m + 1) / 2; e += blockDim.x) {
       const int i = c + 1 + S.ti[e], j = c + 1 + S.tj[e];
-      const double v = S.blk[i][j] - S.blk[i][c] * S.blk[j][c] * p;
+      const T v = S.blk[i][j] - S.blk[i][c] * S.blk[j][c] * p;
       S.blk[i][j] = v;
       if (e == 0) set_pivot(S, c + 1, v, st);   // (i, j) = (c + 1, c + 1)
     }
@@ -298,13 +305,14 @@ __device__ void factor_block(CholSmem& S, int* st) {
 
 // S.aux = inverse of the lower factor in S.blk (L X = I by row elimination:
 // row t is final once scaled, then removed below).
-__device__ void invert_block(CholSmem& S) {
+template <typename T>
+__device__ void invert_block(CholSmem<T>& S) {
   const int tid = threadIdx.x;
   for (int e = tid; e < NBK * (NBK + 1); e += blockDim.x) {
     const int i = e / (NBK + 1), j = e % (NBK + 1);
-    S.aux[i][j] = i == j ? 1.0 : 0.0;
+    S.aux[i][j] = i == j ? T(1) : T(0);
   }
-  if (tid < NBK) S.pinv[tid] = 1.0 / S.blk[tid][tid];
+  if (tid < NBK) S.pinv[tid] = T(1) / S.blk[tid][tid];
   __syncthreads();
   for (int t = 0; t < NBK; ++t) {
     if (tid <= t) S.aux[t][tid] *= S.pinv[t];
@@ -320,24 +328,27 @@ __device__ void invert_block(CholSmem& S) {
 
 // S.blk <- the factored diagonal block at rows/columns [r0, r0 + nb) of l
 // (identity past nb)
-__device__ void load_block(CholSmem& S, const double* __restrict__ l, int N, int r0, int nb, double (*dst)[NBK + 1]) {
+template <typename T>
+__device__ void load_block(const T* __restrict__ l, int N, int r0, int nb, T (*dst)[NBK + 1]) {
   for (int e = threadIdx.x; e < NBK * NBK; e += blockDim.x) {
     const int i = e / NBK, j = e % NBK;
-    dst[i][j] = (i < nb && j <= i) ? __ldcg(l + (int64_t)(r0 + i) * N + r0 + j) : (i == j ? 1.0 : 0.0);
+    dst[i][j] = (i < nb && j <= i) ? __ldcg(l + (int64_t)(r0 + i) * N + r0 + j) : (i == j ? T(1) : T(0));
   }
 }
 
-__device__ void store_block(const CholSmem& S, double* __restrict__ l, int N, int r0, int nb) {
+template <typename T>
+__device__ void store_block(const CholSmem<T>& S, T* __restrict__ l, int N, int r0, int nb) {
   for (int e = threadIdx.x; e < NTRI; e += blockDim.x) {
     const int i = S.ti[e], j = S.tj[e];
     if (i < nb) l[(int64_t)(r0 + i) * N + r0 + j] = S.blk[i][j];
   }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(256)
-k_chol_coop(double* __restrict__ Lf, double* __restrict__ dinv, int* __restrict__ status, int N, int B,
+k_chol_coop(T* __restrict__ Lf, T* __restrict__ dinv, int* __restrict__ status, int N, int B,
             GridBar* __restrict__ bar, int spin_limit) {
-  __shared__ CholSmem S;
+  __shared__ CholSmem<T> S;
   const int nblk = (N + NBK - 1) / NBK;
   const int64_t NN = (int64_t)N * N;
   const int tid = threadIdx.x, G = gridDim.x;
@@ -352,7 +363,7 @@ k_chol_coop(double* __restrict__ Lf, double* __restrict__ dinv, int* __restrict_
   // as their last trailing update lands (look-ahead inside phase C)
   for (int ccd = blockIdx.x; ccd < B; ccd += G) {
     __syncthreads();
-    load_block(S, Lf + ccd * NN, N, 0, min(NBK, N), S.blk);
+    load_block(Lf + ccd * NN, N, 0, min(NBK, N), S.blk);
     __syncthreads();
     factor_block(S, status + ccd);
     store_block(S, Lf + ccd * NN, N, 0, min(NBK, N));
@@ -361,27 +372,27 @@ k_chol_coop(double* __restrict__ Lf, double* __restrict__ dinv, int* __restrict_
   for (int k = 0; ok && k < nblk; ++k) {
     const int kb = k * NBK, nb = min(NBK, N - kb), rem = N - kb - nb;
     if (rem <= 0) break;   // uniform: the last block has no panel
-    const int T = (rem + NBK - 1) / NBK;   // block rows below the diagonal block
+    const int TB = (rem + NBK - 1) / NBK;   // block rows below the diagonal block
     const int r0 = kb + nb;
     // (B) panel pieces: X L_kk^T = A, warp = row of the piece, lane = column
-    for (int item = blockIdx.x; item < B * T * (NBK / PRW); item += G) {
-      const int ccd = item / (T * (NBK / PRW)), pc = item % (T * (NBK / PRW));
+    for (int item = blockIdx.x; item < B * TB * (NBK / PRW); item += G) {
+      const int ccd = item / (TB * (NBK / PRW)), pc = item % (TB * (NBK / PRW));
       const int p0 = r0 + pc * PRW;
-      double* l = Lf + ccd * NN;
+      T* l = Lf + ccd * NN;
       __syncthreads();
-      load_block(S, l, N, kb, nb, S.aux);
+      load_block(l, N, kb, nb, S.aux);
       for (int e = tid; e < PRW * NBK; e += blockDim.x) {
         const int i = e / NBK, c = e % NBK;
-        S.blk[i][c] = (p0 + i < N && c < nb) ? __ldcg(l + (int64_t)(p0 + i) * N + kb + c) : 0.0;
+        S.blk[i][c] = (p0 + i < N && c < nb) ? __ldcg(l + (int64_t)(p0 + i) * N + kb + c) : T(0);
       }
       __syncthreads();
       if (warp < PRW) {
-        const double rd = 1.0 / S.aux[lane][lane];
-        double acc = S.blk[warp][lane], x = 0.0;
+        const T rd = T(1) / S.aux[lane][lane];
+        T acc = S.blk[warp][lane], x = T(0);
 #pragma unroll 4
         for (int t = 0; t < NBK; ++t) {
           if (lane == t) x = acc * rd;
-          const double xt = __shfl_sync(0xffffffffu, x, t);
+          const T xt = __shfl_sync(0xffffffffu, x, t);
           if (lane > t) acc -= xt * S.aux[lane][t];
         }
         if (p0 + warp < N && lane < nb) l[(int64_t)(p0 + warp) * N + kb + lane] = x;
@@ -390,23 +401,23 @@ k_chol_coop(double* __restrict__ Lf, double* __restrict__ dinv, int* __restrict_
     if (!(ok = grid_sync_bounded(bar, &S.flag, spin_limit))) break;
     // (C) the next diagonal block of every CCD (one CTA each: update and
     // factor), then 8 x 32 pieces of the other trailing tiles
-    const int ntile = T * (T + 1) / 2;
+    const int ntile = TB * (TB + 1) / 2;
     const int npiece = (ntile - 1) * (NBK / PRW);
     for (int item = blockIdx.x; item < B + B * npiece; item += G) {
       __syncthreads();
       if (item < B) {
         const int ccd = item, nb2 = min(NBK, rem);
-        double* l = Lf + ccd * NN;
+        T* l = Lf + ccd * NN;
         for (int e = tid; e < NBK * NBK; e += blockDim.x) {
           const int i = e / NBK, c = e % NBK;
-          S.aux[i][c] = (i < nb2 && c < nb) ? __ldcg(l + (int64_t)(r0 + i) * N + kb + c) : 0.0;
+          S.aux[i][c] = (i < nb2 && c < nb) ? __ldcg(l + (int64_t)(r0 + i) * N + kb + c) : T(0);
         }
         __syncthreads();
         for (int e = tid; e < NTRI; e += blockDim.x) {
           const int i = S.ti[e], j = S.tj[e];
-          double v = i == j ? 1.0 : 0.0;
+          T v = i == j ? T(1) : T(0);
           if (i < nb2) {
-            double s0 = 0.0, s1 = 0.0;
+            T s0 = T(0), s1 = T(0);
 #pragma unroll 8
             for (int c = 0; c < NBK; c += 2) {
               s0 += S.aux[i][c] * S.aux[j][c];
@@ -426,20 +437,20 @@ k_chol_coop(double* __restrict__ Lf, double* __restrict__ dinv, int* __restrict_
       while (t > bi) { t -= bi + 1; ++bi; }
       const int bj = t;
       const int i0 = r0 + bi * NBK + (pc % (NBK / PRW)) * PRW, j0 = r0 + bj * NBK;
-      double* l = Lf + ccd * NN;
+      T* l = Lf + ccd * NN;
       for (int e = tid; e < NBK * NBK; e += blockDim.x) {
         const int j = e / NBK, c = e % NBK;
-        S.aux[j][c] = (j0 + j < N && c < nb) ? __ldcg(l + (int64_t)(j0 + j) * N + kb + c) : 0.0;
+        S.aux[j][c] = (j0 + j < N && c < nb) ? __ldcg(l + (int64_t)(j0 + j) * N + kb + c) : T(0);
       }
       for (int e = tid; e < PRW * NBK; e += blockDim.x) {
         const int i = e / NBK, c = e % NBK;
-        S.blk[i][c] = (i0 + i < N && c < nb) ? __ldcg(l + (int64_t)(i0 + i) * N + kb + c) : 0.0;
+        S.blk[i][c] = (i0 + i < N && c < nb) ? __ldcg(l + (int64_t)(i0 + i) * N + kb + c) : T(0);
       }
       __syncthreads();
       const int i = tid / NBK, j = tid % NBK;
       const int gi = i0 + i, gj = j0 + j;
       if (i < PRW && gi < N && gj < N && gj <= gi) {
-        double s0 = 0.0, s1 = 0.0;
+        T s0 = T(0), s1 = T(0);
 #pragma unroll 8
         for (int c = 0; c < NBK; c += 2) {
           s0 += S.blk[i][c] * S.aux[j][c];
@@ -454,10 +465,10 @@ k_chol_coop(double* __restrict__ Lf, double* __restrict__ dinv, int* __restrict_
   for (int item = blockIdx.x; ok && item < B * nblk; item += G) {
     const int ccd = item / nblk, b = item % nblk, jb = b * NBK;
     __syncthreads();
-    load_block(S, Lf + ccd * NN, N, jb, min(NBK, N - jb), S.blk);
+    load_block(Lf + ccd * NN, N, jb, min(NBK, N - jb), S.blk);
     __syncthreads();
     invert_block(S);
-    double* out = dinv + ((int64_t)ccd * nblk + b) * NBK * NBK;
+    T* out = dinv + ((int64_t)ccd * nblk + b) * NBK * NBK;
     for (int e = tid; e < NBK * NBK; e += blockDim.x) out[e] = S.aux[e / NBK][e % NBK];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0 && ((volatile GridBar*)bar)->abort != 0u)
@@ -479,21 +490,26 @@ k_chol_coop(double* __restrict__ Lf, double* __restrict__ dinv, int* __restrict_
 // (bit 4) and the CTA stops.
 constexpr long long kUnset = -1ll;   // all bits set
 
+template <typename T>
 struct SolveSmem {
-  double iv[NBK][NBK + 1];
-  double v[NBK];
-  double part[NBK][9];
+  T iv[NBK][NBK + 1];
+  T v[NBK];
+  T part[NBK][9];
   int fail;
 };
 
 __device__ __forceinline__ double publishable(double v) {
   return isnan(v) ? __longlong_as_double(0x7FF8000000000000ll) : v;
 }
+__device__ __forceinline__ float publishable(float v) { return isnan(v) ? __int_as_float(0x7FC00000) : v; }
+__device__ __forceinline__ bool is_unset(double x) { return __double_as_longlong(x) == kUnset; }
+__device__ __forceinline__ bool is_unset(float x) { return __float_as_int(x) == -1; }
 
-__device__ __forceinline__ bool wait_value(const double* p, double& v) {
+template <typename T>
+__device__ __forceinline__ bool wait_value(const T* p, T& v) {
   for (int it = 0; it < kBarSpin; ++it) {
-    const double x = __ldcv(p);
-    if (__double_as_longlong(x) != kUnset) {
+    const T x = __ldcv(p);
+    if (!is_unset(x)) {
       v = x;
       return true;
     }
@@ -502,11 +518,12 @@ __device__ __forceinline__ bool wait_value(const double* p, double& v) {
   return false;
 }
 
+template <typename T>
 __global__ void __launch_bounds__(256)
-k_chol_solve(const double* __restrict__ Lf, const double* __restrict__ dinv, const double* __restrict__ scale,
-             const double* __restrict__ rhs, double* __restrict__ x, int N, int B, double* __restrict__ ybuf,
-             double* __restrict__ xbuf, int* __restrict__ status) {
-  __shared__ SolveSmem S;
+k_chol_solve(const T* __restrict__ Lf, const T* __restrict__ dinv, const double* __restrict__ scale,
+             const double* __restrict__ rhs, double* __restrict__ x, int N, int B, T* __restrict__ ybuf,
+             T* __restrict__ xbuf, int* __restrict__ status) {
+  __shared__ SolveSmem<T> S;
   const int nblk = (N + NBK - 1) / NBK;
   const int nitem = nblk * B, G = gridDim.x;
   const int tid = threadIdx.x, row = tid >> 3, part = tid & 7;
@@ -516,16 +533,16 @@ k_chol_solve(const double* __restrict__ Lf, const double* __restrict__ dinv, con
   // forward
   for (int o = blockIdx.x; alive && o < nitem; o += G) {
     const int b = o / B, ccd = o % B, jb = b * NBK, nb = min(NBK, N - jb);
-    const double* l = Lf + (int64_t)ccd * N * N;
-    const double* iv = dinv + ((int64_t)ccd * nblk + b) * NBK * NBK;
+    const T* l = Lf + (int64_t)ccd * N * N;
+    const T* iv = dinv + ((int64_t)ccd * nblk + b) * NBK * NBK;
     for (int e = tid; e < NBK * NBK; e += blockDim.x) S.iv[e / NBK][e % NBK] = iv[e];
-    double acc = 0.0;   // thread (row, part): columns part + 8 m of every block j < b
+    T acc = T(0);   // thread (row, part): columns part + 8 m of every block j < b
     for (int j = 0; j < b && waited; ++j) {
-      double lv[NBK / 8], yv[NBK / 8];
-      const double* lr = l + (int64_t)(jb + min(row, nb - 1)) * N + j * NBK + part;
+      T lv[NBK / 8], yv[NBK / 8];
+      const T* lr = l + (int64_t)(jb + min(row, nb - 1)) * N + j * NBK + part;
 #pragma unroll
       for (int m = 0; m < NBK / 8; ++m) lv[m] = __ldcg(lr + 8 * m);
-      const double* y = ybuf + (int64_t)ccd * N + j * NBK + part;
+      const T* y = ybuf + (int64_t)ccd * N + j * NBK + part;
 #pragma unroll
       for (int m = 0; m < NBK / 8; ++m) waited = waited && wait_value(y + 8 * m, yv[m]);
       if (waited && row < nb)
@@ -537,14 +554,14 @@ k_chol_solve(const double* __restrict__ Lf, const double* __restrict__ dinv, con
     __syncthreads();
     if (S.fail) { alive = false; break; }
     if (tid < NBK) {
-      double s = 0.0;
+      T s = T(0);
 #pragma unroll
       for (int p = 0; p < 8; ++p) s += S.part[tid][p];
-      S.v[tid] = tid < nb ? rhs[(int64_t)ccd * N + jb + tid] * scale[(int64_t)ccd * N + jb + tid] - s : 0.0;
+      S.v[tid] = tid < nb ? (T)(rhs[(int64_t)ccd * N + jb + tid] * scale[(int64_t)ccd * N + jb + tid]) - s : T(0);
     }
     __syncthreads();
     if (tid < nb) {
-      double s0 = 0.0, s1 = 0.0;
+      T s0 = T(0), s1 = T(0);
 #pragma unroll
       for (int t = 0; t < NBK; t += 2) {
         s0 += S.iv[tid][t] * S.v[t];
@@ -558,23 +575,23 @@ k_chol_solve(const double* __restrict__ Lf, const double* __restrict__ dinv, con
   const int last = (alive && (int)blockIdx.x < nitem) ? (nitem - 1 - (int)blockIdx.x) / G * G + (int)blockIdx.x : -1;
   for (int o = last; alive && o >= 0; o -= G) {
     const int b = o / B, ccd = o % B, jb = b * NBK, nb = min(NBK, N - jb);
-    const double* l = Lf + (int64_t)ccd * N * N;
-    const double* iv = dinv + ((int64_t)ccd * nblk + b) * NBK * NBK;
+    const T* l = Lf + (int64_t)ccd * N * N;
+    const T* iv = dinv + ((int64_t)ccd * nblk + b) * NBK * NBK;
     for (int e = tid; e < NBK * NBK; e += blockDim.x) S.iv[e / NBK][e % NBK] = iv[e];
-    double acc = 0.0;   // thread (column row, part): rows part + 8 m of every block j > b
+    T acc = T(0);   // thread (column row, part): rows part + 8 m of every block j > b
     for (int j = nblk - 1; j > b && waited; --j) {
       const int nj = min(NBK, N - j * NBK);
-      double lv[NBK / 8], xv[NBK / 8];
+      T lv[NBK / 8], xv[NBK / 8];
 #pragma unroll
       for (int m = 0; m < NBK / 8; ++m) {
         const int r = min(part + 8 * m, nj - 1);
         lv[m] = __ldcg(l + (int64_t)(j * NBK + r) * N + jb + min(row, nb - 1));
       }
-      const double* xs = xbuf + (int64_t)ccd * N + j * NBK;
+      const T* xs = xbuf + (int64_t)ccd * N + j * NBK;
 #pragma unroll
       for (int m = 0; m < NBK / 8; ++m) {
         const int r = part + 8 * m;
-        xv[m] = 0.0;
+        xv[m] = T(0);
         if (r < nj) waited = waited && wait_value(xs + r, xv[m]);
       }
       if (waited && row < nb)
@@ -587,22 +604,22 @@ k_chol_solve(const double* __restrict__ Lf, const double* __restrict__ dinv, con
     __syncthreads();
     if (S.fail) { alive = false; break; }
     if (tid < NBK) {
-      double s = 0.0;
+      T s = T(0);
 #pragma unroll
       for (int p = 0; p < 8; ++p) s += S.part[tid][p];
-      S.v[tid] = tid < nb ? __ldcg(ybuf + (int64_t)ccd * N + jb + tid) - s : 0.0;
+      S.v[tid] = tid < nb ? __ldcg(ybuf + (int64_t)ccd * N + jb + tid) - s : T(0);
     }
     __syncthreads();
     if (tid < nb) {
-      double s0 = 0.0, s1 = 0.0;
+      T s0 = T(0), s1 = T(0);
 #pragma unroll
       for (int t = 0; t < NBK; t += 2) {
         s0 += S.iv[t][tid] * S.v[t];
         s1 += S.iv[t + 1][tid] * S.v[t + 1];
       }
-      const double z = s0 + s1;
+      const T z = s0 + s1;
       xbuf[(int64_t)ccd * N + jb + tid] = publishable(z);
-      const double v = z * scale[(int64_t)ccd * N + jb + tid];
+      const double v = (double)z * scale[(int64_t)ccd * N + jb + tid];
       if (!isfinite(v)) atomicOr(&status[ccd], 2);
       x[(int64_t)ccd * N + jb + tid] = v;
     }
@@ -726,46 +743,91 @@ static cudaError_t launch_coop(const void* fn, int grid, cudaStream_t s, void** 
   return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
-cudaError_t launch_cholesky(const sfft_plan_s* p, const double* A, void* ws) {
+// The FP64 path factors and substitutes in FP64.  The mixed path factors the
+// Jacobi-scaled matrix in FP32 (its condition number is a few hundred on the
+// DECam-shaped pairs, so the FP32 factor's relative error on theta is about
+// 5e-6) and every solution it enters is refined against the FP64 system: by
+// the image-space refinement steps, whose right-hand side is the projection
+// of the residual image (b - A theta), or, without them, by one normal-
+// equations residual step (launch_residual).
+template <typename T>
+static cudaError_t cholesky_T(const sfft_plan_s* p, const double* A, void* ws) {
   int N = p->Nsol, B = p->d.batch;
-  double* Lf = ws_at<double>(ws, p->lfac);
+  T* Lf = ws_at<T>(ws, p->lfac);
   double* scale = ws_at<double>(ws, p->scale);
   int* status = ws_at<int>(ws, p->status);
-  double* dinv = ws_at<double>(ws, p->dinv);
+  T* dinv = ws_at<T>(ws, p->dinv);
   GridBar* bar = ws_at<GridBar>(ws, p->gbar);
   dim3 gi(64, B);
-  k_chol_init<<<gi, 256, 0, p->stream>>>(A, Lf, scale, status, p->N, N, cpr_map(p));
+  k_chol_init<T><<<gi, 256, 0, p->stream>>>(A, Lf, scale, status, p->N, N, cpr_map(p));
   cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBar), p->stream);
   if (e != cudaSuccess) return e;
   // every CTA of the cooperative grid must be resident at once
   const int T0 = (N - NBK + NBK - 1) / NBK;
   const int want = std::max(B, B + B * std::max(T0 * (T0 + 1) / 2 - 1, 1) * (NBK / PRW));
-  const int grid = coop_grid((const void*)k_chol_coop, want, B);
+  const int grid = coop_grid((const void*)k_chol_coop<T>, want, B);
   int spin = p->bar_spin_limit;
   void* args[] = {&Lf, &dinv, &status, &N, &B, &bar, &spin};
-  e = launch_coop((const void*)k_chol_coop, grid, p->stream, args);
+  e = launch_coop((const void*)k_chol_coop<T>, grid, p->stream, args);
   p->nlaunch += 2;
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
-cudaError_t launch_chol_solve(const sfft_plan_s* p, const double* rhs, double* x, void* ws) {
+cudaError_t launch_cholesky(const sfft_plan_s* p, const double* A, void* ws) {
+  return p->fp64 ? cholesky_T<double>(p, A, ws) : cholesky_T<float>(p, A, ws);
+}
+
+template <typename T>
+static cudaError_t chol_solve_T(const sfft_plan_s* p, const double* rhs, double* x, void* ws) {
   int N = p->Nsol, B = p->d.batch;
   const int nitem = ((N + NBK - 1) / NBK) * B;
-  double* Lf = ws_at<double>(ws, p->lfac);
-  double* dinv = ws_at<double>(ws, p->dinv);
+  T* Lf = ws_at<T>(ws, p->lfac);
+  T* dinv = ws_at<T>(ws, p->dinv);
   double* scale = ws_at<double>(ws, p->scale);
-  double* ybuf = ws_at<double>(ws, p->swave);
-  double* xbuf = ybuf + (size_t)p->N * B;
+  T* ybuf = ws_at<T>(ws, p->swave);
+  T* xbuf = ybuf + (size_t)p->N * B;
   int* status = ws_at<int>(ws, p->status);
   // y and x start unset (all bits one)
-  cudaError_t e = cudaMemsetAsync(ybuf, 0xFF, sizeof(double) * 2 * (size_t)p->N * B, p->stream);
+  cudaError_t e = cudaMemsetAsync(ybuf, 0xFF, sizeof(T) * 2 * (size_t)p->N * B, p->stream);
   if (e != cudaSuccess) return e;
-  const int grid = coop_grid((const void*)k_chol_solve, nitem, B);
+  const int grid = coop_grid((const void*)k_chol_solve<T>, nitem, B);
   void* args[] = {&Lf, &dinv, &scale, &rhs, &x, &N, &B, &ybuf, &xbuf, &status};
-  e = launch_coop((const void*)k_chol_solve, grid, p->stream, args);
+  e = launch_coop((const void*)k_chol_solve<T>, grid, p->stream, args);
   p->nlaunch += 1;
   if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_solve(const sfft_plan_s* p, const double* rhs, double* x, void* ws) {
+  return p->fp64 ? chol_solve_T<double>(p, rhs, x, ws) : chol_solve_T<float>(p, rhs, x, ws);
+}
+
+// r = b - A theta for every CCD (FP64; A full, N x N row-major): a warp per row
+__global__ void __launch_bounds__(256)
+k_residual(const double* __restrict__ A, const double* __restrict__ b, const double* __restrict__ theta,
+           double* __restrict__ r, int N) {
+  const int ccd = blockIdx.y, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= N) return;   // whole warps
+  const double* a = A + ((int64_t)ccd * N + row) * N;
+  const double* t = theta + (int64_t)ccd * N;
+  double s0 = 0.0, s1 = 0.0;
+  int c = lane;
+  for (; c + 32 < N; c += 64) {
+    s0 += a[c] * t[c];
+    s1 += a[c + 32] * t[c + 32];
+  }
+  if (c < N) s0 += a[c] * t[c];
+  const double s = warp_sum(s0 + s1);
+  if (lane == 0) r[(int64_t)ccd * N + row] = b[(int64_t)ccd * N + row] - s;
+}
+
+cudaError_t launch_residual(const sfft_plan_s* p, const double* A, const double* b, const double* theta_off,
+                            double* r) {
+  dim3 grid((p->N + 7) / 8, p->d.batch);
+  k_residual<<<grid, 256, 0, p->stream>>>(A, b, theta_off, r, p->N);
+  p->nlaunch += 1;
   return cudaGetLastError();
 }
 

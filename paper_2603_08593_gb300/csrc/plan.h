@@ -147,6 +147,8 @@ cudaError_t launch_contract_slot0(const sfft_plan_s* p, int DM, int job0, int nj
 cudaError_t launch_scatter(const sfft_plan_s* p, double* A, double* b, void* ws, bool rhs_only, double* rhs_out);
 cudaError_t launch_cholesky(const sfft_plan_s* p, const double* A, void* ws);
 cudaError_t launch_chol_solve(const sfft_plan_s* p, const double* rhs, double* x, void* ws);
+cudaError_t launch_residual(const sfft_plan_s* p, const double* A, const double* b, const double* theta_off,
+                            double* r);
 cudaError_t launch_theta_finish(const sfft_plan_s* p, const double* x, double* theta_off, bool add);
 cudaError_t launch_cpr_rhs(const sfft_plan_s* p, const double* b, double* out);
 cudaError_t launch_cpr_expand(const sfft_plan_s* p, const double* x, double* theta_off, bool add);
