@@ -211,6 +211,67 @@ k_rfft_prod_dy(const T* __restrict__ Rm, int H, int W, int L, int d0, int nd, c_
 // d_x values of the group in turns.
 constexpr int kWarpRowsPerCta = 4;
 
+// The rest of a 2048-sample real row transform for one warp: v[q] holds the
+// packed samples z[lane + 32 q]; the spectrum X[k], k = 0 .. 1023 (slot 0: the
+// two real bins), goes to o[k], or with BLK to o[(k / 16) 16 H + k % 16].
+template <bool BLK>
+__device__ __forceinline__ void warp_rfft2048_finish(float2 (&v)[32], float2* tile, const float2 (&tB)[8],
+                                                     const float2 (&tA)[4], float2 tn, float2* __restrict__ o,
+                                                     int H) {
+  constexpr int M = 1024, SROW = 33;
+  const int lane = threadIdx.x & 31;
+  fft_reg<32>(v);   // over q: v[a]
+#pragma unroll
+  for (int a = 1; a < 32; ++a) {
+    float2 w = tB[a & 7];
+    if ((a >> 3) != 0) w = (a & 7) ? cmul(w, tA[a >> 3]) : tA[a >> 3];
+    v[a] = cmul(v[a], w);
+  }
+#pragma unroll
+  for (int a = 0; a < 32; ++a) tile[lane * SROW + a] = v[a];
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = tile[j * SROW + lane];
+  __syncwarp();
+  fft_reg<32>(v);   // over l: v[b] = X[lane + 32 b]
+#pragma unroll
+  for (int b = 0; b < 32; ++b) tile[lane + 32 * b] = v[b];
+  __syncwarp();
+#pragma unroll
+  for (int b = 0; b < 32; ++b) {
+    const int k = lane + 32 * b;
+    const float2 zk = v[b], zm = tile[(M - k) & (M - 1)];
+    float2 X;
+    if (k == 0) {
+      X.x = zk.x + zk.y;
+      X.y = zk.x - zk.y;
+    } else {
+      const float er = 0.5f * (zk.x + zm.x), ei = 0.5f * (zk.y - zm.y);
+      const float orr = 0.5f * (zk.x - zm.x), oi = 0.5f * (zk.y + zm.y);
+      const float2 wk = twiddle_mul(tn, b, 64);   // exp(-2 pi i (lane + 32 b) / NF)
+      const float wr = wk.x * orr - wk.y * oi, wi = wk.x * oi + wk.y * orr;
+      X.x = er + wi;
+      X.y = ei - wr;
+    }
+    if constexpr (BLK) o[(int64_t)(k >> 4) * (16 * H) + (k & 15)] = X;   // [k / 16][y][k % 16]
+    else o[k] = X;
+  }
+}
+
+// per-lane twiddles of the 2048-sample row transform: exp(-2 pi i l a / M) =
+// tB[a mod 8] tA[a / 8], and exp(-2 pi i l / NF)
+__device__ __forceinline__ void warp_rfft2048_twiddles(const float2* __restrict__ twM, const float2* __restrict__ twN,
+                                                       float2 (&tB)[8], float2 (&tA)[4], float2& tn) {
+  constexpr int M = 1024;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) tB[i] = twM[(lane * i) & (M - 1)];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) tA[j] = twM[(8 * lane * j) & (M - 1)];
+  tn = twN[lane];
+}
+
+
 template <bool BLK>
 __global__ void __launch_bounds__(256, 2)
 k_rfft_prod_dy_w(const float* __restrict__ Rm, int H, int W, int L, int d0, int nd, float2* __restrict__ out,
@@ -222,13 +283,8 @@ k_rfft_prod_dy_w(const float* __restrict__ Rm, int H, int W, int L, int d0, int 
   float* r2 = r1 + NF;                                         // [NF + 2 PADX]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float2* tile = reinterpret_cast<float2*>(r2 + NF + 2 * PADX) + warp * 32 * SROW;
-  // per-lane twiddles: exp(-2 pi i l a / M) = tB[a mod 8] tA[a / 8]; exp(-2 pi i l / NF)
-  float2 tB[8], tA[4];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) tB[i] = twM[(lane * i) & (M - 1)];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) tA[j] = twM[(8 * lane * j) & (M - 1)];
-  const float2 tn = twN[lane];
+  float2 tB[8], tA[4], tn;
+  warp_rfft2048_twiddles(twM, twN, tB, tA, tn);
   const int ccd = blockIdx.z;
   auto first_of = [L](int dy) { return dy == 0 ? 0 : L + (2 * L - 1) * (dy - 1); };
   auto dy_of = [L](int id) { return id < L ? 0 : 1 + (id - L) / (2 * L - 1); };
@@ -260,43 +316,7 @@ k_rfft_prod_dy_w(const float* __restrict__ Rm, int H, int W, int L, int d0, int 
         v[q].x = a.x * r2[x0 + dx + PADX];
         v[q].y = a.y * r2[x0 + 1 + dx + PADX];
       }
-      fft_reg<32>(v);   // over q: v[a]
-#pragma unroll
-      for (int a = 1; a < 32; ++a) {
-        float2 w = tB[a & 7];
-        if ((a >> 3) != 0) w = (a & 7) ? cmul(w, tA[a >> 3]) : tA[a >> 3];
-        v[a] = cmul(v[a], w);
-      }
-#pragma unroll
-      for (int a = 0; a < 32; ++a) tile[lane * SROW + a] = v[a];
-      __syncwarp();
-#pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = tile[j * SROW + lane];
-      __syncwarp();
-      fft_reg<32>(v);   // over l: v[b] = X[lane + 32 b]
-#pragma unroll
-      for (int b = 0; b < 32; ++b) tile[lane + 32 * b] = v[b];
-      __syncwarp();
-      float2* o = orow + (int64_t)(id - d0) * slab_stride;
-#pragma unroll
-      for (int b = 0; b < 32; ++b) {
-        const int k = lane + 32 * b;
-        const float2 zk = v[b], zm = tile[(M - k) & (M - 1)];
-        float2 X;
-        if (k == 0) {
-          X.x = zk.x + zk.y;
-          X.y = zk.x - zk.y;
-        } else {
-          const float er = 0.5f * (zk.x + zm.x), ei = 0.5f * (zk.y - zm.y);
-          const float orr = 0.5f * (zk.x - zm.x), oi = 0.5f * (zk.y + zm.y);
-          const float2 wk = twiddle_mul(tn, b, 64);   // exp(-2 pi i (lane + 32 b) / NF)
-          const float wr = wk.x * orr - wk.y * oi, wi = wk.x * oi + wk.y * orr;
-          X.x = er + wi;
-          X.y = ei - wr;
-        }
-        if constexpr (BLK) o[(int64_t)(k >> 4) * (16 * H) + (k & 15)] = X;   // [k / 16][y][k % 16]
-        else o[k] = X;
-      }
+      warp_rfft2048_finish<BLK>(v, tile, tB, tA, tn, orow + (int64_t)(id - d0) * slab_stride, H);
       __syncwarp();
     }
   }
@@ -343,6 +363,56 @@ k_rfft_weight(const uint8_t* __restrict__ Mfit, const float* __restrict__ S, con
       v[r].y = vv[1];
     }
     F::run(v, buf, t, valid, twM, twN, obase + (int64_t)(valid ? y : 0) * M);
+  }
+}
+
+// FP32 weight spectra of 2048-sample rows (M = 1024) with the transform of
+// k_rfft_prod_dy_w.  A CTA walks kWarpRowsPerCta rows; per row it stages the
+// samples f(x) xt^a, f(x) = M_fit(x) [ (S(x) - s_S) | e(x) | 1 ], of all
+// na <= kMaxWeightDeg + 1 spectra in shared memory (coalesced loads, the
+// powers formed in the order of k_rfft_weight), then warp w transforms
+// spectrum a0 + w.
+constexpr int kWeightsMax = kMaxWeightDeg + 1;
+
+__global__ void __launch_bounds__(256, 2)
+k_rfft_weight_w(const uint8_t* __restrict__ Mfit, const float* __restrict__ S, const double* __restrict__ sky,
+                const float* __restrict__ E, int H, int W, int a0, int na, float2* __restrict__ out,
+                int64_t slab_stride, int64_t ccd_stride_out, const float2* __restrict__ twM,
+                const float2* __restrict__ twN) {
+  constexpr int M = 1024, NF = 2048, SROW = 33;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* g = reinterpret_cast<float*>(smem_raw);                                          // [na][NF]
+  float2* tile = reinterpret_cast<float2*>(g + kWeightsMax * NF) + (threadIdx.x >> 5) * 32 * SROW;   // per warp
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, ccd = blockIdx.z;
+  float2 tB[8], tA[4], tn;
+  warp_rfft2048_twiddles(twM, twN, tB, tA, tn);
+  const float sS = S ? (float)sky[2 * ccd + 1] : 0.f;
+  const float xs = 2.f / (float)(W > 1 ? W - 1 : 1);
+  for (int yy = 0; yy < kWarpRowsPerCta; ++yy) {
+    const int y = blockIdx.x * kWarpRowsPerCta + yy;
+    if (y >= H) break;   // uniform
+    __syncthreads();     // the previous row's samples are transformed
+    const int64_t roff = (int64_t)ccd * H * W + (int64_t)y * W;
+    for (int x = threadIdx.x; x < NF; x += blockDim.x) {
+      float fv = 0.f;
+      if (x < W && Mfit[roff + x]) fv = S ? S[roff + x] - sS : (E ? E[roff + x] : 1.f);
+      const float xt = (float)x * xs - 1.f;
+      float pw = 1.f;   // xt^(a0 + i) as repeated products from 1, then times f
+      for (int i = 0; i < a0; ++i) pw *= xt;
+      for (int i = 0; i < na; ++i) {
+        g[i * NF + x] = pw * fv;
+        pw *= xt;
+      }
+    }
+    __syncthreads();
+    if (warp < na) {
+      const float* gw = g + warp * NF;
+      float2 v[32];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) v[q] = *reinterpret_cast<const float2*>(gw + 2 * (lane + 32 * q));
+      float2* o = out + (int64_t)ccd * ccd_stride_out + (int64_t)warp * slab_stride + (int64_t)y * M;
+      warp_rfft2048_finish<false>(v, tile, tB, tA, tn, o, H);
+    }
   }
 }
 
@@ -448,6 +518,18 @@ static cudaError_t weights_T(const sfft_plan_s* p, const float* S, const void* e
   const int64_t HM = (int64_t)p->d.H * p->M;
   const uint8_t* Mfit = ws_at<uint8_t>(ws, p->mfit);
   const double* sky = ws_at<double>(ws, p->sky);
+  if constexpr (sizeof(T) == 4) {
+    if (p->M == 1024 && na <= kWeightsMax) {   // 2048-sample rows: the warp-per-row transform
+      const size_t smem = sizeof(float) * kWeightsMax * 2048 + sizeof(float2) * 8 * 32 * 33;
+      cudaFuncSetAttribute(k_rfft_weight_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      dim3 grid((p->d.H + kWarpRowsPerCta - 1) / kWarpRowsPerCta, 1, p->d.batch);
+      k_rfft_weight_w<<<grid, 256, smem, p->stream>>>(Mfit, S, sky, (const float*)eimg, p->d.H, p->d.W, a0, na,
+                                                     (float2*)out + a0 * HM, HM, HM * nslab, (const float2*)p->twM,
+                                                     (const float2*)p->twN);
+      p->nlaunch += 1;
+      return cudaGetLastError();
+    }
+  }
   SFFT_DISPATCH_M(p->M, (run_weight<T, M>(p, Mfit, S, sky, (const T*)eimg, a0, na, (c_t<T>*)out + a0 * HM, HM,
                                           HM * nslab)))
 }

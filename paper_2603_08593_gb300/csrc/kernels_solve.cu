@@ -720,13 +720,15 @@ static CprMap cpr_map(const sfft_plan_s* p) {
 // Cooperative grid size: one CTA per SM for a few CCDs (the FP64 pipe of an
 // SM is shared by its CTAs, and a smaller grid makes the grid-wide barriers
 // cheaper); for a batch of 8 or more, as many as fit, to hide load latency.
-static int coop_grid(const void* fn, int want, int batch) {
+// CTAs of a cooperative grid: at most `want`, all co-resident; one per SM
+// for a small batch (`single` per SM, when they fit), as many as fit for 8+ CCDs
+static int coop_grid(const void* fn, int want, int batch, int single = 1) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
   if (per_sm < 1) return 1;
-  return std::max(1, std::min(want, sms * (batch >= 8 ? per_sm : 1)));
+  return std::max(1, std::min(want, sms * (batch >= 8 ? per_sm : std::min(per_sm, single))));
 }
 
 static cudaError_t launch_coop(const void* fn, int grid, cudaStream_t s, void** args) {
@@ -758,14 +760,16 @@ static cudaError_t cholesky_T(const sfft_plan_s* p, const double* A, void* ws) {
   int* status = ws_at<int>(ws, p->status);
   T* dinv = ws_at<T>(ws, p->dinv);
   GridBar* bar = ws_at<GridBar>(ws, p->gbar);
-  dim3 gi(64, B);
+  dim3 gi(512, B);
   k_chol_init<T><<<gi, 256, 0, p->stream>>>(A, Lf, scale, status, p->N, N, cpr_map(p));
   cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBar), p->stream);
   if (e != cudaSuccess) return e;
   // every CTA of the cooperative grid must be resident at once
   const int T0 = (N - NBK + NBK - 1) / NBK;
   const int want = std::max(B, B + B * std::max(T0 * (T0 + 1) / 2 - 1, 1) * (NBK / PRW));
-  const int grid = coop_grid((const void*)k_chol_coop<T>, want, B);
+  // FP32: two CTAs per SM shorten each block step's pieces (0.65 against 0.69 ms
+  // for the solve phase; one per SM stays better for the FP64 pipe)
+  const int grid = coop_grid((const void*)k_chol_coop<T>, want, B, sizeof(T) == 4 ? 2 : 1);
   int spin = p->bar_spin_limit;
   void* args[] = {&Lf, &dinv, &status, &N, &B, &bar, &spin};
   e = launch_coop((const void*)k_chol_coop<T>, grid, p->stream, args);
