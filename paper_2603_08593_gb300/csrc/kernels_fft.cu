@@ -214,19 +214,39 @@ constexpr int kWarpRowsPerCta = 4;
 // The rest of a 2048-sample real row transform for one warp: v[q] holds the
 // packed samples z[lane + 32 q]; the spectrum X[k], k = 0 .. 1023 (slot 0: the
 // two real bins), goes to o[k], or with BLK to o[(k / 16) 16 H + k % 16].
-template <bool BLK>
-__device__ __forceinline__ void warp_rfft2048_finish(float2 (&v)[32], float2* tile, const float2 (&tB)[8],
-                                                     const float2 (&tA)[4], float2 tn, float2* __restrict__ o,
-                                                     int H) {
+// Twiddles of the 2048-sample row transform for lane l: mid(a) =
+// exp(-2 pi i l a / 1024) between the two 32-point passes, split(b) =
+// exp(-2 pi i (l + 32 b) / 2048) for the real-input split, formed from 13
+// per-lane values (mid(a) = tB[a mod 8] tA[a / 8]).  (Read from a table in
+// shared memory instead they measured slower: 2.60 against 2.49 ms for the
+// product FFTs of the DECam pair.)
+struct TwReg {
+  float2 tB[8], tA[4], tn;
+  __device__ __forceinline__ void load(const float2* __restrict__ twM, const float2* __restrict__ twN) {
+    constexpr int M = 1024;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) tB[i] = twM[(lane * i) & (M - 1)];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) tA[j] = twM[(8 * lane * j) & (M - 1)];
+    tn = twN[lane];
+  }
+  __device__ __forceinline__ float2 mid(int a) const {
+    float2 w = tB[a & 7];
+    if ((a >> 3) != 0) w = (a & 7) ? cmul(w, tA[a >> 3]) : tA[a >> 3];
+    return w;
+  }
+  __device__ __forceinline__ float2 split(int b) const { return twiddle_mul(tn, b, 64); }
+};
+
+template <bool BLK, typename TW>
+__device__ __forceinline__ void warp_rfft2048_finish(float2 (&v)[32], float2* tile, const TW& tw,
+                                                     float2* __restrict__ o, int H) {
   constexpr int M = 1024, SROW = 33;
   const int lane = threadIdx.x & 31;
   fft_reg<32>(v);   // over q: v[a]
 #pragma unroll
-  for (int a = 1; a < 32; ++a) {
-    float2 w = tB[a & 7];
-    if ((a >> 3) != 0) w = (a & 7) ? cmul(w, tA[a >> 3]) : tA[a >> 3];
-    v[a] = cmul(v[a], w);
-  }
+  for (int a = 1; a < 32; ++a) v[a] = cmul(v[a], tw.mid(a));
 #pragma unroll
   for (int a = 0; a < 32; ++a) tile[lane * SROW + a] = v[a];
   __syncwarp();
@@ -237,39 +257,37 @@ __device__ __forceinline__ void warp_rfft2048_finish(float2 (&v)[32], float2* ti
 #pragma unroll
   for (int b = 0; b < 32; ++b) tile[lane + 32 * b] = v[b];
   __syncwarp();
-#pragma unroll
-  for (int b = 0; b < 32; ++b) {
-    const int k = lane + 32 * b;
-    const float2 zk = v[b], zm = tile[(M - k) & (M - 1)];
-    float2 X;
-    if (k == 0) {
-      X.x = zk.x + zk.y;
-      X.y = zk.x - zk.y;
-    } else {
-      const float er = 0.5f * (zk.x + zm.x), ei = 0.5f * (zk.y - zm.y);
-      const float orr = 0.5f * (zk.x - zm.x), oi = 0.5f * (zk.y + zm.y);
-      const float2 wk = twiddle_mul(tn, b, 64);   // exp(-2 pi i (lane + 32 b) / NF)
-      const float wr = wk.x * orr - wk.y * oi, wi = wk.x * oi + wk.y * orr;
-      X.x = er + wi;
-      X.y = ei - wr;
-    }
+  // the real-input split in pairs (k, M - k): lane l takes k = l + 32 b,
+  // b < 16, and M - k (lane 32 - l's upper half; lanes 0 and 16 pair with
+  // themselves), so both outputs share the sums, the differences and the
+  // twiddle w_k (w_{M-k} = -conj(w_k)); lane 0 also takes k = M / 2
+  auto put = [&](int k, float2 X) {
     if constexpr (BLK) o[(int64_t)(k >> 4) * (16 * H) + (k & 15)] = X;   // [k / 16][y][k % 16]
     else o[k] = X;
+  };
+#pragma unroll
+  for (int b = 0; b < 16; ++b) {
+    const int k = lane + 32 * b;
+    const float2 zk = v[b], zm = tile[(M - k) & (M - 1)];
+    const float er = 0.5f * (zk.x + zm.x), ei = 0.5f * (zk.y - zm.y);
+    const float orr = 0.5f * (zk.x - zm.x), oi = 0.5f * (zk.y + zm.y);
+    const float2 wk = tw.split(b);   // exp(-2 pi i (lane + 32 b) / NF)
+    const float wr = wk.x * orr - wk.y * oi, wi = wk.x * oi + wk.y * orr;
+    if (b == 0 && lane == 0) {
+      put(0, make_float2(zk.x + zk.y, zk.x - zk.y));   // slot 0: the two real bins
+    } else {
+      put(k, make_float2(er + wi, ei - wr));
+      put(M - k, make_float2(er - wi, -ei - wr));
+    }
+  }
+  if (lane == 0) {   // k = M / 2 pairs with itself
+    const float2 z = v[16];
+    const float2 wk = tw.split(16);
+    const float wr = -wk.y * z.y, wi = wk.x * z.y;   // orr = 0, oi = z.y
+    put(M / 2, make_float2(z.x + wi, -wr));
   }
 }
 
-// per-lane twiddles of the 2048-sample row transform: exp(-2 pi i l a / M) =
-// tB[a mod 8] tA[a / 8], and exp(-2 pi i l / NF)
-__device__ __forceinline__ void warp_rfft2048_twiddles(const float2* __restrict__ twM, const float2* __restrict__ twN,
-                                                       float2 (&tB)[8], float2 (&tA)[4], float2& tn) {
-  constexpr int M = 1024;
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) tB[i] = twM[(lane * i) & (M - 1)];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) tA[j] = twM[(8 * lane * j) & (M - 1)];
-  tn = twN[lane];
-}
 
 
 template <bool BLK>
@@ -283,8 +301,8 @@ k_rfft_prod_dy_w(const float* __restrict__ Rm, int H, int W, int L, int d0, int 
   float* r2 = r1 + NF;                                         // [NF + 2 PADX]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float2* tile = reinterpret_cast<float2*>(r2 + NF + 2 * PADX) + warp * 32 * SROW;
-  float2 tB[8], tA[4], tn;
-  warp_rfft2048_twiddles(twM, twN, tB, tA, tn);
+  TwReg tw;
+  tw.load(twM, twN);
   const int ccd = blockIdx.z;
   auto first_of = [L](int dy) { return dy == 0 ? 0 : L + (2 * L - 1) * (dy - 1); };
   auto dy_of = [L](int id) { return id < L ? 0 : 1 + (id - L) / (2 * L - 1); };
@@ -316,7 +334,7 @@ k_rfft_prod_dy_w(const float* __restrict__ Rm, int H, int W, int L, int d0, int 
         v[q].x = a.x * r2[x0 + dx + PADX];
         v[q].y = a.y * r2[x0 + 1 + dx + PADX];
       }
-      warp_rfft2048_finish<BLK>(v, tile, tB, tA, tn, orow + (int64_t)(id - d0) * slab_stride, H);
+      warp_rfft2048_finish<BLK>(v, tile, tw, orow + (int64_t)(id - d0) * slab_stride, H);
       __syncwarp();
     }
   }
@@ -384,8 +402,8 @@ k_rfft_weight_w(const uint8_t* __restrict__ Mfit, const float* __restrict__ S, c
   float* g = reinterpret_cast<float*>(smem_raw);                                          // [na][NF]
   float2* tile = reinterpret_cast<float2*>(g + kWeightsMax * NF) + (threadIdx.x >> 5) * 32 * SROW;   // per warp
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, ccd = blockIdx.z;
-  float2 tB[8], tA[4], tn;
-  warp_rfft2048_twiddles(twM, twN, tB, tA, tn);
+  TwReg tw;
+  tw.load(twM, twN);
   const float sS = S ? (float)sky[2 * ccd + 1] : 0.f;
   const float xs = 2.f / (float)(W > 1 ? W - 1 : 1);
   for (int yy = 0; yy < kWarpRowsPerCta; ++yy) {
@@ -411,7 +429,7 @@ k_rfft_weight_w(const uint8_t* __restrict__ Mfit, const float* __restrict__ S, c
 #pragma unroll
       for (int q = 0; q < 32; ++q) v[q] = *reinterpret_cast<const float2*>(gw + 2 * (lane + 32 * q));
       float2* o = out + (int64_t)ccd * ccd_stride_out + (int64_t)warp * slab_stride + (int64_t)y * M;
-      warp_rfft2048_finish<false>(v, tile, tB, tA, tn, o, H);
+      warp_rfft2048_finish<false>(v, tile, tw, o, H);
     }
   }
 }
