@@ -201,7 +201,7 @@ cudaError_t backward(rb_model_s* m, int n, const float* labels, float* loss_dev,
   cudaError_t e;
   cudaMemsetAsync(G, 0, sizeof(float) * NMASTER, s);
   k_bce_head<<<1, 1024, 0, s>>>(m->logit, labels, n, m->z4, m->params + OW5, m->dz5, m->dz4, loss_dev);
-  k_fc2_grad<<<1, F4, 0, s>>>(m->dz5, m->z4, n, G + OW5, G + OB5);
+  k_fc2_grad<<<F4 / 8, 256, 0, s>>>(m->dz5, m->z4, n, G + OW5, G + OB5);
   // fc1: dW4[k][co] = sum_i a3[i][k] dz4[i][co], db4 = colsum(dz4), da3 = dz4 W4^T
   if ((e = igemm_wgrad(s, F4, K4, n, Dense{m->dz4, n, F4, F4}, Dense{m->a3, n, K4, K4}, G + OW4, m->part))) return e;
   if ((e = colsum(s, m->dz4, n, F4, m->part, G + OB4))) return e;
@@ -209,7 +209,7 @@ cudaError_t backward(rb_model_s* m, int n, const float* labels, float* loss_dev,
                                      nullptr)))
     return e;
   // conv3
-  k_pool_relu_back<<<grid1((int64_t)n * PIX3 * C3), 256, 0, s>>>(m->da, m->i3, m->z3, n, 7, 7, C3, m->dzb);
+  k_pool_relu_back<<<grid1((int64_t)n * PIX3 * C3 / 8), 256, 0, s>>>(m->da, m->i3, m->z3, n, 7, 7, C3, m->dzb);
   if ((e = igemm_wgrad(s, C3, K3, n * PIX3, Dense{m->dzb, n * PIX3, C3, C3}, ConvRows{m->a2, n, 7, 7, C2, 1},
                        G + OW3, m->part)))
     return e;
@@ -218,7 +218,7 @@ cudaError_t backward(rb_model_s* m, int n, const float* labels, float* loss_dev,
                                         ConvW{W + OW3, C2, C3}, m->da, C2, nullptr)))
     return e;
   // conv2
-  k_pool_relu_back<<<grid1((int64_t)n * PIX2 * C2), 256, 0, s>>>(m->da, m->i2, m->z2, n, 15, 15, C2, m->dzb);
+  k_pool_relu_back<<<grid1((int64_t)n * PIX2 * C2 / 8), 256, 0, s>>>(m->da, m->i2, m->z2, n, 15, 15, C2, m->dzb);
   if ((e = igemm_wgrad(s, C2, K2, n * PIX2, Dense{m->dzb, n * PIX2, C2, C2}, ConvRows{m->a1, n, 15, 15, C1, 1},
                        G + OW2, m->part)))
     return e;
@@ -227,7 +227,7 @@ cudaError_t backward(rb_model_s* m, int n, const float* labels, float* loss_dev,
                                         ConvW{W + OW2, C1, C2}, m->da, C1, nullptr)))
     return e;
   // conv1 (no input gradient)
-  k_pool_relu_back<<<grid1((int64_t)n * PIX1 * C1), 256, 0, s>>>(m->da, m->i1, m->z1, n, S31, S31, C1, m->dzb);
+  k_pool_relu_back<<<grid1((int64_t)n * PIX1 * C1 / 8), 256, 0, s>>>(m->da, m->i1, m->z1, n, S31, S31, C1, m->dzb);
   if ((e = igemm_wgrad(s, C1, K1, n * PIX1, Dense{m->dzb, n * PIX1, C1, C1},
                        Conv1Rows{m->xn, n, S31, S31, rbtc::kXnStride},
                        G + OW1, m->part)))

@@ -23,12 +23,24 @@ constexpr int K1 = 32, K2 = 9 * C1, K3 = 9 * C2, K4 = PIX4 * C3;   // GEMM K (co
 // ---------------------------------------------------------------- GEMM launchers
 constexpr int kMaxSplits = 64;
 
-__global__ void k_sum_splits(const float* __restrict__ part, int splits, int64_t mn, float* __restrict__ out) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < mn; e += (int64_t)gridDim.x * blockDim.x) {
+// out[e] = sum over z of part[z mn + e], one warp per element: lane l adds
+// slices l, l + 32, ... in order, then a fixed xor tree (deterministic)
+__global__ void __launch_bounds__(256)
+k_sum_splits(const float* __restrict__ part, int splits, int64_t mn, float* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t e = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); e < mn; e += nw) {
     float s = 0.f;
-    for (int z = 0; z < splits; ++z) s += part[z * mn + e];
-    out[e] = s;
+    for (int z = lane; z < splits; z += 32) s += part[z * mn + e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[e] = s;
   }
+}
+
+inline cudaError_t sum_splits(cudaStream_t s, const float* part, int splits, int64_t mn, float* out) {
+  k_sum_splits<<<(int)std::min<int64_t>((mn + 7) / 8, 4096), 256, 0, s>>>(part, splits, mn, out);
+  return cudaGetLastError();
 }
 
 // C = A B (+ bias): A K-major (rows = M), B outer-major (rows = K) or K-major (rows = N)
@@ -42,11 +54,14 @@ cudaError_t igemm(cudaStream_t s, int M, int N, int K, const LA& la, const LB& l
 
 // Weight gradient G[n][m] (ldc = M) = sum_k A[k][m] B[k][n] over a long k
 // (pixels or stamps): both operands outer-major, split over k into fixed
-// slices of `part` (kMaxSplits * M * N floats) summed in a fixed order.
+// slices of `part` (kMaxSplits * K4 * F4 floats, so up to that many / (M N)
+// slices) summed in a fixed order.  About four CTAs per SM: the small
+// products (conv1: M = N = 32 over 961 pixels a stamp) get many slices.
 template <class LA, class LB>
 cudaError_t igemm_wgrad(cudaStream_t s, int M, int N, int K, const LA& la, const LB& lb, float* G, float* part) {
   const int tiles = ((N + rbg::BN - 1) / rbg::BN) * ((M + rbg::BM - 1) / rbg::BM);
-  int splits = std::min({(K + 1023) / 1024, kMaxSplits, std::max(1, 2 * 152 / tiles)});
+  const int64_t cap = (int64_t)kMaxSplits * K4 * F4 / ((int64_t)M * N);
+  int splits = (int)std::min<int64_t>({(int64_t)(K + 255) / 256, cap, (int64_t)std::max(1, 4 * 152 / tiles)});
   splits = std::max(splits, 1);
   int kchunk = (K + splits - 1) / splits;
   kchunk = (kchunk + rbg::BK - 1) / rbg::BK * rbg::BK;
@@ -56,7 +71,7 @@ cudaError_t igemm_wgrad(cudaStream_t s, int M, int N, int K, const LA& la, const
   float* dst = splits == 1 ? G : part;
   rbg::k_igemm<LA, LB, false, false, true><<<grid, 256, 0, s>>>(M, N, K, kchunk, la, lb, dst, M, mn, nullptr);
   if (splits > 1)
-    k_sum_splits<<<(int)std::min<int64_t>((mn + 255) / 256, 1024), 256, 0, s>>>(part, splits, mn, G);
+    sum_splits(s, part, splits, mn, G);
   return cudaGetLastError();
 }
 
@@ -212,19 +227,35 @@ __global__ void k_relu_pool(const float* __restrict__ z, int n, int h, int w, in
 // pool + ReLU backward: dz[n][h][w][c] = (position == argmax) * da * (z > 0); bf16 output
 __global__ void k_pool_relu_back(const float* __restrict__ da, const uint8_t* __restrict__ idx,
                                  const float* __restrict__ z, int n, int h, int w, int c, bf16* __restrict__ dz) {
-  const int ho = h / 2, wo = w / 2;
-  const int64_t total = (int64_t)n * h * w * c;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int ci = (int)(e % c);
-    const int64_t p = e / c;
-    const int xx = (int)(p % w), yy = (int)((p / w) % h), nn = (int)(p / ((int64_t)w * h));
-    float v = 0.f;
-    const int yo = yy / 2, xo = xx / 2;
-    if (yo < ho && xo < wo && z[e] > 0.f) {
-      const int64_t pe = (((int64_t)nn * ho + yo) * wo + xo) * c + ci;
-      if (idx[pe] == (uint8_t)(((yy & 1) << 1) | (xx & 1))) v = da[pe];
+  // one thread per (pixel, 8 channels): 32-byte loads of z and da, 8 bytes of
+  // indices, a 16-byte store of dz (c is a multiple of 8)
+  const int ho = h / 2, wo = w / 2, c8 = c / 8;
+  const int64_t total = (int64_t)n * h * w * c8;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(t % c8);
+    const int64_t p = t / c8;
+    const int pix = (int)(p % ((int64_t)h * w)), nn = (int)(p / ((int64_t)h * w));
+    const int yy = pix / w, xx = pix - yy * w, yo = yy >> 1, xo = xx >> 1;
+    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (yo < ho && xo < wo) {
+      const int64_t e = p * c + 8 * q;
+      const float4 z0 = *reinterpret_cast<const float4*>(z + e), z1 = *reinterpret_cast<const float4*>(z + e + 4);
+      const int64_t pe = (((int64_t)nn * ho + yo) * wo + xo) * c + 8 * q;
+      const uint2 ix = *reinterpret_cast<const uint2*>(idx + pe);
+      const float4 d0 = *reinterpret_cast<const float4*>(da + pe), d1 = *reinterpret_cast<const float4*>(da + pe + 4);
+      const float zz[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+      const float dd[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+      const uint32_t pos = (uint32_t)(((yy & 1) << 1) | (xx & 1));
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const uint32_t ib = ((i < 4 ? ix.x : ix.y) >> (8 * (i & 3))) & 0xffu;
+        v[i] = (zz[i] > 0.f && ib == pos) ? dd[i] : 0.f;
+      }
     }
-    dz[e] = __float2bfloat16(v);
+    __align__(16) bf16 o[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) o[i] = __float2bfloat16(v[i]);
+    *reinterpret_cast<uint4*>(dz + p * c + 8 * q) = *reinterpret_cast<const uint4*>(o);
   }
 }
 
@@ -271,19 +302,28 @@ __global__ void k_bce_head(const float* __restrict__ logit, const float* __restr
   }
 }
 
-// dw5[j] = sum_i dz5[i] relu(z4[i][j]); db5 = sum dz5
-__global__ void k_fc2_grad(const float* __restrict__ dz5, const float* __restrict__ z4, int n, float* __restrict__ dw5,
-                           float* __restrict__ db5) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < F4) {
-    float s = 0.f;
-    for (int i = 0; i < n; ++i) s += dz5[i] * fmaxf(z4[(int64_t)i * F4 + j], 0.f);
-    dw5[j] = s;
+// dw5[j] = sum_i dz5[i] relu(z4[i][j]), db5 = sum_i dz5[i]: one warp per j
+// (lane l adds samples l, l + 32, ... in order, then a fixed xor tree); the
+// warp of j = 0 also forms db5.  Launch F4 / 8 CTAs of 256 threads.
+__global__ void __launch_bounds__(256)
+k_fc2_grad(const float* __restrict__ dz5, const float* __restrict__ z4, int n, float* __restrict__ dw5,
+           float* __restrict__ db5) {
+  const int lane = threadIdx.x & 31, j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= F4) return;   // whole warps
+  float s = 0.f, sb = 0.f;
+  for (int i = lane; i < n; i += 32) {
+    const float d = dz5[i];
+    s += d * fmaxf(z4[(int64_t)i * F4 + j], 0.f);
+    sb += d;
   }
-  if (j == 0) {
-    float s = 0.f;
-    for (int i = 0; i < n; ++i) s += dz5[i];
-    db5[0] = s;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+  }
+  if (lane == 0) {
+    dw5[j] = s;
+    if (j == 0) db5[0] = sb;
   }
 }
 
@@ -309,7 +349,7 @@ cudaError_t colsum(cudaStream_t st, const bf16* x, int64_t rows, int cols, float
   const int nb = (int)std::min<int64_t>(512, (rows + 255) / 256);
   const int64_t band = (rows + nb - 1) / nb;
   k_colsum_part<<<nb, 256, 0, st>>>(x, rows, cols, band, part);
-  k_sum_splits<<<1, 256, 0, st>>>(part, nb, cols, out);
+  sum_splits(st, part, nb, cols, out);
   return cudaGetLastError();
 }
 

@@ -263,7 +263,7 @@ cudaError_t backward(rbri_model_s* m, int n, const float* labels, float* loss_de
   cudaError_t e;
   cudaMemsetAsync(G, 0, sizeof(float) * QMASTER, s);
   k_bce_head<<<1, 1024, 0, s>>>(m->logit, labels, n, m->z4, m->params + QW5, m->dz5, m->dz4, loss_dev);
-  k_fc2_grad<<<1, F4, 0, s>>>(m->dz5, m->z4, n, G + QW5, G + QB5);
+  k_fc2_grad<<<F4 / 8, 256, 0, s>>>(m->dz5, m->z4, n, G + QW5, G + QB5);
   // fc1: dW4 = sum_i dz4[i] f[i], db4, df = dz4 W4^T
   if ((e = igemm_wgrad(s, F4, K4, n, Dense{m->dz4, n, F4, F4}, Dense{m->fb, n, K4, K4}, G + QW4, m->part))) return e;
   if ((e = colsum(s, m->dz4, n, F4, m->part, G + QB4))) return e;
@@ -273,7 +273,7 @@ cudaError_t backward(rbri_model_s* m, int n, const float* labels, float* loss_de
     return e;
   // rotation average and the last pool
   k_rot_mean_back<<<grid1((int64_t)n4 * K4), 256, 0, s>>>(df, n, m->da);
-  k_pool_relu_back<<<grid1((int64_t)n4 * PIX3 * C2), 256, 0, s>>>(m->da, m->i3, m->zd, n4, 7, 7, C2, m->dzA);
+  k_pool_relu_back<<<grid1((int64_t)n4 * PIX3 * C2 / 8), 256, 0, s>>>(m->da, m->i3, m->zd, n4, 7, 7, C2, m->dzA);
   // res2: zd = conv_d(rc) + a2
   const int64_t m2 = (int64_t)n4 * PIX3 * C2;
   if ((e = conv_back(m, s, n4, 7, C2, C2, m->dzA, m->rc, QWD, QBD, m->da))) return e;
@@ -281,7 +281,7 @@ cudaError_t backward(rbri_model_s* m, int n, const float* labels, float* loss_de
   if ((e = conv_back(m, s, n4, 7, C2, C2, m->dzB, m->a2, QWC, QBC, m->da))) return e;
   k_add_grad<<<grid1(m2), 256, 0, s>>>(m->da, m->dzA, m2);   // the skip path
   // conv2
-  k_pool_relu_back<<<grid1((int64_t)n4 * PIX2 * C2), 256, 0, s>>>(m->da, m->i2, m->z2, n4, 15, 15, C2, m->dzA);
+  k_pool_relu_back<<<grid1((int64_t)n4 * PIX2 * C2 / 8), 256, 0, s>>>(m->da, m->i2, m->z2, n4, 15, 15, C2, m->dzA);
   if ((e = conv_back(m, s, n4, 15, C1, C2, m->dzA, m->r1, QW2, QB2, m->da))) return e;
   // res1: r1 = relu(zb), zb = conv_b(ra) + a1
   const int64_t m1 = (int64_t)n4 * PIX2 * C1;
@@ -291,7 +291,7 @@ cudaError_t backward(rbri_model_s* m, int n, const float* labels, float* loss_de
   if ((e = conv_back(m, s, n4, 15, C1, C1, m->dzB, m->a1, QWA, QBA, m->da))) return e;
   k_add_grad<<<grid1(m1), 256, 0, s>>>(m->da, m->dzA, m1);   // the skip path
   // conv1 (no input gradient)
-  k_pool_relu_back<<<grid1((int64_t)n4 * PIX1 * C1), 256, 0, s>>>(m->da, m->i1, m->z1, n4, S31, S31, C1, m->dzA);
+  k_pool_relu_back<<<grid1((int64_t)n4 * PIX1 * C1 / 8), 256, 0, s>>>(m->da, m->i1, m->z1, n4, S31, S31, C1, m->dzA);
   if ((e = igemm_wgrad(s, C1, K1, n4 * PIX1, Dense{m->dzA, n4 * PIX1, C1, C1},
                        Conv1Rows{m->xr, n4, S31, S31, 3 * PIX1},
                        G + QW1, m->part)))
