@@ -418,10 +418,13 @@ k_contract_slot0(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, in
     }
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // warp sums in T (FP32 on the mixed path: GB300's FP64 pipe retires two
+  // operations per SM per clock, and FP64 shuffle trees here took most of
+  // the kernel's time), the eight warps' sums in FP64
 #pragma unroll
   for (int m = 0; m < NMONO; ++m) {
-    const double s0 = warp_sum((double)dc[m]), s1 = warp_sum((double)nq[m]);
-    if (lane == 0) { red[warp][m] = s0; red[warp][NMONO + m] = s1; }
+    const T s0 = warp_sum(dc[m]), s1 = warp_sum(nq[m]);
+    if (lane == 0) { red[warp][m] = (double)s0; red[warp][NMONO + m] = (double)s1; }
   }
   __syncthreads();
   if (threadIdx.x < 2 * NMONO) {

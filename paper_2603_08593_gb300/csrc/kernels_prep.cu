@@ -30,6 +30,24 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;  // valid on thread 0
 }
 
+// block_sum with the warp stage in T (FP32 on the mixed path: GB300 retires
+// two FP64 operations per SM per clock, so FP64 shuffle trees in every warp
+// dominated the kernels that sum per row) and the warps' sums in FP64
+template <int NT, typename T>
+__device__ __forceinline__ double block_sum_t(T v, double* red) {
+  v = warp_sum(v);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = (double)v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+  }
+  return s;  // valid on thread 0
+}
+
 __global__ void __launch_bounds__(256)
 k_sky_sum(const float* __restrict__ R, const float* __restrict__ S, const uint8_t* __restrict__ bad, int64_t npx,
           double* __restrict__ acc) {
@@ -142,7 +160,7 @@ k_moments(const uint8_t* __restrict__ mfit, const float* __restrict__ S, const d
     }
   }
   const double yt = 2.0 * y / (double)(H > 1 ? H - 1 : 1) - 1.0;
-  const double c = block_sum<256>((double)cnt, red);
+  const double c = block_sum_t<256>(cnt, red);
   if (threadIdx.x == 0 && rowflag) rowflag[(int64_t)ccd * rf_stride + y] = c > 0 ? 1 : 0;
   // every thread must take part in block_sum; branch on c only after the broadcast
   __shared__ double cb;
@@ -151,7 +169,7 @@ k_moments(const uint8_t* __restrict__ mfit, const float* __restrict__ S, const d
   if (cb == 0) return;
   if (mom_bb) {
     for (int a = 0; a <= DBB; ++a) {
-      const double s = block_sum<256>((double)pm[a], red);
+      const double s = block_sum_t<256>(pm[a], red);
       if (threadIdx.x == 0) {
         double yp = 1.0;
         for (int b = 0; a + b <= DBB; ++b) { atomicAdd(&mom_bb[ccd * bb_stride + mono_index(a, b)], s * yp); yp *= yt; }
@@ -159,7 +177,7 @@ k_moments(const uint8_t* __restrict__ mfit, const float* __restrict__ S, const d
     }
   }
   for (int a = 0; a <= DV; ++a) {
-    const double s = block_sum<256>((double)pv[a], red);
+    const double s = block_sum_t<256>(pv[a], red);
     if (threadIdx.x == 0) {
       double yp = 1.0;
       for (int b = 0; a + b <= DV; ++b) { atomicAdd(&mom_v[ccd * v_stride + mono_index(a, b)], s * yp); yp *= yt; }
