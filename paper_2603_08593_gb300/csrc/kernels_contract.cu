@@ -379,10 +379,12 @@ k_contract(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, int M, i
 
 // The two real bins packed in slot 0 (k = 0 and k = Nf/2, each with h = 1):
 //   g_{a,b}(u) += (1/Nf) sum_y yt^b [V_a(y,0) P(y-u_y,0) + (-1)^{u_x} V_a(y,Nf/2) P(y-u_y,Nf/2)]
-// One CTA per (job, lag u_y); FP32 per-thread partial sums over rows, FP64 block sums.
+// One CTA per (job, lag u_y, band of rows_per_band rows); FP32 per-thread
+// partial sums over rows, FP64 block sums, FP64 atomic adds.
 template <typename T, int DM>
 __global__ void __launch_bounds__(256)
-k_contract_slot0(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, int M, int Nf, int L, int rs) {
+k_contract_slot0(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, int M, int Nf, int L, int rs,
+                 int rows_per_band) {
   using T2 = c_t<T>;
   constexpr int NMONO = n_mono(DM);
   __shared__ double red[8][2 * NMONO];
@@ -400,7 +402,8 @@ k_contract_slot0(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, in
   T dc[NMONO], nq[NMONO];
 #pragma unroll
   for (int m = 0; m < NMONO; ++m) { dc[m] = 0; nq[m] = 0; }
-  for (int y = w + (int)threadIdx.x; y < H - w; y += blockDim.x) {
+  const int yb = w + (int)blockIdx.z * rows_per_band, ye = min(H - w, yb + rows_per_band);
+  for (int y = yb + (int)threadIdx.x; y < ye; y += blockDim.x) {
     if (!rowflag[y]) continue;
     const T2 p = P[(int64_t)(y - uy) * rs];   // slot 0 of row y - u_y (rs: row stride of the probe slab)
     const T yt = (T)y * ysc - (T)1;
@@ -443,6 +446,29 @@ k_contract_slot0(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, in
   }
 }
 
+static int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(sms, 1);
+}
+
+// Slot-0 sums of jobs job0 .. job0 + njobs - 1 (rs: row stride of the probe
+// slabs).  A launch of few jobs splits the rows into bands of at least 256
+// rows, for about four CTAs per SM.
+template <typename T, int DM>
+static cudaError_t slot0_T(const sfft_plan_s* p, int job0, int njobs, int rs, void* ws) {
+  const int H = p->d.H, w = (p->d.L - 1) / 2, nrow = std::max(1, H - 2 * w);
+  const int64_t per_band = (int64_t)njobs * max_uy<T>();
+  const int nb_want = (int)std::min<int64_t>((4 * (int64_t)sm_count() + per_band - 1) / per_band, 1 << 16);
+  const int rows = std::max(256, (nrow + nb_want - 1) / nb_want);
+  const int nb = (nrow + rows - 1) / rows;
+  k_contract_slot0<T, DM><<<dim3(njobs, max_uy<T>(), nb), 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, H, p->M,
+                                                                                p->Nf, p->d.L, rs, rows);
+  p->nlaunch += 1;
+  return cudaGetLastError();
+}
+
 template <typename T, int DM, int NS>
 static cudaError_t contract_T(const sfft_plan_s* p, int job0, int njobs, int rows_per_cta, void* ws) {
   constexpr int KT = kt_for<T, DM>();
@@ -451,6 +477,16 @@ static cudaError_t contract_T(const sfft_plan_s* p, int job0, int njobs, int row
   const size_t smem = 2 * sizeof(Stage<T, DM, KT, MU>) + 32 + sizeof(T) * L * L * n_mono(DM);
   auto kern = k_contract<T, DM, KT, NS>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // A launch of few jobs (one CCD's KB or b_K block is a single job) shortens
+  // its row bands until the grid gives every SM about three CTAs.  Each band
+  // ends with a lag DFT over its k-slots, so a band keeps at least 128 rows.
+  const int nk = (p->M + KT - 1) / KT;
+  const int64_t want = 3 * (int64_t)sm_count(), per_band = (int64_t)nk * njobs;
+  if (per_band * ((H + rows_per_cta - 1) / rows_per_cta) < want) {
+    const int nb_want = (int)((want + per_band - 1) / per_band);
+    const int rows = ((H + nb_want - 1) / nb_want + kChunk - 1) / kChunk * kChunk;
+    rows_per_cta = std::min(rows_per_cta, std::max(128, rows));
+  }
   const int nb = (H + rows_per_cta - 1) / rows_per_cta;
   // row bands vary slowest: the CTAs in flight share one band of the weight
   // spectra (read by every job), which then stays in L2 across the jobs
@@ -461,23 +497,18 @@ static cudaError_t contract_T(const sfft_plan_s* p, int job0, int njobs, int row
                                                                             (const c_t<T>*)p->twD, (const T*)p->ytab);
     p->nlaunch += 1;
   }
-  k_contract_slot0<T, DM><<<dim3(njobs, max_uy<T>()), 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, H, p->M,
-                                                                          p->Nf, L, p->M);
-  p->nlaunch += 1;
-  return cudaGetLastError();
+  return slot0_T<T, DM>(p, job0, njobs, p->M, ws);
 }
 
 cudaError_t launch_contract_slot0(const sfft_plan_s* p, int DM, int job0, int njobs, void* ws) {
   if (njobs <= 0) return cudaSuccess;
-  const dim3 grid(njobs, max_uy<float>());
+  const int rs = p->dl ? 16 : p->M;
   switch (DM) {
-    case 0: k_contract_slot0<float, 0><<<grid, 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, p->d.H, p->M, p->Nf, p->d.L, p->dl ? 16 : p->M); break;
-    case 2: k_contract_slot0<float, 2><<<grid, 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, p->d.H, p->M, p->Nf, p->d.L, p->dl ? 16 : p->M); break;
-    case 4: k_contract_slot0<float, 4><<<grid, 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, p->d.H, p->M, p->Nf, p->d.L, p->dl ? 16 : p->M); break;
+    case 0: return slot0_T<float, 0>(p, job0, njobs, rs, ws);
+    case 2: return slot0_T<float, 2>(p, job0, njobs, rs, ws);
+    case 4: return slot0_T<float, 4>(p, job0, njobs, rs, ws);
     default: return cudaErrorInvalidValue;
   }
-  p->nlaunch += 1;
-  return cudaGetLastError();
 }
 
 template <typename T, int NS>
