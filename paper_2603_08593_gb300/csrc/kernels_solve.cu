@@ -171,33 +171,39 @@ __global__ void k_cpr_expand(const double* __restrict__ x, double* __restrict__ 
   }
 }
 
-// scale = diag(A_s)^-1/2; Lf (lower) = D_s A_s D_s; status flags.  A_s is the
-// solved system: A itself (row stride N = Ns) or T A T^T (size Ns).
+// scale = diag(A_s)^-1/2 and the diagonal's status flags, a thread per row.
+// A_s is the solved system: A itself (row stride N = Ns) or T A T^T (size Ns).
+__global__ void k_chol_scale(const double* __restrict__ A, double* __restrict__ scale, int* __restrict__ status,
+                             int N, int Ns, CprMap m) {
+  const int ccd = blockIdx.y;
+  const double* a = A + ccd * (int64_t)N * N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Ns; i += gridDim.x * blockDim.x) {
+    const double d = cpr_entry(a, N, m, i, i);
+    if (!isfinite(d)) atomicOr(&status[ccd], 2);
+    else if (!(d > 0.0)) atomicOr(&status[ccd], 1);
+    scale[(int64_t)ccd * Ns + i] = d > 0.0 ? rsqrt(d) : 0.0;
+  }
+}
+
+// Lf (lower) = D_s A_s D_s with D_s = diag(scale): a CTA per row (strided),
+// a thread per column.  Two FP64 products per element; the reciprocal
+// square roots (a few dozen FP64 operations each on a pipe that retires
+// about two per SM per clock) are formed once per row by k_chol_scale.
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_chol_init(const double* __restrict__ A, T* __restrict__ Lf, double* __restrict__ scale,
+k_chol_init(const double* __restrict__ A, T* __restrict__ Lf, const double* __restrict__ scale,
             int* __restrict__ status, int N, int Ns, CprMap m) {
   const int ccd = blockIdx.y;
-  const int64_t NS2 = (int64_t)Ns * Ns;
   const double* a = A + ccd * (int64_t)N * N;
-  T* l = Lf + ccd * NS2;
-  double* s = scale + (int64_t)ccd * Ns;
-  if (blockIdx.x == 0) {
-    for (int i = threadIdx.x; i < Ns; i += blockDim.x) {
-      const double d = cpr_entry(a, N, m, i, i);
-      if (!isfinite(d)) atomicOr(&status[ccd], 2);
-      else if (!(d > 0.0)) atomicOr(&status[ccd], 1);
+  T* l = Lf + ccd * (int64_t)Ns * Ns;
+  const double* s = scale + (int64_t)ccd * Ns;
+  for (int i = blockIdx.x; i < Ns; i += gridDim.x) {
+    const double si = s[i];
+    for (int j = threadIdx.x; j <= i; j += blockDim.x) {
+      const double v = cpr_entry(a, N, m, i, j);
+      if (!isfinite(v)) atomicOr(&status[ccd], 2);
+      l[(int64_t)i * Ns + j] = (T)(v * si * s[j]);
     }
-  }
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < NS2; t += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t / Ns), j = (int)(t % Ns);
-    if (j > i) continue;
-    const double di = cpr_entry(a, N, m, i, i), dj = cpr_entry(a, N, m, j, j);
-    const double si = di > 0.0 ? rsqrt(di) : 0.0, sj = dj > 0.0 ? rsqrt(dj) : 0.0;
-    const double v = cpr_entry(a, N, m, i, j);
-    if (!isfinite(v)) atomicOr(&status[ccd], 2);
-    l[t] = (T)(v * si * sj);
-    if (i == j) s[i] = si;
   }
 }
 
@@ -760,8 +766,8 @@ static cudaError_t cholesky_T(const sfft_plan_s* p, const double* A, void* ws) {
   int* status = ws_at<int>(ws, p->status);
   T* dinv = ws_at<T>(ws, p->dinv);
   GridBar* bar = ws_at<GridBar>(ws, p->gbar);
-  dim3 gi(512, B);
-  k_chol_init<T><<<gi, 256, 0, p->stream>>>(A, Lf, scale, status, p->N, N, cpr_map(p));
+  k_chol_scale<<<dim3((N + 255) / 256, B), 256, 0, p->stream>>>(A, scale, status, p->N, N, cpr_map(p));
+  k_chol_init<T><<<dim3(std::min(N, 1024), B), 256, 0, p->stream>>>(A, Lf, scale, status, p->N, N, cpr_map(p));
   cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBar), p->stream);
   if (e != cudaSuccess) return e;
   // every CTA of the cooperative grid must be resident at once
@@ -773,7 +779,7 @@ static cudaError_t cholesky_T(const sfft_plan_s* p, const double* A, void* ws) {
   int spin = p->bar_spin_limit;
   void* args[] = {&Lf, &dinv, &status, &N, &B, &bar, &spin};
   e = launch_coop((const void*)k_chol_coop<T>, grid, p->stream, args);
-  p->nlaunch += 2;
+  p->nlaunch += 3;
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
