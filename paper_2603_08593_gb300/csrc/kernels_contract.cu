@@ -379,70 +379,82 @@ k_contract(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, int M, i
 
 // The two real bins packed in slot 0 (k = 0 and k = Nf/2, each with h = 1):
 //   g_{a,b}(u) += (1/Nf) sum_y yt^b [V_a(y,0) P(y-u_y,0) + (-1)^{u_x} V_a(y,Nf/2) P(y-u_y,Nf/2)]
-// One CTA per (job, lag u_y, band of rows_per_band rows); FP32 per-thread
-// partial sums over rows, FP64 block sums, FP64 atomic adds.
+// One CTA per (job, band of at most slot0_rows rows y).  The band's slot-0
+// values (probe rows y - u_y for every u_y of the job, weight rows y for
+// every exponent, row flags) are staged in shared memory once, so each
+// scattered 8- or 16-byte value is read from L2 once per band rather than
+// once per u_y.  Warp i takes u_y = uy_lo + i and lane l the rows
+// y = yb + l (mod 32): per-lane sums and the warp tree in T (FP32 on the
+// mixed path), FP64 atomic adds.
+template <typename T> constexpr int slot0_rows() { return sizeof(T) == 4 ? 512 : 256; }
+
 template <typename T, int DM>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(32 * max_uy<T>())
 k_contract_slot0(const CJob* __restrict__ jobs, char* __restrict__ ws, int H, int M, int Nf, int L, int rs,
                  int rows_per_band) {
   using T2 = c_t<T>;
-  constexpr int NMONO = n_mono(DM);
-  __shared__ double red[8][2 * NMONO];
+  constexpr int NMONO = n_mono(DM), MU = max_uy<T>(), RB = slot0_rows<T>();
+  __shared__ T2 ps[RB + MU - 1];
+  __shared__ T2 vs[DM + 1][RB];
+  __shared__ int fl[RB];
+  __shared__ double red[MU][2 * NMONO];
   const CJob job = jobs[blockIdx.x];
-  const int iu = blockIdx.y;
-  const int nuy = job.uy_hi - job.uy_lo + 1;
-  if (iu >= nuy) return;
-  const int uy = job.uy_lo + iu;
+  const int nuy = job.uy_hi - job.uy_lo + 1;   // at most MU (jobs are split by u_y)
   const int w = (L - 1) / 2;
+  const int yb = w + (int)blockIdx.y * rows_per_band, ye = min(H - w, yb + rows_per_band);
+  const int nr = ye - yb;                      // at most RB
   const int64_t HM = (int64_t)H * M;
   const T2* P = reinterpret_cast<const T2*>(ws + job.probe);
   const T2* V = reinterpret_cast<const T2*>(ws + job.wts);
   const int* rowflag = reinterpret_cast<const int*>(ws + job.rowflag);
+  // probe rows p0 .. p0 + np - 1 = yb - uy_hi .. ye - 1 - uy_lo (inside [0, H))
+  const int p0 = yb - job.uy_hi, np = nr + nuy - 1;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) ps[i] = P[(int64_t)(p0 + i) * rs];   // rs: probe row stride
+  for (int i = threadIdx.x; i < (DM + 1) * nr; i += blockDim.x) {
+    const int a = i / nr, r = i - a * nr;
+    vs[a][r] = V[a * HM + (int64_t)(yb + r) * M];
+  }
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) fl[i] = rowflag[yb + i];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const T ysc = (T)2 / (T)(H > 1 ? H - 1 : 1);
   T dc[NMONO], nq[NMONO];
 #pragma unroll
   for (int m = 0; m < NMONO; ++m) { dc[m] = 0; nq[m] = 0; }
-  const int yb = w + (int)blockIdx.z * rows_per_band, ye = min(H - w, yb + rows_per_band);
-  for (int y = yb + (int)threadIdx.x; y < ye; y += blockDim.x) {
-    if (!rowflag[y]) continue;
-    const T2 p = P[(int64_t)(y - uy) * rs];   // slot 0 of row y - u_y (rs: row stride of the probe slab)
-    const T yt = (T)y * ysc - (T)1;
+  if (warp < nuy) {
+    const int uy = job.uy_lo + warp;
+    for (int r = lane; r < nr; r += 32) {
+      if (!fl[r]) continue;
+      const int y = yb + r;
+      const T2 pv = ps[y - uy - p0];
+      const T yt = (T)y * ysc - (T)1;
 #pragma unroll
-    for (int a = 0; a <= DM; ++a) {
-      const T2 v = V[a * HM + (int64_t)y * M];
-      const T d0 = v.x * p.x, n0 = v.y * p.y;
-      T yp = 1;
+      for (int a = 0; a <= DM; ++a) {
+        const T2 v = vs[a][r];
+        const T d0 = v.x * pv.x, n0 = v.y * pv.y;
+        T yp = 1;
 #pragma unroll
-      for (int b = 0; a + b <= DM; ++b) {
-        dc[mono_index(a, b)] += yp * d0;
-        nq[mono_index(a, b)] += yp * n0;
-        yp *= yt;
+        for (int b = 0; a + b <= DM; ++b) {
+          dc[mono_index(a, b)] += yp * d0;
+          nq[mono_index(a, b)] += yp * n0;
+          yp *= yt;
+        }
       }
     }
   }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // warp sums in T (FP32 on the mixed path: GB300's FP64 pipe retires two
-  // operations per SM per clock, and FP64 shuffle trees here took most of
-  // the kernel's time), the eight warps' sums in FP64
 #pragma unroll
   for (int m = 0; m < NMONO; ++m) {
     const T s0 = warp_sum(dc[m]), s1 = warp_sum(nq[m]);
-    if (lane == 0) { red[warp][m] = (double)s0; red[warp][NMONO + m] = (double)s1; }
-  }
-  __syncthreads();
-  if (threadIdx.x < 2 * NMONO) {
-    double s = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i][threadIdx.x];
-    red[0][threadIdx.x] = s;   // each entry is read and rewritten by the same thread
+    if (lane == 0 && warp < nuy) { red[warp][m] = (double)s0; red[warp][NMONO + m] = (double)s1; }
   }
   __syncthreads();
   const double inv = 1.0 / (double)Nf;
   const int nux = job.ux_hi - job.ux_lo + 1;
-  for (int i = threadIdx.x; i < nux * NMONO; i += blockDim.x) {
-    const int m = i % NMONO, ux = job.ux_lo + i / NMONO;
-    const double v = red[0][m] + ((ux & 1) ? -red[0][NMONO + m] : red[0][NMONO + m]);
-    double* out = reinterpret_cast<double*>(ws + job.out);
-    atomicAdd(out + ((uy + w) * L + (ux + w)) * NMONO + m, v * inv);
+  double* out = reinterpret_cast<double*>(ws + job.out);
+  for (int i = threadIdx.x; i < nuy * nux * NMONO; i += blockDim.x) {
+    const int m = i % NMONO, t = i / NMONO, iu = t / nux, ux = job.ux_lo + t % nux;
+    const double v = red[iu][m] + ((ux & 1) ? -red[iu][NMONO + m] : red[iu][NMONO + m]);
+    atomicAdd(out + ((job.uy_lo + iu + w) * L + (ux + w)) * NMONO + m, v * inv);
   }
 }
 
@@ -454,16 +466,15 @@ static int sm_count() {
 }
 
 // Slot-0 sums of jobs job0 .. job0 + njobs - 1 (rs: row stride of the probe
-// slabs).  A launch of few jobs splits the rows into bands of at least 256
-// rows, for about four CTAs per SM.
+// slabs), in bands of at most slot0_rows rows; a launch of few jobs takes
+// shorter bands (at least 64 rows) for about four CTAs per SM.
 template <typename T, int DM>
 static cudaError_t slot0_T(const sfft_plan_s* p, int job0, int njobs, int rs, void* ws) {
   const int H = p->d.H, w = (p->d.L - 1) / 2, nrow = std::max(1, H - 2 * w);
-  const int64_t per_band = (int64_t)njobs * max_uy<T>();
-  const int nb_want = (int)std::min<int64_t>((4 * (int64_t)sm_count() + per_band - 1) / per_band, 1 << 16);
-  const int rows = std::max(256, (nrow + nb_want - 1) / nb_want);
+  const int nb_want = (int)std::min<int64_t>((4 * (int64_t)sm_count() + njobs - 1) / njobs, 1 << 16);
+  const int rows = std::min(slot0_rows<T>(), std::max(64, (nrow + nb_want - 1) / nb_want));
   const int nb = (nrow + rows - 1) / rows;
-  k_contract_slot0<T, DM><<<dim3(njobs, max_uy<T>(), nb), 256, 0, p->stream>>>(p->d_jobs + job0, (char*)ws, H, p->M,
+  k_contract_slot0<T, DM><<<dim3(njobs, nb), 32 * max_uy<T>(), 0, p->stream>>>(p->d_jobs + job0, (char*)ws, H, p->M,
                                                                                 p->Nf, p->d.L, rs, rows);
   p->nlaunch += 1;
   return cudaGetLastError();
