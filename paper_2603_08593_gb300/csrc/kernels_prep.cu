@@ -48,6 +48,11 @@ __device__ __forceinline__ double block_sum_t(T v, double* red) {
   return s;  // valid on thread 0
 }
 
+// Sums of R, S and the count over the good pixels, per CCD.  Where a CCD's
+// images start on 16-byte boundaries the pixels go in groups of four (float4
+// and uchar4 loads); the launch gives each thread at most 64 groups, so a
+// thread's FP32 partial sums cover at most 256 pixels before the FP64 block
+// sums.
 __global__ void __launch_bounds__(256)
 k_sky_sum(const float* __restrict__ R, const float* __restrict__ S, const uint8_t* __restrict__ bad, int64_t npx,
           double* __restrict__ acc) {
@@ -57,21 +62,38 @@ k_sky_sum(const float* __restrict__ R, const float* __restrict__ S, const uint8_
   const float* s = S + ccd * npx;
   const uint8_t* b = bad ? bad + ccd * npx : nullptr;
   float sr = 0.f, ss = 0.f;
-  double srd = 0.0, ssd = 0.0;
-  int cnt = 0, sub = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npx; i += (int64_t)gridDim.x * blockDim.x) {
-    const float rv = r[i], sv = s[i];
-    const bool g = (!b || b[i] == 0) && isfinite(rv) && isfinite(sv);
-    if (g) { sr += rv; ss += sv; ++cnt; ++sub; }
-    if (sub == 256) { srd += sr; ssd += ss; sr = ss = 0.f; sub = 0; }
+  int cnt = 0;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
+  const bool vec = ((reinterpret_cast<uintptr_t>(r) | reinterpret_cast<uintptr_t>(s)) & 15) == 0 &&
+                   (reinterpret_cast<uintptr_t>(b) & 3) == 0;
+  int64_t i0 = 0;
+  if (vec) {
+    const int64_t n4 = npx / 4;
+    const float4* r4 = reinterpret_cast<const float4*>(r);
+    const float4* s4 = reinterpret_cast<const float4*>(s);
+    const uchar4* b4 = reinterpret_cast<const uchar4*>(b);
+#pragma unroll 4
+    for (int64_t q = t0; q < n4; q += nt) {
+      const float4 rv = r4[q], sv = s4[q];
+      const uchar4 bv = b ? b4[q] : make_uchar4(0, 0, 0, 0);
+      const float ra[4] = {rv.x, rv.y, rv.z, rv.w}, sa[4] = {sv.x, sv.y, sv.z, sv.w};
+      const unsigned char ba[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (ba[k] == 0 && isfinite(ra[k]) && isfinite(sa[k])) { sr += ra[k]; ss += sa[k]; ++cnt; }
+    }
+    i0 = n4 * 4;
   }
-  srd += sr; ssd += ss;
-  double t0 = block_sum<256>(srd, red);
-  if (threadIdx.x == 0) atomicAdd(&acc[4 * ccd + 0], t0);
-  double t1 = block_sum<256>(ssd, red);
-  if (threadIdx.x == 0) atomicAdd(&acc[4 * ccd + 1], t1);
-  double t2 = block_sum<256>((double)cnt, red);
-  if (threadIdx.x == 0) atomicAdd(&acc[4 * ccd + 2], t2);
+  for (int64_t i = i0 + t0; i < npx; i += nt) {
+    const float rv = r[i], sv = s[i];
+    if ((!b || b[i] == 0) && isfinite(rv) && isfinite(sv)) { sr += rv; ss += sv; ++cnt; }
+  }
+  const double d0 = block_sum<256>((double)sr, red);
+  if (threadIdx.x == 0) atomicAdd(&acc[4 * ccd + 0], d0);
+  const double d1 = block_sum<256>((double)ss, red);
+  if (threadIdx.x == 0) atomicAdd(&acc[4 * ccd + 1], d1);
+  const double d2 = block_sum<256>((double)cnt, red);
+  if (threadIdx.x == 0) atomicAdd(&acc[4 * ccd + 2], d2);
 }
 
 __global__ void k_sky_final(const double* __restrict__ acc, double* __restrict__ sky, int batch) {
@@ -200,8 +222,14 @@ cudaError_t launch_sky(const sfft_plan_s* p, const float* R, const float* S, con
   double* acc = ws_at<double>(ws, p->skyacc);
   cudaMemsetAsync(acc, 0, sizeof(double) * 4 * B, p->stream);
   const int64_t npx = (int64_t)p->d.H * p->d.W;
-  dim3 grid(grid_for(npx, 256 * 16, 296), B);
-  k_sky_sum<<<grid, 256, 0, p->stream>>>(R, S, bad, npx, acc);
+  // at least four CTAs per SM, and at most 64 groups of four pixels per thread
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t per_cta = 256 * 64 * 4;
+  const int gx = (int)std::min<int64_t>(std::max<int64_t>(4 * (int64_t)std::max(sms, 1), (npx + per_cta - 1) / per_cta),
+                                        1 << 20);
+  k_sky_sum<<<dim3(gx, B), 256, 0, p->stream>>>(R, S, bad, npx, acc);
   k_sky_final<<<(B + 127) / 128, 128, 0, p->stream>>>(acc, sky, B);
   p->nlaunch += 2;
   return cudaGetLastError();
