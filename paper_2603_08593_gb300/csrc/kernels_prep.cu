@@ -153,57 +153,141 @@ k_erode_cols(const uint8_t* __restrict__ gh, uint8_t* __restrict__ mfit, int H, 
 }
 
 // one block per (row, ccd).  mom_bb[mono(a,b)] for a+b <= DBB, mom_v[mono(a,b)] for a+b <= DV.
+// Per CCD the background moments sum_x M_fit xt^a yt^b (a + b <= DBB) and
+// sum_x M_fit xt^a yt^b v(x) (a + b <= DV), with yt^b factored out of each
+// row.  A CTA takes kMomRows consecutive rows, a warp per row at a time.  A
+// lane sums its pixels in groups of four (float4 / uchar4 loads where the row
+// is 16-byte aligned): each group's sum in T, added to the lane's T sums, then
+// a warp tree in T gives the row's sums.  The row's FP64 contributions are
+// added over the CTA's rows (fixed order) and then atomically to the CCD's
+// moments, so each moment takes H / kMomRows atomic adds per CCD instead of H.
+constexpr int kMomRows = 16;
+
+template <typename T>
+__device__ __forceinline__ void load4(const T* p, T (&v)[4]);
+template <>
+__device__ __forceinline__ void load4<float>(const float* p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+template <>
+__device__ __forceinline__ void load4<double>(const double* p, double (&v)[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_moments(const uint8_t* __restrict__ mfit, const float* __restrict__ S, const double* __restrict__ sky,
           const T* __restrict__ E, int H, int W, int DBB, int DV, double* __restrict__ mom_bb, int64_t bb_stride,
           double* __restrict__ mom_v, int64_t v_stride, int* __restrict__ rowflag, int rf_stride) {
-  __shared__ double red[8];
-  const int y = blockIdx.x, ccd = blockIdx.y;
-  const int64_t row = ((int64_t)ccd * H + y) * W;
+  constexpr int NBB = n_mono(kMaxWeightDeg), NV = n_mono(kMaxD);
+  __shared__ double part[8][NBB + NV];
+  const int ccd = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const T sS = S ? (T)sky[2 * ccd + 1] : (T)0;
   const T xs = (T)2 / (T)(W > 1 ? W - 1 : 1);
-  T pm[kMaxWeightDeg + 1] = {0, 0, 0, 0, 0};
-  T pv[kMaxD + 1] = {0, 0, 0};
-  int cnt = 0;
-  for (int x = threadIdx.x; x < W; x += blockDim.x) {
-    if (!mfit[row + x]) continue;
-    ++cnt;
-    const T xt = (T)x * xs - (T)1;
-    T v = 0;
-    if (S) v = (T)S[row + x] - sS;
-    else if (E) v = E[row + x];
-    T pw = 1;
-#pragma unroll
-    for (int a = 0; a <= kMaxWeightDeg; ++a) {
-      if (a <= DBB) pm[a] += pw;
-      if (a <= kMaxD && a <= DV) pv[a] += pw * v;
-      pw *= xt;
-    }
-  }
-  const double yt = 2.0 * y / (double)(H > 1 ? H - 1 : 1) - 1.0;
-  const double c = block_sum_t<256>(cnt, red);
-  if (threadIdx.x == 0 && rowflag) rowflag[(int64_t)ccd * rf_stride + y] = c > 0 ? 1 : 0;
-  // every thread must take part in block_sum; branch on c only after the broadcast
-  __shared__ double cb;
-  if (threadIdx.x == 0) cb = c;
+  const double ysc = 2.0 / (double)(H > 1 ? H - 1 : 1);
+  // part[w]: warp w's rows, FP64, added to by its lane 0
+  for (int i = threadIdx.x; i < 8 * (NBB + NV); i += blockDim.x) (&part[0][0])[i] = 0.0;
   __syncthreads();
-  if (cb == 0) return;
-  if (mom_bb) {
-    for (int a = 0; a <= DBB; ++a) {
-      const double s = block_sum_t<256>(pm[a], red);
-      if (threadIdx.x == 0) {
+  const int y_end = min(H, ((int)blockIdx.x + 1) * kMomRows);
+  for (int y = (int)blockIdx.x * kMomRows + warp; y < y_end; y += 8) {
+    const int64_t row = ((int64_t)ccd * H + y) * W;
+    const uint8_t* mr = mfit + row;
+    const float* sr = S ? S + row : nullptr;
+    const T* er = E ? E + row : nullptr;
+    T pm[kMaxWeightDeg + 1] = {0, 0, 0, 0, 0};
+    T pv[kMaxD + 1] = {0, 0, 0};
+    int cnt = 0;
+    // adds the pixels of one group (mk: in the fit mask, vk: S - s_S or e)
+    auto add_group = [&](const int x0, const bool (&mk)[4], const T (&vk)[4], int n) {
+      T gm[kMaxWeightDeg + 1] = {0, 0, 0, 0, 0};
+      T gv[kMaxD + 1] = {0, 0, 0};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (k >= n || !mk[k]) continue;
+        ++cnt;
+        const T xt = (T)(x0 + k) * xs - (T)1;
+        T pw = 1;
+#pragma unroll
+        for (int a = 0; a <= kMaxWeightDeg; ++a) {
+          gm[a] += pw;
+          if (a <= kMaxD) gv[a] += pw * vk[k];
+          pw *= xt;
+        }
+      }
+#pragma unroll
+      for (int a = 0; a <= kMaxWeightDeg; ++a) pm[a] += gm[a];
+#pragma unroll
+      for (int a = 0; a <= kMaxD; ++a) pv[a] += gv[a];
+    };
+    const bool vec = (W & 3) == 0 && (reinterpret_cast<uintptr_t>(mr) & 3) == 0 &&
+                     (reinterpret_cast<uintptr_t>(sr) & 15) == 0 && (reinterpret_cast<uintptr_t>(er) & 15) == 0;
+    if (vec) {
+#pragma unroll 4
+      for (int x0 = 4 * lane; x0 < W; x0 += 128) {
+        const uchar4 m4 = *reinterpret_cast<const uchar4*>(mr + x0);
+        const bool mk[4] = {m4.x != 0, m4.y != 0, m4.z != 0, m4.w != 0};
+        T vk[4] = {0, 0, 0, 0};
+        if (sr) {
+          float f[4];
+          load4<float>(sr + x0, f);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) vk[k] = (T)f[k] - sS;
+        } else if (er) {
+          load4<T>(er + x0, vk);
+        }
+        add_group(x0, mk, vk, 4);
+      }
+    } else {
+      for (int x0 = 4 * lane; x0 < W; x0 += 128) {
+        const int n = min(4, W - x0);
+        bool mk[4];
+        T vk[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          mk[k] = k < n && mr[x0 + k] != 0;
+          vk[k] = k < n ? (sr ? (T)sr[x0 + k] - sS : (er ? er[x0 + k] : (T)0)) : (T)0;
+        }
+        add_group(x0, mk, vk, n);
+      }
+    }
+    cnt = warp_sum(cnt);
+#pragma unroll
+    for (int a = 0; a <= kMaxWeightDeg; ++a) pm[a] = warp_sum(pm[a]);
+#pragma unroll
+    for (int a = 0; a <= kMaxD; ++a) pv[a] = warp_sum(pv[a]);
+    if (lane == 0) {
+      if (rowflag) rowflag[(int64_t)ccd * rf_stride + y] = cnt > 0 ? 1 : 0;
+      const double yt = (double)y * ysc - 1.0;
+#pragma unroll
+      for (int a = 0; a <= kMaxWeightDeg; ++a) {
         double yp = 1.0;
-        for (int b = 0; a + b <= DBB; ++b) { atomicAdd(&mom_bb[ccd * bb_stride + mono_index(a, b)], s * yp); yp *= yt; }
+#pragma unroll
+        for (int b = 0; a + b <= kMaxWeightDeg; ++b) {
+          if (a + b <= DBB) part[warp][mono_index(a, b)] += (double)pm[a] * yp;
+          yp *= yt;
+        }
+      }
+#pragma unroll
+      for (int a = 0; a <= kMaxD; ++a) {
+        double yp = 1.0;
+#pragma unroll
+        for (int b = 0; a + b <= kMaxD; ++b) {
+          if (a + b <= DV) part[warp][NBB + mono_index(a, b)] += (double)pv[a] * yp;
+          yp *= yt;
+        }
       }
     }
   }
-  for (int a = 0; a <= DV; ++a) {
-    const double s = block_sum_t<256>(pv[a], red);
-    if (threadIdx.x == 0) {
-      double yp = 1.0;
-      for (int b = 0; a + b <= DV; ++b) { atomicAdd(&mom_v[ccd * v_stride + mono_index(a, b)], s * yp); yp *= yt; }
-    }
+  __syncthreads();
+  const int nbb = mom_bb ? n_mono(DBB) : 0, nv = n_mono(DV);
+  if (threadIdx.x < nbb + nv) {
+    const int i = threadIdx.x < nbb ? threadIdx.x : NBB + (threadIdx.x - nbb);
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += part[w][i];
+    if (threadIdx.x < nbb) atomicAdd(&mom_bb[ccd * bb_stride + threadIdx.x], s);
+    else atomicAdd(&mom_v[ccd * v_stride + (threadIdx.x - nbb)], s);
   }
 }
 
@@ -263,7 +347,7 @@ static cudaError_t moments_T(const sfft_plan_s* p, const float* S, const void* e
   const int H = p->d.H, W = p->d.W, B = p->d.batch;
   const uint8_t* mfit = ws_at<uint8_t>(ws, p->mfit);
   const double* sky = ws_at<double>(ws, p->sky);
-  dim3 g(H, B);
+  dim3 g((H + kMomRows - 1) / kMomRows, B);
   if (!resid) {
     double* bb = ws_at<double>(ws, p->mom_bb);
     double* bv = ws_at<double>(ws, p->mom_b);
