@@ -489,13 +489,21 @@ static cudaError_t contract_T(const sfft_plan_s* p, int job0, int njobs, int row
   auto kern = k_contract<T, DM, KT, NS>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   // A launch of few jobs (one CCD's KB or b_K block is a single job) shortens
-  // its row bands until the grid gives every SM about three CTAs.  Each band
-  // ends with a lag DFT over its k-slots, so a band keeps at least 128 rows.
+  // its row bands until its CTAs fill the resident slots of the SMs: as many
+  // bands as one wave holds, so that no CTA starts after the others finish.
+  // Each band ends with a lag DFT over its k-slots, so a band keeps at least
+  // 128 rows.
   const int nk = (p->M + KT - 1) / KT;
-  const int64_t want = 3 * (int64_t)sm_count(), per_band = (int64_t)nk * njobs;
-  if (per_band * ((H + rows_per_cta - 1) / rows_per_cta) < want) {
-    const int nb_want = (int)((want + per_band - 1) / per_band);
-    const int rows = ((H + nb_want - 1) / nb_want + kChunk - 1) / kChunk * kChunk;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, cta_threads<T, DM, KT, NS>(), smem) != cudaSuccess) {
+    (void)cudaGetLastError();   // a failed query leaves no error for the launches below to report
+    occ = 1;
+  }
+  occ = std::max(occ, 1);
+  const int64_t slots = (int64_t)occ * sm_count(), per_band = (int64_t)nk * njobs;
+  if (per_band * ((H + rows_per_cta - 1) / rows_per_cta) < slots) {
+    const int nb_fit = (int)std::max<int64_t>(1, slots / per_band);   // rounding rows up keeps the count <= this
+    const int rows = ((H + nb_fit - 1) / nb_fit + kChunk - 1) / kChunk * kChunk;
     rows_per_cta = std::min(rows_per_cta, std::max(128, rows));
   }
   const int nb = (H + rows_per_cta - 1) / rows_per_cta;
