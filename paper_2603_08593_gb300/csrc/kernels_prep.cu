@@ -161,7 +161,7 @@ k_erode_cols(const uint8_t* __restrict__ gh, uint8_t* __restrict__ mfit, int H, 
 // a warp tree in T gives the row's sums.  The row's FP64 contributions are
 // added over the CTA's rows (fixed order) and then atomically to the CCD's
 // moments, so each moment takes H / kMomRows atomic adds per CCD instead of H.
-constexpr int kMomRows = 16;
+constexpr int kMomRows = 8;
 
 template <typename T>
 __device__ __forceinline__ void load4(const T* p, T (&v)[4]);

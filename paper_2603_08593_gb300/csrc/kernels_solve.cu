@@ -773,9 +773,10 @@ static cudaError_t cholesky_T(const sfft_plan_s* p, const double* A, void* ws) {
   // every CTA of the cooperative grid must be resident at once
   const int T0 = (N - NBK + NBK - 1) / NBK;
   const int want = std::max(B, B + B * std::max(T0 * (T0 + 1) / 2 - 1, 1) * (NBK / PRW));
-  // FP32: two CTAs per SM shorten each block step's pieces (0.65 against 0.69 ms
-  // for the solve phase; one per SM stays better for the FP64 pipe)
-  const int grid = coop_grid((const void*)k_chol_coop<T>, want, B, sizeof(T) == 4 ? 2 : 1);
+  // FP32: three CTAs per SM shorten each block step's pieces (solve phase
+  // 0.622 ms, against 0.637 with two and 0.69 with one); one per SM stays
+  // better for the FP64 pipe
+  const int grid = coop_grid((const void*)k_chol_coop<T>, want, B, sizeof(T) == 4 ? 3 : 1);
   int spin = p->bar_spin_limit;
   void* args[] = {&Lf, &dinv, &status, &N, &B, &bar, &spin};
   e = launch_coop((const void*)k_chol_coop<T>, grid, p->stream, args);
