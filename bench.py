@@ -44,7 +44,7 @@ KK_TRAFFIC = {
     "kernels_contract_tc.cu": (None, ""),                      # mma.sync kernel (--mma-sync-contract)
     "kernels_contract_umma.cu": (9.975e9, "0d3c235754a7a213"),  # tcgen05, one lane per (d, u_y) pair
     # tcgen05, one lane per difference (default)
-    "kernels_contract_dlane.cu": (8.786e9, "3b64716d63df8ddd"),
+    "kernels_contract_dlane.cu": (8.786e9, "a0e1779911e29c9d"),
 }
 PHASES = ("prep", "fft_weights", "fft_prod", "contract_kk", "contract_rk", "scatter", "solve", "apply", "lag_dft")
 

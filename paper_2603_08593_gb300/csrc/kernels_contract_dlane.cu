@@ -26,7 +26,7 @@
 // over all weight rows of the band; its 2 x NU accumulators (32 FP32 columns
 // each) stay in tensor memory and go to an HBM buffer C[k][d][u_y][32] at the
 // end.  k_lag_dft (kernels_lag_dft.cu) then forms the lags u_x of every
-// (d, u_y) pair, summing the k-slots in FP32 runs of 16 and FP64 across runs.
+// (d, u_y) pair, with FP32 sums within a warp and FP64 across its warps.
 //
 // Roles (704 threads, one CTA per SM):
 //   warps 0-15 A producers: lane l of warp w is difference 32 (w % 4) + l of
