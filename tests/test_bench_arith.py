@@ -52,5 +52,20 @@ def test_decam_contraction_work(bench):
 
 def test_tf32_peak_from_measured_bf16(bench):
     import json
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    peaks, src = bench.measured_peaks()
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        assert src == "measured"
+        assert peaks["bf16_tflops_sustained"] == json.load(open(path))["bf16_tflops_sustained"]
+    else:
+        assert src == "fallback" and peaks == bench.FALLBACK_PEAKS
     assert bench.tf32_peak_tflops(sustained=True) == pytest.approx(peaks["bf16_tflops_sustained"] * 1.1 / 2.25)
+
+
+def test_peaks_fall_back_without_measured_file(bench, monkeypatch, tmp_path):
+    """Without MEASURED_PEAKS.json the roofline denominators are the fallback
+    figures, labelled as such."""
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    peaks, src = bench.measured_peaks()
+    assert src == "fallback" and peaks["hbm_gbs"] == 6800.0
+    assert bench.tf32_peak_tflops(sustained=True) == pytest.approx(1700.0 * 1.1 / 2.25)
